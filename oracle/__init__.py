@@ -1,0 +1,43 @@
+"""FP64 CPU oracle for the Eulerian non-Newtonian time step of Izbassarov et al.,
+"Computational modeling of multiphase viscoelastic and elastoviscoplastic flows"
+(arXiv 1803.09563).
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously-correct
+restatement of the paper's discrete method that the CUDA path is checked against.
+It is imported only by ``tests/``, by ``__graft_entry__.smoke()`` and by the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``.  The product path
+(``paper_1803_09563_gb300``) never imports, links or executes anything here, and
+nothing here imports the product path.
+
+Everything is numpy float64, vectorised over whole arrays with no blocking or
+fusion.  Library primitives used as steps: ``numpy.fft`` (the FFTs of the fast
+Poisson solver).  Each function cites the section / equation / table of the paper
+it restates.  Where the paper is silent the reading taken is stated in the
+docstring ("Reading n"); the same readings are listed in the design notes.
+
+Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
+  grid shifts, centre velocity, velocity gradient ... pinned (brute force, closed forms)
+  WENO5 (Sec. 3.1) ................................. pinned (textbook 5th-order formula,
+                                                     polynomial exactness, ENO switch,
+                                                     convergence order)
+  closures (Table 1), stress RHS (Eq. SRM2) ........ pinned (start-up / oscillatory
+                                                     shear closed forms, Saramito yield
+                                                     time, steady yielded shear)
+  momentum RHS (Eq. NS-num1) ....................... pinned (Taylor-Green decay order,
+                                                     steady Oldroyd-B Poiseuille)
+  Poisson solve + projection (Eqs. NS-num2/3) ...... pinned (sine modes, sparse direct
+                                                     solve, divergence <= 1e-12)
+  RK3 constants (Eq. RK) ........................... pinned (3rd-order convergence on
+                                                     a linear ODE closed form)
+  level set (Eqs. ls-adv, normal, curv, reinit) .... pinned (translation, sphere
+                                                     curvature, Heaviside volume)
+  AB2 (Eqs. ab2tau, ab2) ........................... pinned (2nd-order convergence)
+"""
+
+from .grid import Grid, at  # noqa: F401
+from .weno import hj_weno5, weno5_derivative  # noqa: F401
+from .models import Params, closure, tau_from_B, rt_local  # noqa: F401
+from .stress import centre_velocity, velocity_gradient, stress_rhs  # noqa: F401
+from .momentum import advection, laplacian, div_tau, grad_p, momentum_rhs_n  # noqa: F401
+from .poisson import divergence, eigenvalues, solve_poisson, project  # noqa: F401
+from .step import State, rk3_step, rk3_substep, RK3_ALPHA, RK3_ZETA, RK3_XI  # noqa: F401

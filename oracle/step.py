@@ -1,0 +1,112 @@
+"""Low-storage RK3 time step (Sec. 3.3.1, Eqs. RK-rt, NS-num1, rk3tau, rk3, NS-num2,
+NS-num3, RK).  TEST INFRASTRUCTURE ONLY.
+
+One step advances (u, p, B) from t^n to t^n + dt in three substeps k = 1, 2, 3:
+
+  B^k  = B^{k-1} + dt (zeta^k RT^{k-1} + xi^k RT^{k-2})                (rk3tau)
+  u*   = u^{k-1} + dt [zeta^k N^{k-1} + xi^k N^{k-2} - 2 alpha^k grad p^{k-1}
+                       + alpha^k (div tau^k + div tau^{k-1})]          (NS-num1, rk3)
+  lap psi^k = div u* / (2 alpha^k dt);  p^k = p^{k-1} + psi^k;
+  u^k  = u* - 2 alpha^k dt grad psi^k                                  (NS-num2, NS-num3)
+
+with N = -div(uu) + div[mu_s(grad u + grad u^T)] + f.  Reading 3: the paper writes
+the viscous term with weights alpha^k at levels k and k-1, which would need an
+implicit solve it never describes; the viscous term is taken explicitly with the
+advective weights (zeta^k + xi^k = 2 alpha^k for every k, so the total weight per
+substep is unchanged), while div(tau) keeps alpha^k at levels k and k-1 because
+B^k is known before u* is formed.  The body force f carries the same weights.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .models import tau_from_B
+from .momentum import div_tau, grad_p, momentum_rhs_n
+from .poisson import project
+from .stress import stress_rhs
+
+# Eq. RK
+RK3_ALPHA = (4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0)
+RK3_ZETA = (8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0)
+RK3_XI = (0.0, -17.0 / 60.0, -5.0 / 12.0)
+
+
+@dataclass
+class State:
+    """Prognostic fields on the staggered grid plus the RK3 history terms."""
+    U: np.ndarray
+    V: np.ndarray
+    W: np.ndarray
+    p: np.ndarray
+    B: list
+    RT_hist: list = field(default=None)
+    N_hist: tuple = field(default=None)
+    t: float = 0.0
+    nstep: int = 0
+    psi: np.ndarray = field(default=None)
+
+    @staticmethod
+    def rest(g, U=None, V=None, W=None):
+        """Velocity as given (zero if None), p = 0 and B = I (tau = 0)."""
+        z = g.zeros
+        B = [np.ones(g.shape) if d else np.zeros(g.shape)
+             for d in (True, False, False, True, False, True)]
+        return State(U=z() if U is None else np.array(U, dtype=float),
+                     V=z() if V is None else np.array(V, dtype=float),
+                     W=z() if W is None else np.array(W, dtype=float),
+                     p=z(), B=B)
+
+    def copy(self):
+        cp = lambda a: None if a is None else np.array(a, copy=True)
+        cl = lambda l: None if l is None else [np.array(a, copy=True) for a in l]
+        return State(cp(self.U), cp(self.V), cp(self.W), cp(self.p), cl(self.B),
+                     cl(self.RT_hist), None if self.N_hist is None else tuple(cl(self.N_hist)),
+                     self.t, self.nstep, cp(self.psi))
+
+
+def rk3_substep(s, k, dt, g, prm, force=None):
+    """Substep k (0-based index into Eq. RK) of the RK3 scheme; returns a new State."""
+    alpha, zeta, xi = RK3_ALPHA[k], RK3_ZETA[k], RK3_XI[k]
+    has_stress = prm.model != 'newtonian'
+    # stress update, Eq. rk3tau with RT of Eq. RK-rt
+    if has_stress:
+        RT = stress_rhs(s.U, s.V, s.W, s.B, g, prm)
+        Bn = []
+        for c in range(6):
+            inc = zeta * RT[c]
+            if xi != 0.0:
+                inc = inc + xi * s.RT_hist[c]
+            Bn.append(s.B[c] + dt * inc)
+    else:
+        RT, Bn = None, [b.copy() for b in s.B]
+    # momentum predictor, Eqs. NS-num1 and rk3
+    N = momentum_rhs_n(s.U, s.V, s.W, g, prm.mu_s, force)
+    gp = grad_p(s.p, g)
+    if has_stress:
+        dto = div_tau(tau_from_B(s.B, prm), g)
+        dtn = div_tau(tau_from_B(Bn, prm), g)
+    vel = (s.U, s.V, s.W)
+    star = []
+    for d in range(3):
+        inc = zeta * N[d]
+        if xi != 0.0:
+            inc = inc + xi * s.N_hist[d]
+        inc = inc - 2.0 * alpha * gp[d]
+        if has_stress:
+            inc = inc + alpha * (dtn[d] + dto[d])
+        star.append(vel[d] + dt * inc)
+    if g.walls:
+        star[1][:, g.ny - 1, :] = 0.0
+    # projection, Eqs. NS-num2 and NS-num3
+    U, V, W, psi = project(star[0], star[1], star[2], g, 2.0 * alpha * dt)
+    return State(U=U, V=V, W=W, p=s.p + psi, B=Bn, RT_hist=RT, N_hist=N,
+                 t=s.t + (alpha * 2.0) * dt, nstep=s.nstep, psi=psi)
+
+
+def rk3_step(s, dt, g, prm, force=None):
+    """One full RK3 step (three substeps)."""
+    for k in range(3):
+        s = rk3_substep(s, k, dt, g, prm, force)
+    s.nstep += 1
+    return s

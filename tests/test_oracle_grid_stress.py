@@ -1,0 +1,154 @@
+"""Pins for the oracle's staggered-grid operators: centre velocity, velocity
+gradient (Reading 5), stress-RHS assembly (Eqs. rt / RK-rt) and the momentum
+operators (Eq. NS-num1)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.models import rt_local, Params
+from paper_1803_09563_gb300 import inputs
+
+
+def box(nx=12, ny=10, nz=8, walls=False):
+    ly = 2.0 if walls else 2 * np.pi
+    return oracle.Grid(nx, ny, nz, 2 * np.pi, ly, 2 * np.pi, walls)
+
+
+def test_velocity_gradient_closed_forms():
+    """u = (sin y + sin z + sin x, ...): every entry L_ij = du_i/dx_j of the
+    discrete gradient matches the closed form of its stencil -- a face difference
+    for i = j (factor sin(h/2)/(h/2)), a central difference of centre values for
+    i != j (factor sin(h)/h)."""
+    g = box(16, 12, 10)
+    xc, yc, zc, xf, yf, zf = g.xc(), g.yc(), g.zc(), g.xf(), g.yf(), g.zf()
+    a = np.array([[1.0, 2.0, 3.0], [0.5, 1.5, -1.0], [-2.0, 0.7, 1.1]])
+    # u_i = a_ix sin(x) + a_iy sin(y) + a_iz sin(z), each at the face of component i
+    U = a[0, 0] * np.sin(xf) + a[0, 1] * np.sin(yc) + a[0, 2] * np.sin(zc) + 0 * xf * yc * zc
+    V = a[1, 0] * np.sin(xc) + a[1, 1] * np.sin(yf) + a[1, 2] * np.sin(zc) + 0 * xc * yf * zc
+    W = a[2, 0] * np.sin(xc) + a[2, 1] * np.sin(yc) + a[2, 2] * np.sin(zf) + 0 * xc * yc * zf
+    L = oracle.velocity_gradient(U, V, W, g)
+    h = (g.dx, g.dy, g.dz)
+    cc = (xc, yc, zc)
+    for i in range(3):
+        for j in range(3):
+            fac = np.sin(h[j] / 2) / (h[j] / 2) if i == j else np.sin(h[j]) / h[j]
+            ref = a[i, j] * np.cos(cc[j]) * fac
+            np.testing.assert_allclose(L[i][j], np.broadcast_to(ref, g.shape), atol=1e-12)
+
+
+def test_stress_rhs_uses_L_not_its_transpose():
+    """With a uniform B the advection vanishes exactly and the assembled RT equals
+    the pointwise source with the closed-form gradient; a simple shear u = sin(y)
+    must load tau_xx (upper-convected), not tau_yy."""
+    g = box(8, 16, 6)
+    U = np.broadcast_to(np.sin(g.yc()), g.shape).copy()
+    V, W = g.zeros(), g.zeros()
+    prm = Params.from_groups('oldroyd_b', Re=1.0, Wi=1.0, beta=0.5)
+    B0 = [1.0, 0.2, 0.0, 1.0, 0.0, 1.0]
+    B = [np.full(g.shape, b) for b in B0]
+    rt = oracle.stress_rhs(U, V, W, B, g, prm)
+    Lxy = np.cos(g.yc()) * np.sin(g.dy) / g.dy
+    # d Bxx/dt = 2 Lxy Bxy ; d Byy/dt = 0 ; d Bxy/dt = Lxy Byy - Bxy/lam
+    np.testing.assert_allclose(rt[0], np.broadcast_to(2 * Lxy * 0.2, g.shape), atol=1e-13)
+    np.testing.assert_allclose(rt[3], 0.0, atol=1e-14)
+    np.testing.assert_allclose(rt[1], np.broadcast_to(Lxy * 1.0 - 0.2, g.shape), atol=1e-13)
+
+
+def _translate_one_period(axis, n):
+    shape = {'x': (n, 4, 4), 'y': (4, n, 4), 'z': (4, 4, n)}[axis]
+    g = oracle.Grid(*shape, 2 * np.pi, 2 * np.pi, 2 * np.pi)
+    c = -1.0 if axis == 'y' else 1.0
+    U, V, W = g.zeros(), g.zeros(), g.zeros()
+    {'x': U, 'y': V, 'z': W}[axis][...] = c
+    s = {'x': g.xc(), 'y': g.yc(), 'z': g.zc()}[axis]
+    prm = Params('oldroyd_b', mu_s=0.0, mu_p=0.0, lam=1e30)
+    B = [np.ones(g.shape) if d else np.zeros(g.shape) for d in (1, 0, 0, 1, 0, 1)]
+    B[0] = np.broadcast_to(1.0 + 0.1 * np.sin(s), g.shape).copy()
+    B0 = B[0].copy()
+    nsteps = 5 * n
+    dt = 2 * np.pi / nsteps
+    hist = None
+    for _ in range(nsteps):
+        for k in range(3):
+            rt = oracle.stress_rhs(U, V, W, B, g, prm)
+            B = [B[q] + dt * (oracle.RK3_ZETA[k] * rt[q]
+                              + (oracle.RK3_XI[k] * hist[q] if k else 0.0)) for q in range(6)]
+            hist = rt
+    assert np.abs(B[3] - 1.0).max() == 0.0
+    return np.abs(B[0] - B0).max()
+
+
+@pytest.mark.parametrize("axis", ["x", "y", "z"])
+def test_pure_advection_translates_and_returns(axis):
+    """Uniform velocity along one axis, B_xx = 1 + 0.1 sin(s) and no relaxation
+    (lambda huge): one period of the RK3-WENO5 update returns B_xx to its start.
+    The error falls at least 8x per refinement (CFL fixed) -- a downwind
+    (unstable) or low-order scheme fails this."""
+    e32 = _translate_one_period(axis, 32)
+    e64 = _translate_one_period(axis, 64)
+    assert e32 < 5e-5 and e64 < e32 / 8.0, (e32, e64)
+
+
+def test_momentum_advection_of_uniform_flow_is_zero_and_laplacian_exact_on_modes():
+    g = box(12, 10, 8)
+    U = np.full(g.shape, 0.7)
+    V = np.full(g.shape, -0.3)
+    W = np.full(g.shape, 0.2)
+    A = oracle.advection(U, V, W, g)
+    for a in A:
+        assert np.abs(a).max() < 1e-14
+    # Laplacian of sin(2x) at x-faces: -(2 - 2cos(2h))/h^2 sin(2x)
+    F = np.broadcast_to(np.sin(2 * g.xf()), g.shape).copy()
+    lap = oracle.laplacian(F, g, 'u')
+    ref = -(2 - 2 * np.cos(2 * g.dx)) / g.dx ** 2 * F
+    np.testing.assert_allclose(lap, ref, atol=1e-12)
+
+
+def test_advection_matches_conservative_form_for_a_shear_wave():
+    """u = sin(y) e_x (divergence free, steady Euler solution): div(uu) = 0 in x and y."""
+    g = box(8, 16, 6)
+    U = np.broadcast_to(np.sin(g.yc()), g.shape).copy()
+    A = oracle.advection(U, g.zeros(), g.zeros(), g)
+    for a in A:
+        assert np.abs(a).max() < 1e-14
+
+
+def test_full_viscous_form_reduces_to_laplacian_for_uniform_mu():
+    """div[mu(grad u + grad u^T)] with a uniform mu array equals mu lap(u) for a
+    discretely divergence-free u (periodic and walls)."""
+    for walls in (False, True):
+        geo = inputs.geometry(12, 10, 8, 2 * np.pi, 2.0 if walls else 2 * np.pi, 2 * np.pi, walls)
+        g = oracle.Grid(12, 10, 8, geo['lx'], geo['ly'], geo['lz'], walls)
+        U, V, W = inputs.random_solenoidal(geo, 4, 3)
+        mu = np.full(g.shape, 0.37)
+        full = oracle.momentum.viscous(U, V, W, g, mu)
+        lap = oracle.momentum.viscous(U, V, W, g, 0.37)
+        for f, l in zip(full, lap):
+            if walls:
+                f, l = f[:, :-1], l[:, :-1]   # top wall faces are not updated
+            np.testing.assert_allclose(f, l, atol=1e-10 * np.abs(l).max())
+
+
+def test_div_tau_of_uniform_stress_is_zero_and_linear_stress_exact():
+    g = box(10, 12, 8)
+    tau = [np.full(g.shape, v) for v in (1.0, 2.0, 3.0, 4.0, 5.0, 6.0)]
+    for f in oracle.div_tau(tau, g):
+        assert np.abs(f).max() < 1e-14
+    # tau_xy = sin(y) only: div tau = (d/dy tau_xy, d/dx tau_xy, 0) -> x-face gets
+    # the y-difference of the 4-point edge averages, i.e. cos(y) sin(dy)/dy
+    tau = [g.zeros() for _ in range(6)]
+    tau[1] = np.broadcast_to(np.sin(g.yc()), g.shape).copy()
+    fx, fy, fz = oracle.div_tau(tau, g)
+    np.testing.assert_allclose(fx, np.broadcast_to(np.cos(g.yc()) * np.sin(g.dy) / g.dy, g.shape), atol=1e-12)
+    assert np.abs(fy).max() < 1e-14 and np.abs(fz).max() < 1e-14
+
+
+def test_wall_ghost_rules():
+    g = box(6, 8, 4, walls=True)
+    a = np.random.default_rng(0).standard_normal(g.shape)
+    np.testing.assert_array_equal(oracle.at(a, g, 'c', j=-2)[:, 0], a[:, 0])
+    np.testing.assert_array_equal(oracle.at(a, g, 'u', j=-1)[:, 0], -a[:, 0])
+    np.testing.assert_array_equal(oracle.at(a, g, 'u', j=1)[:, -1], -a[:, -1])
+    np.testing.assert_array_equal(oracle.at(a, g, 'v', j=-1)[:, 0], 0.0)
+    np.testing.assert_array_equal(oracle.at(a, g, 'c', j=3)[:, -1], a[:, -1])

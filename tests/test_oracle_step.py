@@ -1,0 +1,98 @@
+"""Pins for the oracle's whole RK3 step (Sec. 3.3.1): exact Navier-Stokes solutions,
+steady channel flow of an Oldroyd-B fluid, projection bound and discrete symmetries."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_09563_gb300 import inputs
+
+
+def taylor_green_2d_error(n, dt, T, nu=0.1):
+    g = oracle.Grid(n, n, 4, 2 * np.pi, 2 * np.pi, 2 * np.pi)
+    U = np.sin(g.xf()) * np.cos(g.yc()) + 0 * g.zeros()
+    V = -np.cos(g.xc()) * np.sin(g.yf()) + 0 * g.zeros()
+    prm = oracle.Params('newtonian', mu_s=nu, mu_p=0.0, lam=1.0)
+    s = oracle.State.rest(g, U, V, g.zeros())
+    s.p = 0.25 * (np.cos(2 * g.xc()) + np.cos(2 * g.yc())) + 0 * g.zeros()
+    for _ in range(int(round(T / dt))):
+        s = oracle.rk3_step(s, dt, g, prm)
+    decay = np.exp(-2 * nu * T)
+    return np.abs(s.U - U * decay).max(), s, g
+
+
+def test_taylor_green_decay_second_order_in_space():
+    """2D Taylor-Green vortex u = sin x cos y e^{-2 nu t} is an exact Navier-Stokes
+    solution; the error of the central-difference step falls ~4x per refinement."""
+    e16, _, _ = taylor_green_2d_error(16, 0.02, 0.4)
+    e32, s, g = taylor_green_2d_error(32, 0.01, 0.4)
+    assert e32 < 3e-4 and e16 / e32 > 3.6, (e16, e32)
+    assert np.abs(oracle.divergence(s.U, s.V, s.W, g)).max() < 1e-12
+
+
+def test_oldroyd_b_poiseuille_steady_state():
+    """Start-up Poiseuille flow of an Oldroyd-B fluid (Sec. 4.1.1) reaches the steady
+    state u = (G/2 mu_0)(1 - y^2) (to the O(dy^2) of the wall treatment), with
+    tau_xy = mu_p du/dy and tau_xx = 2 lambda mu_p (du/dy)^2 holding exactly for the
+    discrete gradient."""
+    g = oracle.Grid(1, 8, 1, 1.0, 2.0, 1.0, True)
+    prm = oracle.Params.from_groups('oldroyd_b', 1.0, 0.25, 0.5)
+    s = oracle.State.rest(g)
+    for _ in range(500):
+        s = oracle.rk3_step(s, 0.012, g, prm, (2.0, 0.0, 0.0))
+    y = g.yc()[0, :, 0]
+    assert np.abs(s.U[0, :, 0] - (1 - y ** 2)).max() < 0.05
+    L = oracle.velocity_gradient(s.U, s.V, s.W, g)
+    tau = oracle.tau_from_B(s.B, prm)
+    assert np.abs(tau[1] - prm.mu_p * L[0][1]).max() < 1e-6
+    assert np.abs(tau[0] - 2 * prm.lam * prm.mu_p * L[0][1] ** 2).max() < 1e-6
+    assert np.abs(s.V).max() == 0.0
+
+
+def c1_state():
+    n = 32
+    geo = inputs.geometry(n, n, n, 2 * np.pi, 2 * np.pi, 2 * np.pi)
+    g = oracle.Grid(n, n, n, 2 * np.pi, 2 * np.pi, 2 * np.pi)
+    U, V, W = inputs.taylor_green(geo)
+    return g, oracle.State.rest(g, U, V, W)
+
+
+def test_c1_energy_decays_divergence_free_and_mirror_symmetric():
+    """Single-phase Oldroyd-B Taylor-Green box: kinetic energy decreases, the
+    projected field has max|div u| <= 1e-12, and the mirror symmetry
+    u(x) = -u(2 pi - x) of the initial field is kept to round-off."""
+    g, s = c1_state()
+    prm = oracle.Params.from_groups('oldroyd_b', 1.0, 1.0, 0.5)
+    E = [0.5 * (s.U ** 2 + s.V ** 2 + s.W ** 2).mean()]
+    for _ in range(2):
+        s = oracle.rk3_step(s, 1e-3, g, prm)
+        E.append(0.5 * (s.U ** 2 + s.V ** 2 + s.W ** 2).mean())
+        assert np.abs(oracle.divergence(s.U, s.V, s.W, g)).max() <= 1e-12
+    assert E[0] > E[1] > E[2]
+    n = g.nx
+    # face i+1/2 at (i+1)h mirrors to face n-i-2; centre i mirrors to n-1-i
+    mir_face = (n - 2 - np.arange(n)) % n
+    mir_cell = n - 1 - np.arange(n)
+    assert np.abs(s.U + s.U[:, :, mir_face]).max() < 1e-12
+    assert np.abs(s.V - s.V[:, :, mir_cell]).max() < 1e-12
+    assert np.abs(s.B[1] + s.B[1][:, :, mir_cell]).max() < 1e-12
+    assert np.abs(s.B[0] - s.B[0][:, :, mir_cell]).max() < 1e-12
+
+
+def test_saramito_bi_zero_step_equals_oldroyd_b_step():
+    g, s = c1_state()
+    a = oracle.rk3_step(s.copy(), 1e-3, g, oracle.Params.from_groups('oldroyd_b', 1.0, 1.0, 0.5))
+    b = oracle.rk3_step(s.copy(), 1e-3, g, oracle.Params.from_groups('saramito', 1.0, 1.0, 0.5, Bi=0.0))
+    for x, y in zip([a.U, a.V, a.W, a.p] + a.B, [b.U, b.V, b.W, b.p] + b.B):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_rest_state_with_identity_conformation_stays_at_rest():
+    """u = 0, B = I is an exact steady state for every model (tau = 0)."""
+    g = oracle.Grid(8, 8, 8, 1.0, 1.0, 1.0)
+    for model, extra in (('oldroyd_b', {}), ('fene_p', {'L2': 100.0}), ('saramito', {'Bi': 0.3})):
+        prm = oracle.Params.from_groups(model, 1.0, 1.0, 0.5, **extra)
+        s = oracle.rk3_step(oracle.State.rest(g), 1e-2, g, prm)
+        assert np.abs(s.U).max() == 0.0 and np.abs(s.p).max() == 0.0
+        for c, b in enumerate(s.B):
+            assert np.abs(b - (1.0 if c in (0, 3, 5) else 0.0)).max() < 1e-15
