@@ -1,0 +1,373 @@
+"""Benchmark of the EVP time step on GB300.
+
+Workload (default): Saramito EVP channel, 256 x 128 x 128 (x, y, z), periodic in x
+and z, no-slip walls at y = +-1, Re = 100, Wi = 1, Bi = 0.5, beta = 0.5, body force
+dp/dx = 2/Re, dt = 2e-3, laminar Poiseuille base flow plus a seeded solenoidal
+perturbation of max-norm 1e-2 with |k| <= 8.  FP32 fields and stencils, FP64 Thomas
+sweeps and divergence residual ("FP32-served"), with the same run in FP64 ("FP64
+plain") beside it.
+
+A step is one full RK3 step (three substeps: stress update, momentum predictor,
+Poisson solve, projection).  Metric: Mcell-steps/s = cells * steps / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+N > 1 runs under torchrun, one independent replica per GPU (the time step of one
+simulation does not shard); value = cells * steps * N / max-over-ranks time.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-steps/s FP32-served vs FP64 plain at stated error; p50/p99 step latency"
+WORKLOAD = dict(name="saramito_channel_256x128x128", nx=256, ny=128, nz=128, lx=4 * np.pi, ly=2.0,
+                lz=2 * np.pi, walls_y=True, model="saramito", Re=100.0, Wi=1.0, Bi=0.5, beta=0.5,
+                dt=2e-3, seed=1, kmax=8, amp=1e-2)
+
+
+def workload_inputs(w, nz=None):
+    from paper_1803_09563_gb300 import inputs
+    nz = nz or w['nz']
+    lz = w['lz'] * nz / w['nz']
+    geo = inputs.geometry(w['nx'], w['ny'], nz, w['lx'], w['ly'], lz, w['walls_y'])
+    U, V, W = inputs.poiseuille(geo)
+    u2, v2, w2 = inputs.scale_max(*inputs.random_solenoidal(geo, w['seed'], w['kmax']), w['amp'])
+    return geo, U + u2, v2, w2
+
+
+def peaks():
+    p = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d['hbm_gbs']), 'measured'
+    return 6800.0, 'fallback'
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ('clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,'
+         'clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,'
+         'clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', str(self.index), '--query-gpu=' + self.Q,
+                                          '--format=csv,noheader,nounits', '-lms', '100'],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(',')]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == 'active':
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(kernel, w, elt, walls):
+    """Minimum bytes each kernel must move per launch, summed over one step's three
+    substeps (history read skipped at substep 1, history write skipped at substep 3)."""
+    N = w['nx'] * w['ny'] * w['nz']
+    nxh = w['nx'] // 2 + 1
+    spec = 2 * nxh * w['ny'] * w['nz'] * elt     # complex spectral buffer, bytes
+    if kernel == 'stress_weno_update':
+        # read u(3) B(6) [+RT(6)], write B(6) [+RT(6)]
+        words = (3 + 6 + 6 + 6) + (3 + 6 + 6 + 6 + 6) + (3 + 6 + 6 + 6)
+        return words * N * elt, 3
+    if kernel == 'momentum_predictor':
+        # read u(3) p(1) B^{k-1}(6) B^k(6) [+N(3)], write u*(3) [+N(3)]
+        words = (3 + 1 + 12 + 3 + 3) + (3 + 1 + 12 + 3 + 3 + 3) + (3 + 1 + 12 + 3 + 3)
+        return words * N * elt, 3
+    if kernel == 'div_fft_x':
+        return 3 * (3 * N * elt + spec), 3
+    if kernel in ('fft_z_forward', 'fft_z_inverse', 'fft_y_modal_solve'):
+        return 3 * 2 * spec, 3
+    if kernel == 'thomas_y_fp64':
+        return 3 * 2 * spec, 3
+    if kernel == 'ifft_x_psi':
+        return 3 * (spec + N * elt), 3
+    if kernel == 'project_correct':
+        # read u*(3) psi(1) p(1), write u(3) p(1)
+        return 3 * 9 * N * elt, 3
+    return 0, 1
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if one exists for this kernel."""
+    p = os.path.join(ROOT, 'profiles', f'{kernel}__channel_256x128x128_fp32.md')
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith('traffic_bytes_per_launch:'):
+            try:
+                return float(line.split(':', 1)[1])
+            except ValueError:
+                return None
+    return None
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_1803_09563_gb300 import evp
+    torch.cuda.set_device(local_rank)
+    w = WORKLOAD
+    N = w['nx'] * w['ny'] * w['nz']
+    geo, U, V, W = workload_inputs(w)
+    stream = torch.cuda.Stream()
+
+    def make(precision):
+        grid = evp.make_grid(w['nx'], w['ny'], w['nz'], w['lx'], w['ly'], w['lz'], w['walls_y'])
+        prm = evp.make_params(Re=w['Re'], Wi=w['Wi'], beta=w['beta'], Bi=w['Bi'], dpdx=2.0 / w['Re'],
+                              precision=precision)
+        sim = evp.Simulation(grid, w['model'], prm, stream=stream.cuda_stream)
+        sim.set_state(U, V, W)
+        return sim
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device='cuda')
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---------------- FP32-served: timed region
+    sim = make(evp.EVP_FP32)
+    for _ in range(args.warmup):
+        sim.step(w['dt'])
+    sim.sync()
+    evp.evp_kernel_timing(sim.handle, True)
+    evp.evp_kernel_times(sim.handle)       # reset counters
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        sim.step(w['dt'])
+        ev[k + 1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    ktimes = evp.evp_kernel_times(sim.handle)
+    evp.evp_kernel_timing(sim.handle, False)
+    code, bits, maxdiv = sim.sync(raise_on_error=False)
+    total_ms = max_over_ranks(total_ms)
+    value = N * args.steps * world / (total_ms * 1e-3) / 1e6
+    launches = int(sum(c for _, c in ktimes.values()))
+
+    # roofline of the dominant kernel (largest share of device time)
+    hbm, peak_kind = peaks()
+    elt = 4
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    kern = {}
+    for name, (ms, cnt) in ktimes.items():
+        if cnt == 0:
+            continue
+        b, per = algorithmic_bytes(name, w, elt, w['walls_y'])
+        nsteps = cnt / per
+        gbs = b * nsteps / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        kern[name] = {"ms_per_launch": ms / cnt, "launches": cnt, "share": ms / sum(v[0] for v in ktimes.values()),
+                      "algorithmic_GBps": gbs, "frac_of_hbm": gbs / hbm}
+    b_dom, per_dom = algorithmic_bytes(dom, w, elt, w['walls_y'])
+    dom_ms, dom_cnt = ktimes[dom]
+    achieved = b_dom * (dom_cnt / per_dom) / (dom_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom)
+
+    # ---------------- e2e through the C ABI with host buffers
+    fields_io = [evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P] + [evp.EVP_BXX + c for c in range(6)]
+    host = [torch.empty(sim.shape, dtype=torch.float32).pin_memory() for _ in fields_io]
+    for f, h in zip(fields_io, host):
+        evp.evp_get_field(sim.handle, f, h.numpy())
+    e2e_steps = max(2, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for f, h in zip(fields_io, host):
+            evp.evp_set_field(sim.handle, f, h.numpy())
+        sim.step(w['dt'])
+        for f, h in zip(fields_io, host):
+            evp.evp_get_field(sim.handle, f, h.numpy())
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = N * e2e_steps * world / e2e_s / 1e6
+    io_bytes = len(fields_io) * N * 4
+    fp32_fields = [sim.get(f) for f in fields_io]
+    sim.close()
+
+    # ---------------- FP64 plain on the same workload and the same steps
+    sim64 = make(evp.EVP_FP64)
+    n64 = max(2, args.steps // 4)
+    for _ in range(min(args.warmup, 2)):
+        sim64.step(w['dt'])
+    sim64.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(n64):
+        sim64.step(w['dt'])
+    e1.record(stream)
+    stream.synchronize()
+    ms64 = max_over_ranks(e0.elapsed_time(e1))
+    value64 = N * n64 * world / (ms64 * 1e-3) / 1e6
+    # accuracy of FP32-served against FP64 plain after the same number of steps
+    steps_done = args.warmup + args.steps + e2e_steps
+    sim64.close()
+    sim64 = make(evp.EVP_FP64)
+    for _ in range(steps_done):
+        sim64.step(w['dt'])
+    sim64.sync()
+    errs = {}
+    for f, a in zip(fields_io, fp32_fields):
+        b = sim64.get(f)
+        errs[str(f)] = float(np.abs(a.astype(np.float64) - b).max() / max(np.abs(b).max(), 1e-300))
+    sim64.close()
+
+    sl = sorted(step_ms)
+    p50 = sl[len(sl) // 2]
+    p99 = sl[min(len(sl) - 1, int(round(0.99 * (len(sl) - 1))))]
+    names = {evp.EVP_U: 'u', evp.EVP_V: 'v', evp.EVP_W: 'w', evp.EVP_P: 'p'}
+    names.update({evp.EVP_BXX + c: 'B' + s for c, s in enumerate(['xx', 'xy', 'xz', 'yy', 'yz', 'zz'])})
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mcell-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 Thomas + residual)",
+        "data": "synthetic (seeded Poiseuille + solenoidal perturbation)",
+        "config": {"workload": w['name'], "grid": [w['nx'], w['ny'], w['nz']], "model": w['model'],
+                   "Re": w['Re'], "Wi": w['Wi'], "Bi": w['Bi'], "beta": w['beta'], "dt": w['dt'],
+                   "walls_y": True, "integrator": "RK3", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (state 0.5 GB per replica vs 129 MB L2)"},
+        "p50_ms": p50, "p99_ms": p99,
+        "fp64_plain": {"value": value64, "unit": "Mcell-steps/s", "steps": n64, "ms_per_step": ms64 / n64},
+        "fp32_vs_fp64_rel_err": {names[int(k)]: v for k, v in errs.items()},
+        "fp32_vs_fp64_after_steps": steps_done,
+        "max_div_fp64_residual": maxdiv, "status_bits": bits,
+        "e2e": {"value": e2e_value, "unit": "Mcell-steps/s", "h2d_bytes_per_step": io_bytes,
+                "d2h_bytes_per_step": io_bytes, "steps": e2e_steps},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                     "traffic": traffic},
+        "kernels": kern,
+        "clocks": clk,
+    }
+    return line
+
+
+def run_cpu_baseline(args):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
+    one RK3 step of a 256 x 128 x 32 slab of the channel (z shortened 4x)."""
+    import oracle
+    w = WORKLOAD
+    nz = 32
+    geo, U, V, W = workload_inputs(w, nz=nz)
+    g = oracle.Grid(w['nx'], w['ny'], nz, geo['lx'], geo['ly'], geo['lz'], True)
+    prm = oracle.Params.from_groups(w['model'], w['Re'], w['Wi'], w['beta'], Bi=w['Bi'])
+    s = oracle.State.rest(g, U, V, W)
+    t0 = time.perf_counter()
+    s = oracle.rk3_step(s, w['dt'], g, prm, (2.0 / w['Re'], 0.0, 0.0))
+    dt = time.perf_counter() - t0
+    return {"value": w['nx'] * w['ny'] * nz / dt / 1e6, "unit": "Mcell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 RK3 step of a {w['nx']}x{w['ny']}x{nz} slab of the channel (numpy FP64, "
+                      f"single thread), {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=40)
+    ap.add_argument('--warmup', type=int, default=5)
+    ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    args = ap.parse_args()
+    rank = int(os.environ.get('RANK', 0))
+    world = int(os.environ.get('WORLD_SIZE', 1))
+    local_rank = int(os.environ.get('LOCAL_RANK', 0))
+
+    if args.impl == 'reference':
+        # the oracle is the reference arm: rank 0 only, host cores, bounded samples
+        if rank != 0:
+            return
+        vals = []
+        for _ in range(max(1, min(args.steps, 3))):
+            vals.append(run_cpu_baseline(args))
+        v = statistics.median(x['value'] for x in vals)
+        cb = dict(vals[0])
+        cb['value'] = v
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mcell-steps/s", "n_gpus": world,
+                "steps": len(vals), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD['name']}, "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": "Mcell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group('nccl', device_id=torch.device('cuda', local_rank))
+    line = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line['cpu_baseline'] = run_cpu_baseline(args)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == '__main__':
+    main()

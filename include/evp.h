@@ -1,0 +1,176 @@
+/*
+ * evp.h -- C ABI of libevp, a GB300 (sm_103a) implementation of the Eulerian
+ * non-Newtonian time step of Izbassarov et al., "Computational modeling of
+ * multiphase viscoelastic and elastoviscoplastic flows" (arXiv 1803.09563).
+ *
+ * One call advances a simulation on a staggered uniform Cartesian grid (Sec. 3):
+ * the conformation tensor B of Eq. SRM2 with the closures of Table 1 (Oldroyd-B,
+ * FENE-P, Saramito EVP), fifth-order WENO advection of B (Sec. 3.1), the
+ * momentum predictor with div(tau) (Eq. NS-num1), and the fast Poisson
+ * projection (Eqs. NS-num2, NS-num3) with FFTs in the periodic directions and a
+ * tridiagonal (Thomas) solve along a wall-normal y, all integrated with the
+ * low-storage RK3 scheme of Eq. RK.
+ *
+ * Conventions shared by every entry point
+ *   - Plain C types only.  Device pointers are CUDA device addresses on the
+ *     current device; host pointers are ordinary (preferably pinned) memory.
+ *   - Field layout: [nz][ny][nx], x fastest, nx*ny*nz elements.  A face
+ *     velocity at index i is the one on the +1/2 face of cell i (u at
+ *     x = (i+1)dx, v at y = y0 + (j+1)dy, w at z = (k+1)dz); with walls the
+ *     face below cell j = 0 is the bottom wall and v[.., ny-1, ..] the top wall.
+ *     Centred fields (p, B, phi) sit at cell centres.
+ *   - Element type of every field buffer is the state's precision: double for
+ *     EVP_FP64, float for EVP_FP32.
+ *   - Every function returns an evp_status (EVP_OK = 0).  No exception crosses
+ *     the ABI.  On failure evp_last_error() holds a message for the calling
+ *     thread.  Kernel-side conditions (non-finite values, FENE-P trace limit,
+ *     loss of positive definiteness) raise status bits that evp_sync() returns.
+ *   - Asynchrony: evp_step / evp_substep / evp_project / evp_poisson_solve /
+ *     evp_stress_rhs enqueue work on the state's stream and return.
+ *     evp_set_field / evp_get_field and evp_sync synchronise that stream.
+ *   - Threading: a state is used by one host thread at a time.
+ */
+#ifndef EVP_H
+#define EVP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EVP_OK = 0,
+    EVP_ERR_ARG = 1,         /* invalid argument (sizes, ids, null pointers)       */
+    EVP_ERR_OOM = 2,         /* device allocation failed or arena too small         */
+    EVP_ERR_CUDA = 3,        /* a CUDA runtime call failed                          */
+    EVP_ERR_NONFINITE = 4,   /* a kernel produced NaN/Inf (raised at evp_sync)      */
+    EVP_ERR_UNPHYSICAL = 5,  /* FENE-P tr B >= L^2 or det B < 0 (raised at sync)    */
+    EVP_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                       */
+    EVP_ERR_STATE = 7        /* call not valid in the state's configuration         */
+} evp_status;
+
+/* status bits accumulated by the kernels, returned by evp_sync */
+#define EVP_BIT_NONFINITE   0x1u
+#define EVP_BIT_TRACE_LIMIT 0x2u   /* FENE-P: tr B >= L^2 (Table 1 closure singular)  */
+#define EVP_BIT_DET_NEG     0x4u   /* det B < 0: B lost positive definiteness (Sec 3.1) */
+
+/* Grid (Sec. 3): uniform spacing lx/nx, ly/ny, lz/nz.  x and z are periodic;
+ * y is periodic (walls_y = 0) or bounded by no-slip walls at y = -ly/2 and
+ * +ly/2 (walls_y = 1).  nx and nz (and ny when periodic) must be of the form
+ * 2^a 3^b, 8 <= n <= 512; nx even.  With walls 4 <= ny <= 512.             */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz;
+    int walls_y;
+} evp_grid;
+
+typedef enum {
+    EVP_NEWTONIAN = 0,   /* no extra stress (tau = 0)                          */
+    EVP_OLDROYD_B = 1,   /* Table 1: B = tau lambda/mu_p + I, F = 1, a = 1    */
+    EVP_FENE_P = 2,      /* Table 1: F = L^2/(L^2 - tr B), a = L^2/(L^2 - 3)  */
+    EVP_SARAMITO = 3     /* Table 1: F = a = max(0, 1 - tau_y/|tau^d|)        */
+} evp_model;
+
+enum { EVP_FP64 = 0, EVP_FP32 = 1 };
+enum { EVP_RK3 = 0, EVP_AB2 = 1 };
+
+/* Dimensionless groups and options.  Scalings (rho = 1): mu_s = beta/Re,
+ * mu_p = (1-beta)/Re, lambda = Wi; tau_y = Bi/Re (bi_def = 0, Bi against the
+ * viscous stress, Sec. 4.1.3) or tau_y = Bi (bi_def = 1, Bi against rho g L,
+ * Sec. 4.2.3).  Body forces: a uniform force dpdx along x (the channel's
+ * pressure gradient) and the ABC force
+ * abc_amp*(sin kz + cos ky, sin kx + cos kz, sin ky + cos kx), k = abc_k.      */
+typedef struct {
+    double Re, Wi, beta, Bi, L2;
+    int bi_def;
+    double dpdx;
+    double abc_amp, abc_k;
+    int precision;      /* EVP_FP64 or EVP_FP32 (the Thomas sweeps run in FP64 in both) */
+    int integrator;     /* EVP_RK3 (Eq. RK); EVP_AB2 reserved for the two-phase step    */
+    double reserved[16];
+} evp_params;
+
+/* Field identifiers for evp_set_field / evp_get_field */
+typedef enum {
+    EVP_U = 0, EVP_V = 1, EVP_W = 2, EVP_P = 3,
+    EVP_BXX = 4, EVP_BXY = 5, EVP_BXZ = 6, EVP_BYY = 7, EVP_BYZ = 8, EVP_BZZ = 9,
+    EVP_RT_XX = 10, /* ... EVP_RT_XX+5: RK3 history RT^{k-2} (Eq. RK-rt)          */
+    EVP_NH_X = 16,  /* ... EVP_NH_X+2: RK3 history of -div(uu)+viscous+force     */
+    EVP_PSI = 19,   /* last projection variable psi (read only)                  */
+    EVP_NFIELDS = 20
+} evp_field;
+
+typedef struct evp_state_s evp_state;
+
+/* Bytes of device memory a state with this configuration needs (its arena). */
+size_t evp_state_bytes(const evp_grid* grid, evp_model model, const evp_params* params);
+
+/* Create a state: B = I (tau = 0), u = p = 0, histories zero.
+ *   stream: a cudaStream_t, or NULL to let the state create its own stream.
+ *   arena:  NULL to let the library allocate evp_state_bytes() on the device,
+ *           or a caller-owned device buffer of at least arena_bytes >=
+ *           evp_state_bytes(); the caller keeps ownership and must keep it alive
+ *           until evp_destroy.  The state never retains any other caller pointer.
+ * Errors: EVP_ERR_ARG (bad sizes/model/params), EVP_ERR_OOM, EVP_ERR_CUDA.    */
+int evp_init(const evp_grid* grid, evp_model model, const evp_params* params,
+             void* stream, void* arena, size_t arena_bytes, evp_state** out);
+
+/* Release the state (and its arena and stream if the library created them). */
+int evp_destroy(evp_state* s);
+
+/* Copy a whole field (nx*ny*nz elements of the state's precision) into / out of
+ * the state.  src/dst are device pointers when *_on_device != 0, host pointers
+ * otherwise.  Synchronous with respect to the host.  EVP_PSI is read only.    */
+int evp_set_field(evp_state* s, int field, const void* src, int src_on_device);
+int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device);
+
+/* One full RK3 time step of size dt (Sec. 3.3.1, Eqs. RK-rt..NS-num3, RK):
+ * three substeps, each B update (Eq. rk3tau), momentum predictor (Eq. rk3),
+ * Poisson solve (Eq. NS-num2) and correction (Eq. NS-num3).  Asynchronous.   */
+int evp_step(evp_state* s, double dt);
+
+/* Substep k = 0, 1, 2 of the RK3 scheme alone (Eq. RK constants alpha^k,
+ * zeta^k, xi^k).  For k > 0 the histories RT^{k-2} and N^{k-2} are the ones in
+ * the state (set them with evp_set_field to reproduce an arbitrary substep).  */
+int evp_substep(evp_state* s, double dt, int k);
+
+/* Project the current velocity onto the discretely divergence-free space:
+ * lap(phi) = div u, u <- u - grad(phi) (Eqs. var-poisson, projection with
+ * dt = 1).  The pressure field is left unchanged.  Asynchronous.              */
+int evp_project(evp_state* s);
+
+/* Solve lap(psi) = rhs with the state's fast Poisson solver (FFT in periodic
+ * directions, FP64 Thomas along a wall-bounded y; Eq. NS-num2).  rhs and psi
+ * are device buffers of nx*ny*nz elements (state precision); rhs may equal psi.
+ * Periodic: the mean of rhs is ignored and psi has zero mean.  Walls: the
+ * (kx, kz) = (0, 0) system is pinned by psi = 0 in its first row.             */
+int evp_poisson_solve(evp_state* s, const void* rhs, void* psi);
+
+/* Evaluate RT = (aI - F B)/lambda - (u.grad B - B.grad u - grad u^T.B) of Eq. rt
+ * at the current state into rt (device, 6*nx*ny*nz elements, component-major
+ * in the order xx, xy, xz, yy, yz, zz).                                        */
+int evp_stress_rhs(evp_state* s, void* rt);
+
+/* Wait for the state's stream.  Returns EVP_ERR_NONFINITE / EVP_ERR_UNPHYSICAL
+ * when kernels raised the matching bits since the last sync (bits in *bits),
+ * else EVP_OK.  *max_div (may be NULL) receives max |div u| of the last
+ * projection, computed in FP64.  Bits and residual are cleared afterwards.     */
+int evp_sync(evp_state* s, unsigned* bits, double* max_div);
+
+/* Per-kernel timing with CUDA events on the state's stream (off by default).
+ * evp_kernel_times fills up to n entries of accumulated milliseconds and
+ * launch counts (synchronises); evp_kernel_name names entry i.              */
+int evp_kernel_timing(evp_state* s, int enable);
+int evp_kernel_times(evp_state* s, double* ms, long long* launches, int n);
+const char* evp_kernel_name(int i);
+int evp_num_kernels(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* evp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EVP_H */

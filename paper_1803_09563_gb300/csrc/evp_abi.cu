@@ -1,0 +1,745 @@
+// Host side of libevp: the C ABI of evp.h, the device arena, the constant tables
+// (FFT twiddles, modal eigenvalues, Thomas pivots, forcing tables) and the RK3
+// orchestration of Sec. 3.3.1 (Eqs. RK-rt, NS-num1, rk3tau, rk3, NS-num2, NS-num3, RK).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "evp_internal.cuh"
+
+using namespace evp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return EVP_ERR_CUDA;
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+    } while (0)
+
+// Wray's low-storage RK3 constants (Eq. RK)
+const double RK_ALPHA[3] = {4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0};
+const double RK_ZETA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+const double RK_XI[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+
+const char* KERNEL_NAMES[K_COUNT] = {"stress_weno_update", "momentum_predictor", "div_fft_x",
+                                     "fft_z_forward",      "fft_y_modal_solve",  "thomas_y_fp64",
+                                     "fft_z_inverse",      "ifft_x_psi",         "project_correct"};
+
+bool is_2a3b(int n) {
+    if (n < 1) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct evp_state_s {
+    evp_grid g;
+    evp_model model;
+    evp_params prm;
+    bool fp32;
+    size_t elt;          // bytes per element
+    size_t N;            // cells
+    int nxh;
+    cudaStream_t st;
+    bool own_stream;
+    char* arena;
+    size_t arena_bytes;
+    bool own_arena;
+    // field storage (element type = precision)
+    void* U[2];
+    void* V[2];
+    void* W[2];
+    void* B[2][6];
+    void* RT[6];
+    void* NH[3];
+    void* P;
+    void* PSI;
+    void* spec;
+    // tables
+    void* twx;
+    void* twy;
+    void* twz;
+    void* lamx;
+    void* lamy;
+    void* lamz;
+    void* trig;
+    double* thomas_m;
+    unsigned* d_status;
+    unsigned long long* d_maxdiv;
+    int cu, cb;          // current velocity / B buffer
+    ModelConst mc;
+    // timing
+    bool timing;
+    std::vector<cudaEvent_t> ev_free;
+    struct Pend {
+        int kid;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pend> pending;
+    cudaEvent_t cur_start;
+    double ms[K_COUNT];
+    long long launches[K_COUNT];
+};
+
+namespace {
+
+cudaEvent_t get_event(evp_state* s) {
+    if (!s->ev_free.empty()) {
+        cudaEvent_t e = s->ev_free.back();
+        s->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void flush_timing(evp_state* s) {
+    if (s->pending.empty()) return;
+    cudaStreamSynchronize(s->st);
+    for (auto& p : s->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            s->ms[p.kid] += ms;
+            s->launches[p.kid] += 1;
+        }
+        s->ev_free.push_back(p.a);
+        s->ev_free.push_back(p.b);
+    }
+    s->pending.clear();
+}
+
+void hook_begin(void* ctx, int) {
+    evp_state* s = static_cast<evp_state*>(ctx);
+    s->cur_start = get_event(s);
+    cudaEventRecord(s->cur_start, s->st);
+}
+
+void hook_end(void* ctx, int kid) {
+    evp_state* s = static_cast<evp_state*>(ctx);
+    cudaEvent_t e = get_event(s);
+    cudaEventRecord(e, s->st);
+    s->pending.push_back({kid, s->cur_start, e});
+    if (s->pending.size() >= 2048) flush_timing(s);
+}
+
+TimingHook hook_of(evp_state* s) {
+    TimingHook h;
+    h.begin = s->timing ? hook_begin : nullptr;
+    h.end = s->timing ? hook_end : nullptr;
+    h.ctx = s;
+    return h;
+}
+
+int validate(const evp_grid* g, evp_model model, const evp_params* p) {
+    if (!g || !p) return fail(EVP_ERR_ARG, "null grid or params");
+    auto fft_ok = [](int n) { return n >= 8 && n <= 512 && is_2a3b(n); };
+    if (!fft_ok(g->nx) || (g->nx % 2) != 0) return fail(EVP_ERR_ARG, "nx must be even, 2^a 3^b, 8..512");
+    if (!fft_ok(g->nz)) return fail(EVP_ERR_ARG, "nz must be 2^a 3^b, 8..512");
+    if (g->walls_y) {
+        if (g->ny < 4 || g->ny > 512) return fail(EVP_ERR_ARG, "ny with walls must be 4..512");
+    } else if (!fft_ok(g->ny)) {
+        return fail(EVP_ERR_ARG, "periodic ny must be 2^a 3^b, 8..512");
+    }
+    if (!(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0)) return fail(EVP_ERR_ARG, "box lengths must be positive");
+    if (model < EVP_NEWTONIAN || model > EVP_SARAMITO) return fail(EVP_ERR_ARG, "unknown model");
+    if (!(p->Re > 0)) return fail(EVP_ERR_ARG, "Re must be positive");
+    if (!(p->beta >= 0 && p->beta <= 1)) return fail(EVP_ERR_ARG, "beta must be in [0, 1]");
+    if (model != EVP_NEWTONIAN && !(p->Wi > 0)) return fail(EVP_ERR_ARG, "Wi must be positive");
+    if (model == EVP_FENE_P && !(p->L2 > 3)) return fail(EVP_ERR_ARG, "FENE-P needs L2 > 3");
+    if (model == EVP_SARAMITO && !(p->Bi >= 0)) return fail(EVP_ERR_ARG, "Bi must be >= 0");
+    if (p->precision != EVP_FP64 && p->precision != EVP_FP32) return fail(EVP_ERR_ARG, "bad precision");
+    if (p->integrator != EVP_RK3) return fail(EVP_ERR_ARG, "only the RK3 integrator is available");
+    return EVP_OK;
+}
+
+struct Layout {
+    size_t off[64];
+    int n = 0;
+    size_t total = 0;
+    size_t add(size_t bytes) {
+        size_t o = total;
+        off[n++] = o;
+        total += align_up(bytes);
+        return o;
+    }
+};
+
+// Build the arena layout; returns total bytes.  With base != null also assigns pointers.
+size_t plan(evp_state* s, char* base) {
+    const evp_grid& g = s->g;
+    const size_t N = (size_t)g.nx * g.ny * g.nz;
+    const size_t e = s->elt;
+    const int nxh = g.nx / 2 + 1;
+    Layout L;
+    auto P = [&](size_t bytes) -> void* { size_t o = L.add(bytes); return base ? base + o : nullptr; };
+    for (int b = 0; b < 2; ++b) {
+        void* u = P(N * e);
+        void* v = P(N * e);
+        void* w = P(N * e);
+        if (base) { s->U[b] = u; s->V[b] = v; s->W[b] = w; }
+    }
+    for (int b = 0; b < 2; ++b)
+        for (int c = 0; c < 6; ++c) {
+            void* p = P(N * e);
+            if (base) s->B[b][c] = p;
+        }
+    for (int c = 0; c < 6; ++c) { void* p = P(N * e); if (base) s->RT[c] = p; }
+    for (int c = 0; c < 3; ++c) { void* p = P(N * e); if (base) s->NH[c] = p; }
+    void* p = P(N * e);
+    void* psi = P(N * e);
+    void* spec = P((size_t)nxh * g.ny * g.nz * 2 * e);
+    void* twx = P((size_t)g.nx * 2 * e);
+    void* twy = P((size_t)g.ny * 2 * e);
+    void* twz = P((size_t)g.nz * 2 * e);
+    void* lamx = P((size_t)nxh * e);
+    void* lamy = P((size_t)g.ny * e);
+    void* lamz = P((size_t)g.nz * e);
+    void* trig = P((size_t)2 * (g.nx + g.ny + g.nz) * e);
+    void* thm = g.walls_y ? P((size_t)(g.nz / 2 + 1) * g.ny * nxh * sizeof(double)) : nullptr;
+    void* st = P(sizeof(unsigned));
+    void* md = P(sizeof(unsigned long long));
+    if (base) {
+        s->P = p; s->PSI = psi; s->spec = spec;
+        s->twx = twx; s->twy = twy; s->twz = twz;
+        s->lamx = lamx; s->lamy = lamy; s->lamz = lamz; s->trig = trig;
+        s->thomas_m = static_cast<double*>(thm);
+        s->d_status = static_cast<unsigned*>(st);
+        s->d_maxdiv = static_cast<unsigned long long*>(md);
+    }
+    return L.total;
+}
+
+template <typename T>
+__global__ void k_fill(T* p, size_t n, T v) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+template <typename T>
+std::vector<T> to_t(const std::vector<double>& v) {
+    return std::vector<T>(v.begin(), v.end());
+}
+
+template <typename T>
+int upload_tables(evp_state* s) {
+    const evp_grid& g = s->g;
+    const double dx = g.lx / g.nx, dy = g.ly / g.ny, dz = g.lz / g.nz;
+    const int nxh = g.nx / 2 + 1;
+    const double twopi = 6.283185307179586476925286766559;
+    auto tw = [&](int n) {
+        std::vector<double> v(2 * n);
+        for (int m = 0; m < n; ++m) {
+            v[2 * m] = std::cos(twopi * m / n);
+            v[2 * m + 1] = -std::sin(twopi * m / n);
+        }
+        return v;
+    };
+    auto lam = [&](int n, int cnt, double h) {
+        std::vector<double> v(cnt);
+        for (int m = 0; m < cnt; ++m) v[m] = (2.0 - 2.0 * std::cos(twopi * m / n)) / (h * h);
+        return v;
+    };
+    auto put = [&](void* dst, const std::vector<double>& v) -> cudaError_t {
+        std::vector<T> t = to_t<T>(v);
+        return cudaMemcpyAsync(dst, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, s->st);
+    };
+    CK(put(s->twx, tw(g.nx)));
+    CK(put(s->twy, tw(g.ny)));
+    CK(put(s->twz, tw(g.nz)));
+    std::vector<double> lx = lam(g.nx, nxh, dx), ly = lam(g.ny, g.ny, dy), lz = lam(g.nz, g.nz, dz);
+    CK(put(s->lamx, lx));
+    CK(put(s->lamy, ly));
+    CK(put(s->lamz, lz));
+    // ABC forcing tables sin/cos(k x_i), (k y_j), (k z_k) at cell centres
+    {
+        const double k = s->prm.abc_k;
+        const double y0 = g.walls_y ? -0.5 * g.ly : 0.0;
+        std::vector<double> t;
+        for (int i = 0; i < g.nx; ++i) t.push_back(std::sin(k * (i + 0.5) * dx));
+        for (int i = 0; i < g.nx; ++i) t.push_back(std::cos(k * (i + 0.5) * dx));
+        for (int j = 0; j < g.ny; ++j) t.push_back(std::sin(k * (y0 + (j + 0.5) * dy)));
+        for (int j = 0; j < g.ny; ++j) t.push_back(std::cos(k * (y0 + (j + 0.5) * dy)));
+        for (int q = 0; q < g.nz; ++q) t.push_back(std::sin(k * (q + 0.5) * dz));
+        for (int q = 0; q < g.nz; ++q) t.push_back(std::cos(k * (q + 0.5) * dz));
+        CK(put(s->trig, t));
+    }
+    if (g.walls_y) {
+        // Thomas pivots m_j = 1/(b_j - a_j c'_{j-1}), c'_j = u_j m_j, per (kz <= nz/2, kx)
+        const int ny = g.ny, nkz = g.nz / 2 + 1;
+        const double idy2 = 1.0 / (dy * dy);
+        std::vector<double> lzf = lam(g.nz, nkz, dz);
+        std::vector<double> M((size_t)nkz * ny * nxh);
+        for (int kz = 0; kz < nkz; ++kz)
+            for (int kx = 0; kx < nxh; ++kx) {
+                const double lm = lx[kx] + lzf[kz];
+                const bool pinned = (kx == 0 && kz == 0);
+                double cprev = 0.0;
+                for (int j = 0; j < ny; ++j) {
+                    const double lo = j > 0 ? idy2 : 0.0;
+                    double up = j < ny - 1 ? idy2 : 0.0;
+                    double d = -2.0 * idy2 - lm + (j == 0 ? idy2 : 0.0) + (j == ny - 1 ? idy2 : 0.0);
+                    if (pinned && j == 0) {
+                        d = 1.0;
+                        up = 0.0;
+                    }
+                    const double m = 1.0 / (d - lo * cprev);
+                    M[((size_t)kz * ny + j) * nxh + kx] = m;
+                    cprev = up * m;
+                }
+            }
+        CK(cudaMemcpyAsync(s->thomas_m, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    }
+    return cudaStreamSynchronize(s->st) == cudaSuccess ? EVP_OK : cuda_fail(cudaGetLastError(), "tables");
+}
+
+template <typename T>
+Geo<T> geo_of(const evp_state* s) {
+    Geo<T> g;
+    g.nx = s->g.nx;
+    g.ny = s->g.ny;
+    g.nz = s->g.nz;
+    g.walls = s->g.walls_y;
+    g.idx = T(s->g.nx / s->g.lx);
+    g.idy = T(s->g.ny / s->g.ly);
+    g.idz = T(s->g.nz / s->g.lz);
+    return g;
+}
+
+template <typename T>
+FFTTables<T> tables_of(const evp_state* s) {
+    using CT = typename Cplx<T>::type;
+    FFTTables<T> t;
+    t.twx = static_cast<const CT*>(s->twx);
+    t.twy = static_cast<const CT*>(s->twy);
+    t.twz = static_cast<const CT*>(s->twz);
+    t.nrx = fft_radices(s->g.nx, t.radx);
+    t.nry = s->g.walls_y ? 0 : fft_radices(s->g.ny, t.rady);
+    t.nrz = fft_radices(s->g.nz, t.radz);
+    t.lamx = static_cast<const T*>(s->lamx);
+    t.lamy = static_cast<const T*>(s->lamy);
+    t.lamz = static_cast<const T*>(s->lamz);
+    t.thomas_m = s->thomas_m;
+    const double dy = s->g.ly / s->g.ny;
+    t.idy2 = 1.0 / (dy * dy);
+    return t;
+}
+
+template <typename T>
+double poisson_norm(const evp_state* s) {
+    const evp_grid& g = s->g;
+    return g.walls_y ? 1.0 / (double(g.nx) * g.nz) : 1.0 / (double(g.nx) * g.ny * g.nz);
+}
+
+template <typename T>
+int run_poisson(evp_state* s, const T* Us, const T* Vs, const T* Ws, const T* rhs, double rscale, T* psi) {
+    PoissonArgs<T> a;
+    a.Us = Us;
+    a.Vs = Vs;
+    a.Ws = Ws;
+    a.rhs = rhs;
+    a.rscale = T(rscale);
+    a.spec = static_cast<typename Cplx<T>::type*>(s->spec);
+    a.psi = psi;
+    a.norm = poisson_norm<T>(s);
+    cudaError_t e = launch_poisson<T>(geo_of<T>(s), tables_of<T>(s), a, s->st, hook_of(s));
+    return e == cudaSuccess ? EVP_OK : cuda_fail(e, "poisson");
+}
+
+template <typename T>
+int run_correct(evp_state* s, const T* Us, const T* Vs, const T* Ws, T* U, T* V, T* W, T* P, double coef) {
+    CorrectArgs<T> a;
+    a.Us = Us;
+    a.Vs = Vs;
+    a.Ws = Ws;
+    a.psi = static_cast<const T*>(s->PSI);
+    a.U = U;
+    a.V = V;
+    a.W = W;
+    a.P = P;
+    a.coef = T(coef);
+    a.maxdiv = s->d_maxdiv;
+    a.status = s->d_status;
+    a.idx_d = s->g.nx / s->g.lx;
+    a.idy_d = s->g.ny / s->g.ly;
+    a.idz_d = s->g.nz / s->g.lz;
+    // residual of this projection only
+    CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
+    cudaError_t e = launch_correct<T>(geo_of<T>(s), a, s->st, hook_of(s));
+    return e == cudaSuccess ? EVP_OK : cuda_fail(e, "correct");
+}
+
+template <typename T>
+int substep_t(evp_state* s, double dt, int k, bool last_in_step) {
+    const double al = RK_ALPHA[k], ze = RK_ZETA[k], xi = RK_XI[k];
+    const bool stress = s->model != EVP_NEWTONIAN;
+    const int cu = s->cu, cb = s->cb;
+    const Geo<T> g = geo_of<T>(s);
+    const TimingHook th = hook_of(s);
+    const bool read_hist = xi != 0.0, write_hist = !last_in_step;
+    if (stress) {
+        StressArgs<T> a;
+        a.U = static_cast<const T*>(s->U[cu]);
+        a.V = static_cast<const T*>(s->V[cu]);
+        a.W = static_cast<const T*>(s->W[cu]);
+        for (int c = 0; c < 6; ++c) {
+            a.B[c] = static_cast<const T*>(s->B[cb][c]);
+            a.Bn[c] = static_cast<T*>(s->B[1 - cb][c]);
+            a.RT[c] = static_cast<T*>(s->RT[c]);
+        }
+        a.dt_zeta = T(dt * ze);
+        a.dt_xi = T(dt * xi);
+        a.read_hist = read_hist;
+        a.write_hist = write_hist;
+        a.rhs_only = 0;
+        a.status = s->d_status;
+        cudaError_t e = launch_stress<T>(g, s->mc, a, s->st, th);
+        if (e != cudaSuccess) return cuda_fail(e, "stress kernel");
+    }
+    {
+        MomentumArgs<T> a;
+        a.U = static_cast<const T*>(s->U[cu]);
+        a.V = static_cast<const T*>(s->V[cu]);
+        a.W = static_cast<const T*>(s->W[cu]);
+        a.P = static_cast<const T*>(s->P);
+        for (int c = 0; c < 6; ++c) {
+            a.Bo[c] = static_cast<const T*>(s->B[cb][c]);
+            a.Bn[c] = static_cast<const T*>(s->B[stress ? 1 - cb : cb][c]);
+        }
+        a.Us = static_cast<T*>(s->U[1 - cu]);
+        a.Vs = static_cast<T*>(s->V[1 - cu]);
+        a.Ws = static_cast<T*>(s->W[1 - cu]);
+        for (int c = 0; c < 3; ++c) a.NH[c] = static_cast<T*>(s->NH[c]);
+        a.dt = T(dt);
+        a.zeta = T(ze);
+        a.xi = T(xi);
+        a.alpha = T(al);
+        a.read_hist = read_hist;
+        a.write_hist = write_hist;
+        a.has_stress = stress;
+        a.dpdx = T(s->prm.dpdx);
+        a.abc_amp = T(s->prm.abc_amp);
+        a.trig = s->prm.abc_amp != 0.0 ? static_cast<const T*>(s->trig) : nullptr;
+        cudaError_t e = launch_momentum<T>(g, s->mc, a, s->st, th);
+        if (e != cudaSuccess) return cuda_fail(e, "momentum kernel");
+    }
+    const double coef = 2.0 * al * dt;
+    int r = run_poisson<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
+                           static_cast<const T*>(s->W[1 - cu]), nullptr, 1.0 / coef, static_cast<T*>(s->PSI));
+    if (r) return r;
+    r = run_correct<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
+                       static_cast<const T*>(s->W[1 - cu]), static_cast<T*>(s->U[cu]), static_cast<T*>(s->V[cu]),
+                       static_cast<T*>(s->W[cu]), static_cast<T*>(s->P), coef);
+    if (r) return r;
+    if (stress) s->cb = 1 - cb;
+    return EVP_OK;
+}
+
+void* field_ptr(evp_state* s, int f) {
+    if (f == EVP_U) return s->U[s->cu];
+    if (f == EVP_V) return s->V[s->cu];
+    if (f == EVP_W) return s->W[s->cu];
+    if (f == EVP_P) return s->P;
+    if (f >= EVP_BXX && f <= EVP_BZZ) return s->B[s->cb][f - EVP_BXX];
+    if (f >= EVP_RT_XX && f < EVP_RT_XX + 6) return s->RT[f - EVP_RT_XX];
+    if (f >= EVP_NH_X && f < EVP_NH_X + 3) return s->NH[f - EVP_NH_X];
+    if (f == EVP_PSI) return s->PSI;
+    return nullptr;
+}
+
+template <typename T>
+int init_fields(evp_state* s) {
+    const size_t N = s->N;
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaMemsetAsync(s->U[b], 0, N * sizeof(T), s->st));
+        CK(cudaMemsetAsync(s->V[b], 0, N * sizeof(T), s->st));
+        CK(cudaMemsetAsync(s->W[b], 0, N * sizeof(T), s->st));
+        for (int c = 0; c < 6; ++c) {
+            const bool diag = (c == 0 || c == 3 || c == 5);
+            if (diag) {
+                k_fill<T><<<(unsigned)((N + 255) / 256), 256, 0, s->st>>>(static_cast<T*>(s->B[b][c]), N, T(1));
+                CK(cudaGetLastError());
+            } else {
+                CK(cudaMemsetAsync(s->B[b][c], 0, N * sizeof(T), s->st));
+            }
+        }
+    }
+    for (int c = 0; c < 6; ++c) CK(cudaMemsetAsync(s->RT[c], 0, N * sizeof(T), s->st));
+    for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(s->NH[c], 0, N * sizeof(T), s->st));
+    CK(cudaMemsetAsync(s->P, 0, N * sizeof(T), s->st));
+    CK(cudaMemsetAsync(s->PSI, 0, N * sizeof(T), s->st));
+    CK(cudaMemsetAsync(s->d_status, 0, sizeof(unsigned), s->st));
+    CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return EVP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* evp_last_error(void) { return g_err.c_str(); }
+
+int evp_num_kernels(void) { return K_COUNT; }
+
+const char* evp_kernel_name(int i) { return (i >= 0 && i < K_COUNT) ? KERNEL_NAMES[i] : ""; }
+
+size_t evp_state_bytes(const evp_grid* grid, evp_model model, const evp_params* params) {
+    if (validate(grid, model, params) != EVP_OK) return 0;
+    evp_state tmp;
+    tmp.g = *grid;
+    tmp.elt = params->precision == EVP_FP32 ? 4 : 8;
+    return plan(&tmp, nullptr);
+}
+
+int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, void* stream, void* arena,
+             size_t arena_bytes, evp_state** out) {
+    if (!out) return fail(EVP_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    int r = validate(grid, model, params);
+    if (r) return r;
+    evp_state* s = new (std::nothrow) evp_state();
+    if (!s) return fail(EVP_ERR_OOM, "host allocation failed");
+    s->g = *grid;
+    s->model = model;
+    s->prm = *params;
+    s->fp32 = params->precision == EVP_FP32;
+    s->elt = s->fp32 ? 4 : 8;
+    s->N = (size_t)grid->nx * grid->ny * grid->nz;
+    s->nxh = grid->nx / 2 + 1;
+    s->timing = false;
+    for (int k = 0; k < K_COUNT; ++k) {
+        s->ms[k] = 0;
+        s->launches[k] = 0;
+    }
+    const double mu0 = 1.0 / params->Re;
+    s->mc.model = model;
+    s->mc.inv_lam = model == EVP_NEWTONIAN ? 0.0 : 1.0 / params->Wi;
+    s->mc.gmod = model == EVP_NEWTONIAN ? 0.0 : (1.0 - params->beta) * mu0 / params->Wi;
+    s->mc.tau_y = params->bi_def == 0 ? params->Bi * mu0 : params->Bi;
+    s->mc.L2 = params->L2;
+    s->mc.a_fene = model == EVP_FENE_P ? params->L2 / (params->L2 - 3.0) : 1.0;
+    s->mc.mu_s = params->beta * mu0;
+    if (stream) {
+        s->st = static_cast<cudaStream_t>(stream);
+        s->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete s;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        s->own_stream = true;
+    }
+    const size_t need = plan(s, nullptr);
+    if (arena) {
+        if (arena_bytes < need) {
+            if (s->own_stream) cudaStreamDestroy(s->st);
+            delete s;
+            return fail(EVP_ERR_OOM, "arena smaller than evp_state_bytes()");
+        }
+        s->arena = static_cast<char*>(arena);
+        s->own_arena = false;
+    } else {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) {
+            if (s->own_stream) cudaStreamDestroy(s->st);
+            delete s;
+            cudaGetLastError();
+            return fail(EVP_ERR_OOM, std::string("cudaMalloc of the state arena failed: ") + cudaGetErrorString(e));
+        }
+        s->arena = static_cast<char*>(p);
+        s->own_arena = true;
+    }
+    s->arena_bytes = need;
+    plan(s, s->arena);
+    s->cu = 0;
+    s->cb = 0;
+    r = s->fp32 ? upload_tables<float>(s) : upload_tables<double>(s);
+    if (!r) r = s->fp32 ? init_fields<float>(s) : init_fields<double>(s);
+    if (r) {
+        std::string keep = g_err;
+        evp_destroy(s);
+        g_err = keep;
+        return r;
+    }
+    *out = s;
+    return EVP_OK;
+}
+
+int evp_destroy(evp_state* s) {
+    if (!s) return EVP_OK;
+    if (s->st) cudaStreamSynchronize(s->st);
+    for (auto& p : s->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : s->ev_free) cudaEventDestroy(e);
+    if (s->own_arena && s->arena) cudaFree(s->arena);
+    if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+    delete s;
+    return EVP_OK;
+}
+
+int evp_set_field(evp_state* s, int field, const void* src, int src_on_device) {
+    if (!s || !src) return fail(EVP_ERR_ARG, "null state or source");
+    if (field == EVP_PSI) return fail(EVP_ERR_ARG, "EVP_PSI is read only");
+    void* dst = field_ptr(s, field);
+    if (!dst) return fail(EVP_ERR_ARG, "unknown field id");
+    const size_t bytes = s->N * s->elt;
+    CK(cudaMemcpyAsync(dst, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+    if (field == EVP_V && s->g.walls_y) {
+        // the stored top face is the wall: v = 0
+        const size_t row = (size_t)s->g.nx * s->elt;
+        CK(cudaMemset2DAsync(static_cast<char*>(dst) + (size_t)(s->g.ny - 1) * row, (size_t)s->g.ny * row, 0, row,
+                             s->g.nz, s->st));
+    }
+    CK(cudaStreamSynchronize(s->st));
+    return EVP_OK;
+}
+
+int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device) {
+    if (!s || !dst) return fail(EVP_ERR_ARG, "null state or destination");
+    const void* src = field_ptr(s, field);
+    if (!src) return fail(EVP_ERR_ARG, "unknown field id");
+    CK(cudaMemcpyAsync(dst, src, s->N * s->elt, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return EVP_OK;
+}
+
+int evp_substep(evp_state* s, double dt, int k) {
+    if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (k < 0 || k > 2) return fail(EVP_ERR_ARG, "substep index must be 0, 1 or 2");
+    if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
+    return s->fp32 ? substep_t<float>(s, dt, k, false) : substep_t<double>(s, dt, k, false);
+}
+
+int evp_step(evp_state* s, double dt) {
+    if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
+    for (int k = 0; k < 3; ++k) {
+        int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2) : substep_t<double>(s, dt, k, k == 2);
+        if (r) return r;
+    }
+    return EVP_OK;
+}
+
+int evp_project(evp_state* s) {
+    if (!s) return fail(EVP_ERR_ARG, "null state");
+    const int cu = s->cu;
+    int r;
+    if (s->fp32) {
+        r = run_poisson<float>(s, (const float*)s->U[cu], (const float*)s->V[cu], (const float*)s->W[cu], nullptr,
+                               1.0, (float*)s->PSI);
+        if (!r)
+            r = run_correct<float>(s, (const float*)s->U[cu], (const float*)s->V[cu], (const float*)s->W[cu],
+                                   (float*)s->U[1 - cu], (float*)s->V[1 - cu], (float*)s->W[1 - cu], nullptr, 1.0);
+    } else {
+        r = run_poisson<double>(s, (const double*)s->U[cu], (const double*)s->V[cu], (const double*)s->W[cu],
+                                nullptr, 1.0, (double*)s->PSI);
+        if (!r)
+            r = run_correct<double>(s, (const double*)s->U[cu], (const double*)s->V[cu], (const double*)s->W[cu],
+                                    (double*)s->U[1 - cu], (double*)s->V[1 - cu], (double*)s->W[1 - cu], nullptr, 1.0);
+    }
+    if (!r) s->cu = 1 - cu;
+    return r;
+}
+
+int evp_poisson_solve(evp_state* s, const void* rhs, void* psi) {
+    if (!s || !rhs || !psi) return fail(EVP_ERR_ARG, "null argument");
+    if (s->fp32) return run_poisson<float>(s, nullptr, nullptr, nullptr, (const float*)rhs, 1.0, (float*)psi);
+    return run_poisson<double>(s, nullptr, nullptr, nullptr, (const double*)rhs, 1.0, (double*)psi);
+}
+
+int evp_stress_rhs(evp_state* s, void* rt) {
+    if (!s || !rt) return fail(EVP_ERR_ARG, "null argument");
+    if (s->model == EVP_NEWTONIAN) return fail(EVP_ERR_STATE, "a Newtonian state has no stress");
+    auto go = [&](auto tag) -> int {
+        using T = decltype(tag);
+        StressArgs<T> a;
+        const int cu = s->cu, cb = s->cb;
+        a.U = static_cast<const T*>(s->U[cu]);
+        a.V = static_cast<const T*>(s->V[cu]);
+        a.W = static_cast<const T*>(s->W[cu]);
+        for (int c = 0; c < 6; ++c) {
+            a.B[c] = static_cast<const T*>(s->B[cb][c]);
+            a.Bn[c] = nullptr;
+            a.RT[c] = static_cast<T*>(rt) + (size_t)c * s->N;
+        }
+        a.dt_zeta = T(0);
+        a.dt_xi = T(0);
+        a.read_hist = 0;
+        a.write_hist = 0;
+        a.rhs_only = 1;
+        a.status = s->d_status;
+        cudaError_t e = launch_stress<T>(geo_of<T>(s), s->mc, a, s->st, hook_of(s));
+        return e == cudaSuccess ? EVP_OK : cuda_fail(e, "stress kernel");
+    };
+    return s->fp32 ? go(float(0)) : go(double(0));
+}
+
+int evp_sync(evp_state* s, unsigned* bits, double* max_div) {
+    if (!s) return fail(EVP_ERR_ARG, "null state");
+    CK(cudaStreamSynchronize(s->st));
+    unsigned st = 0;
+    unsigned long long md = 0;
+    CK(cudaMemcpy(&st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&md, s->d_maxdiv, sizeof(md), cudaMemcpyDeviceToHost));
+    CK(cudaMemsetAsync(s->d_status, 0, sizeof(unsigned), s->st));
+    CK(cudaStreamSynchronize(s->st));
+    if (bits) *bits = st;
+    if (max_div) {
+        double d;
+        std::memcpy(&d, &md, sizeof(d));
+        *max_div = d;
+    }
+    if (st & EVP_BIT_NONFINITE) return fail(EVP_ERR_NONFINITE, "non-finite values in the fields");
+    if (st & (EVP_BIT_TRACE_LIMIT | EVP_BIT_DET_NEG))
+        return fail(EVP_ERR_UNPHYSICAL, "B lost positive definiteness or reached the FENE-P trace limit");
+    return EVP_OK;
+}
+
+int evp_kernel_timing(evp_state* s, int enable) {
+    if (!s) return fail(EVP_ERR_ARG, "null state");
+    flush_timing(s);
+    s->timing = enable != 0;
+    return EVP_OK;
+}
+
+int evp_kernel_times(evp_state* s, double* ms, long long* launches, int n) {
+    if (!s) return fail(EVP_ERR_ARG, "null state");
+    flush_timing(s);
+    for (int k = 0; k < n && k < K_COUNT; ++k) {
+        if (ms) ms[k] = s->ms[k];
+        if (launches) launches[k] = s->launches[k];
+    }
+    for (int k = 0; k < K_COUNT; ++k) {
+        s->ms[k] = 0;
+        s->launches[k] = 0;
+    }
+    return EVP_OK;
+}
+
+}  // extern "C"

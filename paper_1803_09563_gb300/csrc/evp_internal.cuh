@@ -1,0 +1,200 @@
+// Internal declarations shared by the libevp translation units: grid index maps,
+// kernel argument blocks and the launch functions of each kernel family.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "evp.h"
+
+namespace evp {
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+// Kernel identifiers for the per-kernel event timing.
+enum KernelId {
+    K_STRESS = 0,     // S1 + S2: centre velocity/gradient, WENO5 advection, closure, B update
+    K_MOMENTUM,       // S3: momentum predictor u*
+    K_DIV_FFTX,       // S4 + S5(x): Poisson right-hand side fused into the x real-to-complex FFT
+    K_FFT_Z_FWD,      // S5(z): forward complex FFT along z
+    K_SOLVE_Y,        // S5(y) + S6 + S7(y), periodic y: FFT, modal division, inverse FFT
+    K_THOMAS,         // S6, walls: FP64 tridiagonal solve per (kx, kz)
+    K_FFT_Z_INV,      // S7(z): inverse complex FFT along z
+    K_IFFTX,          // S7(x): complex-to-real inverse FFT along x -> psi
+    K_CORRECT,        // S8: u = u* - c grad psi, p += psi, FP64 divergence residual
+    K_COUNT
+};
+
+// Geometry as seen by the kernels.  Spacings are passed as reciprocals.
+template <typename T>
+struct Geo {
+    int nx, ny, nz, walls;
+    T idx, idy, idz;      // 1/dx, 1/dy, 1/dz
+};
+
+// ----------------------------------------------------------------- index maps
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <typename T>
+__device__ __forceinline__ size_t lin(const Geo<T>& g, int i, int j, int k) {
+    return ((size_t)k * g.ny + j) * g.nx + i;
+}
+
+// y index of a cell-centred value: zero-gradient copy at walls, periodic wrap otherwise
+template <typename T>
+__device__ __forceinline__ int ycen(const Geo<T>& g, int j) {
+    if (g.walls) return j < 0 ? 0 : (j >= g.ny ? g.ny - 1 : j);
+    return wrap(j, g.ny);
+}
+
+// u or w (centred in y) at (i, j, k) with i, k wrapped and the no-slip odd ghost in y
+template <typename T>
+__device__ __forceinline__ T ld_uw(const Geo<T>& g, const T* __restrict__ F, int i, int j, int k) {
+    i = wrap(i, g.nx);
+    k = wrap(k, g.nz);
+    if (g.walls) {
+        if (j < 0) return -__ldg(F + lin(g, i, -1 - j, k));
+        if (j >= g.ny) return -__ldg(F + lin(g, i, 2 * g.ny - 1 - j, k));
+        return __ldg(F + lin(g, i, j, k));
+    }
+    return __ldg(F + lin(g, i, wrap(j, g.ny), k));
+}
+
+// v (on y faces) at (i, j, k): zero outside the stored range at walls
+template <typename T>
+__device__ __forceinline__ T ld_v(const Geo<T>& g, const T* __restrict__ F, int i, int j, int k) {
+    i = wrap(i, g.nx);
+    k = wrap(k, g.nz);
+    if (g.walls) {
+        if (j < 0 || j >= g.ny) return T(0);
+        return __ldg(F + lin(g, i, j, k));
+    }
+    return __ldg(F + lin(g, i, wrap(j, g.ny), k));
+}
+
+// centred scalar at (i, j, k)
+template <typename T>
+__device__ __forceinline__ T ld_c(const Geo<T>& g, const T* __restrict__ F, int i, int j, int k) {
+    return __ldg(F + lin(g, wrap(i, g.nx), ycen(g, j), wrap(k, g.nz)));
+}
+
+// ------------------------------------------------------------- model constants
+struct ModelConst {
+    int model;          // evp_model
+    double inv_lam;     // 1/lambda
+    double gmod;        // mu_p / lambda
+    double tau_y;       // Saramito yield stress
+    double L2, a_fene;  // FENE-P L^2 and a = L^2/(L^2-3)
+    double mu_s;        // solvent viscosity
+};
+
+// ------------------------------------------------------------ argument blocks
+template <typename T>
+struct StressArgs {
+    const T* U;
+    const T* V;
+    const T* W;
+    const T* B[6];
+    T* Bn[6];          // B^k (update mode)
+    T* RT[6];          // history RT^{k-2} in / RT^{k-1} out (update), or RT out (rhs mode)
+    T dt_zeta, dt_xi;
+    int read_hist, write_hist, rhs_only;
+    unsigned* status;
+};
+
+template <typename T>
+struct MomentumArgs {
+    const T* U;
+    const T* V;
+    const T* W;
+    const T* P;
+    const T* Bo[6];    // B^{k-1}
+    const T* Bn[6];    // B^k
+    T* Us;
+    T* Vs;
+    T* Ws;             // u* out
+    T* NH[3];          // history N^{k-2} in / N^{k-1} out
+    T dt, zeta, xi, alpha;
+    int read_hist, write_hist, has_stress;
+    T dpdx, abc_amp;
+    const T* trig;     // ABC force tables: sin/cos of k x_i, k y_j, k z_k (6 arrays)
+};
+
+template <typename T>
+struct FFTTables {
+    const typename Cplx<T>::type* twx;   // exp(-2 pi i m / nx), m < nx
+    const typename Cplx<T>::type* twy;
+    const typename Cplx<T>::type* twz;
+    int radx[12], nrx;
+    int rady[12], nry;
+    int radz[12], nrz;
+    const T* lamx;     // modal eigenvalues (2 - 2cos(2 pi m/n))/h^2, T precision
+    const T* lamy;
+    const T* lamz;
+    const double* thomas_m;   // walls: pivot reciprocals [nz/2+1][ny][nxh]
+    double idy2;              // 1/dy^2 in FP64 (Thomas off-diagonals)
+};
+
+template <typename T>
+struct PoissonArgs {
+    // right-hand side: either divergence of (Us, Vs, Ws) times rscale, or a given field
+    const T* Us;
+    const T* Vs;
+    const T* Ws;
+    const T* rhs;      // if non-null, used instead of the divergence
+    T rscale;
+    typename Cplx<T>::type* spec;     // [nz][ny][nxh] complex
+    T* psi;            // psi out
+    double norm;       // 1/(nx nz) (walls) or 1/(nx ny nz) (periodic)
+};
+
+template <typename T>
+struct CorrectArgs {
+    const T* Us;
+    const T* Vs;
+    const T* Ws;
+    const T* psi;
+    T* U;
+    T* V;
+    T* W;
+    T* P;              // p += psi if non-null
+    T coef;            // 2 alpha dt (or 1 for a plain projection)
+    unsigned long long* maxdiv;   // FP64 bits of max |div u|
+    unsigned* status;
+    double idx_d, idy_d, idz_d;   // FP64 reciprocal spacings for the residual
+};
+
+// ----------------------------------------------------------- launch functions
+// Each returns cudaSuccess or the launch error; ``t`` is a timing hook that
+// records events around the launch when enabled.
+struct TimingHook {
+    void (*begin)(void* ctx, int kid);
+    void (*end)(void* ctx, int kid);
+    void* ctx;
+    void b(int kid) const { if (begin) begin(ctx, kid); }
+    void e(int kid) const { if (end) end(ctx, kid); }
+};
+
+template <typename T>
+cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a,
+                          cudaStream_t st, const TimingHook& th);
+
+template <typename T>
+cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const MomentumArgs<T>& a,
+                            cudaStream_t st, const TimingHook& th);
+
+template <typename T>
+cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a,
+                           cudaStream_t st, const TimingHook& th);
+
+template <typename T>
+cudaError_t launch_correct(const Geo<T>& g, const CorrectArgs<T>& a, cudaStream_t st,
+                           const TimingHook& th);
+
+// radix plan of n = 4^a 3^b 2^c (radix-4 first); returns the number of stages or -1
+int fft_radices(int n, int* rad);
+
+}  // namespace evp

@@ -1,0 +1,443 @@
+// S4-S8: the fast Poisson solver and projection of Eqs. NS-num2 and NS-num3.
+//
+//   lap(psi) = div(u*) / (2 alpha^k dt);  u^k = u* - 2 alpha^k dt grad(psi);  p^k = p^{k-1} + psi
+//
+// psi is found with FFTs in the periodic directions and, along a wall-bounded y,
+// an FP64 tridiagonal (Thomas) solve per Fourier mode; the modal eigenvalues are
+// those of the discrete 7-point Laplacian, (2 - 2 cos(2 pi m/n))/h^2.
+//
+// Passes over the spectral buffer spec[nz][ny][nx/2+1] (complex):
+//   k_div_fftx    divergence of u* (scaled) fused into the x real-to-complex FFT;
+//                 two real lines are packed into one complex FFT and split after.
+//   k_fft_col     forward complex FFT along z (columns of TK consecutive kx).
+//   k_fft_col     periodic y: forward FFT along y, modal division, inverse FFT,
+//                 all in shared memory (one pass).
+//   k_thomas      walls: FP64 Thomas sweep along y per (kx, kz), pivots from a table.
+//   k_fft_col     inverse FFT along z.
+//   k_ifftx       x complex-to-real inverse FFT -> psi.
+//   k_correct     u = u* - c grad psi, p += psi, FP64 max |div u|.
+//
+// The FFT is a Stockham auto-sort transform in shared memory with radix-4, -3 and
+// -2 stages (n = 2^a 3^b), twiddles read from a table exp(-2 pi i m/n).
+#include <cfloat>
+
+#include "evp_internal.cuh"
+
+namespace evp {
+
+namespace {
+
+template <typename T>
+using C = typename Cplx<T>::type;
+
+template <typename T>
+__device__ __forceinline__ C<T> mk(T x, T y) {
+    C<T> r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ C<T> add(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ C<T> sub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T, bool INV>
+__device__ __forceinline__ C<T> twmul(C<T> a, C<T> w) {
+    if (INV) w.y = -w.y;
+    return mk<T>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV>
+__device__ __forceinline__ C<T> rot(C<T> a) { return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x); }
+
+// One Stockham pass structure over ``nlines`` lines held in shared memory:
+// element (line l, index m) at buf[l*ls + m*es].  Butterflies j are spread over
+// (tj, nj) and lines over (tl, nl).  Returns the buffer holding the result.
+template <typename T, bool INV>
+__device__ C<T>* fft_smem(C<T>* a, C<T>* b, int n, const int* rad, int nst, const C<T>* __restrict__ tw,
+                          int nlines, int es, int ls, int tj, int nj, int tl, int nl) {
+    int Ns = 1;
+    for (int s = 0; s < nst; ++s) {
+        const int R = rad[s];
+        const int nR = n / R;
+        const int tws = n / (Ns * R);
+        for (int jb = tj; jb < nR; jb += nj) {
+            const int kk = jb % Ns;
+            const int dbase = (jb - kk) * R + kk;
+            const C<T> w1 = __ldg(tw + kk * tws);
+            if (R == 4) {
+                const C<T> w2 = __ldg(tw + 2 * kk * tws), w3 = __ldg(tw + 3 * kk * tws);
+                for (int l = tl; l < nlines; l += nl) {
+                    const C<T>* s0 = a + (size_t)l * ls;
+                    C<T>* d0 = b + (size_t)l * ls;
+                    C<T> x0 = s0[(jb) * es];
+                    C<T> x1 = twmul<T, INV>(s0[(jb + nR) * es], w1);
+                    C<T> x2 = twmul<T, INV>(s0[(jb + 2 * nR) * es], w2);
+                    C<T> x3 = twmul<T, INV>(s0[(jb + 3 * nR) * es], w3);
+                    const C<T> s02 = add<T>(x0, x2), d02 = sub<T>(x0, x2);
+                    const C<T> s13 = add<T>(x1, x3), r13 = rot<T, INV>(sub<T>(x1, x3));
+                    d0[(dbase) * es] = add<T>(s02, s13);
+                    d0[(dbase + Ns) * es] = add<T>(d02, r13);
+                    d0[(dbase + 2 * Ns) * es] = sub<T>(s02, s13);
+                    d0[(dbase + 3 * Ns) * es] = sub<T>(d02, r13);
+                }
+            } else if (R == 3) {
+                const C<T> w2 = __ldg(tw + 2 * kk * tws);
+                const T h3 = T(0.86602540378443864676);   // sin(2 pi / 3)
+                for (int l = tl; l < nlines; l += nl) {
+                    const C<T>* s0 = a + (size_t)l * ls;
+                    C<T>* d0 = b + (size_t)l * ls;
+                    C<T> x0 = s0[(jb) * es];
+                    C<T> x1 = twmul<T, INV>(s0[(jb + nR) * es], w1);
+                    C<T> x2 = twmul<T, INV>(s0[(jb + 2 * nR) * es], w2);
+                    const C<T> s = add<T>(x1, x2), d = sub<T>(x1, x2);
+                    const C<T> m = mk<T>(x0.x - T(0.5) * s.x, x0.y - T(0.5) * s.y);
+                    const C<T> r = rot<T, INV>(d);
+                    const C<T> t = mk<T>(h3 * r.x, h3 * r.y);
+                    d0[(dbase) * es] = add<T>(x0, s);
+                    d0[(dbase + Ns) * es] = add<T>(m, t);
+                    d0[(dbase + 2 * Ns) * es] = sub<T>(m, t);
+                }
+            } else {
+                for (int l = tl; l < nlines; l += nl) {
+                    const C<T>* s0 = a + (size_t)l * ls;
+                    C<T>* d0 = b + (size_t)l * ls;
+                    C<T> x0 = s0[(jb) * es];
+                    C<T> x1 = twmul<T, INV>(s0[(jb + nR) * es], w1);
+                    d0[(dbase) * es] = add<T>(x0, x1);
+                    d0[(dbase + Ns) * es] = sub<T>(x0, x1);
+                }
+            }
+        }
+        __syncthreads();
+        C<T>* t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// right-hand side value of real line L (= k*ny + j) at x index i
+template <typename T>
+__device__ __forceinline__ T rhs_value(const Geo<T>& g, const PoissonArgs<T>& a, int L, int i) {
+    if (a.rhs) return __ldg(a.rhs + (size_t)L * g.nx + i);
+    const int j = L % g.ny, k = L / g.ny;
+    const size_t c0 = (size_t)L * g.nx + i;
+    const T du = __ldg(a.Us + c0) - ld_uw(g, a.Us, i - 1, j, k);
+    const T dv = __ldg(a.Vs + c0) - ld_v(g, a.Vs, i, j - 1, k);
+    const T dw = __ldg(a.Ws + c0) - ld_uw(g, a.Ws, i, j, k - 1);
+    return (du * g.idx + dv * g.idy + dw * g.idz) * a.rscale;
+}
+
+// S4 + S5(x): r = div(u*)/(2 alpha dt) fused into the x real-to-complex FFT.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_div_fftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nx = g.nx, nxh = nx / 2 + 1;
+    C<T>* sa = reinterpret_cast<C<T>*>(smraw);
+    C<T>* sb = sa + (size_t)np * nx;
+    const int NL = g.ny * g.nz;
+    const int q0 = blockIdx.x * np;
+    for (int l = threadIdx.y; l < np; l += blockDim.y) {
+        const int L0 = 2 * (q0 + l), L1 = L0 + 1;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const T r0 = L0 < NL ? rhs_value(g, a, L0, i) : T(0);
+            const T r1 = L1 < NL ? rhs_value(g, a, L1, i) : T(0);
+            sa[(size_t)l * nx + i] = mk<T>(r0, r1);
+        }
+    }
+    __syncthreads();
+    C<T>* res = fft_smem<T, false>(sa, sb, nx, tb.radx, tb.nrx, tb.twx, np, 1, nx, threadIdx.x, blockDim.x,
+                                   threadIdx.y, blockDim.y);
+    // split the packed pair: A_m = (Z_m + conj Z_{n-m})/2, B_m = (Z_m - conj Z_{n-m})/(2i)
+    for (int l = threadIdx.y; l < np; l += blockDim.y) {
+        const int L0 = 2 * (q0 + l), L1 = L0 + 1;
+        if (L0 >= NL) continue;
+        for (int m = threadIdx.x; m < nxh; m += blockDim.x) {
+            const C<T> Z = res[(size_t)l * nx + m];
+            const C<T> Zr = res[(size_t)l * nx + (m == 0 ? 0 : nx - m)];
+            a.spec[(size_t)L0 * nxh + m] = mk<T>(T(0.5) * (Z.x + Zr.x), T(0.5) * (Z.y - Zr.y));
+            if (L1 < NL) a.spec[(size_t)L1 * nxh + m] = mk<T>(T(0.5) * (Z.y + Zr.y), T(0.5) * (Zr.x - Z.x));
+        }
+    }
+}
+
+// S7(x): complex-to-real inverse FFT along x of two lines per complex FFT -> psi
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_ifftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nx = g.nx, nxh = nx / 2 + 1, half = nx / 2;
+    C<T>* sa = reinterpret_cast<C<T>*>(smraw);
+    C<T>* sb = sa + (size_t)np * nx;
+    const int NL = g.ny * g.nz;
+    const int q0 = blockIdx.x * np;
+    for (int l = threadIdx.y; l < np; l += blockDim.y) {
+        const int L0 = 2 * (q0 + l), L1 = L0 + 1;
+        for (int m = threadIdx.x; m < nx; m += blockDim.x) {
+            C<T> A = mk<T>(T(0), T(0)), B = mk<T>(T(0), T(0));
+            const int mm = m <= half ? m : nx - m;
+            if (L0 < NL) A = a.spec[(size_t)L0 * nxh + mm];
+            if (L1 < NL) B = a.spec[(size_t)L1 * nxh + mm];
+            if (mm == 0 || mm == half) {   // DC and Nyquist of a real line are real
+                A.y = T(0);
+                B.y = T(0);
+            }
+            if (m > half) {                // Hermitian extension
+                A.y = -A.y;
+                B.y = -B.y;
+            }
+            sa[(size_t)l * nx + m] = mk<T>(A.x - B.y, A.y + B.x);
+        }
+    }
+    __syncthreads();
+    C<T>* res = fft_smem<T, true>(sa, sb, nx, tb.radx, tb.nrx, tb.twx, np, 1, nx, threadIdx.x, blockDim.x,
+                                  threadIdx.y, blockDim.y);
+    for (int l = threadIdx.y; l < np; l += blockDim.y) {
+        const int L0 = 2 * (q0 + l), L1 = L0 + 1;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const C<T> z = res[(size_t)l * nx + i];
+            if (L0 < NL) a.psi[(size_t)L0 * nx + i] = z.x;
+            if (L1 < NL) a.psi[(size_t)L1 * nx + i] = z.y;
+        }
+    }
+}
+
+// Column FFT along z (or y) over TK consecutive kx.  SOLVE (periodic y pass):
+// forward FFT, multiply by -norm/(lx+ly+lz) (zero mode -> 0), inverse FFT.
+template <typename T, bool INV, bool SOLVE>
+__global__ void __launch_bounds__(256)
+k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axis_y, size_t estride,
+          size_t ostride, int tk) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = axis_y ? g.ny : g.nz;
+    const int* rad = axis_y ? tb.rady : tb.radz;
+    const int nrad = axis_y ? tb.nry : tb.nrz;
+    const C<T>* tw = axis_y ? tb.twy : tb.twz;
+    C<T>* sa = reinterpret_cast<C<T>*>(smraw);
+    C<T>* sb = sa + (size_t)n * tk;
+    const int nxh = g.nx / 2 + 1;
+    const int kx0 = blockIdx.x * tk;
+    const size_t base = blockIdx.y * ostride;
+    for (int m = threadIdx.y; m < n; m += blockDim.y)
+        for (int t = threadIdx.x; t < tk; t += blockDim.x) {
+            const int kx = kx0 + t;
+            sa[(size_t)m * tk + t] = kx < nxh ? a.spec[base + m * estride + kx] : mk<T>(T(0), T(0));
+        }
+    __syncthreads();
+    C<T>* res = fft_smem<T, INV>(sa, sb, n, rad, nrad, tw, tk, tk, 1, threadIdx.y, blockDim.y, threadIdx.x,
+                                 blockDim.x);
+    if (SOLVE) {
+        const int kz = blockIdx.y;
+        const T lz = __ldg(tb.lamz + kz);
+        for (int m = threadIdx.y; m < n; m += blockDim.y)
+            for (int t = threadIdx.x; t < tk; t += blockDim.x) {
+                const int kx = kx0 + t;
+                if (kx >= nxh) continue;
+                const T lam = __ldg(tb.lamx + kx) + __ldg(tb.lamy + m) + lz;
+                const T f = lam == T(0) ? T(0) : T(-a.norm) / lam;
+                C<T> v = res[(size_t)m * tk + t];
+                res[(size_t)m * tk + t] = mk<T>(v.x * f, v.y * f);
+            }
+        __syncthreads();
+        C<T>* other = (res == sa) ? sb : sa;
+        res = fft_smem<T, true>(res, other, n, rad, nrad, tw, tk, tk, 1, threadIdx.y, blockDim.y, threadIdx.x,
+                                blockDim.x);
+    }
+    for (int m = threadIdx.y; m < n; m += blockDim.y)
+        for (int t = threadIdx.x; t < tk; t += blockDim.x) {
+            const int kx = kx0 + t;
+            if (kx < nxh) a.spec[base + m * estride + kx] = res[(size_t)m * tk + t];
+        }
+}
+
+// S6 with walls: for each (kx, kz) solve
+//   psi_{j-1}/dy^2 - (2/dy^2 + lx + lz) psi_j + psi_{j+1}/dy^2 = r_j
+// with Neumann rows at j = 0 and ny-1 and the (0, 0) system pinned by psi_0 = 0,
+// in FP64.  m_j = 1/(b_j - a_j c'_{j-1}) comes from a host-built FP64 table;
+// the forward sweep keeps d'_j in shared memory for the back substitution.
+template <typename T>
+__global__ void __launch_bounds__(64)
+k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, double idy2) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double2* dp = reinterpret_cast<double2*>(smraw);   // [ny][blockDim.x]
+    const int nxh = g.nx / 2 + 1, ny = g.ny, nz = g.nz;
+    const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int kz = blockIdx.y;
+    if (kx >= nxh) return;
+    const int kzh = kz <= nz - kz ? kz : nz - kz;
+    const bool pinned = (kx == 0 && kz == 0);
+    const double* M = tb.thomas_m + (size_t)kzh * ny * nxh + kx;
+    C<T>* col = a.spec + (size_t)kz * ny * nxh + kx;
+    const int tb_ = blockDim.x, t = threadIdx.x;
+    const double nrm = a.norm;
+    double px = 0.0, py = 0.0;
+    for (int j = 0; j < ny; ++j) {
+        const C<T> r = col[(size_t)j * nxh];
+        double rx = double(r.x) * nrm, ry = double(r.y) * nrm;
+        if (pinned && j == 0) rx = ry = 0.0;
+        const double lo = j > 0 ? idy2 : 0.0;
+        const double m = __ldg(M + (size_t)j * nxh);
+        px = (rx - lo * px) * m;
+        py = (ry - lo * py) * m;
+        dp[(size_t)j * tb_ + t] = make_double2(px, py);
+    }
+    double xx = px, xy = py;
+    col[(size_t)(ny - 1) * nxh] = mk<T>(T(xx), T(xy));
+    for (int j = ny - 2; j >= 0; --j) {
+        const double up = (pinned && j == 0) ? 0.0 : idy2;
+        const double cpj = up * __ldg(M + (size_t)j * nxh);
+        const double2 d = dp[(size_t)j * tb_ + t];
+        xx = d.x - cpj * xx;
+        xy = d.y - cpj * xy;
+        col[(size_t)j * nxh] = mk<T>(T(xx), T(xy));
+    }
+}
+
+// S8: u^k = u* - c grad psi at the faces, p += psi, FP64 max |div u^k|
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, double idz_d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    double dmax = 0.0;
+    unsigned bits = 0;
+    if (i < g.nx && j < g.ny) {
+        const size_t c0 = lin(g, i, j, k);
+        const T c = a.coef;
+        const T pc = __ldg(a.psi + c0);
+        const T px = ld_c(g, a.psi, i + 1, j, k), py = ld_c(g, a.psi, i, j + 1, k), pz = ld_c(g, a.psi, i, j, k + 1);
+        const T Un = __ldg(a.Us + c0) - c * ((px - pc) * g.idx);
+        const bool top = g.walls && j == g.ny - 1;
+        const T Vn = top ? T(0) : __ldg(a.Vs + c0) - c * ((py - pc) * g.idy);
+        const T Wn = __ldg(a.Ws + c0) - c * ((pz - pc) * g.idz);
+        a.U[c0] = Un;
+        a.V[c0] = Vn;
+        a.W[c0] = Wn;
+        if (a.P) a.P[c0] += pc;
+        // the faces below the cell, recomputed the way their owners write them
+        const T pxm = ld_c(g, a.psi, i - 1, j, k), pym = ld_c(g, a.psi, i, j - 1, k), pzm = ld_c(g, a.psi, i, j, k - 1);
+        const T Ul = ld_uw(g, a.Us, i - 1, j, k) - c * ((pc - pxm) * g.idx);
+        const T Vl = (g.walls && j == 0) ? T(0) : ld_v(g, a.Vs, i, j - 1, k) - c * ((pc - pym) * g.idy);
+        const T Wl = ld_uw(g, a.Ws, i, j, k - 1) - c * ((pc - pzm) * g.idz);
+        const double dv = (double(Un) - double(Ul)) * idx_d + (double(Vn) - double(Vl)) * idy_d
+                          + (double(Wn) - double(Wl)) * idz_d;
+        dmax = fabs(dv);
+        if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn)) bits |= EVP_BIT_NONFINITE;
+        if (!(dmax <= DBL_MAX)) {
+            dmax = 0.0;
+            bits |= EVP_BIT_NONFINITE;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (dmax > 0.0) atomicMax(a.maxdiv, (unsigned long long)__double_as_longlong(dmax));
+        if (bits) atomicOr(a.status, bits);
+    }
+}
+
+template <typename T>
+size_t col_smem(int n, int tk) { return 2 * (size_t)n * tk * sizeof(C<T>); }
+
+template <typename T>
+void set_smem(const void* f, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+int fft_radices(int n, int* rad) {
+    int s = 0;
+    while (n % 4 == 0 && n > 2) { rad[s++] = 4; n /= 4; }
+    while (n % 3 == 0) { rad[s++] = 3; n /= 3; }
+    while (n % 2 == 0) { rad[s++] = 2; n /= 2; }
+    return n == 1 ? s : -1;
+}
+
+template <typename T>
+cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a, cudaStream_t st,
+                           const TimingHook& th) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = nx / 2 + 1;
+    const int NL = ny * nz;
+    // ---- x pass: np complex lines (2 np real lines) per block
+    const int np = nx >= 2048 ? 1 : 2048 / nx;
+    const int tx = nx >= 512 ? 128 : (nx >= 256 ? 64 : 32);
+    dim3 bx(tx, 256 / tx);
+    const int npairs = (NL + 1) / 2;
+    dim3 gx((npairs + np - 1) / np);
+    const size_t smx = 2 * (size_t)np * nx * sizeof(C<T>);
+    set_smem<T>((const void*)k_div_fftx<T>, smx);
+    th.b(K_DIV_FFTX);
+    k_div_fftx<T><<<gx, bx, smx, st>>>(g, tb, a, np);
+    th.e(K_DIV_FFTX);
+
+    const int tk = sizeof(T) == 4 ? 16 : 8;
+    dim3 bc(tk, 256 / tk);
+    // ---- forward z
+    {
+        dim3 gc((nxh + tk - 1) / tk, ny);
+        const size_t sm = col_smem<T>(nz, tk);
+        set_smem<T>((const void*)k_fft_col<T, false, false>, sm);
+        th.b(K_FFT_Z_FWD);
+        k_fft_col<T, false, false><<<gc, bc, sm, st>>>(g, tb, a, 0, (size_t)ny * nxh, (size_t)nxh, tk);
+        th.e(K_FFT_Z_FWD);
+    }
+    if (!g.walls) {
+        dim3 gc((nxh + tk - 1) / tk, nz);
+        const size_t sm = col_smem<T>(ny, tk);
+        set_smem<T>((const void*)k_fft_col<T, false, true>, sm);
+        th.b(K_SOLVE_Y);
+        k_fft_col<T, false, true><<<gc, bc, sm, st>>>(g, tb, a, 1, (size_t)nxh, (size_t)ny * nxh, tk);
+        th.e(K_SOLVE_Y);
+    } else {
+        const int tt = ny <= 256 ? 32 : 16;
+        dim3 gt((nxh + tt - 1) / tt, nz);
+        const size_t sm = (size_t)ny * tt * sizeof(double2);
+        set_smem<T>((const void*)k_thomas<T>, sm);
+        th.b(K_THOMAS);
+        k_thomas<T><<<gt, tt, sm, st>>>(g, tb, a, tb.idy2);
+        th.e(K_THOMAS);
+    }
+    // ---- inverse z
+    {
+        dim3 gc((nxh + tk - 1) / tk, ny);
+        const size_t sm = col_smem<T>(nz, tk);
+        set_smem<T>((const void*)k_fft_col<T, true, false>, sm);
+        th.b(K_FFT_Z_INV);
+        k_fft_col<T, true, false><<<gc, bc, sm, st>>>(g, tb, a, 0, (size_t)ny * nxh, (size_t)nxh, tk);
+        th.e(K_FFT_Z_INV);
+    }
+    set_smem<T>((const void*)k_ifftx<T>, smx);
+    th.b(K_IFFTX);
+    k_ifftx<T><<<gx, bx, smx, st>>>(g, tb, a, np);
+    th.e(K_IFFTX);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_correct(const Geo<T>& g, const CorrectArgs<T>& a, cudaStream_t st, const TimingHook& th) {
+    dim3 block(32, 8, 1);
+    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    th.b(K_CORRECT);
+    k_correct<T><<<grid, block, 0, st>>>(g, a, a.idx_d, a.idy_d, a.idz_d);
+    th.e(K_CORRECT);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_poisson<float>(const Geo<float>&, const FFTTables<float>&, const PoissonArgs<float>&,
+                                           cudaStream_t, const TimingHook&);
+template cudaError_t launch_poisson<double>(const Geo<double>&, const FFTTables<double>&,
+                                            const PoissonArgs<double>&, cudaStream_t, const TimingHook&);
+template cudaError_t launch_correct<float>(const Geo<float>&, const CorrectArgs<float>&, cudaStream_t,
+                                           const TimingHook&);
+template cudaError_t launch_correct<double>(const Geo<double>&, const CorrectArgs<double>&, cudaStream_t,
+                                            const TimingHook&);
+
+}  // namespace evp

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libevp (include/evp.h).  Argument marshalling only:
+every step of the time step runs in the library's CUDA kernels.  There is no
+fallback -- if libevp.so is missing or cannot be loaded, ``load()`` raises.
+
+The functions keep the C names (``evp_init``, ``evp_step``, ...).  Arrays may be
+torch tensors (CUDA or CPU) or numpy arrays; device tensors are passed by
+pointer (``on_device=1``), host arrays by host pointer.
+"""
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_size_t, c_uint, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, 'libevp.so')
+
+# evp_status
+EVP_OK, EVP_ERR_ARG, EVP_ERR_OOM, EVP_ERR_CUDA, EVP_ERR_NONFINITE, EVP_ERR_UNPHYSICAL, EVP_ERR_TIMEOUT, \
+    EVP_ERR_STATE = range(8)
+EVP_BIT_NONFINITE, EVP_BIT_TRACE_LIMIT, EVP_BIT_DET_NEG = 0x1, 0x2, 0x4
+# evp_model
+EVP_NEWTONIAN, EVP_OLDROYD_B, EVP_FENE_P, EVP_SARAMITO = range(4)
+MODEL_IDS = {'newtonian': 0, 'oldroyd_b': 1, 'fene_p': 2, 'saramito': 3}
+EVP_FP64, EVP_FP32 = 0, 1
+EVP_RK3, EVP_AB2 = 0, 1
+# evp_field
+EVP_U, EVP_V, EVP_W, EVP_P = 0, 1, 2, 3
+EVP_BXX, EVP_BXY, EVP_BXZ, EVP_BYY, EVP_BYZ, EVP_BZZ = range(4, 10)
+EVP_RT_XX = 10
+EVP_NH_X = 16
+EVP_PSI = 19
+
+
+class evp_grid(ctypes.Structure):
+    _fields_ = [('nx', c_int), ('ny', c_int), ('nz', c_int), ('lx', c_double), ('ly', c_double),
+                ('lz', c_double), ('walls_y', c_int)]
+
+
+class evp_params(ctypes.Structure):
+    _fields_ = [('Re', c_double), ('Wi', c_double), ('beta', c_double), ('Bi', c_double), ('L2', c_double),
+                ('bi_def', c_int), ('dpdx', c_double), ('abc_amp', c_double), ('abc_k', c_double),
+                ('precision', c_int), ('integrator', c_int), ('reserved', c_double * 16)]
+
+
+class EvpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f'libevp error {code}: {msg}')
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libevp.so (built by ``paper_1803_09563_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f'libevp.so not found at {path}: build it with '
+                           '`python -c "import __graft_entry__ as g; g.build()"`')
+    lib = ctypes.CDLL(path)
+    sig = {
+        'evp_state_bytes': (c_size_t, [POINTER(evp_grid), c_int, POINTER(evp_params)]),
+        'evp_init': (c_int, [POINTER(evp_grid), c_int, POINTER(evp_params), c_void_p, c_void_p, c_size_t,
+                             POINTER(c_void_p)]),
+        'evp_destroy': (c_int, [c_void_p]),
+        'evp_set_field': (c_int, [c_void_p, c_int, c_void_p, c_int]),
+        'evp_get_field': (c_int, [c_void_p, c_int, c_void_p, c_int]),
+        'evp_step': (c_int, [c_void_p, c_double]),
+        'evp_substep': (c_int, [c_void_p, c_double, c_int]),
+        'evp_project': (c_int, [c_void_p]),
+        'evp_poisson_solve': (c_int, [c_void_p, c_void_p, c_void_p]),
+        'evp_stress_rhs': (c_int, [c_void_p, c_void_p]),
+        'evp_sync': (c_int, [c_void_p, POINTER(c_uint), POINTER(c_double)]),
+        'evp_kernel_timing': (c_int, [c_void_p, c_int]),
+        'evp_kernel_times': (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), c_int]),
+        'evp_kernel_name': (c_char_p, [c_int]),
+        'evp_num_kernels': (c_int, []),
+        'evp_last_error': (c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names declared in include/evp.h that the binding resolves."""
+    return ['evp_state_bytes', 'evp_init', 'evp_destroy', 'evp_set_field', 'evp_get_field', 'evp_step',
+            'evp_substep', 'evp_project', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_sync', 'evp_kernel_timing',
+            'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error']
+
+
+def _check(code):
+    if code != EVP_OK:
+        raise EvpError(code, load().evp_last_error().decode())
+    return code
+
+
+def _ptr(a):
+    """(pointer, on_device, nbytes) of a torch tensor or numpy array (contiguous)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            assert a.is_contiguous()
+            if a.is_cuda:
+                # the library works on its own stream: finish torch's pending work on the tensor
+                torch.cuda.current_stream(a.device).synchronize()
+            return a.data_ptr(), int(a.is_cuda), a.numel() * a.element_size()
+    except ImportError:
+        pass
+    assert isinstance(a, np.ndarray) and a.flags['C_CONTIGUOUS']
+    return a.ctypes.data, 0, a.nbytes
+
+
+def make_grid(nx, ny, nz, lx, ly, lz, walls_y=False):
+    return evp_grid(int(nx), int(ny), int(nz), float(lx), float(ly), float(lz), int(bool(walls_y)))
+
+
+def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_amp=0.0, abc_k=0.0,
+                precision=EVP_FP64, integrator=EVP_RK3):
+    p = evp_params()
+    p.Re, p.Wi, p.beta, p.Bi, p.L2 = float(Re), float(Wi), float(beta), float(Bi), float(L2)
+    p.bi_def, p.dpdx, p.abc_amp, p.abc_k = int(bi_def), float(dpdx), float(abc_amp), float(abc_k)
+    p.precision, p.integrator = int(precision), int(integrator)
+    return p
+
+
+def evp_state_bytes(grid, model, params):
+    return load().evp_state_bytes(ctypes.byref(grid), int(model), ctypes.byref(params))
+
+
+def evp_init(grid, model, params, stream=None, arena=None, arena_bytes=0):
+    h = c_void_p()
+    _check(load().evp_init(ctypes.byref(grid), int(model), ctypes.byref(params), stream, arena,
+                           arena_bytes, ctypes.byref(h)))
+    return h
+
+
+def evp_destroy(state):
+    return _check(load().evp_destroy(state))
+
+
+def evp_set_field(state, field, src):
+    p, dev, _ = _ptr(src)
+    return _check(load().evp_set_field(state, int(field), p, dev))
+
+
+def evp_get_field(state, field, dst):
+    p, dev, _ = _ptr(dst)
+    return _check(load().evp_get_field(state, int(field), p, dev))
+
+
+def evp_step(state, dt):
+    return _check(load().evp_step(state, float(dt)))
+
+
+def evp_substep(state, dt, k):
+    return _check(load().evp_substep(state, float(dt), int(k)))
+
+
+def evp_project(state):
+    return _check(load().evp_project(state))
+
+
+def evp_poisson_solve(state, rhs, psi):
+    return _check(load().evp_poisson_solve(state, _ptr(rhs)[0], _ptr(psi)[0]))
+
+
+def evp_stress_rhs(state, rt):
+    return _check(load().evp_stress_rhs(state, _ptr(rt)[0]))
+
+
+def evp_sync(state, raise_on_error=True):
+    """Returns (code, status bits, max |div u| of the last projection)."""
+    bits = c_uint(0)
+    md = c_double(0.0)
+    code = load().evp_sync(state, ctypes.byref(bits), ctypes.byref(md))
+    if raise_on_error and code not in (EVP_OK,):
+        _check(code)
+    return code, bits.value, md.value
+
+
+def evp_kernel_timing(state, enable):
+    return _check(load().evp_kernel_timing(state, int(bool(enable))))
+
+
+def evp_kernel_times(state):
+    """{kernel name: (total ms, launches)} since the last call (synchronises)."""
+    lib = load()
+    n = lib.evp_num_kernels()
+    ms = (c_double * n)()
+    cnt = (c_longlong * n)()
+    _check(lib.evp_kernel_times(state, ms, cnt, n))
+    return {lib.evp_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(n)}
+
+
+def evp_last_error():
+    return load().evp_last_error().decode()
+
+
+class Simulation:
+    """Owns one libevp state; fields move as numpy float64 arrays (converted to the
+    state's precision) or as CUDA tensors of that precision."""
+
+    def __init__(self, grid, model, params, stream=None):
+        import torch
+        self.grid, self.params = grid, params
+        self.model = MODEL_IDS[model] if isinstance(model, str) else int(model)
+        self.shape = (grid.nz, grid.ny, grid.nx)
+        self.dtype = torch.float32 if params.precision == EVP_FP32 else torch.float64
+        self.np_dtype = np.float32 if params.precision == EVP_FP32 else np.float64
+        self.handle = evp_init(grid, self.model, params, stream)
+
+    def close(self):
+        if self.handle is not None:
+            evp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set(self, field, arr):
+        import torch
+        if isinstance(arr, torch.Tensor):
+            t = arr.to(self.dtype).contiguous()
+        else:
+            t = np.ascontiguousarray(np.asarray(arr, dtype=self.np_dtype).reshape(self.shape))
+        evp_set_field(self.handle, field, t)
+
+    def get(self, field, device=False):
+        import torch
+        if device:
+            out = torch.empty(self.shape, dtype=self.dtype, device='cuda')
+        else:
+            out = np.empty(self.shape, dtype=self.np_dtype)
+        evp_get_field(self.handle, field, out)
+        return out
+
+    def set_state(self, U=None, V=None, W=None, p=None, B=None):
+        for f, a in ((EVP_U, U), (EVP_V, V), (EVP_W, W), (EVP_P, p)):
+            if a is not None:
+                self.set(f, a)
+        if B is not None:
+            for c in range(6):
+                self.set(EVP_BXX + c, B[c])
+
+    def step(self, dt):
+        evp_step(self.handle, dt)
+
+    def substep(self, dt, k):
+        evp_substep(self.handle, dt, k)
+
+    def project(self):
+        evp_project(self.handle)
+
+    def sync(self, raise_on_error=True):
+        return evp_sync(self.handle, raise_on_error)

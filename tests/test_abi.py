@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol that
+include/evp.h declares (no compute calls)."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, 'include', 'evp.h')).read()
+    src = re.sub(r'/\*.*?\*/', '', src, flags=re.S)
+    return sorted(set(re.findall(r'\b(evp_[a-z_0-9]+)\s*\(', src)))
+
+
+@pytest.fixture(scope='module')
+def libpath():
+    from paper_1803_09563_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ('evp_init', 'evp_step', 'evp_project', 'evp_set_field', 'evp_get_field', 'evp_sync',
+                 'evp_destroy', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_last_error'):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(['nm', '-D', '--defined-only', libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r' T (evp_\w+)', out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_resolves_declared_names(libpath):
+    from paper_1803_09563_gb300 import evp
+    assert set(evp.exported_symbols()) == set(declared_functions())
+    lib = evp.load(libpath)
+    assert lib.evp_num_kernels() >= 9
+    assert lib.evp_kernel_name(0).decode() == 'stress_weno_update'
+
+
+def test_state_bytes_validates_without_a_gpu(libpath):
+    from paper_1803_09563_gb300 import evp
+    evp.load(libpath)
+    g = evp.make_grid(256, 128, 128, 4 * 3.141592653589793, 2.0, 2 * 3.141592653589793, True)
+    p = evp.make_params(Re=100, Wi=1, beta=0.5, Bi=0.5, precision=evp.EVP_FP32)
+    nb = evp.evp_state_bytes(g, evp.EVP_SARAMITO, p)
+    N = 256 * 128 * 128
+    assert 29 * N * 4 <= nb < 40 * N * 4
+    bad = evp.make_grid(250, 128, 128, 1.0, 1.0, 1.0, True)
+    assert evp.evp_state_bytes(bad, evp.EVP_SARAMITO, p) == 0

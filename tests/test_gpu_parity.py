@@ -1,0 +1,214 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, row by row:
+S1+S2 stress RHS, S4-S7 Poisson solve, S8 projection, whole RK3 substeps and steps.
+
+Relative error of a field = max|gpu - oracle| / max(max|oracle|, 1e-300).
+Tolerances: FP64 path 1e-10 (whole steps) / 1e-12 (single operators);
+FP32 path 1e-5 per step from the same FP64 state rounded to FP32.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_09563_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(got, ref):
+    return float(np.abs(np.asarray(got, dtype=np.float64) - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+# (nx, ny, nz, walls): several tiles of 32x8 plus ragged tails, both boundary types
+SHAPES = [(48, 24, 18, False), (36, 20, 16, True), (32, 32, 32, False), (64, 12, 24, True)]
+MODELS = [('oldroyd_b', {}), ('fene_p', {'L2': 60.0}), ('saramito', {'Bi': 0.4})]
+
+
+def setup_case(evp, shape, model, extra, precision, seed=3, re=2.0, dpdx=0.0):
+    nx, ny, nz, walls = shape
+    ly = 2.0 if walls else 2 * np.pi
+    geo = inputs.geometry(nx, ny, nz, 2 * np.pi, ly, 2 * np.pi, walls)
+    U, V, W = inputs.scale_max(*inputs.random_solenoidal(geo, seed, 3), 1.0)
+    if walls:
+        U = U + inputs.poiseuille(geo)[0]
+    B = inputs.random_conformation(geo, seed + 1, amp=0.3)
+    p = np.random.default_rng(seed + 2).standard_normal((nz, ny, nx)) * 0.1
+    g = oracle.Grid(nx, ny, nz, geo['lx'], geo['ly'], geo['lz'], walls)
+    prm_o = oracle.Params.from_groups(model, Re=re, Wi=0.8, beta=0.4, **extra)
+    sim = evp.Simulation(evp.make_grid(nx, ny, nz, geo['lx'], geo['ly'], geo['lz'], walls), model,
+                         evp.make_params(Re=re, Wi=0.8, beta=0.4, precision=precision, dpdx=dpdx, **extra))
+    sim.set_state(U, V, W, p, B)
+    st = oracle.State.rest(g, U, V, W)
+    st.p = p.copy()
+    st.B = [b.copy() for b in B]
+    if precision == evp.EVP_FP32:
+        # the oracle starts from exactly the FP32-rounded state the GPU holds
+        rd = lambda a: a.astype(np.float32).astype(np.float64)
+        st.U, st.V, st.W, st.p = rd(st.U), rd(st.V), rd(st.W), rd(st.p)
+        st.B = [rd(b) for b in st.B]
+    if walls:
+        st.V[:, -1] = 0.0
+    return sim, st, g, prm_o
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("model,extra", MODELS)
+def test_stress_rhs_fp64(evp, shape, model, extra):
+    import torch
+    sim, st, g, prm = setup_case(evp, shape, model, extra, evp.EVP_FP64)
+    out = torch.empty((6,) + sim.shape, dtype=torch.float64, device='cuda')
+    evp.evp_stress_rhs(sim.handle, out)
+    sim.sync()
+    ref = oracle.stress_rhs(st.U, st.V, st.W, st.B, g, prm)
+    for c in range(6):
+        assert rel(out[c].cpu().numpy(), ref[c]) < 1e-12, (c, rel(out[c].cpu().numpy(), ref[c]))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_stress_rhs_fp32(evp, shape):
+    import torch
+    sim, st, g, prm = setup_case(evp, shape, 'saramito', {'Bi': 0.4}, evp.EVP_FP32)
+    out = torch.empty((6,) + sim.shape, dtype=torch.float32, device='cuda')
+    evp.evp_stress_rhs(sim.handle, out)
+    sim.sync()
+    ref = oracle.stress_rhs(st.U, st.V, st.W, st.B, g, prm)
+    for c in range(6):
+        assert rel(out[c].cpu().numpy(), ref[c]) < 1e-5
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-6)])
+def test_poisson_solve(evp, shape, prec, tol):
+    import torch
+    nx, ny, nz, walls = shape
+    sim, st, g, prm = setup_case(evp, shape, 'oldroyd_b', {}, prec)
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal((nz, ny, nx))
+    r -= r.mean()
+    if prec == 1:
+        r = r.astype(np.float32).astype(np.float64)
+    dt = torch.float32 if prec else torch.float64
+    rd = torch.tensor(r, dtype=dt, device='cuda')
+    psi = torch.empty_like(rd)
+    evp.evp_poisson_solve(sim.handle, rd, psi)
+    sim.sync()
+    ref = oracle.solve_poisson(r, g)
+    got = psi.cpu().numpy().astype(np.float64)
+    if not walls:
+        got = got - got.mean()
+        ref = ref - ref.mean()
+    assert rel(got, ref) < tol
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_project_divergence_and_parity(evp, shape):
+    sim, st, g, prm = setup_case(evp, shape, 'oldroyd_b', {}, evp.EVP_FP64)
+    rng = np.random.default_rng(4)
+    U, V, W = (rng.standard_normal(sim.shape) for _ in range(3))
+    if shape[3]:
+        V[:, -1] = 0.0
+    sim.set_state(U, V, W)
+    sim.project()
+    code, bits, maxdiv = sim.sync()
+    U2, V2, W2, _ = oracle.project(U, V, W, g, 1.0)
+    for f, ref in ((evp.EVP_U, U2), (evp.EVP_V, V2), (evp.EVP_W, W2)):
+        assert rel(sim.get(f), ref) < 1e-12
+    assert maxdiv <= 1e-12 * max(1.0, np.abs(U).max() / g.dx)
+    d = oracle.divergence(sim.get(evp.EVP_U), sim.get(evp.EVP_V), sim.get(evp.EVP_W), g)
+    assert np.abs(d).max() <= 1e-12 * max(1.0, np.abs(U).max() / g.dx)
+
+
+def fields(sim, evp):
+    return ([sim.get(f) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P)]
+            + [sim.get(evp.EVP_BXX + c) for c in range(6)])
+
+
+def oracle_fields(st):
+    return [st.U, st.V, st.W, st.p] + list(st.B)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("model,extra", MODELS)
+def test_rk3_step_fp64(evp, shape, model, extra):
+    # channel shapes carry the uniform body force of the Poiseuille problem
+    dpdx = 0.05 if shape[3] else 0.0
+    force = (dpdx, 0.0, 0.0) if dpdx else None
+    sim, st, g, prm = setup_case(evp, shape, model, extra, evp.EVP_FP64, dpdx=dpdx)
+    dt = 2e-3
+    for _ in range(2):
+        sim.step(dt)
+        st = oracle.rk3_step(st, dt, g, prm, force)
+    code, bits, maxdiv = sim.sync()
+    for got, ref in zip(fields(sim, evp), oracle_fields(st)):
+        assert rel(got, ref) < 1e-10
+    assert maxdiv < 1e-11
+
+
+@pytest.mark.parametrize("shape", SHAPES[:2])
+@pytest.mark.parametrize("model,extra", MODELS)
+def test_rk3_step_fp32(evp, shape, model, extra):
+    """FP32 velocity and stress within 1e-5 of the FP64 oracle after one step.
+    The pressure is recovered from div(u*)/(2 alpha dt): FP32 rounding of u*
+    (relative eps32) leaves a spurious divergence ~ eps32 |u|/h, so psi carries an
+    absolute error ~ eps32 |u| h / (2 alpha dt); it is checked against 8x that bound."""
+    sim, st0, g, prm = setup_case(evp, shape, model, extra, evp.EVP_FP32)
+    dt = 2e-3
+    sim.step(dt)
+    st = oracle.rk3_step(st0, dt, g, prm)
+    sim.sync()
+    got = fields(sim, evp)
+    ref = oracle_fields(st)
+    for q, (a, b) in enumerate(zip(got, ref)):
+        if q == 3:
+            continue
+        assert rel(a, b) < 1e-5, (q, rel(a, b))
+    eps32 = float(np.finfo(np.float32).eps)
+    umax = max(np.abs(st0.U).max(), np.abs(st0.V).max(), np.abs(st0.W).max())
+    h = max(g.dx, g.dy, g.dz)
+    bound = 8.0 * sum(eps32 * umax * h / (2.0 * a * dt) for a in oracle.RK3_ALPHA)
+    assert np.abs(got[3] - ref[3]).max() < bound
+
+
+def test_c1_ten_steps_fp64(evp):
+    """Single-phase Oldroyd-B Taylor-Green box, 32^3, Re = 1, Wi = 1, beta = 0.5,
+    10 RK3 steps of dt = 1e-3: every field within 1e-10 of the oracle."""
+    n, L = 32, 2 * np.pi
+    geo = inputs.geometry(n, n, n, L, L, L)
+    U, V, W = inputs.taylor_green(geo)
+    sim = evp.Simulation(evp.make_grid(n, n, n, L, L, L), 'oldroyd_b',
+                         evp.make_params(Re=1.0, Wi=1.0, beta=0.5, precision=evp.EVP_FP64))
+    sim.set_state(U, V, W)
+    g = oracle.Grid(n, n, n, L, L, L)
+    st = oracle.State.rest(g, U, V, W)
+    prm = oracle.Params.from_groups('oldroyd_b', 1.0, 1.0, 0.5)
+    for _ in range(10):
+        sim.step(1e-3)
+        st = oracle.rk3_step(st, 1e-3, g, prm)
+    code, bits, maxdiv = sim.sync()
+    assert code == 0 and bits == 0
+    for got, ref in zip(fields(sim, evp), oracle_fields(st)):
+        assert rel(got, ref) < 1e-10
+    assert maxdiv <= 1e-12
+
+
+def test_nonfinite_input_raises_status(evp):
+    n = 16
+    sim = evp.Simulation(evp.make_grid(n, n, n, 1.0, 1.0, 1.0), 'oldroyd_b',
+                         evp.make_params(Re=1.0, Wi=1.0, beta=0.5))
+    U = np.zeros((n, n, n))
+    U[3, 4, 5] = np.nan
+    sim.set(evp.EVP_U, U)
+    sim.step(1e-3)
+    code, bits, _ = sim.sync(raise_on_error=False)
+    assert code == evp.EVP_ERR_NONFINITE and bits & evp.EVP_BIT_NONFINITE
+    # the state stays usable after the error is reported
+    sim.set(evp.EVP_U, np.zeros((n, n, n)))
+    code, bits, _ = sim.sync(raise_on_error=False)
+    assert code == 0
+
+
+def test_bad_arguments_rejected(evp):
+    with pytest.raises(evp.EvpError):
+        evp.Simulation(evp.make_grid(20, 16, 16, 1.0, 1.0, 1.0), 'oldroyd_b', evp.make_params(Re=1.0))
+    with pytest.raises(evp.EvpError):
+        evp.Simulation(evp.make_grid(16, 16, 16, 1.0, 1.0, 1.0), 'fene_p', evp.make_params(Re=1.0, L2=2.0))
