@@ -83,7 +83,8 @@ struct evp_state_s {
     void* lamy;
     void* lamz;
     void* trig;
-    double* thomas_m;
+    double2* thomas_m;
+    double* thomas_d;
     unsigned* d_status;
     unsigned long long* d_maxdiv;
     int cu, cb;          // current velocity / B buffer
@@ -216,14 +217,16 @@ size_t plan(evp_state* s, char* base) {
     void* lamy = P((size_t)g.ny * e);
     void* lamz = P((size_t)g.nz * e);
     void* trig = P((size_t)2 * (g.nx + g.ny + g.nz) * e);
-    void* thm = g.walls_y ? P((size_t)(g.nz / 2 + 1) * g.ny * nxh * sizeof(double)) : nullptr;
+    void* thm = g.walls_y ? P((size_t)(g.nz / 2 + 1) * g.ny * nxh * sizeof(double2)) : nullptr;
+    void* thd = g.walls_y ? P((size_t)2 * nxh * g.ny * g.nz * sizeof(double)) : nullptr;
     void* st = P(sizeof(unsigned));
     void* md = P(sizeof(unsigned long long));
     if (base) {
         s->P = p; s->PSI = psi; s->spec = spec;
         s->twx = twx; s->twy = twy; s->twz = twz;
         s->lamx = lamx; s->lamy = lamy; s->lamz = lamz; s->trig = trig;
-        s->thomas_m = static_cast<double*>(thm);
+        s->thomas_m = static_cast<double2*>(thm);
+        s->thomas_d = static_cast<double*>(thd);
         s->d_status = static_cast<unsigned*>(st);
         s->d_maxdiv = static_cast<unsigned long long*>(md);
     }
@@ -289,7 +292,7 @@ int upload_tables(evp_state* s) {
         const int ny = g.ny, nkz = g.nz / 2 + 1;
         const double idy2 = 1.0 / (dy * dy);
         std::vector<double> lzf = lam(g.nz, nkz, dz);
-        std::vector<double> M((size_t)nkz * ny * nxh);
+        std::vector<double> M((size_t)nkz * ny * nxh * 2);
         for (int kz = 0; kz < nkz; ++kz)
             for (int kx = 0; kx < nxh; ++kx) {
                 const double lm = lx[kx] + lzf[kz];
@@ -304,8 +307,9 @@ int upload_tables(evp_state* s) {
                         up = 0.0;
                     }
                     const double m = 1.0 / (d - lo * cprev);
-                    M[((size_t)kz * ny + j) * nxh + kx] = m;
                     cprev = up * m;
+                    M[2 * (((size_t)kz * ny + j) * nxh + kx)] = m;
+                    M[2 * (((size_t)kz * ny + j) * nxh + kx) + 1] = cprev;
                 }
             }
         CK(cudaMemcpyAsync(s->thomas_m, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
@@ -362,12 +366,15 @@ int run_poisson(evp_state* s, const T* Us, const T* Vs, const T* Ws, const T* rh
     a.spec = static_cast<typename Cplx<T>::type*>(s->spec);
     a.psi = psi;
     a.norm = poisson_norm<T>(s);
+    a.out_scale = s->g.walls_y ? T(a.norm) : T(1);
+    a.scratch = s->thomas_d;
     cudaError_t e = launch_poisson<T>(geo_of<T>(s), tables_of<T>(s), a, s->st, hook_of(s));
     return e == cudaSuccess ? EVP_OK : cuda_fail(e, "poisson");
 }
 
 template <typename T>
-int run_correct(evp_state* s, const T* Us, const T* Vs, const T* Ws, T* U, T* V, T* W, T* P, double coef) {
+int run_correct(evp_state* s, const T* Us, const T* Vs, const T* Ws, T* U, T* V, T* W, T* P, double coef,
+                bool residual) {
     CorrectArgs<T> a;
     a.Us = Us;
     a.Vs = Vs;
@@ -378,19 +385,21 @@ int run_correct(evp_state* s, const T* Us, const T* Vs, const T* Ws, T* U, T* V,
     a.W = W;
     a.P = P;
     a.coef = T(coef);
-    a.maxdiv = s->d_maxdiv;
+    a.maxdiv = residual ? s->d_maxdiv : nullptr;
     a.status = s->d_status;
     a.idx_d = s->g.nx / s->g.lx;
     a.idy_d = s->g.ny / s->g.ly;
     a.idz_d = s->g.nz / s->g.lz;
     // residual of this projection only
-    CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
+    if (residual) CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
     cudaError_t e = launch_correct<T>(geo_of<T>(s), a, s->st, hook_of(s));
     return e == cudaSuccess ? EVP_OK : cuda_fail(e, "correct");
 }
 
+// One RK3 substep.  in_step: part of evp_step (then the FP64 residual, which
+// evp_sync reports for the last projection, is evaluated on the third substep only).
 template <typename T>
-int substep_t(evp_state* s, double dt, int k, bool last_in_step) {
+int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
     const double al = RK_ALPHA[k], ze = RK_ZETA[k], xi = RK_XI[k];
     const bool stress = s->model != EVP_NEWTONIAN;
     const int cu = s->cu, cb = s->cb;
@@ -449,7 +458,7 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step) {
     if (r) return r;
     r = run_correct<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
                        static_cast<const T*>(s->W[1 - cu]), static_cast<T*>(s->U[cu]), static_cast<T*>(s->V[cu]),
-                       static_cast<T*>(s->W[cu]), static_cast<T*>(s->P), coef);
+                       static_cast<T*>(s->W[cu]), static_cast<T*>(s->P), coef, !in_step || k == 2);
     if (r) return r;
     if (stress) s->cb = 1 - cb;
     return EVP_OK;
@@ -633,14 +642,14 @@ int evp_substep(evp_state* s, double dt, int k) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
     if (k < 0 || k > 2) return fail(EVP_ERR_ARG, "substep index must be 0, 1 or 2");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
-    return s->fp32 ? substep_t<float>(s, dt, k, false) : substep_t<double>(s, dt, k, false);
+    return s->fp32 ? substep_t<float>(s, dt, k, false, false) : substep_t<double>(s, dt, k, false, false);
 }
 
 int evp_step(evp_state* s, double dt) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
     for (int k = 0; k < 3; ++k) {
-        int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2) : substep_t<double>(s, dt, k, k == 2);
+        int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2, true) : substep_t<double>(s, dt, k, k == 2, true);
         if (r) return r;
     }
     return EVP_OK;
@@ -655,13 +664,14 @@ int evp_project(evp_state* s) {
                                1.0, (float*)s->PSI);
         if (!r)
             r = run_correct<float>(s, (const float*)s->U[cu], (const float*)s->V[cu], (const float*)s->W[cu],
-                                   (float*)s->U[1 - cu], (float*)s->V[1 - cu], (float*)s->W[1 - cu], nullptr, 1.0);
+                                   (float*)s->U[1 - cu], (float*)s->V[1 - cu], (float*)s->W[1 - cu], nullptr, 1.0, true);
     } else {
         r = run_poisson<double>(s, (const double*)s->U[cu], (const double*)s->V[cu], (const double*)s->W[cu],
                                 nullptr, 1.0, (double*)s->PSI);
         if (!r)
             r = run_correct<double>(s, (const double*)s->U[cu], (const double*)s->V[cu], (const double*)s->W[cu],
-                                    (double*)s->U[1 - cu], (double*)s->V[1 - cu], (double*)s->W[1 - cu], nullptr, 1.0);
+                                    (double*)s->U[1 - cu], (double*)s->V[1 - cu], (double*)s->W[1 - cu], nullptr, 1.0,
+                                    true);
     }
     if (!r) s->cu = 1 - cu;
     return r;

@@ -134,7 +134,7 @@ struct FFTTables {
     const T* lamx;     // modal eigenvalues (2 - 2cos(2 pi m/n))/h^2, T precision
     const T* lamy;
     const T* lamz;
-    const double* thomas_m;   // walls: pivot reciprocals [nz/2+1][ny][nxh]
+    const double2* thomas_m;  // walls: (m_j, c'_j) per system, [nz/2+1][ny][nxh]
     double idy2;              // 1/dy^2 in FP64 (Thomas off-diagonals)
 };
 
@@ -149,6 +149,8 @@ struct PoissonArgs {
     typename Cplx<T>::type* spec;     // [nz][ny][nxh] complex
     T* psi;            // psi out
     double norm;       // 1/(nx nz) (walls) or 1/(nx ny nz) (periodic)
+    T out_scale;       // factor applied to psi by the inverse x pass (walls: norm)
+    double* scratch;   // walls: FP64 forward-sweep values, 2 (nx/2+1) ny nz doubles
 };
 
 template <typename T>

@@ -1,170 +1,321 @@
 // S3: momentum predictor of Eqs. NS-num1 and rk3 on the staggered grid.
 //
 // u* = u^{k-1} + dt [zeta^k N^{k-1} + xi^k N^{k-2} - 2 alpha^k grad p^{k-1}
-//                    + alpha^k (div tau^k + div tau^{k-1})]
+//                    + alpha^k div(tau^k + tau^{k-1})]
 // N  = -div(uu) + mu_s lap(u) + f
 //
 // div(uu) by second-order central differences (products at centres and edges),
 // the viscous term explicit with the advective weights, div(tau) at faces from
-// centre tau with 4-point edge averages for the off-diagonal parts.  One thread
-// computes the three faces (i+1/2, j, k), (i, j+1/2, k), (i, j, k+1/2) of cell
-// (i, j, k); with walls the top y-face stays zero.
+// centre tau with 4-point edge averages for the off-diagonal parts (div is linear,
+// so the two stress levels are summed first).  Each thread computes the three
+// faces (i+1/2, j, k), (i, j+1/2, k), (i, j, k+1/2) of its cell; with walls the
+// top y-face stays zero.
+//
+// A 32 x 8 tile walks a chunk of z planes.  Shared memory holds planes k-1..k+1
+// (1-cell x-y halo) of u, v, w (4-slot ring, refilled by cp.async), of the summed
+// stress S = tau^k + tau^{k-1} (3-slot ring, built from raw B planes staged by
+// cp.async) and of p, plus the cell's momentum history.
 #include "evp_internal.cuh"
 
 namespace evp {
 
 namespace {
 
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int VW = TX + 2, VH = TY + 2, VPL = VW * VH;   // plane with 1-cell halo
+constexpr int NV = (VPL + NT - 1) / NT;                  // plane cells per thread (2)
+
 template <typename T>
 __device__ __forceinline__ T sq(T x) { return x * x; }
 
-// tau component c (xx xy xz yy yz zz) at a centre, from B (Table 1 inverted)
+__device__ __forceinline__ int pmod(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename T>
+struct MomSmem {
+    T V[3][4][VPL];      // u, v, w: ring slots for planes k-1 .. k+2
+    T S[6][3][VPL];      // summed stress: ring slots for planes k-1 .. k+1
+    T Braw[12][VPL];     // raw B^{k-1} (0..5) and B^k (6..11) of the plane being staged
+    T P[3][VPL];         // pressure planes k, k+1 (+ staging)
+    T H[2][3][NT];       // momentum history of the tile's cells, planes k and k+1
+};
+
 template <typename T, int MODEL>
-__device__ __forceinline__ T tau_at(const Geo<T>& g, const ModelConst& mc, const T* const* B,
-                                    int c, int i, int j, int k) {
-    const T gm = T(mc.gmod);
-    const size_t o = lin(g, wrap(i, g.nx), ycen(g, j), wrap(k, g.nz));
-    const T bc = __ldg(B[c] + o);
-    const bool diag = (c == 0 || c == 3 || c == 5);
-    if (MODEL == EVP_FENE_P) {
-        const T tr = __ldg(B[0] + o) + __ldg(B[3] + o) + __ldg(B[5] + o);
-        const T F = T(mc.L2) / (T(mc.L2) - tr);
-        return gm * (F * bc - (diag ? T(mc.a_fene) : T(0)));
+__global__ void __launch_bounds__(NT, 1)
+k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_chunk) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    MomSmem<T>& sm = *reinterpret_cast<MomSmem<T>*>(smraw);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = i < g.nx && j < g.ny;
+    const size_t plane = (size_t)g.nx * g.ny;
+    const bool stress = MODEL != EVP_NEWTONIAN;
+
+    // per-thread plane cells: offsets for centred fields (copy ghosts) and for
+    // u, w (odd ghosts) / v (zero outside) with their ghost factors
+    size_t coff[NV], voff[3][NV];
+    signed char vfac[3][NV];
+    int psm[NV];
+#pragma unroll
+    for (int r = 0; r < NV; ++r) {
+        const int e = tid + r * NT;
+        psm[r] = e < VPL ? e : -1;
+        const int vy = e / VW, vx = e % VW;
+        const int gx = pmod(i0 + vx - 1, g.nx);
+        const int gy = j0 + vy - 1;
+        coff[r] = 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            voff[q][r] = 0;
+            vfac[q][r] = 0;
+        }
+        if (e >= VPL) continue;
+        if (!g.walls) {
+            const int y = pmod(gy, g.ny);
+            coff[r] = (size_t)y * g.nx + gx;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                voff[q][r] = coff[r];
+                vfac[q][r] = 1;
+            }
+        } else {
+            coff[r] = (size_t)min(max(gy, 0), g.ny - 1) * g.nx + gx;
+            const int my = gy < 0 ? -1 - gy : (gy >= g.ny ? 2 * g.ny - 1 - gy : gy);
+            const bool inside = gy >= 0 && gy < g.ny;
+            voff[0][r] = voff[2][r] = (size_t)min(max(my, 0), g.ny - 1) * g.nx + gx;
+            vfac[0][r] = vfac[2][r] = (my >= 0 && my < g.ny) ? (inside ? 1 : -1) : 0;
+            voff[1][r] = (size_t)(inside ? gy : 0) * g.nx + gx;
+            vfac[1][r] = inside ? 1 : 0;
+        }
     }
-    return gm * (bc - (diag ? T(1) : T(0)));
-}
+    const T* vel[3] = {a.U, a.V, a.W};
+    auto fetch_vel = [&](int kk) {
+        const size_t pv = (size_t)pmod(kk, g.nz) * plane;
+        const int slot = pmod(kk, 4);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int r = 0; r < NV; ++r) {
+                if (psm[r] < 0) continue;
+                T* dst = &sm.V[q][slot][psm[r]];
+                if (vfac[q][r] == 1)
+                    cp_async(dst, vel[q] + pv + voff[q][r]);
+                else
+                    *dst = vfac[q][r] == 0 ? T(0) : -__ldg(vel[q] + pv + voff[q][r]);
+            }
+    };
+    auto fetch_p = [&](int kk) {
+        const size_t pp = (size_t)pmod(kk, g.nz) * plane;
+#pragma unroll
+        for (int r = 0; r < NV; ++r)
+            if (psm[r] >= 0) cp_async(&sm.P[pmod(kk, 3)][psm[r]], a.P + pp + coff[r]);
+    };
+    auto fetch_braw = [&](int kk) {
+        if (!stress) return;
+        const size_t pb = (size_t)pmod(kk, g.nz) * plane;
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int r = 0; r < NV; ++r)
+                if (psm[r] >= 0) {
+                    cp_async(&sm.Braw[c][psm[r]], a.Bo[c] + pb + coff[r]);
+                    cp_async(&sm.Braw[6 + c][psm[r]], a.Bn[c] + pb + coff[r]);
+                }
+    };
+    // staged raw B -> summed stress S in ring slot kk mod 3 (Table 1 inverted)
+    auto build_s = [&](int kk) {
+        if (!stress) return;
+        const T gm = T(mc.gmod);
+        const int slot = pmod(kk, 3);
+#pragma unroll
+        for (int r = 0; r < NV; ++r) {
+            const int e = psm[r];
+            if (e < 0) continue;
+            if (MODEL == EVP_FENE_P) {
+                const T L2 = T(mc.L2), av = T(mc.a_fene);
+                const T Fo = L2 / (L2 - (sm.Braw[0][e] + sm.Braw[3][e] + sm.Braw[5][e]));
+                const T Fn = L2 / (L2 - (sm.Braw[6][e] + sm.Braw[9][e] + sm.Braw[11][e]));
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    const bool d = (c == 0 || c == 3 || c == 5);
+                    sm.S[c][slot][e] = gm * (Fn * sm.Braw[6 + c][e] - (d ? av : T(0)))
+                                       + gm * (Fo * sm.Braw[c][e] - (d ? av : T(0)));
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    const bool d = (c == 0 || c == 3 || c == 5);
+                    sm.S[c][slot][e] = gm * (sm.Braw[6 + c][e] - (d ? T(1) : T(0)))
+                                       + gm * (sm.Braw[c][e] - (d ? T(1) : T(0)));
+                }
+            }
+        }
+    };
+    const size_t cell0 = (size_t)min(j, g.ny - 1) * g.nx + min(i, g.nx - 1);
+    auto fetch_hist = [&](int kk) {
+        if (!a.read_hist || kk >= k1) return;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cp_async(&sm.H[kk & 1][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
+    };
 
-// 4-point average of tau_c over the centres (i + {0, di}, j + {0, dj}, k + {0, dk})
-// where exactly two of di, dj, dk are non-zero.
-template <typename T, int MODEL>
-__device__ __forceinline__ T tau_edge(const Geo<T>& g, const ModelConst& mc, const T* const* B, int c,
-                                      int i, int j, int k, int di, int dj, int dk) {
-    // the two offsets as (o1, o2); summed in the order (0,0), (0,o2), (o1,0), (o1,o2)
-    int a1i = 0, a1j = 0, a1k = 0, a2i = 0, a2j = 0, a2k = 0;
-    if (di) {
-        a1i = di;
-        if (dj) a2j = dj; else a2k = dk;
-    } else {
-        a1j = dj;
-        a2k = dk;
+    // ---- prologue: velocity k0-1 .. k0+1, p k0 .. k0+1, S k0-1 .. k0+1, history k0
+    fetch_vel(k0 - 1);
+    fetch_vel(k0);
+    fetch_vel(k0 + 1);
+    fetch_p(k0);
+    fetch_p(k0 + 1);
+    fetch_hist(k0);
+    for (int d = -1; d <= 1; ++d) {
+        fetch_braw(k0 + d);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        build_s(k0 + d);
+        __syncthreads();
     }
-    T s = tau_at<T, MODEL>(g, mc, B, c, i, j, k);
-    s += tau_at<T, MODEL>(g, mc, B, c, i + a2i, j + a2j, k + a2k);
-    s += tau_at<T, MODEL>(g, mc, B, c, i + a1i, j + a1j, k + a1k);
-    s += tau_at<T, MODEL>(g, mc, B, c, i + a1i + a2i, j + a1j + a2j, k + a1k + a2k);
-    return T(0.25) * s;
-}
 
-// div tau at the three faces of cell (i, j, k)
-template <typename T, int MODEL>
-__device__ __forceinline__ void div_tau(const Geo<T>& g, const ModelConst& mc, const T* const* B,
-                                        int i, int j, int k, T& fx, T& fy, T& fz) {
-    // x-face (i+1/2, j, k)
-    fx = (tau_at<T, MODEL>(g, mc, B, 0, i + 1, j, k) - tau_at<T, MODEL>(g, mc, B, 0, i, j, k)) * g.idx
-         + (tau_edge<T, MODEL>(g, mc, B, 1, i, j, k, 1, 1, 0) - tau_edge<T, MODEL>(g, mc, B, 1, i, j, k, 1, -1, 0)) * g.idy
-         + (tau_edge<T, MODEL>(g, mc, B, 2, i, j, k, 1, 0, 1) - tau_edge<T, MODEL>(g, mc, B, 2, i, j, k, 1, 0, -1)) * g.idz;
-    // y-face (i, j+1/2, k)
-    fy = (tau_edge<T, MODEL>(g, mc, B, 1, i, j, k, 1, 1, 0) - tau_edge<T, MODEL>(g, mc, B, 1, i, j, k, -1, 1, 0)) * g.idx
-         + (tau_at<T, MODEL>(g, mc, B, 3, i, j + 1, k) - tau_at<T, MODEL>(g, mc, B, 3, i, j, k)) * g.idy
-         + (tau_edge<T, MODEL>(g, mc, B, 4, i, j, k, 0, 1, 1) - tau_edge<T, MODEL>(g, mc, B, 4, i, j, k, 0, 1, -1)) * g.idz;
-    // z-face (i, j, k+1/2)
-    fz = (tau_edge<T, MODEL>(g, mc, B, 2, i, j, k, 1, 0, 1) - tau_edge<T, MODEL>(g, mc, B, 2, i, j, k, -1, 0, 1)) * g.idx
-         + (tau_edge<T, MODEL>(g, mc, B, 4, i, j, k, 0, 1, 1) - tau_edge<T, MODEL>(g, mc, B, 4, i, j, k, 0, -1, 1)) * g.idy
-         + (tau_at<T, MODEL>(g, mc, B, 5, i, j, k + 1) - tau_at<T, MODEL>(g, mc, B, 5, i, j, k)) * g.idz;
-}
-
-template <typename T, int MODEL>
-__global__ void __launch_bounds__(256)
-k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const size_t c0 = lin(g, i, j, k);
-    const T* U = a.U;
-    const T* V = a.V;
-    const T* W = a.W;
-    auto u = [&](int di, int dj, int dk) { return ld_uw(g, U, i + di, j + dj, k + dk); };
-    auto v = [&](int di, int dj, int dk) { return ld_v(g, V, i + di, j + dj, k + dk); };
-    auto w = [&](int di, int dj, int dk) { return ld_uw(g, W, i + di, j + dj, k + dk); };
     const T h = T(0.5);
-    const T u0 = u(0, 0, 0), v0 = v(0, 0, 0), w0 = w(0, 0, 0);
-
-    // ---- div(uu) at the three faces
-    const T Ax = (sq(h * (u0 + u(1, 0, 0))) - sq(h * (u(-1, 0, 0) + u0))) * g.idx
-                 + (h * (u0 + u(0, 1, 0)) * h * (v0 + v(1, 0, 0))
-                    - h * (u(0, -1, 0) + u0) * h * (v(0, -1, 0) + v(1, -1, 0))) * g.idy
-                 + (h * (u0 + u(0, 0, 1)) * h * (w0 + w(1, 0, 0))
-                    - h * (u(0, 0, -1) + u0) * h * (w(0, 0, -1) + w(1, 0, -1))) * g.idz;
-    const T Ay = (h * (u0 + u(0, 1, 0)) * h * (v0 + v(1, 0, 0))
-                  - h * (u(-1, 0, 0) + u(-1, 1, 0)) * h * (v(-1, 0, 0) + v0)) * g.idx
-                 + (sq(h * (v0 + v(0, 1, 0))) - sq(h * (v(0, -1, 0) + v0))) * g.idy
-                 + (h * (v0 + v(0, 0, 1)) * h * (w0 + w(0, 1, 0))
-                    - h * (v(0, 0, -1) + v0) * h * (w(0, 0, -1) + w(0, 1, -1))) * g.idz;
-    const T Az = (h * (u0 + u(0, 0, 1)) * h * (w0 + w(1, 0, 0))
-                  - h * (u(-1, 0, 0) + u(-1, 0, 1)) * h * (w(-1, 0, 0) + w0)) * g.idx
-                 + (h * (v0 + v(0, 0, 1)) * h * (w0 + w(0, 1, 0))
-                    - h * (v(0, -1, 0) + v(0, -1, 1)) * h * (w(0, -1, 0) + w0)) * g.idy
-                 + (sq(h * (w0 + w(0, 0, 1))) - sq(h * (w(0, 0, -1) + w0))) * g.idz;
-
-    // ---- mu_s lap(u)
     const T idx2 = g.idx * g.idx, idy2 = g.idy * g.idy, idz2 = g.idz * g.idz;
     const T mu = T(mc.mu_s);
-    const T Lu = (u(1, 0, 0) - T(2) * u0 + u(-1, 0, 0)) * idx2 + (u(0, 1, 0) - T(2) * u0 + u(0, -1, 0)) * idy2
-                 + (u(0, 0, 1) - T(2) * u0 + u(0, 0, -1)) * idz2;
-    const T Lv = (v(1, 0, 0) - T(2) * v0 + v(-1, 0, 0)) * idx2 + (v(0, 1, 0) - T(2) * v0 + v(0, -1, 0)) * idy2
-                 + (v(0, 0, 1) - T(2) * v0 + v(0, 0, -1)) * idz2;
-    const T Lw = (w(1, 0, 0) - T(2) * w0 + w(-1, 0, 0)) * idx2 + (w(0, 1, 0) - T(2) * w0 + w(0, -1, 0)) * idy2
-                 + (w(0, 0, 1) - T(2) * w0 + w(0, 0, -1)) * idz2;
-
-    // ---- body force: uniform dp/dx plus ABC forcing (separable tables)
-    T fx = a.dpdx, fy = T(0), fz = T(0);
-    if (a.trig) {
-        const T* sx = a.trig;
-        const T* cx = sx + g.nx;
-        const T* sy = cx + g.nx;
-        const T* cy = sy + g.ny;
-        const T* sz = cy + g.ny;
-        const T* cz = sz + g.nz;
-        fx += a.abc_amp * (sz[k] + cy[j]);
-        fy = a.abc_amp * (sx[i] + cz[k]);
-        fz = a.abc_amp * (sy[j] + cx[i]);
-    }
-    const T Nx = -Ax + mu * Lu + fx;
-    const T Ny = -Ay + mu * Lv + fy;
-    const T Nz = -Az + mu * Lw + fz;
-
-    // ---- pressure gradient at the faces
-    const T p0 = __ldg(a.P + c0);
-    const T gpx = (ld_c(g, a.P, i + 1, j, k) - p0) * g.idx;
-    const T gpy = (ld_c(g, a.P, i, j + 1, k) - p0) * g.idy;
-    const T gpz = (ld_c(g, a.P, i, j, k + 1) - p0) * g.idz;
-
-    T ix = a.zeta * Nx, iy = a.zeta * Ny, iz = a.zeta * Nz;
-    if (a.read_hist) {
-        ix += a.xi * a.NH[0][c0];
-        iy += a.xi * a.NH[1][c0];
-        iz += a.xi * a.NH[2][c0];
-    }
     const T two_a = T(2) * a.alpha;
-    ix -= two_a * gpx;
-    iy -= two_a * gpy;
-    iz -= two_a * gpz;
-    if (MODEL != EVP_NEWTONIAN) {
-        T ox, oy, oz, nx_, ny_, nz_;
-        div_tau<T, MODEL>(g, mc, a.Bn, i, j, k, nx_, ny_, nz_);
-        div_tau<T, MODEL>(g, mc, a.Bo, i, j, k, ox, oy, oz);
-        ix += a.alpha * (nx_ + ox);
-        iy += a.alpha * (ny_ + oy);
-        iz += a.alpha * (nz_ + oz);
-    }
-    a.Us[c0] = u0 + a.dt * ix;
-    a.Vs[c0] = (g.walls && j == g.ny - 1) ? T(0) : v0 + a.dt * iy;
-    a.Ws[c0] = w0 + a.dt * iz;
-    if (a.write_hist) {
-        a.NH[0][c0] = Nx;
-        a.NH[1][c0] = Ny;
-        a.NH[2][c0] = Nz;
+    const int o = (ty + 1) * VW + tx + 1;
+    const T* sx_ = a.trig;
+
+    for (int k = k0; k < k1; ++k) {
+        // ---- asynchronous prefetch of plane k+2 (velocity, raw B, p) and the history of k+1
+        fetch_vel(k + 2);
+        fetch_braw(k + 2);
+        fetch_p(k + 2);
+        fetch_hist(k + 1);
+        cp_async_commit();
+
+        const T* U0 = sm.V[0][pmod(k, 4)];
+        const T* Um1 = sm.V[0][pmod(k - 1, 4)];
+        const T* Up1 = sm.V[0][pmod(k + 1, 4)];
+        const T* V0 = sm.V[1][pmod(k, 4)];
+        const T* Vm1 = sm.V[1][pmod(k - 1, 4)];
+        const T* Vp1 = sm.V[1][pmod(k + 1, 4)];
+        const T* W0 = sm.V[2][pmod(k, 4)];
+        const T* Wm1 = sm.V[2][pmod(k - 1, 4)];
+        const T* Wp1 = sm.V[2][pmod(k + 1, 4)];
+        // value at (i+di, j+dj) of a plane
+        auto at = [&](const T* Pl, int di, int dj) { return Pl[o + dj * VW + di]; };
+        const T u0 = at(U0, 0, 0), v0 = at(V0, 0, 0), w0 = at(W0, 0, 0);
+
+        // ---- div(uu) at the three faces
+        const T Ax = (sq(h * (u0 + at(U0, 1, 0))) - sq(h * (at(U0, -1, 0) + u0))) * g.idx
+                     + (h * (u0 + at(U0, 0, 1)) * h * (v0 + at(V0, 1, 0))
+                        - h * (at(U0, 0, -1) + u0) * h * (at(V0, 0, -1) + at(V0, 1, -1))) * g.idy
+                     + (h * (u0 + at(Up1, 0, 0)) * h * (w0 + at(W0, 1, 0))
+                        - h * (at(Um1, 0, 0) + u0) * h * (at(Wm1, 0, 0) + at(Wm1, 1, 0))) * g.idz;
+        const T Ay = (h * (u0 + at(U0, 0, 1)) * h * (v0 + at(V0, 1, 0))
+                      - h * (at(U0, -1, 0) + at(U0, -1, 1)) * h * (at(V0, -1, 0) + v0)) * g.idx
+                     + (sq(h * (v0 + at(V0, 0, 1))) - sq(h * (at(V0, 0, -1) + v0))) * g.idy
+                     + (h * (v0 + at(Vp1, 0, 0)) * h * (w0 + at(W0, 0, 1))
+                        - h * (at(Vm1, 0, 0) + v0) * h * (at(Wm1, 0, 0) + at(Wm1, 0, 1))) * g.idz;
+        const T Az = (h * (u0 + at(Up1, 0, 0)) * h * (w0 + at(W0, 1, 0))
+                      - h * (at(U0, -1, 0) + at(Up1, -1, 0)) * h * (at(W0, -1, 0) + w0)) * g.idx
+                     + (h * (v0 + at(Vp1, 0, 0)) * h * (w0 + at(W0, 0, 1))
+                        - h * (at(V0, 0, -1) + at(Vp1, 0, -1)) * h * (at(W0, 0, -1) + w0)) * g.idy
+                     + (sq(h * (w0 + at(Wp1, 0, 0))) - sq(h * (at(Wm1, 0, 0) + w0))) * g.idz;
+
+        // ---- mu_s lap(u)
+        const T Lu = (at(U0, 1, 0) - T(2) * u0 + at(U0, -1, 0)) * idx2 + (at(U0, 0, 1) - T(2) * u0 + at(U0, 0, -1)) * idy2
+                     + (at(Up1, 0, 0) - T(2) * u0 + at(Um1, 0, 0)) * idz2;
+        const T Lv = (at(V0, 1, 0) - T(2) * v0 + at(V0, -1, 0)) * idx2 + (at(V0, 0, 1) - T(2) * v0 + at(V0, 0, -1)) * idy2
+                     + (at(Vp1, 0, 0) - T(2) * v0 + at(Vm1, 0, 0)) * idz2;
+        const T Lw = (at(W0, 1, 0) - T(2) * w0 + at(W0, -1, 0)) * idx2 + (at(W0, 0, 1) - T(2) * w0 + at(W0, 0, -1)) * idy2
+                     + (at(Wp1, 0, 0) - T(2) * w0 + at(Wm1, 0, 0)) * idz2;
+
+        // ---- body force: uniform dp/dx plus ABC forcing (separable tables)
+        T fx = a.dpdx, fy = T(0), fz = T(0);
+        if (sx_ && active) {
+            const T* cx = sx_ + g.nx;
+            const T* sy = cx + g.nx;
+            const T* cy = sy + g.ny;
+            const T* sz = cy + g.ny;
+            const T* cz = sz + g.nz;
+            fx += a.abc_amp * (__ldg(sz + k) + __ldg(cy + j));
+            fy = a.abc_amp * (__ldg(sx_ + i) + __ldg(cz + k));
+            fz = a.abc_amp * (__ldg(sy + j) + __ldg(cx + i));
+        }
+        const T Nx = -Ax + mu * Lu + fx;
+        const T Ny = -Ay + mu * Lv + fy;
+        const T Nz = -Az + mu * Lw + fz;
+
+        // ---- pressure gradient
+        const T* P0 = sm.P[pmod(k, 3)];
+        const T* P1 = sm.P[pmod(k + 1, 3)];
+        const T p0 = at(P0, 0, 0);
+        const T gpx = (at(P0, 1, 0) - p0) * g.idx;
+        const T gpy = (at(P0, 0, 1) - p0) * g.idy;
+        const T gpz = (at(P1, 0, 0) - p0) * g.idz;
+
+        T ix = a.zeta * Nx, iy = a.zeta * Ny, iz = a.zeta * Nz;
+        if (a.read_hist) {
+            ix += a.xi * sm.H[k & 1][0][tid];
+            iy += a.xi * sm.H[k & 1][1][tid];
+            iz += a.xi * sm.H[k & 1][2][tid];
+        }
+        ix -= two_a * gpx;
+        iy -= two_a * gpy;
+        iz -= two_a * gpz;
+        if (stress) {
+            const int s0 = pmod(k, 3), sm1 = pmod(k - 1, 3), sp1 = pmod(k + 1, 3);
+            auto S = [&](int c, int slot, int di, int dj) { return sm.S[c][slot][o + dj * VW + di]; };
+            // 4-point average over centres (0 or di) x (0 or dj) in one plane
+            auto e4 = [&](int c, int slot, int di, int dj) {
+                return T(0.25) * (S(c, slot, 0, 0) + S(c, slot, 0, dj) + S(c, slot, di, 0) + S(c, slot, di, dj));
+            };
+            // 4-point average over (0 or di) x planes (k, k+dk) at row j, or (0 or dj) x planes
+            auto e4z = [&](int c, int di, int dj, int slot2) {
+                return T(0.25) * (S(c, s0, 0, 0) + S(c, slot2, 0, 0) + S(c, s0, di, dj) + S(c, slot2, di, dj));
+            };
+            const T fxs = (S(0, s0, 1, 0) - S(0, s0, 0, 0)) * g.idx
+                          + (e4(1, s0, 1, 1) - e4(1, s0, 1, -1)) * g.idy
+                          + (e4z(2, 1, 0, sp1) - e4z(2, 1, 0, sm1)) * g.idz;
+            const T fys = (e4(1, s0, 1, 1) - e4(1, s0, -1, 1)) * g.idx
+                          + (S(3, s0, 0, 1) - S(3, s0, 0, 0)) * g.idy
+                          + (e4z(4, 0, 1, sp1) - e4z(4, 0, 1, sm1)) * g.idz;
+            const T fzs = (e4z(2, 1, 0, sp1) - e4z(2, -1, 0, sp1)) * g.idx
+                          + (e4z(4, 0, 1, sp1) - e4z(4, 0, -1, sp1)) * g.idy
+                          + (S(5, sp1, 0, 0) - S(5, s0, 0, 0)) * g.idz;
+            ix += a.alpha * fxs;
+            iy += a.alpha * fys;
+            iz += a.alpha * fzs;
+        }
+        if (active) {
+            const size_t c0 = (size_t)k * plane + (size_t)j * g.nx + i;
+            a.Us[c0] = u0 + a.dt * ix;
+            a.Vs[c0] = (g.walls && j == g.ny - 1) ? T(0) : v0 + a.dt * iy;
+            a.Ws[c0] = w0 + a.dt * iz;
+            if (a.write_hist) {
+                a.NH[0][c0] = Nx;
+                a.NH[1][c0] = Ny;
+                a.NH[2][c0] = Nz;
+            }
+        }
+
+        // ---- advance: the staged raw B becomes S plane k+2 (slot of plane k-1)
+        cp_async_wait_all();
+        __syncthreads();
+        build_s(k + 2);
+        __syncthreads();
     }
 }
 
@@ -173,14 +324,27 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a) {
 template <typename T>
 cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const MomentumArgs<T>& a,
                             cudaStream_t st, const TimingHook& th) {
-    dim3 block(32, 8, 1);
-    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    const int per_sm = sizeof(T) == 4 ? 2 : 1;
+    int chunks = (4 * 152 * per_sm + tiles - 1) / tiles;
+    int kz = (g.nz + chunks - 1) / chunks;
+    kz = kz < 8 ? 8 : kz;
+    chunks = (g.nz + kz - 1) / kz;
+    dim3 block(TX, TY, 1);
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
+    const size_t smem = sizeof(MomSmem<T>);
     th.b(K_MOMENTUM);
     switch (mc.model) {
-        case EVP_NEWTONIAN: k_momentum<T, EVP_NEWTONIAN><<<grid, block, 0, st>>>(g, mc, a); break;
-        case EVP_OLDROYD_B: k_momentum<T, EVP_OLDROYD_B><<<grid, block, 0, st>>>(g, mc, a); break;
-        case EVP_FENE_P: k_momentum<T, EVP_FENE_P><<<grid, block, 0, st>>>(g, mc, a); break;
-        case EVP_SARAMITO: k_momentum<T, EVP_SARAMITO><<<grid, block, 0, st>>>(g, mc, a); break;
+#define EVP_LAUNCH_MOM(M)                                                                                  \
+    case M:                                                                                                \
+        cudaFuncSetAttribute(k_momentum<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        k_momentum<T, M><<<grid, block, smem, st>>>(g, mc, a, kz);                                        \
+        break;
+        EVP_LAUNCH_MOM(EVP_NEWTONIAN)
+        EVP_LAUNCH_MOM(EVP_OLDROYD_B)
+        EVP_LAUNCH_MOM(EVP_FENE_P)
+        EVP_LAUNCH_MOM(EVP_SARAMITO)
+#undef EVP_LAUNCH_MOM
         default: return cudaErrorInvalidValue;
     }
     th.e(K_MOMENTUM);

@@ -199,8 +199,8 @@ k_ifftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
         const int L0 = 2 * (q0 + l), L1 = L0 + 1;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const C<T> z = res[(size_t)l * nx + i];
-            if (L0 < NL) a.psi[(size_t)L0 * nx + i] = z.x;
-            if (L1 < NL) a.psi[(size_t)L1 * nx + i] = z.y;
+            if (L0 < NL) a.psi[(size_t)L0 * nx + i] = z.x * a.out_scale;
+            if (L1 < NL) a.psi[(size_t)L1 * nx + i] = z.y * a.out_scale;
         }
     }
 }
@@ -256,90 +256,164 @@ k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axi
 // S6 with walls: for each (kx, kz) solve
 //   psi_{j-1}/dy^2 - (2/dy^2 + lx + lz) psi_j + psi_{j+1}/dy^2 = r_j
 // with Neumann rows at j = 0 and ny-1 and the (0, 0) system pinned by psi_0 = 0,
-// in FP64.  m_j = 1/(b_j - a_j c'_{j-1}) comes from a host-built FP64 table;
-// the forward sweep keeps d'_j in shared memory for the back substitution.
+// in FP64.  Real and imaginary parts are independent recurrences with the same
+// real coefficients: one thread per (system, part).  m_j = 1/(b_j - a_j c'_{j-1})
+// and c'_j come from a host-built FP64 table; the forward-sweep values d'_j go to
+// an FP64 scratch in global memory (L2-resident) for the back substitution.  The
+// FFT normalisation is applied later, in the inverse x pass.
 template <typename T>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(128)
 k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, double idy2) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    double2* dp = reinterpret_cast<double2*>(smraw);   // [ny][blockDim.x]
     const int nxh = g.nx / 2 + 1, ny = g.ny, nz = g.nz;
-    const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // 2*kx + part
+    const int kx = t >> 1, part = t & 1;
     const int kz = blockIdx.y;
     if (kx >= nxh) return;
     const int kzh = kz <= nz - kz ? kz : nz - kz;
     const bool pinned = (kx == 0 && kz == 0);
-    const double* M = tb.thomas_m + (size_t)kzh * ny * nxh + kx;
-    C<T>* col = a.spec + (size_t)kz * ny * nxh + kx;
-    const int tb_ = blockDim.x, t = threadIdx.x;
-    const double nrm = a.norm;
-    double px = 0.0, py = 0.0;
-    for (int j = 0; j < ny; ++j) {
-        const C<T> r = col[(size_t)j * nxh];
-        double rx = double(r.x) * nrm, ry = double(r.y) * nrm;
-        if (pinned && j == 0) rx = ry = 0.0;
-        const double lo = j > 0 ? idy2 : 0.0;
-        const double m = __ldg(M + (size_t)j * nxh);
-        px = (rx - lo * px) * m;
-        py = (ry - lo * py) * m;
-        dp[(size_t)j * tb_ + t] = make_double2(px, py);
+    const double2* M = tb.thomas_m + (size_t)kzh * ny * nxh + kx;         // (m_j, c'_j)
+    T* col = reinterpret_cast<T*>(a.spec + (size_t)kz * ny * nxh) + t;    // this part of (kx, kz)
+    double* D = a.scratch + (size_t)kz * ny * (2 * nxh) + t;
+    const size_t rs = 2 * (size_t)nxh;                                    // row stride in T / double
+    // rows are processed in batches of RB with their loads issued up front, so the
+    // FP64 recurrence does not wait on one memory round trip per row
+    constexpr int RB = 8;
+    double d = 0.0;
+    for (int jb = 0; jb < ny; jb += RB) {
+        double rr[RB], mm[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int jj = jb + u;
+            rr[u] = jj < ny ? double(col[jj * rs]) : 0.0;
+            mm[u] = jj < ny ? __ldg(&M[(size_t)jj * nxh].x) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int jj = jb + u;
+            if (jj >= ny) break;
+            const double r = (pinned && jj == 0) ? 0.0 : rr[u];
+            const double lo = jj > 0 ? idy2 : 0.0;
+            d = (r - lo * d) * mm[u];
+            D[jj * rs] = d;
+        }
     }
-    double xx = px, xy = py;
-    col[(size_t)(ny - 1) * nxh] = mk<T>(T(xx), T(xy));
-    for (int j = ny - 2; j >= 0; --j) {
-        const double up = (pinned && j == 0) ? 0.0 : idy2;
-        const double cpj = up * __ldg(M + (size_t)j * nxh);
-        const double2 d = dp[(size_t)j * tb_ + t];
-        xx = d.x - cpj * xx;
-        xy = d.y - cpj * xy;
-        col[(size_t)j * nxh] = mk<T>(T(xx), T(xy));
+    double x = d;
+    col[(ny - 1) * rs] = T(x);
+    for (int jt = ny - 2; jt >= 0; jt -= RB) {
+        double dd[RB], cc[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int jj = jt - u;
+            dd[u] = jj >= 0 ? D[jj * rs] : 0.0;
+            cc[u] = jj >= 0 ? __ldg(&M[(size_t)jj * nxh].y) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int jj = jt - u;
+            if (jj < 0) break;
+            x = dd[u] - cc[u] * x;
+            col[jj * rs] = T(x);
+        }
     }
 }
 
-// S8: u^k = u* - c grad psi at the faces, p += psi, FP64 max |div u^k|
-template <typename T>
+// S8: u^k = u* - c grad psi at the faces, p += psi, FP64 max |div u^k|.
+// A 32 x 8 tile walks a chunk of z planes; psi and w* of the column below are
+// carried from the previous plane.  One FP64 atomic max per block.
+template <typename T, bool RESID>
 __global__ void __launch_bounds__(256)
-k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, double idz_d) {
+k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, double idz_d, int kz_chunk) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+    const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
+    const bool active = i < g.nx && j < g.ny;
     double dmax = 0.0;
     unsigned bits = 0;
-    if (i < g.nx && j < g.ny) {
-        const size_t c0 = lin(g, i, j, k);
+    if (active) {
         const T c = a.coef;
-        const T pc = __ldg(a.psi + c0);
-        const T px = ld_c(g, a.psi, i + 1, j, k), py = ld_c(g, a.psi, i, j + 1, k), pz = ld_c(g, a.psi, i, j, k + 1);
-        const T Un = __ldg(a.Us + c0) - c * ((px - pc) * g.idx);
-        const bool top = g.walls && j == g.ny - 1;
-        const T Vn = top ? T(0) : __ldg(a.Vs + c0) - c * ((py - pc) * g.idy);
-        const T Wn = __ldg(a.Ws + c0) - c * ((pz - pc) * g.idz);
-        a.U[c0] = Un;
-        a.V[c0] = Vn;
-        a.W[c0] = Wn;
-        if (a.P) a.P[c0] += pc;
-        // the faces below the cell, recomputed the way their owners write them
-        const T pxm = ld_c(g, a.psi, i - 1, j, k), pym = ld_c(g, a.psi, i, j - 1, k), pzm = ld_c(g, a.psi, i, j, k - 1);
-        const T Ul = ld_uw(g, a.Us, i - 1, j, k) - c * ((pc - pxm) * g.idx);
-        const T Vl = (g.walls && j == 0) ? T(0) : ld_v(g, a.Vs, i, j - 1, k) - c * ((pc - pym) * g.idy);
-        const T Wl = ld_uw(g, a.Ws, i, j, k - 1) - c * ((pc - pzm) * g.idz);
-        const double dv = (double(Un) - double(Ul)) * idx_d + (double(Vn) - double(Vl)) * idy_d
-                          + (double(Wn) - double(Wl)) * idz_d;
-        dmax = fabs(dv);
-        if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn)) bits |= EVP_BIT_NONFINITE;
-        if (!(dmax <= DBL_MAX)) {
-            dmax = 0.0;
-            bits |= EVP_BIT_NONFINITE;
+        const T* __restrict__ Psi = a.psi;
+        const T* __restrict__ Us = a.Us;
+        const T* __restrict__ Vs = a.Vs;
+        const T* __restrict__ Ws = a.Ws;
+        T* __restrict__ U = a.U;
+        T* __restrict__ V = a.V;
+        T* __restrict__ W = a.W;
+        T* __restrict__ P = a.P;
+        const size_t plane = (size_t)g.nx * g.ny;
+        const size_t cj = (size_t)j * g.nx + i;
+        const int ip = wrap(i + 1, g.nx), im = wrap(i - 1, g.nx);
+        const int jp = ycen(g, j + 1), jm = ycen(g, j - 1);
+        const bool top = g.walls && j == g.ny - 1, bottom = g.walls && j == 0;
+        const size_t cxp = (size_t)j * g.nx + ip, cxm = (size_t)j * g.nx + im;
+        const size_t cyp = (size_t)jp * g.nx + i, cym = (size_t)jm * g.nx + i;
+        // column values of plane k-1 carried along z
+        const int km = wrap(k0 - 1, g.nz);
+        T psi_m = __ldg(Psi + km * plane + cj);
+        T pc = __ldg(Psi + (size_t)k0 * plane + cj);
+        T ws_m = __ldg(Ws + km * plane + cj);
+        for (int k = k0; k < k1; ++k) {
+            const size_t o = (size_t)k * plane;
+            const T pz = __ldg(Psi + (size_t)wrap(k + 1, g.nz) * plane + cj);
+            const T px = __ldg(Psi + o + cxp), pxm = __ldg(Psi + o + cxm);
+            const T py = __ldg(Psi + o + cyp), pym = __ldg(Psi + o + cym);
+            const T us = __ldg(Us + o + cj), usm = __ldg(Us + o + cxm);
+            const T vs = __ldg(Vs + o + cj), vsm = bottom ? T(0) : __ldg(Vs + o + cym);
+            const T ws = __ldg(Ws + o + cj);
+            const T pold = P ? P[o + cj] : T(0);
+            const T Un = us - c * ((px - pc) * g.idx);
+            const T Vn = top ? T(0) : vs - c * ((py - pc) * g.idy);
+            const T Wn = ws - c * ((pz - pc) * g.idz);
+            U[o + cj] = Un;
+            V[o + cj] = Vn;
+            W[o + cj] = Wn;
+            if (P) P[o + cj] = pold + pc;
+            if (!RESID) {
+                if (!isfinite(Un + Vn + Wn)) bits |= EVP_BIT_NONFINITE;
+                psi_m = pc;
+                pc = pz;
+                ws_m = ws;
+                continue;
+            }
+            // the faces below the cell, recomputed the way their owners write them
+            const T Ul = usm - c * ((pc - pxm) * g.idx);
+            const T Vl = bottom ? T(0) : vsm - c * ((pc - pym) * g.idy);
+            const T Wl = ws_m - c * ((pc - psi_m) * g.idz);
+            const double dv = (double(Un) - double(Ul)) * idx_d + (double(Vn) - double(Vl)) * idy_d
+                              + (double(Wn) - double(Wl)) * idz_d;
+            const double ad = fabs(dv);
+            if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn) || !(ad <= DBL_MAX)) bits |= EVP_BIT_NONFINITE;
+            else dmax = fmax(dmax, ad);
+            psi_m = pc;
+            pc = pz;
+            ws_m = ws;
         }
     }
+    __shared__ double red[8];
+    __shared__ unsigned rbits[8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
         bits |= __shfl_xor_sync(0xffffffffu, bits, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (dmax > 0.0) atomicMax(a.maxdiv, (unsigned long long)__double_as_longlong(dmax));
-        if (bits) atomicOr(a.status, bits);
+    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[warp] = dmax;
+        rbits[warp] = bits;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x * blockDim.y) >> 5;
+        dmax = lane < nw ? red[lane] : 0.0;
+        bits = lane < nw ? rbits[lane] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+        }
+        if (lane == 0) {
+            if (RESID && dmax > 0.0) atomicMax(a.maxdiv, (unsigned long long)__double_as_longlong(dmax));
+            if (bits) atomicOr(a.status, bits);
+        }
     }
 }
 
@@ -397,12 +471,10 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
         k_fft_col<T, false, true><<<gc, bc, sm, st>>>(g, tb, a, 1, (size_t)nxh, (size_t)ny * nxh, tk);
         th.e(K_SOLVE_Y);
     } else {
-        const int tt = ny <= 256 ? 32 : 16;
-        dim3 gt((nxh + tt - 1) / tt, nz);
-        const size_t sm = (size_t)ny * tt * sizeof(double2);
-        set_smem<T>((const void*)k_thomas<T>, sm);
+        const int tt = 128;
+        dim3 gt((2 * nxh + tt - 1) / tt, nz);
         th.b(K_THOMAS);
-        k_thomas<T><<<gt, tt, sm, st>>>(g, tb, a, tb.idy2);
+        k_thomas<T><<<gt, tt, 0, st>>>(g, tb, a, tb.idy2);
         th.e(K_THOMAS);
     }
     // ---- inverse z
@@ -424,9 +496,16 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
 template <typename T>
 cudaError_t launch_correct(const Geo<T>& g, const CorrectArgs<T>& a, cudaStream_t st, const TimingHook& th) {
     dim3 block(32, 8, 1);
-    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    const int tiles = ((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+    int chunks = (8 * 152 + tiles - 1) / tiles;
+    int kz = (g.nz + chunks - 1) / chunks;
+    chunks = (g.nz + kz - 1) / kz;
+    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, chunks);
     th.b(K_CORRECT);
-    k_correct<T><<<grid, block, 0, st>>>(g, a, a.idx_d, a.idy_d, a.idz_d);
+    if (a.maxdiv)
+        k_correct<T, true><<<grid, block, 0, st>>>(g, a, a.idx_d, a.idy_d, a.idz_d, kz);
+    else
+        k_correct<T, false><<<grid, block, 0, st>>>(g, a, a.idx_d, a.idy_d, a.idz_d, kz);
     th.e(K_CORRECT);
     return cudaGetLastError();
 }

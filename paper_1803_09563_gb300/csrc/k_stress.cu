@@ -4,7 +4,7 @@
 // RT = (a I - F B)/lambda - (u.grad B - B.grad u - grad u^T.B)     (Eq. rt / RK-rt)
 // B^k = B^{k-1} + dt (zeta^k RT^{k-1} + xi^k RT^{k-2})            (Eq. rk3tau)
 //
-// One thread per cell; neighbours are read through the read-only cache.
+// z-marching tiles: see the kernel for the data staging.
 #include <cfloat>
 
 #include "evp_internal.cuh"
@@ -14,38 +14,43 @@ namespace evp {
 namespace {
 
 // Fifth-order WENO combination (Sec. 3.1) of five undivided differences ordered
-// from far upwind to downwind: Jiang-Shu smoothness indicators, linear weights
-// (1/10, 6/10, 3/10), eps = 1e-6, power 2.  The normalised weights
-// alpha_k / sum(alpha) are formed by multiplying every alpha_k = d_k/e_k through
-// by e_1 e_2 e_3, which leaves one division per reconstruction.
+// from far upwind to downwind, times ``scale``: Jiang-Shu smoothness indicators,
+// linear weights (1/10, 6/10, 3/10), eps = 1e-6, power 2.  Algebraically
+// rearranged for fewer operations, with the same value:
+//  * the indicators use the second differences a_k and b_k of the differences;
+//    eps and all three indicators are scaled by 12/13 (a common factor of
+//    eps + S_k cancels in the normalised weights);
+//  * the weights alpha_k = d_k/e_k^2 are multiplied through by 10 e_1^2 e_2^2 e_3^2,
+//    which leaves one division.
 template <typename T>
-__device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5) {
-    const T c13 = T(13.0 / 12.0), q = T(0.25), eps = T(1.0e-6);
-    T q1 = v1 * T(1.0 / 3.0) - v2 * T(7.0 / 6.0) + v3 * T(11.0 / 6.0);
-    T q2 = -v2 * T(1.0 / 6.0) + v3 * T(5.0 / 6.0) + v4 * T(1.0 / 3.0);
-    T q3 = v3 * T(1.0 / 3.0) + v4 * T(5.0 / 6.0) - v5 * T(1.0 / 6.0);
-    T a = v1 - T(2) * v2 + v3, b = v1 - T(4) * v2 + T(3) * v3;
-    T s1 = c13 * a * a + q * b * b;
-    a = v2 - T(2) * v3 + v4;
-    b = v2 - v4;
-    T s2 = c13 * a * a + q * b * b;
-    a = v3 - T(2) * v4 + v5;
-    b = T(3) * v3 - T(4) * v4 + v5;
-    T s3 = c13 * a * a + q * b * b;
-    T e1 = eps + s1, e2 = eps + s2, e3 = eps + s3;
-    e1 *= e1;
-    e2 *= e2;
-    e3 *= e3;
-    T w1 = T(0.1) * e2 * e3, w2 = T(0.6) * e1 * e3, w3 = T(0.3) * e1 * e2;
-    T den = w1 + w2 + w3;
-    if (sizeof(T) == 4 && !(den <= T(FLT_MAX))) {
-        // products overflowed single precision: fall back to the three-division form
-        w1 = T(0.1) / e1;
-        w2 = T(0.6) / e2;
-        w3 = T(0.3) / e3;
-        den = w1 + w2 + w3;
+__device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5, T scale) {
+    const T eps = T(1.0e-6 * 12.0 / 13.0), r = T(3.0 / 13.0);
+    // candidates: q1, 6 q2, 3 q3
+    const T q1 = v1 * T(1.0 / 3.0) - v2 * T(7.0 / 6.0) + v3 * T(11.0 / 6.0);
+    const T q2 = -v2 + T(5) * v3 + T(2) * v4;
+    const T q3 = v3 + T(2.5) * v4 - T(0.5) * v5;
+    const T e12 = v1 - v2, e23 = v2 - v3, e34 = v3 - v4, e45 = v4 - v5;
+    const T a1 = e12 - e23, a2 = e23 - e34, a3 = e34 - e45;
+    const T b1 = a1 - T(2) * e23, b2 = e23 + e34, b3 = a3 + T(2) * e34;
+    // (12/13)(eps + S_k) = a_k^2 + (3/13) b_k^2 + (12/13) eps
+    T s1 = fma(b1 * r, b1, fma(a1, a1, eps));
+    T s2 = fma(b2 * r, b2, fma(a2, a2, eps));
+    T s3 = fma(b3 * r, b3, fma(a3, a3, eps));
+    s1 *= s1;
+    s2 *= s2;
+    s3 *= s3;
+    const T w1 = s2 * s3, w2 = s1 * s3, w3 = s1 * s2;
+    T den = fma(T(3), w3, fma(T(6), w2, w1));
+    T num = fma(w3, q3, fma(w2, q2, w1 * q1)) * scale;
+    if (sizeof(T) == 4) {
+        // single precision: CUDA's fast division holds to 2 ulp while the divisor
+        // stays below 2^126; beyond that (products near overflow) use the
+        // three-division form
+        if (den <= T(8.5e37)) return __fdividef(float(num), float(den));
+        const T x1 = T(1) / s1, x2 = T(1) / s2, x3 = T(1) / s3;
+        return (x1 * q1 + x2 * q2 + x3 * q3) * scale / (x1 + T(6) * x2 + T(3) * x3);
     }
-    return (w1 * q1 + w2 * q2 + w3 * q3) / den;
+    return num / den;
 }
 
 // storage index of the symmetric component (a, b): xx xy xz yy yz zz
@@ -57,135 +62,310 @@ __device__ __forceinline__ constexpr int col_of(int c) { return c == 0 ? 0 : ((c
 
 // |u| * (upwind WENO5 derivative) of a centred field along one axis, from the
 // six values phi(c + m*sig*step), m = -3..2, where sig = +1 for a positive
-// velocity (left-biased stencil) and -1 otherwise (right-biased, mirrored).
+// velocity (left-biased stencil) and -1 otherwise (right-biased, mirrored; the
+// differences then change sign exactly, and so does the WENO combination).
+// ``vih`` = |u| / h.
 template <typename T>
-__device__ __forceinline__ T upwind_term(T vel, T ih, T pm3, T pm2, T pm1, T p0, T pp1, T pp2) {
-    return fabs(vel) * ih * weno5(pm2 - pm3, pm1 - pm2, p0 - pm1, pp1 - p0, pp2 - pp1);
+__device__ __forceinline__ T upwind_term(T vih, T pm3, T pm2, T pm1, T p0, T pp1, T pp2) {
+    return weno5(pm2 - pm3, pm1 - pm2, p0 - pm1, pp1 - p0, pp2 - pp1, vih);
 }
 
+// Tile geometry of the z-marching kernel: a 32 x 8 tile of cells in x-y walks
+// through a chunk of z planes.  B of the tile's own column lives in a 7-plane
+// register window (z stencils); the current plane of B with a 3-cell x-y halo
+// and three planes of u, v, w with a 1-cell halo live in shared memory.
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int BW = TX + 6, BH = TY + 6, BPL = BW * BH;    // B plane with halo 3
+constexpr int VW = TX + 2, VH = TY + 2, VPL = VW * VH;    // velocity plane with halo 1
+constexpr int BHALO = BPL - NT;                           // 276 halo cells per B plane
+constexpr int NBH = (BHALO + NT - 1) / NT;                // halo cells per thread (2)
+constexpr int NVH = (VPL + NT - 1) / NT;                  // velocity cells per thread (2)
+
+__device__ __forceinline__ int pmod(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// (row, col) inside the 38 x 14 B plane of halo cell h (0 <= h < 276)
+__device__ __forceinline__ void bhalo_pos(int h, int& hy, int& hx) {
+    if (h < 3 * BW) {
+        hy = h / BW;
+        hx = h % BW;
+    } else if (h < 6 * BW) {
+        const int q = h - 3 * BW;
+        hy = TY + 3 + q / BW;
+        hx = q % BW;
+    } else {
+        const int q = h - 6 * BW;
+        hy = 3 + q / 6;
+        const int c = q % 6;
+        hx = c < 3 ? c : TX + c;
+    }
+}
+
+template <typename T>
+struct StressSmem {
+    T B[2][6][BPL];     // plane k (being used) and plane k+1 (arriving) of B, 3-cell halo
+    T V[3][4][VPL];     // [u, v, w][ring slot: planes k-1 .. k+2][plane with 1-cell halo]
+    T N[6][NT];         // plane k+4 of B for the tile's own columns (arriving)
+    T H[2][6][NT];      // RK3 history RT^{k-2} of planes k and k+1 for the tile's cells
+};
+
+// asynchronous global -> shared copy of one element (cp.async, L1-allocating)
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T, int MODEL>
-__global__ void __launch_bounds__(256)
-k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const size_t c0 = lin(g, i, j, k);
-    const int im = wrap(i - 1, g.nx), km = wrap(k - 1, g.nz);
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chunk) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    StressSmem<T>& sm = *reinterpret_cast<StressSmem<T>*>(smraw);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int k0 = blockIdx.z * kz_chunk;
+    const int k1 = min(k0 + kz_chunk, g.nz);
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = (i < g.nx) && (j < g.ny);
+    const size_t plane = (size_t)g.nx * g.ny;
+    // the column this thread loads (wrapped / clamped so that ragged threads hold
+    // the periodic or ghost image their neighbours' stencils need)
+    const int jc = g.walls ? min(j, g.ny - 1) : pmod(j, g.ny);
+    const size_t col = (size_t)jc * g.nx + pmod(i, g.nx);
 
-    // ---- S1: centre velocity and velocity gradient (Reading 5)
-    const T Uc = __ldg(a.U + c0), Um = ld_uw(g, a.U, im, j, k);
-    const T Vc = __ldg(a.V + c0), Vm = ld_v(g, a.V, i, j - 1, k);
-    const T Wc = __ldg(a.W + c0), Wm = ld_uw(g, a.W, i, j, km);
-    const T uc = T(0.5) * (Um + Uc), vc = T(0.5) * (Vm + Vc), wc = T(0.5) * (Wm + Wc);
-    T L[3][3];
-    L[0][0] = (Uc - Um) * g.idx;
-    L[1][1] = (Vc - Vm) * g.idy;
-    L[2][2] = (Wc - Wm) * g.idz;
-    {
-        // u centred: average of faces i-1 and i, odd ghosts in y at walls
-        auto ucen = [&](int jj, int kk) {
-            return T(0.5) * (ld_uw(g, a.U, i - 1, jj, kk) + ld_uw(g, a.U, i, jj, kk));
-        };
-        auto wcen = [&](int ii, int jj) {
-            return T(0.5) * (ld_uw(g, a.W, ii, jj, k - 1) + ld_uw(g, a.W, ii, jj, k));
-        };
-        auto vcen = [&](int ii, int kk) {
-            return T(0.5) * (ld_v(g, a.V, ii, j - 1, kk) + ld_v(g, a.V, ii, j, kk));
-        };
-        const T hx = T(0.5) * g.idx, hy = T(0.5) * g.idy, hz = T(0.5) * g.idz;
-        L[0][1] = (ucen(j + 1, k) - ucen(j - 1, k)) * hy;
-        L[0][2] = (ucen(j, k + 1) - ucen(j, k - 1)) * hz;
-        L[1][0] = (vcen(i + 1, k) - vcen(i - 1, k)) * hx;
-        L[1][2] = (vcen(i, k + 1) - vcen(i, k - 1)) * hz;
-        L[2][0] = (wcen(i + 1, j) - wcen(i - 1, j)) * hx;
-        L[2][1] = (wcen(i, j + 1) - wcen(i, j - 1)) * hy;
-    }
-
-    // ---- B at the cell and the Table 1 closure
-    T b[6];
+    // plane offsets of this thread's B halo cells
+    size_t hoff[NBH];
+    int hsm[NBH];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) b[c] = __ldg(a.B[c] + c0);
-    T F = T(1), av = T(1);
-    if (MODEL == EVP_FENE_P) {
-        const T tr = b[0] + b[3] + b[5];
-        F = T(mc.L2) / (T(mc.L2) - tr);
-        av = T(mc.a_fene);
-    } else if (MODEL == EVP_SARAMITO) {
-        const T gm = T(mc.gmod);
-        T t[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) t[c] = gm * (b[c] - ((c == 0 || c == 3 || c == 5) ? T(1) : T(0)));
-        const T tr3 = (t[0] + t[3] + t[5]) / T(3);
-        const T d0 = t[0] - tr3, d3 = t[3] - tr3, d5 = t[5] - tr3;
-        const T mag = sqrt(T(0.5) * (d0 * d0 + d3 * d3 + d5 * d5) + t[1] * t[1] + t[2] * t[2] + t[4] * t[4]);
-        const T ty = T(mc.tau_y);
-        if (mag > T(0)) {
-            const T f = T(1) - ty / mag;
-            F = f > T(0) ? f : T(0);
-        } else {
-            F = ty > T(0) ? T(0) : T(1);
+    for (int r = 0; r < NBH; ++r) {
+        const int h = tid + r * NT;
+        hsm[r] = -1;
+        hoff[r] = 0;
+        if (h < BHALO) {
+            int hy, hx;
+            bhalo_pos(h, hy, hx);
+            const int gx = pmod(i0 + hx - 3, g.nx);
+            const int gy = g.walls ? ycen(g, j0 + hy - 3) : pmod(j0 + hy - 3, g.ny);
+            hoff[r] = (size_t)gy * g.nx + gx;
+            hsm[r] = hy * BW + hx;
         }
-        av = F;
     }
-
-    // ---- per-direction stencil offsets: sig = +1 (left-biased) if velocity > 0
-    const int sx = uc > T(0) ? 1 : -1, sy = vc > T(0) ? 1 : -1, sz = wc > T(0) ? 1 : -1;
-    int xi_[6], yj_[6], zk_[6];
+    // plane offsets and ghost factors (+1 copy, -1 no-slip mirror, 0 wall) of this
+    // thread's velocity cells, per component u, v, w
+    size_t voff[3][NVH];
+    signed char vfac[3][NVH];
+    int vsm[NVH];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) {
-        xi_[m] = wrap(i + (m - 3) * sx, g.nx);
-        yj_[m] = ycen(g, j + (m - 3) * sy);
-        zk_[m] = wrap(k + (m - 3) * sz, g.nz);
+    for (int r = 0; r < NVH; ++r) {
+        const int e = tid + r * NT;
+        vsm[r] = e < VPL ? e : -1;
+        const int vy = e / VW, vx = e % VW;
+        const int gx = pmod(i0 + vx - 1, g.nx);
+        int gy = j0 + vy - 1;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            voff[q][r] = 0;
+            vfac[q][r] = 0;
+        }
+        if (e >= VPL) continue;
+        if (!g.walls) {
+            gy = pmod(gy, g.ny);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                voff[q][r] = (size_t)gy * g.nx + gx;
+                vfac[q][r] = 1;
+            }
+        } else {
+            const int my = gy < 0 ? -1 - gy : (gy >= g.ny ? 2 * g.ny - 1 - gy : gy);
+            const bool inside = gy >= 0 && gy < g.ny;
+            voff[0][r] = voff[2][r] = (size_t)min(max(my, 0), g.ny - 1) * g.nx + gx;
+            vfac[0][r] = vfac[2][r] = (my >= 0 && my < g.ny) ? (inside ? 1 : -1) : 0;
+            voff[1][r] = (size_t)(inside ? gy : 0) * g.nx + gx;
+            vfac[1][r] = inside ? 1 : 0;
+        }
     }
-    const size_t rowk = (size_t)k * g.ny;
+    const T* vel[3] = {a.U, a.V, a.W};
+    // velocity plane kk (unwrapped index) into ring slot kk mod 4
+    auto fetch_vel = [&](int kk) {
+        const size_t pv = (size_t)pmod(kk, g.nz) * plane;
+        const int slot = pmod(kk, 4);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int r = 0; r < NVH; ++r) {
+                if (vsm[r] < 0) continue;
+                T* dst = &sm.V[q][slot][vsm[r]];
+                if (vfac[q][r] == 1)
+                    cp_async(dst, vel[q] + pv + voff[q][r]);
+                else
+                    *dst = vfac[q][r] == 0 ? T(0) : -__ldg(vel[q] + pv + voff[q][r]);
+            }
+    };
+    auto fetch_halo = [&](int kk) {
+        const size_t ph = (size_t)pmod(kk, g.nz) * plane;
+        const int buf = kk & 1;
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int r = 0; r < NBH; ++r)
+                if (hsm[r] >= 0) cp_async(&sm.B[buf][c][hsm[r]], a.B[c] + ph + hoff[r]);
+    };
+
+    // ---- prologue: B window (planes k0-3 .. k0+3), velocity planes k0-1 .. k0+1, plane k0 of B
+    T w[6][7];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int m = 0; m < 7; ++m) w[c][m] = __ldg(a.B[c] + (size_t)pmod(k0 + m - 3, g.nz) * plane + col);
+    fetch_vel(k0 - 1);
+    fetch_vel(k0);
+    fetch_vel(k0 + 1);
+    fetch_halo(k0);
+    // RK3 history of this thread's cell in plane kk -> staging buffer kk & 1
+    const size_t cell0 = (size_t)j * g.nx + i;
+    auto fetch_hist = [&](int kk) {
+        if (!a.read_hist || !active || kk >= k1) return;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) cp_async(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0);
+    };
+    fetch_hist(k0);
+    const int ob = (ty + 3) * BW + tx + 3;   // this cell in a B plane
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sm.B[k0 & 1][c][ob] = w[c][3];
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
 
     const T inv_lam = T(mc.inv_lam);
     const T dtz = a.dt_zeta, dtx = a.dt_xi;
+    const T hx = T(0.5) * g.idx, hy = T(0.5) * g.idy, hz = T(0.5) * g.idz;
+    const int o = (ty + 1) * VW + tx + 1;     // this cell in a velocity plane
     unsigned bits = 0;
-    T bn[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        const T* __restrict__ Bc = a.B[c];
-        // x
-        T px[6];
-#pragma unroll
-        for (int m = 0; m < 6; ++m) px[m] = __ldg(Bc + (rowk + j) * g.nx + xi_[m]);
-        T adv = upwind_term(uc, g.idx, px[0], px[1], px[2], px[3], px[4], px[5]);
-#pragma unroll
-        for (int m = 0; m < 6; ++m) px[m] = __ldg(Bc + (rowk + yj_[m]) * g.nx + i);
-        adv += upwind_term(vc, g.idy, px[0], px[1], px[2], px[3], px[4], px[5]);
-#pragma unroll
-        for (int m = 0; m < 6; ++m) px[m] = __ldg(Bc + ((size_t)zk_[m] * g.ny + j) * g.nx + i);
-        adv += upwind_term(wc, g.idz, px[0], px[1], px[2], px[3], px[4], px[5]);
 
-        // upper-convected terms (L B + B L^T)_ab, Reading 2
-        const int ra = row_of(c), cb = col_of(c);
-        T ucd = T(0);
+    for (int k = k0; k < k1; ++k) {
+        // ---- asynchronous prefetch: plane k+4 of B (own column), halo of plane k+1, velocity plane k+2
+        {
+            const size_t pb = (size_t)pmod(k + 4, g.nz) * plane;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) ucd += L[ra][q] * b[symi(q, cb)] + b[symi(ra, q)] * L[cb][q];
-        const bool diag = (c == 0 || c == 3 || c == 5);
-        const T src = ((diag ? av : T(0)) - F * b[c]) * inv_lam;
-        const T rt = src + ucd - adv;
-
-        if (a.rhs_only) {
-            a.RT[c][c0] = rt;
-        } else {
-            T inc = dtz * rt;
-            if (a.read_hist) inc += dtx * a.RT[c][c0];
-            bn[c] = b[c] + inc;
-            a.Bn[c][c0] = bn[c];
-            if (a.write_hist) a.RT[c][c0] = rt;
-            if (!isfinite(bn[c])) bits |= EVP_BIT_NONFINITE;
+            for (int c = 0; c < 6; ++c) cp_async(&sm.N[c][tid], a.B[c] + pb + col);
+            fetch_halo(k + 1);
+            fetch_vel(k + 2);
+            fetch_hist(k + 1);
+            cp_async_commit();
         }
+
+        // ---- S1: centre velocity and gradient (Reading 5) from the velocity ring
+        const T* Up_ = sm.V[0][pmod(k - 1, 4)];
+        const T* Uc_ = sm.V[0][pmod(k, 4)];
+        const T* Un_ = sm.V[0][pmod(k + 1, 4)];
+        const T* Vp_ = sm.V[1][pmod(k - 1, 4)];
+        const T* Vc_ = sm.V[1][pmod(k, 4)];
+        const T* Vn_ = sm.V[1][pmod(k + 1, 4)];
+        const T* Wp_ = sm.V[2][pmod(k - 1, 4)];
+        const T* Wc_ = sm.V[2][pmod(k, 4)];
+        const T Uc = Uc_[o], Um = Uc_[o - 1];
+        const T Vc = Vc_[o], Vm = Vc_[o - VW];
+        const T Wc = Wc_[o], Wm = Wp_[o];
+        const T uc = T(0.5) * (Um + Uc), vc = T(0.5) * (Vm + Vc), wc = T(0.5) * (Wm + Wc);
+        T L[3][3];
+        L[0][0] = (Uc - Um) * g.idx;
+        L[1][1] = (Vc - Vm) * g.idy;
+        L[2][2] = (Wc - Wm) * g.idz;
+        L[0][1] = (T(0.5) * (Uc_[o + VW - 1] + Uc_[o + VW]) - T(0.5) * (Uc_[o - VW - 1] + Uc_[o - VW])) * hy;
+        L[0][2] = (T(0.5) * (Un_[o - 1] + Un_[o]) - T(0.5) * (Up_[o - 1] + Up_[o])) * hz;
+        L[1][0] = (T(0.5) * (Vc_[o + 1 - VW] + Vc_[o + 1]) - T(0.5) * (Vc_[o - 1 - VW] + Vc_[o - 1])) * hx;
+        L[1][2] = (T(0.5) * (Vn_[o - VW] + Vn_[o]) - T(0.5) * (Vp_[o - VW] + Vp_[o])) * hz;
+        L[2][0] = (T(0.5) * (Wp_[o + 1] + Wc_[o + 1]) - T(0.5) * (Wp_[o - 1] + Wc_[o - 1])) * hx;
+        L[2][1] = (T(0.5) * (Wp_[o + VW] + Wc_[o + VW]) - T(0.5) * (Wp_[o - VW] + Wc_[o - VW])) * hy;
+
+        // ---- Table 1 closure at the cell
+        T F = T(1), av = T(1);
+        if (MODEL == EVP_FENE_P) {
+            const T tr = w[0][3] + w[3][3] + w[5][3];
+            F = T(mc.L2) / (T(mc.L2) - tr);
+            av = T(mc.a_fene);
+        } else if (MODEL == EVP_SARAMITO) {
+            const T gm = T(mc.gmod);
+            T t[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) t[c] = gm * (w[c][3] - ((c == 0 || c == 3 || c == 5) ? T(1) : T(0)));
+            const T tr3 = (t[0] + t[3] + t[5]) * T(1.0 / 3.0);
+            const T d0 = t[0] - tr3, d3 = t[3] - tr3, d5 = t[5] - tr3;
+            const T mag = sqrt(T(0.5) * (d0 * d0 + d3 * d3 + d5 * d5) + t[1] * t[1] + t[2] * t[2] + t[4] * t[4]);
+            const T tyv = T(mc.tau_y);
+            if (mag > T(0)) {
+                const T f = T(1) - tyv / mag;
+                F = f > T(0) ? f : T(0);
+            } else {
+                F = tyv > T(0) ? T(0) : T(1);
+            }
+            av = F;
+        }
+
+        // ---- WENO5 advection (stencil direction +1 for a positive velocity), UCD, update
+        const int sx = uc > T(0) ? 1 : -1, syw = vc > T(0) ? BW : -BW;
+        const bool zpos = wc > T(0);
+        const size_t cell = (size_t)k * plane + (size_t)j * g.nx + i;
+        const T* Bk = sm.B[k & 1][0];
+        const T vx_ = fabs(uc) * g.idx, vy_ = fabs(vc) * g.idy, vz_ = fabs(wc) * g.idz;
+        T bn[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const T* P = Bk + c * BPL;
+            T adv = upwind_term(vx_, P[ob - 3 * sx], P[ob - 2 * sx], P[ob - sx], P[ob], P[ob + sx], P[ob + 2 * sx]);
+            adv += upwind_term(vy_, P[ob - 3 * syw], P[ob - 2 * syw], P[ob - syw], P[ob], P[ob + syw], P[ob + 2 * syw]);
+            // z stencil from the register window, mirrored for a non-positive w
+            const T z0 = zpos ? w[c][0] : w[c][6], z1 = zpos ? w[c][1] : w[c][5], z2 = zpos ? w[c][2] : w[c][4];
+            const T z4 = zpos ? w[c][4] : w[c][2], z5 = zpos ? w[c][5] : w[c][1];
+            adv += upwind_term(vz_, z0, z1, z2, w[c][3], z4, z5);
+            const int ra = row_of(c), cb = col_of(c);
+            T ucd = T(0);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) ucd += L[ra][q] * w[symi(q, cb)][3] + w[symi(ra, q)][3] * L[cb][q];
+            const bool diag = (c == 0 || c == 3 || c == 5);
+            const T src = ((diag ? av : T(0)) - F * w[c][3]) * inv_lam;
+            const T rt = src + ucd - adv;
+            if (active) {
+                if (a.rhs_only) {
+                    a.RT[c][cell] = rt;
+                } else {
+                    T inc = dtz * rt;
+                    if (a.read_hist) inc += dtx * sm.H[k & 1][c][tid];
+                    bn[c] = w[c][3] + inc;
+                    a.Bn[c][cell] = bn[c];
+                    if (a.write_hist) a.RT[c][cell] = rt;
+                }
+            }
+        }
+        if (active && !a.rhs_only) {
+            // a non-finite component makes the sum non-finite
+            if (!isfinite(bn[0] + bn[1] + bn[2] + bn[3] + bn[4] + bn[5])) bits |= EVP_BIT_NONFINITE;
+            if (MODEL == EVP_FENE_P && bn[0] + bn[3] + bn[5] >= T(mc.L2)) bits |= EVP_BIT_TRACE_LIMIT;
+            const T det = bn[0] * (bn[3] * bn[5] - bn[4] * bn[4]) - bn[1] * (bn[1] * bn[5] - bn[4] * bn[2])
+                          + bn[2] * (bn[1] * bn[4] - bn[3] * bn[2]);
+            if (det < T(0)) bits |= EVP_BIT_DET_NEG;
+        }
+
+        // ---- advance the window; publish the interior of plane k+1
+        cp_async_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+#pragma unroll
+            for (int m = 0; m < 6; ++m) w[c][m] = w[c][m + 1];
+            w[c][6] = sm.N[c][tid];
+            sm.B[(k + 1) & 1][c][ob] = w[c][3];
+        }
+        __syncthreads();
     }
-    if (!a.rhs_only) {
-        if (MODEL == EVP_FENE_P && bn[0] + bn[3] + bn[5] >= T(mc.L2)) bits |= EVP_BIT_TRACE_LIMIT;
-        const T det = bn[0] * (bn[3] * bn[5] - bn[4] * bn[4]) - bn[1] * (bn[1] * bn[5] - bn[4] * bn[2])
-                      + bn[2] * (bn[1] * bn[4] - bn[3] * bn[2]);
-        if (det < T(0)) bits |= EVP_BIT_DET_NEG;
-        if (bits) atomicOr(a.status, bits);
-    }
+    if (bits) atomicOr(a.status, bits);
 }
 
 }  // namespace
@@ -193,13 +373,29 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a) {
 template <typename T>
 cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a,
                           cudaStream_t st, const TimingHook& th) {
-    dim3 block(32, 8, 1);
-    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    // z chunk: about four CTAs per SM slot-wave over the whole grid, at least 8 planes
+    const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    int chunks = (4 * 152 * 2 + tiles - 1) / tiles;
+    int kz = (g.nz + chunks - 1) / chunks;
+    kz = kz < 8 ? 8 : kz;
+    chunks = (g.nz + kz - 1) / kz;
+    dim3 block(TX, TY, 1);
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
+    const size_t smem = sizeof(StressSmem<T>);
     th.b(K_STRESS);
     switch (mc.model) {
-        case EVP_OLDROYD_B: k_stress<T, EVP_OLDROYD_B><<<grid, block, 0, st>>>(g, mc, a); break;
-        case EVP_FENE_P: k_stress<T, EVP_FENE_P><<<grid, block, 0, st>>>(g, mc, a); break;
-        case EVP_SARAMITO: k_stress<T, EVP_SARAMITO><<<grid, block, 0, st>>>(g, mc, a); break;
+        case EVP_OLDROYD_B:
+            cudaFuncSetAttribute(k_stress<T, EVP_OLDROYD_B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_stress<T, EVP_OLDROYD_B><<<grid, block, smem, st>>>(g, mc, a, kz);
+            break;
+        case EVP_FENE_P:
+            cudaFuncSetAttribute(k_stress<T, EVP_FENE_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_stress<T, EVP_FENE_P><<<grid, block, smem, st>>>(g, mc, a, kz);
+            break;
+        case EVP_SARAMITO:
+            cudaFuncSetAttribute(k_stress<T, EVP_SARAMITO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_stress<T, EVP_SARAMITO><<<grid, block, smem, st>>>(g, mc, a, kz);
+            break;
         default: return cudaErrorInvalidValue;
     }
     th.e(K_STRESS);
