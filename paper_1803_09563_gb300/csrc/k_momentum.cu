@@ -32,6 +32,8 @@ __device__ __forceinline__ int pmod(int a, int n) {
     int r = a % n;
     return r < 0 ? r + n : r;
 }
+// a in [-n, 2n): one conditional wrap, no division
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 template <typename T>
 __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
@@ -105,8 +107,8 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     }
     const T* vel[3] = {a.U, a.V, a.W};
     auto fetch_vel = [&](int kk) {
-        const size_t pv = (size_t)pmod(kk, g.nz) * plane;
-        const int slot = pmod(kk, 4);
+        const size_t pv = (size_t)wrap1(kk, g.nz) * plane;
+        const int slot = kk & 3;
 #pragma unroll
         for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -120,14 +122,14 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
             }
     };
     auto fetch_p = [&](int kk) {
-        const size_t pp = (size_t)pmod(kk, g.nz) * plane;
+        const size_t pp = (size_t)wrap1(kk, g.nz) * plane;
 #pragma unroll
         for (int r = 0; r < NV; ++r)
             if (psm[r] >= 0) cp_async(&sm.P[pmod(kk, 3)][psm[r]], a.P + pp + coff[r]);
     };
     auto fetch_braw = [&](int kk) {
         if (!stress) return;
-        const size_t pb = (size_t)pmod(kk, g.nz) * plane;
+        const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
 #pragma unroll
         for (int c = 0; c < 6; ++c)
 #pragma unroll
@@ -137,17 +139,18 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
                     cp_async(&sm.Braw[6 + c][psm[r]], a.Bn[c] + pb + coff[r]);
                 }
     };
+    const T kgm = T(mc.gmod), kL2 = T(mc.L2), kaf = T(mc.a_fene);
     // staged raw B -> summed stress S in ring slot kk mod 3 (Table 1 inverted)
     auto build_s = [&](int kk) {
         if (!stress) return;
-        const T gm = T(mc.gmod);
+        const T gm = kgm;
         const int slot = pmod(kk, 3);
 #pragma unroll
         for (int r = 0; r < NV; ++r) {
             const int e = psm[r];
             if (e < 0) continue;
             if (MODEL == EVP_FENE_P) {
-                const T L2 = T(mc.L2), av = T(mc.a_fene);
+                const T L2 = kL2, av = kaf;
                 const T Fo = L2 / (L2 - (sm.Braw[0][e] + sm.Braw[3][e] + sm.Braw[5][e]));
                 const T Fn = L2 / (L2 - (sm.Braw[6][e] + sm.Braw[9][e] + sm.Braw[11][e]));
 #pragma unroll
@@ -204,15 +207,15 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         fetch_hist(k + 1);
         cp_async_commit();
 
-        const T* U0 = sm.V[0][pmod(k, 4)];
-        const T* Um1 = sm.V[0][pmod(k - 1, 4)];
-        const T* Up1 = sm.V[0][pmod(k + 1, 4)];
-        const T* V0 = sm.V[1][pmod(k, 4)];
-        const T* Vm1 = sm.V[1][pmod(k - 1, 4)];
-        const T* Vp1 = sm.V[1][pmod(k + 1, 4)];
-        const T* W0 = sm.V[2][pmod(k, 4)];
-        const T* Wm1 = sm.V[2][pmod(k - 1, 4)];
-        const T* Wp1 = sm.V[2][pmod(k + 1, 4)];
+        const T* U0 = sm.V[0][(k & 3)];
+        const T* Um1 = sm.V[0][((k - 1) & 3)];
+        const T* Up1 = sm.V[0][((k + 1) & 3)];
+        const T* V0 = sm.V[1][(k & 3)];
+        const T* Vm1 = sm.V[1][((k - 1) & 3)];
+        const T* Vp1 = sm.V[1][((k + 1) & 3)];
+        const T* W0 = sm.V[2][(k & 3)];
+        const T* Wm1 = sm.V[2][((k - 1) & 3)];
+        const T* Wp1 = sm.V[2][((k + 1) & 3)];
         // value at (i+di, j+dj) of a plane
         auto at = [&](const T* Pl, int di, int dj) { return Pl[o + dj * VW + di]; };
         const T u0 = at(U0, 0, 0), v0 = at(V0, 0, 0), w0 = at(W0, 0, 0);

@@ -140,8 +140,10 @@ k_div_fftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np
     C<T>* sb = sa + (size_t)np * nx;
     const int NL = g.ny * g.nz;
     const int q0 = blockIdx.x * np;
+#pragma unroll 2
     for (int l = threadIdx.y; l < np; l += blockDim.y) {
         const int L0 = 2 * (q0 + l), L1 = L0 + 1;
+#pragma unroll 4
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             const T r0 = L0 < NL ? rhs_value(g, a, L0, i) : T(0);
             const T r1 = L1 < NL ? rhs_value(g, a, L1, i) : T(0);
@@ -174,8 +176,10 @@ k_ifftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
     C<T>* sb = sa + (size_t)np * nx;
     const int NL = g.ny * g.nz;
     const int q0 = blockIdx.x * np;
+#pragma unroll 2
     for (int l = threadIdx.y; l < np; l += blockDim.y) {
         const int L0 = 2 * (q0 + l), L1 = L0 + 1;
+#pragma unroll 4
         for (int m = threadIdx.x; m < nx; m += blockDim.x) {
             C<T> A = mk<T>(T(0), T(0)), B = mk<T>(T(0), T(0));
             const int mm = m <= half ? m : nx - m;
@@ -221,6 +225,7 @@ k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axi
     const int nxh = g.nx / 2 + 1;
     const int kx0 = blockIdx.x * tk;
     const size_t base = blockIdx.y * ostride;
+#pragma unroll 8
     for (int m = threadIdx.y; m < n; m += blockDim.y)
         for (int t = threadIdx.x; t < tk; t += blockDim.x) {
             const int kx = kx0 + t;
@@ -346,46 +351,60 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, do
         const bool top = g.walls && j == g.ny - 1, bottom = g.walls && j == 0;
         const size_t cxp = (size_t)j * g.nx + ip, cxm = (size_t)j * g.nx + im;
         const size_t cyp = (size_t)jp * g.nx + i, cym = (size_t)jm * g.nx + i;
-        // column values of plane k-1 carried along z
+        // values of plane k-1 carried along z; the loads of plane k+1 are issued
+        // while plane k is being computed
+        struct Pl {
+            T pz, px, pxm, py, pym, us, usm, vs, vsm, ws, pold;
+        };
+        auto load = [&](int k) {
+            Pl v;
+            const size_t o = (size_t)k * plane;
+            v.pz = __ldg(Psi + (size_t)wrap(k + 1, g.nz) * plane + cj);
+            v.px = __ldg(Psi + o + cxp);
+            v.pxm = __ldg(Psi + o + cxm);
+            v.py = __ldg(Psi + o + cyp);
+            v.pym = __ldg(Psi + o + cym);
+            v.us = __ldg(Us + o + cj);
+            v.usm = __ldg(Us + o + cxm);
+            v.vs = __ldg(Vs + o + cj);
+            v.vsm = bottom ? T(0) : __ldg(Vs + o + cym);
+            v.ws = __ldg(Ws + o + cj);
+            v.pold = P ? P[o + cj] : T(0);
+            return v;
+        };
         const int km = wrap(k0 - 1, g.nz);
         T psi_m = __ldg(Psi + km * plane + cj);
         T pc = __ldg(Psi + (size_t)k0 * plane + cj);
         T ws_m = __ldg(Ws + km * plane + cj);
+        Pl cur = load(k0);
         for (int k = k0; k < k1; ++k) {
             const size_t o = (size_t)k * plane;
-            const T pz = __ldg(Psi + (size_t)wrap(k + 1, g.nz) * plane + cj);
-            const T px = __ldg(Psi + o + cxp), pxm = __ldg(Psi + o + cxm);
-            const T py = __ldg(Psi + o + cyp), pym = __ldg(Psi + o + cym);
-            const T us = __ldg(Us + o + cj), usm = __ldg(Us + o + cxm);
-            const T vs = __ldg(Vs + o + cj), vsm = bottom ? T(0) : __ldg(Vs + o + cym);
-            const T ws = __ldg(Ws + o + cj);
-            const T pold = P ? P[o + cj] : T(0);
-            const T Un = us - c * ((px - pc) * g.idx);
-            const T Vn = top ? T(0) : vs - c * ((py - pc) * g.idy);
-            const T Wn = ws - c * ((pz - pc) * g.idz);
+            Pl nxt = cur;
+            if (k + 1 < k1) nxt = load(k + 1);
+            const T Un = cur.us - c * ((cur.px - pc) * g.idx);
+            const T Vn = top ? T(0) : cur.vs - c * ((cur.py - pc) * g.idy);
+            const T Wn = cur.ws - c * ((cur.pz - pc) * g.idz);
             U[o + cj] = Un;
             V[o + cj] = Vn;
             W[o + cj] = Wn;
-            if (P) P[o + cj] = pold + pc;
-            if (!RESID) {
-                if (!isfinite(Un + Vn + Wn)) bits |= EVP_BIT_NONFINITE;
-                psi_m = pc;
-                pc = pz;
-                ws_m = ws;
-                continue;
+            if (P) P[o + cj] = cur.pold + pc;
+            if (RESID) {
+                // the faces below the cell, recomputed the way their owners write them
+                const T Ul = cur.usm - c * ((pc - cur.pxm) * g.idx);
+                const T Vl = bottom ? T(0) : cur.vsm - c * ((pc - cur.pym) * g.idy);
+                const T Wl = ws_m - c * ((pc - psi_m) * g.idz);
+                const double dv = (double(Un) - double(Ul)) * idx_d + (double(Vn) - double(Vl)) * idy_d
+                                  + (double(Wn) - double(Wl)) * idz_d;
+                const double ad = fabs(dv);
+                if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn) || !(ad <= DBL_MAX)) bits |= EVP_BIT_NONFINITE;
+                else dmax = fmax(dmax, ad);
+            } else if (!isfinite(Un + Vn + Wn)) {
+                bits |= EVP_BIT_NONFINITE;
             }
-            // the faces below the cell, recomputed the way their owners write them
-            const T Ul = usm - c * ((pc - pxm) * g.idx);
-            const T Vl = bottom ? T(0) : vsm - c * ((pc - pym) * g.idy);
-            const T Wl = ws_m - c * ((pc - psi_m) * g.idz);
-            const double dv = (double(Un) - double(Ul)) * idx_d + (double(Vn) - double(Vl)) * idy_d
-                              + (double(Wn) - double(Wl)) * idz_d;
-            const double ad = fabs(dv);
-            if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn) || !(ad <= DBL_MAX)) bits |= EVP_BIT_NONFINITE;
-            else dmax = fmax(dmax, ad);
             psi_m = pc;
-            pc = pz;
-            ws_m = ws;
+            pc = cur.pz;
+            ws_m = cur.ws;
+            cur = nxt;
         }
     }
     __shared__ double red[8];

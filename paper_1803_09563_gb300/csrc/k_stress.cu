@@ -85,6 +85,8 @@ __device__ __forceinline__ int pmod(int a, int n) {
     int r = a % n;
     return r < 0 ? r + n : r;
 }
+// a in [-n, 2n): one conditional wrap, no division
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // (row, col) inside the 38 x 14 B plane of halo cell h (0 <= h < 276)
 __device__ __forceinline__ void bhalo_pos(int h, int& hy, int& hx) {
@@ -194,8 +196,8 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     const T* vel[3] = {a.U, a.V, a.W};
     // velocity plane kk (unwrapped index) into ring slot kk mod 4
     auto fetch_vel = [&](int kk) {
-        const size_t pv = (size_t)pmod(kk, g.nz) * plane;
-        const int slot = pmod(kk, 4);
+        const size_t pv = (size_t)wrap1(kk, g.nz) * plane;
+        const int slot = kk & 3;
 #pragma unroll
         for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -209,7 +211,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             }
     };
     auto fetch_halo = [&](int kk) {
-        const size_t ph = (size_t)pmod(kk, g.nz) * plane;
+        const size_t ph = (size_t)wrap1(kk, g.nz) * plane;
         const int buf = kk & 1;
 #pragma unroll
         for (int c = 0; c < 6; ++c)
@@ -244,6 +246,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     __syncthreads();
 
     const T inv_lam = T(mc.inv_lam);
+    const T kL2 = T(mc.L2), kaf = T(mc.a_fene), kgm = T(mc.gmod), kty = T(mc.tau_y);
     const T dtz = a.dt_zeta, dtx = a.dt_xi;
     const T hx = T(0.5) * g.idx, hy = T(0.5) * g.idy, hz = T(0.5) * g.idz;
     const int o = (ty + 1) * VW + tx + 1;     // this cell in a velocity plane
@@ -252,7 +255,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     for (int k = k0; k < k1; ++k) {
         // ---- asynchronous prefetch: plane k+4 of B (own column), halo of plane k+1, velocity plane k+2
         {
-            const size_t pb = (size_t)pmod(k + 4, g.nz) * plane;
+            const size_t pb = (size_t)wrap1(k + 4, g.nz) * plane;
 #pragma unroll
             for (int c = 0; c < 6; ++c) cp_async(&sm.N[c][tid], a.B[c] + pb + col);
             fetch_halo(k + 1);
@@ -262,14 +265,14 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         }
 
         // ---- S1: centre velocity and gradient (Reading 5) from the velocity ring
-        const T* Up_ = sm.V[0][pmod(k - 1, 4)];
-        const T* Uc_ = sm.V[0][pmod(k, 4)];
-        const T* Un_ = sm.V[0][pmod(k + 1, 4)];
-        const T* Vp_ = sm.V[1][pmod(k - 1, 4)];
-        const T* Vc_ = sm.V[1][pmod(k, 4)];
-        const T* Vn_ = sm.V[1][pmod(k + 1, 4)];
-        const T* Wp_ = sm.V[2][pmod(k - 1, 4)];
-        const T* Wc_ = sm.V[2][pmod(k, 4)];
+        const T* Up_ = sm.V[0][((k - 1) & 3)];
+        const T* Uc_ = sm.V[0][(k & 3)];
+        const T* Un_ = sm.V[0][((k + 1) & 3)];
+        const T* Vp_ = sm.V[1][((k - 1) & 3)];
+        const T* Vc_ = sm.V[1][(k & 3)];
+        const T* Vn_ = sm.V[1][((k + 1) & 3)];
+        const T* Wp_ = sm.V[2][((k - 1) & 3)];
+        const T* Wc_ = sm.V[2][(k & 3)];
         const T Uc = Uc_[o], Um = Uc_[o - 1];
         const T Vc = Vc_[o], Vm = Vc_[o - VW];
         const T Wc = Wc_[o], Wm = Wp_[o];
@@ -289,17 +292,17 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         T F = T(1), av = T(1);
         if (MODEL == EVP_FENE_P) {
             const T tr = w[0][3] + w[3][3] + w[5][3];
-            F = T(mc.L2) / (T(mc.L2) - tr);
-            av = T(mc.a_fene);
+            F = kL2 / (kL2 - tr);
+            av = kaf;
         } else if (MODEL == EVP_SARAMITO) {
-            const T gm = T(mc.gmod);
+            const T gm = kgm;
             T t[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) t[c] = gm * (w[c][3] - ((c == 0 || c == 3 || c == 5) ? T(1) : T(0)));
             const T tr3 = (t[0] + t[3] + t[5]) * T(1.0 / 3.0);
             const T d0 = t[0] - tr3, d3 = t[3] - tr3, d5 = t[5] - tr3;
             const T mag = sqrt(T(0.5) * (d0 * d0 + d3 * d3 + d5 * d5) + t[1] * t[1] + t[2] * t[2] + t[4] * t[4]);
-            const T tyv = T(mc.tau_y);
+            const T tyv = kty;
             if (mag > T(0)) {
                 const T f = T(1) - tyv / mag;
                 F = f > T(0) ? f : T(0);
@@ -347,7 +350,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         if (active && !a.rhs_only) {
             // a non-finite component makes the sum non-finite
             if (!isfinite(bn[0] + bn[1] + bn[2] + bn[3] + bn[4] + bn[5])) bits |= EVP_BIT_NONFINITE;
-            if (MODEL == EVP_FENE_P && bn[0] + bn[3] + bn[5] >= T(mc.L2)) bits |= EVP_BIT_TRACE_LIMIT;
+            if (MODEL == EVP_FENE_P && bn[0] + bn[3] + bn[5] >= kL2) bits |= EVP_BIT_TRACE_LIMIT;
             const T det = bn[0] * (bn[3] * bn[5] - bn[4] * bn[4]) - bn[1] * (bn[1] * bn[5] - bn[4] * bn[2])
                           + bn[2] * (bn[1] * bn[4] - bn[3] * bn[2]);
             if (det < T(0)) bits |= EVP_BIT_DET_NEG;
