@@ -147,6 +147,30 @@ int evp_project(evp_state* s);
  * (kx, kz) = (0, 0) system is pinned by psi = 0 in its first row.             */
 int evp_poisson_solve(evp_state* s, const void* rhs, void* psi);
 
+/* No-allocation variant of evp_poisson_solve (the paper has no counterpart).
+ * For callers that cannot allocate device memory where they need a solve: code
+ * that runs while a stream is being captured into a CUDA graph, plugins whose
+ * host framework owns all device memory, or processes held to a fixed memory
+ * budget.  It needs no evp_state and calls no cudaMalloc/cudaFree or any other
+ * allocating routine.  All scratch (spectral buffer, FFT tables, Thomas pivots
+ * and the FP64 sweep buffer) lives in one file-scope device array of 8 MiB that
+ * every GPU loading the library holds until the process exits.
+ *   grid:      as for evp_init; the solve's scratch must fit in the 8 MiB array
+ *              (for example 64^3 in FP64 or 96^3 in FP32, periodic), else
+ *              EVP_ERR_ARG with a message giving the bytes needed.
+ *   precision: EVP_FP64 or EVP_FP32 (element type of rhs and psi).
+ *   rhs, psi:  device buffers of nx*ny*nz elements, caller-owned; rhs may equal psi.
+ *   stream:    cudaStream_t to run on (NULL = legacy default stream).
+ * The result is that of evp_poisson_solve on the same grid.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current, and every call whose grid or precision differs from the
+ * previous call's on that device uploads its tables into the array; make such
+ * calls before any stream capture.  All calls on a device share the array and
+ * it keeps the last call's contents (nothing in it needs to start at zero):
+ * calls that overlap on the GPU, on any streams, race and give wrong results.
+ * Asynchronous on ``stream``.                                                    */
+int evp_poisson_solve_static(const evp_grid* grid, int precision, const void* rhs, void* psi, void* stream);
+
 /* Evaluate RT = (aI - F B)/lambda - (u.grad B - B.grad u - grad u^T.B) of Eq. rt
  * at the current state into rt (device, 6*nx*ny*nz elements, component-major
  * in the order xx, xy, xz, yy, yz, zz).                                        */

@@ -52,6 +52,11 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+namespace evp {
+// lets other translation units of the library report through evp_last_error()
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace evp
+
 struct evp_state_s {
     evp_grid g;
     evp_model model;

@@ -75,6 +75,7 @@ def load(path=None):
         'evp_project': (c_int, [c_void_p]),
         'evp_poisson_solve': (c_int, [c_void_p, c_void_p, c_void_p]),
         'evp_stress_rhs': (c_int, [c_void_p, c_void_p]),
+        'evp_poisson_solve_static': (c_int, [POINTER(evp_grid), c_int, c_void_p, c_void_p, c_void_p]),
         'evp_sync': (c_int, [c_void_p, POINTER(c_uint), POINTER(c_double)]),
         'evp_kernel_timing': (c_int, [c_void_p, c_int]),
         'evp_kernel_times': (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), c_int]),
@@ -94,7 +95,7 @@ def exported_symbols():
     """Names declared in include/evp.h that the binding resolves."""
     return ['evp_state_bytes', 'evp_init', 'evp_destroy', 'evp_set_field', 'evp_get_field', 'evp_step',
             'evp_substep', 'evp_project', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_sync', 'evp_kernel_timing',
-            'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error']
+            'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error', 'evp_poisson_solve_static']
 
 
 def _check(code):
@@ -171,6 +172,12 @@ def evp_project(state):
 
 def evp_poisson_solve(state, rhs, psi):
     return _check(load().evp_poisson_solve(state, _ptr(rhs)[0], _ptr(psi)[0]))
+
+
+def evp_poisson_solve_static(grid, precision, rhs, psi, stream=None):
+    """The no-allocation Poisson solve (static device scratch; see evp.h)."""
+    return _check(load().evp_poisson_solve_static(ctypes.byref(grid), int(precision), _ptr(rhs)[0], _ptr(psi)[0],
+                                                  stream))
 
 
 def evp_stress_rhs(state, rt):
