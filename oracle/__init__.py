@@ -41,3 +41,5 @@ from .stress import centre_velocity, velocity_gradient, stress_rhs  # noqa: F401
 from .momentum import advection, laplacian, div_tau, grad_p, momentum_rhs_n  # noqa: F401
 from .poisson import divergence, eigenvalues, solve_poisson, project  # noqa: F401
 from .step import State, rk3_step, rk3_substep, RK3_ALPHA, RK3_ZETA, RK3_XI  # noqa: F401
+from . import levelset  # noqa: F401,E402
+from .ab2 import TwoPhase, ab2_step  # noqa: F401,E402

@@ -1,0 +1,85 @@
+"""Adams-Bashforth two-phase step (Sec. 3.2.2, Eqs. ab2tau, ab2, rt, ru, var-poisson,
+projection) with the level set of Sec. 3.2.1.  TEST INFRASTRUCTURE ONLY.
+
+From t^n to t^n + dt:
+  1. advance the level set (TVD-RK3 + WENO5, velocity u^n); every
+     ``reinit_every`` steps re-distance it (Eq. reinit);
+  2. mixture properties from H(phi^{n+1}): mu_s, mu_p = X1 H + X2 (1 - H),
+     lambda and rho uniform (rho = 1: Boussinesq);
+  3. B^{n+1} = B^n + dt (3/2 RT^n - 1/2 RT^{n-1})                    (Eq. ab2tau)
+  4. u*      = u^n + dt (3/2 RU^n - 1/2 RU^{n-1})                    (Eq. ab2)
+     RU^n = -div(uu)^n + div[mu_s^{n+1}(grad u^n + grad u^n^T)] + div tau^n + f^{n+1}
+  5. lap p^{n+1} = div u*/dt;  u^{n+1} = u* - dt grad p^{n+1}        (Eqs. var-poisson, projection)
+
+Reading 11:
+  * fluid 1 (phi > 0) is the outer EVP fluid (mu_s = beta/Re, mu_p = (1-beta)/Re);
+    fluid 2 (the drop) is Newtonian with total viscosity mu_ratio/Re;
+  * tau^n is formed from B^n with mu_p^{n+1} (the properties are updated first);
+  * the first step is forward Euler (weights 1, 0); the paper is silent on it;
+  * f = CSF force (Eq. fLS) + mean-free Boussinesq buoyancy, see ``levelset``.
+"""
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import levelset as ls
+from .models import Params, tau_from_B
+from .momentum import advection, div_tau, viscous
+from .poisson import project
+from .step import State
+from .stress import stress_rhs
+
+
+@dataclass
+class TwoPhase:
+    """Coefficients of the two-phase (drop) problem."""
+    model: str
+    Re: float
+    Wi: float
+    beta: float
+    tau_y: float
+    mu_ratio: float = 1.0
+    L2: float = 0.0
+    eps_cells: float = 1.5
+    sigma: float = 0.1
+    drho_g: float = 1.0
+    reinit_every: int = 10
+    reinit_iters: int = 3
+
+    def mixture(self, H):
+        mu_s = self.beta / self.Re * H + self.mu_ratio / self.Re * (1.0 - H)
+        mu_p = (1.0 - self.beta) / self.Re * H
+        return mu_s, mu_p
+
+
+def ab2_step(s, phi, dt, g, tp, nstep):
+    """One AB2 step; ``nstep`` counts completed steps (0 for the first).
+    ``s.RT_hist`` / ``s.N_hist`` carry RT^{n-1} / RU^{n-1}.  Returns (State, phi)."""
+    eps = tp.eps_cells * g.dx
+    # 1. level set
+    phi = ls.advect(phi, s.U, s.V, s.W, g, dt)
+    if tp.reinit_every > 0 and (nstep + 1) % tp.reinit_every == 0:
+        phi = ls.reinitialise(phi, g, tp.reinit_iters)
+    # 2. mixture properties at n+1
+    H = ls.heaviside(phi, eps)
+    mu_s, mu_p = tp.mixture(H)
+    prm = Params(tp.model, mu_s=mu_s, mu_p=mu_p, lam=tp.Wi, tau_y=tp.tau_y, L2=tp.L2)
+    w1, w0 = (1.0, 0.0) if nstep == 0 else (1.5, -0.5)
+    # 3. stress, Eq. ab2tau
+    RT = stress_rhs(s.U, s.V, s.W, s.B, g, prm)
+    Bn = [s.B[c] + dt * (w1 * RT[c] + (w0 * s.RT_hist[c] if w0 else 0.0)) for c in range(6)]
+    # 4. momentum, Eq. ab2 with RU of Eq. ru
+    A = advection(s.U, s.V, s.W, g)
+    Vv = viscous(s.U, s.V, s.W, g, mu_s)
+    dtau = div_tau(tau_from_B(s.B, prm), g)
+    fc = ls.interface_force_centres(phi, g, tp.sigma, eps, tp.drho_g)
+    F = ls.centres_to_faces(fc, g)
+    RU = [-A[d] + Vv[d] + dtau[d] + F[d] for d in range(3)]
+    vel = (s.U, s.V, s.W)
+    star = [vel[d] + dt * (w1 * RU[d] + (w0 * s.N_hist[d] if w0 else 0.0)) for d in range(3)]
+    if g.walls:
+        star[1][:, g.ny - 1, :] = 0.0
+    # 5. projection with dt (rho = 1)
+    U, V, W, psi = project(star[0], star[1], star[2], g, dt)
+    return State(U=U, V=V, W=W, p=psi, B=Bn, RT_hist=RT, N_hist=RU, t=s.t + dt, nstep=nstep + 1, psi=psi), phi

@@ -1,0 +1,138 @@
+"""Pins for the oracle's level set, interface force and AB2 step (Secs. 3.2.1, 3.2.2)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import levelset as ls
+from oracle.ab2 import TwoPhase, ab2_step
+from oracle.models import Params, rt_local
+from paper_1803_09563_gb300 import inputs
+
+
+def box(n, L=2.0):
+    return oracle.Grid(n, n, n, L, L, L)
+
+
+def sphere(g, c, R):
+    geo = inputs.geometry(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, g.walls)
+    return inputs.sphere_distance(geo, c, R)
+
+
+def test_heaviside_and_delta_integrate_to_volume_and_area():
+    """For a signed distance to a sphere, int(1 - H) and int(delta) have closed
+    forms: the volume plus 16 pi R eps^2 (1/12 - 1/(2 pi^2)) and the area times
+    (1 + eps^2 (1/3 - 2/pi^2)/R^2), from integrating the smoothed profiles
+    across the shell.  The grid quadrature matches them to 1e-4."""
+    g = box(48)
+    R = 0.55
+    phi = sphere(g, (1.0, 1.0, 1.0), R)
+    eps = 1.5 * g.dx
+    dv = g.dx ** 3
+    vol = ((1.0 - ls.heaviside(phi, eps)).sum() * dv)
+    area = ls.delta(phi, eps).sum() * dv
+    vol_ref = 4.0 / 3.0 * np.pi * R ** 3 + 16.0 * np.pi * R * eps ** 2 * (1.0 / 12.0 - 0.5 / np.pi ** 2)
+    area_ref = 4.0 * np.pi * (R ** 2 + eps ** 2 * (1.0 / 3.0 - 2.0 / np.pi ** 2))
+    assert abs(vol - vol_ref) / vol_ref < 1e-4, (vol, vol_ref)
+    assert abs(area - area_ref) / area_ref < 1e-3, (area, area_ref)
+    # H is 0 deep inside, 1 far outside, 1/2 on the interface; delta = dH/dphi
+    assert ls.heaviside(np.array(-1.0), eps) == 0.0 and ls.heaviside(np.array(1.0), eps) == 1.0
+    assert ls.heaviside(np.array(0.0), eps) == 0.5
+    x = np.linspace(-eps, eps, 101)
+    num = np.gradient(ls.heaviside(x, eps), x)
+    assert np.abs(num - ls.delta(x, eps))[2:-2].max() < 1e-2 / eps
+
+
+def test_sphere_curvature_is_minus_two_over_r():
+    """kappa = -div n (Eq. curv): -2/R on the interface of a sphere (phi > 0 outside)."""
+    for n, tol in ((32, 0.05), (64, 0.02)):
+        g = box(n)
+        R = 0.6
+        phi = sphere(g, (1.0, 1.0, 1.0), R)
+        kap = ls.curvature(ls.normals(phi, g), g)
+        band = np.abs(phi) < 0.5 * g.dx
+        rel = np.abs(kap[band] + 2.0 / (R + phi[band])).max() * R / 2.0
+        assert rel < tol, (n, rel)
+
+
+def test_uniform_translation_returns_sphere():
+    """Uniform velocity across one period: the zero level set returns to its start."""
+    n = 32
+    g = oracle.Grid(n, n, n, 2.0, 2.0, 2.0)
+    phi0 = sphere(g, (1.0, 1.0, 1.0), 0.5)
+    U = np.full(g.shape, 1.0)
+    V = np.full(g.shape, 0.5)
+    W = np.zeros(g.shape)
+    phi = phi0.copy()
+    steps = 80
+    dt = 2.0 / steps      # one period in x, half in y
+    for _ in range(steps):
+        phi = ls.advect(phi, U, V, W, g, dt)
+    # shifted back by (2, 1, 0): the y shift of half a period is 16 cells
+    ref = np.roll(phi0, -16, axis=1)
+    band = np.abs(ref) < 2 * g.dx
+    assert np.abs(phi - ref)[band].max() < 0.02 * g.dx
+    # the interface did not move: sign agrees away from the resolution limit
+    assert np.all(np.sign(phi[np.abs(ref) > g.dx]) == np.sign(ref[np.abs(ref) > g.dx]))
+
+
+def test_reinitialisation_keeps_distance_and_repairs_a_distorted_field():
+    g = box(40)
+    phi0 = sphere(g, (1.0, 1.0, 1.0), 0.6)
+    band = np.abs(phi0) < 3 * g.dx
+    # an exact signed distance is (nearly) a fixed point
+    phi1 = ls.reinitialise(phi0, g, 3)
+    assert np.abs(phi1 - phi0)[band].max() < 0.05 * g.dx
+    # a stretched field phi0 * (2 + x) keeps its zero level set and recovers |grad| ~ 1
+    x = g.xc() + 0 * phi0
+    bad = phi0 * (2.0 + 0.5 * x)
+    fixed = ls.reinitialise(bad, g, 20)
+    gx, gy, gz = np.gradient(fixed, g.dx)
+    gn = np.sqrt(gx ** 2 + gy ** 2 + gz ** 2)
+    near = np.abs(phi0) < 1.5 * g.dx
+    assert np.abs(gn[near] - 1.0).mean() < 0.1
+    assert np.abs(fixed - phi0)[np.abs(phi0) < 0.5 * g.dx].max() < 0.3 * g.dx
+
+
+def test_ab2_coefficients_second_order_on_an_ode():
+    """The AB2 weights (3/2, -1/2) with a forward-Euler first step converge at
+    second order on the Oldroyd-B start-up shear closed form."""
+    prm = Params.from_groups('oldroyd_b', Re=1.0, Wi=0.7, beta=0.3)
+    L = [[0.0, 1.0, 0.0], [0.0] * 3, [0.0] * 3]
+
+    def run(dt, T=1.0):
+        B = [np.array(1.0 if c in (0, 3, 5) else 0.0) for c in range(6)]
+        hist = None
+        for n in range(int(round(T / dt))):
+            rt = rt_local(B, L, prm)
+            w1, w0 = (1.0, 0.0) if n == 0 else (1.5, -0.5)
+            B = [B[c] + dt * (w1 * rt[c] + (w0 * hist[c] if w0 else 0.0)) for c in range(6)]
+            hist = rt
+        return prm.mu_p / prm.lam * B[1]
+
+    ref = prm.mu_p * 1.0 * (1.0 - np.exp(-1.0 / prm.lam))
+    errs = [abs(run(dt) - ref) for dt in (0.02, 0.01, 0.005)]
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 1.9, errs
+
+
+def test_ab2_drop_step_is_projected_and_rises():
+    """A few AB2 steps of the EVP drop: divergence <= 1e-12 after each projection,
+    the drop volume is kept to a few percent, and buoyancy lifts the drop."""
+    n = 24
+    g = oracle.Grid(n, 2 * n, n, 1.5, 3.0, 1.5)
+    phi = sphere(g, (0.75, 0.9, 0.75), 0.35)
+    tp = TwoPhase('saramito', Re=35.0, Wi=1.0, beta=0.5, tau_y=0.02, sigma=0.1, drho_g=1.0,
+                  reinit_every=3, reinit_iters=2)
+    s = oracle.State.rest(g)
+    s.RT_hist, s.N_hist = None, None
+    eps = tp.eps_cells * g.dx
+    vol0 = (1.0 - ls.heaviside(phi, eps)).sum()
+    for it in range(6):
+        s, phi = ab2_step(s, phi, 2e-2, g, tp, it)
+        assert np.abs(oracle.divergence(s.U, s.V, s.W, g)).max() < 1e-12
+    vol = (1.0 - ls.heaviside(phi, eps)).sum()
+    assert abs(vol - vol0) / vol0 < 0.05
+    Hin = 1.0 - ls.heaviside(phi, eps)
+    vbar = (0.5 * (s.V + oracle.at(s.V, g, 'v', j=-1)) * Hin).sum() / Hin.sum()
+    assert vbar > 0.0
