@@ -78,17 +78,32 @@ enum { EVP_RK3 = 0, EVP_AB2 = 1 };
 /* Dimensionless groups and options.  Scalings (rho = 1): mu_s = beta/Re,
  * mu_p = (1-beta)/Re, lambda = Wi; tau_y = Bi/Re (bi_def = 0, Bi against the
  * viscous stress, Sec. 4.1.3) or tau_y = Bi (bi_def = 1, Bi against rho g L,
- * Sec. 4.2.3).  Body forces: a uniform force dpdx along x (the channel's
- * pressure gradient) and the ABC force
- * abc_amp*(sin kz + cos ky, sin kx + cos kz, sin ky + cos kx), k = abc_k.      */
+ * Sec. 4.2.3).  Body forces (RK3 only): a uniform force dpdx along x (the
+ * channel's pressure gradient) and the ABC force
+ * abc_amp*(sin kz + cos ky, sin kx + cos kz, sin ky + cos kx), k = abc_k.
+ *
+ * integrator = EVP_AB2 selects the two-phase drop step of Secs. 3.2.1-3.2.2:
+ * a level set phi (phi > 0 outer fluid with the model above, phi < 0 a
+ * Newtonian drop of total viscosity mu_ratio/Re), advected by TVD-RK3 + WENO5
+ * and re-distanced every reinit_every steps with reinit_iters pseudo-steps
+ * (Eq. reinit); mixture viscosities from H(phi) smoothed over ls_eps_cells
+ * cells; CSF surface tension sigma (Eq. fLS) and Boussinesq buoyancy drho_g
+ * (minus its domain mean) along +y; AB2 for B and u (Eqs. ab2tau, ab2) with a
+ * forward-Euler first step; pressure from one projection per step.            */
 typedef struct {
     double Re, Wi, beta, Bi, L2;
     int bi_def;
     double dpdx;
     double abc_amp, abc_k;
     int precision;      /* EVP_FP64 or EVP_FP32 (the Thomas sweeps run in FP64 in both) */
-    int integrator;     /* EVP_RK3 (Eq. RK); EVP_AB2 reserved for the two-phase step    */
-    double reserved[16];
+    int integrator;     /* EVP_RK3 (Eq. RK) or EVP_AB2 (two-phase step)                 */
+    double mu_ratio;    /* AB2: drop total viscosity / outer total viscosity            */
+    double ls_eps_cells;/* AB2: half-width of the smoothed Heaviside, in cells          */
+    double sigma;       /* AB2: surface tension                                          */
+    double drho_g;      /* AB2: buoyancy, density difference times gravity               */
+    int reinit_every;   /* AB2: re-distance every this many steps (0: never)            */
+    int reinit_iters;   /* AB2: pseudo-time steps per re-distancing (dtau = dx/2)       */
+    double reserved[10];
 } evp_params;
 
 /* Field identifiers for evp_set_field / evp_get_field */
@@ -98,7 +113,8 @@ typedef enum {
     EVP_RT_XX = 10, /* ... EVP_RT_XX+5: RK3 history RT^{k-2} (Eq. RK-rt)          */
     EVP_NH_X = 16,  /* ... EVP_NH_X+2: RK3 history of -div(uu)+viscous+force     */
     EVP_PSI = 19,   /* last projection variable psi (read only)                  */
-    EVP_NFIELDS = 20
+    EVP_PHI = 20,   /* AB2 two-phase states: level set phi at cell centres       */
+    EVP_NFIELDS = 21
 } evp_field;
 
 typedef struct evp_state_s evp_state;
@@ -130,8 +146,12 @@ int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device);
  * Poisson solve (Eq. NS-num2) and correction (Eq. NS-num3).  Asynchronous.   */
 int evp_step(evp_state* s, double dt);
 
+/* With integrator EVP_AB2, evp_step is one two-phase AB2 step of size dt
+ * (level set, re-distancing when due, interface force, B and u updates,
+ * projection with dt); steps are counted from evp_init.                       */
+
 /* Substep k = 0, 1, 2 of the RK3 scheme alone (Eq. RK constants alpha^k,
- * zeta^k, xi^k).  For k > 0 the histories RT^{k-2} and N^{k-2} are the ones in
+ * zeta^k, xi^k; EVP_ERR_STATE for an AB2 state).  For k > 0 the histories RT^{k-2} and N^{k-2} are the ones in
  * the state (set them with evp_set_field to reproduce an arbitrary substep).  */
 int evp_substep(evp_state* s, double dt, int k);
 

@@ -39,7 +39,8 @@ const double RK_XI[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 
 const char* KERNEL_NAMES[K_COUNT] = {"stress_weno_update", "momentum_predictor", "div_fft_x",
                                      "fft_z_forward",      "fft_y_modal_solve",  "thomas_y_fp64",
-                                     "fft_z_inverse",      "ifft_x_psi",         "project_correct"};
+                                     "fft_z_inverse",      "ifft_x_psi",         "project_correct",
+                                     "levelset_stage",     "interface_force"};
 
 bool is_2a3b(int n) {
     if (n < 1) return false;
@@ -92,6 +93,18 @@ struct evp_state_s {
     double* thomas_d;
     unsigned* d_status;
     unsigned long long* d_maxdiv;
+    // two-phase (AB2) fields
+    bool ab2;
+    void* PHI;
+    void* PHI0;
+    void* PHIA;
+    void* PHIB;
+    void* HF;
+    void* NRM[3];
+    void* FC[3];
+    double* partials;
+    double* mean_1mH;
+    long long nstep;     // AB2 steps taken
     int cu, cb;          // current velocity / B buffer
     ModelConst mc;
     // timing
@@ -175,7 +188,14 @@ int validate(const evp_grid* g, evp_model model, const evp_params* p) {
     if (model == EVP_FENE_P && !(p->L2 > 3)) return fail(EVP_ERR_ARG, "FENE-P needs L2 > 3");
     if (model == EVP_SARAMITO && !(p->Bi >= 0)) return fail(EVP_ERR_ARG, "Bi must be >= 0");
     if (p->precision != EVP_FP64 && p->precision != EVP_FP32) return fail(EVP_ERR_ARG, "bad precision");
-    if (p->integrator != EVP_RK3) return fail(EVP_ERR_ARG, "only the RK3 integrator is available");
+    if (p->integrator != EVP_RK3 && p->integrator != EVP_AB2) return fail(EVP_ERR_ARG, "unknown integrator");
+    if (p->integrator == EVP_AB2) {
+        if (p->dpdx != 0.0 || p->abc_amp != 0.0)
+            return fail(EVP_ERR_ARG, "the AB2 two-phase step takes no dpdx or ABC forcing");
+        if (!(p->mu_ratio > 0) || !(p->ls_eps_cells > 0) || !(p->sigma >= 0) || p->reinit_every < 0 ||
+            p->reinit_iters < 0)
+            return fail(EVP_ERR_ARG, "bad two-phase parameters (mu_ratio, ls_eps_cells, sigma, reinit)");
+    }
     return EVP_OK;
 }
 
@@ -224,6 +244,13 @@ size_t plan(evp_state* s, char* base) {
     void* trig = P((size_t)2 * (g.nx + g.ny + g.nz) * e);
     void* thm = g.walls_y ? P((size_t)(g.nz / 2 + 1) * g.ny * nxh * sizeof(double2)) : nullptr;
     void* thd = g.walls_y ? P((size_t)2 * nxh * g.ny * g.nz * sizeof(double)) : nullptr;
+    const bool ab2 = s->prm.integrator == EVP_AB2;
+    void* ls[12] = {nullptr};
+    if (ab2)
+        for (int q = 0; q < 12; ++q) ls[q] = P(N * e);   // phi, phi0, phiA, phiB, H, n(3), f(3), spare
+    const size_t nparts = (size_t)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.nz;
+    void* parts = ab2 ? P(nparts * sizeof(double)) : nullptr;
+    void* mean = ab2 ? P(sizeof(double)) : nullptr;
     void* st = P(sizeof(unsigned));
     void* md = P(sizeof(unsigned long long));
     if (base) {
@@ -234,6 +261,18 @@ size_t plan(evp_state* s, char* base) {
         s->thomas_d = static_cast<double*>(thd);
         s->d_status = static_cast<unsigned*>(st);
         s->d_maxdiv = static_cast<unsigned long long*>(md);
+        s->ab2 = ab2;
+        s->PHI = ls[0];
+        s->PHI0 = ls[1];
+        s->PHIA = ls[2];
+        s->PHIB = ls[3];
+        s->HF = ls[4];
+        for (int q = 0; q < 3; ++q) {
+            s->NRM[q] = ls[5 + q];
+            s->FC[q] = ls[8 + q];
+        }
+        s->partials = static_cast<double*>(parts);
+        s->mean_1mH = static_cast<double*>(mean);
     }
     return L.total;
 }
@@ -379,7 +418,7 @@ int run_poisson(evp_state* s, const T* Us, const T* Vs, const T* Ws, const T* rh
 
 template <typename T>
 int run_correct(evp_state* s, const T* Us, const T* Vs, const T* Ws, T* U, T* V, T* W, T* P, double coef,
-                bool residual) {
+                bool residual, bool p_replace = false) {
     CorrectArgs<T> a;
     a.Us = Us;
     a.Vs = Vs;
@@ -389,6 +428,7 @@ int run_correct(evp_state* s, const T* Us, const T* Vs, const T* Ws, T* U, T* V,
     a.V = V;
     a.W = W;
     a.P = P;
+    a.p_replace = p_replace ? 1 : 0;
     a.coef = T(coef);
     a.maxdiv = residual ? s->d_maxdiv : nullptr;
     a.status = s->d_status;
@@ -427,6 +467,8 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
         a.write_hist = write_hist;
         a.rhs_only = 0;
         a.status = s->d_status;
+        a.H = nullptr;
+        a.mu_p1 = a.mu_p2 = T(0);
         cudaError_t e = launch_stress<T>(g, s->mc, a, s->st, th);
         if (e != cudaSuccess) return cuda_fail(e, "stress kernel");
     }
@@ -469,6 +511,131 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
     return EVP_OK;
 }
 
+// One two-phase AB2 step (Secs. 3.2.1-3.2.2): level set, re-distancing when due,
+// interface force, B (Eq. ab2tau) and u* (Eq. ab2), projection with dt.
+template <typename T>
+int ab2_step_t(evp_state* s, double dt) {
+    const Geo<T> g = geo_of<T>(s);
+    const TimingHook th = hook_of(s);
+    const evp_params& p = s->prm;
+    const int cu = s->cu, cb = s->cb;
+    const double dx = s->g.lx / s->g.nx;
+    const bool stress = s->model != EVP_NEWTONIAN;
+    auto stage = [&](const void* phin, const void* phis, void* out, double a, double b, bool reinit, double h) {
+        LsArgs<T> L;
+        L.U = static_cast<const T*>(s->U[cu]);
+        L.V = static_cast<const T*>(s->V[cu]);
+        L.W = static_cast<const T*>(s->W[cu]);
+        L.phin = static_cast<const T*>(phin);
+        L.phis = static_cast<const T*>(phis);
+        L.phi0 = static_cast<const T*>(s->PHI0);
+        L.out = static_cast<T*>(out);
+        L.pt_a = T(a);
+        L.pt_b = T(b);
+        L.dt = T(h);
+        L.h = T(dx);
+        return launch_ls_stage<T>(g, L, reinit, s->st, th);
+    };
+    // 1. level set: TVD-RK3 with u^n; the third stage writes phi in place
+    cudaError_t e;
+    if ((e = stage(s->PHI, s->PHI, s->PHIA, 0.0, 1.0, false, dt)) != cudaSuccess) return cuda_fail(e, "level set");
+    if ((e = stage(s->PHI, s->PHIA, s->PHIB, 0.75, 0.25, false, dt)) != cudaSuccess) return cuda_fail(e, "level set");
+    if ((e = stage(s->PHI, s->PHIB, s->PHI, 1.0 / 3.0, 2.0 / 3.0, false, dt)) != cudaSuccess)
+        return cuda_fail(e, "level set");
+    if (p.reinit_every > 0 && (s->nstep + 1) % p.reinit_every == 0 && p.reinit_iters > 0) {
+        CK(cudaMemcpyAsync(s->PHI0, s->PHI, s->N * sizeof(T), cudaMemcpyDeviceToDevice, s->st));
+        const double dtau = 0.5 * dx;
+        for (int it = 0; it < p.reinit_iters; ++it) {
+            if ((e = stage(s->PHI, s->PHI, s->PHIA, 0.0, 1.0, true, dtau)) != cudaSuccess) return cuda_fail(e, "reinit");
+            if ((e = stage(s->PHI, s->PHIA, s->PHIB, 0.75, 0.25, true, dtau)) != cudaSuccess)
+                return cuda_fail(e, "reinit");
+            if ((e = stage(s->PHI, s->PHIB, s->PHI, 1.0 / 3.0, 2.0 / 3.0, true, dtau)) != cudaSuccess)
+                return cuda_fail(e, "reinit");
+        }
+    }
+    // 2. H, normals, interface force at n+1
+    {
+        IfaceArgs<T> I;
+        I.phi = static_cast<const T*>(s->PHI);
+        I.H = static_cast<T*>(s->HF);
+        for (int q = 0; q < 3; ++q) {
+            I.n[q] = static_cast<T*>(s->NRM[q]);
+            I.f[q] = static_cast<T*>(s->FC[q]);
+        }
+        I.partials = s->partials;
+        I.mean_1mH = s->mean_1mH;
+        I.eps = T(p.ls_eps_cells * dx);
+        I.sigma = T(p.sigma);
+        I.drho_g = T(p.drho_g);
+        if ((e = launch_interface<T>(g, I, s->st, th)) != cudaSuccess) return cuda_fail(e, "interface");
+    }
+    const bool first = s->nstep == 0;
+    const double w1 = first ? 1.0 : 1.5, w0 = first ? 0.0 : -0.5;
+    const double mu0 = 1.0 / p.Re;
+    const T mp1 = T((1.0 - p.beta) * mu0), mp2 = T(0);
+    // 3. B^{n+1} = B^n + dt (w1 RT^n + w0 RT^{n-1})
+    if (stress) {
+        StressArgs<T> a;
+        a.U = static_cast<const T*>(s->U[cu]);
+        a.V = static_cast<const T*>(s->V[cu]);
+        a.W = static_cast<const T*>(s->W[cu]);
+        for (int c = 0; c < 6; ++c) {
+            a.B[c] = static_cast<const T*>(s->B[cb][c]);
+            a.Bn[c] = static_cast<T*>(s->B[1 - cb][c]);
+            a.RT[c] = static_cast<T*>(s->RT[c]);
+        }
+        a.dt_zeta = T(dt * w1);
+        a.dt_xi = T(dt * w0);
+        a.read_hist = !first;
+        a.write_hist = 1;
+        a.rhs_only = 0;
+        a.status = s->d_status;
+        a.H = static_cast<const T*>(s->HF);
+        a.mu_p1 = mp1;
+        a.mu_p2 = mp2;
+        if ((e = launch_stress<T>(g, s->mc, a, s->st, th)) != cudaSuccess) return cuda_fail(e, "stress kernel");
+    }
+    // 4. u* = u^n + dt (w1 RU^n + w0 RU^{n-1}), tau^n from B^n with mu_p(H^{n+1})
+    {
+        MomAB2Args<T> m;
+        m.U = static_cast<const T*>(s->U[cu]);
+        m.V = static_cast<const T*>(s->V[cu]);
+        m.W = static_cast<const T*>(s->W[cu]);
+        for (int c = 0; c < 6; ++c) m.B[c] = static_cast<const T*>(s->B[cb][c]);
+        m.H = static_cast<const T*>(s->HF);
+        for (int q = 0; q < 3; ++q) {
+            m.f[q] = static_cast<const T*>(s->FC[q]);
+            m.NH[q] = static_cast<T*>(s->NH[q]);
+        }
+        m.Us = static_cast<T*>(s->U[1 - cu]);
+        m.Vs = static_cast<T*>(s->V[1 - cu]);
+        m.Ws = static_cast<T*>(s->W[1 - cu]);
+        m.w1dt = T(dt * w1);
+        m.w0dt = T(dt * w0);
+        m.read_hist = !first;
+        m.mu_s1 = T(p.beta * mu0);
+        m.mu_s2 = T(p.mu_ratio * mu0);
+        m.mu_p1 = mp1;
+        m.mu_p2 = mp2;
+        m.inv_lam = T(s->mc.inv_lam);
+        m.L2 = T(s->mc.L2);
+        m.a_fene = T(s->mc.a_fene);
+        if ((e = launch_momentum_ab2<T>(g, s->model, m, s->st, th)) != cudaSuccess)
+            return cuda_fail(e, "momentum kernel");
+    }
+    // 5. projection with dt: p^{n+1} = psi
+    int r = run_poisson<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
+                           static_cast<const T*>(s->W[1 - cu]), nullptr, 1.0 / dt, static_cast<T*>(s->PSI));
+    if (r) return r;
+    r = run_correct<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
+                       static_cast<const T*>(s->W[1 - cu]), static_cast<T*>(s->U[cu]), static_cast<T*>(s->V[cu]),
+                       static_cast<T*>(s->W[cu]), static_cast<T*>(s->P), dt, true, true);
+    if (r) return r;
+    if (stress) s->cb = 1 - cb;
+    s->nstep += 1;
+    return EVP_OK;
+}
+
 void* field_ptr(evp_state* s, int f) {
     if (f == EVP_U) return s->U[s->cu];
     if (f == EVP_V) return s->V[s->cu];
@@ -478,6 +645,7 @@ void* field_ptr(evp_state* s, int f) {
     if (f >= EVP_RT_XX && f < EVP_RT_XX + 6) return s->RT[f - EVP_RT_XX];
     if (f >= EVP_NH_X && f < EVP_NH_X + 3) return s->NH[f - EVP_NH_X];
     if (f == EVP_PSI) return s->PSI;
+    if (f == EVP_PHI) return s->ab2 ? s->PHI : nullptr;
     return nullptr;
 }
 
@@ -502,6 +670,12 @@ int init_fields(evp_state* s) {
     for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(s->NH[c], 0, N * sizeof(T), s->st));
     CK(cudaMemsetAsync(s->P, 0, N * sizeof(T), s->st));
     CK(cudaMemsetAsync(s->PSI, 0, N * sizeof(T), s->st));
+    if (s->ab2) {
+        void* z[] = {s->PHI, s->PHI0, s->PHIA, s->PHIB, s->HF, s->NRM[0], s->NRM[1], s->NRM[2],
+                     s->FC[0], s->FC[1], s->FC[2]};
+        for (void* q : z) CK(cudaMemsetAsync(q, 0, N * sizeof(T), s->st));
+    }
+    s->nstep = 0;
     CK(cudaMemsetAsync(s->d_status, 0, sizeof(unsigned), s->st));
     CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
     CK(cudaStreamSynchronize(s->st));
@@ -522,6 +696,7 @@ size_t evp_state_bytes(const evp_grid* grid, evp_model model, const evp_params* 
     if (validate(grid, model, params) != EVP_OK) return 0;
     evp_state tmp;
     tmp.g = *grid;
+    tmp.prm = *params;
     tmp.elt = params->precision == EVP_FP32 ? 4 : 8;
     return plan(&tmp, nullptr);
 }
@@ -645,6 +820,7 @@ int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device) {
 
 int evp_substep(evp_state* s, double dt, int k) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (s->ab2) return fail(EVP_ERR_STATE, "evp_substep is an RK3 call; this state integrates with AB2");
     if (k < 0 || k > 2) return fail(EVP_ERR_ARG, "substep index must be 0, 1 or 2");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
     return s->fp32 ? substep_t<float>(s, dt, k, false, false) : substep_t<double>(s, dt, k, false, false);
@@ -653,6 +829,7 @@ int evp_substep(evp_state* s, double dt, int k) {
 int evp_step(evp_state* s, double dt) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
+    if (s->ab2) return s->fp32 ? ab2_step_t<float>(s, dt) : ab2_step_t<double>(s, dt);
     for (int k = 0; k < 3; ++k) {
         int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2, true) : substep_t<double>(s, dt, k, k == 2, true);
         if (r) return r;
@@ -709,6 +886,8 @@ int evp_stress_rhs(evp_state* s, void* rt) {
         a.write_hist = 0;
         a.rhs_only = 1;
         a.status = s->d_status;
+        a.H = nullptr;
+        a.mu_p1 = a.mu_p2 = T(0);
         cudaError_t e = launch_stress<T>(geo_of<T>(s), s->mc, a, s->st, hook_of(s));
         return e == cudaSuccess ? EVP_OK : cuda_fail(e, "stress kernel");
     };

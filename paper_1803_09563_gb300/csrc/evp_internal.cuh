@@ -25,6 +25,8 @@ enum KernelId {
     K_FFT_Z_INV,      // S7(z): inverse complex FFT along z
     K_IFFTX,          // S7(x): complex-to-real inverse FFT along x -> psi
     K_CORRECT,        // S8: u = u* - c grad psi, p += psi, FP64 divergence residual
+    K_LEVELSET,       // S9: TVD-RK3 stage of level-set advection or re-distancing
+    K_INTERFACE,      // S9: H, normals, curvature, CSF and buoyancy force
     K_COUNT
 };
 
@@ -103,6 +105,8 @@ struct StressArgs {
     T dt_zeta, dt_xi;
     int read_hist, write_hist, rhs_only;
     unsigned* status;
+    const T* H;        // two-phase: Heaviside of the level set (null: single phase)
+    T mu_p1, mu_p2;    // two-phase: polymer viscosity of fluid 1 (H = 1) and fluid 2
 };
 
 template <typename T>
@@ -162,11 +166,54 @@ struct CorrectArgs {
     T* U;
     T* V;
     T* W;
-    T* P;              // p += psi if non-null
+    T* P;              // p += psi if non-null (p = psi with p_replace)
+    int p_replace;     // AB2 step: the pressure is psi itself (Eq. projection)
     T coef;            // 2 alpha dt (or 1 for a plain projection)
     unsigned long long* maxdiv;   // FP64 bits of max |div u|
     unsigned* status;
     double idx_d, idy_d, idz_d;   // FP64 reciprocal spacings for the residual
+};
+
+// two-phase step (level set, interface force, AB2 momentum)
+template <typename T>
+struct LsArgs {
+    const T* U;
+    const T* V;
+    const T* W;        // velocity u^n (advection)
+    const T* phin;     // phi at the start of the TVD-RK3 step (pointwise term)
+    const T* phis;     // stage input (stencil)
+    const T* phi0;     // re-distancing: phi before it started, for S(phi0)
+    T* out;            // out = pt_a phin + pt_b (phis + dt rhs(phis))
+    T pt_a, pt_b, dt;
+    T h;               // grid spacing (S(phi0) smoothing width)
+};
+
+template <typename T>
+struct IfaceArgs {
+    const T* phi;
+    T* H;
+    T* n[3];           // unit normal at centres
+    T* f[3];           // interface force at centres
+    double* partials;  // per-block sums of 1 - H
+    double* mean_1mH;  // domain mean of 1 - H
+    T eps, sigma, drho_g;
+};
+
+template <typename T>
+struct MomAB2Args {
+    const T* U;
+    const T* V;
+    const T* W;
+    const T* B[6];     // B^n
+    const T* H;
+    const T* f[3];     // interface force at centres
+    T* Us;
+    T* Vs;
+    T* Ws;
+    T* NH[3];          // RU^{n-1} in (if read_hist), RU^n out
+    T w1dt, w0dt;      // dt * 3/2 and dt * (-1/2) (dt and 0 on the first step)
+    int read_hist;
+    T mu_s1, mu_s2, mu_p1, mu_p2, inv_lam, L2, a_fene;
 };
 
 // ----------------------------------------------------------- launch functions
@@ -195,6 +242,20 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
 template <typename T>
 cudaError_t launch_correct(const Geo<T>& g, const CorrectArgs<T>& a, cudaStream_t st,
                            const TimingHook& th);
+
+template <typename T>
+cudaError_t launch_ls_stage(const Geo<T>& g, const LsArgs<T>& a, bool reinit, cudaStream_t st,
+                            const TimingHook& th);
+
+template <typename T>
+size_t iface_partials(const Geo<T>& g);
+
+template <typename T>
+cudaError_t launch_interface(const Geo<T>& g, const IfaceArgs<T>& a, cudaStream_t st, const TimingHook& th);
+
+template <typename T>
+cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>& a, cudaStream_t st,
+                                const TimingHook& th);
 
 // radix plan of n = 4^a 3^b 2^c (radix-4 first); returns the number of stages or -1
 int fft_radices(int n, int* rad);

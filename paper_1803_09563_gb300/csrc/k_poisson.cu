@@ -369,7 +369,7 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, do
             v.vs = __ldg(Vs + o + cj);
             v.vsm = bottom ? T(0) : __ldg(Vs + o + cym);
             v.ws = __ldg(Ws + o + cj);
-            v.pold = P ? P[o + cj] : T(0);
+            v.pold = (P && !a.p_replace) ? P[o + cj] : T(0);
             return v;
         };
         const int km = wrap(k0 - 1, g.nz);
@@ -387,7 +387,7 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, do
             U[o + cj] = Un;
             V[o + cj] = Vn;
             W[o + cj] = Wn;
-            if (P) P[o + cj] = cur.pold + pc;
+            if (P) P[o + cj] = a.p_replace ? pc : cur.pold + pc;
             if (RESID) {
                 // the faces below the cell, recomputed the way their owners write them
                 const T Ul = cur.usm - c * ((pc - cur.pxm) * g.idx);

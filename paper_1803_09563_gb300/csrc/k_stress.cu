@@ -8,50 +8,11 @@
 #include <cfloat>
 
 #include "evp_internal.cuh"
+#include "weno.cuh"
 
 namespace evp {
 
 namespace {
-
-// Fifth-order WENO combination (Sec. 3.1) of five undivided differences ordered
-// from far upwind to downwind, times ``scale``: Jiang-Shu smoothness indicators,
-// linear weights (1/10, 6/10, 3/10), eps = 1e-6, power 2.  Algebraically
-// rearranged for fewer operations, with the same value:
-//  * the indicators use the second differences a_k and b_k of the differences;
-//    eps and all three indicators are scaled by 12/13 (a common factor of
-//    eps + S_k cancels in the normalised weights);
-//  * the weights alpha_k = d_k/e_k^2 are multiplied through by 10 e_1^2 e_2^2 e_3^2,
-//    which leaves one division.
-template <typename T>
-__device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5, T scale) {
-    const T eps = T(1.0e-6 * 12.0 / 13.0), r = T(3.0 / 13.0);
-    // candidates: q1, 6 q2, 3 q3
-    const T q1 = v1 * T(1.0 / 3.0) - v2 * T(7.0 / 6.0) + v3 * T(11.0 / 6.0);
-    const T q2 = -v2 + T(5) * v3 + T(2) * v4;
-    const T q3 = v3 + T(2.5) * v4 - T(0.5) * v5;
-    const T e12 = v1 - v2, e23 = v2 - v3, e34 = v3 - v4, e45 = v4 - v5;
-    const T a1 = e12 - e23, a2 = e23 - e34, a3 = e34 - e45;
-    const T b1 = a1 - T(2) * e23, b2 = e23 + e34, b3 = a3 + T(2) * e34;
-    // (12/13)(eps + S_k) = a_k^2 + (3/13) b_k^2 + (12/13) eps
-    T s1 = fma(b1 * r, b1, fma(a1, a1, eps));
-    T s2 = fma(b2 * r, b2, fma(a2, a2, eps));
-    T s3 = fma(b3 * r, b3, fma(a3, a3, eps));
-    s1 *= s1;
-    s2 *= s2;
-    s3 *= s3;
-    const T w1 = s2 * s3, w2 = s1 * s3, w3 = s1 * s2;
-    T den = fma(T(3), w3, fma(T(6), w2, w1));
-    T num = fma(w3, q3, fma(w2, q2, w1 * q1)) * scale;
-    if (sizeof(T) == 4) {
-        // single precision: CUDA's fast division holds to 2 ulp while the divisor
-        // stays below 2^126; beyond that (products near overflow) use the
-        // three-division form
-        if (den <= T(8.5e37)) return __fdividef(float(num), float(den));
-        const T x1 = T(1) / s1, x2 = T(1) / s2, x3 = T(1) / s3;
-        return (x1 * q1 + x2 * q2 + x3 * q3) * scale / (x1 + T(6) * x2 + T(3) * x3);
-    }
-    return num / den;
-}
 
 // storage index of the symmetric component (a, b): xx xy xz yy yz zz
 __device__ __forceinline__ constexpr int symi(int a, int b) {
@@ -60,15 +21,6 @@ __device__ __forceinline__ constexpr int symi(int a, int b) {
 __device__ __forceinline__ constexpr int row_of(int c) { return c < 3 ? 0 : (c < 5 ? 1 : 2); }
 __device__ __forceinline__ constexpr int col_of(int c) { return c == 0 ? 0 : ((c == 1 || c == 3) ? 1 : 2); }
 
-// |u| * (upwind WENO5 derivative) of a centred field along one axis, from the
-// six values phi(c + m*sig*step), m = -3..2, where sig = +1 for a positive
-// velocity (left-biased stencil) and -1 otherwise (right-biased, mirrored; the
-// differences then change sign exactly, and so does the WENO combination).
-// ``vih`` = |u| / h.
-template <typename T>
-__device__ __forceinline__ T upwind_term(T vih, T pm3, T pm2, T pm1, T p0, T pp1, T pp2) {
-    return weno5(pm2 - pm3, pm1 - pm2, p0 - pm1, pp1 - p0, pp2 - pp1, vih);
-}
 
 // Tile geometry of the z-marching kernel: a 32 x 8 tile of cells in x-y walks
 // through a chunk of z planes.  B of the tile's own column lives in a 7-plane
@@ -295,7 +247,12 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             F = kL2 / (kL2 - tr);
             av = kaf;
         } else if (MODEL == EVP_SARAMITO) {
-            const T gm = kgm;
+            T gm = kgm;
+            if (a.H) {
+                // two-phase mixture: polymer viscosity mu_p(H) of the cell
+                const T Hc = __ldg(a.H + (size_t)k * plane + col);
+                gm = (a.mu_p1 * Hc + a.mu_p2 * (T(1) - Hc)) * inv_lam;
+            }
             T t[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) t[c] = gm * (w[c][3] - ((c == 0 || c == 3 || c == 5) ? T(1) : T(0)));

@@ -1,0 +1,342 @@
+// S9 + S10: level set, interface force and the AB2 momentum predictor of the
+// two-phase step (Secs. 3.2.1 and 3.2.2).
+//
+//   k_ls_stage      one TVD-RK3 stage of the level-set advection (Eq. ls-adv,
+//                   WENO5 upwinded by the centre velocity) or of the
+//                   re-distancing equation (Eq. reinit, Godunov |grad phi| from
+//                   the WENO5 one-sided derivatives, S(phi0) = phi0/sqrt(phi0^2 + h^2))
+//   k_iface_a       H(phi), n = grad phi/|grad phi| (central), per-block sums of 1 - H
+//   k_sum_partials  FP64 sum of the block sums (fixed order: deterministic)
+//   k_iface_b       kappa = -div n, the CSF force sigma kappa delta(phi) n (Eq. fLS) and
+//                   the mean-free Boussinesq buoyancy, at cell centres
+//   k_momentum_ab2  RU = -div(uu) + div[mu_s(H)(grad u + grad u^T)] + div tau(mu_p(H)) + f
+//                   and u* = u + dt (w1 RU^n + w0 RU^{n-1})   (Eqs. ru, ab2)
+// One thread per cell; neighbours through the read-only cache.
+#include <cfloat>
+
+#include "evp_internal.cuh"
+#include "weno.cuh"
+
+namespace evp {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T sqr(T x) { return x * x; }
+
+template <typename T, bool REINIT>
+__global__ void __launch_bounds__(256) k_ls_stage(const Geo<T> g, const LsArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const size_t c0 = lin(g, i, j, k);
+    const T* P = a.phis;
+    T p[3][7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+        p[0][m] = ld_c(g, P, i + m - 3, j, k);
+        p[1][m] = ld_c(g, P, i, j + m - 3, k);
+        p[2][m] = ld_c(g, P, i, j, k + m - 3);
+    }
+    const T ih[3] = {g.idx, g.idy, g.idz};
+    T rhs;
+    if (!REINIT) {
+        // -u.grad(phi): upwind WENO5 per direction, velocity at the centre
+        const T uc = T(0.5) * (ld_uw(g, a.U, i - 1, j, k) + __ldg(a.U + c0));
+        const T vc = T(0.5) * (ld_v(g, a.V, i, j - 1, k) + __ldg(a.V + c0));
+        const T wc = T(0.5) * (ld_uw(g, a.W, i, j, k - 1) + __ldg(a.W + c0));
+        const T vel[3] = {uc, vc, wc};
+        T adv = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const T s = fabs(vel[d]) * ih[d];
+            if (vel[d] > T(0))
+                adv += upwind_term(s, p[d][0], p[d][1], p[d][2], p[d][3], p[d][4], p[d][5]);
+            else
+                adv += upwind_term(s, p[d][6], p[d][5], p[d][4], p[d][3], p[d][2], p[d][1]);
+        }
+        rhs = -adv;
+    } else {
+        const T f0 = __ldg(a.phi0 + c0);
+        const T sg = f0 / sqrt(f0 * f0 + a.h * a.h);
+        T sum = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            // left-biased (a) and right-biased (b) derivatives; the mirrored stencil
+            // gives the negated right-biased one
+            const T dl = upwind_term(ih[d], p[d][0], p[d][1], p[d][2], p[d][3], p[d][4], p[d][5]);
+            const T dr = -upwind_term(ih[d], p[d][6], p[d][5], p[d][4], p[d][3], p[d][2], p[d][1]);
+            const T pos = fmax(sqr(fmax(dl, T(0))), sqr(fmin(dr, T(0))));
+            const T neg = fmax(sqr(fmin(dl, T(0))), sqr(fmax(dr, T(0))));
+            sum += sg > T(0) ? pos : neg;
+        }
+        rhs = -sg * (sqrt(sum) - T(1));
+    }
+    // plain load: the third stage writes phi in place (each cell by its own thread)
+    const T pn = a.pt_a != T(0) ? a.phin[c0] : T(0);
+    a.out[c0] = a.pt_a * pn + a.pt_b * (p[0][3] + a.dt * rhs);
+}
+
+// H and the unit normal at cell centres; per-block FP64 sum of (1 - H)
+template <typename T>
+__global__ void __launch_bounds__(256) k_iface_a(const Geo<T> g, const IfaceArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    double part = 0.0;
+    if (i < g.nx && j < g.ny) {
+        const size_t c0 = lin(g, i, j, k);
+        const T ph = __ldg(a.phi + c0);
+        const T eps = a.eps;
+        T H;
+        if (ph < -eps) H = T(0);
+        else if (ph > eps) H = T(1);
+        else H = T(0.5) * (T(1) + ph / eps + sin(T(3.14159265358979323846) * ph / eps) * T(0.31830988618379067154));
+        a.H[c0] = H;
+        part = 1.0 - double(H);
+        const T gx = (ld_c(g, a.phi, i + 1, j, k) - ld_c(g, a.phi, i - 1, j, k)) * (T(0.5) * g.idx);
+        const T gy = (ld_c(g, a.phi, i, j + 1, k) - ld_c(g, a.phi, i, j - 1, k)) * (T(0.5) * g.idy);
+        const T gz = (ld_c(g, a.phi, i, j, k + 1) - ld_c(g, a.phi, i, j, k - 1)) * (T(0.5) * g.idz);
+        T mag = sqrt(gx * gx + gy * gy + gz * gz);
+        mag = mag > T(1e-12) ? mag : T(1e-12);
+        a.n[0][c0] = gx / mag;
+        a.n[1][c0] = gy / mag;
+        a.n[2][c0] = gz / mag;
+    }
+    // fixed-shape block reduction -> one partial per block
+    __shared__ double red[256];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    red[t] = part;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) red[t] += red[t + s];
+        __syncthreads();
+    }
+    if (t == 0) a.partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(256) k_sum_partials(const double* partials, int n, double scale, double* out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int q = threadIdx.x; q < n; q += 256) s += partials[q];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] * scale;
+}
+
+// CSF force sigma kappa delta(phi) n plus buoyancy (1 - H - mean(1 - H)) drho_g e_y
+template <typename T>
+__global__ void __launch_bounds__(256) k_iface_b(const Geo<T> g, const IfaceArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const size_t c0 = lin(g, i, j, k);
+    const T kap = -((ld_c(g, a.n[0], i + 1, j, k) - ld_c(g, a.n[0], i - 1, j, k)) * (T(0.5) * g.idx)
+                    + (ld_c(g, a.n[1], i, j + 1, k) - ld_c(g, a.n[1], i, j - 1, k)) * (T(0.5) * g.idy)
+                    + (ld_c(g, a.n[2], i, j, k + 1) - ld_c(g, a.n[2], i, j, k - 1)) * (T(0.5) * g.idz));
+    const T ph = __ldg(a.phi + c0);
+    const T eps = a.eps;
+    const T dl = fabs(ph) > eps ? T(0) : T(0.5) / eps * (T(1) + cos(T(3.14159265358979323846) * ph / eps));
+    const T s = a.sigma * kap * dl;
+    const T buoy = (T(1) - __ldg(a.H + c0)) * a.drho_g - T(*a.mean_1mH * double(a.drho_g));
+    a.f[0][c0] = s * __ldg(a.n[0] + c0);
+    a.f[1][c0] = s * __ldg(a.n[1] + c0) + buoy;
+    a.f[2][c0] = s * __ldg(a.n[2] + c0);
+}
+
+// tau component c at a centre from B^n with the mixture polymer viscosity mu_p(H)
+template <typename T, int MODEL>
+__device__ __forceinline__ T tau_mix(const Geo<T>& g, const MomAB2Args<T>& a, int c, int i, int j, int k) {
+    const size_t o = lin(g, wrap(i, g.nx), ycen(g, j), wrap(k, g.nz));
+    const T H = __ldg(a.H + o);
+    const T gm = (a.mu_p1 * H + a.mu_p2 * (T(1) - H)) * a.inv_lam;
+    const bool diag = (c == 0 || c == 3 || c == 5);
+    const T bc = __ldg(a.B[c] + o);
+    if (MODEL == EVP_FENE_P) {
+        const T tr = __ldg(a.B[0] + o) + __ldg(a.B[3] + o) + __ldg(a.B[5] + o);
+        const T F = a.L2 / (a.L2 - tr);
+        return gm * (F * bc - (diag ? a.a_fene : T(0)));
+    }
+    return gm * (bc - (diag ? T(1) : T(0)));
+}
+
+// average of tau_c over (0 or d1) x (0 or d2) around (i, j, k); offsets as in the RK3 kernel
+template <typename T, int MODEL>
+__device__ __forceinline__ T tau_e4(const Geo<T>& g, const MomAB2Args<T>& a, int c, int i, int j, int k, int di,
+                                    int dj, int dk) {
+    int a1i = 0, a1j = 0, a1k = 0, a2i = 0, a2j = 0, a2k = 0;
+    if (di) {
+        a1i = di;
+        if (dj) a2j = dj; else a2k = dk;
+    } else {
+        a1j = dj;
+        a2k = dk;
+    }
+    return T(0.25) * (tau_mix<T, MODEL>(g, a, c, i, j, k) + tau_mix<T, MODEL>(g, a, c, i + a2i, j + a2j, k + a2k)
+                      + tau_mix<T, MODEL>(g, a, c, i + a1i, j + a1j, k + a1k)
+                      + tau_mix<T, MODEL>(g, a, c, i + a1i + a2i, j + a1j + a2j, k + a1k + a2k));
+}
+
+template <typename T, int MODEL>
+__global__ void __launch_bounds__(256) k_momentum_ab2(const Geo<T> g, const MomAB2Args<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const size_t c0 = lin(g, i, j, k);
+    auto u = [&](int di, int dj, int dk) { return ld_uw(g, a.U, i + di, j + dj, k + dk); };
+    auto v = [&](int di, int dj, int dk) { return ld_v(g, a.V, i + di, j + dj, k + dk); };
+    auto w = [&](int di, int dj, int dk) { return ld_uw(g, a.W, i + di, j + dj, k + dk); };
+    auto mu = [&](int di, int dj, int dk) {
+        const T H = ld_c(g, a.H, i + di, j + dj, k + dk);
+        return a.mu_s1 * H + a.mu_s2 * (T(1) - H);
+    };
+    // viscosity averaged over the 4 centres (0 or d1) x (0 or d2), shifted by (si, sj, sk)
+    auto mue = [&](int si, int sj, int sk, int di, int dj, int dk) {
+        int a1i = 0, a1j = 0, a1k = 0, a2i = 0, a2j = 0, a2k = 0;
+        if (di) {
+            a1i = di;
+            if (dj) a2j = dj; else a2k = dk;
+        } else {
+            a1j = dj;
+            a2k = dk;
+        }
+        return T(0.25) * (mu(si, sj, sk) + mu(si + a2i, sj + a2j, sk + a2k) + mu(si + a1i, sj + a1j, sk + a1k)
+                          + mu(si + a1i + a2i, sj + a1j + a2j, sk + a1k + a2k));
+    };
+    const T h = T(0.5);
+    const T u0 = u(0, 0, 0), v0 = v(0, 0, 0), w0 = w(0, 0, 0);
+    const T ix = g.idx, iy = g.idy, iz = g.idz;
+
+    // ---- div(uu) (same discretisation as the RK3 predictor)
+    const T Ax = (sqr(h * (u0 + u(1, 0, 0))) - sqr(h * (u(-1, 0, 0) + u0))) * ix
+                 + (h * (u0 + u(0, 1, 0)) * h * (v0 + v(1, 0, 0)) - h * (u(0, -1, 0) + u0) * h * (v(0, -1, 0) + v(1, -1, 0))) * iy
+                 + (h * (u0 + u(0, 0, 1)) * h * (w0 + w(1, 0, 0)) - h * (u(0, 0, -1) + u0) * h * (w(0, 0, -1) + w(1, 0, -1))) * iz;
+    const T Ay = (h * (u0 + u(0, 1, 0)) * h * (v0 + v(1, 0, 0)) - h * (u(-1, 0, 0) + u(-1, 1, 0)) * h * (v(-1, 0, 0) + v0)) * ix
+                 + (sqr(h * (v0 + v(0, 1, 0))) - sqr(h * (v(0, -1, 0) + v0))) * iy
+                 + (h * (v0 + v(0, 0, 1)) * h * (w0 + w(0, 1, 0)) - h * (v(0, 0, -1) + v0) * h * (w(0, 0, -1) + w(0, 1, -1))) * iz;
+    const T Az = (h * (u0 + u(0, 0, 1)) * h * (w0 + w(1, 0, 0)) - h * (u(-1, 0, 0) + u(-1, 0, 1)) * h * (w(-1, 0, 0) + w0)) * ix
+                 + (h * (v0 + v(0, 0, 1)) * h * (w0 + w(0, 1, 0)) - h * (v(0, -1, 0) + v(0, -1, 1)) * h * (w(0, -1, 0) + w0)) * iy
+                 + (sqr(h * (w0 + w(0, 0, 1))) - sqr(h * (w(0, 0, -1) + w0))) * iz;
+
+    // ---- div[mu (grad u + grad u^T)], normal stresses at centres, shear at edges
+    auto sxx = [&](int di) { return T(2) * mu(di, 0, 0) * (u(di, 0, 0) - u(di - 1, 0, 0)) * ix; };
+    auto syy = [&](int dj) { return T(2) * mu(0, dj, 0) * (v(0, dj, 0) - v(0, dj - 1, 0)) * iy; };
+    auto szz = [&](int dk) { return T(2) * mu(0, 0, dk) * (w(0, 0, dk) - w(0, 0, dk - 1)) * iz; };
+    // shear stress at the xy edge (i+si+1/2, j+sj+1/2), etc.
+    auto sxy = [&](int si, int sj) {
+        return mue(si, sj, 0, 1, 1, 0) * ((u(si, sj + 1, 0) - u(si, sj, 0)) * iy + (v(si + 1, sj, 0) - v(si, sj, 0)) * ix);
+    };
+    auto sxz = [&](int si, int sk) {
+        return mue(si, 0, sk, 1, 0, 1) * ((u(si, 0, sk + 1) - u(si, 0, sk)) * iz + (w(si + 1, 0, sk) - w(si, 0, sk)) * ix);
+    };
+    auto syz = [&](int sj, int sk) {
+        return mue(0, sj, sk, 0, 1, 1) * ((v(0, sj, sk + 1) - v(0, sj, sk)) * iz + (w(0, sj + 1, sk) - w(0, sj, sk)) * iy);
+    };
+    const T Vx = (sxx(1) - sxx(0)) * ix + (sxy(0, 0) - sxy(0, -1)) * iy + (sxz(0, 0) - sxz(0, -1)) * iz;
+    const T Vy = (sxy(0, 0) - sxy(-1, 0)) * ix + (syy(1) - syy(0)) * iy + (syz(0, 0) - syz(0, -1)) * iz;
+    const T Vz = (sxz(0, 0) - sxz(-1, 0)) * ix + (syz(0, 0) - syz(-1, 0)) * iy + (szz(1) - szz(0)) * iz;
+
+    // ---- div tau^n with mu_p(H)
+    T dtx = T(0), dty = T(0), dtz = T(0);
+    if (MODEL != EVP_NEWTONIAN) {
+        dtx = (tau_mix<T, MODEL>(g, a, 0, i + 1, j, k) - tau_mix<T, MODEL>(g, a, 0, i, j, k)) * ix
+              + (tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, 1, 0) - tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, -1, 0)) * iy
+              + (tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, 1) - tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, -1)) * iz;
+        dty = (tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, 1, 0) - tau_e4<T, MODEL>(g, a, 1, i, j, k, -1, 1, 0)) * ix
+              + (tau_mix<T, MODEL>(g, a, 3, i, j + 1, k) - tau_mix<T, MODEL>(g, a, 3, i, j, k)) * iy
+              + (tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, 1) - tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, -1)) * iz;
+        dtz = (tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, 1) - tau_e4<T, MODEL>(g, a, 2, i, j, k, -1, 0, 1)) * ix
+              + (tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, 1) - tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, -1, 1)) * iy
+              + (tau_mix<T, MODEL>(g, a, 5, i, j, k + 1) - tau_mix<T, MODEL>(g, a, 5, i, j, k)) * iz;
+    }
+
+    // ---- interface force: mean of the two centres next to each face
+    const T Fx = h * (__ldg(a.f[0] + c0) + ld_c(g, a.f[0], i + 1, j, k));
+    const T Fy = h * (__ldg(a.f[1] + c0) + ld_c(g, a.f[1], i, j + 1, k));
+    const T Fz = h * (__ldg(a.f[2] + c0) + ld_c(g, a.f[2], i, j, k + 1));
+
+    const T Nx = -Ax + Vx + dtx + Fx;
+    const T Ny = -Ay + Vy + dty + Fy;
+    const T Nz = -Az + Vz + dtz + Fz;
+    T ux = a.w1dt * Nx, uy = a.w1dt * Ny, uz = a.w1dt * Nz;
+    if (a.read_hist) {
+        ux += a.w0dt * a.NH[0][c0];
+        uy += a.w0dt * a.NH[1][c0];
+        uz += a.w0dt * a.NH[2][c0];
+    }
+    a.Us[c0] = u0 + ux;
+    a.Vs[c0] = (g.walls && j == g.ny - 1) ? T(0) : v0 + uy;
+    a.Ws[c0] = w0 + uz;
+    a.NH[0][c0] = Nx;
+    a.NH[1][c0] = Ny;
+    a.NH[2][c0] = Nz;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_ls_stage(const Geo<T>& g, const LsArgs<T>& a, bool reinit, cudaStream_t st,
+                            const TimingHook& th) {
+    dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    th.b(K_LEVELSET);
+    if (reinit)
+        k_ls_stage<T, true><<<grid, block, 0, st>>>(g, a);
+    else
+        k_ls_stage<T, false><<<grid, block, 0, st>>>(g, a);
+    th.e(K_LEVELSET);
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t iface_partials(const Geo<T>& g) {
+    return (size_t)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.nz;
+}
+
+template <typename T>
+cudaError_t launch_interface(const Geo<T>& g, const IfaceArgs<T>& a, cudaStream_t st, const TimingHook& th) {
+    dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    const int np = (int)iface_partials(g);
+    th.b(K_INTERFACE);
+    k_iface_a<T><<<grid, block, 0, st>>>(g, a);
+    k_sum_partials<<<1, 256, 0, st>>>(a.partials, np, 1.0 / (double(g.nx) * g.ny * g.nz), a.mean_1mH);
+    k_iface_b<T><<<grid, block, 0, st>>>(g, a);
+    th.e(K_INTERFACE);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>& a, cudaStream_t st,
+                                const TimingHook& th) {
+    dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    th.b(K_MOMENTUM);
+    switch (model) {
+        case EVP_NEWTONIAN: k_momentum_ab2<T, EVP_NEWTONIAN><<<grid, block, 0, st>>>(g, a); break;
+        case EVP_OLDROYD_B: k_momentum_ab2<T, EVP_OLDROYD_B><<<grid, block, 0, st>>>(g, a); break;
+        case EVP_FENE_P: k_momentum_ab2<T, EVP_FENE_P><<<grid, block, 0, st>>>(g, a); break;
+        case EVP_SARAMITO: k_momentum_ab2<T, EVP_SARAMITO><<<grid, block, 0, st>>>(g, a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    th.e(K_MOMENTUM);
+    return cudaGetLastError();
+}
+
+#define EVP_INST(T)                                                                                           \
+    template cudaError_t launch_ls_stage<T>(const Geo<T>&, const LsArgs<T>&, bool, cudaStream_t,              \
+                                            const TimingHook&);                                               \
+    template size_t iface_partials<T>(const Geo<T>&);                                                         \
+    template cudaError_t launch_interface<T>(const Geo<T>&, const IfaceArgs<T>&, cudaStream_t,                \
+                                             const TimingHook&);                                              \
+    template cudaError_t launch_momentum_ab2<T>(const Geo<T>&, int, const MomAB2Args<T>&, cudaStream_t,       \
+                                                const TimingHook&);
+EVP_INST(float)
+EVP_INST(double)
+#undef EVP_INST
+
+}  // namespace evp

@@ -1,0 +1,83 @@
+"""Parity of the two-phase AB2 step (level set S9 + AB2 S10, Secs. 3.2.1-3.2.2)
+through the C ABI against the oracle's ab2_step: level set advection (TVD-RK3 +
+WENO5), re-distancing, H / normals / curvature / CSF + buoyancy, mixture
+viscosities, AB2 stress and momentum, projection with dt."""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import levelset as ls
+from oracle.ab2 import TwoPhase, ab2_step
+from paper_1803_09563_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(got, ref):
+    return float(np.abs(np.asarray(got, dtype=np.float64) - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def drop_case(evp, precision, n=16, walls=False, model='saramito', steps=3, reinit_every=2):
+    nx, ny, nz = n, 2 * n, n
+    L = 1.5
+    geo = inputs.geometry(nx, ny, nz, L, 2 * L, L, walls)
+    g = oracle.Grid(nx, ny, nz, L, 2 * L, L, walls)
+    c = (0.75, 0.9 - (L if walls else 0.0), 0.75)
+    phi = inputs.sphere_distance(geo, c, 0.35)
+    tau_y = 0.02
+    tp = TwoPhase(model, Re=35.0, Wi=1.0, beta=0.5, tau_y=tau_y, mu_ratio=1.0, L2=50.0, sigma=0.1,
+                  drho_g=1.0, reinit_every=reinit_every, reinit_iters=2)
+    prm = evp.make_params(Re=35.0, Wi=1.0, beta=0.5, Bi=tau_y, bi_def=1, L2=50.0, precision=precision,
+                          integrator=evp.EVP_AB2, mu_ratio=1.0, ls_eps_cells=1.5, sigma=0.1, drho_g=1.0,
+                          reinit_every=reinit_every, reinit_iters=2)
+    sim = evp.Simulation(evp.make_grid(nx, ny, nz, L, 2 * L, L, walls), model, prm)
+    sim.set(evp.EVP_PHI, phi)
+    st = oracle.State.rest(g)
+    if precision == evp.EVP_FP32:
+        phi = phi.astype(np.float32).astype(np.float64)
+    dt = 2e-2
+    for it in range(steps):
+        sim.step(dt)
+        st, phi = ab2_step(st, phi, dt, g, tp, it)
+    code, bits, maxdiv = sim.sync()
+    return sim, st, phi, g, maxdiv
+
+
+def fields(sim, evp):
+    return ([sim.get(f) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P, evp.EVP_PHI)]
+            + [sim.get(evp.EVP_BXX + c) for c in range(6)])
+
+
+def ref_fields(st, phi):
+    return [st.U, st.V, st.W, st.p, phi] + list(st.B)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("model", ['saramito', 'oldroyd_b'])
+def test_ab2_drop_steps_fp64(evp, walls, model):
+    sim, st, phi, g, maxdiv = drop_case(evp, evp.EVP_FP64, walls=walls, model=model)
+    names = ['u', 'v', 'w', 'p', 'phi', 'Bxx', 'Bxy', 'Bxz', 'Byy', 'Byz', 'Bzz']
+    for name, got, ref in zip(names, fields(sim, evp), ref_fields(st, phi)):
+        assert rel(got, ref) < 1e-10, (name, rel(got, ref))
+    assert maxdiv < 1e-10
+
+
+def test_ab2_drop_steps_fp32(evp):
+    sim, st, phi, g, maxdiv = drop_case(evp, evp.EVP_FP32, steps=2)
+    names = ['u', 'v', 'w', 'p', 'phi', 'Bxx', 'Bxy', 'Bxz', 'Byy', 'Byz', 'Bzz']
+    for name, got, ref in zip(names, fields(sim, evp), ref_fields(st, phi)):
+        if name == 'p':
+            continue
+        assert rel(got, ref) < 1e-5, (name, rel(got, ref))
+
+
+def test_ab2_rejects_rk3_only_calls(evp):
+    prm = evp.make_params(Re=35.0, Wi=1.0, beta=0.5, integrator=evp.EVP_AB2, sigma=0.1, drho_g=1.0)
+    sim = evp.Simulation(evp.make_grid(16, 16, 16, 1.0, 1.0, 1.0), 'oldroyd_b', prm)
+    with pytest.raises(evp.EvpError) as e:
+        evp.evp_substep(sim.handle, 1e-3, 0)
+    assert e.value.code == evp.EVP_ERR_STATE
+    with pytest.raises(evp.EvpError):
+        evp.Simulation(evp.make_grid(16, 16, 16, 1.0, 1.0, 1.0), 'oldroyd_b',
+                       evp.make_params(Re=35.0, integrator=evp.EVP_AB2, dpdx=1.0))
