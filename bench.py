@@ -148,6 +148,22 @@ def ncu_traffic(kernel):
     return None
 
 
+def max_over_ranks(x, world, device):
+    """Max of a scalar over all ranks (the slowest replica sets the job time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells, steps, world, seconds):
+    """Whole-job Mcell-steps/s: every replica advances ``cells`` for ``steps`` steps."""
+    return cells * steps * world / seconds / 1e6
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_1803_09563_gb300 import evp
@@ -170,13 +186,8 @@ def run_gpu(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device='cuda')
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(x):
+        return max_over_ranks(x, world, 'cuda')
 
     # ---------------- FP32-served: timed region
     sim = make(evp.EVP_FP32)
@@ -203,8 +214,8 @@ def run_gpu(args, rank, world, local_rank):
     ktimes = evp.evp_kernel_times(sim.handle)
     evp.evp_kernel_timing(sim.handle, False)
     code, bits, maxdiv = sim.sync(raise_on_error=False)
-    total_ms = max_over_ranks(total_ms)
-    value = N * args.steps * world / (total_ms * 1e-3) / 1e6
+    total_ms = max_ranks(total_ms)
+    value = job_rate(N, args.steps, world, total_ms * 1e-3)
     launches = int(sum(c for _, c in ktimes.values()))
 
     # roofline of the dominant kernel (largest share of device time)
@@ -241,8 +252,8 @@ def run_gpu(args, rank, world, local_rank):
         for f, h in zip(fields_io, host):
             evp.evp_get_field(sim.handle, f, h.numpy())
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = N * e2e_steps * world / e2e_s / 1e6
+    e2e_s = max_ranks(time.perf_counter() - t0)
+    e2e_value = job_rate(N, e2e_steps, world, e2e_s)
     io_bytes = len(fields_io) * N * 4
     fp32_fields = [sim.get(f) for f in fields_io]
     sim.close()
@@ -260,8 +271,8 @@ def run_gpu(args, rank, world, local_rank):
         sim64.step(w['dt'])
     e1.record(stream)
     stream.synchronize()
-    ms64 = max_over_ranks(e0.elapsed_time(e1))
-    value64 = N * n64 * world / (ms64 * 1e-3) / 1e6
+    ms64 = max_ranks(e0.elapsed_time(e1))
+    value64 = job_rate(N, n64, world, ms64 * 1e-3)
     # accuracy of FP32-served against FP64 plain after the same number of steps
     steps_done = args.warmup + args.steps + e2e_steps
     sim64.close()
