@@ -77,9 +77,13 @@ __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <typename T, int MODEL>
+// MODE: 0 = right-hand side only, 1 = update without history read (first RK3
+// substep / first AB2 step), 2 = update reading and writing the history,
+// 3 = update reading the history without writing it (last RK3 substep)
+template <typename T, int MODEL, int MODE>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chunk) {
+    constexpr bool RHS_ONLY = MODE == 0, READ_H = MODE >= 2, WRITE_H = MODE == 1 || MODE == 2;
     extern __shared__ __align__(16) unsigned char smraw[];
     StressSmem<T>& sm = *reinterpret_cast<StressSmem<T>*>(smraw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -185,7 +189,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     // RK3 history of this thread's cell in plane kk -> staging buffer kk & 1
     const size_t cell0 = (size_t)j * g.nx + i;
     auto fetch_hist = [&](int kk) {
-        if (!a.read_hist || !active || kk >= k1) return;
+        if (!READ_H || !active || kk >= k1) return;
 #pragma unroll
         for (int c = 0; c < 6; ++c) cp_async(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0);
     };
@@ -292,19 +296,19 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             const bool diag = (c == 0 || c == 3 || c == 5);
             const T src = ((diag ? av : T(0)) - F * w[c][3]) * inv_lam;
             const T rt = src + ucd - adv;
-            if (active) {
-                if (a.rhs_only) {
-                    a.RT[c][cell] = rt;
-                } else {
-                    T inc = dtz * rt;
-                    if (a.read_hist) inc += dtx * sm.H[k & 1][c][tid];
-                    bn[c] = w[c][3] + inc;
+            if (RHS_ONLY) {
+                if (active) a.RT[c][cell] = rt;
+            } else {
+                T inc = dtz * rt;
+                if (READ_H) inc += dtx * sm.H[k & 1][c][tid];
+                bn[c] = w[c][3] + inc;
+                if (active) {
                     a.Bn[c][cell] = bn[c];
-                    if (a.write_hist) a.RT[c][cell] = rt;
+                    if (WRITE_H) a.RT[c][cell] = rt;
                 }
             }
         }
-        if (active && !a.rhs_only) {
+        if (active && !RHS_ONLY) {
             // a non-finite component makes the sum non-finite
             if (!isfinite(bn[0] + bn[1] + bn[2] + bn[3] + bn[4] + bn[5])) bits |= EVP_BIT_NONFINITE;
             if (MODEL == EVP_FENE_P && bn[0] + bn[3] + bn[5] >= kL2) bits |= EVP_BIT_TRACE_LIMIT;
@@ -342,20 +346,27 @@ cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArg
     dim3 block(TX, TY, 1);
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
     const size_t smem = sizeof(StressSmem<T>);
+    const int mode = a.rhs_only ? 0 : (!a.read_hist ? 1 : (a.write_hist ? 2 : 3));
     th.b(K_STRESS);
-    switch (mc.model) {
-        case EVP_OLDROYD_B:
-            cudaFuncSetAttribute(k_stress<T, EVP_OLDROYD_B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_stress<T, EVP_OLDROYD_B><<<grid, block, smem, st>>>(g, mc, a, kz);
-            break;
-        case EVP_FENE_P:
-            cudaFuncSetAttribute(k_stress<T, EVP_FENE_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_stress<T, EVP_FENE_P><<<grid, block, smem, st>>>(g, mc, a, kz);
-            break;
-        case EVP_SARAMITO:
-            cudaFuncSetAttribute(k_stress<T, EVP_SARAMITO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_stress<T, EVP_SARAMITO><<<grid, block, smem, st>>>(g, mc, a, kz);
-            break;
+    switch (mc.model * 4 + mode) {
+#define EVP_LAUNCH_STRESS(M, MD)                                                                              \
+    case M * 4 + MD:                                                                                          \
+        cudaFuncSetAttribute(k_stress<T, M, MD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+        k_stress<T, M, MD><<<grid, block, smem, st>>>(g, mc, a, kz);                                          \
+        break;
+        EVP_LAUNCH_STRESS(EVP_OLDROYD_B, 0)
+        EVP_LAUNCH_STRESS(EVP_OLDROYD_B, 1)
+        EVP_LAUNCH_STRESS(EVP_OLDROYD_B, 2)
+        EVP_LAUNCH_STRESS(EVP_OLDROYD_B, 3)
+        EVP_LAUNCH_STRESS(EVP_FENE_P, 0)
+        EVP_LAUNCH_STRESS(EVP_FENE_P, 1)
+        EVP_LAUNCH_STRESS(EVP_FENE_P, 2)
+        EVP_LAUNCH_STRESS(EVP_FENE_P, 3)
+        EVP_LAUNCH_STRESS(EVP_SARAMITO, 0)
+        EVP_LAUNCH_STRESS(EVP_SARAMITO, 1)
+        EVP_LAUNCH_STRESS(EVP_SARAMITO, 2)
+        EVP_LAUNCH_STRESS(EVP_SARAMITO, 3)
+#undef EVP_LAUNCH_STRESS
         default: return cudaErrorInvalidValue;
     }
     th.e(K_STRESS);
