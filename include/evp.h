@@ -146,6 +146,14 @@ int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device);
  * Poisson solve (Eq. NS-num2) and correction (Eq. NS-num3).  Asynchronous.   */
 int evp_step(evp_state* s, double dt);
 
+/* Replay evp_step from CUDA graphs (RK3 states): the first step for a given dt
+ * and buffer parity is captured on the state's stream and instantiated, later
+ * steps launch the graph, cutting the per-step host cost of the 24 kernel
+ * launches (small grids, many concurrent simulations).  Not while kernel timing
+ * is on.  If the stream cannot be captured the state falls back to direct
+ * launches.  EVP_ERR_STATE for AB2 states.  Off by default.                    */
+int evp_set_graph(evp_state* s, int enable);
+
 /* With integrator EVP_AB2, evp_step is one two-phase AB2 step of size dt
  * (level set, re-distancing when due, interface force, B and u updates,
  * projection with dt); steps are counted from evp_init.                       */

@@ -106,6 +106,15 @@ struct evp_state_s {
     double* mean_1mH;
     long long nstep;     // AB2 steps taken
     int cu, cb;          // current velocity / B buffer
+    // CUDA-graph replay of evp_step: one executable graph per parity of the B
+    // buffer at the start of the step (the three substeps flip it each time)
+    bool use_graph;
+    struct StepGraph {
+        bool valid;
+        double dt;
+        int cb_after;
+        cudaGraphExec_t exec;
+    } graphs[2];
     ModelConst mc;
     // timing
     bool timing;
@@ -714,6 +723,8 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
     s->prm = *params;
     s->fp32 = params->precision == EVP_FP32;
     s->elt = s->fp32 ? 4 : 8;
+    s->use_graph = false;
+    for (auto& gr : s->graphs) gr.valid = false;
     s->N = (size_t)grid->nx * grid->ny * grid->nz;
     s->nxh = grid->nx / 2 + 1;
     s->timing = false;
@@ -785,6 +796,8 @@ int evp_destroy(evp_state* s) {
         cudaEventDestroy(p.b);
     }
     for (auto e : s->ev_free) cudaEventDestroy(e);
+    for (auto& gr : s->graphs)
+        if (gr.valid) cudaGraphExecDestroy(gr.exec);
     if (s->own_arena && s->arena) cudaFree(s->arena);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     delete s;
@@ -826,10 +839,66 @@ int evp_substep(evp_state* s, double dt, int k) {
     return s->fp32 ? substep_t<float>(s, dt, k, false, false) : substep_t<double>(s, dt, k, false, false);
 }
 
-int evp_step(evp_state* s, double dt) {
+namespace {
+int rk3_step_direct(evp_state* s, double dt) {
+    for (int k = 0; k < 3; ++k) {
+        int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2, true) : substep_t<double>(s, dt, k, k == 2, true);
+        if (r) return r;
+    }
+    return EVP_OK;
+}
+
+// Replay (capturing on first use) the graph of one RK3 step for this dt and B parity.
+int rk3_step_graph(evp_state* s, double dt) {
+    auto& gr = s->graphs[s->cb];
+    if (!gr.valid || gr.dt != dt) {
+        if (gr.valid) {
+            cudaGraphExecDestroy(gr.exec);
+            gr.valid = false;
+        }
+        const int cu0 = s->cu, cb0 = s->cb;
+        cudaError_t eb = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
+        int r = EVP_OK;
+        cudaGraph_t graph = nullptr;
+        cudaError_t ec = eb;
+        if (eb == cudaSuccess) {
+            r = rk3_step_direct(s, dt);
+            ec = cudaStreamEndCapture(s->st, &graph);
+        }
+        const int cb_after = s->cb;
+        s->cu = cu0;
+        s->cb = cb0;
+        cudaError_t ei = cudaErrorUnknown;
+        if (r == EVP_OK && ec == cudaSuccess && graph) ei = cudaGraphInstantiate(&gr.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            // capture is not available on this stream: run the step directly from now on
+            cudaGetLastError();
+            s->use_graph = false;
+            return rk3_step_direct(s, dt);
+        }
+        gr.valid = true;
+        gr.dt = dt;
+        gr.cb_after = cb_after;
+    }
+    CK(cudaGraphLaunch(gr.exec, s->st));
+    s->cb = gr.cb_after;
+    return EVP_OK;
+}
+}  // namespace
+
+extern "C" int evp_set_graph(evp_state* s, int enable) {
+    if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (enable && s->ab2) return fail(EVP_ERR_STATE, "graph replay covers the RK3 step only");
+    s->use_graph = enable != 0;
+    return EVP_OK;
+}
+
+extern "C" int evp_step(evp_state* s, double dt) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
     if (s->ab2) return s->fp32 ? ab2_step_t<float>(s, dt) : ab2_step_t<double>(s, dt);
+    if (s->use_graph && !s->timing) return rk3_step_graph(s, dt);
     for (int k = 0; k < 3; ++k) {
         int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2, true) : substep_t<double>(s, dt, k, k == 2, true);
         if (r) return r;

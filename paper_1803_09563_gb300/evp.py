@@ -74,6 +74,7 @@ def load(path=None):
         'evp_set_field': (c_int, [c_void_p, c_int, c_void_p, c_int]),
         'evp_get_field': (c_int, [c_void_p, c_int, c_void_p, c_int]),
         'evp_step': (c_int, [c_void_p, c_double]),
+        'evp_set_graph': (c_int, [c_void_p, c_int]),
         'evp_substep': (c_int, [c_void_p, c_double, c_int]),
         'evp_project': (c_int, [c_void_p]),
         'evp_poisson_solve': (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -98,7 +99,8 @@ def exported_symbols():
     """Names declared in include/evp.h that the binding resolves."""
     return ['evp_state_bytes', 'evp_init', 'evp_destroy', 'evp_set_field', 'evp_get_field', 'evp_step',
             'evp_substep', 'evp_project', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_sync', 'evp_kernel_timing',
-            'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error', 'evp_poisson_solve_static']
+            'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error', 'evp_poisson_solve_static',
+            'evp_set_graph']
 
 
 def _check(code):
@@ -166,6 +168,10 @@ def evp_get_field(state, field, dst):
 
 def evp_step(state, dt):
     return _check(load().evp_step(state, float(dt)))
+
+
+def evp_set_graph(state, enable):
+    return _check(load().evp_set_graph(state, int(bool(enable))))
 
 
 def evp_substep(state, dt, k):
