@@ -317,12 +317,61 @@ def run_gpu(args, rank, world, local_rank):
     return line
 
 
+def run_serving(steps_scale=0.1):
+    """Serving mix: a seeded Poisson stream of 64 periodic Saramito requests, grids
+    from {32, 48, 64, 96, 128}^3, Wi in U[0.5, 4], Bi in U[0, 1], beta in U[0.3, 0.9],
+    random solenoidal velocity (|k| <= 4, max-norm 1), FP32, 120 GB budget, graph
+    replay.  Step counts are the mix's 100-1000 scaled by ``steps_scale``."""
+    from paper_1803_09563_gb300 import serve
+    lo, hi = max(1, int(100 * steps_scale)), max(2, int(1000 * steps_scale))
+    reqs = serve.mixed_requests(64, seed=3, steps=(lo, hi), rate=0.5)
+    prepared = {r.rid: serve.request_inputs(r) for r in reqs}      # client side, untimed
+    _, rep = serve.Server(budget_bytes=120 * 10 ** 9).run(reqs, prepared=prepared)
+    rep["steps_per_request"] = [lo, hi]
+    rep["workload"] = "serving_mix_64_requests_32-128^3_saramito_fp32"
+    return rep
+
+
+def run_small_grid():
+    """Single-phase Oldroyd-B Taylor-Green box 32^3 in FP64 (the 10-step parity
+    workload): per-step latency with direct launches and with graph replay."""
+    import torch
+    from paper_1803_09563_gb300 import evp, inputs
+    n, L = 32, 2 * np.pi
+    geo = inputs.geometry(n, n, n, L, L, L)
+    U, V, W = inputs.taylor_green(geo)
+    out = {}
+    for graph in (False, True):
+        stream = torch.cuda.Stream()
+        sim = evp.Simulation(evp.make_grid(n, n, n, L, L, L), 'oldroyd_b',
+                             evp.make_params(Re=1.0, Wi=1.0, beta=0.5, precision=evp.EVP_FP64),
+                             stream=stream.cuda_stream)
+        sim.set_state(U, V, W)
+        if graph:
+            evp.evp_set_graph(sim.handle, True)
+        for _ in range(4):
+            sim.step(1e-3)
+        sim.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = 200
+        e0.record(stream)
+        for _ in range(steps):
+            sim.step(1e-3)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out["graph" if graph else "direct"] = {"ms_per_step": ms, "Mcell_steps_per_s": n ** 3 / (ms * 1e-3) / 1e6}
+        sim.close()
+    out["workload"] = "oldroyd_b_taylor_green_32^3_fp64"
+    return out
+
+
 def run_cpu_baseline(args):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload:
-    one RK3 step of a 256 x 128 x 32 slab of the channel (z shortened 4x)."""
+    one RK3 step of a 256 x 128 x 64 slab of the channel (z halved)."""
     import oracle
     w = WORKLOAD
-    nz = 32
+    nz = 64
     geo, U, V, W = workload_inputs(w, nz=nz)
     g = oracle.Grid(w['nx'], w['ny'], nz, geo['lx'], geo['ly'], geo['lz'], True)
     prm = oracle.Params.from_groups(w['model'], w['Re'], w['Wi'], w['beta'], Bi=w['Bi'])
@@ -342,6 +391,7 @@ def main():
     ap.add_argument('--warmup', type=int, default=5)
     ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-extras', action='store_true', help='skip the serving-mix and small-grid sections')
     args = ap.parse_args()
     rank = int(os.environ.get('RANK', 0))
     world = int(os.environ.get('WORLD_SIZE', 1))
@@ -371,6 +421,9 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group('nccl', device_id=torch.device('cuda', local_rank))
     line = run_gpu(args, rank, world, local_rank)
+    if not args.no_extras:
+        line['serving'] = run_serving()
+        line['small_grid'] = run_small_grid()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line['cpu_baseline'] = run_cpu_baseline(args)

@@ -327,11 +327,12 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
 template <typename T>
 cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const MomentumArgs<T>& a,
                             cudaStream_t st, const TimingHook& th) {
+    // z chunks: about four waves of CTAs; small grids go down to one plane per CTA
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     const int per_sm = sizeof(T) == 4 ? 2 : 1;
     int chunks = (4 * 152 * per_sm + tiles - 1) / tiles;
-    int kz = (g.nz + chunks - 1) / chunks;
-    kz = kz < 8 ? 8 : kz;
+    chunks = chunks > g.nz ? g.nz : chunks;
+    const int kz = (g.nz + chunks - 1) / chunks;
     chunks = (g.nz + kz - 1) / kz;
     dim3 block(TX, TY, 1);
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);

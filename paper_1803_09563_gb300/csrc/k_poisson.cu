@@ -460,10 +460,12 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = nx / 2 + 1;
     const int NL = ny * nz;
     // ---- x pass: np complex lines (2 np real lines) per block
-    const int np = nx >= 2048 ? 1 : 2048 / nx;
+    // np complex lines per block, fewer on small grids so that every SM gets blocks
+    const int npairs = (NL + 1) / 2;
+    int np = nx >= 2048 ? 1 : 2048 / nx;
+    while (np > 1 && (npairs + np - 1) / np < 2 * 152) np /= 2;
     const int tx = nx >= 512 ? 128 : (nx >= 256 ? 64 : 32);
     dim3 bx(tx, 256 / tx);
-    const int npairs = (NL + 1) / 2;
     dim3 gx((npairs + np - 1) / np);
     const size_t smx = 2 * (size_t)np * nx * sizeof(C<T>);
     set_smem<T>((const void*)k_div_fftx<T>, smx);

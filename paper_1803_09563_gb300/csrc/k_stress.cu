@@ -337,11 +337,13 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
 template <typename T>
 cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a,
                           cudaStream_t st, const TimingHook& th) {
-    // z chunk: about four CTAs per SM slot-wave over the whole grid, at least 8 planes
+    // z chunks: about four waves of CTAs over all SMs (two CTAs per SM in FP32,
+    // one in FP64); small grids go down to one plane per CTA so that every SM works
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-    int chunks = (4 * 152 * 2 + tiles - 1) / tiles;
-    int kz = (g.nz + chunks - 1) / chunks;
-    kz = kz < 8 ? 8 : kz;
+    const int per_sm = sizeof(T) == 4 ? 2 : 1;
+    int chunks = (4 * 152 * per_sm + tiles - 1) / tiles;
+    chunks = chunks > g.nz ? g.nz : chunks;
+    const int kz = (g.nz + chunks - 1) / chunks;
     chunks = (g.nz + kz - 1) / kz;
     dim3 block(TX, TY, 1);
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
