@@ -103,7 +103,11 @@ typedef struct {
     double drho_g;      /* AB2: buoyancy, density difference times gravity               */
     int reinit_every;   /* AB2: re-distance every this many steps (0: never)            */
     int reinit_iters;   /* AB2: pseudo-time steps per re-distancing (dtau = dx/2)       */
-    double reserved[10];
+    int penalization;   /* RK3: volume-penalisation IBM for fixed obstacles (Sec. 3.3.2):
+                           u** = (1 - alpha) u* before each projection (Eq. forceAdded),
+                           alpha = solid fraction of the control volume around each
+                           velocity node, set with EVP_SOLID_X/Y/Z (zero at init)       */
+    double reserved[9];
 } evp_params;
 
 /* Field identifiers for evp_set_field / evp_get_field */
@@ -114,7 +118,9 @@ typedef enum {
     EVP_NH_X = 16,  /* ... EVP_NH_X+2: RK3 history of -div(uu)+viscous+force     */
     EVP_PSI = 19,   /* last projection variable psi (read only)                  */
     EVP_PHI = 20,   /* AB2 two-phase states: level set phi at cell centres       */
-    EVP_NFIELDS = 21
+    EVP_SOLID_X = 21, EVP_SOLID_Y = 22, EVP_SOLID_Z = 23,
+                    /* penalization states: solid fractions alpha at u, v, w nodes */
+    EVP_NFIELDS = 24
 } evp_field;
 
 typedef struct evp_state_s evp_state;

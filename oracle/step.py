@@ -65,8 +65,13 @@ class State:
                      self.t, self.nstep, cp(self.psi))
 
 
-def rk3_substep(s, k, dt, g, prm, force=None):
-    """Substep k (0-based index into Eq. RK) of the RK3 scheme; returns a new State."""
+def rk3_substep(s, k, dt, g, prm, force=None, solid=None):
+    """Substep k (0-based index into Eq. RK) of the RK3 scheme; returns a new State.
+
+    ``solid`` (optional triple of face arrays alpha) switches on the volume-penalisation
+    IBM for fixed obstacles (Sec. 3.3.2, Eqs. Vol, forceAdded): the predicted
+    velocity becomes u** = (1 - alpha) u* before the projection, alpha being the
+    solid volume fraction of the control volume around each velocity node."""
     alpha, zeta, xi = RK3_ALPHA[k], RK3_ZETA[k], RK3_XI[k]
     has_stress = prm.model != 'newtonian'
     # stress update, Eq. rk3tau with RT of Eq. RK-rt
@@ -96,6 +101,8 @@ def rk3_substep(s, k, dt, g, prm, force=None):
         if has_stress:
             inc = inc + alpha * (dtn[d] + dto[d])
         star.append(vel[d] + dt * inc)
+    if solid is not None:
+        star = [(1.0 - solid[d]) * star[d] for d in range(3)]
     if g.walls:
         star[1][:, g.ny - 1, :] = 0.0
     # projection, Eqs. NS-num2 and NS-num3
@@ -104,9 +111,9 @@ def rk3_substep(s, k, dt, g, prm, force=None):
                  t=s.t + (alpha * 2.0) * dt, nstep=s.nstep, psi=psi)
 
 
-def rk3_step(s, dt, g, prm, force=None):
-    """One full RK3 step (three substeps)."""
+def rk3_step(s, dt, g, prm, force=None, solid=None):
+    """One full RK3 step (three substeps); ``solid`` as in rk3_substep."""
     for k in range(3):
-        s = rk3_substep(s, k, dt, g, prm, force)
+        s = rk3_substep(s, k, dt, g, prm, force, solid)
     s.nstep += 1
     return s

@@ -102,6 +102,7 @@ struct evp_state_s {
     void* HF;
     void* NRM[3];
     void* FC[3];
+    void* SOL[3];        // penalization: solid fractions at the velocity nodes
     double* partials;
     double* mean_1mH;
     long long nstep;     // AB2 steps taken
@@ -199,6 +200,7 @@ int validate(const evp_grid* g, evp_model model, const evp_params* p) {
     if (p->precision != EVP_FP64 && p->precision != EVP_FP32) return fail(EVP_ERR_ARG, "bad precision");
     if (p->integrator != EVP_RK3 && p->integrator != EVP_AB2) return fail(EVP_ERR_ARG, "unknown integrator");
     if (p->integrator == EVP_AB2) {
+        if (p->penalization) return fail(EVP_ERR_ARG, "volume penalisation is part of the RK3 step only");
         if (p->dpdx != 0.0 || p->abc_amp != 0.0)
             return fail(EVP_ERR_ARG, "the AB2 two-phase step takes no dpdx or ABC forcing");
         if (!(p->mu_ratio > 0) || !(p->ls_eps_cells > 0) || !(p->sigma >= 0) || p->reinit_every < 0 ||
@@ -259,6 +261,9 @@ size_t plan(evp_state* s, char* base) {
         for (int q = 0; q < 12; ++q) ls[q] = P(N * e);   // phi, phi0, phiA, phiB, H, n(3), f(3), spare
     const size_t nparts = (size_t)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.nz;
     void* parts = ab2 ? P(nparts * sizeof(double)) : nullptr;
+    void* sol[3] = {nullptr, nullptr, nullptr};
+    if (s->prm.penalization)
+        for (int q = 0; q < 3; ++q) sol[q] = P(N * e);
     void* mean = ab2 ? P(sizeof(double)) : nullptr;
     void* st = P(sizeof(unsigned));
     void* md = P(sizeof(unsigned long long));
@@ -281,6 +286,7 @@ size_t plan(evp_state* s, char* base) {
             s->FC[q] = ls[8 + q];
         }
         s->partials = static_cast<double*>(parts);
+        for (int q = 0; q < 3; ++q) s->SOL[q] = sol[q];
         s->mean_1mH = static_cast<double*>(mean);
     }
     return L.total;
@@ -505,6 +511,7 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
         a.dpdx = T(s->prm.dpdx);
         a.abc_amp = T(s->prm.abc_amp);
         a.trig = s->prm.abc_amp != 0.0 ? static_cast<const T*>(s->trig) : nullptr;
+        for (int q = 0; q < 3; ++q) a.solid[q] = static_cast<const T*>(s->SOL[q]);
         cudaError_t e = launch_momentum<T>(g, s->mc, a, s->st, th);
         if (e != cudaSuccess) return cuda_fail(e, "momentum kernel");
     }
@@ -655,6 +662,7 @@ void* field_ptr(evp_state* s, int f) {
     if (f >= EVP_NH_X && f < EVP_NH_X + 3) return s->NH[f - EVP_NH_X];
     if (f == EVP_PSI) return s->PSI;
     if (f == EVP_PHI) return s->ab2 ? s->PHI : nullptr;
+    if (f >= EVP_SOLID_X && f <= EVP_SOLID_Z) return s->SOL[f - EVP_SOLID_X];
     return nullptr;
 }
 
@@ -679,6 +687,8 @@ int init_fields(evp_state* s) {
     for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(s->NH[c], 0, N * sizeof(T), s->st));
     CK(cudaMemsetAsync(s->P, 0, N * sizeof(T), s->st));
     CK(cudaMemsetAsync(s->PSI, 0, N * sizeof(T), s->st));
+    for (int q = 0; q < 3; ++q)
+        if (s->SOL[q]) CK(cudaMemsetAsync(s->SOL[q], 0, N * sizeof(T), s->st));
     if (s->ab2) {
         void* z[] = {s->PHI, s->PHI0, s->PHIA, s->PHIB, s->HF, s->NRM[0], s->NRM[1], s->NRM[2],
                      s->FC[0], s->FC[1], s->FC[2]};

@@ -125,6 +125,7 @@ struct MomentumArgs {
     int read_hist, write_hist, has_stress;
     T dpdx, abc_amp;
     const T* trig;     // ABC force tables: sin/cos of k x_i, k y_j, k z_k (6 arrays)
+    const T* solid[3]; // volume penalisation: solid fractions at u, v, w nodes (null: off)
 };
 
 template <typename T>

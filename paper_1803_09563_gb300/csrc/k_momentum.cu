@@ -304,9 +304,16 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         }
         if (active) {
             const size_t c0 = (size_t)k * plane + (size_t)j * g.nx + i;
-            a.Us[c0] = u0 + a.dt * ix;
-            a.Vs[c0] = (g.walls && j == g.ny - 1) ? T(0) : v0 + a.dt * iy;
-            a.Ws[c0] = w0 + a.dt * iz;
+            T us = u0 + a.dt * ix, vs = v0 + a.dt * iy, ws = w0 + a.dt * iz;
+            if (a.solid[0]) {
+                // volume penalisation of fixed obstacles, Eq. forceAdded
+                us *= T(1) - __ldg(a.solid[0] + c0);
+                vs *= T(1) - __ldg(a.solid[1] + c0);
+                ws *= T(1) - __ldg(a.solid[2] + c0);
+            }
+            a.Us[c0] = us;
+            a.Vs[c0] = (g.walls && j == g.ny - 1) ? T(0) : vs;
+            a.Ws[c0] = ws;
             if (a.write_hist) {
                 a.NH[0][c0] = Nx;
                 a.NH[1][c0] = Ny;

@@ -32,6 +32,7 @@ EVP_RT_XX = 10
 EVP_NH_X = 16
 EVP_PSI = 19
 EVP_PHI = 20
+EVP_SOLID_X, EVP_SOLID_Y, EVP_SOLID_Z = 21, 22, 23
 
 
 class evp_grid(ctypes.Structure):
@@ -44,7 +45,7 @@ class evp_params(ctypes.Structure):
                 ('bi_def', c_int), ('dpdx', c_double), ('abc_amp', c_double), ('abc_k', c_double),
                 ('precision', c_int), ('integrator', c_int), ('mu_ratio', c_double), ('ls_eps_cells', c_double),
                 ('sigma', c_double), ('drho_g', c_double), ('reinit_every', c_int), ('reinit_iters', c_int),
-                ('reserved', c_double * 10)]
+                ('penalization', c_int), ('reserved', c_double * 9)]
 
 
 class EvpError(RuntimeError):
@@ -131,13 +132,14 @@ def make_grid(nx, ny, nz, lx, ly, lz, walls_y=False):
 
 def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_amp=0.0, abc_k=0.0,
                 precision=EVP_FP64, integrator=EVP_RK3, mu_ratio=1.0, ls_eps_cells=1.5, sigma=0.0, drho_g=0.0,
-                reinit_every=10, reinit_iters=3):
+                reinit_every=10, reinit_iters=3, penalization=0):
     p = evp_params()
     p.Re, p.Wi, p.beta, p.Bi, p.L2 = float(Re), float(Wi), float(beta), float(Bi), float(L2)
     p.bi_def, p.dpdx, p.abc_amp, p.abc_k = int(bi_def), float(dpdx), float(abc_amp), float(abc_k)
     p.precision, p.integrator = int(precision), int(integrator)
     p.mu_ratio, p.ls_eps_cells, p.sigma, p.drho_g = float(mu_ratio), float(ls_eps_cells), float(sigma), float(drho_g)
     p.reinit_every, p.reinit_iters = int(reinit_every), int(reinit_iters)
+    p.penalization = int(penalization)
     return p
 
 

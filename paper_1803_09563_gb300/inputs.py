@@ -173,3 +173,28 @@ def random_conformation(geo, seed, amp=0.2):
         f /= 3.0
         B.append((1.0 if diag else 0.0) + amp * (0.5 if not diag else 1.0) * f)
     return B
+
+
+def solid_fractions(geo, inside, samples=4):
+    """Solid volume fraction of the control volume around every u, v and w node
+    (the cell shifted by half a cell along that component's axis), by sub-sampling
+    each control volume on a samples^3 lattice.  ``inside(x, y, z)`` is a
+    vectorised predicate of the solid region.  Returns (ax, ay, az)."""
+    nx, ny, nz, dx, dy, dz, y0 = _axes(geo)
+    off = (np.arange(samples) + 0.5) / samples - 0.5          # sub-cell offsets in cell units
+    out = []
+    for shift in ((1.0, 0.5, 0.5), (0.5, 1.0, 0.5), (0.5, 0.5, 1.0)):
+        # node positions: face of component d, centres in the other two directions
+        xs = (np.arange(nx) + shift[0]) * dx
+        ys = y0 + (np.arange(ny) + shift[1]) * dy
+        zs = (np.arange(nz) + shift[2]) * dz
+        acc = np.zeros((nz, ny, nx))
+        for ox in off:
+            for oy in off:
+                for oz in off:
+                    X = (xs + ox * dx)[None, None, :]
+                    Y = (ys + oy * dy)[None, :, None]
+                    Z = (zs + oz * dz)[:, None, None]
+                    acc += inside(X + 0 * Y + 0 * Z, Y + 0 * X + 0 * Z, Z + 0 * X + 0 * Y)
+        out.append(acc / samples ** 3)
+    return tuple(out)

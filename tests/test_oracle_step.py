@@ -96,3 +96,44 @@ def test_rest_state_with_identity_conformation_stays_at_rest():
         assert np.abs(s.U).max() == 0.0 and np.abs(s.p).max() == 0.0
         for c, b in enumerate(s.B):
             assert np.abs(b - (1.0 if c in (0, 3, 5) else 0.0)).max() < 1e-15
+
+
+def test_volume_penalisation_limits():
+    """Eq. forceAdded: alpha = 0 leaves the step unchanged (bitwise); alpha = 1 on
+    every face gives u** = 0 before the projection, hence u = 0 after it; and a
+    fixed solid block in a driven channel keeps the velocity inside it small
+    compared with the bulk flow."""
+    g, s = c1_state()
+    prm = oracle.Params.from_groups('oldroyd_b', 1.0, 1.0, 0.5)
+    zero = (g.zeros(), g.zeros(), g.zeros())
+    a = oracle.rk3_step(s.copy(), 1e-3, g, prm)
+    b = oracle.rk3_step(s.copy(), 1e-3, g, prm, solid=zero)
+    for x, y in zip([a.U, a.V, a.W, a.p] + a.B, [b.U, b.V, b.W, b.p] + b.B):
+        np.testing.assert_array_equal(x, y)
+    one = tuple(np.ones(g.shape) for _ in range(3))
+    c = oracle.rk3_substep(s.copy(), 0, 1e-3, g, prm, solid=one)
+    assert max(np.abs(c.U).max(), np.abs(c.V).max(), np.abs(c.W).max()) == 0.0
+    # channel with a solid block in its middle
+    geo = inputs.geometry(16, 16, 8, 4.0, 2.0, 2.0, True)
+    gc = oracle.Grid(16, 16, 8, 4.0, 2.0, 2.0, True)
+    block = lambda x, y, z: ((np.abs(x - 2.0) < 0.5) & (np.abs(y) < 0.5)).astype(float)
+    al = inputs.solid_fractions(geo, block)
+    U, V, W = inputs.poiseuille(geo)
+    st = oracle.State.rest(gc, U, V, W)
+    pr = oracle.Params.from_groups('newtonian', 10.0, 1.0, 1.0)
+    for _ in range(40):
+        st = oracle.rk3_step(st, 5e-3, gc, pr, (0.2, 0.0, 0.0), al)
+    solid = al[0] > 0.99
+    assert np.abs(st.U[solid]).max() < 0.05 * np.abs(st.U).max()
+    assert np.abs(oracle.divergence(st.U, st.V, st.W, gc)).max() < 1e-12
+
+
+def test_solid_fractions_of_a_block():
+    """The sub-sampled fractions integrate to the block's volume and are exactly
+    0 / 1 away from its surface."""
+    geo = inputs.geometry(16, 16, 16, 2.0, 2.0, 2.0)
+    block = lambda x, y, z: ((np.abs(x - 1.0) < 0.4) & (np.abs(y - 1.0) < 0.3) & (np.abs(z - 1.0) < 0.5)).astype(float)
+    for a in inputs.solid_fractions(geo, block, samples=8):
+        vol = a.sum() * (2.0 / 16) ** 3
+        assert abs(vol - 0.8 * 0.6 * 1.0) < 0.02
+        assert set(np.unique(a[(a > 0) & (a < 1)]).round(6)) <= set((np.arange(1, 512) / 512).round(6))
