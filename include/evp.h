@@ -103,11 +103,15 @@ typedef struct {
     double drho_g;      /* AB2: buoyancy, density difference times gravity               */
     int reinit_every;   /* AB2: re-distance every this many steps (0: never)            */
     int reinit_iters;   /* AB2: pseudo-time steps per re-distancing (dtau = dx/2)       */
+    double rho_ratio;   /* AB2: 0 = Boussinesq drop (drho_g); > 0 = drop / outer density
+                           ratio, solved with the constant-coefficient splitting of
+                           Eqs. poisson-LS and projection-LS, rho_0 = the smaller density */
+    double gravity;     /* AB2 with rho_ratio > 0: gravity g along -y                   */
     int penalization;   /* RK3: volume-penalisation IBM for fixed obstacles (Sec. 3.3.2):
                            u** = (1 - alpha) u* before each projection (Eq. forceAdded),
                            alpha = solid fraction of the control volume around each
                            velocity node, set with EVP_SOLID_X/Y/Z (zero at init)       */
-    double reserved[9];
+    double reserved[7];
 } evp_params;
 
 /* Field identifiers for evp_set_field / evp_get_field */

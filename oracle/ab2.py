@@ -17,6 +17,16 @@ Reading 11:
   * tau^n is formed from B^n with mu_p^{n+1} (the properties are updated first);
   * the first step is forward Euler (weights 1, 0); the paper is silent on it;
   * f = CSF force (Eq. fLS) + mean-free Boussinesq buoyancy, see ``levelset``.
+
+With a density contrast (``rho_ratio`` = rho_2/rho_1, rho_1 = 1) the step follows
+the constant-coefficient splitting of Eqs. poisson-LS and projection-LS
+(Dong-Shen): with p_hat = 2 p^n - p^{n-1} and rho_0 = min(rho_1, rho_2),
+  lap p^{n+1} = div[(1 - rho_0/rho) grad p_hat] + (rho_0/dt) div u*,
+  u^{n+1} = u* - dt [grad p^{n+1}/rho_0 + (1/rho - 1/rho_0) grad p_hat],
+and RU carries 1/rho on the viscous, polymer and surface-tension terms (Eq. ru).
+Reading 15: rho at a face is the mean of its two neighbouring centres; gravity g
+(along -y) acts through (1 - rho_bar/rho) g per unit mass, rho_bar the domain mean,
+since a periodic pressure cannot carry the mean weight; p^{-1} = p^0.
 """
 
 from dataclasses import dataclass
@@ -25,8 +35,9 @@ import numpy as np
 
 from . import levelset as ls
 from .models import Params, tau_from_B
-from .momentum import advection, div_tau, viscous
-from .poisson import project
+from .grid import at
+from .momentum import advection, div_tau, grad_p, viscous
+from .poisson import divergence, project, solve_poisson
 from .step import State
 from .stress import stress_rhs
 
@@ -46,11 +57,36 @@ class TwoPhase:
     drho_g: float = 1.0
     reinit_every: int = 10
     reinit_iters: int = 3
+    rho_ratio: float = None
+    gravity: float = 1.0
 
     def mixture(self, H):
         mu_s = self.beta / self.Re * H + self.mu_ratio / self.Re * (1.0 - H)
         mu_p = (1.0 - self.beta) / self.Re * H
         return mu_s, mu_p
+
+
+def face_mean(c, g):
+    """Centre field averaged onto the u, v and w faces."""
+    return (0.5 * (c + at(c, g, 'c', i=1)), 0.5 * (c + at(c, g, 'c', j=1)), 0.5 * (c + at(c, g, 'c', k=1)))
+
+
+def split_projection(star, p_n, p_nm1, rho, dt, g, rho0):
+    """Dong-Shen constant-coefficient projection (Eqs. poisson-LS, projection-LS).
+    Returns (U, V, W, p^{n+1})."""
+    rf = face_mean(rho, g)
+    ph = 2.0 * p_n - p_nm1
+    gph = grad_p(ph, g)
+    flux = [(1.0 - rho0 / rf[d]) * gph[d] for d in range(3)]
+    if g.walls:
+        flux[1][:, g.ny - 1, :] = 0.0
+    r = divergence(*flux, g) + rho0 / dt * divergence(*star, g)
+    p_new = solve_poisson(r, g)
+    gp = grad_p(p_new, g)
+    out = [star[d] - dt * (gp[d] / rho0 + (1.0 / rf[d] - 1.0 / rho0) * gph[d]) for d in range(3)]
+    if g.walls:
+        out[1][:, g.ny - 1, :] = 0.0
+    return out[0], out[1], out[2], p_new
 
 
 def ab2_step(s, phi, dt, g, tp, nstep):
@@ -73,13 +109,27 @@ def ab2_step(s, phi, dt, g, tp, nstep):
     A = advection(s.U, s.V, s.W, g)
     Vv = viscous(s.U, s.V, s.W, g, mu_s)
     dtau = div_tau(tau_from_B(s.B, prm), g)
-    fc = ls.interface_force_centres(phi, g, tp.sigma, eps, tp.drho_g)
+    dens = tp.rho_ratio is not None
+    fc = ls.interface_force_centres(phi, g, tp.sigma, eps, 0.0 if dens else tp.drho_g)
     F = ls.centres_to_faces(fc, g)
-    RU = [-A[d] + Vv[d] + dtau[d] + F[d] for d in range(3)]
+    if dens:
+        rho = H + tp.rho_ratio * (1.0 - H)
+        rf = face_mean(rho, g)
+        rbar = rho.mean()
+        grav = (0.0, -tp.gravity, 0.0)
+        RU = [-A[d] + (Vv[d] + dtau[d] + F[d]) / rf[d] + (1.0 - rbar / rf[d]) * grav[d] for d in range(3)]
+    else:
+        RU = [-A[d] + Vv[d] + dtau[d] + F[d] for d in range(3)]
     vel = (s.U, s.V, s.W)
     star = [vel[d] + dt * (w1 * RU[d] + (w0 * s.N_hist[d] if w0 else 0.0)) for d in range(3)]
     if g.walls:
         star[1][:, g.ny - 1, :] = 0.0
-    # 5. projection with dt (rho = 1)
+    # 5. projection with dt
+    if dens:
+        p_nm1 = s.p if s.psi is None or nstep == 0 else s.psi
+        U, V, W, p_new = split_projection(star, s.p, p_nm1, rho, dt, g, min(1.0, tp.rho_ratio))
+        # psi carries p^{n} to the next step as its p^{n-1}
+        return State(U=U, V=V, W=W, p=p_new, B=Bn, RT_hist=RT, N_hist=RU, t=s.t + dt, nstep=nstep + 1,
+                     psi=s.p), phi
     U, V, W, psi = project(star[0], star[1], star[2], g, dt)
     return State(U=U, V=V, W=W, p=psi, B=Bn, RT_hist=RT, N_hist=RU, t=s.t + dt, nstep=nstep + 1, psi=psi), phi

@@ -103,6 +103,7 @@ struct evp_state_s {
     void* NRM[3];
     void* FC[3];
     void* SOL[3];        // penalization: solid fractions at the velocity nodes
+    void* POLD;          // AB2 with a density contrast: p^{n-1}
     double* partials;
     double* mean_1mH;
     long long nstep;     // AB2 steps taken
@@ -203,6 +204,7 @@ int validate(const evp_grid* g, evp_model model, const evp_params* p) {
         if (p->penalization) return fail(EVP_ERR_ARG, "volume penalisation is part of the RK3 step only");
         if (p->dpdx != 0.0 || p->abc_amp != 0.0)
             return fail(EVP_ERR_ARG, "the AB2 two-phase step takes no dpdx or ABC forcing");
+        if (!(p->rho_ratio >= 0)) return fail(EVP_ERR_ARG, "rho_ratio must be >= 0 (0: Boussinesq)");
         if (!(p->mu_ratio > 0) || !(p->ls_eps_cells > 0) || !(p->sigma >= 0) || p->reinit_every < 0 ||
             p->reinit_iters < 0)
             return fail(EVP_ERR_ARG, "bad two-phase parameters (mu_ratio, ls_eps_cells, sigma, reinit)");
@@ -258,7 +260,7 @@ size_t plan(evp_state* s, char* base) {
     const bool ab2 = s->prm.integrator == EVP_AB2;
     void* ls[12] = {nullptr};
     if (ab2)
-        for (int q = 0; q < 12; ++q) ls[q] = P(N * e);   // phi, phi0, phiA, phiB, H, n(3), f(3), spare
+        for (int q = 0; q < 12; ++q) ls[q] = P(N * e);   // phi, phi0, phiA, phiB, H, n(3), f(3), p^{n-1}
     const size_t nparts = (size_t)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.nz;
     void* parts = ab2 ? P(nparts * sizeof(double)) : nullptr;
     void* sol[3] = {nullptr, nullptr, nullptr};
@@ -285,6 +287,7 @@ size_t plan(evp_state* s, char* base) {
             s->NRM[q] = ls[5 + q];
             s->FC[q] = ls[8 + q];
         }
+        s->POLD = ls[11];
         s->partials = static_cast<double*>(parts);
         for (int q = 0; q < 3; ++q) s->SOL[q] = sol[q];
         s->mean_1mH = static_cast<double*>(mean);
@@ -582,7 +585,7 @@ int ab2_step_t(evp_state* s, double dt) {
         I.mean_1mH = s->mean_1mH;
         I.eps = T(p.ls_eps_cells * dx);
         I.sigma = T(p.sigma);
-        I.drho_g = T(p.drho_g);
+        I.drho_g = T(p.rho_ratio > 0 ? 0.0 : p.drho_g);
         if ((e = launch_interface<T>(g, I, s->st, th)) != cudaSuccess) return cuda_fail(e, "interface");
     }
     const bool first = s->nstep == 0;
@@ -636,8 +639,47 @@ int ab2_step_t(evp_state* s, double dt) {
         m.inv_lam = T(s->mc.inv_lam);
         m.L2 = T(s->mc.L2);
         m.a_fene = T(s->mc.a_fene);
+        m.rho_ratio = T(p.rho_ratio);
+        m.gravity = T(p.gravity);
+        m.mean_1mH = s->mean_1mH;
         if ((e = launch_momentum_ab2<T>(g, s->model, m, s->st, th)) != cudaSuccess)
             return cuda_fail(e, "momentum kernel");
+    }
+    if (p.rho_ratio > 0) {
+        // 5'. constant-coefficient split projection (Eqs. poisson-LS, projection-LS)
+        if (first) CK(cudaMemcpyAsync(s->POLD, s->P, s->N * sizeof(T), cudaMemcpyDeviceToDevice, s->st));
+        SplitArgs<T> q;
+        q.Us = static_cast<const T*>(s->U[1 - cu]);
+        q.Vs = static_cast<const T*>(s->V[1 - cu]);
+        q.Ws = static_cast<const T*>(s->W[1 - cu]);
+        q.P = static_cast<const T*>(s->P);
+        q.Pold = static_cast<const T*>(s->POLD);
+        q.H = static_cast<const T*>(s->HF);
+        q.R = static_cast<T*>(s->PSI);
+        q.U = static_cast<T*>(s->U[cu]);
+        q.V = static_cast<T*>(s->V[cu]);
+        q.W = static_cast<T*>(s->W[cu]);
+        q.rho_ratio = T(p.rho_ratio);
+        q.rho0 = T(p.rho_ratio < 1.0 ? p.rho_ratio : 1.0);
+        q.dt = T(dt);
+        q.maxdiv = s->d_maxdiv;
+        q.status = s->d_status;
+        q.idx_d = s->g.nx / s->g.lx;
+        q.idy_d = s->g.ny / s->g.ly;
+        q.idz_d = s->g.nz / s->g.lz;
+        if ((e = launch_split_rhs<T>(g, q, s->st, th)) != cudaSuccess) return cuda_fail(e, "split rhs");
+        int r = run_poisson<T>(s, nullptr, nullptr, nullptr, static_cast<const T*>(s->PSI), 1.0, static_cast<T*>(s->PSI));
+        if (r) return r;
+        CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
+        if ((e = launch_split_correct<T>(g, q, s->st, th)) != cudaSuccess) return cuda_fail(e, "split correct");
+        // rotate: p^{n-1} <- p^n, p^n <- p^{n+1}; the old p^{n-1} buffer becomes scratch
+        void* old = s->POLD;
+        s->POLD = s->P;
+        s->P = s->PSI;
+        s->PSI = old;
+        if (stress) s->cb = 1 - cb;
+        s->nstep += 1;
+        return EVP_OK;
     }
     // 5. projection with dt: p^{n+1} = psi
     int r = run_poisson<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
@@ -691,7 +733,7 @@ int init_fields(evp_state* s) {
         if (s->SOL[q]) CK(cudaMemsetAsync(s->SOL[q], 0, N * sizeof(T), s->st));
     if (s->ab2) {
         void* z[] = {s->PHI, s->PHI0, s->PHIA, s->PHIB, s->HF, s->NRM[0], s->NRM[1], s->NRM[2],
-                     s->FC[0], s->FC[1], s->FC[2]};
+                     s->FC[0], s->FC[1], s->FC[2], s->POLD};
         for (void* q : z) CK(cudaMemsetAsync(q, 0, N * sizeof(T), s->st));
     }
     s->nstep = 0;

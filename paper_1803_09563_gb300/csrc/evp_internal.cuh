@@ -215,6 +215,28 @@ struct MomAB2Args {
     T w1dt, w0dt;      // dt * 3/2 and dt * (-1/2) (dt and 0 on the first step)
     int read_hist;
     T mu_s1, mu_s2, mu_p1, mu_p2, inv_lam, L2, a_fene;
+    // density contrast (rho_ratio > 0): rho = H + rho_ratio (1 - H), gravity along -y
+    T rho_ratio, gravity;
+    const double* mean_1mH;   // domain mean of 1 - H (for the mean density)
+};
+
+// Dong-Shen split projection (Eqs. poisson-LS, projection-LS)
+template <typename T>
+struct SplitArgs {
+    const T* Us;
+    const T* Vs;
+    const T* Ws;       // u*
+    const T* P;        // p^n
+    const T* Pold;     // p^{n-1}
+    const T* H;        // Heaviside at n+1
+    T* R;              // right-hand side out (rhs kernel) / p^{n+1} in (correction)
+    T* U;
+    T* V;
+    T* W;              // u^{n+1} out
+    T rho_ratio, rho0, dt;
+    unsigned long long* maxdiv;
+    unsigned* status;
+    double idx_d, idy_d, idz_d;
 };
 
 // ----------------------------------------------------------- launch functions
@@ -257,6 +279,12 @@ cudaError_t launch_interface(const Geo<T>& g, const IfaceArgs<T>& a, cudaStream_
 template <typename T>
 cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>& a, cudaStream_t st,
                                 const TimingHook& th);
+
+template <typename T>
+cudaError_t launch_split_rhs(const Geo<T>& g, const SplitArgs<T>& a, cudaStream_t st, const TimingHook& th);
+
+template <typename T>
+cudaError_t launch_split_correct(const Geo<T>& g, const SplitArgs<T>& a, cudaStream_t st, const TimingHook& th);
 
 // radix plan of n = 4^a 3^b 2^c (radix-4 first); returns the number of stages or -1
 int fft_radices(int n, int* rad);

@@ -262,9 +262,25 @@ __global__ void __launch_bounds__(256) k_momentum_ab2(const Geo<T> g, const MomA
     const T Fy = h * (__ldg(a.f[1] + c0) + ld_c(g, a.f[1], i, j + 1, k));
     const T Fz = h * (__ldg(a.f[2] + c0) + ld_c(g, a.f[2], i, j, k + 1));
 
-    const T Nx = -Ax + Vx + dtx + Fx;
-    const T Ny = -Ay + Vy + dty + Fy;
-    const T Nz = -Az + Vz + dtz + Fz;
+    T Nx, Ny, Nz;
+    if (a.rho_ratio > T(0)) {
+        // density contrast: 1/rho on the stress terms, (1 - rho_bar/rho) g per unit mass
+        auto rho = [&](int di, int dj, int dk) {
+            const T Hc = ld_c(g, a.H, i + di, j + dj, k + dk);
+            return Hc + a.rho_ratio * (T(1) - Hc);
+        };
+        const T r0 = rho(0, 0, 0);
+        const T rfx = h * (r0 + rho(1, 0, 0)), rfy = h * (r0 + rho(0, 1, 0)), rfz = h * (r0 + rho(0, 0, 1));
+        const double m = *a.mean_1mH;
+        const T rbar = T((1.0 - m) + double(a.rho_ratio) * m);
+        Nx = -Ax + (Vx + dtx + Fx) / rfx;
+        Ny = -Ay + (Vy + dty + Fy) / rfy + (T(1) - rbar / rfy) * (-a.gravity);
+        Nz = -Az + (Vz + dtz + Fz) / rfz;
+    } else {
+        Nx = -Ax + Vx + dtx + Fx;
+        Ny = -Ay + Vy + dty + Fy;
+        Nz = -Az + Vz + dtz + Fz;
+    }
     T ux = a.w1dt * Nx, uy = a.w1dt * Ny, uz = a.w1dt * Nz;
     if (a.read_hist) {
         ux += a.w0dt * a.NH[0][c0];
@@ -279,7 +295,120 @@ __global__ void __launch_bounds__(256) k_momentum_ab2(const Geo<T> g, const MomA
     a.NH[2][c0] = Nz;
 }
 
+// density at a centre from the Heaviside: rho_1 = 1 (H = 1), rho_2 = rho_ratio
+template <typename T>
+__device__ __forceinline__ T rho_c(const Geo<T>& g, const SplitArgs<T>& a, int i, int j, int k) {
+    const T H = ld_c(g, a.H, i, j, k);
+    return H + a.rho_ratio * (T(1) - H);
+}
+
+// p_hat = 2 p^n - p^{n-1} at a centre
+template <typename T>
+__device__ __forceinline__ T phat(const Geo<T>& g, const SplitArgs<T>& a, int i, int j, int k) {
+    return T(2) * ld_c(g, a.P, i, j, k) - ld_c(g, a.Pold, i, j, k);
+}
+
+// r = div[(1 - rho_0/rho_f) grad p_hat] + (rho_0/dt) div u*   (Eq. poisson-LS)
+template <typename T>
+__global__ void __launch_bounds__(256) k_split_rhs(const Geo<T> g, const SplitArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const size_t c0 = lin(g, i, j, k);
+    const T r0 = rho_c(g, a, i, j, k), p0 = phat(g, a, i, j, k);
+    // flux (1 - rho_0/rho_f) d p_hat / dn through the +1/2 face of (i, j, k) offset by (di, dj, dk)
+    auto fx = [&](int di) {
+        const T ra = rho_c(g, a, i + di, j, k), rb = rho_c(g, a, i + di + 1, j, k);
+        return (T(1) - a.rho0 / (T(0.5) * (ra + rb))) * (phat(g, a, i + di + 1, j, k) - phat(g, a, i + di, j, k)) * g.idx;
+    };
+    auto fy = [&](int dj) {
+        const int jf = j + dj;
+        if (g.walls && (jf < 0 || jf >= g.ny - 1)) return T(0);   // no flux through the walls
+        const T ra = rho_c(g, a, i, jf, k), rb = rho_c(g, a, i, jf + 1, k);
+        return (T(1) - a.rho0 / (T(0.5) * (ra + rb))) * (phat(g, a, i, jf + 1, k) - phat(g, a, i, jf, k)) * g.idy;
+    };
+    auto fz = [&](int dk) {
+        const T ra = rho_c(g, a, i, j, k + dk), rb = rho_c(g, a, i, j, k + dk + 1);
+        return (T(1) - a.rho0 / (T(0.5) * (ra + rb))) * (phat(g, a, i, j, k + dk + 1) - phat(g, a, i, j, k + dk)) * g.idz;
+    };
+    (void)r0;
+    (void)p0;
+    const T divf = (fx(0) - fx(-1)) * g.idx + (fy(0) - fy(-1)) * g.idy + (fz(0) - fz(-1)) * g.idz;
+    const T du = __ldg(a.Us + c0) - ld_uw(g, a.Us, i - 1, j, k);
+    const T dv = __ldg(a.Vs + c0) - ld_v(g, a.Vs, i, j - 1, k);
+    const T dw = __ldg(a.Ws + c0) - ld_uw(g, a.Ws, i, j, k - 1);
+    a.R[c0] = divf + a.rho0 / a.dt * (du * g.idx + dv * g.idy + dw * g.idz);
+}
+
+// u^{n+1} = u* - dt [grad p^{n+1}/rho_0 + (1/rho_f - 1/rho_0) grad p_hat]   (Eq. projection-LS)
+// and the FP64 max |div u^{n+1}|
+template <typename T>
+__global__ void __launch_bounds__(256) k_split_correct(const Geo<T> g, const SplitArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    double dmax = 0.0;
+    unsigned bits = 0;
+    if (i < g.nx && j < g.ny) {
+        const size_t c0 = lin(g, i, j, k);
+        const T ir0 = T(1) / a.rho0;
+        // corrected face value of component d at the +1/2 face of (ii, jj, kk)
+        auto face = [&](int d, int ii, int jj, int kk) {
+            int oi = d == 0, oj = d == 1, ok = d == 2;
+            if (d == 1 && g.walls && (jj < 0 || jj >= g.ny - 1)) return T(0);
+            const T* S = d == 0 ? a.Us : (d == 1 ? a.Vs : a.Ws);
+            const T us = d == 1 ? ld_v(g, S, ii, jj, kk) : ld_uw(g, S, ii, jj, kk);
+            const T h = d == 0 ? g.idx : (d == 1 ? g.idy : g.idz);
+            const T ra = rho_c(g, a, ii, jj, kk), rb = rho_c(g, a, ii + oi, jj + oj, kk + ok);
+            const T rf = T(0.5) * (ra + rb);
+            const T gp = (ld_c(g, a.R, ii + oi, jj + oj, kk + ok) - ld_c(g, a.R, ii, jj, kk)) * h;
+            const T gh = (phat(g, a, ii + oi, jj + oj, kk + ok) - phat(g, a, ii, jj, kk)) * h;
+            return us - a.dt * (gp * ir0 + (T(1) / rf - ir0) * gh);
+        };
+        const T Un = face(0, i, j, k), Vn = face(1, i, j, k), Wn = face(2, i, j, k);
+        a.U[c0] = Un;
+        a.V[c0] = Vn;
+        a.W[c0] = Wn;
+        const T Ul = face(0, i - 1, j, k), Vl = face(1, i, j - 1, k), Wl = face(2, i, j, k - 1);
+        const double dv = (double(Un) - double(Ul)) * a.idx_d + (double(Vn) - double(Vl)) * a.idy_d
+                          + (double(Wn) - double(Wl)) * a.idz_d;
+        dmax = fabs(dv);
+        if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn) || !(dmax <= DBL_MAX)) {
+            bits |= EVP_BIT_NONFINITE;
+            dmax = 0.0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (dmax > 0.0) atomicMax(a.maxdiv, (unsigned long long)__double_as_longlong(dmax));
+        if (bits) atomicOr(a.status, bits);
+    }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_split_rhs(const Geo<T>& g, const SplitArgs<T>& a, cudaStream_t st, const TimingHook& th) {
+    dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    th.b(K_DIV_FFTX);
+    k_split_rhs<T><<<grid, block, 0, st>>>(g, a);
+    th.e(K_DIV_FFTX);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_split_correct(const Geo<T>& g, const SplitArgs<T>& a, cudaStream_t st, const TimingHook& th) {
+    dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    th.b(K_CORRECT);
+    k_split_correct<T><<<grid, block, 0, st>>>(g, a);
+    th.e(K_CORRECT);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_ls_stage(const Geo<T>& g, const LsArgs<T>& a, bool reinit, cudaStream_t st,
@@ -334,7 +463,10 @@ cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>&
     template cudaError_t launch_interface<T>(const Geo<T>&, const IfaceArgs<T>&, cudaStream_t,                \
                                              const TimingHook&);                                              \
     template cudaError_t launch_momentum_ab2<T>(const Geo<T>&, int, const MomAB2Args<T>&, cudaStream_t,       \
-                                                const TimingHook&);
+                                                const TimingHook&);                                           \
+    template cudaError_t launch_split_rhs<T>(const Geo<T>&, const SplitArgs<T>&, cudaStream_t, const TimingHook&); \
+    template cudaError_t launch_split_correct<T>(const Geo<T>&, const SplitArgs<T>&, cudaStream_t,            \
+                                                 const TimingHook&);
 EVP_INST(float)
 EVP_INST(double)
 #undef EVP_INST

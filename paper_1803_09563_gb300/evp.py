@@ -45,7 +45,8 @@ class evp_params(ctypes.Structure):
                 ('bi_def', c_int), ('dpdx', c_double), ('abc_amp', c_double), ('abc_k', c_double),
                 ('precision', c_int), ('integrator', c_int), ('mu_ratio', c_double), ('ls_eps_cells', c_double),
                 ('sigma', c_double), ('drho_g', c_double), ('reinit_every', c_int), ('reinit_iters', c_int),
-                ('penalization', c_int), ('reserved', c_double * 9)]
+                ('rho_ratio', c_double), ('gravity', c_double), ('penalization', c_int),
+                ('reserved', c_double * 7)]
 
 
 class EvpError(RuntimeError):
@@ -132,7 +133,7 @@ def make_grid(nx, ny, nz, lx, ly, lz, walls_y=False):
 
 def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_amp=0.0, abc_k=0.0,
                 precision=EVP_FP64, integrator=EVP_RK3, mu_ratio=1.0, ls_eps_cells=1.5, sigma=0.0, drho_g=0.0,
-                reinit_every=10, reinit_iters=3, penalization=0):
+                reinit_every=10, reinit_iters=3, penalization=0, rho_ratio=0.0, gravity=0.0):
     p = evp_params()
     p.Re, p.Wi, p.beta, p.Bi, p.L2 = float(Re), float(Wi), float(beta), float(Bi), float(L2)
     p.bi_def, p.dpdx, p.abc_amp, p.abc_k = int(bi_def), float(dpdx), float(abc_amp), float(abc_k)
@@ -140,6 +141,7 @@ def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_am
     p.mu_ratio, p.ls_eps_cells, p.sigma, p.drho_g = float(mu_ratio), float(ls_eps_cells), float(sigma), float(drho_g)
     p.reinit_every, p.reinit_iters = int(reinit_every), int(reinit_iters)
     p.penalization = int(penalization)
+    p.rho_ratio, p.gravity = float(rho_ratio), float(gravity)
     return p
 
 

@@ -18,7 +18,7 @@ def rel(got, ref):
     return float(np.abs(np.asarray(got, dtype=np.float64) - ref).max() / max(np.abs(ref).max(), 1e-300))
 
 
-def drop_case(evp, precision, n=16, walls=False, model='saramito', steps=3, reinit_every=2):
+def drop_case(evp, precision, n=16, walls=False, model='saramito', steps=3, reinit_every=2, rho_ratio=None):
     nx, ny, nz = n, 2 * n, n
     L = 1.5
     geo = inputs.geometry(nx, ny, nz, L, 2 * L, L, walls)
@@ -27,10 +27,10 @@ def drop_case(evp, precision, n=16, walls=False, model='saramito', steps=3, rein
     phi = inputs.sphere_distance(geo, c, 0.35)
     tau_y = 0.02
     tp = TwoPhase(model, Re=35.0, Wi=1.0, beta=0.5, tau_y=tau_y, mu_ratio=1.0, L2=50.0, sigma=0.1,
-                  drho_g=1.0, reinit_every=reinit_every, reinit_iters=2)
+                  drho_g=1.0, reinit_every=reinit_every, reinit_iters=2, rho_ratio=rho_ratio, gravity=1.0)
     prm = evp.make_params(Re=35.0, Wi=1.0, beta=0.5, Bi=tau_y, bi_def=1, L2=50.0, precision=precision,
                           integrator=evp.EVP_AB2, mu_ratio=1.0, ls_eps_cells=1.5, sigma=0.1, drho_g=1.0,
-                          reinit_every=reinit_every, reinit_iters=2)
+                          reinit_every=reinit_every, reinit_iters=2, rho_ratio=rho_ratio or 0.0, gravity=1.0)
     sim = evp.Simulation(evp.make_grid(nx, ny, nz, L, 2 * L, L, walls), model, prm)
     sim.set(evp.EVP_PHI, phi)
     st = oracle.State.rest(g)
@@ -57,6 +57,19 @@ def ref_fields(st, phi):
 @pytest.mark.parametrize("model", ['saramito', 'oldroyd_b'])
 def test_ab2_drop_steps_fp64(evp, walls, model):
     sim, st, phi, g, maxdiv = drop_case(evp, evp.EVP_FP64, walls=walls, model=model)
+    names = ['u', 'v', 'w', 'p', 'phi', 'Bxx', 'Bxy', 'Bxz', 'Byy', 'Byz', 'Bzz']
+    for name, got, ref in zip(names, fields(sim, evp), ref_fields(st, phi)):
+        assert rel(got, ref) < 1e-10, (name, rel(got, ref))
+    assert maxdiv < 1e-10
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_density_contrast_drop_fp64(evp, walls):
+    """k_rho = 0.1 drop with the Dong-Shen split projection (Eqs. poisson-LS,
+    projection-LS): four steps (the pressure history p^{n-1} enters from the
+    second step on) against the oracle."""
+    sim, st, phi, g, maxdiv = drop_case(evp, evp.EVP_FP64, walls=walls, model='oldroyd_b', steps=4,
+                                        rho_ratio=0.1)
     names = ['u', 'v', 'w', 'p', 'phi', 'Bxx', 'Bxy', 'Bxz', 'Byy', 'Byz', 'Bzz']
     for name, got, ref in zip(names, fields(sim, evp), ref_fields(st, phi)):
         assert rel(got, ref) < 1e-10, (name, rel(got, ref))
