@@ -332,6 +332,45 @@ def run_serving(steps_scale=0.1):
     return rep
 
 
+def run_fene_turbulence(steps=4):
+    """FENE-P forced turbulence: triply periodic 256^3 on a 2 pi box, L^2 = 900,
+    Wi = 5, beta = 0.9, Re = 200, ABC forcing (A = 1, k = 2), initial solenoidal
+    velocity with a k^-5/3 spectrum for 1 <= |k| <= 16 (u_rms = 1, seed 2), B = I,
+    dt = 1e-3.  FP32 and FP64 side by side from the same state; the relative
+    difference of every field after ``steps`` steps is reported."""
+    import torch
+    from paper_1803_09563_gb300 import evp, inputs
+    n, L = 256, 2 * np.pi
+    geo = inputs.geometry(n, n, n, L, L, L)
+    U, V, W = inputs.scale_rms(*inputs.random_solenoidal(geo, 2, 16, spectrum='k-5/3', periodic_fft=True), 1.0)
+    out = {"workload": "fene_p_turbulence_256^3", "steps": steps}
+    res = {}
+    for prec, name in ((evp.EVP_FP32, 'fp32'), (evp.EVP_FP64, 'fp64')):
+        stream = torch.cuda.Stream()
+        sim = evp.Simulation(evp.make_grid(n, n, n, L, L, L), 'fene_p',
+                             evp.make_params(Re=200.0, Wi=5.0, beta=0.9, L2=900.0, abc_amp=1.0, abc_k=2.0,
+                                             precision=prec), stream=stream.cuda_stream)
+        sim.set_state(U, V, W)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sim.step(1e-3)
+        sim.sync()
+        e0.record(stream)
+        for _ in range(steps - 1):
+            sim.step(1e-3)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / max(1, steps - 1)
+        code, bits, maxdiv = sim.sync(raise_on_error=False)
+        out[name] = {"ms_per_step": ms, "Mcell_steps_per_s": n ** 3 / (ms * 1e-3) / 1e6, "max_div": maxdiv,
+                     "status": code}
+        res[name] = [sim.get(f).astype(np.float64) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_BXX,
+                                                                 evp.EVP_BXY)]
+        sim.close()
+    out["fp32_vs_fp64_rel_err"] = {k: float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+                                   for k, a, b in zip(('u', 'v', 'w', 'Bxx', 'Bxy'), res['fp32'], res['fp64'])}
+    return out
+
+
 def run_small_grid():
     """Single-phase Oldroyd-B Taylor-Green box 32^3 in FP64 (the 10-step parity
     workload): per-step latency with direct launches and with graph replay."""
@@ -424,6 +463,7 @@ def main():
     if not args.no_extras:
         line['serving'] = run_serving()
         line['small_grid'] = run_small_grid()
+        line['fene_p_turbulence'] = run_fene_turbulence()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line['cpu_baseline'] = run_cpu_baseline(args)

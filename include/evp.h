@@ -69,7 +69,8 @@ typedef enum {
     EVP_NEWTONIAN = 0,   /* no extra stress (tau = 0)                          */
     EVP_OLDROYD_B = 1,   /* Table 1: B = tau lambda/mu_p + I, F = 1, a = 1    */
     EVP_FENE_P = 2,      /* Table 1: F = L^2/(L^2 - tr B), a = L^2/(L^2 - 3)  */
-    EVP_SARAMITO = 3     /* Table 1: F = a = max(0, 1 - tau_y/|tau^d|)        */
+    EVP_SARAMITO = 3,    /* Table 1: F = a = max(0, 1 - tau_y/|tau^d|)        */
+    EVP_NEO_HOOKEAN = 4  /* Table 1: B = tau/G, F = a = 0; G = mu_p/lambda    */
 } evp_model;
 
 enum { EVP_FP64 = 0, EVP_FP32 = 1 };

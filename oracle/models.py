@@ -16,6 +16,9 @@ Reading 2 (gradient convention): (grad u)_ij = du_j/dx_i, so
 B.grad u + grad u^T.B = L B + B L^T with L_ij = du_i/dx_j (upper-convected).
 Reading 7: the Saramito factor is max(0, 1 - tau_y/|tau^d|), with F = 0 at
 |tau^d| = 0 when tau_y > 0 and F = 1 when tau_y = 0 (Bi = 0 is Oldroyd-B).
+Neo-Hookean (Table 1, first row): B = tau/G with F = a = 0, i.e. no relaxation;
+the shear modulus is G = mu_p/lambda (the infinite-relaxation-time limit of a
+viscoelastic fluid at fixed modulus, as the paper describes it).
 """
 
 from dataclasses import dataclass
@@ -27,7 +30,7 @@ COMPS = ('xx', 'xy', 'xz', 'yy', 'yz', 'zz')
 COMP_IJ = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
 DIAG = (True, False, False, True, False, True)
 
-MODELS = ('newtonian', 'oldroyd_b', 'fene_p', 'saramito')
+MODELS = ('newtonian', 'oldroyd_b', 'fene_p', 'saramito', 'neo_hookean')
 
 
 def comp_index(a, b):
@@ -59,6 +62,8 @@ def closure(B, prm):
     """(F, a) of Table 1 at every cell."""
     if prm.model in ('oldroyd_b', 'newtonian'):
         return 1.0, 1.0
+    if prm.model == 'neo_hookean':
+        return 0.0, 0.0
     if prm.model == 'fene_p':
         trB = B[0] + B[3] + B[5]
         F = prm.L2 / (prm.L2 - trB)
@@ -89,6 +94,8 @@ def tau_from_B(B, prm):
     if prm.model == 'fene_p':
         F, a = closure(B, prm)
         return [g * (F * B[c] - (a if DIAG[c] else 0.0)) for c in range(6)]
+    if prm.model == 'neo_hookean':
+        return [g * B[c] for c in range(6)]
     return [g * (B[c] - (1.0 if DIAG[c] else 0.0)) for c in range(6)]
 
 

@@ -192,7 +192,7 @@ int validate(const evp_grid* g, evp_model model, const evp_params* p) {
         return fail(EVP_ERR_ARG, "periodic ny must be 2^a 3^b, 8..512");
     }
     if (!(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0)) return fail(EVP_ERR_ARG, "box lengths must be positive");
-    if (model < EVP_NEWTONIAN || model > EVP_SARAMITO) return fail(EVP_ERR_ARG, "unknown model");
+    if (model < EVP_NEWTONIAN || model > EVP_NEO_HOOKEAN) return fail(EVP_ERR_ARG, "unknown model");
     if (!(p->Re > 0)) return fail(EVP_ERR_ARG, "Re must be positive");
     if (!(p->beta >= 0 && p->beta <= 1)) return fail(EVP_ERR_ARG, "beta must be in [0, 1]");
     if (model != EVP_NEWTONIAN && !(p->Wi > 0)) return fail(EVP_ERR_ARG, "Wi must be positive");

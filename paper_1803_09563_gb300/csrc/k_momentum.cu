@@ -159,6 +159,10 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
                     sm.S[c][slot][e] = gm * (Fn * sm.Braw[6 + c][e] - (d ? av : T(0)))
                                        + gm * (Fo * sm.Braw[c][e] - (d ? av : T(0)));
                 }
+            } else if (MODEL == EVP_NEO_HOOKEAN) {
+                // Table 1: tau = G B
+#pragma unroll
+                for (int c = 0; c < 6; ++c) sm.S[c][slot][e] = gm * sm.Braw[6 + c][e] + gm * sm.Braw[c][e];
             } else {
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
@@ -355,6 +359,7 @@ cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const Momentu
         EVP_LAUNCH_MOM(EVP_OLDROYD_B)
         EVP_LAUNCH_MOM(EVP_FENE_P)
         EVP_LAUNCH_MOM(EVP_SARAMITO)
+        EVP_LAUNCH_MOM(EVP_NEO_HOOKEAN)
 #undef EVP_LAUNCH_MOM
         default: return cudaErrorInvalidValue;
     }

@@ -246,7 +246,10 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
 
         // ---- Table 1 closure at the cell
         T F = T(1), av = T(1);
-        if (MODEL == EVP_FENE_P) {
+        if (MODEL == EVP_NEO_HOOKEAN) {
+            F = T(0);
+            av = T(0);
+        } else if (MODEL == EVP_FENE_P) {
             const T tr = w[0][3] + w[3][3] + w[5][3];
             F = kL2 / (kL2 - tr);
             av = kaf;
@@ -368,6 +371,10 @@ cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArg
         EVP_LAUNCH_STRESS(EVP_SARAMITO, 1)
         EVP_LAUNCH_STRESS(EVP_SARAMITO, 2)
         EVP_LAUNCH_STRESS(EVP_SARAMITO, 3)
+        EVP_LAUNCH_STRESS(EVP_NEO_HOOKEAN, 0)
+        EVP_LAUNCH_STRESS(EVP_NEO_HOOKEAN, 1)
+        EVP_LAUNCH_STRESS(EVP_NEO_HOOKEAN, 2)
+        EVP_LAUNCH_STRESS(EVP_NEO_HOOKEAN, 3)
 #undef EVP_LAUNCH_STRESS
         default: return cudaErrorInvalidValue;
     }

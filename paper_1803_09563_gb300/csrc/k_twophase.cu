@@ -163,6 +163,7 @@ __device__ __forceinline__ T tau_mix(const Geo<T>& g, const MomAB2Args<T>& a, in
         const T F = a.L2 / (a.L2 - tr);
         return gm * (F * bc - (diag ? a.a_fene : T(0)));
     }
+    if (MODEL == EVP_NEO_HOOKEAN) return gm * bc;
     return gm * (bc - (diag ? T(1) : T(0)));
 }
 
@@ -450,6 +451,7 @@ cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>&
         case EVP_OLDROYD_B: k_momentum_ab2<T, EVP_OLDROYD_B><<<grid, block, 0, st>>>(g, a); break;
         case EVP_FENE_P: k_momentum_ab2<T, EVP_FENE_P><<<grid, block, 0, st>>>(g, a); break;
         case EVP_SARAMITO: k_momentum_ab2<T, EVP_SARAMITO><<<grid, block, 0, st>>>(g, a); break;
+        case EVP_NEO_HOOKEAN: k_momentum_ab2<T, EVP_NEO_HOOKEAN><<<grid, block, 0, st>>>(g, a); break;
         default: return cudaErrorInvalidValue;
     }
     th.e(K_MOMENTUM);

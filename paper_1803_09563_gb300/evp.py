@@ -21,8 +21,8 @@ EVP_OK, EVP_ERR_ARG, EVP_ERR_OOM, EVP_ERR_CUDA, EVP_ERR_NONFINITE, EVP_ERR_UNPHY
     EVP_ERR_STATE = range(8)
 EVP_BIT_NONFINITE, EVP_BIT_TRACE_LIMIT, EVP_BIT_DET_NEG = 0x1, 0x2, 0x4
 # evp_model
-EVP_NEWTONIAN, EVP_OLDROYD_B, EVP_FENE_P, EVP_SARAMITO = range(4)
-MODEL_IDS = {'newtonian': 0, 'oldroyd_b': 1, 'fene_p': 2, 'saramito': 3}
+EVP_NEWTONIAN, EVP_OLDROYD_B, EVP_FENE_P, EVP_SARAMITO, EVP_NEO_HOOKEAN = range(5)
+MODEL_IDS = {'newtonian': 0, 'oldroyd_b': 1, 'fene_p': 2, 'saramito': 3, 'neo_hookean': 4}
 EVP_FP64, EVP_FP32 = 0, 1
 EVP_RK3, EVP_AB2 = 0, 1
 # evp_field

@@ -70,6 +70,22 @@ def _curl(Ax, Ay, Az, geo):
     return U, V, W
 
 
+def _spectral_potential_periodic(geo, rng, kmin, kmax, amp_of_k, xo, yo, zo):
+    """Random real field on a triply periodic box sampled at x = (i + xo) dx,
+    y = (j + yo) dy, z = (k + zo) dz: Fourier modes kmin <= |k| <= kmax with
+    amplitude amp_of_k(|k|) and random complex coefficients, one inverse 3-D FFT."""
+    nx, ny, nz, dx, dy, dz, y0 = _axes(geo)
+    kx = np.fft.fftfreq(nx, 1.0 / nx)[None, None, :]
+    ky = np.fft.fftfreq(ny, 1.0 / ny)[None, :, None]
+    kz = np.fft.fftfreq(nz, 1.0 / nz)[:, None, None]
+    mag = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    mask = (mag >= kmin) & (mag <= kmax)
+    amp = np.where(mask, amp_of_k(np.where(mask, mag, 1.0)), 0.0)
+    coef = amp * (rng.standard_normal(mag.shape) + 1j * rng.standard_normal(mag.shape))
+    shift = np.exp(2j * np.pi * (kx * xo / nx + ky * yo / ny + kz * zo / nz))
+    return np.real(np.fft.ifftn(coef * shift)) * (nx * ny * nz)
+
+
 def _spectral_potential(geo, rng, kmin, kmax, amp_of_k, y_positions, xo, zo):
     """Random real field periodic in x and z (and y unless walls) sampled on the
     lattice x = (i + xo) dx, z = (k + zo) dz and the y values ``y_positions``."""
@@ -102,11 +118,13 @@ def _spectral_potential(geo, rng, kmin, kmax, amp_of_k, y_positions, xo, zo):
     return out
 
 
-def random_solenoidal(geo, seed, kmax, kmin=1.0, spectrum='flat', wall_envelope=True):
+def random_solenoidal(geo, seed, kmax, kmin=1.0, spectrum='flat', wall_envelope=True, periodic_fft=False):
     """Discretely divergence-free random velocity (discrete curl of a random vector
     potential).  ``spectrum`` 'flat' weights all modes 1 <= |k| <= kmax equally,
     'k-5/3' shapes the velocity spectrum like k^-5/3.  With walls the potential is
     multiplied by (1 - (2y/ly)^2)^2 so that v vanishes on both walls.
+    ``periodic_fft`` draws a triply periodic potential with one 3-D FFT per
+    component (fast on large boxes; a different realisation for the same seed).
     Returned unscaled (the caller normalises)."""
     rng = np.random.default_rng(seed)
     nx, ny, nz, dx, dy, dz, y0 = _axes(geo)
@@ -117,6 +135,15 @@ def random_solenoidal(geo, seed, kmax, kmin=1.0, spectrum='flat', wall_envelope=
         amp = lambda k: k ** (-11.0 / 6.0 - 1.0)
     else:
         raise ValueError(spectrum)
+    if not geo['walls_y'] and periodic_fft:
+        # triply periodic: potentials on their staggered lattices from 3-D FFTs;
+        # the extra leading y-row is the periodic image of the last one
+        Ax = _spectral_potential_periodic(geo, rng, kmin, kmax, amp, 0.5, 1.0, 1.0)
+        Ay = _spectral_potential_periodic(geo, rng, kmin, kmax, amp, 1.0, 0.5, 1.0)
+        Az = _spectral_potential_periodic(geo, rng, kmin, kmax, amp, 1.0, 1.0, 0.5)
+        Ax = np.concatenate([Ax[:, -1:, :], Ax], axis=1)
+        Az = np.concatenate([Az[:, -1:, :], Az], axis=1)
+        return _curl(Ax, Ay, Az, geo)
     y_cell = y0 + (np.arange(ny) + 0.5) * dy
     y_edge = y0 + np.arange(-1, ny) * dy + dy        # edges j-1/2 for j = 0..ny
     Ax = _spectral_potential(geo, rng, kmin, kmax, amp, y_edge, 0.5, 1.0)

@@ -207,3 +207,17 @@ def test_saramito_elastic_solid_limit():
         assert closure(Bs[n], prm)[0] == 0.0
         assert abs(tau[1] - G * gam) < 1e-8
         assert abs(tau[0] - G * gam ** 2) < 1e-8
+
+
+def test_neo_hookean_shear_is_elastic():
+    """Table 1 first row (F = a = 0): homogeneous shear gives the elastic closed
+    form B_xy = gdot t, B_xx = 1 + (gdot t)^2, tau = G B with no relaxation."""
+    prm = Params.from_groups('neo_hookean', Re=1.0, Wi=2.0, beta=0.4)
+    G = prm.mu_p / prm.lam
+    ts, Bs = integrate_homogeneous(prm, shear_L(0.8), 3.0, 1e-3)
+    for n in (500, 1500, 3000):
+        t = ts[n]
+        assert abs(Bs[n][1] - 0.8 * t) < 1e-10
+        assert abs(Bs[n][0] - (1 + (0.8 * t) ** 2)) < 1e-9
+        assert abs(tau_from_B(Bs[n], prm)[1] - G * 0.8 * t) < 1e-10
+        assert abs(Bs[n][3] - 1.0) < 1e-14
