@@ -23,6 +23,9 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   closures (Table 1), stress RHS (Eq. SRM2) ........ pinned (start-up / oscillatory
                                                      shear closed forms, Saramito yield
                                                      time, steady yielded shear)
+  local artificial diffusion (Sec. 3.1) ............ pinned (sine-mode eigenvalues of the
+                                                     stencil, trigger thresholds, wall
+                                                     row, conservation)
   momentum RHS (Eq. NS-num1) ....................... pinned (Taylor-Green decay order,
                                                      steady Oldroyd-B Poiseuille)
   Poisson solve + projection (Eqs. NS-num2/3) ...... pinned (sine modes, sparse direct
@@ -37,7 +40,7 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
 from .grid import Grid, at  # noqa: F401
 from .weno import hj_weno5, weno5_derivative  # noqa: F401
 from .models import Params, closure, tau_from_B, rt_local  # noqa: F401
-from .stress import centre_velocity, velocity_gradient, stress_rhs  # noqa: F401
+from .stress import centre_velocity, velocity_gradient, stress_rhs, determinant, diffusion_cells  # noqa: F401
 from .momentum import advection, laplacian, div_tau, grad_p, momentum_rhs_n  # noqa: F401
 from .poisson import divergence, eigenvalues, solve_poisson, project  # noqa: F401
 from .step import State, rk3_step, rk3_substep, RK3_ALPHA, RK3_ZETA, RK3_XI  # noqa: F401

@@ -59,6 +59,7 @@ class TwoPhase:
     reinit_iters: int = 3
     rho_ratio: float = None
     gravity: float = 1.0
+    art_diff: float = 0.0
 
     def mixture(self, H):
         mu_s = self.beta / self.Re * H + self.mu_ratio / self.Re * (1.0 - H)
@@ -100,7 +101,7 @@ def ab2_step(s, phi, dt, g, tp, nstep):
     # 2. mixture properties at n+1
     H = ls.heaviside(phi, eps)
     mu_s, mu_p = tp.mixture(H)
-    prm = Params(tp.model, mu_s=mu_s, mu_p=mu_p, lam=tp.Wi, tau_y=tp.tau_y, L2=tp.L2)
+    prm = Params(tp.model, mu_s=mu_s, mu_p=mu_p, lam=tp.Wi, tau_y=tp.tau_y, L2=tp.L2, art_diff=tp.art_diff)
     w1, w0 = (1.0, 0.0) if nstep == 0 else (1.5, -0.5)
     # 3. stress, Eq. ab2tau
     RT = stress_rhs(s.U, s.V, s.W, s.B, g, prm)

@@ -16,6 +16,8 @@ Reading 2 (gradient convention): (grad u)_ij = du_j/dx_i, so
 B.grad u + grad u^T.B = L B + B L^T with L_ij = du_i/dx_j (upper-convected).
 Reading 7: the Saramito factor is max(0, 1 - tau_y/|tau^d|), with F = 0 at
 |tau^d| = 0 when tau_y > 0 and F = 1 when tau_y = 0 (Bi = 0 is Oldroyd-B).
+Reading 16 (local artificial diffusion, Sec. 3.1): a constant diffusivity
+art_diff (the paper says the amount is tuned per case and gives none; 0 = off).
 Neo-Hookean (Table 1, first row): B = tau/G with F = a = 0, i.e. no relaxation;
 the shear modulus is G = mu_p/lambda (the infinite-relaxation-time limit of a
 viscoelastic fluid at fixed modulus, as the paper describes it).
@@ -48,14 +50,15 @@ class Params:
     lam: object
     tau_y: object = 0.0
     L2: float = 0.0
+    art_diff: float = 0.0
 
     @staticmethod
-    def from_groups(model, Re, Wi, beta, Bi=0.0, L2=0.0, bi_def=0):
+    def from_groups(model, Re, Wi, beta, Bi=0.0, L2=0.0, bi_def=0, art_diff=0.0):
         """Reading 1: dimensionless groups -> coefficients (rho = 1)."""
         assert model in MODELS
         mu0 = 1.0 / Re
         tau_y = Bi * mu0 if bi_def == 0 else Bi
-        return Params(model, beta * mu0, (1.0 - beta) * mu0, Wi, tau_y, L2)
+        return Params(model, beta * mu0, (1.0 - beta) * mu0, Wi, tau_y, L2, art_diff)
 
 
 def closure(B, prm):

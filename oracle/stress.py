@@ -10,7 +10,16 @@ gradients du/dx, dv/dy, dw/dz are the face difference across the cell; the
 off-diagonal gradients are central differences of the centre velocities of the
 two neighbouring cells.  u.grad B uses the WENO5 derivative upwinded by the
 centre velocity (see ``weno``).
+
+Local artificial diffusion (Sec. 3.1, Reading 16): where B has lost positive
+definiteness (det B < 0) or, for FENE-P, where tr B has reached 95 % of L^2,
+art_diff times the 7-point Laplacian of B (zero-gradient ghosts at walls) is
+added to RT.  The cells are selected from the B the right-hand side is formed
+from, so the term takes the time-integration weights of RT.
 """
+
+import numpy as np
+
 
 from .grid import at
 from .models import rt_local
@@ -62,10 +71,36 @@ def advection_B(B, uc, vc, wc, g):
     return out
 
 
+def determinant(B):
+    """det of the symmetric tensor stored as (xx, xy, xz, yy, yz, zz), by cofactors
+    along the first row."""
+    xx, xy, xz, yy, yz, zz = B
+    return xx * (yy * zz - yz * yz) - xy * (xy * zz - yz * xz) + xz * (xy * yz - yy * xz)
+
+
+def diffusion_cells(B, prm):
+    """Boolean mask of the cells that receive the artificial diffusion (Sec. 3.1)."""
+    mask = determinant(B) < 0.0
+    if prm.model == 'fene_p':
+        mask = mask | (B[0] + B[3] + B[5] >= 0.95 * prm.L2)
+    return mask
+
+
+def centre_laplacian(f, g):
+    """7-point Laplacian of a centred field with the copy ghost rule."""
+    return ((at(f, g, 'c', i=1) - 2.0 * f + at(f, g, 'c', i=-1)) / g.dx ** 2
+            + (at(f, g, 'c', j=1) - 2.0 * f + at(f, g, 'c', j=-1)) / g.dy ** 2
+            + (at(f, g, 'c', k=1) - 2.0 * f + at(f, g, 'c', k=-1)) / g.dz ** 2)
+
+
 def stress_rhs(U, V, W, B, g, prm):
     """RT of Eq. rt (AB2) / the bracket of Eq. RK-rt (RK3) at one time level."""
     uc, vc, wc = centre_velocity(U, V, W, g)
     L = velocity_gradient(U, V, W, g)
     src = rt_local(B, L, prm)
     adv = advection_B(B, uc, vc, wc, g)
-    return [src[c] - adv[c] for c in range(6)]
+    rt = [src[c] - adv[c] for c in range(6)]
+    if getattr(prm, 'art_diff', 0.0) > 0.0:
+        mask = diffusion_cells(B, prm)
+        rt = [rt[c] + np.where(mask, prm.art_diff * centre_laplacian(B[c], g), 0.0) for c in range(6)]
+    return rt
