@@ -64,7 +64,8 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (host monotonic time, csv line)
+        self.window = None
 
     def start(self):
         try:
@@ -78,7 +79,20 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def wait_first(self, timeout=10.0):
+        """Block until nvidia-smi has printed its first sample (its start-up takes
+        longer than a short timed region)."""
+        t0 = time.monotonic()
+        while self.proc is not None and not self.lines and time.monotonic() - t0 < timeout:
+            time.sleep(0.02)
+
+    def begin(self):
+        self.window = [time.monotonic(), None]
+
+    def end(self):
+        self.window[1] = time.monotonic()
 
     def stop(self):
         if self.proc is None:
@@ -90,7 +104,12 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
-        for l in self.lines:
+        lines = self.lines
+        if self.window is not None and self.window[1] is not None:
+            inside = [x for x in lines if self.window[0] <= x[0] <= self.window[1]]
+            # a region shorter than the sampling period: the first sample after it began
+            lines = inside or [x for x in lines if x[0] >= self.window[0]][:1]
+        for _, l in lines:
             parts = [x.strip() for x in l.split(',')]
             if len(parts) < 7:
                 continue
@@ -198,15 +217,18 @@ def run_gpu(args, rank, world, local_rank):
     evp.evp_kernel_times(sim.handle)       # reset counters
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = ClockSampler(local_rank)
+    clocks.start()
+    clocks.wait_first()
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     ev[0].record(stream)
     for k in range(args.steps):
         sim.step(w['dt'])
         ev[k + 1].record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
+    clocks.end()
     barrier()
     clk = clocks.stop()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
@@ -426,7 +448,7 @@ def run_cpu_baseline(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
-    ap.add_argument('--steps', type=int, default=40)
+    ap.add_argument('--steps', type=int, default=400)
     ap.add_argument('--warmup', type=int, default=5)
     ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')

@@ -45,7 +45,7 @@ typedef enum {
     EVP_ERR_OOM = 2,         /* device allocation failed or arena too small         */
     EVP_ERR_CUDA = 3,        /* a CUDA runtime call failed                          */
     EVP_ERR_NONFINITE = 4,   /* a kernel produced NaN/Inf (raised at evp_sync)      */
-    EVP_ERR_UNPHYSICAL = 5,  /* FENE-P tr B >= L^2 or det B < 0 (raised at sync)    */
+    EVP_ERR_UNPHYSICAL = 5,  /* FENE-P tr B >= L^2, or det B < 0 without art_diff (raised at sync) */
     EVP_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                       */
     EVP_ERR_STATE = 7        /* call not valid in the state's configuration         */
 } evp_status;
@@ -112,7 +112,13 @@ typedef struct {
                            u** = (1 - alpha) u* before each projection (Eq. forceAdded),
                            alpha = solid fraction of the control volume around each
                            velocity node, set with EVP_SOLID_X/Y/Z (zero at init)       */
-    double reserved[7];
+    double art_diff;    /* local artificial diffusion of B (Sec. 3.1), 0 = off: where
+                           det B < 0, or tr B >= 0.95 L^2 for FENE-P (tested on the B the
+                           stress right-hand side is formed from), art_diff times the
+                           7-point Laplacian of B is added to that right-hand side.  The
+                           paper gives no value ("tuned" per case).  Explicit: keep
+                           art_diff*dt*(2/dx^2 + 2/dy^2 + 2/dz^2) below about 1          */
+    double reserved[6];
 } evp_params;
 
 /* Field identifiers for evp_set_field / evp_get_field */
@@ -217,9 +223,18 @@ int evp_stress_rhs(evp_state* s, void* rt);
 
 /* Wait for the state's stream.  Returns EVP_ERR_NONFINITE / EVP_ERR_UNPHYSICAL
  * when kernels raised the matching bits since the last sync (bits in *bits),
- * else EVP_OK.  *max_div (may be NULL) receives max |div u| of the last
+ * else EVP_OK.  With art_diff > 0, EVP_BIT_DET_NEG is reported in *bits but is
+ * not an error: det B < 0 is then the condition the diffusion treats.  *max_div (may be NULL) receives max |div u| of the last
  * projection, computed in FP64.  Bits and residual are cleared afterwards.     */
 int evp_sync(evp_state* s, unsigned* bits, double* max_div);
+
+/* Self-test of the current device (the paper has no counterpart): checks the
+ * integer-operation binary32 -> binary64 widening that the FP64 divergence
+ * residual uses against the hardware conversion instruction, bit for bit, over
+ * all 2^32 binary32 patterns.  *mismatches receives the number of differing
+ * results (0 when the device behaves as IEEE 754 specifies).  Synchronous;
+ * allocates 8 bytes.                                                           */
+int evp_selftest(unsigned long long* mismatches);
 
 /* Per-kernel timing with CUDA events on the state's stream (off by default).
  * evp_kernel_times fills up to n entries of accumulated milliseconds and

@@ -198,6 +198,7 @@ int validate(const evp_grid* g, evp_model model, const evp_params* p) {
     if (model != EVP_NEWTONIAN && !(p->Wi > 0)) return fail(EVP_ERR_ARG, "Wi must be positive");
     if (model == EVP_FENE_P && !(p->L2 > 3)) return fail(EVP_ERR_ARG, "FENE-P needs L2 > 3");
     if (model == EVP_SARAMITO && !(p->Bi >= 0)) return fail(EVP_ERR_ARG, "Bi must be >= 0");
+    if (!(p->art_diff >= 0) || !(p->art_diff < 1e300)) return fail(EVP_ERR_ARG, "art_diff must be finite and >= 0");
     if (p->precision != EVP_FP64 && p->precision != EVP_FP32) return fail(EVP_ERR_ARG, "bad precision");
     if (p->integrator != EVP_RK3 && p->integrator != EVP_AB2) return fail(EVP_ERR_ARG, "unknown integrator");
     if (p->integrator == EVP_AB2) {
@@ -792,6 +793,7 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
     s->mc.L2 = params->L2;
     s->mc.a_fene = model == EVP_FENE_P ? params->L2 / (params->L2 - 3.0) : 1.0;
     s->mc.mu_s = params->beta * mu0;
+    s->mc.art_diff = model == EVP_NEWTONIAN ? 0.0 : params->art_diff;
     if (stream) {
         s->st = static_cast<cudaStream_t>(stream);
         s->own_stream = false;
@@ -1031,8 +1033,17 @@ int evp_sync(evp_state* s, unsigned* bits, double* max_div) {
         *max_div = d;
     }
     if (st & EVP_BIT_NONFINITE) return fail(EVP_ERR_NONFINITE, "non-finite values in the fields");
-    if (st & (EVP_BIT_TRACE_LIMIT | EVP_BIT_DET_NEG))
-        return fail(EVP_ERR_UNPHYSICAL, "B lost positive definiteness or reached the FENE-P trace limit");
+    if (st & EVP_BIT_TRACE_LIMIT) return fail(EVP_ERR_UNPHYSICAL, "B reached the FENE-P trace limit");
+    // with the local artificial diffusion on, det B < 0 is the condition it treats
+    if ((st & EVP_BIT_DET_NEG) && !(s->mc.art_diff > 0))
+        return fail(EVP_ERR_UNPHYSICAL, "B lost positive definiteness");
+    return EVP_OK;
+}
+
+int evp_selftest(unsigned long long* mismatches) {
+    if (!mismatches) return fail(EVP_ERR_ARG, "null output");
+    const cudaError_t e = evp::run_selftest(mismatches);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test kernels");
     return EVP_OK;
 }
 

@@ -91,7 +91,22 @@ struct ModelConst {
     double tau_y;       // Saramito yield stress
     double L2, a_fene;  // FENE-P L^2 and a = L^2/(L^2-3)
     double mu_s;        // solvent viscosity
+    double art_diff;    // local artificial diffusivity of B (0: off)
 };
+
+// Exact binary32 -> binary64 widening (IEEE 754) with integer operations, so that
+// FP64 reductions over FP32 fields leave the FP64 pipe to the arithmetic: for a
+// normal number the exponent is rebiased by 1023 - 127 = 896 and the 23-bit
+// fraction moves to the top of the 52-bit one.  Zero, subnormals, infinities and
+// NaN take the conversion instruction.
+__device__ __forceinline__ double widen_f32(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)x;
+    const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double widen_f32(double x) { return x; }
 
 // ------------------------------------------------------------ argument blocks
 template <typename T>
@@ -249,6 +264,9 @@ struct TimingHook {
     void b(int kid) const { if (begin) begin(ctx, kid); }
     void e(int kid) const { if (end) end(ctx, kid); }
 };
+
+// device self-test of widen_f32 (k_selftest.cu)
+cudaError_t run_selftest(unsigned long long* mismatches);
 
 template <typename T>
 cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a,

@@ -332,7 +332,9 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, do
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
     const bool active = i < g.nx && j < g.ny;
-    double dmax = 0.0;
+    // max |div u| kept as the bit pattern of a non-negative double (ordered like
+    // the unsigned integer)
+    unsigned long long dmax_b = 0ull;
     unsigned bits = 0;
     if (active) {
         const T c = a.coef;
@@ -393,11 +395,13 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, do
                 const T Ul = cur.usm - c * ((pc - cur.pxm) * g.idx);
                 const T Vl = bottom ? T(0) : cur.vsm - c * ((pc - cur.pym) * g.idy);
                 const T Wl = ws_m - c * ((pc - psi_m) * g.idz);
-                const double dv = (double(Un) - double(Ul)) * idx_d + (double(Vn) - double(Vl)) * idy_d
-                                  + (double(Wn) - double(Wl)) * idz_d;
-                const double ad = fabs(dv);
-                if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn) || !(ad <= DBL_MAX)) bits |= EVP_BIT_NONFINITE;
-                else dmax = fmax(dmax, ad);
+                const double dv = (widen_f32(Un) - widen_f32(Ul)) * idx_d + (widen_f32(Vn) - widen_f32(Vl)) * idy_d
+                                  + (widen_f32(Wn) - widen_f32(Wl)) * idz_d;
+                const unsigned long long ab = (unsigned long long)__double_as_longlong(dv) & 0x7fffffffffffffffull;
+                // |dv| finite <=> its exponent field is not all ones
+                if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn) || ab >= 0x7ff0000000000000ull)
+                    bits |= EVP_BIT_NONFINITE;
+                else dmax_b = ab > dmax_b ? ab : dmax_b;
             } else if (!isfinite(Un + Vn + Wn)) {
                 bits |= EVP_BIT_NONFINITE;
             }
@@ -407,30 +411,32 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, do
             cur = nxt;
         }
     }
-    __shared__ double red[8];
+    __shared__ unsigned long long red[8];
     __shared__ unsigned rbits[8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, dmax_b, o);
+        dmax_b = other > dmax_b ? other : dmax_b;
         bits |= __shfl_xor_sync(0xffffffffu, bits, o);
     }
     const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
-        red[warp] = dmax;
+        red[warp] = dmax_b;
         rbits[warp] = bits;
     }
     __syncthreads();
     if (warp == 0) {
         const int nw = (blockDim.x * blockDim.y) >> 5;
-        dmax = lane < nw ? red[lane] : 0.0;
+        dmax_b = lane < nw ? red[lane] : 0ull;
         bits = lane < nw ? rbits[lane] : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, dmax_b, o);
+            dmax_b = other > dmax_b ? other : dmax_b;
             bits |= __shfl_xor_sync(0xffffffffu, bits, o);
         }
         if (lane == 0) {
-            if (RESID && dmax > 0.0) atomicMax(a.maxdiv, (unsigned long long)__double_as_longlong(dmax));
+            if (RESID && dmax_b > 0ull) atomicMax(a.maxdiv, dmax_b);
             if (bits) atomicOr(a.status, bits);
         }
     }

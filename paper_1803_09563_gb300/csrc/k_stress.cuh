@@ -2,9 +2,12 @@
 // components of B, the Table 1 closure and the RK3 update of Eq. rk3tau.
 //
 // RT = (a I - F B)/lambda - (u.grad B - B.grad u - grad u^T.B)     (Eq. rt / RK-rt)
+//      [+ kappa_ad lap B where det B < 0 or, FENE-P, tr B >= 0.95 L^2  (Sec. 3.1)]
 // B^k = B^{k-1} + dt (zeta^k RT^{k-1} + xi^k RT^{k-2})            (Eq. rk3tau)
 //
-// z-marching tiles: see the kernel for the data staging.
+// z-marching tiles: see the kernel for the data staging.  The kernel template is
+// instantiated once per precision, in k_stress_f32.cu and k_stress_f64.cu.
+#pragma once
 #include <cfloat>
 
 #include "evp_internal.cuh"
@@ -79,8 +82,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // MODE: 0 = right-hand side only, 1 = update without history read (first RK3
 // substep / first AB2 step), 2 = update reading and writing the history,
-// 3 = update reading the history without writing it (last RK3 substep)
-template <typename T, int MODEL, int MODE>
+// 3 = update reading the history without writing it (last RK3 substep).
+// DIFF: the local artificial diffusion is on (ModelConst::art_diff > 0).
+template <typename T, int MODEL, int MODE, bool DIFF>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chunk) {
     constexpr bool RHS_ONLY = MODE == 0, READ_H = MODE >= 2, WRITE_H = MODE == 1 || MODE == 2;
@@ -189,9 +193,11 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     // RK3 history of this thread's cell in plane kk -> staging buffer kk & 1
     const size_t cell0 = (size_t)j * g.nx + i;
     auto fetch_hist = [&](int kk) {
-        if (!READ_H || !active || kk >= k1) return;
+        if constexpr (READ_H) {
+            if (!active || kk >= k1) return;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) cp_async(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0);
+            for (int c = 0; c < 6; ++c) cp_async(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0);
+        }
     };
     fetch_hist(k0);
     const int ob = (ty + 3) * BW + tx + 3;   // this cell in a B plane
@@ -276,6 +282,17 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             av = F;
         }
 
+        // ---- local artificial diffusion (Sec. 3.1): selected from B^{k-1} of the cell
+        T kad = T(0);
+        if constexpr (DIFF) {
+            const T det0 = w[0][3] * (w[3][3] * w[5][3] - w[4][3] * w[4][3])
+                           - w[1][3] * (w[1][3] * w[5][3] - w[4][3] * w[2][3])
+                           + w[2][3] * (w[1][3] * w[4][3] - w[3][3] * w[2][3]);
+            bool hit = det0 < T(0);
+            if (MODEL == EVP_FENE_P) hit = hit || (w[0][3] + w[3][3] + w[5][3] >= T(0.95) * kL2);
+            kad = hit ? T(mc.art_diff) : T(0);
+        }
+
         // ---- WENO5 advection (stencil direction +1 for a positive velocity), UCD, update
         const int sx = uc > T(0) ? 1 : -1, syw = vc > T(0) ? BW : -BW;
         const bool zpos = wc > T(0);
@@ -298,7 +315,13 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             for (int q = 0; q < 3; ++q) ucd += L[ra][q] * w[symi(q, cb)][3] + w[symi(ra, q)][3] * L[cb][q];
             const bool diag = (c == 0 || c == 3 || c == 5);
             const T src = ((diag ? av : T(0)) - F * w[c][3]) * inv_lam;
-            const T rt = src + ucd - adv;
+            T rt = src + ucd - adv;
+            if (DIFF && kad != T(0)) {
+                const T b0 = w[c][3];
+                rt += kad * ((P[ob - 1] + P[ob + 1] - T(2) * b0) * (g.idx * g.idx)
+                             + (P[ob - BW] + P[ob + BW] - T(2) * b0) * (g.idy * g.idy)
+                             + (w[c][2] + w[c][4] - T(2) * b0) * (g.idz * g.idz));
+            }
             if (RHS_ONLY) {
                 if (active) a.RT[c][cell] = rt;
             } else {
@@ -352,13 +375,15 @@ cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArg
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
     const size_t smem = sizeof(StressSmem<T>);
     const int mode = a.rhs_only ? 0 : (!a.read_hist ? 1 : (a.write_hist ? 2 : 3));
+    const int diff = mc.art_diff > 0.0 ? 1 : 0;
     th.b(K_STRESS);
-    switch (mc.model * 4 + mode) {
-#define EVP_LAUNCH_STRESS(M, MD)                                                                              \
-    case M * 4 + MD:                                                                                          \
-        cudaFuncSetAttribute(k_stress<T, M, MD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
-        k_stress<T, M, MD><<<grid, block, smem, st>>>(g, mc, a, kz);                                          \
+    switch ((mc.model * 4 + mode) * 2 + diff) {
+#define EVP_LAUNCH_STRESS_D(M, MD, D)                                                                         \
+    case (M * 4 + MD) * 2 + D:                                                                                \
+        cudaFuncSetAttribute(k_stress<T, M, MD, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_stress<T, M, MD, D><<<grid, block, smem, st>>>(g, mc, a, kz);                                       \
         break;
+#define EVP_LAUNCH_STRESS(M, MD) EVP_LAUNCH_STRESS_D(M, MD, false) EVP_LAUNCH_STRESS_D(M, MD, true)
         EVP_LAUNCH_STRESS(EVP_OLDROYD_B, 0)
         EVP_LAUNCH_STRESS(EVP_OLDROYD_B, 1)
         EVP_LAUNCH_STRESS(EVP_OLDROYD_B, 2)
@@ -376,15 +401,12 @@ cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArg
         EVP_LAUNCH_STRESS(EVP_NEO_HOOKEAN, 2)
         EVP_LAUNCH_STRESS(EVP_NEO_HOOKEAN, 3)
 #undef EVP_LAUNCH_STRESS
+#undef EVP_LAUNCH_STRESS_D
         default: return cudaErrorInvalidValue;
     }
     th.e(K_STRESS);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_stress<float>(const Geo<float>&, const ModelConst&, const StressArgs<float>&,
-                                          cudaStream_t, const TimingHook&);
-template cudaError_t launch_stress<double>(const Geo<double>&, const ModelConst&, const StressArgs<double>&,
-                                           cudaStream_t, const TimingHook&);
 
 }  // namespace evp

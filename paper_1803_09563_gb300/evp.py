@@ -9,7 +9,7 @@ pointer (``on_device=1``), host arrays by host pointer.
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_size_t, c_uint, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_size_t, c_uint, c_ulonglong, c_void_p
 
 import numpy as np
 
@@ -46,7 +46,7 @@ class evp_params(ctypes.Structure):
                 ('precision', c_int), ('integrator', c_int), ('mu_ratio', c_double), ('ls_eps_cells', c_double),
                 ('sigma', c_double), ('drho_g', c_double), ('reinit_every', c_int), ('reinit_iters', c_int),
                 ('rho_ratio', c_double), ('gravity', c_double), ('penalization', c_int),
-                ('reserved', c_double * 7)]
+                ('art_diff', c_double), ('reserved', c_double * 6)]
 
 
 class EvpError(RuntimeError):
@@ -83,6 +83,7 @@ def load(path=None):
         'evp_stress_rhs': (c_int, [c_void_p, c_void_p]),
         'evp_poisson_solve_static': (c_int, [POINTER(evp_grid), c_int, c_void_p, c_void_p, c_void_p]),
         'evp_sync': (c_int, [c_void_p, POINTER(c_uint), POINTER(c_double)]),
+        'evp_selftest': (c_int, [POINTER(c_ulonglong)]),
         'evp_kernel_timing': (c_int, [c_void_p, c_int]),
         'evp_kernel_times': (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), c_int]),
         'evp_kernel_name': (c_char_p, [c_int]),
@@ -102,7 +103,7 @@ def exported_symbols():
     return ['evp_state_bytes', 'evp_init', 'evp_destroy', 'evp_set_field', 'evp_get_field', 'evp_step',
             'evp_substep', 'evp_project', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_sync', 'evp_kernel_timing',
             'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error', 'evp_poisson_solve_static',
-            'evp_set_graph']
+            'evp_set_graph', 'evp_selftest']
 
 
 def _check(code):
@@ -133,7 +134,7 @@ def make_grid(nx, ny, nz, lx, ly, lz, walls_y=False):
 
 def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_amp=0.0, abc_k=0.0,
                 precision=EVP_FP64, integrator=EVP_RK3, mu_ratio=1.0, ls_eps_cells=1.5, sigma=0.0, drho_g=0.0,
-                reinit_every=10, reinit_iters=3, penalization=0, rho_ratio=0.0, gravity=0.0):
+                reinit_every=10, reinit_iters=3, penalization=0, rho_ratio=0.0, gravity=0.0, art_diff=0.0):
     p = evp_params()
     p.Re, p.Wi, p.beta, p.Bi, p.L2 = float(Re), float(Wi), float(beta), float(Bi), float(L2)
     p.bi_def, p.dpdx, p.abc_amp, p.abc_k = int(bi_def), float(dpdx), float(abc_amp), float(abc_k)
@@ -142,6 +143,7 @@ def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_am
     p.reinit_every, p.reinit_iters = int(reinit_every), int(reinit_iters)
     p.penalization = int(penalization)
     p.rho_ratio, p.gravity = float(rho_ratio), float(gravity)
+    p.art_diff = float(art_diff)
     return p
 
 
@@ -208,6 +210,14 @@ def evp_sync(state, raise_on_error=True):
     if raise_on_error and code not in (EVP_OK,):
         _check(code)
     return code, bits.value, md.value
+
+
+def evp_selftest():
+    """Mismatches of the integer-operation FP32 -> FP64 widening against the
+    device's conversion instruction over all 2^32 patterns (0 expected)."""
+    bad = c_ulonglong(0)
+    _check(load().evp_selftest(ctypes.byref(bad)))
+    return bad.value
 
 
 def evp_kernel_timing(state, enable):

@@ -57,3 +57,27 @@ def test_state_bytes_validates_without_a_gpu(libpath):
     assert 29 * N * 4 <= nb < 40 * N * 4
     bad = evp.make_grid(250, 128, 128, 1.0, 1.0, 1.0, True)
     assert evp.evp_state_bytes(bad, evp.EVP_SARAMITO, p) == 0
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of evp_grid and evp_params have the C layout: a small C
+    program compiled against include/evp.h prints sizeof and every offsetof."""
+    from paper_1803_09563_gb300 import evp
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "evp.h"', 'int main(void) {']
+    for cname, ct in (('evp_grid', evp.evp_grid), ('evp_params', evp.evp_params)):
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in ct._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / 'layout.c'
+    src.write_text('\n'.join(lines))
+    exe = tmp_path / 'layout'
+    subprocess.run(['gcc', '-std=c99', '-I', os.path.join(ROOT, 'include'), str(src), '-o', str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cname, fname, val = line.split()
+        got[(cname, fname)] = int(val)
+    for cname, ct in (('evp_grid', evp.evp_grid), ('evp_params', evp.evp_params)):
+        assert got[(cname, 'sizeof')] == ctypes.sizeof(ct), cname
+        for fname, _ in ct._fields_:
+            assert got[(cname, fname)] == getattr(ct, fname).offset, (cname, fname)

@@ -269,3 +269,88 @@ def test_abc_forcing_fene_p_fp64(evp):
     sim.sync()
     for got, ref in zip(fields(sim, evp), oracle_fields(st)):
         assert rel(got, ref) < 1e-10
+
+
+def defect_conformation(geo, seed, L2):
+    """B near I, with one ball where tr B is about 0.97 L^2 (the FENE-P trace trigger)
+    and one ball where B_xx < 0 (det B < 0); every cell is far from both thresholds."""
+    B = inputs.random_conformation(geo, seed, amp=0.3)
+    y0 = -geo['ly'] / 2 if geo['walls_y'] else 0.0
+    cy = y0 + 0.5 * geo['ly']
+    ball_a = inputs.sphere_distance(geo, (0.3 * geo['lx'], cy, 0.3 * geo['lz']), 0.22 * geo['lz']) < 0
+    ball_b = inputs.sphere_distance(geo, (0.7 * geo['lx'], cy, 0.7 * geo['lz']), 0.22 * geo['lz']) < 0
+    for c in (0, 3, 5):
+        B[c] = np.where(ball_a, B[c] + (0.97 * L2 - 3.0) / 3.0, B[c])
+    B[0] = np.where(ball_b, B[0] - 2.0, B[0])
+    return B, ball_a, ball_b
+
+
+def diffusion_case(evp, shape, precision, art):
+    nx, ny, nz, walls = shape
+    L2 = 60.0
+    sim, st, g, prm = setup_case(evp, shape, 'fene_p', {'L2': L2, 'art_diff': art}, precision)
+    geo = inputs.geometry(nx, ny, nz, g.lx, g.ly, g.lz, walls)
+    B, ball_a, ball_b = defect_conformation(geo, 11, L2)
+    if precision == evp.EVP_FP32:
+        B = [b.astype(np.float32).astype(np.float64) for b in B]
+    sim.set_state(B=B)
+    st.B = [b.copy() for b in B]
+    # both sides select the same cells: no cell within reach of a threshold
+    det = oracle.determinant(B)
+    tr = B[0] + B[3] + B[5]
+    assert ball_a.any() and ball_b.any() and (det < 0).sum() == ball_b.sum()
+    assert np.abs(det).min() > 1e-2 and np.abs(tr - 0.95 * L2).min() > 0.1
+    return sim, st, g, prm
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1]])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_artificial_diffusion_rhs(evp, shape, prec, tol):
+    """Sec. 3.1 local artificial diffusion in the stress right-hand side: FENE-P
+    with cells over 0.95 L^2 and cells with det B < 0."""
+    import torch
+    sim, st, g, prm = diffusion_case(evp, shape, prec, 0.05)
+    out = torch.empty((6,) + sim.shape, dtype=torch.float32 if prec else torch.float64, device='cuda')
+    evp.evp_stress_rhs(sim.handle, out)
+    sim.sync()
+    ref = oracle.stress_rhs(st.U, st.V, st.W, st.B, g, prm)
+    plain = oracle.stress_rhs(st.U, st.V, st.W, st.B, g, oracle.Params.from_groups('fene_p', 2.0, 0.8, 0.4, L2=60.0))
+    assert max(np.abs(r - q).max() for r, q in zip(ref, plain)) > 1e-2   # the term is present
+    for c in range(6):
+        assert rel(out[c].cpu().numpy(), ref[c]) < tol, (c, rel(out[c].cpu().numpy(), ref[c]))
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1]])
+def test_artificial_diffusion_steps_fp64(evp, shape):
+    sim, st, g, prm = diffusion_case(evp, shape, evp.EVP_FP64, 0.02)
+    dt = 1e-3
+    for _ in range(2):
+        sim.step(dt)
+        st = oracle.rk3_step(st, dt, g, prm)
+    code, bits, _ = sim.sync()
+    assert code == evp.EVP_OK and bits & evp.EVP_BIT_DET_NEG     # reported, not an error
+    for f, ref in [(evp.EVP_U, st.U), (evp.EVP_V, st.V), (evp.EVP_W, st.W), (evp.EVP_P, st.p)] + \
+            [(evp.EVP_BXX + c, st.B[c]) for c in range(6)]:
+        assert rel(sim.get(f), ref) < 1e-10, (f, rel(sim.get(f), ref))
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1]])
+def test_fp32_residual_is_the_fp64_divergence_of_the_stored_fields(evp, shape):
+    """The residual evp_sync reports after an FP32 step is max |div u| of the FP32
+    velocity the step stored, evaluated in FP64 (to the rounding of that sum)."""
+    sim, st, g, prm = setup_case(evp, shape, 'saramito', {'Bi': 0.4}, evp.EVP_FP32)
+    for _ in range(2):
+        sim.step(2e-3)
+    code, bits, maxdiv = sim.sync()
+    U, V, W = (sim.get(f).astype(np.float64) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W))
+    host = np.abs(oracle.divergence(U, V, W, g)).max()
+    # the terms are ~|u|/h while their sum is at the FP32 rounding level: allow a
+    # few FP64 ulps of the terms (an FP32-rounded evaluation would be ~1e8 times off)
+    terms = np.abs(U).max() / g.dx + np.abs(V).max() / g.dy + np.abs(W).max() / g.dz
+    assert host > 0 and abs(maxdiv - host) <= 8 * 2.0 ** -52 * terms, (maxdiv, host, terms)
+
+
+def test_device_conversion_selftest(evp):
+    """The integer-operation FP32 -> FP64 widening of the FP64 residual agrees bit
+    for bit with the conversion instruction on every binary32 pattern."""
+    assert evp.evp_selftest() == 0
