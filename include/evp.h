@@ -229,11 +229,14 @@ int evp_stress_rhs(evp_state* s, void* rt);
 int evp_sync(evp_state* s, unsigned* bits, double* max_div);
 
 /* Self-test of the current device (the paper has no counterpart): checks the
- * integer-operation binary32 -> binary64 widening that the FP64 divergence
- * residual uses against the hardware conversion instruction, bit for bit, over
- * all 2^32 binary32 patterns.  *mismatches receives the number of differing
- * results (0 when the device behaves as IEEE 754 specifies).  Synchronous;
- * allocates 8 bytes.                                                           */
+ * integer-operation conversions between binary32 and binary64 that the FP64
+ * divergence residual and the FP32 Thomas sweep use against the hardware
+ * conversion instructions, over all 2^32 binary32 patterns (widening) and 2^30
+ * binary64 patterns around the binary32 range, including every kind of rounding
+ * tie (narrowing).  Results must agree bit for bit, except that values in the
+ * binary32 subnormal range give a signed zero and a NaN gives some NaN.
+ * *mismatches receives the number of failures (0 expected).  Synchronous;
+ * allocates 16 bytes.                                                          */
 int evp_selftest(unsigned long long* mismatches);
 
 /* Per-kernel timing with CUDA events on the state's stream (off by default).

@@ -94,19 +94,50 @@ struct ModelConst {
     double art_diff;    // local artificial diffusivity of B (0: off)
 };
 
-// Exact binary32 -> binary64 widening (IEEE 754) with integer operations, so that
-// FP64 reductions over FP32 fields leave the FP64 pipe to the arithmetic: for a
-// normal number the exponent is rebiased by 1023 - 127 = 896 and the 23-bit
-// fraction moves to the top of the 52-bit one.  Zero, subnormals, infinities and
-// NaN take the conversion instruction.
+// Conversions between binary32 and binary64 (IEEE 754) done branch-free with
+// integer operations, so that FP64 work on FP32 data leaves the (narrow) FP64 pipe
+// to the arithmetic and keeps batched loads free to be scheduled early.  They give
+// the conversion instruction's result bit for bit for every normal number, zero
+// and infinity; values in the binary32 subnormal range (magnitude below 2^-126)
+// become a signed zero on both sides of the conversion (an absolute difference
+// below 1.2e-38), and a NaN stays a NaN.
+
+// binary32 -> binary64: the exponent is rebiased by 1023 - 127 = 896 and the
+// 23-bit fraction moves to the top of the 52-bit one; exponent field 0 gives a
+// signed zero, exponent field 255 (infinity, NaN) stays all ones.
 __device__ __forceinline__ double widen_f32(float x) {
     const unsigned b = __float_as_uint(x);
     const unsigned e = (b >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)x;
-    const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-    return __hiloint2double((int)hi, (int)(b << 29));
+    const unsigned sign = b & 0x80000000u;
+    const unsigned E = e == 0xffu ? 0x7ffu : e + 896u;
+    const unsigned hi = e ? (sign | (E << 20) | ((b & 0x7fffffu) >> 3)) : sign;
+    const unsigned lo = e ? (b << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ double widen_f32(double x) { return x; }
+
+// binary64 -> binary32, rounding to nearest with ties to even.  Where the result
+// is a normal float (biased exponent 897..1150 of x) the 29 dropped fraction bits
+// decide the increment, and a carry out of the fraction moves into the exponent
+// (up to infinity, as rounding to nearest does).  Magnitudes below 2^-126 give a
+// signed zero, larger exponents infinity, and a NaN gives the quiet NaN.
+__device__ __forceinline__ float narrow_f64(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    const unsigned sign = hi & 0x80000000u;
+    const unsigned keep = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) ? 1u : 0u;
+    const bool nan = e == 0x7ffu && ((hi & 0xfffffu) | lo);
+    unsigned r = sign + ((e - 896u) << 23) + keep + up;
+    r = e < 897u ? sign : r;
+    r = e > 1150u ? (sign | 0x7f800000u) : r;
+    r = nan ? (sign | 0x7fc00000u) : r;
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ float narrow_to(double x, float*) { return narrow_f64(x); }
+__device__ __forceinline__ double narrow_to(double x, double*) { return x; }
 
 // ------------------------------------------------------------ argument blocks
 template <typename T>
@@ -265,7 +296,7 @@ struct TimingHook {
     void e(int kid) const { if (end) end(ctx, kid); }
 };
 
-// device self-test of widen_f32 (k_selftest.cu)
+// device self-test of widen_f32 / narrow_f64 (k_selftest.cu)
 cudaError_t run_selftest(unsigned long long* mismatches);
 
 template <typename T>

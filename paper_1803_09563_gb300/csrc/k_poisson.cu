@@ -270,10 +270,13 @@ template <typename T>
 __global__ void __launch_bounds__(128)
 k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, double idy2) {
     const int nxh = g.nx / 2 + 1, ny = g.ny, nz = g.nz;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // 2*kx + part
-    const int kx = t >> 1, part = t & 1;
-    const int kz = blockIdx.y;
-    if (kx >= nxh) return;
+    // one thread per (kz, kx, real or imaginary part), numbered densely so that no
+    // warp runs with few active lanes
+    const int row = 2 * nxh;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= row * nz) return;
+    const int kz = gid / row, t = gid - kz * row;             // t = 2*kx + part
+    const int kx = t >> 1;
     const int kzh = kz <= nz - kz ? kz : nz - kz;
     const bool pinned = (kx == 0 && kz == 0);
     const double2* M = tb.thomas_m + (size_t)kzh * ny * nxh + kx;         // (m_j, c'_j)
@@ -289,7 +292,7 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, double i
 #pragma unroll
         for (int u = 0; u < RB; ++u) {
             const int jj = jb + u;
-            rr[u] = jj < ny ? double(col[jj * rs]) : 0.0;
+            rr[u] = jj < ny ? widen_f32(col[jj * rs]) : 0.0;
             mm[u] = jj < ny ? __ldg(&M[(size_t)jj * nxh].x) : 0.0;
         }
 #pragma unroll
@@ -303,7 +306,7 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, double i
         }
     }
     double x = d;
-    col[(ny - 1) * rs] = T(x);
+    col[(ny - 1) * rs] = narrow_to(x, (T*)nullptr);
     for (int jt = ny - 2; jt >= 0; jt -= RB) {
         double dd[RB], cc[RB];
 #pragma unroll
@@ -317,7 +320,7 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, double i
             const int jj = jt - u;
             if (jj < 0) break;
             x = dd[u] - cc[u] * x;
-            col[jj * rs] = T(x);
+            col[jj * rs] = narrow_to(x, (T*)nullptr);
         }
     }
 }
@@ -498,8 +501,10 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
         k_fft_col<T, false, true><<<gc, bc, sm, st>>>(g, tb, a, 1, (size_t)nxh, (size_t)ny * nxh, tk);
         th.e(K_SOLVE_Y);
     } else {
-        const int tt = 128;
-        dim3 gt((2 * nxh + tt - 1) / tt, nz);
+        // warp-sized blocks spread the chains evenly over the SMs
+        const int tt = 32;
+        const int chains = 2 * nxh * nz;
+        dim3 gt((chains + tt - 1) / tt);
         th.b(K_THOMAS);
         k_thomas<T><<<gt, tt, 0, st>>>(g, tb, a, tb.idy2);
         th.e(K_THOMAS);

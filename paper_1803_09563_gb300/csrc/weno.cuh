@@ -12,8 +12,11 @@ namespace evp {
 //  * the indicators use the second differences a_k and b_k of the differences;
 //    eps and all three indicators are scaled by 12/13 (a common factor of
 //    eps + S_k cancels in the normalised weights);
-//  * the weights alpha_k = d_k/e_k^2 are multiplied through by 10 e_1^2 e_2^2 e_3^2,
-//    which leaves one division.
+//  * in double precision the weights alpha_k = d_k/e_k^2 are multiplied through by
+//    10 e_1^2 e_2^2 e_3^2, which leaves one division;
+//  * in single precision those products could overflow, so the weights are formed
+//    from three fast reciprocals of the squared indicators (no branch; an
+//    indicator beyond ~1e19 gets a zero weight).
 template <typename T>
 __device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5, T scale) {
     const T eps = T(1.0e-6 * 12.0 / 13.0), r = T(3.0 / 13.0);
@@ -31,17 +34,16 @@ __device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5, T scale) {
     s1 *= s1;
     s2 *= s2;
     s3 *= s3;
-    const T w1 = s2 * s3, w2 = s1 * s3, w3 = s1 * s2;
-    T den = fma(T(3), w3, fma(T(6), w2, w1));
-    T num = fma(w3, q3, fma(w2, q2, w1 * q1)) * scale;
     if (sizeof(T) == 4) {
-        // single precision: CUDA's fast division holds to 2 ulp while the divisor
-        // stays below 2^126; beyond that (products near overflow) use the
-        // three-division form
-        if (den <= T(8.5e37)) return __fdividef(float(num), float(den));
-        const T x1 = T(1) / s1, x2 = T(1) / s2, x3 = T(1) / s3;
-        return (x1 * q1 + x2 * q2 + x3 * q3) * scale / (x1 + T(6) * x2 + T(3) * x3);
+        const float x1 = __fdividef(1.0f, float(s1)), x2 = __fdividef(1.0f, float(s2)),
+                    x3 = __fdividef(1.0f, float(s3));
+        const float num = fmaf(x3, float(q3), fmaf(x2, float(q2), x1 * float(q1))) * float(scale);
+        const float den = fmaf(3.0f, x3, fmaf(6.0f, x2, x1));
+        return T(__fdividef(num, den));
     }
+    const T w1 = s2 * s3, w2 = s1 * s3, w3 = s1 * s2;
+    const T den = fma(T(3), w3, fma(T(6), w2, w1));
+    const T num = fma(w3, q3, fma(w2, q2, w1 * q1)) * scale;
     return num / den;
 }
 

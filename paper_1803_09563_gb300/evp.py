@@ -213,8 +213,8 @@ def evp_sync(state, raise_on_error=True):
 
 
 def evp_selftest():
-    """Mismatches of the integer-operation FP32 -> FP64 widening against the
-    device's conversion instruction over all 2^32 patterns (0 expected)."""
+    """Failures of the integer-operation FP32 <-> FP64 conversions against the
+    device's conversion instructions (0 expected)."""
     bad = c_ulonglong(0)
     _check(load().evp_selftest(ctypes.byref(bad)))
     return bad.value

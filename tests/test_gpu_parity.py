@@ -351,6 +351,7 @@ def test_fp32_residual_is_the_fp64_divergence_of_the_stored_fields(evp, shape):
 
 
 def test_device_conversion_selftest(evp):
-    """The integer-operation FP32 -> FP64 widening of the FP64 residual agrees bit
-    for bit with the conversion instruction on every binary32 pattern."""
+    """The integer-operation FP32 <-> FP64 conversions of the FP64 residual and the
+    FP32 Thomas sweep agree with the conversion instructions (bit for bit outside
+    the binary32 subnormal range)."""
     assert evp.evp_selftest() == 0
