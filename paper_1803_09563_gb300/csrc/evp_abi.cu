@@ -351,30 +351,8 @@ int upload_tables(evp_state* s) {
         CK(put(s->trig, t));
     }
     if (g.walls_y) {
-        // Thomas pivots m_j = 1/(b_j - a_j c'_{j-1}), c'_j = u_j m_j, per (kz <= nz/2, kx)
-        const int ny = g.ny, nkz = g.nz / 2 + 1;
-        const double idy2 = 1.0 / (dy * dy);
-        std::vector<double> lzf = lam(g.nz, nkz, dz);
-        std::vector<double> M((size_t)nkz * ny * nxh * 2);
-        for (int kz = 0; kz < nkz; ++kz)
-            for (int kx = 0; kx < nxh; ++kx) {
-                const double lm = lx[kx] + lzf[kz];
-                const bool pinned = (kx == 0 && kz == 0);
-                double cprev = 0.0;
-                for (int j = 0; j < ny; ++j) {
-                    const double lo = j > 0 ? idy2 : 0.0;
-                    double up = j < ny - 1 ? idy2 : 0.0;
-                    double d = -2.0 * idy2 - lm + (j == 0 ? idy2 : 0.0) + (j == ny - 1 ? idy2 : 0.0);
-                    if (pinned && j == 0) {
-                        d = 1.0;
-                        up = 0.0;
-                    }
-                    const double m = 1.0 / (d - lo * cprev);
-                    cprev = up * m;
-                    M[2 * (((size_t)kz * ny + j) * nxh + kx)] = m;
-                    M[2 * (((size_t)kz * ny + j) * nxh + kx) + 1] = cprev;
-                }
-            }
+        // FP64 Thomas table (m_j, e_j) per (kz <= nz/2, kx)
+        const std::vector<double> M = thomas_table(g.ny, g.nz, nxh, dy, lx, lam(g.nz, g.nz / 2 + 1, dz));
         CK(cudaMemcpyAsync(s->thomas_m, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
     }
     return cudaStreamSynchronize(s->st) == cudaSuccess ? EVP_OK : cuda_fail(cudaGetLastError(), "tables");

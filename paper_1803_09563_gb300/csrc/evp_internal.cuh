@@ -8,6 +8,8 @@
 
 #include "evp.h"
 
+#include <vector>
+
 namespace evp {
 
 template <typename T> struct Cplx;
@@ -186,7 +188,7 @@ struct FFTTables {
     const T* lamy;
     const T* lamz;
     const double2* thomas_m;  // walls: (m_j, c'_j) per system, [nz/2+1][ny][nxh]
-    double idy2;              // 1/dy^2 in FP64 (Thomas off-diagonals)
+    double idy2;              // walls: 1/dy^2 in FP64 (the Thomas sub-diagonal)
 };
 
 template <typename T>
@@ -295,6 +297,40 @@ struct TimingHook {
     void b(int kid) const { if (begin) begin(ctx, kid); }
     void e(int kid) const { if (end) end(ctx, kid); }
 };
+
+// Host: the FP64 Thomas table for the wall-bounded Poisson solve.  For every
+// (kz <= nz/2, kx) system of size ny (rows idy2 psi_{j-1} - (2 idy2 + lx + lz)
+// psi_j + idy2 psi_{j+1}, Neumann rows at both ends, the (0, 0) system pinned by
+// psi_0 = 0) entry j holds (m_j, c'_j): the reciprocal pivot m_j = 1/(b_j - a_j c'_{j-1})
+// and the normalised super-diagonal c'_j = u_j m_j (0 on the last and the pinned
+// row).  Layout [kz][j][kx] as interleaved (m, c') pairs.
+inline std::vector<double> thomas_table(int ny, int nz, int nxh, double dy, const std::vector<double>& lamx,
+                                        const std::vector<double>& lamz_half) {
+    const int nkz = nz / 2 + 1;
+    const double idy2 = 1.0 / (dy * dy);
+    std::vector<double> M((size_t)nkz * ny * nxh * 2);
+    for (int kz = 0; kz < nkz; ++kz)
+        for (int kx = 0; kx < nxh; ++kx) {
+            const double lm = lamx[kx] + lamz_half[kz];
+            const bool pinned = (kx == 0 && kz == 0);
+            double cprev = 0.0;
+            for (int j = 0; j < ny; ++j) {
+                const double lo = j > 0 ? idy2 : 0.0;
+                double up = j < ny - 1 ? idy2 : 0.0;
+                double d = -2.0 * idy2 - lm + (j == 0 ? idy2 : 0.0) + (j == ny - 1 ? idy2 : 0.0);
+                if (pinned && j == 0) {
+                    d = 1.0;
+                    up = 0.0;
+                }
+                const double m = 1.0 / (d - lo * cprev);
+                cprev = up * m;
+                const size_t o = 2 * (((size_t)kz * ny + j) * nxh + kx);
+                M[o] = m;
+                M[o + 1] = cprev;
+            }
+        }
+    return M;
+}
 
 // device self-test of widen_f32 / narrow_f64 (k_selftest.cu)
 cudaError_t run_selftest(unsigned long long* mismatches);

@@ -117,29 +117,7 @@ int upload_static_tables(const evp_grid& g, unsigned char* base, const StaticLay
     if ((e = put(L.lamy, lam(g.ny, g.ny, dy))) != cudaSuccess) return EVP_ERR_CUDA;
     if ((e = put(L.lamz, lam(g.nz, g.nz, dz))) != cudaSuccess) return EVP_ERR_CUDA;
     if (g.walls_y) {
-        const int ny = g.ny, nkz = g.nz / 2 + 1;
-        const double idy2 = 1.0 / (dy * dy);
-        const std::vector<double> lz = lam(g.nz, nkz, dz);
-        std::vector<double> M((size_t)nkz * ny * nxh * 2);
-        for (int kz = 0; kz < nkz; ++kz)
-            for (int kx = 0; kx < nxh; ++kx) {
-                const double lm = lx[kx] + lz[kz];
-                const bool pinned = (kx == 0 && kz == 0);
-                double cprev = 0.0;
-                for (int j = 0; j < ny; ++j) {
-                    const double lo = j > 0 ? idy2 : 0.0;
-                    double up = j < ny - 1 ? idy2 : 0.0;
-                    double d = -2.0 * idy2 - lm + (j == 0 ? idy2 : 0.0) + (j == ny - 1 ? idy2 : 0.0);
-                    if (pinned && j == 0) {
-                        d = 1.0;
-                        up = 0.0;
-                    }
-                    const double m = 1.0 / (d - lo * cprev);
-                    cprev = up * m;
-                    M[2 * (((size_t)kz * ny + j) * nxh + kx)] = m;
-                    M[2 * (((size_t)kz * ny + j) * nxh + kx) + 1] = cprev;
-                }
-            }
+        const std::vector<double> M = thomas_table(g.ny, g.nz, nxh, dy, lx, lam(g.nz, g.nz / 2 + 1, dz));
         if ((e = cudaMemcpyAsync(base + L.thm, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
             return EVP_ERR_CUDA;

@@ -61,8 +61,9 @@ __device__ C<T>* fft_smem(C<T>* a, C<T>* b, int n, const int* rad, int nst, cons
         const int R = rad[s];
         const int nR = n / R;
         const int tws = n / (Ns * R);
+        const bool pow2 = (Ns & (Ns - 1)) == 0;
         for (int jb = tj; jb < nR; jb += nj) {
-            const int kk = jb % Ns;
+            const int kk = pow2 ? (jb & (Ns - 1)) : jb % Ns;
             const int dbase = (jb - kk) * R + kk;
             const C<T> w1 = __ldg(tw + kk * tws);
             if (R == 4) {
@@ -118,15 +119,38 @@ __device__ C<T>* fft_smem(C<T>* a, C<T>* b, int n, const int* rad, int nst, cons
     return a;
 }
 
-// right-hand side value of real line L (= k*ny + j) at x index i
+// Rows that the divergence of real line L (= k*ny + j) reads: u*, v*, w* of the
+// line itself, v* of the row below (null at a wall: the face below j = 0 carries
+// v = 0) and w* of the plane below (periodic in z).
 template <typename T>
-__device__ __forceinline__ T rhs_value(const Geo<T>& g, const PoissonArgs<T>& a, int L, int i) {
-    if (a.rhs) return __ldg(a.rhs + (size_t)L * g.nx + i);
-    const int j = L % g.ny, k = L / g.ny;
-    const size_t c0 = (size_t)L * g.nx + i;
-    const T du = __ldg(a.Us + c0) - ld_uw(g, a.Us, i - 1, j, k);
-    const T dv = __ldg(a.Vs + c0) - ld_v(g, a.Vs, i, j - 1, k);
-    const T dw = __ldg(a.Ws + c0) - ld_uw(g, a.Ws, i, j, k - 1);
+struct DivRows {
+    const T* u;
+    const T* v;
+    const T* vm;
+    const T* w;
+    const T* wm;
+};
+template <typename T>
+__device__ __forceinline__ DivRows<T> div_rows(const Geo<T>& g, const PoissonArgs<T>& a, int L) {
+    const int k = L / g.ny, j = L - k * g.ny;
+    const size_t o = (size_t)L * g.nx;
+    DivRows<T> r;
+    r.u = a.Us + o;
+    r.v = a.Vs + o;
+    r.w = a.Ws + o;
+    const int jm = j > 0 ? j - 1 : (g.walls ? -1 : g.ny - 1);
+    r.vm = jm < 0 ? nullptr : a.Vs + ((size_t)k * g.ny + jm) * g.nx;
+    const int km = k > 0 ? k - 1 : g.nz - 1;
+    r.wm = a.Ws + ((size_t)km * g.ny + j) * g.nx;
+    return r;
+}
+// r = div(u*) * rscale at x index i of the line whose rows are ``r``
+template <typename T>
+__device__ __forceinline__ T div_value(const Geo<T>& g, const PoissonArgs<T>& a, const DivRows<T>& r, int i) {
+    const int im = i > 0 ? i - 1 : g.nx - 1;
+    const T du = __ldg(r.u + i) - __ldg(r.u + im);
+    const T dv = __ldg(r.v + i) - (r.vm ? __ldg(r.vm + i) : T(0));
+    const T dw = __ldg(r.w + i) - __ldg(r.wm + i);
     return (du * g.idx + dv * g.idy + dw * g.idz) * a.rscale;
 }
 
@@ -140,15 +164,21 @@ k_div_fftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np
     C<T>* sb = sa + (size_t)np * nx;
     const int NL = g.ny * g.nz;
     const int q0 = blockIdx.x * np;
-#pragma unroll 2
     for (int l = threadIdx.y; l < np; l += blockDim.y) {
         const int L0 = 2 * (q0 + l), L1 = L0 + 1;
-#pragma unroll 4
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            const T r0 = L0 < NL ? rhs_value(g, a, L0, i) : T(0);
-            const T r1 = L1 < NL ? rhs_value(g, a, L1, i) : T(0);
-            sa[(size_t)l * nx + i] = mk<T>(r0, r1);
+        C<T>* dst = sa + (size_t)l * nx;
+        if (a.rhs) {
+            // explicit right-hand side (the plain Poisson solve)
+            for (int i = threadIdx.x; i < nx; i += blockDim.x)
+                dst[i] = mk<T>(L0 < NL ? __ldg(a.rhs + (size_t)L0 * nx + i) : T(0),
+                               L1 < NL ? __ldg(a.rhs + (size_t)L1 * nx + i) : T(0));
+            continue;
         }
+        const bool ok0 = L0 < NL, ok1 = L1 < NL;
+        const DivRows<T> r0 = div_rows(g, a, ok0 ? L0 : 0), r1 = div_rows(g, a, ok1 ? L1 : 0);
+#pragma unroll 4
+        for (int i = threadIdx.x; i < nx; i += blockDim.x)
+            dst[i] = mk<T>(ok0 ? div_value(g, a, r0, i) : T(0), ok1 ? div_value(g, a, r1, i) : T(0));
     }
     __syncthreads();
     C<T>* res = fft_smem<T, false>(sa, sb, nx, tb.radx, tb.nrx, tb.twx, np, 1, nx, threadIdx.x, blockDim.x,
@@ -262,16 +292,18 @@ k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axi
 //   psi_{j-1}/dy^2 - (2/dy^2 + lx + lz) psi_j + psi_{j+1}/dy^2 = r_j
 // with Neumann rows at j = 0 and ny-1 and the (0, 0) system pinned by psi_0 = 0,
 // in FP64.  Real and imaginary parts are independent recurrences with the same
-// real coefficients: one thread per (system, part).  m_j = 1/(b_j - a_j c'_{j-1})
-// and c'_j come from a host-built FP64 table; the forward-sweep values d'_j go to
-// an FP64 scratch in global memory (L2-resident) for the back substitution.  The
-// FFT normalisation is applied later, in the inverse x pass.
+// real coefficients: one thread per (system, part), numbered densely over
+// (kz, kx, part) in warp-sized blocks.  m_j = 1/(b_j - a_j c'_{j-1}) and c'_j come
+// from a host-built FP64 table; the forward-sweep values d'_j go to an FP64
+// scratch in global memory for the back substitution.  Rows are handled in
+// batches of TB whose loads are issued one batch ahead, so the recurrence does
+// not wait on a memory round trip per row; rows that do not fill a batch are
+// done one by one.  The FFT normalisation is applied later, in the inverse x pass.
 template <typename T>
-__global__ void __launch_bounds__(128)
-k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, double idy2) {
+__global__ void __launch_bounds__(32)
+k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+    constexpr int TB = 16;
     const int nxh = g.nx / 2 + 1, ny = g.ny, nz = g.nz;
-    // one thread per (kz, kx, real or imaginary part), numbered densely so that no
-    // warp runs with few active lanes
     const int row = 2 * nxh;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= row * nz) return;
@@ -283,44 +315,95 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, double i
     T* col = reinterpret_cast<T*>(a.spec + (size_t)kz * ny * nxh) + t;    // this part of (kx, kz)
     double* D = a.scratch + (size_t)kz * ny * (2 * nxh) + t;
     const size_t rs = 2 * (size_t)nxh;                                    // row stride in T / double
-    // rows are processed in batches of RB with their loads issued up front, so the
-    // FP64 recurrence does not wait on one memory round trip per row
-    constexpr int RB = 8;
+    const size_t ms = (size_t)nxh;                                        // row stride of the table
+    const double idy2 = tb.idy2;
+
+    // ---- forward: d'_j = (r_j - idy2 d'_{j-1}) m_j, d'_0 = r_0 m_0
+    const int nfull = ny / TB * TB;
     double d = 0.0;
-    for (int jb = 0; jb < ny; jb += RB) {
-        double rr[RB], mm[RB];
+    T rf[TB];
+    double mm[TB];
+    if (nfull > 0) {
 #pragma unroll
-        for (int u = 0; u < RB; ++u) {
-            const int jj = jb + u;
-            rr[u] = jj < ny ? widen_f32(col[jj * rs]) : 0.0;
-            mm[u] = jj < ny ? __ldg(&M[(size_t)jj * nxh].x) : 0.0;
+        for (int u = 0; u < TB; ++u) {
+            rf[u] = col[u * rs];
+            mm[u] = __ldg(&M[u * ms].x);
+        }
+    }
+    for (int jb = 0; jb < nfull; jb += TB) {
+        T rn[TB];
+        double mn[TB];
+        const bool more = jb + TB < nfull;
+        if (more) {
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+                rn[u] = col[(jb + TB + u) * rs];
+                mn[u] = __ldg(&M[(jb + TB + u) * ms].x);
+            }
         }
 #pragma unroll
-        for (int u = 0; u < RB; ++u) {
+        for (int u = 0; u < TB; ++u) {
             const int jj = jb + u;
-            if (jj >= ny) break;
-            const double r = (pinned && jj == 0) ? 0.0 : rr[u];
+            const double r = (pinned && jj == 0) ? 0.0 : widen_f32(rf[u]);
             const double lo = jj > 0 ? idy2 : 0.0;
             d = (r - lo * d) * mm[u];
             D[jj * rs] = d;
         }
+        if (more) {
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+                rf[u] = rn[u];
+                mm[u] = mn[u];
+            }
+        }
     }
+    for (int jj = nfull; jj < ny; ++jj) {
+        const double r = (pinned && jj == 0) ? 0.0 : widen_f32(col[jj * rs]);
+        const double lo = jj > 0 ? idy2 : 0.0;
+        d = (r - lo * d) * __ldg(&M[jj * ms].x);
+        D[jj * rs] = d;
+    }
+
+    // ---- back substitution: psi_{ny-1} = d'_{ny-1}, psi_j = d'_j - c'_j psi_{j+1}
     double x = d;
     col[(ny - 1) * rs] = narrow_to(x, (T*)nullptr);
-    for (int jt = ny - 2; jt >= 0; jt -= RB) {
-        double dd[RB], cc[RB];
+    // the top rows that do not fill a batch, then full batches down to row 0
+    const int top = ny - 2;
+    const int nrest = (ny - 1) % TB;
+    for (int jj = top; jj > top - nrest; --jj) {
+        x = D[jj * rs] - __ldg(&M[jj * ms].y) * x;
+        col[jj * rs] = narrow_to(x, (T*)nullptr);
+    }
+    const int jstart = top - nrest;                 // first row of the first full batch (from the top)
+    if (jstart >= 0) {
+        double dd[TB], cc[TB];
 #pragma unroll
-        for (int u = 0; u < RB; ++u) {
-            const int jj = jt - u;
-            dd[u] = jj >= 0 ? D[jj * rs] : 0.0;
-            cc[u] = jj >= 0 ? __ldg(&M[(size_t)jj * nxh].y) : 0.0;
+        for (int u = 0; u < TB; ++u) {
+            dd[u] = D[(jstart - u) * rs];
+            cc[u] = __ldg(&M[(jstart - u) * ms].y);
         }
+        for (int jt = jstart; jt >= 0; jt -= TB) {
+            double dn[TB], cn[TB];
+            const bool more = jt - TB >= 0;
+            if (more) {
 #pragma unroll
-        for (int u = 0; u < RB; ++u) {
-            const int jj = jt - u;
-            if (jj < 0) break;
-            x = dd[u] - cc[u] * x;
-            col[jj * rs] = narrow_to(x, (T*)nullptr);
+                for (int u = 0; u < TB; ++u) {
+                    dn[u] = D[(jt - TB - u) * rs];
+                    cn[u] = __ldg(&M[(jt - TB - u) * ms].y);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+                x = dd[u] - cc[u] * x;
+                col[(jt - u) * rs] = narrow_to(x, (T*)nullptr);
+            }
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < TB; ++u) {
+                    dd[u] = dn[u];
+                    cc[u] = cn[u];
+                }
+            }
         }
     }
 }
@@ -506,7 +589,7 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
         const int chains = 2 * nxh * nz;
         dim3 gt((chains + tt - 1) / tt);
         th.b(K_THOMAS);
-        k_thomas<T><<<gt, tt, 0, st>>>(g, tb, a, tb.idy2);
+        k_thomas<T><<<gt, tt, 0, st>>>(g, tb, a);
         th.e(K_THOMAS);
     }
     // ---- inverse z
