@@ -143,8 +143,9 @@ size_t evp_state_bytes(const evp_grid* grid, evp_model model, const evp_params* 
  *   stream: a cudaStream_t, or NULL to let the state create its own stream.
  *   arena:  NULL to let the library allocate evp_state_bytes() on the device,
  *           or a caller-owned device buffer of at least arena_bytes >=
- *           evp_state_bytes(); the caller keeps ownership and must keep it alive
- *           until evp_destroy.  The state never retains any other caller pointer.
+ *           evp_state_bytes(), 256-byte aligned (as cudaMalloc returns); the
+ *           caller keeps ownership and must keep it alive until evp_destroy.
+ *           The state never retains any other caller pointer.
  * Errors: EVP_ERR_ARG (bad sizes/model/params), EVP_ERR_OOM, EVP_ERR_CUDA.    */
 int evp_init(const evp_grid* grid, evp_model model, const evp_params* params,
              void* stream, void* arena, size_t arena_bytes, evp_state** out);

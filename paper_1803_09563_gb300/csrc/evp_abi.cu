@@ -790,6 +790,11 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
             delete s;
             return fail(EVP_ERR_OOM, "arena smaller than evp_state_bytes()");
         }
+        if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) {
+            if (s->own_stream) cudaStreamDestroy(s->st);
+            delete s;
+            return fail(EVP_ERR_ARG, "arena must be 256-byte aligned");
+        }
         s->arena = static_cast<char*>(arena);
         s->own_arena = false;
     } else {

@@ -14,7 +14,11 @@
 // A 32 x 8 tile walks a chunk of z planes.  Shared memory holds planes k-1..k+1
 // (1-cell x-y halo) of u, v, w (4-slot ring, refilled by cp.async), of the summed
 // stress S = tau^k + tau^{k-1} (3-slot ring, built from raw B planes staged by
-// cp.async) and of p, plus the cell's momentum history.
+// cp.async) and of p, plus the cell's momentum history.  A plane row is 40 wide
+// with the tile's interior at columns 4..35, so that when nx is a multiple of
+// 16 bytes' worth of elements every row is staged in 16-byte cp.async chunks
+// (x = i0-4 .. i0+35, wrapped periodically chunk by chunk); other grids stage
+// element by element.
 #include "evp_internal.cuh"
 
 namespace evp {
@@ -22,8 +26,10 @@ namespace evp {
 namespace {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int VW = TX + 2, VH = TY + 2, VPL = VW * VH;   // plane with 1-cell halo
-constexpr int NV = (VPL + NT - 1) / NT;                  // plane cells per thread (2)
+constexpr int VW = TX + 8, XO = 4;                       // plane row width; column of the tile's i0
+constexpr int VH = TY + 2, VPL = VW * VH;                // rows j0-1 .. j0+8
+constexpr int SW = TX + 2;                               // columns the stencils use: XO-1 .. XO+TX
+constexpr int NV = (SW * VH + NT - 1) / NT;              // used plane cells per thread (2)
 
 template <typename T>
 __device__ __forceinline__ T sq(T x) { return x * x; }
@@ -34,6 +40,12 @@ __device__ __forceinline__ int pmod(int a, int n) {
 }
 // a in [-n, 2n): one conditional wrap, no division
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// 16-byte asynchronous copy (L2 only)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
@@ -55,7 +67,8 @@ struct MomSmem {
     T H[2][3][NT];       // momentum history of the tile's cells, planes k and k+1
 };
 
-template <typename T, int MODEL>
+// VEC: rows are staged in 16-byte chunks (needs nx * sizeof(T) % 16 == 0)
+template <typename T, int MODEL, bool VEC>
 __global__ void __launch_bounds__(NT, 1)
 k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_chunk) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -68,47 +81,109 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     const size_t plane = (size_t)g.nx * g.ny;
     const bool stress = MODEL != EVP_NEWTONIAN;
 
-    // per-thread plane cells: offsets for centred fields (copy ghosts) and for
-    // u, w (odd ghosts) / v (zero outside) with their ghost factors
+    // Row ghost rules (walls): centred fields copy the nearest row; u and w take
+    // the odd mirror (no slip), v is zero outside the stored faces.  Periodic y
+    // wraps.  For plane row y (= j0-1+r) returns the source row and the factor
+    // (+1 copy, -1 negated copy, 0 zero) of velocity component q, or of a centred
+    // field for q = 3.
+    auto row_rule = [&](int gy, int q, int& src) -> int {
+        if (!g.walls) {
+            src = pmod(gy, g.ny);
+            return 1;
+        }
+        if (q == 3) {
+            src = min(max(gy, 0), g.ny - 1);
+            return 1;
+        }
+        const bool inside = gy >= 0 && gy < g.ny;
+        if (q == 1) {
+            src = inside ? gy : 0;
+            return inside ? 1 : 0;
+        }
+        const int my = gy < 0 ? -1 - gy : (gy >= g.ny ? 2 * g.ny - 1 - gy : gy);
+        src = min(max(my, 0), g.ny - 1);
+        return (my >= 0 && my < g.ny) ? (inside ? 1 : -1) : 0;
+    };
+
+    // element-wise staging: this thread's used plane cells (row r, column XO-1+c)
     size_t coff[NV], voff[3][NV];
     signed char vfac[3][NV];
     int psm[NV];
+    // chunk staging: this thread's 16-byte chunk of a plane (row ch / CPR)
+    constexpr int E = 16 / (int)sizeof(T);                // elements per chunk
+    constexpr int CPR = VW / E, NCH = CPR * VH;           // chunks per row / plane
+    int csm = -1;
+    size_t ccoff = 0, cvoff[3] = {0, 0, 0};
+    signed char cvfac[3] = {0, 0, 0};
+    if (VEC) {
+        if (tid < NCH) {
+            const int r = tid / CPR, q0 = (tid - r * CPR) * E;
+            csm = r * VW + q0;
+            const int gx = pmod(i0 - XO + q0, g.nx);      // a whole chunk: nx is a multiple of E
+            int src;
+            row_rule(j0 - 1 + r, 3, src);
+            ccoff = (size_t)src * g.nx + gx;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                cvfac[q] = (signed char)row_rule(j0 - 1 + r, q, src);
+                cvoff[q] = (size_t)src * g.nx + gx;
+            }
+        }
+    }
 #pragma unroll
     for (int r = 0; r < NV; ++r) {
         const int e = tid + r * NT;
-        psm[r] = e < VPL ? e : -1;
-        const int vy = e / VW, vx = e % VW;
-        const int gx = pmod(i0 + vx - 1, g.nx);
-        const int gy = j0 + vy - 1;
+        const int vy = e / SW, vx = e - vy * SW;
+        psm[r] = e < SW * VH ? vy * VW + vx + XO - 1 : -1;
         coff[r] = 0;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             voff[q][r] = 0;
             vfac[q][r] = 0;
         }
-        if (e >= VPL) continue;
-        if (!g.walls) {
-            const int y = pmod(gy, g.ny);
-            coff[r] = (size_t)y * g.nx + gx;
+        if (VEC || e >= SW * VH) continue;
+        const int gx = pmod(i0 + vx - 1, g.nx);
+        int src;
+        row_rule(j0 + vy - 1, 3, src);
+        coff[r] = (size_t)src * g.nx + gx;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                voff[q][r] = coff[r];
-                vfac[q][r] = 1;
-            }
-        } else {
-            coff[r] = (size_t)min(max(gy, 0), g.ny - 1) * g.nx + gx;
-            const int my = gy < 0 ? -1 - gy : (gy >= g.ny ? 2 * g.ny - 1 - gy : gy);
-            const bool inside = gy >= 0 && gy < g.ny;
-            voff[0][r] = voff[2][r] = (size_t)min(max(my, 0), g.ny - 1) * g.nx + gx;
-            vfac[0][r] = vfac[2][r] = (my >= 0 && my < g.ny) ? (inside ? 1 : -1) : 0;
-            voff[1][r] = (size_t)(inside ? gy : 0) * g.nx + gx;
-            vfac[1][r] = inside ? 1 : 0;
+        for (int q = 0; q < 3; ++q) {
+            vfac[q][r] = (signed char)row_rule(j0 + vy - 1, q, src);
+            voff[q][r] = (size_t)src * g.nx + gx;
         }
     }
     const T* vel[3] = {a.U, a.V, a.W};
+    // E elements from global (one 16-byte vector) into shared, times fac (+1, -1, 0)
+    auto copy_scaled = [&](T* dst, const T* src, int fac) {
+        if (sizeof(T) == 4) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (fac) {
+                v = __ldg(reinterpret_cast<const float4*>(src));
+                v.x = -v.x; v.y = -v.y; v.z = -v.z; v.w = -v.w;
+            }
+            *reinterpret_cast<float4*>(dst) = v;
+        } else {
+            double2 v = make_double2(0.0, 0.0);
+            if (fac) {
+                v = __ldg(reinterpret_cast<const double2*>(src));
+                v.x = -v.x; v.y = -v.y;
+            }
+            *reinterpret_cast<double2*>(dst) = v;
+        }
+    };
     auto fetch_vel = [&](int kk) {
         const size_t pv = (size_t)wrap1(kk, g.nz) * plane;
         const int slot = kk & 3;
+        if (VEC) {
+            if (csm < 0) return;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                T* dst = &sm.V[q][slot][csm];
+                if (cvfac[q] == 1) cp_async16(dst, vel[q] + pv + cvoff[q]);
+                else copy_scaled(dst, vel[q] + pv + cvoff[q], cvfac[q]);
+            }
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -123,13 +198,27 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     };
     auto fetch_p = [&](int kk) {
         const size_t pp = (size_t)wrap1(kk, g.nz) * plane;
+        const int slot = pmod(kk, 3);
+        if (VEC) {
+            if (csm >= 0) cp_async16(&sm.P[slot][csm], a.P + pp + ccoff);
+            return;
+        }
 #pragma unroll
         for (int r = 0; r < NV; ++r)
-            if (psm[r] >= 0) cp_async(&sm.P[pmod(kk, 3)][psm[r]], a.P + pp + coff[r]);
+            if (psm[r] >= 0) cp_async(&sm.P[slot][psm[r]], a.P + pp + coff[r]);
     };
     auto fetch_braw = [&](int kk) {
         if (!stress) return;
         const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
+        if (VEC) {
+            if (csm < 0) return;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                cp_async16(&sm.Braw[c][csm], a.Bo[c] + pb + ccoff);
+                cp_async16(&sm.Braw[6 + c][csm], a.Bn[c] + pb + ccoff);
+            }
+            return;
+        }
 #pragma unroll
         for (int c = 0; c < 6; ++c)
 #pragma unroll
@@ -174,8 +263,21 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         }
     };
     const size_t cell0 = (size_t)min(j, g.ny - 1) * g.nx + min(i, g.nx - 1);
+    // history chunk of this thread (own cells of row hr, columns hq .. hq+E-1)
+    constexpr int HCR = TX / E;                          // chunks per tile row
+    const int hr = tid / HCR, hq = (tid - hr * HCR) * E;
+    const bool hch = VEC && tid < TY * HCR && j0 + hr < g.ny && i0 + hq < g.nx;
+    const size_t hoff = (size_t)(j0 + hr) * g.nx + i0 + hq;
     auto fetch_hist = [&](int kk) {
         if (!a.read_hist || kk >= k1) return;
+        if (VEC) {
+            if (hch) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    cp_async16(&sm.H[kk & 1][q][hr * TX + hq], a.NH[q] + (size_t)kk * plane + hoff);
+            }
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < 3; ++q) cp_async(&sm.H[kk & 1][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
     };
@@ -200,7 +302,7 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     const T idx2 = g.idx * g.idx, idy2 = g.idy * g.idy, idz2 = g.idz * g.idz;
     const T mu = T(mc.mu_s);
     const T two_a = T(2) * a.alpha;
-    const int o = (ty + 1) * VW + tx + 1;
+    const int o = (ty + 1) * VW + tx + XO;
     const T* sx_ = a.trig;
 
     for (int k = k0; k < k1; ++k) {
@@ -349,18 +451,21 @@ cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const Momentu
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
     const size_t smem = sizeof(MomSmem<T>);
     th.b(K_MOMENTUM);
-    switch (mc.model) {
-#define EVP_LAUNCH_MOM(M)                                                                                  \
-    case M:                                                                                                \
-        cudaFuncSetAttribute(k_momentum<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-        k_momentum<T, M><<<grid, block, smem, st>>>(g, mc, a, kz);                                        \
+    const bool vec = (g.nx * sizeof(T)) % 16 == 0;
+    switch (mc.model * 2 + (vec ? 1 : 0)) {
+#define EVP_LAUNCH_MOM_V(M, V)                                                                                \
+    case M * 2 + V:                                                                                           \
+        cudaFuncSetAttribute(k_momentum<T, M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        k_momentum<T, M, V><<<grid, block, smem, st>>>(g, mc, a, kz);                                        \
         break;
+#define EVP_LAUNCH_MOM(M) EVP_LAUNCH_MOM_V(M, false) EVP_LAUNCH_MOM_V(M, true)
         EVP_LAUNCH_MOM(EVP_NEWTONIAN)
         EVP_LAUNCH_MOM(EVP_OLDROYD_B)
         EVP_LAUNCH_MOM(EVP_FENE_P)
         EVP_LAUNCH_MOM(EVP_SARAMITO)
         EVP_LAUNCH_MOM(EVP_NEO_HOOKEAN)
 #undef EVP_LAUNCH_MOM
+#undef EVP_LAUNCH_MOM_V
         default: return cudaErrorInvalidValue;
     }
     th.e(K_MOMENTUM);
