@@ -28,13 +28,18 @@ __device__ __forceinline__ constexpr int col_of(int c) { return c == 0 ? 0 : ((c
 // Tile geometry of the z-marching kernel: a 32 x 8 tile of cells in x-y walks
 // through a chunk of z planes.  B of the tile's own column lives in a 7-plane
 // register window (z stencils); the current plane of B with a 3-cell x-y halo
-// and three planes of u, v, w with a 1-cell halo live in shared memory.
+// and three planes of u, v, w with a 1-cell halo live in shared memory.  Plane
+// rows are 40 wide with the tile's i0 at column 4 (x = i0-4 .. i0+35), so that
+// when nx is a whole number of 16-byte chunks every row is staged in 16-byte
+// cp.async chunks; other grids stage element by element.
 constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int BW = TX + 6, BH = TY + 6, BPL = BW * BH;    // B plane with halo 3
-constexpr int VW = TX + 2, VH = TY + 2, VPL = VW * VH;    // velocity plane with halo 1
-constexpr int BHALO = BPL - NT;                           // 276 halo cells per B plane
+constexpr int XO = 4;                                     // column of x = i0 in a plane row
+constexpr int BW = TX + 8, BH = TY + 6, BPL = BW * BH;    // B plane rows j0-3 .. j0+10
+constexpr int VW = TX + 8, VH = TY + 2, VPL = VW * VH;    // velocity plane rows j0-1 .. j0+8
+constexpr int BHALO = (TX + 6) * BH - NT;                 // 276 halo cells the stencils use
 constexpr int NBH = (BHALO + NT - 1) / NT;                // halo cells per thread (2)
-constexpr int NVH = (VPL + NT - 1) / NT;                  // velocity cells per thread (2)
+constexpr int VUSED = (TX + 2) * VH;                      // velocity cells the stencils use
+constexpr int NVH = (VUSED + NT - 1) / NT;                // velocity cells per thread (2)
 
 __device__ __forceinline__ int pmod(int a, int n) {
     int r = a % n;
@@ -43,21 +48,47 @@ __device__ __forceinline__ int pmod(int a, int n) {
 // a in [-n, 2n): one conditional wrap, no division
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-// (row, col) inside the 38 x 14 B plane of halo cell h (0 <= h < 276)
+// (row, x - (i0-3)) of used halo cell h (0 <= h < 276) of a B plane: three full
+// rows above and below the tile, three cells left and right of its 8 rows
 __device__ __forceinline__ void bhalo_pos(int h, int& hy, int& hx) {
-    if (h < 3 * BW) {
-        hy = h / BW;
-        hx = h % BW;
-    } else if (h < 6 * BW) {
-        const int q = h - 3 * BW;
-        hy = TY + 3 + q / BW;
-        hx = q % BW;
+    constexpr int W = TX + 6;
+    if (h < 3 * W) {
+        hy = h / W;
+        hx = h % W;
+    } else if (h < 6 * W) {
+        const int q = h - 3 * W;
+        hy = TY + 3 + q / W;
+        hx = q % W;
     } else {
-        const int q = h - 6 * BW;
+        const int q = h - 6 * W;
         hy = 3 + q / 6;
         const int c = q % 6;
         hx = c < 3 ? c : TX + c;
     }
+}
+
+// chunk h (16 bytes, E elements) of the halo ring of a B plane: whole rows 0..2
+// and BH-3..BH-1, and the chunks covering columns 0..3 and TX+4..TX+7 of rows
+// 3..BH-4.  Returns (row, first column).
+template <int E>
+__device__ __forceinline__ void bring_pos(int h, int& row, int& col) {
+    constexpr int CPR = BW / E, LC = XO / E;
+    if (h < 6 * CPR) {
+        const int r = h / CPR;
+        row = r < 3 ? r : BH - 6 + r;
+        col = (h - r * CPR) * E;
+    } else {
+        const int q = h - 6 * CPR;
+        const int r = q / (2 * LC), s = q - r * (2 * LC);
+        row = 3 + r;
+        col = s < LC ? s * E : TX + XO + (s - LC) * E;
+    }
+}
+
+// 16-byte asynchronous copy (L2 only)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
 template <typename T>
@@ -84,7 +115,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // substep / first AB2 step), 2 = update reading and writing the history,
 // 3 = update reading the history without writing it (last RK3 substep).
 // DIFF: the local artificial diffusion is on (ModelConst::art_diff > 0).
-template <typename T, int MODEL, int MODE, bool DIFF>
+// VEC: planes are staged in 16-byte chunks (needs nx * sizeof(T) % 16 == 0).
+template <typename T, int MODEL, int MODE, bool DIFF, bool VEC>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chunk) {
     constexpr bool RHS_ONLY = MODE == 0, READ_H = MODE >= 2, WRITE_H = MODE == 1 || MODE == 2;
@@ -102,62 +134,163 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     const int jc = g.walls ? min(j, g.ny - 1) : pmod(j, g.ny);
     const size_t col = (size_t)jc * g.nx + pmod(i, g.nx);
 
-    // plane offsets of this thread's B halo cells
+    // ---- row ghost rules (walls): centred fields copy the nearest row, u and w
+    // take the odd mirror (no slip), v is zero outside the stored faces; a
+    // periodic y wraps.  Returns the source row and the factor (+1 copy, -1
+    // negated copy, 0 zero) of velocity component q, or of B for q = 3.
+    auto row_rule = [&](int gy, int q, int& src) -> int {
+        if (!g.walls) {
+            src = pmod(gy, g.ny);
+            return 1;
+        }
+        if (q == 3) {
+            src = min(max(gy, 0), g.ny - 1);
+            return 1;
+        }
+        const bool inside = gy >= 0 && gy < g.ny;
+        if (q == 1) {
+            src = inside ? gy : 0;
+            return inside ? 1 : 0;
+        }
+        const int my = gy < 0 ? -1 - gy : (gy >= g.ny ? 2 * g.ny - 1 - gy : gy);
+        src = min(max(my, 0), g.ny - 1);
+        return (my >= 0 && my < g.ny) ? (inside ? 1 : -1) : 0;
+    };
+    constexpr int E = 16 / (int)sizeof(T);             // elements per 16-byte chunk
+    constexpr int CPR = BW / E;                        // chunks per plane row
+    constexpr int RING = 6 * CPR + 2 * TY * (XO / E);  // halo-ring chunks of a B plane
+    constexpr int NRC = (6 * RING + NT - 1) / NT;      // ring copies per thread (6 fields)
+    constexpr int VCH = CPR * VH;                      // chunks of a velocity plane
+    constexpr int OCH = TY * (TX / E);                 // chunks of the tile's own cells
+    constexpr int NOC = (6 * OCH + NT - 1) / NT;       // own-cell copies per thread (6 fields)
+
+    // element-wise staging (VEC false): this thread's B halo and velocity cells
     size_t hoff[NBH];
     int hsm[NBH];
+    size_t voff[3][NVH];
+    signed char vfac[3][NVH];
+    int vsm[NVH];
+    // chunk staging (VEC true): ring copies (field, plane offset, shared offset),
+    // the velocity chunk, and the own-cell chunks (field, row, column)
+    unsigned rc_off[NRC];
+    int rc_sm[NRC];
+    int csm = -1;
+    size_t cvoff[3] = {0, 0, 0};
+    signed char cvfac[3] = {0, 0, 0};
+    unsigned oc_off[NOC], oc_hoff[NOC];
+    int oc_sm[NOC];
+    bool oc_act[NOC];
+    if (VEC) {
+#pragma unroll
+        for (int r = 0; r < NRC; ++r) {
+            const int idx = tid + r * NT;
+            rc_sm[r] = -1;
+            rc_off[r] = 0;
+            if (idx < 6 * RING) {
+                const int c = idx / RING, h = idx - c * RING;
+                int row, colq;
+                bring_pos<E>(h, row, colq);
+                int src;
+                row_rule(j0 + row - 3, 3, src);
+                rc_off[r] = (unsigned)((size_t)src * g.nx + pmod(i0 - XO + colq, g.nx));
+                rc_sm[r] = c * BPL + row * BW + colq;
+            }
+        }
+        if (tid < VCH) {
+            const int r = tid / CPR, q0 = (tid - r * CPR) * E;
+            csm = r * VW + q0;
+            const int gx = pmod(i0 - XO + q0, g.nx);
+            int src;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                cvfac[q] = (signed char)row_rule(j0 - 1 + r, q, src);
+                cvoff[q] = (size_t)src * g.nx + gx;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NOC; ++r) {
+            const int idx = tid + r * NT;
+            oc_sm[r] = -1;
+            oc_off[r] = oc_hoff[r] = 0;
+            oc_act[r] = false;
+            if (idx < 6 * OCH) {
+                const int c = idx / OCH, h = idx - c * OCH;
+                const int row = h / (TX / E), q0 = (h - row * (TX / E)) * E;
+                int src;
+                row_rule(j0 + row, 3, src);
+                oc_off[r] = (unsigned)((size_t)src * g.nx + pmod(i0 + q0, g.nx));
+                oc_sm[r] = c * NT + row * TX + q0;
+                oc_act[r] = j0 + row < g.ny && i0 + q0 < g.nx;
+                oc_hoff[r] = (unsigned)((size_t)(j0 + row) * g.nx + i0 + q0);
+            }
+        }
+    }
 #pragma unroll
     for (int r = 0; r < NBH; ++r) {
         const int h = tid + r * NT;
         hsm[r] = -1;
         hoff[r] = 0;
-        if (h < BHALO) {
+        if (!VEC && h < BHALO) {
             int hy, hx;
             bhalo_pos(h, hy, hx);
-            const int gx = pmod(i0 + hx - 3, g.nx);
-            const int gy = g.walls ? ycen(g, j0 + hy - 3) : pmod(j0 + hy - 3, g.ny);
-            hoff[r] = (size_t)gy * g.nx + gx;
-            hsm[r] = hy * BW + hx;
+            int src;
+            row_rule(j0 + hy - 3, 3, src);
+            hoff[r] = (size_t)src * g.nx + pmod(i0 + hx - 3, g.nx);
+            hsm[r] = hy * BW + hx + XO - 3;
         }
     }
-    // plane offsets and ghost factors (+1 copy, -1 no-slip mirror, 0 wall) of this
-    // thread's velocity cells, per component u, v, w
-    size_t voff[3][NVH];
-    signed char vfac[3][NVH];
-    int vsm[NVH];
 #pragma unroll
     for (int r = 0; r < NVH; ++r) {
         const int e = tid + r * NT;
-        vsm[r] = e < VPL ? e : -1;
-        const int vy = e / VW, vx = e % VW;
-        const int gx = pmod(i0 + vx - 1, g.nx);
-        int gy = j0 + vy - 1;
+        const int vy = e / (TX + 2), vx = e - vy * (TX + 2);
+        vsm[r] = (!VEC && e < VUSED) ? vy * VW + vx + XO - 1 : -1;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             voff[q][r] = 0;
             vfac[q][r] = 0;
         }
-        if (e >= VPL) continue;
-        if (!g.walls) {
-            gy = pmod(gy, g.ny);
+        if (vsm[r] < 0) continue;
+        const int gx = pmod(i0 + vx - 1, g.nx);
+        int src;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                voff[q][r] = (size_t)gy * g.nx + gx;
-                vfac[q][r] = 1;
-            }
-        } else {
-            const int my = gy < 0 ? -1 - gy : (gy >= g.ny ? 2 * g.ny - 1 - gy : gy);
-            const bool inside = gy >= 0 && gy < g.ny;
-            voff[0][r] = voff[2][r] = (size_t)min(max(my, 0), g.ny - 1) * g.nx + gx;
-            vfac[0][r] = vfac[2][r] = (my >= 0 && my < g.ny) ? (inside ? 1 : -1) : 0;
-            voff[1][r] = (size_t)(inside ? gy : 0) * g.nx + gx;
-            vfac[1][r] = inside ? 1 : 0;
+        for (int q = 0; q < 3; ++q) {
+            vfac[q][r] = (signed char)row_rule(j0 + vy - 1, q, src);
+            voff[q][r] = (size_t)src * g.nx + gx;
         }
     }
     const T* vel[3] = {a.U, a.V, a.W};
+    // E elements from global (one 16-byte vector) into shared, times fac (+1, -1, 0)
+    auto copy_scaled = [&](T* dst, const T* src, int fac) {
+        if (sizeof(T) == 4) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (fac) {
+                v = __ldg(reinterpret_cast<const float4*>(src));
+                v.x = -v.x; v.y = -v.y; v.z = -v.z; v.w = -v.w;
+            }
+            *reinterpret_cast<float4*>(dst) = v;
+        } else {
+            double2 v = make_double2(0.0, 0.0);
+            if (fac) {
+                v = __ldg(reinterpret_cast<const double2*>(src));
+                v.x = -v.x; v.y = -v.y;
+            }
+            *reinterpret_cast<double2*>(dst) = v;
+        }
+    };
     // velocity plane kk (unwrapped index) into ring slot kk mod 4
     auto fetch_vel = [&](int kk) {
         const size_t pv = (size_t)wrap1(kk, g.nz) * plane;
         const int slot = kk & 3;
+        if (VEC) {
+            if (csm < 0) return;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                T* dst = &sm.V[q][slot][csm];
+                if (cvfac[q] == 1) cp_async16(dst, vel[q] + pv + cvoff[q]);
+                else copy_scaled(dst, vel[q] + pv + cvoff[q], cvfac[q]);
+            }
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -170,14 +303,39 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
                     *dst = vfac[q][r] == 0 ? T(0) : -__ldg(vel[q] + pv + voff[q][r]);
             }
     };
+    // halo ring of B plane kk into buffer kk & 1
     auto fetch_halo = [&](int kk) {
         const size_t ph = (size_t)wrap1(kk, g.nz) * plane;
         const int buf = kk & 1;
+        if (VEC) {
+#pragma unroll
+            for (int r = 0; r < NRC; ++r)
+                if (rc_sm[r] >= 0) {
+                    const int c = rc_sm[r] / BPL;
+                    cp_async16(&sm.B[buf][0][0] + rc_sm[r], a.B[c] + ph + rc_off[r]);
+                }
+            return;
+        }
 #pragma unroll
         for (int c = 0; c < 6; ++c)
 #pragma unroll
             for (int r = 0; r < NBH; ++r)
                 if (hsm[r] >= 0) cp_async(&sm.B[buf][c][hsm[r]], a.B[c] + ph + hoff[r]);
+    };
+    // plane kk+4 of B for the tile's own columns (the window's next plane)
+    auto fetch_next = [&](int kk) {
+        const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
+        if (VEC) {
+#pragma unroll
+            for (int r = 0; r < NOC; ++r)
+                if (oc_sm[r] >= 0) {
+                    const int c = oc_sm[r] / NT;
+                    cp_async16(&sm.N[0][0] + oc_sm[r], a.B[c] + pb + oc_off[r]);
+                }
+            return;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) cp_async(&sm.N[c][tid], a.B[c] + pb + col);
     };
 
     // ---- prologue: B window (planes k0-3 .. k0+3), velocity planes k0-1 .. k0+1, plane k0 of B
@@ -194,13 +352,23 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     const size_t cell0 = (size_t)j * g.nx + i;
     auto fetch_hist = [&](int kk) {
         if constexpr (READ_H) {
-            if (!active || kk >= k1) return;
+            if (kk >= k1) return;
+            if (VEC) {
+#pragma unroll
+                for (int r = 0; r < NOC; ++r)
+                    if (oc_sm[r] >= 0 && oc_act[r]) {
+                        const int c = oc_sm[r] / NT;
+                        cp_async16(&sm.H[kk & 1][0][0] + oc_sm[r], a.RT[c] + (size_t)kk * plane + oc_hoff[r]);
+                    }
+                return;
+            }
+            if (!active) return;
 #pragma unroll
             for (int c = 0; c < 6; ++c) cp_async(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0);
         }
     };
     fetch_hist(k0);
-    const int ob = (ty + 3) * BW + tx + 3;   // this cell in a B plane
+    const int ob = (ty + 3) * BW + tx + XO;   // this cell in a B plane
 #pragma unroll
     for (int c = 0; c < 6; ++c) sm.B[k0 & 1][c][ob] = w[c][3];
     cp_async_commit();
@@ -211,15 +379,13 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     const T kL2 = T(mc.L2), kaf = T(mc.a_fene), kgm = T(mc.gmod), kty = T(mc.tau_y);
     const T dtz = a.dt_zeta, dtx = a.dt_xi;
     const T hx = T(0.5) * g.idx, hy = T(0.5) * g.idy, hz = T(0.5) * g.idz;
-    const int o = (ty + 1) * VW + tx + 1;     // this cell in a velocity plane
+    const int o = (ty + 1) * VW + tx + XO;    // this cell in a velocity plane
     unsigned bits = 0;
 
     for (int k = k0; k < k1; ++k) {
         // ---- asynchronous prefetch: plane k+4 of B (own column), halo of plane k+1, velocity plane k+2
         {
-            const size_t pb = (size_t)wrap1(k + 4, g.nz) * plane;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) cp_async(&sm.N[c][tid], a.B[c] + pb + col);
+            fetch_next(k + 4);
             fetch_halo(k + 1);
             fetch_vel(k + 2);
             fetch_hist(k + 1);
@@ -360,28 +526,19 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
 
 }  // namespace
 
-template <typename T>
-cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a,
-                          cudaStream_t st, const TimingHook& th) {
-    // z chunks: about four waves of CTAs over all SMs (two CTAs per SM in FP32,
-    // one in FP64); small grids go down to one plane per CTA so that every SM works
-    const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-    const int per_sm = sizeof(T) == 4 ? 2 : 1;
-    int chunks = (4 * 152 * per_sm + tiles - 1) / tiles;
-    chunks = chunks > g.nz ? g.nz : chunks;
-    const int kz = (g.nz + chunks - 1) / chunks;
-    chunks = (g.nz + kz - 1) / kz;
+template <typename T, bool VEC>
+cudaError_t launch_stress_v(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a, cudaStream_t st,
+                            dim3 grid, int kz) {
     dim3 block(TX, TY, 1);
-    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
     const size_t smem = sizeof(StressSmem<T>);
     const int mode = a.rhs_only ? 0 : (!a.read_hist ? 1 : (a.write_hist ? 2 : 3));
     const int diff = mc.art_diff > 0.0 ? 1 : 0;
-    th.b(K_STRESS);
     switch ((mc.model * 4 + mode) * 2 + diff) {
-#define EVP_LAUNCH_STRESS_D(M, MD, D)                                                                         \
-    case (M * 4 + MD) * 2 + D:                                                                                \
-        cudaFuncSetAttribute(k_stress<T, M, MD, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        k_stress<T, M, MD, D><<<grid, block, smem, st>>>(g, mc, a, kz);                                       \
+#define EVP_LAUNCH_STRESS_D(M, MD, D)                                                                        \
+    case (M * 4 + MD) * 2 + D:                                                                               \
+        cudaFuncSetAttribute(k_stress<T, M, MD, D, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                             (int)smem);                                                                     \
+        k_stress<T, M, MD, D, VEC><<<grid, block, smem, st>>>(g, mc, a, kz);                                 \
         break;
 #define EVP_LAUNCH_STRESS(M, MD) EVP_LAUNCH_STRESS_D(M, MD, false) EVP_LAUNCH_STRESS_D(M, MD, true)
         EVP_LAUNCH_STRESS(EVP_OLDROYD_B, 0)
@@ -404,6 +561,31 @@ cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArg
 #undef EVP_LAUNCH_STRESS_D
         default: return cudaErrorInvalidValue;
     }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a,
+                          cudaStream_t st, const TimingHook& th) {
+    // z chunks: about four waves of CTAs over all SMs (two CTAs per SM in FP32,
+    // one in FP64); small grids go down to one plane per CTA so that every SM works
+    const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    const int per_sm = sizeof(T) == 4 ? 2 : 1;
+    int chunks = (4 * 152 * per_sm + tiles - 1) / tiles;
+    chunks = chunks > g.nz ? g.nz : chunks;
+    const int kz = (g.nz + chunks - 1) / chunks;
+    chunks = (g.nz + kz - 1) / kz;
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
+    th.b(K_STRESS);
+    cudaError_t e;
+    // 16-byte chunks need whole chunks per row: always so in FP64 (nx is even)
+    if constexpr (sizeof(T) == 8) {
+        e = launch_stress_v<T, true>(g, mc, a, st, grid, kz);
+    } else {
+        e = (g.nx * sizeof(T)) % 16 == 0 ? launch_stress_v<T, true>(g, mc, a, st, grid, kz)
+                                         : launch_stress_v<T, false>(g, mc, a, st, grid, kz);
+    }
+    if (e != cudaSuccess) return e;
     th.e(K_STRESS);
     return cudaGetLastError();
 }
