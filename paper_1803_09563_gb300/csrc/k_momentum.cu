@@ -57,15 +57,20 @@ __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// all but the most recently committed group have landed
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Planes are staged two ahead: while plane k is computed, plane k+2 has landed
+// (or is landing) and plane k+3 is being requested.
 template <typename T>
 struct MomSmem {
-    T V[3][4][VPL];      // u, v, w: ring slots for planes k-1 .. k+2
+    T V[3][5][VPL];      // u, v, w: ring slots for planes k-1 .. k+3
     T S[6][3][VPL];      // summed stress: ring slots for planes k-1 .. k+1
-    T Braw[12][VPL];     // raw B^{k-1} (0..5) and B^k (6..11) of the plane being staged
-    T P[3][VPL];         // pressure planes k, k+1 (+ staging)
-    T H[2][3][NT];       // momentum history of the tile's cells, planes k and k+1
+    T Braw[2][12][VPL];  // raw B^{k-1} (0..5) and B^k (6..11) of planes k+2 and k+3
+    T P[4][VPL];         // pressure planes k .. k+3
+    T H[4][3][NT];       // momentum history of the tile's cells, planes k .. k+2
 };
+__device__ __forceinline__ int vslot(int kk) { return (kk + 5) % 5; }   // kk >= -5
 
 // VEC: rows are staged in 16-byte chunks (needs nx * sizeof(T) % 16 == 0)
 template <typename T, int MODEL, bool VEC>
@@ -173,7 +178,7 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     };
     auto fetch_vel = [&](int kk) {
         const size_t pv = (size_t)wrap1(kk, g.nz) * plane;
-        const int slot = kk & 3;
+        const int slot = vslot(kk);
         if (VEC) {
             if (csm < 0) return;
 #pragma unroll
@@ -198,7 +203,7 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     };
     auto fetch_p = [&](int kk) {
         const size_t pp = (size_t)wrap1(kk, g.nz) * plane;
-        const int slot = pmod(kk, 3);
+        const int slot = kk & 3;
         if (VEC) {
             if (csm >= 0) cp_async16(&sm.P[slot][csm], a.P + pp + ccoff);
             return;
@@ -214,8 +219,8 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
             if (csm < 0) return;
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                cp_async16(&sm.Braw[c][csm], a.Bo[c] + pb + ccoff);
-                cp_async16(&sm.Braw[6 + c][csm], a.Bn[c] + pb + ccoff);
+                cp_async16(&sm.Braw[kk & 1][c][csm], a.Bo[c] + pb + ccoff);
+                cp_async16(&sm.Braw[kk & 1][6 + c][csm], a.Bn[c] + pb + ccoff);
             }
             return;
         }
@@ -224,8 +229,8 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
 #pragma unroll
             for (int r = 0; r < NV; ++r)
                 if (psm[r] >= 0) {
-                    cp_async(&sm.Braw[c][psm[r]], a.Bo[c] + pb + coff[r]);
-                    cp_async(&sm.Braw[6 + c][psm[r]], a.Bn[c] + pb + coff[r]);
+                    cp_async(&sm.Braw[kk & 1][c][psm[r]], a.Bo[c] + pb + coff[r]);
+                    cp_async(&sm.Braw[kk & 1][6 + c][psm[r]], a.Bn[c] + pb + coff[r]);
                 }
     };
     const T kgm = T(mc.gmod), kL2 = T(mc.L2), kaf = T(mc.a_fene);
@@ -234,30 +239,31 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         if (!stress) return;
         const T gm = kgm;
         const int slot = pmod(kk, 3);
+        const T(*Br)[VPL] = sm.Braw[kk & 1];
 #pragma unroll
         for (int r = 0; r < NV; ++r) {
             const int e = psm[r];
             if (e < 0) continue;
             if (MODEL == EVP_FENE_P) {
                 const T L2 = kL2, av = kaf;
-                const T Fo = L2 / (L2 - (sm.Braw[0][e] + sm.Braw[3][e] + sm.Braw[5][e]));
-                const T Fn = L2 / (L2 - (sm.Braw[6][e] + sm.Braw[9][e] + sm.Braw[11][e]));
+                const T Fo = L2 / (L2 - (Br[0][e] + Br[3][e] + Br[5][e]));
+                const T Fn = L2 / (L2 - (Br[6][e] + Br[9][e] + Br[11][e]));
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
                     const bool d = (c == 0 || c == 3 || c == 5);
-                    sm.S[c][slot][e] = gm * (Fn * sm.Braw[6 + c][e] - (d ? av : T(0)))
-                                       + gm * (Fo * sm.Braw[c][e] - (d ? av : T(0)));
+                    sm.S[c][slot][e] = gm * (Fn * Br[6 + c][e] - (d ? av : T(0)))
+                                       + gm * (Fo * Br[c][e] - (d ? av : T(0)));
                 }
             } else if (MODEL == EVP_NEO_HOOKEAN) {
                 // Table 1: tau = G B
 #pragma unroll
-                for (int c = 0; c < 6; ++c) sm.S[c][slot][e] = gm * sm.Braw[6 + c][e] + gm * sm.Braw[c][e];
+                for (int c = 0; c < 6; ++c) sm.S[c][slot][e] = gm * Br[6 + c][e] + gm * Br[c][e];
             } else {
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
                     const bool d = (c == 0 || c == 3 || c == 5);
-                    sm.S[c][slot][e] = gm * (sm.Braw[6 + c][e] - (d ? T(1) : T(0)))
-                                       + gm * (sm.Braw[c][e] - (d ? T(1) : T(0)));
+                    sm.S[c][slot][e] = gm * (Br[6 + c][e] - (d ? T(1) : T(0)))
+                                       + gm * (Br[c][e] - (d ? T(1) : T(0)));
                 }
             }
         }
@@ -274,15 +280,16 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
             if (hch) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
-                    cp_async16(&sm.H[kk & 1][q][hr * TX + hq], a.NH[q] + (size_t)kk * plane + hoff);
+                    cp_async16(&sm.H[kk & 3][q][hr * TX + hq], a.NH[q] + (size_t)kk * plane + hoff);
             }
             return;
         }
 #pragma unroll
-        for (int q = 0; q < 3; ++q) cp_async(&sm.H[kk & 1][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
+        for (int q = 0; q < 3; ++q) cp_async(&sm.H[kk & 3][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
     };
 
     // ---- prologue: velocity k0-1 .. k0+1, p k0 .. k0+1, S k0-1 .. k0+1, history k0
+    // in place; then plane k0+2 and the history of k0+1 requested
     fetch_vel(k0 - 1);
     fetch_vel(k0);
     fetch_vel(k0 + 1);
@@ -297,6 +304,11 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         build_s(k0 + d);
         __syncthreads();
     }
+    fetch_vel(k0 + 2);
+    fetch_braw(k0 + 2);
+    fetch_p(k0 + 2);
+    fetch_hist(k0 + 1);
+    cp_async_commit();
 
     const T h = T(0.5);
     const T idx2 = g.idx * g.idx, idy2 = g.idy * g.idy, idz2 = g.idz * g.idz;
@@ -306,22 +318,23 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     const T* sx_ = a.trig;
 
     for (int k = k0; k < k1; ++k) {
-        // ---- asynchronous prefetch of plane k+2 (velocity, raw B, p) and the history of k+1
-        fetch_vel(k + 2);
-        fetch_braw(k + 2);
-        fetch_p(k + 2);
-        fetch_hist(k + 1);
+        // ---- asynchronous request of plane k+3 (velocity, raw B, p) and the history of k+2
+        fetch_vel(k + 3);
+        fetch_braw(k + 3);
+        fetch_p(k + 3);
+        fetch_hist(k + 2);
         cp_async_commit();
 
-        const T* U0 = sm.V[0][(k & 3)];
-        const T* Um1 = sm.V[0][((k - 1) & 3)];
-        const T* Up1 = sm.V[0][((k + 1) & 3)];
-        const T* V0 = sm.V[1][(k & 3)];
-        const T* Vm1 = sm.V[1][((k - 1) & 3)];
-        const T* Vp1 = sm.V[1][((k + 1) & 3)];
-        const T* W0 = sm.V[2][(k & 3)];
-        const T* Wm1 = sm.V[2][((k - 1) & 3)];
-        const T* Wp1 = sm.V[2][((k + 1) & 3)];
+        const int vm1 = vslot(k - 1), v0s = vslot(k), vp1 = vslot(k + 1);
+        const T* U0 = sm.V[0][v0s];
+        const T* Um1 = sm.V[0][vm1];
+        const T* Up1 = sm.V[0][vp1];
+        const T* V0 = sm.V[1][v0s];
+        const T* Vm1 = sm.V[1][vm1];
+        const T* Vp1 = sm.V[1][vp1];
+        const T* W0 = sm.V[2][v0s];
+        const T* Wm1 = sm.V[2][vm1];
+        const T* Wp1 = sm.V[2][vp1];
         // value at (i+di, j+dj) of a plane
         auto at = [&](const T* Pl, int di, int dj) { return Pl[o + dj * VW + di]; };
         const T u0 = at(U0, 0, 0), v0 = at(V0, 0, 0), w0 = at(W0, 0, 0);
@@ -368,8 +381,8 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         const T Nz = -Az + mu * Lw + fz;
 
         // ---- pressure gradient
-        const T* P0 = sm.P[pmod(k, 3)];
-        const T* P1 = sm.P[pmod(k + 1, 3)];
+        const T* P0 = sm.P[k & 3];
+        const T* P1 = sm.P[(k + 1) & 3];
         const T p0 = at(P0, 0, 0);
         const T gpx = (at(P0, 1, 0) - p0) * g.idx;
         const T gpy = (at(P0, 0, 1) - p0) * g.idy;
@@ -377,9 +390,9 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
 
         T ix = a.zeta * Nx, iy = a.zeta * Ny, iz = a.zeta * Nz;
         if (a.read_hist) {
-            ix += a.xi * sm.H[k & 1][0][tid];
-            iy += a.xi * sm.H[k & 1][1][tid];
-            iz += a.xi * sm.H[k & 1][2][tid];
+            ix += a.xi * sm.H[k & 3][0][tid];
+            iy += a.xi * sm.H[k & 3][1][tid];
+            iz += a.xi * sm.H[k & 3][2][tid];
         }
         ix -= two_a * gpx;
         iy -= two_a * gpy;
@@ -427,8 +440,9 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
             }
         }
 
-        // ---- advance: the staged raw B becomes S plane k+2 (slot of plane k-1)
-        cp_async_wait_all();
+        // ---- advance: plane k+2 has landed (only plane k+3 may be in flight); its
+        // raw B becomes S plane k+2 (slot of plane k-1)
+        cp_async_wait_prev();
         __syncthreads();
         build_s(k + 2);
         __syncthreads();
