@@ -153,18 +153,39 @@ def algorithmic_bytes(kernel, w, elt, walls):
     return 0, 1
 
 
+# CUDA sources that determine each profiled kernel's code (for the staleness check)
+KERNEL_SOURCES = {
+    'stress_weno_update': ['k_stress.cuh', 'k_stress_f32.cu', 'weno.cuh', 'evp_internal.cuh'],
+}
+
+
+def kernel_sources_sha256(kernel):
+    """SHA-256 over the CUDA sources of ``kernel`` (file names and contents, in order)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(kernel, []):
+        h.update(f.encode())
+        with open(os.path.join(ROOT, 'paper_1803_09563_gb300', 'csrc', f), 'rb') as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def ncu_traffic(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if one exists for this kernel."""
+    """DRAM bytes per launch from the committed ncu summary of this kernel, or None
+    when there is none or its kernel sources have changed since it was captured."""
     p = os.path.join(ROOT, 'profiles', f'{kernel}__channel_256x128x128_fp32.md')
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
+    traffic, sha = None, None
     for line in open(p):
         if line.startswith('traffic_bytes_per_launch:'):
             try:
-                return float(line.split(':', 1)[1])
+                traffic = float(line.split(':', 1)[1])
             except ValueError:
                 return None
-    return None
+        elif line.startswith('source_sha256:'):
+            sha = line.split(':', 1)[1].strip()
+    return traffic if sha == kernel_sources_sha256(kernel) else None
 
 
 def max_over_ranks(x, world, device):
