@@ -172,6 +172,15 @@ int evp_step(evp_state* s, double dt);
  * launches.  EVP_ERR_STATE for AB2 states.  Off by default.                    */
 int evp_set_graph(evp_state* s, int enable);
 
+/* Programmatic dependent launch of the step's kernels when they are launched
+ * directly (on by default; a graph-replayed step uses plain launches, which
+ * measured faster there): each kernel may be scheduled while the previous one is
+ * finishing and waits inside (griddepcontrol.wait) until that kernel's results
+ * are visible, which hides launch latency between the 24 kernels of an RK3 step.
+ * Results are identical either way.  Synchronises the state's stream; captured
+ * step graphs are rebuilt on the next step.  The paper has no counterpart.      */
+int evp_set_pdl(evp_state* s, int enable);
+
 /* With integrator EVP_AB2, evp_step is one two-phase AB2 step of size dt
  * (level set, re-distancing when due, interface force, B and u updates,
  * projection with dt); steps are counted from evp_init.                       */

@@ -294,9 +294,36 @@ struct TimingHook {
     void (*begin)(void* ctx, int kid);
     void (*end)(void* ctx, int kid);
     void* ctx;
+    bool pdl = false;    // launch with programmatic dependent launch (see launch_k)
     void b(int kid) const { if (begin) begin(ctx, kid); }
     void e(int kid) const { if (end) end(ctx, kid); }
 };
+
+// Programmatic dependent launch.  A kernel launched with ``pdl`` may be scheduled
+// while the previous kernel on the stream is still running (its launch and
+// set-up overlap that kernel's tail); every such kernel first executes pdl_wait(),
+// which returns once the previous grid has completed and its memory is visible,
+// before it touches global memory.  pdl_trigger() lets the next kernel be
+// scheduled once every CTA of this grid has started.  Both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                     Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // Host: the FP64 Thomas table for the wall-bounded Poisson solve.  For every
 // (kz <= nz/2, kx) system of size ny (rows idy2 psi_{j-1} - (2 idy2 + lx + lz)

@@ -76,6 +76,8 @@ __device__ __forceinline__ int vslot(int kk) { return (kk + 5) % 5; }   // kk >=
 template <typename T, int MODEL, bool VEC>
 __global__ void __launch_bounds__(NT, 1)
 k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_chunk) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     MomSmem<T>& sm = *reinterpret_cast<MomSmem<T>*>(smraw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -470,7 +472,8 @@ cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const Momentu
 #define EVP_LAUNCH_MOM_V(M, V)                                                                                \
     case M * 2 + V:                                                                                           \
         cudaFuncSetAttribute(k_momentum<T, M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-        k_momentum<T, M, V><<<grid, block, smem, st>>>(g, mc, a, kz);                                        \
+        if (cudaError_t e = launch_k(k_momentum<T, M, V>, grid, block, smem, st, th.pdl, g, mc, a, kz))     \
+            return e;                                                                                          \
         break;
 #define EVP_LAUNCH_MOM(M) EVP_LAUNCH_MOM_V(M, false) EVP_LAUNCH_MOM_V(M, true)
         EVP_LAUNCH_MOM(EVP_NEWTONIAN)

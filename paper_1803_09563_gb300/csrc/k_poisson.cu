@@ -158,6 +158,8 @@ __device__ __forceinline__ T div_value(const Geo<T>& g, const PoissonArgs<T>& a,
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_div_fftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx, nxh = nx / 2 + 1;
     C<T>* sa = reinterpret_cast<C<T>*>(smraw);
@@ -200,6 +202,8 @@ k_div_fftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_ifftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nx = g.nx, nxh = nx / 2 + 1, half = nx / 2;
     C<T>* sa = reinterpret_cast<C<T>*>(smraw);
@@ -245,6 +249,8 @@ template <typename T, bool INV, bool SOLVE>
 __global__ void __launch_bounds__(256)
 k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axis_y, size_t estride,
           size_t ostride, int tk) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     const int n = axis_y ? g.ny : g.nz;
     const int* rad = axis_y ? tb.rady : tb.radz;
@@ -302,6 +308,8 @@ k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axi
 template <typename T>
 __global__ void __launch_bounds__(32)
 k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int TB = 16;
     const int nxh = g.nx / 2 + 1, ny = g.ny, nz = g.nz;
     const int row = 2 * nxh;
@@ -414,6 +422,8 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
 template <typename T, bool RESID>
 __global__ void __launch_bounds__(256)
 k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, double idz_d, int kz_chunk) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
@@ -562,7 +572,7 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
     const size_t smx = 2 * (size_t)np * nx * sizeof(C<T>);
     set_smem<T>((const void*)k_div_fftx<T>, smx);
     th.b(K_DIV_FFTX);
-    k_div_fftx<T><<<gx, bx, smx, st>>>(g, tb, a, np);
+    if (cudaError_t e = launch_k(k_div_fftx<T>, gx, bx, smx, st, th.pdl, g, tb, a, np)) return e;
     th.e(K_DIV_FFTX);
 
     const int tk = sizeof(T) == 4 ? 16 : 8;
@@ -573,7 +583,9 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
         const size_t sm = col_smem<T>(nz, tk);
         set_smem<T>((const void*)k_fft_col<T, false, false>, sm);
         th.b(K_FFT_Z_FWD);
-        k_fft_col<T, false, false><<<gc, bc, sm, st>>>(g, tb, a, 0, (size_t)ny * nxh, (size_t)nxh, tk);
+        if (cudaError_t e = launch_k(k_fft_col<T, false, false>, gc, bc, sm, st, th.pdl, g, tb, a, 0, (size_t)ny * nxh,
+                                     (size_t)nxh, tk))
+            return e;
         th.e(K_FFT_Z_FWD);
     }
     if (!g.walls) {
@@ -581,7 +593,9 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
         const size_t sm = col_smem<T>(ny, tk);
         set_smem<T>((const void*)k_fft_col<T, false, true>, sm);
         th.b(K_SOLVE_Y);
-        k_fft_col<T, false, true><<<gc, bc, sm, st>>>(g, tb, a, 1, (size_t)nxh, (size_t)ny * nxh, tk);
+        if (cudaError_t e = launch_k(k_fft_col<T, false, true>, gc, bc, sm, st, th.pdl, g, tb, a, 1, (size_t)nxh,
+                                     (size_t)ny * nxh, tk))
+            return e;
         th.e(K_SOLVE_Y);
     } else {
         // warp-sized blocks spread the chains evenly over the SMs
@@ -589,7 +603,7 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
         const int chains = 2 * nxh * nz;
         dim3 gt((chains + tt - 1) / tt);
         th.b(K_THOMAS);
-        k_thomas<T><<<gt, tt, 0, st>>>(g, tb, a);
+        if (cudaError_t e = launch_k(k_thomas<T>, gt, dim3(tt), 0, st, th.pdl, g, tb, a)) return e;
         th.e(K_THOMAS);
     }
     // ---- inverse z
@@ -598,12 +612,14 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
         const size_t sm = col_smem<T>(nz, tk);
         set_smem<T>((const void*)k_fft_col<T, true, false>, sm);
         th.b(K_FFT_Z_INV);
-        k_fft_col<T, true, false><<<gc, bc, sm, st>>>(g, tb, a, 0, (size_t)ny * nxh, (size_t)nxh, tk);
+        if (cudaError_t e = launch_k(k_fft_col<T, true, false>, gc, bc, sm, st, th.pdl, g, tb, a, 0, (size_t)ny * nxh,
+                                     (size_t)nxh, tk))
+            return e;
         th.e(K_FFT_Z_INV);
     }
     set_smem<T>((const void*)k_ifftx<T>, smx);
     th.b(K_IFFTX);
-    k_ifftx<T><<<gx, bx, smx, st>>>(g, tb, a, np);
+    if (cudaError_t e = launch_k(k_ifftx<T>, gx, bx, smx, st, th.pdl, g, tb, a, np)) return e;
     th.e(K_IFFTX);
     return cudaGetLastError();
 }
@@ -617,10 +633,10 @@ cudaError_t launch_correct(const Geo<T>& g, const CorrectArgs<T>& a, cudaStream_
     chunks = (g.nz + kz - 1) / kz;
     dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, chunks);
     th.b(K_CORRECT);
-    if (a.maxdiv)
-        k_correct<T, true><<<grid, block, 0, st>>>(g, a, a.idx_d, a.idy_d, a.idz_d, kz);
-    else
-        k_correct<T, false><<<grid, block, 0, st>>>(g, a, a.idx_d, a.idy_d, a.idz_d, kz);
+    const cudaError_t e = a.maxdiv
+        ? launch_k(k_correct<T, true>, grid, block, 0, st, th.pdl, g, a, a.idx_d, a.idy_d, a.idz_d, kz)
+        : launch_k(k_correct<T, false>, grid, block, 0, st, th.pdl, g, a, a.idx_d, a.idy_d, a.idz_d, kz);
+    if (e != cudaSuccess) return e;
     th.e(K_CORRECT);
     return cudaGetLastError();
 }

@@ -120,6 +120,8 @@ template <typename T, int MODEL, int MODE, bool DIFF, bool VEC>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chunk) {
     constexpr bool RHS_ONLY = MODE == 0, READ_H = MODE >= 2, WRITE_H = MODE == 1 || MODE == 2;
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     StressSmem<T>& sm = *reinterpret_cast<StressSmem<T>*>(smraw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -528,7 +530,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
 
 template <typename T, bool VEC>
 cudaError_t launch_stress_v(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a, cudaStream_t st,
-                            dim3 grid, int kz) {
+                            dim3 grid, int kz, bool pdl) {
     dim3 block(TX, TY, 1);
     const size_t smem = sizeof(StressSmem<T>);
     const int mode = a.rhs_only ? 0 : (!a.read_hist ? 1 : (a.write_hist ? 2 : 3));
@@ -538,7 +540,8 @@ cudaError_t launch_stress_v(const Geo<T>& g, const ModelConst& mc, const StressA
     case (M * 4 + MD) * 2 + D:                                                                               \
         cudaFuncSetAttribute(k_stress<T, M, MD, D, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                              (int)smem);                                                                     \
-        k_stress<T, M, MD, D, VEC><<<grid, block, smem, st>>>(g, mc, a, kz);                                 \
+        if (cudaError_t e = launch_k(k_stress<T, M, MD, D, VEC>, grid, block, smem, st, pdl, g, mc, a, kz))  \
+            return e;                                                                                        \
         break;
 #define EVP_LAUNCH_STRESS(M, MD) EVP_LAUNCH_STRESS_D(M, MD, false) EVP_LAUNCH_STRESS_D(M, MD, true)
         EVP_LAUNCH_STRESS(EVP_OLDROYD_B, 0)
@@ -580,10 +583,10 @@ cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArg
     cudaError_t e;
     // 16-byte chunks need whole chunks per row: always so in FP64 (nx is even)
     if constexpr (sizeof(T) == 8) {
-        e = launch_stress_v<T, true>(g, mc, a, st, grid, kz);
+        e = launch_stress_v<T, true>(g, mc, a, st, grid, kz, th.pdl);
     } else {
-        e = (g.nx * sizeof(T)) % 16 == 0 ? launch_stress_v<T, true>(g, mc, a, st, grid, kz)
-                                         : launch_stress_v<T, false>(g, mc, a, st, grid, kz);
+        e = (g.nx * sizeof(T)) % 16 == 0 ? launch_stress_v<T, true>(g, mc, a, st, grid, kz, th.pdl)
+                                         : launch_stress_v<T, false>(g, mc, a, st, grid, kz, th.pdl);
     }
     if (e != cudaSuccess) return e;
     th.e(K_STRESS);

@@ -77,6 +77,7 @@ def load(path=None):
         'evp_get_field': (c_int, [c_void_p, c_int, c_void_p, c_int]),
         'evp_step': (c_int, [c_void_p, c_double]),
         'evp_set_graph': (c_int, [c_void_p, c_int]),
+        'evp_set_pdl': (c_int, [c_void_p, c_int]),
         'evp_substep': (c_int, [c_void_p, c_double, c_int]),
         'evp_project': (c_int, [c_void_p]),
         'evp_poisson_solve': (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -103,7 +104,7 @@ def exported_symbols():
     return ['evp_state_bytes', 'evp_init', 'evp_destroy', 'evp_set_field', 'evp_get_field', 'evp_step',
             'evp_substep', 'evp_project', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_sync', 'evp_kernel_timing',
             'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error', 'evp_poisson_solve_static',
-            'evp_set_graph', 'evp_selftest']
+            'evp_set_graph', 'evp_selftest', 'evp_set_pdl']
 
 
 def _check(code):
@@ -178,6 +179,10 @@ def evp_step(state, dt):
 
 def evp_set_graph(state, enable):
     return _check(load().evp_set_graph(state, int(bool(enable))))
+
+
+def evp_set_pdl(state, enable):
+    return _check(load().evp_set_pdl(state, int(bool(enable))))
 
 
 def evp_substep(state, dt, k):
