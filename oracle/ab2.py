@@ -3,7 +3,8 @@ projection) with the level set of Sec. 3.2.1.  TEST INFRASTRUCTURE ONLY.
 
 From t^n to t^n + dt:
   1. advance the level set (TVD-RK3 + WENO5, velocity u^n); every
-     ``reinit_every`` steps re-distance it (Eq. reinit);
+     ``reinit_every`` steps re-distance it (Eq. reinit); with ``mass_iters`` > 0
+     shift it to keep the drop volume of the first step (Reading 17);
   2. mixture properties from H(phi^{n+1}): mu_s, mu_p = X1 H + X2 (1 - H),
      lambda and rho uniform (rho = 1: Boussinesq);
   3. B^{n+1} = B^n + dt (3/2 RT^n - 1/2 RT^{n-1})                    (Eq. ab2tau)
@@ -60,6 +61,7 @@ class TwoPhase:
     rho_ratio: float = None
     gravity: float = 1.0
     art_diff: float = 0.0
+    mass_iters: int = 0
 
     def mixture(self, H):
         mu_s = self.beta / self.Re * H + self.mu_ratio / self.Re * (1.0 - H)
@@ -94,10 +96,14 @@ def ab2_step(s, phi, dt, g, tp, nstep):
     """One AB2 step; ``nstep`` counts completed steps (0 for the first).
     ``s.RT_hist`` / ``s.N_hist`` carry RT^{n-1} / RU^{n-1}.  Returns (State, phi)."""
     eps = tp.eps_cells * g.dx
-    # 1. level set
+    # 1. level set (Reading 17: the drop volume of the first step is kept)
+    if tp.mass_iters > 0 and nstep == 0:
+        tp.v0 = ls.drop_volume(phi, g, eps)
     phi = ls.advect(phi, s.U, s.V, s.W, g, dt)
     if tp.reinit_every > 0 and (nstep + 1) % tp.reinit_every == 0:
         phi = ls.reinitialise(phi, g, tp.reinit_iters)
+    if tp.mass_iters > 0:
+        phi = ls.mass_correct(phi, g, eps, tp.v0, tp.mass_iters)
     # 2. mixture properties at n+1
     H = ls.heaviside(phi, eps)
     mu_s, mu_p = tp.mixture(H)

@@ -17,6 +17,12 @@ interface.  Reading 10 (the paper cites Ge et al. for the details it omits):
   * CSF force sigma kappa delta(phi) n at cell centres (Eq. fLS), averaged onto faces;
   * Boussinesq buoyancy +(1 - H) drho_g along y at centres, minus its domain mean
     (a periodic box has no net acceleration), averaged onto v faces.
+Reading 17 (mass conservation; the paper names a mass-conserving interface-
+correction level set and cites Ge et al. for it without giving the correction):
+after each level-set step phi is shifted uniformly, phi <- phi + d, with d from
+Newton iterations on the smoothed volume of fluid 2, V(phi) = sum (1 - H(phi)) dV,
+whose derivative is dV/dd = -sum delta(phi) dV, so that V returns to its value
+at the first step.
 """
 
 import numpy as np
@@ -123,3 +129,24 @@ def centres_to_faces(fc, g):
     if g.walls:
         Fy[:, g.ny - 1, :] = 0.0
     return Fx, Fy, Fz
+
+
+def drop_volume(phi, g, eps):
+    """Smoothed volume of fluid 2 (phi < 0): sum of 1 - H(phi) over the cells."""
+    return float((1.0 - heaviside(phi, eps)).sum()) * g.dx * g.dy * g.dz
+
+
+def mass_correct(phi, g, eps, v0, iters):
+    """Reading 17: uniform shift of phi restoring the smoothed drop volume v0,
+    ``iters`` Newton iterations d <- d + (V(phi + d) - v0) / A(phi + d) with
+    A = sum delta(phi + d) dV."""
+    dv = g.dx * g.dy * g.dz
+    d = 0.0
+    for _ in range(iters):
+        p = phi + d
+        v = float((1.0 - heaviside(p, eps)).sum()) * dv
+        a = float(delta(p, eps).sum()) * dv
+        if a > 0.0:
+            d += (v - v0) / a
+    return phi + d
+

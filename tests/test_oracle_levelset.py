@@ -226,3 +226,42 @@ def test_light_drop_rises_with_density_contrast():
     Hin = 1.0 - ls.heaviside(phi, 1.5 * g.dx)
     vbar = (0.5 * (s.V + oracle.at(s.V, g, 'v', j=-1)) * Hin).sum() / Hin.sum()
     assert vbar > 0.0
+
+
+def test_mass_correction_undoes_a_uniform_shift():
+    """Reading 17: for an exact signed distance phi of a sphere, the correction of
+    phi + 0.013 back to the volume of phi returns phi (the smoothed volume is a
+    strictly decreasing function of the shift, so the Newton root is -0.013)."""
+    n, L = 32, 1.0
+    g = oracle.Grid(n, n, n, L, L, L)
+    geo = inputs.geometry(n, n, n, L, L, L)
+    phi = inputs.sphere_distance(geo, (0.5, 0.47, 0.52), 0.23)
+    eps = 1.5 * g.dx
+    v0 = ls.drop_volume(phi, g, eps)
+    out = ls.mass_correct(phi + 0.013, g, eps, v0, iters=6)
+    assert np.abs(out - phi).max() < 1e-12
+    assert abs(ls.drop_volume(out, g, eps) - v0) < 1e-13 * v0
+    # zero iterations and a field already at v0 leave phi unchanged
+    np.testing.assert_array_equal(ls.mass_correct(phi, g, eps, v0, iters=0), phi)
+    assert np.abs(ls.mass_correct(phi, g, eps, v0, iters=3) - phi).max() == 0.0
+
+
+def test_mass_correction_keeps_the_drop_volume_over_ab2_steps():
+    """With the correction on, the smoothed drop volume after every AB2 step equals
+    the initial one (to the Newton tolerance); without it, advection and
+    re-distancing change it."""
+    n = 16
+    g = oracle.Grid(n, 2 * n, n, 1.5, 3.0, 1.5)
+    geo = inputs.geometry(n, 2 * n, n, 1.5, 3.0, 1.5)
+    phi0 = inputs.sphere_distance(geo, (0.75, 0.9, 0.75), 0.35)
+    eps = 1.5 * g.dx
+    v0 = ls.drop_volume(phi0, g, eps)
+    drift = {}
+    for iters in (0, 4):
+        tp = TwoPhase('saramito', Re=35.0, Wi=1.0, beta=0.5, tau_y=0.02, sigma=0.1, drho_g=1.0,
+                      reinit_every=2, reinit_iters=2, mass_iters=iters)
+        st, phi = oracle.State.rest(g), phi0.copy()
+        for it in range(4):
+            st, phi = ab2_step(st, phi, 2e-2, g, tp, it)
+        drift[iters] = abs(ls.drop_volume(phi, g, eps) - v0) / v0
+    assert drift[4] < 1e-12 and drift[0] > 1e-6, drift
