@@ -118,7 +118,12 @@ typedef struct {
                            7-point Laplacian of B is added to that right-hand side.  The
                            paper gives no value ("tuned" per case).  Explicit: keep
                            art_diff*dt*(2/dx^2 + 2/dy^2 + 2/dz^2) below about 1          */
-    double reserved[6];
+    int ls_mass_iters;  /* AB2: 0 = off; else after each level-set step phi is shifted
+                           uniformly, phi + d, with d from this many Newton iterations on
+                           the smoothed drop volume sum (1 - H(phi)) dV, so that it keeps
+                           its value of the first step (a mass-preserving reading of the
+                           interface-correction level set the paper cites)              */
+    double reserved[5];
 } evp_params;
 
 /* Field identifiers for evp_set_field / evp_get_field */

@@ -106,6 +106,7 @@ struct evp_state_s {
     void* POLD;          // AB2 with a density contrast: p^{n-1}
     double* partials;
     double* mean_1mH;
+    double* mass;        // mass correction: 2 x block partials, v0, d
     long long nstep;     // AB2 steps taken
     int cu, cb;          // current velocity / B buffer
     // CUDA-graph replay of evp_step: one executable graph per parity of the B
@@ -211,6 +212,9 @@ int validate(const evp_grid* g, evp_model model, const evp_params* p) {
         if (!(p->mu_ratio > 0) || !(p->ls_eps_cells > 0) || !(p->sigma >= 0) || p->reinit_every < 0 ||
             p->reinit_iters < 0)
             return fail(EVP_ERR_ARG, "bad two-phase parameters (mu_ratio, ls_eps_cells, sigma, reinit)");
+        if (p->ls_mass_iters < 0 || p->ls_mass_iters > 50) return fail(EVP_ERR_ARG, "ls_mass_iters must be 0..50");
+    } else if (p->ls_mass_iters != 0) {
+        return fail(EVP_ERR_ARG, "the level-set mass correction is part of the AB2 two-phase step");
     }
     return EVP_OK;
 }
@@ -270,6 +274,7 @@ size_t plan(evp_state* s, char* base) {
     if (s->prm.penalization)
         for (int q = 0; q < 3; ++q) sol[q] = P(N * e);
     void* mean = ab2 ? P(sizeof(double)) : nullptr;
+    void* mass = (ab2 && s->prm.ls_mass_iters > 0) ? P((2 * nparts + 2) * sizeof(double)) : nullptr;
     void* st = P(sizeof(unsigned));
     void* md = P(sizeof(unsigned long long));
     if (base) {
@@ -294,6 +299,7 @@ size_t plan(evp_state* s, char* base) {
         s->partials = static_cast<double*>(parts);
         for (int q = 0; q < 3; ++q) s->SOL[q] = sol[q];
         s->mean_1mH = static_cast<double*>(mean);
+        s->mass = static_cast<double*>(mass);
     }
     return L.total;
 }
@@ -536,8 +542,19 @@ int ab2_step_t(evp_state* s, double dt) {
         L.h = T(dx);
         return launch_ls_stage<T>(g, L, reinit, s->st, th);
     };
-    // 1. level set: TVD-RK3 with u^n; the third stage writes phi in place
+    // mass correction (Reading 17): shift of phi restoring the drop volume of the first step
+    const size_t np_mass = iface_partials(g);
+    MassArgs<T> M;
+    M.phi = static_cast<T*>(s->PHI);
+    M.eps = T(p.ls_eps_cells * dx);
+    M.partials = s->mass;
+    M.v0 = s->mass ? s->mass + 2 * np_mass : nullptr;
+    M.d = s->mass ? s->mass + 2 * np_mass + 1 : nullptr;
+    M.dv = (s->g.lx / s->g.nx) * (s->g.ly / s->g.ny) * (s->g.lz / s->g.nz);
     cudaError_t e;
+    if (p.ls_mass_iters > 0 && s->nstep == 0)
+        if ((e = launch_mass_correct<T>(g, M, 0, 0, s->st, th)) != cudaSuccess) return cuda_fail(e, "mass correction");
+    // 1. level set: TVD-RK3 with u^n; the third stage writes phi in place
     if ((e = stage(s->PHI, s->PHI, s->PHIA, 0.0, 1.0, false, dt)) != cudaSuccess) return cuda_fail(e, "level set");
     if ((e = stage(s->PHI, s->PHIA, s->PHIB, 0.75, 0.25, false, dt)) != cudaSuccess) return cuda_fail(e, "level set");
     if ((e = stage(s->PHI, s->PHIB, s->PHI, 1.0 / 3.0, 2.0 / 3.0, false, dt)) != cudaSuccess)
@@ -553,6 +570,9 @@ int ab2_step_t(evp_state* s, double dt) {
                 return cuda_fail(e, "reinit");
         }
     }
+    if (p.ls_mass_iters > 0)
+        if ((e = launch_mass_correct<T>(g, M, 1, p.ls_mass_iters, s->st, th)) != cudaSuccess)
+            return cuda_fail(e, "mass correction");
     // 2. H, normals, interface force at n+1
     {
         IfaceArgs<T> I;

@@ -248,6 +248,18 @@ struct IfaceArgs {
     T eps, sigma, drho_g;
 };
 
+// mass-preserving level-set shift (two-phase step): phi <- phi + d with d from
+// Newton iterations on the smoothed drop volume
+template <typename T>
+struct MassArgs {
+    T* phi;
+    T eps;
+    double* partials;  // per-block sums: [0, np) of 1 - H(phi + d), [np, 2 np) of delta(phi + d)
+    double* v0;        // target drop volume
+    double* d;         // accumulated shift
+    double dv;         // cell volume
+};
+
 template <typename T>
 struct MomAB2Args {
     const T* U;
@@ -387,6 +399,11 @@ size_t iface_partials(const Geo<T>& g);
 
 template <typename T>
 cudaError_t launch_interface(const Geo<T>& g, const IfaceArgs<T>& a, cudaStream_t st, const TimingHook& th);
+
+// mode 0: v0 <- drop volume of phi; mode 1: ``iters`` Newton updates of d, then phi += d
+template <typename T>
+cudaError_t launch_mass_correct(const Geo<T>& g, const MassArgs<T>& a, int mode, int iters, cudaStream_t st,
+                                const TimingHook& th);
 
 template <typename T>
 cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>& a, cudaStream_t st,

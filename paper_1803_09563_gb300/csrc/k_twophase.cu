@@ -7,6 +7,8 @@
 //                   the WENO5 one-sided derivatives, S(phi0) = phi0/sqrt(phi0^2 + h^2))
 //   k_iface_a       H(phi), n = grad phi/|grad phi| (central), per-block sums of 1 - H
 //   k_sum_partials  FP64 sum of the block sums (fixed order: deterministic)
+//   k_mass_*        mass-preserving uniform shift of phi: block sums of 1 - H and
+//                   delta at phi + d, Newton update of d on the device, phi += d
 //   k_iface_b       kappa = -div n, the CSF force sigma kappa delta(phi) n (Eq. fLS) and
 //                   the mean-free Boussinesq buoyancy, at cell centres
 //   k_momentum_ab2  RU = -div(uu) + div[mu_s(H)(grad u + grad u^T)] + div tau(mu_p(H)) + f
@@ -127,6 +129,83 @@ __global__ void __launch_bounds__(256) k_sum_partials(const double* partials, in
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = red[0] * scale;
+}
+
+// Mass correction: per-block FP64 sums of 1 - H(phi + d) and delta(phi + d)
+template <typename T>
+__global__ void __launch_bounds__(256) k_mass_partials(const Geo<T> g, const MassArgs<T> a, int np) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    double v = 0.0, ar = 0.0;
+    if (i < g.nx && j < g.ny) {
+        const T ph = __ldg(a.phi + lin(g, i, j, k)) + T(*a.d);
+        const T eps = a.eps;
+        T H, D;
+        if (ph < -eps) {
+            H = T(0);
+            D = T(0);
+        } else if (ph > eps) {
+            H = T(1);
+            D = T(0);
+        } else {
+            const T x = T(3.14159265358979323846) * ph / eps;
+            H = T(0.5) * (T(1) + ph / eps + sin(x) * T(0.31830988618379067154));
+            D = T(0.5) / eps * (T(1) + cos(x));
+        }
+        v = 1.0 - double(H);
+        ar = double(D);
+    }
+    __shared__ double rv[256], ra[256];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    rv[t] = v;
+    ra[t] = ar;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) {
+            rv[t] += rv[t + w];
+            ra[t] += ra[t + w];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        a.partials[b] = rv[0];
+        a.partials[np + b] = ra[0];
+    }
+}
+
+// Mass correction: sum the block partials (fixed order) and either record the
+// volume (mode 0) or take one Newton step d += (V - v0)/A (mode 1)
+__global__ void __launch_bounds__(256) k_mass_newton(const double* partials, int np, double dv, double* v0,
+                                                     double* d, int mode) {
+    __shared__ double rv[256], ra[256];
+    double v = 0.0, ar = 0.0;
+    for (int q = threadIdx.x; q < np; q += 256) {
+        v += partials[q];
+        ar += partials[np + q];
+    }
+    rv[threadIdx.x] = v;
+    ra[threadIdx.x] = ar;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            rv[threadIdx.x] += rv[threadIdx.x + w];
+            ra[threadIdx.x] += ra[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double V = rv[0] * dv, A = ra[0] * dv;
+        if (mode == 0) *v0 = V;
+        else if (A > 0.0) *d += (V - *v0) / A;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mass_shift(T* phi, size_t n, const double* d) {
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) phi[c] += T(*d);
 }
 
 // CSF force sigma kappa delta(phi) n plus buoyancy (1 - H - mean(1 - H)) drho_g e_y
@@ -442,6 +521,29 @@ cudaError_t launch_interface(const Geo<T>& g, const IfaceArgs<T>& a, cudaStream_
 }
 
 template <typename T>
+cudaError_t launch_mass_correct(const Geo<T>& g, const MassArgs<T>& a, int mode, int iters, cudaStream_t st,
+                                const TimingHook& th) {
+    dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    const int np = (int)iface_partials(g);
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    th.b(K_LEVELSET);
+    cudaError_t e = cudaMemsetAsync(a.d, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    if (mode == 0) {
+        k_mass_partials<T><<<grid, block, 0, st>>>(g, a, np);
+        k_mass_newton<<<1, 256, 0, st>>>(a.partials, np, a.dv, a.v0, a.d, 0);
+    } else {
+        for (int it = 0; it < iters; ++it) {
+            k_mass_partials<T><<<grid, block, 0, st>>>(g, a, np);
+            k_mass_newton<<<1, 256, 0, st>>>(a.partials, np, a.dv, a.v0, a.d, 1);
+        }
+        k_mass_shift<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.phi, n, a.d);
+    }
+    th.e(K_LEVELSET);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>& a, cudaStream_t st,
                                 const TimingHook& th) {
     dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
@@ -464,6 +566,8 @@ cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>&
     template size_t iface_partials<T>(const Geo<T>&);                                                         \
     template cudaError_t launch_interface<T>(const Geo<T>&, const IfaceArgs<T>&, cudaStream_t,                \
                                              const TimingHook&);                                              \
+    template cudaError_t launch_mass_correct<T>(const Geo<T>&, const MassArgs<T>&, int, int, cudaStream_t,    \
+                                                const TimingHook&);                                           \
     template cudaError_t launch_momentum_ab2<T>(const Geo<T>&, int, const MomAB2Args<T>&, cudaStream_t,       \
                                                 const TimingHook&);                                           \
     template cudaError_t launch_split_rhs<T>(const Geo<T>&, const SplitArgs<T>&, cudaStream_t, const TimingHook&); \

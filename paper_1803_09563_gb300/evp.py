@@ -46,7 +46,7 @@ class evp_params(ctypes.Structure):
                 ('precision', c_int), ('integrator', c_int), ('mu_ratio', c_double), ('ls_eps_cells', c_double),
                 ('sigma', c_double), ('drho_g', c_double), ('reinit_every', c_int), ('reinit_iters', c_int),
                 ('rho_ratio', c_double), ('gravity', c_double), ('penalization', c_int),
-                ('art_diff', c_double), ('reserved', c_double * 6)]
+                ('art_diff', c_double), ('ls_mass_iters', c_int), ('reserved', c_double * 5)]
 
 
 class EvpError(RuntimeError):
@@ -135,7 +135,8 @@ def make_grid(nx, ny, nz, lx, ly, lz, walls_y=False):
 
 def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_amp=0.0, abc_k=0.0,
                 precision=EVP_FP64, integrator=EVP_RK3, mu_ratio=1.0, ls_eps_cells=1.5, sigma=0.0, drho_g=0.0,
-                reinit_every=10, reinit_iters=3, penalization=0, rho_ratio=0.0, gravity=0.0, art_diff=0.0):
+                reinit_every=10, reinit_iters=3, penalization=0, rho_ratio=0.0, gravity=0.0, art_diff=0.0,
+                ls_mass_iters=0):
     p = evp_params()
     p.Re, p.Wi, p.beta, p.Bi, p.L2 = float(Re), float(Wi), float(beta), float(Bi), float(L2)
     p.bi_def, p.dpdx, p.abc_amp, p.abc_k = int(bi_def), float(dpdx), float(abc_amp), float(abc_k)
@@ -145,6 +146,7 @@ def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_am
     p.penalization = int(penalization)
     p.rho_ratio, p.gravity = float(rho_ratio), float(gravity)
     p.art_diff = float(art_diff)
+    p.ls_mass_iters = int(ls_mass_iters)
     return p
 
 
