@@ -12,6 +12,8 @@ lambda(m) = (2 - 2 cos(2 pi m / n)) / h^2, so that the projection is exact; the
 periodic zero mode is set to zero; with walls psi has Neumann rows at j = 0 and
 j = ny-1 (the missing neighbour and its coefficient dropped), and the singular
 (kx, kz) = (0, 0) system is pinned by replacing its first row with psi_0 = 0.
+The same transforms solve the Helmholtz problems of the implicit viscous option
+(``solve_helmholtz``, Reading 18).
 """
 
 import numpy as np
@@ -85,6 +87,38 @@ def solve_poisson(r, g):
     ph = thomas(lower, diag, upper, rhs)
     ph = np.moveaxis(ph, 0, 1)
     return np.real(np.fft.ifft(np.fft.ifft(ph, axis=0), axis=2))
+
+
+def solve_helmholtz(r, g, c, kind):
+    """x with x - c lap(x) = r for a velocity component, lap the 7-point Laplacian
+    with that component's ghost rule (Reading 18): 'u' (u or w, centred in y; at
+    walls the odd no-slip mirror x_{-1} = -x_0, x_ny = -x_{ny-1}) or 'v' (y-faces;
+    at walls x = 0 on the bottom wall face below j = 0 and on the stored top face
+    j = ny-1, so rows 0 .. ny-2 are solved and row ny-1 is zero)."""
+    lx = eigenvalues(g.nx, g.dx)[None, None, :]
+    lz = eigenvalues(g.nz, g.dz)[:, None, None]
+    if not g.walls:
+        ly = eigenvalues(g.ny, g.dy)[None, :, None]
+        return np.real(np.fft.ifftn(np.fft.fftn(r) / (1.0 + c * (lx + ly + lz))))
+    rh = np.fft.fft(np.fft.fft(r, axis=2), axis=0)
+    ny, cy = g.ny, c / g.dy ** 2
+    lam = (lx + lz)[:, 0, :]
+    m = ny if kind == 'u' else ny - 1                      # unknown rows
+    lower = np.full((m,) + lam.shape, -cy)
+    upper = np.full((m,) + lam.shape, -cy)
+    diag = np.broadcast_to(1.0 + c * lam + 2.0 * cy, (m,) + lam.shape).copy()
+    lower[0] = 0.0
+    upper[m - 1] = 0.0
+    if kind == 'u':
+        # odd mirror: the ghost -x_0 (-x_{ny-1}) folds into the diagonal
+        diag[0] += cy
+        diag[m - 1] += cy
+    rhs = np.moveaxis(rh, 1, 0)[:m].copy()
+    xh = thomas(lower, diag, upper, rhs)
+    out = np.zeros((ny,) + lam.shape, dtype=complex)
+    out[:m] = xh
+    out = np.moveaxis(out, 0, 1)
+    return np.real(np.fft.ifft(np.fft.ifft(out, axis=0), axis=2))
 
 
 def project(U, V, W, g, coef):

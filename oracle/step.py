@@ -15,6 +15,13 @@ implicit solve it never describes; the viscous term is taken explicitly with the
 advective weights (zeta^k + xi^k = 2 alpha^k for every k, so the total weight per
 substep is unchanged), while div(tau) keeps alpha^k at levels k and k-1 because
 B^k is known before u* is formed.  The body force f carries the same weights.
+
+Reading 18 (option ``implicit_viscous``, Eq. NS-num1 read literally, uniform
+mu_s): the viscous term keeps alpha^k at levels k-1 (explicit) and k (implicit,
+Crank-Nicolson within the substep), N holds -div(uu) + f only, and u* solves
+  u* - alpha^k dt mu_s lap(u*) = u^{k-1} + dt [zeta^k N^{k-1} + xi^k N^{k-2}
+      - 2 alpha^k grad p^{k-1} + alpha^k (div tau^k + div tau^{k-1}) + alpha^k mu_s lap(u^{k-1})]
+per component, with that component's wall rule (``poisson.solve_helmholtz``).
 """
 
 from dataclasses import dataclass, field
@@ -22,8 +29,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .models import tau_from_B
-from .momentum import div_tau, grad_p, momentum_rhs_n
-from .poisson import project
+from .momentum import div_tau, grad_p, laplacian, momentum_rhs_n
+from .poisson import project, solve_helmholtz
 from .stress import stress_rhs
 
 # Eq. RK
@@ -65,7 +72,7 @@ class State:
                      self.t, self.nstep, cp(self.psi))
 
 
-def rk3_substep(s, k, dt, g, prm, force=None, solid=None):
+def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False):
     """Substep k (0-based index into Eq. RK) of the RK3 scheme; returns a new State.
 
     ``solid`` (optional triple of face arrays alpha) switches on the volume-penalisation
@@ -86,7 +93,7 @@ def rk3_substep(s, k, dt, g, prm, force=None, solid=None):
     else:
         RT, Bn = None, [b.copy() for b in s.B]
     # momentum predictor, Eqs. NS-num1 and rk3
-    N = momentum_rhs_n(s.U, s.V, s.W, g, prm.mu_s, force)
+    N = momentum_rhs_n(s.U, s.V, s.W, g, 0.0 if implicit_viscous else prm.mu_s, force)
     gp = grad_p(s.p, g)
     if has_stress:
         dto = div_tau(tau_from_B(s.B, prm), g)
@@ -100,7 +107,14 @@ def rk3_substep(s, k, dt, g, prm, force=None, solid=None):
         inc = inc - 2.0 * alpha * gp[d]
         if has_stress:
             inc = inc + alpha * (dtn[d] + dto[d])
+        if implicit_viscous:
+            inc = inc + alpha * prm.mu_s * laplacian(vel[d], g, 'v' if d == 1 else 'u')
         star.append(vel[d] + dt * inc)
+    if implicit_viscous:
+        if g.walls:
+            star[1][:, g.ny - 1, :] = 0.0
+        c = alpha * dt * prm.mu_s
+        star = [solve_helmholtz(star[d], g, c, 'v' if d == 1 else 'u') for d in range(3)]
     if solid is not None:
         star = [(1.0 - solid[d]) * star[d] for d in range(3)]
     if g.walls:
@@ -111,9 +125,10 @@ def rk3_substep(s, k, dt, g, prm, force=None, solid=None):
                  t=s.t + (alpha * 2.0) * dt, nstep=s.nstep, psi=psi)
 
 
-def rk3_step(s, dt, g, prm, force=None, solid=None):
-    """One full RK3 step (three substeps); ``solid`` as in rk3_substep."""
+def rk3_step(s, dt, g, prm, force=None, solid=None, implicit_viscous=False):
+    """One full RK3 step (three substeps); ``solid`` and ``implicit_viscous`` as in
+    rk3_substep."""
     for k in range(3):
-        s = rk3_substep(s, k, dt, g, prm, force, solid)
+        s = rk3_substep(s, k, dt, g, prm, force, solid, implicit_viscous)
     s.nstep += 1
     return s
