@@ -123,6 +123,12 @@ typedef struct {
                            the smoothed drop volume sum (1 - H(phi)) dV, so that it keeps
                            its value of the first step (a mass-preserving reading of the
                            interface-correction level set the paper cites)              */
+    int viscous_implicit;/* RK3: 0 = explicit viscous term (advective weights); 1 = Eq.
+                           NS-num1 read literally: alpha^k mu_s lap u at levels k-1
+                           (explicit) and k (implicit), i.e. one Helmholtz solve
+                           u* - alpha^k dt mu_s lap u* = rhs per velocity component and
+                           substep (FFT in x, z; FP64 Thomas along a wall-bounded y).
+                           Not with penalization.                                       */
     double reserved[5];
 } evp_params;
 

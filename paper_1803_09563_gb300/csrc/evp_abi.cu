@@ -107,6 +107,8 @@ struct evp_state_s {
     double* partials;
     double* mean_1mH;
     double* mass;        // mass correction: 2 x block partials, v0, d
+    double2* helm[3][2]; // implicit viscous, walls: Thomas tables per substep, (u/w, v)
+    double helm_dt;      // dt the Helmholtz tables were built for
     long long nstep;     // AB2 steps taken
     int cu, cb;          // current velocity / B buffer
     // CUDA-graph replay of evp_step: one executable graph per parity of the B
@@ -216,6 +218,11 @@ int validate(const evp_grid* g, evp_model model, const evp_params* p) {
     } else if (p->ls_mass_iters != 0) {
         return fail(EVP_ERR_ARG, "the level-set mass correction is part of the AB2 two-phase step");
     }
+    if (p->viscous_implicit) {
+        if (p->viscous_implicit != 1) return fail(EVP_ERR_ARG, "viscous_implicit must be 0 or 1");
+        if (p->integrator != EVP_RK3) return fail(EVP_ERR_ARG, "the implicit viscous option is part of the RK3 step");
+        if (p->penalization) return fail(EVP_ERR_ARG, "the implicit viscous option does not combine with penalization");
+    }
     return EVP_OK;
 }
 
@@ -275,6 +282,10 @@ size_t plan(evp_state* s, char* base) {
         for (int q = 0; q < 3; ++q) sol[q] = P(N * e);
     void* mean = ab2 ? P(sizeof(double)) : nullptr;
     void* mass = (ab2 && s->prm.ls_mass_iters > 0) ? P((2 * nparts + 2) * sizeof(double)) : nullptr;
+    void* helm[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    if (s->prm.viscous_implicit && g.walls_y)
+        for (int k = 0; k < 3; ++k)
+            for (int q = 0; q < 2; ++q) helm[k][q] = P((size_t)(g.nz / 2 + 1) * g.ny * nxh * sizeof(double2));
     void* st = P(sizeof(unsigned));
     void* md = P(sizeof(unsigned long long));
     if (base) {
@@ -300,6 +311,9 @@ size_t plan(evp_state* s, char* base) {
         for (int q = 0; q < 3; ++q) s->SOL[q] = sol[q];
         s->mean_1mH = static_cast<double*>(mean);
         s->mass = static_cast<double*>(mass);
+        for (int k = 0; k < 3; ++k)
+            for (int q = 0; q < 2; ++q) s->helm[k][q] = static_cast<double2*>(helm[k][q]);
+        s->helm_dt = -1.0;
     }
     return L.total;
 }
@@ -421,6 +435,54 @@ int run_poisson(evp_state* s, const T* Us, const T* Vs, const T* Ws, const T* rh
     return e == cudaSuccess ? EVP_OK : cuda_fail(e, "poisson");
 }
 
+// Implicit viscous option: field <- solution of x - c lap(x) = field for one
+// velocity component (kind_v: the v rule), in place through the spectral buffer
+template <typename T>
+int run_helmholtz(evp_state* s, T* field, double c, int k, bool kind_v) {
+    PoissonArgs<T> a;
+    a.Us = a.Vs = a.Ws = nullptr;
+    a.rhs = field;
+    a.rscale = T(1);
+    a.spec = static_cast<typename Cplx<T>::type*>(s->spec);
+    a.psi = field;
+    a.norm = poisson_norm<T>(s);
+    a.out_scale = s->g.walls_y ? T(a.norm) : T(1);
+    a.scratch = s->thomas_d;
+    if (s->g.walls_y) {
+        const double dy = s->g.ly / s->g.ny;
+        a.ttab = s->helm[k][kind_v ? 1 : 0];
+        a.tsub = -c / (dy * dy);
+    } else {
+        a.hcoef = T(c);
+    }
+    cudaError_t e = launch_poisson<T>(geo_of<T>(s), tables_of<T>(s), a, s->st, hook_of(s));
+    return e == cudaSuccess ? EVP_OK : cuda_fail(e, "helmholtz");
+}
+
+// Host: (re)build the Helmholtz Thomas tables of the three substeps for this dt
+int prepare_helmholtz(evp_state* s, double dt) {
+    if (!s->prm.viscous_implicit || !s->g.walls_y || s->helm_dt == dt) return EVP_OK;
+    const evp_grid& g = s->g;
+    const int nxh = g.nx / 2 + 1;
+    const double dx = g.lx / g.nx, dy = g.ly / g.ny, dz = g.lz / g.nz;
+    auto lam = [&](int n, int cnt, double h) {
+        std::vector<double> v(cnt);
+        for (int m = 0; m < cnt; ++m) v[m] = (2.0 - 2.0 * std::cos(2.0 * M_PI * m / n)) / (h * h);
+        return v;
+    };
+    const std::vector<double> lx = lam(g.nx, nxh, dx), lz = lam(g.nz, g.nz / 2 + 1, dz);
+    const double mu_s = s->prm.beta / s->prm.Re;
+    static const double RK3_ALPHA_H[3] = {4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0};
+    CK(cudaStreamSynchronize(s->st));
+    for (int k = 0; k < 3; ++k)
+        for (int q = 0; q < 2; ++q) {
+            const std::vector<double> M = helmholtz_table(g.ny, g.nz, nxh, dy, lx, lz, RK3_ALPHA_H[k] * dt * mu_s, q == 1);
+            CK(cudaMemcpy(s->helm[k][q], M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+    s->helm_dt = dt;
+    return EVP_OK;
+}
+
 template <typename T>
 int run_correct(evp_state* s, const T* Us, const T* Vs, const T* Ws, T* U, T* V, T* W, T* P, double coef,
                 bool residual, bool p_replace = false) {
@@ -502,8 +564,16 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
         a.abc_amp = T(s->prm.abc_amp);
         a.trig = s->prm.abc_amp != 0.0 ? static_cast<const T*>(s->trig) : nullptr;
         for (int q = 0; q < 3; ++q) a.solid[q] = static_cast<const T*>(s->SOL[q]);
+        a.cn = s->prm.viscous_implicit ? 1 : 0;
         cudaError_t e = launch_momentum<T>(g, s->mc, a, s->st, th);
         if (e != cudaSuccess) return cuda_fail(e, "momentum kernel");
+    }
+    if (s->prm.viscous_implicit) {
+        // Helmholtz solve per component: u* - alpha dt mu_s lap u* = rhs (Reading 18)
+        const double c = al * dt * s->mc.mu_s;
+        T* star[3] = {static_cast<T*>(s->U[1 - cu]), static_cast<T*>(s->V[1 - cu]), static_cast<T*>(s->W[1 - cu])};
+        for (int q = 0; q < 3; ++q)
+            if (int r = run_helmholtz<T>(s, star[q], c, k, q == 1)) return r;
     }
     const double coef = 2.0 * al * dt;
     int r = run_poisson<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
@@ -896,6 +966,7 @@ int evp_substep(evp_state* s, double dt, int k) {
     if (s->ab2) return fail(EVP_ERR_STATE, "evp_substep is an RK3 call; this state integrates with AB2");
     if (k < 0 || k > 2) return fail(EVP_ERR_ARG, "substep index must be 0, 1 or 2");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
+    if (int r = prepare_helmholtz(s, dt)) return r;
     return s->fp32 ? substep_t<float>(s, dt, k, false, false) : substep_t<double>(s, dt, k, false, false);
 }
 
@@ -976,6 +1047,7 @@ extern "C" int evp_set_pdl(evp_state* s, int enable) {
 extern "C" int evp_step(evp_state* s, double dt) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
+    if (int r = prepare_helmholtz(s, dt)) return r;
     if (s->ab2) return s->fp32 ? ab2_step_t<float>(s, dt) : ab2_step_t<double>(s, dt);
     if (s->use_graph && !s->timing) return rk3_step_graph(s, dt);
     for (int k = 0; k < 3; ++k) {

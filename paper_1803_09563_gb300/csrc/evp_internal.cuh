@@ -172,6 +172,7 @@ struct MomentumArgs {
     T dt, zeta, xi, alpha;
     int read_hist, write_hist, has_stress;
     T dpdx, abc_amp;
+    int cn = 0;        // implicit viscous option: N without the viscous term, alpha mu lap(u) explicit
     const T* trig;     // ABC force tables: sin/cos of k x_i, k y_j, k z_k (6 arrays)
     const T* solid[3]; // volume penalisation: solid fractions at u, v, w nodes (null: off)
 };
@@ -201,6 +202,12 @@ struct PoissonArgs {
     T rscale;
     typename Cplx<T>::type* spec;     // [nz][ny][nxh] complex
     T* psi;            // psi out
+    // Helmholtz problems x - c lap(x) = r (implicit viscous option): with walls the
+    // Thomas table and constant sub-diagonal replace the Poisson ones (no pinned
+    // mode); periodic y divides the modes by 1 + hcoef lam.  ttab null: Poisson.
+    const double2* ttab = nullptr;
+    double tsub = 0.0;
+    T hcoef = T(0);
     double norm;       // 1/(nx nz) (walls) or 1/(nx ny nz) (periodic)
     T out_scale;       // factor applied to psi by the inverse x pass (walls: norm)
     double* scratch;   // walls: FP64 forward-sweep values, 2 (nx/2+1) ny nz doubles
@@ -361,6 +368,38 @@ inline std::vector<double> thomas_table(int ny, int nz, int nxh, double dy, cons
                     d = 1.0;
                     up = 0.0;
                 }
+                const double m = 1.0 / (d - lo * cprev);
+                cprev = up * m;
+                const size_t o = 2 * (((size_t)kz * ny + j) * nxh + kx);
+                M[o] = m;
+                M[o + 1] = cprev;
+            }
+        }
+    return M;
+}
+
+// Host: FP64 Thomas table (m_j, c'_j), same layout as thomas_table, of the
+// Helmholtz systems x - c lap(x) = r of the implicit viscous option per
+// (kz <= nz/2, kx): rows -cy x_{j-1} + (1 + c(lx + lz) + 2 cy) x_j - cy x_{j+1},
+// cy = c/dy^2.  kind_v false (u, w centred in y): the odd no-slip mirror adds cy
+// to the first and last diagonals.  kind_v true (v on y-faces): rows 0..ny-2
+// with zero Dirichlet faces beyond them; row ny-1 (the top wall face) has m = 0,
+// which makes its solution zero.
+inline std::vector<double> helmholtz_table(int ny, int nz, int nxh, double dy, const std::vector<double>& lamx,
+                                           const std::vector<double>& lamz_half, double c, bool kind_v) {
+    const int nkz = nz / 2 + 1;
+    const double cy = c / (dy * dy);
+    const int m_rows = kind_v ? ny - 1 : ny;
+    std::vector<double> M((size_t)nkz * ny * nxh * 2, 0.0);
+    for (int kz = 0; kz < nkz; ++kz)
+        for (int kx = 0; kx < nxh; ++kx) {
+            const double base = 1.0 + c * (lamx[kx] + lamz_half[kz]) + 2.0 * cy;
+            double cprev = 0.0;
+            for (int j = 0; j < m_rows; ++j) {
+                const double lo = j > 0 ? -cy : 0.0;
+                const double up = j < m_rows - 1 ? -cy : 0.0;
+                double d = base;
+                if (!kind_v && (j == 0 || j == m_rows - 1)) d += cy;
                 const double m = 1.0 / (d - lo * cprev);
                 cprev = up * m;
                 const size_t o = 2 * (((size_t)kz * ny + j) * nxh + kx);

@@ -378,9 +378,12 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
             fy = a.abc_amp * (__ldg(sx_ + i) + __ldg(cz + k));
             fz = a.abc_amp * (__ldg(sy + j) + __ldg(cx + i));
         }
-        const T Nx = -Ax + mu * Lu + fx;
-        const T Ny = -Ay + mu * Lv + fy;
-        const T Nz = -Az + mu * Lw + fz;
+        // implicit viscous option: the viscous term leaves N (alpha mu lap u^{k-1} is
+        // added below; alpha mu lap u* is taken by the Helmholtz solves)
+        const T mun = a.cn ? T(0) : mu;
+        const T Nx = -Ax + mun * Lu + fx;
+        const T Ny = -Ay + mun * Lv + fy;
+        const T Nz = -Az + mun * Lw + fz;
 
         // ---- pressure gradient
         const T* P0 = sm.P[k & 3];
@@ -399,6 +402,12 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         ix -= two_a * gpx;
         iy -= two_a * gpy;
         iz -= two_a * gpz;
+        if (a.cn) {
+            const T am = a.alpha * mu;
+            ix += am * Lu;
+            iy += am * Lv;
+            iz += am * Lw;
+        }
         if (stress) {
             const int s0 = pmod(k, 3), sm1 = pmod(k - 1, 3), sp1 = pmod(k + 1, 3);
             auto S = [&](int c, int slot, int di, int dj) { return sm.S[c][slot][o + dj * VW + di]; };

@@ -278,7 +278,8 @@ k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axi
                 const int kx = kx0 + t;
                 if (kx >= nxh) continue;
                 const T lam = __ldg(tb.lamx + kx) + __ldg(tb.lamy + m) + lz;
-                const T f = lam == T(0) ? T(0) : T(-a.norm) / lam;
+                const T f = a.hcoef > T(0) ? T(a.norm) / (T(1) + a.hcoef * lam)
+                                           : (lam == T(0) ? T(0) : T(-a.norm) / lam);
                 C<T> v = res[(size_t)m * tk + t];
                 res[(size_t)m * tk + t] = mk<T>(v.x * f, v.y * f);
             }
@@ -318,13 +319,13 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
     const int kz = gid / row, t = gid - kz * row;             // t = 2*kx + part
     const int kx = t >> 1;
     const int kzh = kz <= nz - kz ? kz : nz - kz;
-    const bool pinned = (kx == 0 && kz == 0);
-    const double2* M = tb.thomas_m + (size_t)kzh * ny * nxh + kx;         // (m_j, c'_j)
+    const bool pinned = !a.ttab && kx == 0 && kz == 0;                     // Poisson only
+    const double2* M = (a.ttab ? a.ttab : tb.thomas_m) + (size_t)kzh * ny * nxh + kx;   // (m_j, c'_j)
     T* col = reinterpret_cast<T*>(a.spec + (size_t)kz * ny * nxh) + t;    // this part of (kx, kz)
     double* D = a.scratch + (size_t)kz * ny * (2 * nxh) + t;
     const size_t rs = 2 * (size_t)nxh;                                    // row stride in T / double
     const size_t ms = (size_t)nxh;                                        // row stride of the table
-    const double idy2 = tb.idy2;
+    const double idy2 = a.ttab ? a.tsub : tb.idy2;                        // the sub-diagonal
 
     // ---- forward: d'_j = (r_j - idy2 d'_{j-1}) m_j, d'_0 = r_0 m_0
     const int nfull = ny / TB * TB;

@@ -391,3 +391,65 @@ def test_programmatic_dependent_launch_changes_nothing(evp, graph, shape, model,
         sim.close()
     for a, b in zip(*out):
         np.testing.assert_array_equal(a, b)
+
+
+def implicit_case(evp, shape, prec, model='oldroyd_b', extra=None):
+    extra = extra or {}
+    nx, ny, nz, walls = shape
+    sim0, st, g, prm = setup_case(evp, shape, model, extra, prec)
+    sim0.close()
+    ly = 2.0 if walls else 2 * np.pi
+    sim = evp.Simulation(evp.make_grid(nx, ny, nz, 2 * np.pi, ly, 2 * np.pi, walls), model,
+                         evp.make_params(Re=2.0, Wi=0.8, beta=0.4, precision=prec, viscous_implicit=1, **extra))
+    sim.set_state(st.U, st.V, st.W, st.p, st.B)
+    return sim, st, g, prm
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_implicit_viscous_steps_fp64(evp, shape):
+    """Eq. NS-num1 read literally (Helmholtz solve per component and substep):
+    two RK3 steps against the oracle, FP64."""
+    sim, st, g, prm = implicit_case(evp, shape, evp.EVP_FP64, 'saramito', {'Bi': 0.4})
+    dt = 2e-3
+    for _ in range(2):
+        sim.step(dt)
+        st = oracle.rk3_step(st, dt, g, prm, implicit_viscous=True)
+    code, bits, maxdiv = sim.sync()
+    for got, ref in zip(fields(sim, evp), oracle_fields(st)):
+        assert rel(got, ref) < 1e-10, rel(got, ref)
+    assert maxdiv < 1e-11
+
+
+@pytest.mark.parametrize("shape", SHAPES[:2])
+def test_implicit_viscous_step_fp32(evp, shape):
+    sim, st, g, prm = implicit_case(evp, shape, evp.EVP_FP32)
+    dt = 2e-3
+    sim.step(dt)
+    st = oracle.rk3_step(st, dt, g, prm, implicit_viscous=True)
+    sim.sync()
+    for q, (got, ref) in enumerate(zip(fields(sim, evp), oracle_fields(st))):
+        if q == 3:
+            continue    # FP32 pressure: see test_rk3_step_fp32
+        assert rel(got, ref) < 1e-5, (q, rel(got, ref))
+
+
+def test_implicit_viscous_channel_mode_decay(evp):
+    """A no-slip shear mode u_j = sin(pi m (j + 1/2)/ny) decays by the closed-form
+    Crank-Nicolson factor prod_k (1 - a_k dt nu lam)/(1 + a_k dt nu lam) per step,
+    here over 5 steps with a dt 20 times the explicit viscous limit."""
+    nx, ny, nz = 8, 24, 8
+    m, Re = 2, 10.0
+    nu, dy = 1.0 / Re, 2.0 / ny
+    U = np.broadcast_to(np.sin(np.pi * m * (np.arange(ny) + 0.5) / ny)[None, :, None], (nz, ny, nx)).copy()
+    sim = evp.Simulation(evp.make_grid(nx, ny, nz, 1.0, 2.0, 1.0, True), 'newtonian',
+                         evp.make_params(Re=Re, beta=1.0, viscous_implicit=1))
+    sim.set_state(U=U)
+    lam = (2 - 2 * np.cos(np.pi * m / ny)) / dy ** 2
+    dt = 20 * dy ** 2 / (6 * nu)
+    f = 1.0
+    for a in oracle.RK3_ALPHA:
+        f *= (1 - a * dt * nu * lam) / (1 + a * dt * nu * lam)
+    for _ in range(5):
+        sim.step(dt)
+    sim.sync()
+    np.testing.assert_allclose(sim.get(evp.EVP_U), U * f ** 5, rtol=0, atol=1e-12)
