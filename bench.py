@@ -425,6 +425,37 @@ def run_fene_turbulence(steps=4):
     return out
 
 
+def run_implicit_viscous(steps=50):
+    """The C2 channel with the implicit viscous option (three Helmholtz solves per
+    substep), FP32, graph replay: what the literal reading of Eq. NS-num1 costs."""
+    import torch
+    from paper_1803_09563_gb300 import evp
+    w = WORKLOAD
+    geo, U, V, W = workload_inputs(w)
+    stream = torch.cuda.Stream()
+    out = {"workload": "saramito_channel_256x128x128_fp32_implicit_viscous", "steps": steps}
+    for name, vi in (('explicit', 0), ('implicit', 1)):
+        grid = evp.make_grid(w['nx'], w['ny'], w['nz'], w['lx'], w['ly'], w['lz'], w['walls_y'])
+        prm = evp.make_params(Re=w['Re'], Wi=w['Wi'], beta=w['beta'], Bi=w['Bi'], dpdx=2.0 / w['Re'],
+                              precision=evp.EVP_FP32, viscous_implicit=vi)
+        sim = evp.Simulation(grid, w['model'], prm, stream=stream.cuda_stream)
+        sim.set_state(U, V, W)
+        evp.evp_set_graph(sim.handle, True)
+        for _ in range(3):
+            sim.step(w['dt'])
+        sim.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            sim.step(w['dt'])
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "Mcell_steps_per_s": w['nx'] * w['ny'] * w['nz'] / (ms * 1e-3) / 1e6}
+        sim.close()
+    return out
+
+
 def run_small_grid():
     """Single-phase Oldroyd-B Taylor-Green box 32^3 in FP64 (the 10-step parity
     workload): per-step latency with direct launches and with graph replay."""
@@ -518,6 +549,7 @@ def main():
         line['serving'] = run_serving()
         line['small_grid'] = run_small_grid()
         line['fene_p_turbulence'] = run_fene_turbulence()
+        line['implicit_viscous'] = run_implicit_viscous()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line['cpu_baseline'] = run_cpu_baseline(args)
