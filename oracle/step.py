@@ -22,6 +22,11 @@ Crank-Nicolson within the substep), N holds -div(uu) + f only, and u* solves
   u* - alpha^k dt mu_s lap(u*) = u^{k-1} + dt [zeta^k N^{k-1} + xi^k N^{k-2}
       - 2 alpha^k grad p^{k-1} + alpha^k (div tau^k + div tau^{k-1}) + alpha^k mu_s lap(u^{k-1})]
 per component, with that component's wall rule (``poisson.solve_helmholtz``).
+
+Rigid particles (``State.particles``, Sec. 3.3.2): after u* (and any implicit
+viscous solve or penalisation) the discrete-forcing IBM of ``ibm`` turns u* into
+u** before the projection; the centres then advance with their prescribed
+velocity over the substep.
 """
 
 from dataclasses import dataclass, field
@@ -31,6 +36,7 @@ import numpy as np
 from .models import tau_from_B
 from .momentum import div_tau, grad_p, laplacian, momentum_rhs_n
 from .poisson import project, solve_helmholtz
+from . import ibm
 from .stress import stress_rhs
 
 # Eq. RK
@@ -52,6 +58,8 @@ class State:
     t: float = 0.0
     nstep: int = 0
     psi: np.ndarray = field(default=None)
+    particles: list = field(default=None)     # rigid particles of the IBM (Reading 19)
+    particle_forces: list = field(default=None)
 
     @staticmethod
     def rest(g, U=None, V=None, W=None):
@@ -67,12 +75,13 @@ class State:
     def copy(self):
         cp = lambda a: None if a is None else np.array(a, copy=True)
         cl = lambda l: None if l is None else [np.array(a, copy=True) for a in l]
+        parts = None if self.particles is None else [dict(q, centre=tuple(q['centre'])) for q in self.particles]
         return State(cp(self.U), cp(self.V), cp(self.W), cp(self.p), cl(self.B),
                      cl(self.RT_hist), None if self.N_hist is None else tuple(cl(self.N_hist)),
-                     self.t, self.nstep, cp(self.psi))
+                     self.t, self.nstep, cp(self.psi), parts, self.particle_forces)
 
 
-def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False):
+def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3):
     """Substep k (0-based index into Eq. RK) of the RK3 scheme; returns a new State.
 
     ``solid`` (optional triple of face arrays alpha) switches on the volume-penalisation
@@ -117,18 +126,28 @@ def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False
         star = [solve_helmholtz(star[d], g, c, 'v' if d == 1 else 'u') for d in range(3)]
     if solid is not None:
         star = [(1.0 - solid[d]) * star[d] for d in range(3)]
+    pforces = None
+    if s.particles:
+        # discrete-forcing IBM of rigid particles (Eqs. IBM a-d, CoVe2) over the
+        # substep's time increment, particles at their positions of level k-1
+        star, pforces = ibm.force(star, g, s.particles, 2.0 * alpha * dt, ibm_iters)
     if g.walls:
         star[1][:, g.ny - 1, :] = 0.0
     # projection, Eqs. NS-num2 and NS-num3
     U, V, W, psi = project(star[0], star[1], star[2], g, 2.0 * alpha * dt)
+    parts = None
+    if s.particles:
+        # prescribed motion: the centres advance with U_p over the substep
+        parts = [dict(q, centre=tuple(np.asarray(q['centre'], dtype=float) + 2.0 * alpha * dt * np.asarray(q['u'])))
+                 for q in s.particles]
     return State(U=U, V=V, W=W, p=s.p + psi, B=Bn, RT_hist=RT, N_hist=N,
-                 t=s.t + (alpha * 2.0) * dt, nstep=s.nstep, psi=psi)
+                 t=s.t + (alpha * 2.0) * dt, nstep=s.nstep, psi=psi, particles=parts, particle_forces=pforces)
 
 
-def rk3_step(s, dt, g, prm, force=None, solid=None, implicit_viscous=False):
-    """One full RK3 step (three substeps); ``solid`` and ``implicit_viscous`` as in
-    rk3_substep."""
+def rk3_step(s, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3):
+    """One full RK3 step (three substeps); ``solid``, ``implicit_viscous`` and the
+    IBM options as in rk3_substep."""
     for k in range(3):
-        s = rk3_substep(s, k, dt, g, prm, force, solid, implicit_viscous)
+        s = rk3_substep(s, k, dt, g, prm, force, solid, implicit_viscous, ibm_iters)
     s.nstep += 1
     return s
