@@ -40,7 +40,7 @@ const double RK_XI[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 const char* KERNEL_NAMES[K_COUNT] = {"stress_weno_update", "momentum_predictor", "div_fft_x",
                                      "fft_z_forward",      "fft_y_modal_solve",  "thomas_y_fp64",
                                      "fft_z_inverse",      "ifft_x_psi",         "project_correct",
-                                     "levelset_stage",     "interface_force"};
+                                     "levelset_stage",     "interface_force",    "ibm_forcing"};
 
 bool is_2a3b(int n) {
     if (n < 1) return false;
@@ -109,6 +109,11 @@ struct evp_state_s {
     double* mass;        // mass correction: 2 x block partials, v0, d
     double2* helm[3][2]; // implicit viscous, walls: Thomas tables per substep, (u/w, v)
     double helm_dt;      // dt the Helmholtz tables were built for
+    // rigid particles (discrete-forcing IBM): one device block holding the arrays below
+    int n_part, n_lag, ibm_iters;
+    void* ibm_block;
+    double *i_off, *i_dvl, *i_centre, *i_vel, *i_omg, *i_Facc, *i_dF, *i_force;
+    int *i_owner, *i_start;
     long long nstep;     // AB2 steps taken
     int cu, cb;          // current velocity / B buffer
     // CUDA-graph replay of evp_step: one executable graph per parity of the B
@@ -575,6 +580,35 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
         for (int q = 0; q < 3; ++q)
             if (int r = run_helmholtz<T>(s, star[q], c, k, q == 1)) return r;
     }
+    if (s->n_part > 0) {
+        // discrete-forcing IBM of the rigid particles: u* -> u** (Eqs. IBM, CoVe2)
+        IbmArgs<T> b;
+        b.U[0] = static_cast<T*>(s->U[1 - cu]);
+        b.U[1] = static_cast<T*>(s->V[1 - cu]);
+        b.U[2] = static_cast<T*>(s->W[1 - cu]);
+        b.off = s->i_off;
+        b.owner = s->i_owner;
+        b.start = s->i_start;
+        b.dvl = s->i_dvl;
+        b.centre = s->i_centre;
+        b.pvel = s->i_vel;
+        b.pomg = s->i_omg;
+        b.Facc = s->i_Facc;
+        b.dF = s->i_dF;
+        b.pforce = s->i_force;
+        b.nl = s->n_lag;
+        b.np = s->n_part;
+        b.nx = s->g.nx;
+        b.ny = s->g.ny;
+        b.nz = s->g.nz;
+        b.dx = s->g.lx / s->g.nx;
+        b.dy = s->g.ly / s->g.ny;
+        b.dz = s->g.lz / s->g.nz;
+        b.y0 = s->g.walls_y ? -0.5 * s->g.ly : 0.0;
+        b.dts = 2.0 * al * dt;
+        cudaError_t e = launch_ibm<T>(b, s->ibm_iters, s->st, th);
+        if (e != cudaSuccess) return cuda_fail(e, "ibm");
+    }
     const double coef = 2.0 * al * dt;
     int r = run_poisson<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
                            static_cast<const T*>(s->W[1 - cu]), nullptr, 1.0 / coef, static_cast<T*>(s->PSI));
@@ -848,6 +882,9 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
     s->elt = s->fp32 ? 4 : 8;
     s->use_graph = false;
     s->pdl = true;
+    s->n_part = s->n_lag = 0;
+    s->ibm_iters = 3;
+    s->ibm_block = nullptr;
     for (auto& gr : s->graphs) gr.valid = false;
     s->N = (size_t)grid->nx * grid->ny * grid->nz;
     s->nxh = grid->nx / 2 + 1;
@@ -921,6 +958,7 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
 int evp_destroy(evp_state* s) {
     if (!s) return EVP_OK;
     if (s->st) cudaStreamSynchronize(s->st);
+    if (s->ibm_block) cudaFree(s->ibm_block);
     for (auto& p : s->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -1041,6 +1079,105 @@ extern "C" int evp_set_pdl(evp_state* s, int enable) {
             cudaGraphExecDestroy(gr.exec);
             gr.valid = false;
         }
+    return EVP_OK;
+}
+
+extern "C" int evp_set_particles(evp_state* s, int n, const double* desc, int iters) {
+    if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (s->ab2) return fail(EVP_ERR_STATE, "rigid particles belong to the RK3 step");
+    if (n < 0 || n > 4096 || (n > 0 && !desc)) return fail(EVP_ERR_ARG, "bad particle count or descriptor");
+    if (iters < 1 || iters > 20) return fail(EVP_ERR_ARG, "iters must be 1..20");
+    const evp_grid& g = s->g;
+    const double dx = g.lx / g.nx, dy = g.ly / g.ny, dz = g.lz / g.nz;
+    if (n > 0 && (std::fabs(dx - dy) > 1e-12 * dx || std::fabs(dx - dz) > 1e-12 * dx))
+        return fail(EVP_ERR_ARG, "the IBM needs cubic cells (dx = dy = dz)");
+    // Lagrangian points (Reading 19): retracted sphere, spiral lattice, equal shell volumes
+    std::vector<double> off, dvl, centre, vel, omg;
+    std::vector<int> owner, start(1, 0);
+    const double golden = M_PI * (3.0 - std::sqrt(5.0));
+    for (int p = 0; p < n; ++p) {
+        const double* d = desc + 10 * p;
+        const double R = d[3];
+        if (!(R >= 2.0 * dx)) return fail(EVP_ERR_ARG, "particle radius must be at least 2 dx");
+        if (g.walls_y && !(std::fabs(d[1]) + R + 2.0 * dy <= 0.5 * g.ly))
+            return fail(EVP_ERR_ARG, "particles must stay R + 2 dy away from the walls");
+        for (int q = 0; q < 10; ++q)
+            if (!std::isfinite(d[q])) return fail(EVP_ERR_ARG, "non-finite particle descriptor");
+        const double rr = R - 0.3 * dx;
+        const int nl = (int)std::lround(M_PI / 3.0 * (12.0 * (rr / dx) * (rr / dx) + 1.0));
+        for (int l = 0; l < nl; ++l) {
+            const double z = 1.0 - (2.0 * l + 1.0) / nl, rho = std::sqrt(1.0 - z * z), th = golden * l;
+            off.push_back(rr * rho * std::cos(th));
+            off.push_back(rr * rho * std::sin(th));
+            off.push_back(rr * z);
+            owner.push_back(p);
+        }
+        start.push_back(start.back() + nl);
+        dvl.push_back(M_PI * dx * (12.0 * rr * rr + dx * dx) / (3.0 * nl));
+        for (int q = 0; q < 3; ++q) {
+            centre.push_back(d[q]);
+            vel.push_back(d[4 + q]);
+            omg.push_back(d[7 + q]);
+        }
+    }
+    CK(cudaStreamSynchronize(s->st));
+    for (auto& gr : s->graphs)   // the step graph holds the particle arrays
+        if (gr.valid) {
+            cudaGraphExecDestroy(gr.exec);
+            gr.valid = false;
+        }
+    if (s->ibm_block) {
+        cudaFree(s->ibm_block);
+        s->ibm_block = nullptr;
+    }
+    s->n_part = s->n_lag = 0;
+    if (n == 0) return EVP_OK;
+    const size_t nl = owner.size();
+    const size_t doubles = 3 * nl + n + 3 * n * 3 + 3 * nl * 2 + 6 * n;
+    const size_t bytes = doubles * sizeof(double) + (nl + n + 1) * sizeof(int);
+    if (cudaMalloc(&s->ibm_block, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->ibm_block = nullptr;
+        return fail(EVP_ERR_OOM, "particle arrays");
+    }
+    double* b = static_cast<double*>(s->ibm_block);
+    s->i_off = b;
+    s->i_dvl = s->i_off + 3 * nl;
+    s->i_centre = s->i_dvl + n;
+    s->i_vel = s->i_centre + 3 * n;
+    s->i_omg = s->i_vel + 3 * n;
+    s->i_Facc = s->i_omg + 3 * n;
+    s->i_dF = s->i_Facc + 3 * nl;
+    s->i_force = s->i_dF + 3 * nl;
+    s->i_owner = reinterpret_cast<int*>(s->i_force + 6 * n);
+    s->i_start = s->i_owner + nl;
+    CK(cudaMemcpy(s->i_off, off.data(), off.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->i_dvl, dvl.data(), dvl.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->i_centre, centre.data(), centre.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->i_vel, vel.data(), vel.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->i_omg, omg.data(), omg.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemset(s->i_Facc, 0, 3 * nl * sizeof(double)));
+    CK(cudaMemset(s->i_force, 0, 6 * n * sizeof(double)));
+    CK(cudaMemcpy(s->i_owner, owner.data(), owner.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->i_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
+    s->n_part = n;
+    s->n_lag = (int)nl;
+    s->ibm_iters = iters;
+    return EVP_OK;
+}
+
+extern "C" int evp_get_particles(evp_state* s, int n, double* out) {
+    if (!s || !out) return fail(EVP_ERR_ARG, "null state or output");
+    if (n != s->n_part) return fail(EVP_ERR_ARG, "n must equal the number of particles set");
+    if (n == 0) return EVP_OK;
+    CK(cudaStreamSynchronize(s->st));
+    std::vector<double> c(3 * (size_t)n), f(6 * (size_t)n);
+    CK(cudaMemcpy(c.data(), s->i_centre, c.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(f.data(), s->i_force, f.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int p = 0; p < n; ++p) {
+        for (int q = 0; q < 3; ++q) out[9 * p + q] = c[3 * p + q];
+        for (int q = 0; q < 6; ++q) out[9 * p + 3 + q] = f[6 * p + q];
+    }
     return EVP_OK;
 }
 

@@ -29,6 +29,7 @@ enum KernelId {
     K_CORRECT,        // S8: u = u* - c grad psi, p += psi, FP64 divergence residual
     K_LEVELSET,       // S9: TVD-RK3 stage of level-set advection or re-distancing
     K_INTERFACE,      // S9: H, normals, curvature, CSF and buoyancy force
+    K_IBM,            // discrete-forcing IBM of rigid particles (multi-direct iterations)
     K_COUNT
 };
 
@@ -255,6 +256,26 @@ struct IfaceArgs {
     T eps, sigma, drho_g;
 };
 
+// discrete-forcing IBM of rigid particles (k_ibm.cu); Lagrangian points of
+// particle p are l = start[p] .. start[p+1]-1
+template <typename T>
+struct IbmArgs {
+    T* U[3];                // u* -> u** in place
+    const double* off;      // [nl][3] point offsets from the particle centre
+    const int* owner;       // [nl] particle of each point
+    const int* start;       // [np+1]
+    const double* dvl;      // [np] volume carried by each point of the particle
+    double* centre;         // [np][3] (advanced by the finishing kernel)
+    const double* pvel;     // [np][3] prescribed velocity
+    const double* pomg;     // [np][3] prescribed angular velocity
+    double* Facc;           // [nl][3] accumulated Lagrangian force
+    double* dF;             // [nl][3] this iteration's increment
+    double* pforce;         // [np][6] force and torque on each particle
+    int nl, np, nx, ny, nz;
+    double dx, dy, dz, y0;  // cell sizes, y of the bottom of the box
+    double dts;             // the substep's time increment 2 alpha dt
+};
+
 // mass-preserving level-set shift (two-phase step): phi <- phi + d with d from
 // Newton iterations on the smoothed drop volume
 template <typename T>
@@ -438,6 +459,9 @@ size_t iface_partials(const Geo<T>& g);
 
 template <typename T>
 cudaError_t launch_interface(const Geo<T>& g, const IfaceArgs<T>& a, cudaStream_t st, const TimingHook& th);
+
+template <typename T>
+cudaError_t launch_ibm(const IbmArgs<T>& a, int iters, cudaStream_t st, const TimingHook& th);
 
 // mode 0: v0 <- drop volume of phi; mode 1: ``iters`` Newton updates of d, then phi += d
 template <typename T>

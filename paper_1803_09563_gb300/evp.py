@@ -79,6 +79,8 @@ def load(path=None):
         'evp_step': (c_int, [c_void_p, c_double]),
         'evp_set_graph': (c_int, [c_void_p, c_int]),
         'evp_set_pdl': (c_int, [c_void_p, c_int]),
+        'evp_set_particles': (c_int, [c_void_p, c_int, c_void_p, c_int]),
+        'evp_get_particles': (c_int, [c_void_p, c_int, c_void_p]),
         'evp_substep': (c_int, [c_void_p, c_double, c_int]),
         'evp_project': (c_int, [c_void_p]),
         'evp_poisson_solve': (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -105,7 +107,7 @@ def exported_symbols():
     return ['evp_state_bytes', 'evp_init', 'evp_destroy', 'evp_set_field', 'evp_get_field', 'evp_step',
             'evp_substep', 'evp_project', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_sync', 'evp_kernel_timing',
             'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error', 'evp_poisson_solve_static',
-            'evp_set_graph', 'evp_selftest', 'evp_set_pdl']
+            'evp_set_graph', 'evp_selftest', 'evp_set_pdl', 'evp_set_particles', 'evp_get_particles']
 
 
 def _check(code):
@@ -187,6 +189,21 @@ def evp_set_graph(state, enable):
 
 def evp_set_pdl(state, enable):
     return _check(load().evp_set_pdl(state, int(bool(enable))))
+
+
+def evp_set_particles(state, particles, iters=3):
+    """``particles``: sequence of (centre (3), radius, velocity (3), angular velocity (3))."""
+    desc = np.ascontiguousarray(np.asarray([list(c) + [r] + list(u) + list(w) for c, r, u, w in particles],
+                                           dtype=np.float64).reshape(-1))
+    n = len(particles)
+    return _check(load().evp_set_particles(state, n, desc.ctypes.data if n else None, int(iters)))
+
+
+def evp_get_particles(state, n):
+    """(n, 9) array: centre, force and torque on each particle (last substep)."""
+    out = np.zeros((max(n, 1), 9), dtype=np.float64)
+    _check(load().evp_get_particles(state, n, out.ctypes.data))
+    return out[:n]
 
 
 def evp_substep(state, dt, k):

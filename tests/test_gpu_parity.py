@@ -453,3 +453,78 @@ def test_implicit_viscous_channel_mode_decay(evp):
         sim.step(dt)
     sim.sync()
     np.testing.assert_allclose(sim.get(evp.EVP_U), U * f ** 5, rtol=0, atol=1e-12)
+
+
+PARTICLES = [((0.72, 0.95, 1.1), 0.3, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0)),
+             ((1.35, 1.05, 0.55), 0.25, (0.2, -0.1, 0.05), (0.3, -0.4, 1.5))]
+
+
+def particle_case(evp, prec, walls=False):
+    n = 32
+    shape = (n, 24, 16, True) if walls else (n, n, n, False)
+    nx, ny, nz, _ = shape
+    lx, ly, lz = (2.0, 1.5, 1.0) if walls else (2.0, 2.0, 2.0)
+    geo = inputs.geometry(nx, ny, nz, lx, ly, lz, walls)
+    U, V, W = inputs.scale_max(*inputs.random_solenoidal(geo, 5, 3), 1.0)
+    if walls:
+        U = U + inputs.poiseuille(geo)[0]
+    g = oracle.Grid(nx, ny, nz, lx, ly, lz, walls)
+    prm = oracle.Params.from_groups('oldroyd_b', Re=5.0, Wi=0.8, beta=0.4)
+    sim = evp.Simulation(evp.make_grid(nx, ny, nz, lx, ly, lz, walls), 'oldroyd_b',
+                         evp.make_params(Re=5.0, Wi=0.8, beta=0.4, precision=prec))
+    parts = PARTICLES if not walls else [((1.0, 0.05, 0.5), 0.3, (0.1, 0.0, 0.0), (0.0, 0.0, 0.8))]
+    sim.set_state(U, V, W)
+    evp.evp_set_particles(sim.handle, parts, iters=3)
+    st = oracle.State.rest(g, U, V, W)
+    if prec == evp.EVP_FP32:
+        rd = lambda a: a.astype(np.float32).astype(np.float64)
+        st.U, st.V, st.W = rd(st.U), rd(st.V), rd(st.W)
+    if walls:
+        st.V[:, -1] = 0.0
+    st.particles = [{'centre': c, 'radius': r, 'u': u, 'omega': w} for c, r, u, w in parts]
+    return sim, st, g, prm, len(parts)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_ibm_particles_fp64(evp, walls):
+    """Discrete-forcing IBM (Eqs. IBM a-d, CoVe2) with a fixed and a moving,
+    spinning sphere: two RK3 steps against the oracle, fields, centres, forces."""
+    sim, st, g, prm, n = particle_case(evp, evp.EVP_FP64, walls)
+    dt = 2e-3
+    for _ in range(2):
+        sim.step(dt)
+        st = oracle.rk3_step(st, dt, g, prm)
+    code, bits, maxdiv = sim.sync()
+    for got, ref in zip(fields(sim, evp), oracle_fields(st)):
+        assert rel(got, ref) < 1e-10, rel(got, ref)
+    assert maxdiv < 1e-11
+    out = evp.evp_get_particles(sim.handle, n)
+    for p in range(n):
+        np.testing.assert_allclose(out[p, :3], st.particles[p]['centre'], rtol=0, atol=1e-14)
+        ft = np.concatenate(st.particle_forces[p])
+        assert np.abs(out[p, 3:] - ft).max() < 1e-9 * np.abs(ft).max(), (out[p, 3:], ft)
+
+
+def test_ibm_particles_fp32(evp):
+    sim, st, g, prm, n = particle_case(evp, evp.EVP_FP32)
+    dt = 2e-3
+    sim.step(dt)
+    st = oracle.rk3_step(st, dt, g, prm)
+    sim.sync()
+    for q, (got, ref) in enumerate(zip(fields(sim, evp), oracle_fields(st))):
+        if q == 3:
+            continue    # FP32 pressure: see test_rk3_step_fp32
+        assert rel(got, ref) < 1e-5, (q, rel(got, ref))
+
+
+def test_ibm_rejects_bad_particles(evp):
+    sim = evp.Simulation(evp.make_grid(32, 24, 16, 2.0, 1.5, 1.0, True), 'newtonian', evp.make_params(Re=5.0))
+    for bad in ([((1.0, 0.0, 0.5), 0.1, (0, 0, 0), (0, 0, 0))],          # radius below 2 dx
+                [((1.0, 0.5, 0.5), 0.3, (0, 0, 0), (0, 0, 0))]):          # too close to the top wall
+        with pytest.raises(evp.EvpError) as e:
+            evp.evp_set_particles(sim.handle, bad)
+        assert e.value.code == evp.EVP_ERR_ARG
+    sim2 = evp.Simulation(evp.make_grid(32, 24, 16, 2.0, 2.0, 1.0, True), 'newtonian', evp.make_params(Re=5.0))
+    with pytest.raises(evp.EvpError):
+        evp.evp_set_particles(sim2.handle, [((1.0, 0.0, 0.5), 0.3, (0, 0, 0), (0, 0, 0))])   # non-cubic cells
+    evp.evp_set_particles(sim.handle, [])
