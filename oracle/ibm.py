@@ -24,6 +24,17 @@ Reading 19 (the paper gives the scheme but not these details):
     U_p, omega_p; the centre moves with U_p); dt_s is the substep's time increment
     2 alpha^k dt (it cancels in u**, only the reported forces depend on it);
   * particles stay at least R + 2 dx away from walls (no wall stencils).
+Reading 20 (free motion; the paper gives Eqs. NewtonEulerWim1/2 and says they are
+integrated with the RK3 scheme): per substep, with dt_s = 2 alpha^k dt, the
+particle's inner-fluid integrals I_u = int_Vp u dV and I_r = int_Vp r x u dV taken
+as sums over velocity nodes of phi_s u dV (phi_s = solid fraction of the node's
+control volume from 4^3 sub-samples, r from the centre to the node) of u^{k-1}
+(before) and of u** (after the forcing), at the centre X^{k-1}:
+  rho_p V_p (U^k - U^{k-1}) = -dt_s sum F_l dV_l + (I_u^k - I_u^{k-1}) + dt_s (rho_p - 1) V_p g,
+  I_p (omega^k - omega^{k-1}) = -dt_s sum r_l x F_l dV_l + (I_r^k - I_r^{k-1}),
+  X^k = X^{k-1} + dt_s (U^k + U^{k-1}) / 2,
+rho_f = 1, V_p = 4 pi R^3/3, I_p = 2 rho_p V_p R^2 / 5, g along -y; no collisions.
+A prescribed particle keeps U_p and omega_p and moves by dt_s U_p.
 """
 
 import numpy as np
@@ -129,3 +140,54 @@ def force(star, g, particles, dts, iters):
     for pts, off, dvl, target, Facc in layout:
         out.append((-(Facc * dvl).sum(axis=0), -(np.cross(off, Facc) * dvl).sum(axis=0)))
     return ustar, out
+
+
+def inner_integrals(U, V, W, g, centre, radius, samples=4):
+    """(I_u, I_r): sums of phi_s u dV and phi_s r x u dV over the velocity nodes
+    (Reading 20); x and z (and a periodic y) use the minimum-image offset."""
+    sub = (np.arange(samples) + 0.5) / samples - 0.5
+    cell = g.dx * g.dy * g.dz
+    L = (g.lx, g.ly, g.lz)
+    periodic = (True, not g.walls, True)
+    Iu, Ir = np.zeros(3), np.zeros(3)
+    for comp, F in enumerate((U, V, W)):
+        xs, ys, zs, y0 = _lattice(g, comp)
+        def rel(c, d):
+            r = c - centre[d]
+            if periodic[d]:
+                r = (r + 0.5 * L[d]) % L[d] - 0.5 * L[d]
+            return r
+        rx = rel(xs, 0)[None, None, :]
+        ry = rel(ys, 1)[None, :, None]
+        rz = rel(zs, 2)[:, None, None]
+        frac = np.zeros(g.shape)
+        for ox in sub:
+            for oy in sub:
+                for oz in sub:
+                    d2 = (rx + ox * g.dx) ** 2 + (ry + oy * g.dy) ** 2 + (rz + oz * g.dz) ** 2
+                    frac += d2 < radius * radius
+        w = frac / samples ** 3 * cell * F
+        r = (rx + 0 * w, ry + 0 * w, rz + 0 * w)
+        Iu[comp] += w.sum()
+        # r x u: with (c, a, b) cyclic, (r x u)_a gains r_b u_c and (r x u)_b loses r_a u_c
+        a, b = (comp + 1) % 3, (comp + 2) % 3
+        Ir[a] += (r[b] * w).sum()
+        Ir[b] -= (r[a] * w).sum()
+    return Iu, Ir
+
+
+def particle_update(p, force, torque, I0, I1, dts, gravity):
+    """Reading 20: one substep of the Newton-Euler equations of a free sphere
+    (``p['rho']`` > 0) or of a prescribed one; returns the updated particle."""
+    c = np.asarray(p['centre'], dtype=float)
+    u0 = np.asarray(p['u'], dtype=float)
+    if p.get('rho', 0.0) > 0.0:
+        R, rho = p['radius'], p['rho']
+        vp = 4.0 / 3.0 * np.pi * R ** 3
+        ip = 0.4 * rho * vp * R * R
+        g = np.array([0.0, -gravity, 0.0])
+        u1 = u0 + (dts * np.asarray(force) + (I1[0] - I0[0]) + dts * (rho - 1.0) * vp * g) / (rho * vp)
+        w1 = np.asarray(p['omega'], dtype=float) + (dts * np.asarray(torque) + (I1[1] - I0[1])) / ip
+        return dict(p, centre=tuple(c + 0.5 * dts * (u1 + u0)), u=tuple(u1), omega=tuple(w1))
+    return dict(p, centre=tuple(c + dts * u0))
+

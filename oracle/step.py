@@ -81,7 +81,7 @@ class State:
                      self.t, self.nstep, cp(self.psi), parts, self.particle_forces)
 
 
-def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3):
+def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3, gravity=0.0):
     """Substep k (0-based index into Eq. RK) of the RK3 scheme; returns a new State.
 
     ``solid`` (optional triple of face arrays alpha) switches on the volume-penalisation
@@ -129,25 +129,29 @@ def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False
     pforces = None
     if s.particles:
         # discrete-forcing IBM of rigid particles (Eqs. IBM a-d, CoVe2) over the
-        # substep's time increment, particles at their positions of level k-1
+        # substep's time increment, particles at their positions of level k-1;
+        # inner-fluid integrals of free particles before and after (Reading 20)
+        I0 = [ibm.inner_integrals(s.U, s.V, s.W, g, q['centre'], q['radius']) if q.get('rho', 0.0) > 0.0 else None
+              for q in s.particles]
         star, pforces = ibm.force(star, g, s.particles, 2.0 * alpha * dt, ibm_iters)
+        I1 = [ibm.inner_integrals(star[0], star[1], star[2], g, q['centre'], q['radius'])
+              if q.get('rho', 0.0) > 0.0 else None for q in s.particles]
     if g.walls:
         star[1][:, g.ny - 1, :] = 0.0
     # projection, Eqs. NS-num2 and NS-num3
     U, V, W, psi = project(star[0], star[1], star[2], g, 2.0 * alpha * dt)
     parts = None
     if s.particles:
-        # prescribed motion: the centres advance with U_p over the substep
-        parts = [dict(q, centre=tuple(np.asarray(q['centre'], dtype=float) + 2.0 * alpha * dt * np.asarray(q['u'])))
-                 for q in s.particles]
+        parts = [ibm.particle_update(q, f[0], f[1], a, b, 2.0 * alpha * dt, gravity)
+                 for q, f, a, b in zip(s.particles, pforces, I0, I1)]
     return State(U=U, V=V, W=W, p=s.p + psi, B=Bn, RT_hist=RT, N_hist=N,
                  t=s.t + (alpha * 2.0) * dt, nstep=s.nstep, psi=psi, particles=parts, particle_forces=pforces)
 
 
-def rk3_step(s, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3):
+def rk3_step(s, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3, gravity=0.0):
     """One full RK3 step (three substeps); ``solid``, ``implicit_viscous`` and the
     IBM options as in rk3_substep."""
     for k in range(3):
-        s = rk3_substep(s, k, dt, g, prm, force, solid, implicit_viscous, ibm_iters)
+        s = rk3_substep(s, k, dt, g, prm, force, solid, implicit_viscous, ibm_iters, gravity)
     s.nstep += 1
     return s

@@ -79,3 +79,56 @@ def test_multi_direct_forcing_drives_the_surface_velocity_to_the_target():
     q = {'centre': (1.2, 1.2, 1.2), 'radius': 0.4, 'u': (0, 0, 0), 'omega': (0, 0, 2.0)}
     us, ft = ibm.force([np.zeros(g.shape)] * 3, g, [q], 0.01, 3)
     assert ft[0][1][2] < 0 and np.abs(ft[0][0]).max() < 1e-3 * abs(ft[0][1][2])
+
+
+def test_inner_integrals_of_uniform_and_rigid_fields():
+    """For u = const the integrals are the sampled particle volume times u (and
+    about zero moment); for a rigid rotation u = omega x r about the centre the
+    angular integral is the sampled moment of inertia, close to 2/5 V R^2 omega."""
+    g = oracle.Grid(32, 32, 32, 2.0, 2.0, 2.0)
+    c, R = (1.0, 1.03, 0.97), 0.45
+    ones, zero = np.ones(g.shape), np.zeros(g.shape)
+    Iu, Ir = ibm.inner_integrals(0.7 * ones, zero, -0.2 * ones, g, c, R)
+    vol = 4 / 3 * np.pi * R ** 3
+    assert abs(Iu[0] / 0.7 - vol) < 0.01 * vol and abs(Iu[2] / -0.2 - vol) < 0.01 * vol and Iu[1] == 0.0
+    assert np.abs(Ir).max() < 1e-3 * vol
+    # rigid rotation about z through the centre, sampled on each lattice
+    om = 1.3
+    xs, ys, zs, y0 = ibm._lattice(g, 0)
+    Uz = -om * (ys[None, :, None] - c[1]) + 0 * g.zeros()
+    xs, ys, zs, y0 = ibm._lattice(g, 1)
+    Vz = om * (xs[None, None, :] - c[0]) + 0 * g.zeros()
+    Iu, Ir = ibm.inner_integrals(Uz, Vz, zero, g, c, R)
+    assert abs(Ir[2] - 0.4 * vol * R * R * om) < 0.03 * 0.4 * vol * R * R * om
+    assert np.abs(Iu).max() < 1e-3 * vol
+
+
+def test_free_particle_first_substep_under_gravity():
+    """A heavy sphere at rest in fluid at rest: in the first substep the IBM force
+    and the inner-fluid integrals vanish, so U^1 = dt_s (1 - 1/rho) g and
+    X^1 = X^0 + dt_s U^1 / 2 (closed form)."""
+    g = oracle.Grid(24, 24, 24, 2.4, 2.4, 2.4)
+    p = {'centre': (1.2, 1.2, 1.2), 'radius': 0.4, 'u': (0, 0, 0), 'omega': (0, 0, 0), 'rho': 2.5}
+    s = oracle.State.rest(g)
+    s.particles = [p]
+    prm = oracle.Params.from_groups('newtonian', 10.0, 1.0, 1.0)
+    out = oracle.rk3_substep(s, 0, 0.01, g, prm, gravity=9.81)
+    dts = 2 * oracle.RK3_ALPHA[0] * 0.01
+    uy = -dts * (1 - 1 / 2.5) * 9.81
+    q = out.particles[0]
+    assert abs(q['u'][1] - uy) < 1e-14 and abs(q['u'][0]) < 1e-14 and abs(q['u'][2]) < 1e-14
+    assert abs(q['centre'][1] - (1.2 + 0.5 * dts * uy)) < 1e-14
+
+
+def test_neutrally_buoyant_sphere_in_uniform_flow_keeps_its_velocity():
+    """rho_p = rho_f, u = U everywhere and U_p = U: the forcing and the change of
+    the inner integrals vanish, so the particle keeps U and the flow is unchanged."""
+    g = oracle.Grid(24, 24, 24, 2.4, 2.4, 2.4)
+    U0 = (0.3, -0.1, 0.2)
+    s = oracle.State.rest(g, U0[0] + 0 * g.zeros(), U0[1] + 0 * g.zeros(), U0[2] + 0 * g.zeros())
+    s.particles = [{'centre': (1.2, 1.2, 1.2), 'radius': 0.4, 'u': U0, 'omega': (0, 0, 0), 'rho': 1.0}]
+    prm = oracle.Params.from_groups('newtonian', 10.0, 1.0, 1.0)
+    out = oracle.rk3_step(s, 0.01, g, prm)
+    assert np.abs(np.asarray(out.particles[0]['u']) - U0).max() < 1e-12
+    assert np.abs(np.asarray(out.particles[0]['omega'])).max() < 1e-12
+    assert np.abs(out.U - U0[0]).max() < 1e-12 and np.abs(out.V - U0[1]).max() < 1e-12
