@@ -107,7 +107,7 @@ typedef struct {
     double rho_ratio;   /* AB2: 0 = Boussinesq drop (drho_g); > 0 = drop / outer density
                            ratio, solved with the constant-coefficient splitting of
                            Eqs. poisson-LS and projection-LS, rho_0 = the smaller density */
-    double gravity;     /* AB2 with rho_ratio > 0: gravity g along -y                   */
+    double gravity;     /* gravity g along -y: AB2 with rho_ratio > 0, and free IBM particles */
     int penalization;   /* RK3: volume-penalisation IBM for fixed obstacles (Sec. 3.3.2):
                            u** = (1 - alpha) u* before each projection (Eq. forceAdded),
                            alpha = solid fraction of the control volume around each
@@ -192,25 +192,29 @@ int evp_set_graph(evp_state* s, int enable);
  * step graphs are rebuilt on the next step.  The paper has no counterpart.      */
 int evp_set_pdl(evp_state* s, int enable);
 
-/* Rigid spherical particles with prescribed motion, coupled to the RK3 step by the
- * discrete-forcing immersed boundary method of Sec. 3.3.2 (Eqs. IBM a-d with
- * the multi-direct forcing of Eq. CoVe2, iters iterations per substep, 3 in the
- * paper): after u* is formed, the velocity interpolated with the three-point
- * Roma kernel to Lagrangian points on each sphere (retracted by 0.3 dx, spiral
- * lattice, about one point per dx^2 of surface) is driven towards the surface
- * velocity U_p + omega_p x r, and u** replaces u* in the projection.
- *   desc: host, n x 10 doubles per particle: centre x, y, z; radius; U_p (3);
- *         omega_p (3).  Centres then move with U_p.  n = 0 removes them.
- * Needs cubic cells, radius >= 2 dx, and (walls) |y_c| + R + 2 dy <= ly/2.
- * Free motion (the Newton-Euler equations with the inner-fluid terms) is not
- * part of this call.  Synchronises; the step graph is rebuilt.
+/* Rigid spherical particles coupled to the RK3 step by the discrete-forcing
+ * immersed boundary method of Sec. 3.3.2 (Eqs. IBM a-d with the multi-direct
+ * forcing of Eq. CoVe2, iters iterations per substep, 3 in the paper): after u*
+ * is formed, the velocity interpolated with the three-point Roma kernel to
+ * Lagrangian points on each sphere (retracted by 0.3 dx, spiral lattice, about
+ * one point per dx^2 of surface) is driven towards the surface velocity
+ * U_p + omega_p x r, and u** replaces u* in the projection.
+ *   desc: host, n x 11 doubles per particle: centre x, y, z; radius; U_p (3);
+ *         omega_p (3); density ratio rho_p/rho_f.  A ratio of 0 prescribes the
+ *         motion (U_p, omega_p constant, the centre moves with U_p); a positive
+ *         ratio makes the sphere free: the Newton-Euler equations of the paper
+ *         (Eqs. NewtonEulerWim1/2, with the inner-fluid integrals, gravity
+ *         evp_params.gravity along -y, no collisions) advance U_p, omega_p and the
+ *         centre every substep.  n = 0 removes the particles.
+ * Needs cubic cells, radius >= 2 dx, 2 (R + 2 dx) below the periodic lengths and
+ * (walls) |y_c| + R + 2 dy <= ly/2.  Synchronises; the step graph is rebuilt.
  * Errors: EVP_ERR_ARG, EVP_ERR_STATE (AB2 states), EVP_ERR_OOM.               */
 int evp_set_particles(evp_state* s, int n, const double* desc, int iters);
 
-/* Per particle, 9 doubles into out (host): current centre (3), then the force
- * (3) and torque about the centre (3) that the fluid exerted on it in the last
- * substep, -sum F_l dV_l and -sum r_l x F_l dV_l.  n must equal the count set.
- * Synchronises the state's stream.                                             */
+/* Per particle, 15 doubles into out (host): current centre (3), velocity (3),
+ * angular velocity (3), then the force (3) and torque about the centre (3) that
+ * the IBM exerted on it in the last substep, -sum F_l dV_l and
+ * -sum r_l x F_l dV_l.  n must equal the count set.  Synchronises.             */
 int evp_get_particles(evp_state* s, int n, double* out);
 
 /* With integrator EVP_AB2, evp_step is one two-phase AB2 step of size dt

@@ -112,8 +112,9 @@ struct evp_state_s {
     // rigid particles (discrete-forcing IBM): one device block holding the arrays below
     int n_part, n_lag, ibm_iters;
     void* ibm_block;
-    double *i_off, *i_dvl, *i_centre, *i_vel, *i_omg, *i_Facc, *i_dF, *i_force;
+    double *i_off, *i_dvl, *i_centre, *i_vel, *i_omg, *i_Facc, *i_dF, *i_force, *i_rad, *i_dens, *i_int;
     int *i_owner, *i_start;
+    int any_free;
     long long nstep;     // AB2 steps taken
     int cu, cb;          // current velocity / B buffer
     // CUDA-graph replay of evp_step: one executable graph per parity of the B
@@ -596,17 +597,31 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
         b.Facc = s->i_Facc;
         b.dF = s->i_dF;
         b.pforce = s->i_force;
+        b.pvel_w = s->i_vel;
+        b.pomg_w = s->i_omg;
+        b.prad = s->i_rad;
+        b.pdens = s->i_dens;
+        b.I0 = s->i_int;
+        b.I1 = s->i_int + 6 * s->n_part;
         b.nl = s->n_lag;
         b.np = s->n_part;
         b.nx = s->g.nx;
         b.ny = s->g.ny;
         b.nz = s->g.nz;
+        b.walls = s->g.walls_y;
+        b.any_free = s->any_free;
         b.dx = s->g.lx / s->g.nx;
         b.dy = s->g.ly / s->g.ny;
         b.dz = s->g.lz / s->g.nz;
         b.y0 = s->g.walls_y ? -0.5 * s->g.ly : 0.0;
+        b.lx = s->g.lx;
+        b.ly = s->g.ly;
+        b.lz = s->g.lz;
         b.dts = 2.0 * al * dt;
-        cudaError_t e = launch_ibm<T>(b, s->ibm_iters, s->st, th);
+        b.gravity = s->prm.gravity;
+        const T* uold[3] = {static_cast<const T*>(s->U[cu]), static_cast<const T*>(s->V[cu]),
+                            static_cast<const T*>(s->W[cu])};
+        cudaError_t e = launch_ibm<T>(b, uold, s->ibm_iters, s->st, th);
         if (e != cudaSuccess) return cuda_fail(e, "ibm");
     }
     const double coef = 2.0 * al * dt;
@@ -885,6 +900,7 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
     s->n_part = s->n_lag = 0;
     s->ibm_iters = 3;
     s->ibm_block = nullptr;
+    s->any_free = 0;
     for (auto& gr : s->graphs) gr.valid = false;
     s->N = (size_t)grid->nx * grid->ny * grid->nz;
     s->nxh = grid->nx / 2 + 1;
@@ -1092,17 +1108,20 @@ extern "C" int evp_set_particles(evp_state* s, int n, const double* desc, int it
     if (n > 0 && (std::fabs(dx - dy) > 1e-12 * dx || std::fabs(dx - dz) > 1e-12 * dx))
         return fail(EVP_ERR_ARG, "the IBM needs cubic cells (dx = dy = dz)");
     // Lagrangian points (Reading 19): retracted sphere, spiral lattice, equal shell volumes
-    std::vector<double> off, dvl, centre, vel, omg;
+    std::vector<double> off, dvl, centre, vel, omg, rad, dens;
     std::vector<int> owner, start(1, 0);
     const double golden = M_PI * (3.0 - std::sqrt(5.0));
     for (int p = 0; p < n; ++p) {
-        const double* d = desc + 10 * p;
+        const double* d = desc + 11 * p;
         const double R = d[3];
         if (!(R >= 2.0 * dx)) return fail(EVP_ERR_ARG, "particle radius must be at least 2 dx");
         if (g.walls_y && !(std::fabs(d[1]) + R + 2.0 * dy <= 0.5 * g.ly))
             return fail(EVP_ERR_ARG, "particles must stay R + 2 dy away from the walls");
-        for (int q = 0; q < 10; ++q)
+        for (int q = 0; q < 11; ++q)
             if (!std::isfinite(d[q])) return fail(EVP_ERR_ARG, "non-finite particle descriptor");
+        if (d[10] < 0.0) return fail(EVP_ERR_ARG, "particle density ratio must be >= 0 (0: prescribed motion)");
+        if (2.0 * (R + 2.0 * dx) >= std::min(g.lx, g.lz) || (!g.walls_y && 2.0 * (R + 2.0 * dy) >= g.ly))
+            return fail(EVP_ERR_ARG, "particle too large for the periodic box");
         const double rr = R - 0.3 * dx;
         const int nl = (int)std::lround(M_PI / 3.0 * (12.0 * (rr / dx) * (rr / dx) + 1.0));
         for (int l = 0; l < nl; ++l) {
@@ -1119,6 +1138,8 @@ extern "C" int evp_set_particles(evp_state* s, int n, const double* desc, int it
             vel.push_back(d[4 + q]);
             omg.push_back(d[7 + q]);
         }
+        rad.push_back(R);
+        dens.push_back(d[10]);
     }
     CK(cudaStreamSynchronize(s->st));
     for (auto& gr : s->graphs)   // the step graph holds the particle arrays
@@ -1133,7 +1154,7 @@ extern "C" int evp_set_particles(evp_state* s, int n, const double* desc, int it
     s->n_part = s->n_lag = 0;
     if (n == 0) return EVP_OK;
     const size_t nl = owner.size();
-    const size_t doubles = 3 * nl + n + 3 * n * 3 + 3 * nl * 2 + 6 * n;
+    const size_t doubles = 3 * nl + n + 3 * n * 3 + 3 * nl * 2 + 6 * n + 2 * n + 12 * n;
     const size_t bytes = doubles * sizeof(double) + (nl + n + 1) * sizeof(int);
     if (cudaMalloc(&s->ibm_block, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -1149,7 +1170,10 @@ extern "C" int evp_set_particles(evp_state* s, int n, const double* desc, int it
     s->i_Facc = s->i_omg + 3 * n;
     s->i_dF = s->i_Facc + 3 * nl;
     s->i_force = s->i_dF + 3 * nl;
-    s->i_owner = reinterpret_cast<int*>(s->i_force + 6 * n);
+    s->i_rad = s->i_force + 6 * n;
+    s->i_dens = s->i_rad + n;
+    s->i_int = s->i_dens + n;
+    s->i_owner = reinterpret_cast<int*>(s->i_int + 12 * n);
     s->i_start = s->i_owner + nl;
     CK(cudaMemcpy(s->i_off, off.data(), off.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s->i_dvl, dvl.data(), dvl.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -1158,11 +1182,16 @@ extern "C" int evp_set_particles(evp_state* s, int n, const double* desc, int it
     CK(cudaMemcpy(s->i_omg, omg.data(), omg.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemset(s->i_Facc, 0, 3 * nl * sizeof(double)));
     CK(cudaMemset(s->i_force, 0, 6 * n * sizeof(double)));
+    CK(cudaMemcpy(s->i_rad, rad.data(), rad.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->i_dens, dens.data(), dens.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemset(s->i_int, 0, 12 * n * sizeof(double)));
     CK(cudaMemcpy(s->i_owner, owner.data(), owner.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(s->i_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
     s->n_part = n;
     s->n_lag = (int)nl;
     s->ibm_iters = iters;
+    s->any_free = 0;
+    for (double r : dens) s->any_free |= r > 0.0;
     return EVP_OK;
 }
 
@@ -1171,12 +1200,18 @@ extern "C" int evp_get_particles(evp_state* s, int n, double* out) {
     if (n != s->n_part) return fail(EVP_ERR_ARG, "n must equal the number of particles set");
     if (n == 0) return EVP_OK;
     CK(cudaStreamSynchronize(s->st));
-    std::vector<double> c(3 * (size_t)n), f(6 * (size_t)n);
+    std::vector<double> c(3 * (size_t)n), u(3 * (size_t)n), w(3 * (size_t)n), f(6 * (size_t)n);
     CK(cudaMemcpy(c.data(), s->i_centre, c.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(u.data(), s->i_vel, u.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(w.data(), s->i_omg, w.size() * sizeof(double), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(f.data(), s->i_force, f.size() * sizeof(double), cudaMemcpyDeviceToHost));
     for (int p = 0; p < n; ++p) {
-        for (int q = 0; q < 3; ++q) out[9 * p + q] = c[3 * p + q];
-        for (int q = 0; q < 6; ++q) out[9 * p + 3 + q] = f[6 * p + q];
+        for (int q = 0; q < 3; ++q) {
+            out[15 * p + q] = c[3 * p + q];
+            out[15 * p + 3 + q] = u[3 * p + q];
+            out[15 * p + 6 + q] = w[3 * p + q];
+        }
+        for (int q = 0; q < 6; ++q) out[15 * p + 9 + q] = f[6 * p + q];
     }
     return EVP_OK;
 }

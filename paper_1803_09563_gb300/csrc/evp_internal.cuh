@@ -271,9 +271,17 @@ struct IbmArgs {
     double* Facc;           // [nl][3] accumulated Lagrangian force
     double* dF;             // [nl][3] this iteration's increment
     double* pforce;         // [np][6] force and torque on each particle
-    int nl, np, nx, ny, nz;
+    double* pvel_w;         // [np][3] velocity, updated for free particles
+    double* pomg_w;         // [np][3] angular velocity, updated for free particles
+    const double* prad;     // [np] radius
+    const double* pdens;    // [np] density ratio rho_p / rho_f (0: prescribed motion)
+    double* I0;             // [np][6] inner-fluid integrals int u dV, int r x u dV before the forcing
+    double* I1;             // [np][6] ... after it
+    int nl, np, nx, ny, nz, walls, any_free;
     double dx, dy, dz, y0;  // cell sizes, y of the bottom of the box
+    double lx, ly, lz;
     double dts;             // the substep's time increment 2 alpha dt
+    double gravity;         // along -y, acting on free particles
 };
 
 // mass-preserving level-set shift (two-phase step): phi <- phi + d with d from
@@ -460,8 +468,12 @@ size_t iface_partials(const Geo<T>& g);
 template <typename T>
 cudaError_t launch_interface(const Geo<T>& g, const IfaceArgs<T>& a, cudaStream_t st, const TimingHook& th);
 
+// the whole particle coupling of one substep: inner integrals of u^{k-1} (free
+// particles), the multi-direct forcing of u* (in a.U), force and torque, inner
+// integrals of u**, particle update
 template <typename T>
-cudaError_t launch_ibm(const IbmArgs<T>& a, int iters, cudaStream_t st, const TimingHook& th);
+cudaError_t launch_ibm(const IbmArgs<T>& a, const T* const uold[3], int iters, cudaStream_t st,
+                       const TimingHook& th);
 
 // mode 0: v0 <- drop volume of phi; mode 1: ``iters`` Newton updates of d, then phi += d
 template <typename T>

@@ -192,16 +192,22 @@ def evp_set_pdl(state, enable):
 
 
 def evp_set_particles(state, particles, iters=3):
-    """``particles``: sequence of (centre (3), radius, velocity (3), angular velocity (3))."""
-    desc = np.ascontiguousarray(np.asarray([list(c) + [r] + list(u) + list(w) for c, r, u, w in particles],
-                                           dtype=np.float64).reshape(-1))
+    """``particles``: sequence of (centre (3), radius, velocity (3), angular velocity (3)
+    [, density ratio rho_p/rho_f: 0 or absent = prescribed motion])."""
+    rows = []
+    for q in particles:
+        c, r, u, w = q[:4]
+        dens = q[4] if len(q) > 4 else 0.0
+        rows.append(list(c) + [r] + list(u) + list(w) + [dens])
+    desc = np.ascontiguousarray(np.asarray(rows, dtype=np.float64).reshape(-1))
     n = len(particles)
     return _check(load().evp_set_particles(state, n, desc.ctypes.data if n else None, int(iters)))
 
 
 def evp_get_particles(state, n):
-    """(n, 9) array: centre, force and torque on each particle (last substep)."""
-    out = np.zeros((max(n, 1), 9), dtype=np.float64)
+    """(n, 15) array: centre, velocity, angular velocity, force and torque on each
+    particle (the last two from the last substep)."""
+    out = np.zeros((max(n, 1), 15), dtype=np.float64)
     _check(load().evp_get_particles(state, n, out.ctypes.data))
     return out[:n]
 

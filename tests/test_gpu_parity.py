@@ -502,7 +502,7 @@ def test_ibm_particles_fp64(evp, walls):
     for p in range(n):
         np.testing.assert_allclose(out[p, :3], st.particles[p]['centre'], rtol=0, atol=1e-14)
         ft = np.concatenate(st.particle_forces[p])
-        assert np.abs(out[p, 3:] - ft).max() < 1e-9 * np.abs(ft).max(), (out[p, 3:], ft)
+        assert np.abs(out[p, 9:] - ft).max() < 1e-9 * np.abs(ft).max(), (out[p, 9:], ft)
 
 
 def test_ibm_particles_fp32(evp):
@@ -528,3 +528,43 @@ def test_ibm_rejects_bad_particles(evp):
     with pytest.raises(evp.EvpError):
         evp.evp_set_particles(sim2.handle, [((1.0, 0.0, 0.5), 0.3, (0, 0, 0), (0, 0, 0))])   # non-cubic cells
     evp.evp_set_particles(sim.handle, [])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ibm_free_particles(evp, prec):
+    """Free spheres (Newton-Euler with the inner-fluid integrals, gravity along -y):
+    a heavy one released in a shear flow and a light spinning one; two RK3 steps
+    against the oracle: fields, centres, velocities, angular velocities."""
+    n, L = 32, 2.0
+    geo = inputs.geometry(n, n, n, L, L, L)
+    U, V, W = inputs.scale_max(*inputs.random_solenoidal(geo, 9, 3), 0.5)
+    g = oracle.Grid(n, n, n, L, L, L)
+    prm = oracle.Params.from_groups('oldroyd_b', Re=5.0, Wi=0.8, beta=0.4)
+    sim = evp.Simulation(evp.make_grid(n, n, n, L, L, L), 'oldroyd_b',
+                         evp.make_params(Re=5.0, Wi=0.8, beta=0.4, precision=prec, gravity=3.0))
+    parts = [((0.7, 1.1, 0.9), 0.3, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), 2.5),
+             ((1.4, 0.8, 1.3), 0.25, (0.1, 0.0, -0.1), (0.0, 0.0, 2.0), 0.8)]
+    sim.set_state(U, V, W)
+    evp.evp_set_particles(sim.handle, parts, iters=3)
+    st = oracle.State.rest(g, U, V, W)
+    if prec == evp.EVP_FP32:
+        rd = lambda a: a.astype(np.float32).astype(np.float64)
+        st.U, st.V, st.W = rd(st.U), rd(st.V), rd(st.W)
+    st.particles = [{'centre': c, 'radius': r, 'u': u, 'omega': w, 'rho': d} for c, r, u, w, d in parts]
+    dt = 2e-3
+    for _ in range(2):
+        sim.step(dt)
+        st = oracle.rk3_step(st, dt, g, prm, gravity=3.0)
+    sim.sync()
+    tol = 1e-10 if prec == 0 else 1e-5
+    for q, (got, ref) in enumerate(zip(fields(sim, evp), oracle_fields(st))):
+        if prec == 1 and q == 3:
+            continue
+        assert rel(got, ref) < tol, (q, rel(got, ref))
+    out = evp.evp_get_particles(sim.handle, 2)
+    for p in range(2):
+        ref = st.particles[p]
+        assert np.abs(out[p, :3] - ref['centre']).max() < (1e-13 if prec == 0 else 1e-7)
+        for a, b in ((out[p, 3:6], ref['u']), (out[p, 6:9], ref['omega'])):
+            assert np.abs(a - np.asarray(b)).max() < (1e-9 if prec == 0 else 1e-4) * max(1.0, np.abs(b).max()), (a, b)
+
