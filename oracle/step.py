@@ -23,6 +23,12 @@ Crank-Nicolson within the substep), N holds -div(uu) + f only, and u* solves
       - 2 alpha^k grad p^{k-1} + alpha^k (div tau^k + div tau^{k-1}) + alpha^k mu_s lap(u^{k-1})]
 per component, with that component's wall rule (``poisson.solve_helmholtz``).
 
+Soft particles (``State.phis``, Sec. 3.3.2, Reading 21; neo-Hookean model only):
+the solid volume fraction phi_s is advected like B (WENO5 u.grad phi_s with the
+RK3 weights and its own history), B evolves with the neo-Hookean closure (F = a
+= 0) everywhere, and the extra stress is tau = phi_s G (B - I), G = mu_p/lambda:
+elastic in the solid, zero in the (Newtonian) fluid, zero for B = I.
+
 Rigid particles (``State.particles``, Sec. 3.3.2): after u* (and any implicit
 viscous solve or penalisation) the discrete-forcing IBM of ``ibm`` turns u* into
 u** before the projection; the centres then advance with their prescribed
@@ -37,7 +43,8 @@ from .models import tau_from_B
 from .momentum import div_tau, grad_p, laplacian, momentum_rhs_n
 from .poisson import project, solve_helmholtz
 from . import ibm
-from .stress import stress_rhs
+from .stress import centre_velocity, stress_rhs
+from .weno import weno5_derivative
 
 # Eq. RK
 RK3_ALPHA = (4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0)
@@ -60,6 +67,8 @@ class State:
     psi: np.ndarray = field(default=None)
     particles: list = field(default=None)     # rigid particles of the IBM (Reading 19)
     particle_forces: list = field(default=None)
+    phis: np.ndarray = field(default=None)     # solid fraction of soft particles (Reading 21)
+    phis_hist: np.ndarray = field(default=None)
 
     @staticmethod
     def rest(g, U=None, V=None, W=None):
@@ -78,7 +87,8 @@ class State:
         parts = None if self.particles is None else [dict(q, centre=tuple(q['centre'])) for q in self.particles]
         return State(cp(self.U), cp(self.V), cp(self.W), cp(self.p), cl(self.B),
                      cl(self.RT_hist), None if self.N_hist is None else tuple(cl(self.N_hist)),
-                     self.t, self.nstep, cp(self.psi), parts, self.particle_forces)
+                     self.t, self.nstep, cp(self.psi), parts, self.particle_forces, cp(self.phis),
+                     cp(self.phis_hist))
 
 
 def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3, gravity=0.0):
@@ -90,6 +100,18 @@ def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False
     solid volume fraction of the control volume around each velocity node."""
     alpha, zeta, xi = RK3_ALPHA[k], RK3_ZETA[k], RK3_XI[k]
     has_stress = prm.model != 'newtonian'
+    soft = s.phis is not None
+    if soft:
+        # Reading 21: phi_s advected like B (WENO5, RK3 weights), tau = phi_s G (B - I)
+        assert prm.model == 'neo_hookean'
+        uc, vc, wc = centre_velocity(s.U, s.V, s.W, g)
+        Rphi = -(uc * weno5_derivative(s.phis, g, 'x', uc) + vc * weno5_derivative(s.phis, g, 'y', vc)
+                 + wc * weno5_derivative(s.phis, g, 'z', wc))
+        inc = zeta * Rphi + (xi * s.phis_hist if xi != 0.0 else 0.0)
+        phis_new = s.phis + dt * inc
+        gmod = prm.mu_p / prm.lam
+        def soft_tau(B, phi):
+            return [phi * gmod * (B[c] - (1.0 if c in (0, 3, 5) else 0.0)) for c in range(6)]
     # stress update, Eq. rk3tau with RT of Eq. RK-rt
     if has_stress:
         RT = stress_rhs(s.U, s.V, s.W, s.B, g, prm)
@@ -104,7 +126,10 @@ def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False
     # momentum predictor, Eqs. NS-num1 and rk3
     N = momentum_rhs_n(s.U, s.V, s.W, g, 0.0 if implicit_viscous else prm.mu_s, force)
     gp = grad_p(s.p, g)
-    if has_stress:
+    if has_stress and soft:
+        dto = div_tau(soft_tau(s.B, s.phis), g)
+        dtn = div_tau(soft_tau(Bn, phis_new), g)
+    elif has_stress:
         dto = div_tau(tau_from_B(s.B, prm), g)
         dtn = div_tau(tau_from_B(Bn, prm), g)
     vel = (s.U, s.V, s.W)
@@ -145,7 +170,8 @@ def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False
         parts = [ibm.particle_update(q, f[0], f[1], a, b, 2.0 * alpha * dt, gravity)
                  for q, f, a, b in zip(s.particles, pforces, I0, I1)]
     return State(U=U, V=V, W=W, p=s.p + psi, B=Bn, RT_hist=RT, N_hist=N,
-                 t=s.t + (alpha * 2.0) * dt, nstep=s.nstep, psi=psi, particles=parts, particle_forces=pforces)
+                 t=s.t + (alpha * 2.0) * dt, nstep=s.nstep, psi=psi, particles=parts, particle_forces=pforces,
+                 phis=phis_new if soft else None, phis_hist=Rphi if soft else None)
 
 
 def rk3_step(s, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3, gravity=0.0):
