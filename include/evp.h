@@ -129,7 +129,12 @@ typedef struct {
                            u* - alpha^k dt mu_s lap u* = rhs per velocity component and
                            substep (FFT in x, z; FP64 Thomas along a wall-bounded y).
                            Not with penalization.                                       */
-    double reserved[5];
+    int soft_particles; /* RK3, model EVP_NEO_HOOKEAN: soft particles in one continuum
+                           (Sec. 3.3.2): the solid volume fraction phi_s (field EVP_PHI,
+                           0 fluid .. 1 solid) is advected like B (WENO5, RK3 weights)
+                           and the extra stress is phi_s G (B - I), G = mu_p/lambda; the
+                           surrounding fluid is Newtonian (mu_s)                        */
+    double reserved[4];
 } evp_params;
 
 /* Field identifiers for evp_set_field / evp_get_field */
@@ -139,7 +144,8 @@ typedef enum {
     EVP_RT_XX = 10, /* ... EVP_RT_XX+5: RK3 history RT^{k-2} (Eq. RK-rt)          */
     EVP_NH_X = 16,  /* ... EVP_NH_X+2: RK3 history of -div(uu)+viscous+force     */
     EVP_PSI = 19,   /* last projection variable psi (read only)                  */
-    EVP_PHI = 20,   /* AB2 two-phase states: level set phi at cell centres       */
+    EVP_PHI = 20,   /* AB2: level set phi at cell centres; RK3 with soft_particles:
+                       the solid volume fraction phi_s                              */
     EVP_SOLID_X = 21, EVP_SOLID_Y = 22, EVP_SOLID_Z = 23,
                     /* penalization states: solid fractions alpha at u, v, w nodes */
     EVP_NFIELDS = 24

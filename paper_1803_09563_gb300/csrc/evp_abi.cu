@@ -107,6 +107,8 @@ struct evp_state_s {
     double* partials;
     double* mean_1mH;
     double* mass;        // mass correction: 2 x block partials, v0, d
+    void* PHS[2];        // soft particles: solid fraction, buffer cb = current level
+    void* PHSH;          // soft particles: history of its right-hand side
     double2* helm[3][2]; // implicit viscous, walls: Thomas tables per substep, (u/w, v)
     double helm_dt;      // dt the Helmholtz tables were built for
     // rigid particles (discrete-forcing IBM): one device block holding the arrays below
@@ -224,6 +226,11 @@ int validate(const evp_grid* g, evp_model model, const evp_params* p) {
     } else if (p->ls_mass_iters != 0) {
         return fail(EVP_ERR_ARG, "the level-set mass correction is part of the AB2 two-phase step");
     }
+    if (p->soft_particles) {
+        if (p->soft_particles != 1) return fail(EVP_ERR_ARG, "soft_particles must be 0 or 1");
+        if (model != EVP_NEO_HOOKEAN) return fail(EVP_ERR_ARG, "soft particles need the neo-Hookean model");
+        if (p->integrator != EVP_RK3) return fail(EVP_ERR_ARG, "soft particles are part of the RK3 step");
+    }
     if (p->viscous_implicit) {
         if (p->viscous_implicit != 1) return fail(EVP_ERR_ARG, "viscous_implicit must be 0 or 1");
         if (p->integrator != EVP_RK3) return fail(EVP_ERR_ARG, "the implicit viscous option is part of the RK3 step");
@@ -288,6 +295,9 @@ size_t plan(evp_state* s, char* base) {
         for (int q = 0; q < 3; ++q) sol[q] = P(N * e);
     void* mean = ab2 ? P(sizeof(double)) : nullptr;
     void* mass = (ab2 && s->prm.ls_mass_iters > 0) ? P((2 * nparts + 2) * sizeof(double)) : nullptr;
+    void* phs[3] = {nullptr, nullptr, nullptr};
+    if (s->prm.soft_particles)
+        for (int q = 0; q < 3; ++q) phs[q] = P(N * e);
     void* helm[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     if (s->prm.viscous_implicit && g.walls_y)
         for (int k = 0; k < 3; ++k)
@@ -317,6 +327,9 @@ size_t plan(evp_state* s, char* base) {
         for (int q = 0; q < 3; ++q) s->SOL[q] = sol[q];
         s->mean_1mH = static_cast<double*>(mean);
         s->mass = static_cast<double*>(mass);
+        s->PHS[0] = phs[0];
+        s->PHS[1] = phs[1];
+        s->PHSH = phs[2];
         for (int k = 0; k < 3; ++k)
             for (int q = 0; q < 2; ++q) s->helm[k][q] = static_cast<double2*>(helm[k][q]);
         s->helm_dt = -1.0;
@@ -571,6 +584,23 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
         a.trig = s->prm.abc_amp != 0.0 ? static_cast<const T*>(s->trig) : nullptr;
         for (int q = 0; q < 3; ++q) a.solid[q] = static_cast<const T*>(s->SOL[q]);
         a.cn = s->prm.viscous_implicit ? 1 : 0;
+        if (s->prm.soft_particles) {
+            // solid fraction phi^k from phi^{k-1} with u^{k-1}, then tau = phi_s G (B - I)
+            PhisArgs<T> f;
+            f.U = static_cast<const T*>(s->U[cu]);
+            f.V = static_cast<const T*>(s->V[cu]);
+            f.W = static_cast<const T*>(s->W[cu]);
+            f.phi = static_cast<const T*>(s->PHS[cb]);
+            f.phin = static_cast<T*>(s->PHS[1 - cb]);
+            f.hist = static_cast<T*>(s->PHSH);
+            f.dt_zeta = T(dt * ze);
+            f.dt_xi = T(dt * xi);
+            f.read_hist = read_hist;
+            f.write_hist = write_hist;
+            if (cudaError_t e = launch_phis<T>(g, f, s->st, th)) return cuda_fail(e, "solid fraction");
+            a.phis_o = f.phi;
+            a.phis_n = f.phin;
+        }
         cudaError_t e = launch_momentum<T>(g, s->mc, a, s->st, th);
         if (e != cudaSuccess) return cuda_fail(e, "momentum kernel");
     }
@@ -823,7 +853,7 @@ void* field_ptr(evp_state* s, int f) {
     if (f >= EVP_RT_XX && f < EVP_RT_XX + 6) return s->RT[f - EVP_RT_XX];
     if (f >= EVP_NH_X && f < EVP_NH_X + 3) return s->NH[f - EVP_NH_X];
     if (f == EVP_PSI) return s->PSI;
-    if (f == EVP_PHI) return s->ab2 ? s->PHI : nullptr;
+    if (f == EVP_PHI) return s->ab2 ? s->PHI : (s->prm.soft_particles ? s->PHS[s->cb] : nullptr);
     if (f >= EVP_SOLID_X && f <= EVP_SOLID_Z) return s->SOL[f - EVP_SOLID_X];
     return nullptr;
 }
@@ -851,6 +881,11 @@ int init_fields(evp_state* s) {
     CK(cudaMemsetAsync(s->PSI, 0, N * sizeof(T), s->st));
     for (int q = 0; q < 3; ++q)
         if (s->SOL[q]) CK(cudaMemsetAsync(s->SOL[q], 0, N * sizeof(T), s->st));
+    if (s->prm.soft_particles) {
+        CK(cudaMemsetAsync(s->PHS[0], 0, N * sizeof(T), s->st));
+        CK(cudaMemsetAsync(s->PHS[1], 0, N * sizeof(T), s->st));
+        CK(cudaMemsetAsync(s->PHSH, 0, N * sizeof(T), s->st));
+    }
     if (s->ab2) {
         void* z[] = {s->PHI, s->PHI0, s->PHIA, s->PHIB, s->HF, s->NRM[0], s->NRM[1], s->NRM[2],
                      s->FC[0], s->FC[1], s->FC[2], s->POLD};

@@ -174,6 +174,8 @@ struct MomentumArgs {
     int read_hist, write_hist, has_stress;
     T dpdx, abc_amp;
     int cn = 0;        // implicit viscous option: N without the viscous term, alpha mu lap(u) explicit
+    const T* phis_o = nullptr;   // soft particles: solid fraction at levels k-1 and k,
+    const T* phis_n = nullptr;   //   tau = phi_s G (B - I) (neo-Hookean model)
     const T* trig;     // ABC force tables: sin/cos of k x_i, k y_j, k z_k (6 arrays)
     const T* solid[3]; // volume penalisation: solid fractions at u, v, w nodes (null: off)
 };
@@ -254,6 +256,20 @@ struct IfaceArgs {
     double* partials;  // per-block sums of 1 - H
     double* mean_1mH;  // domain mean of 1 - H
     T eps, sigma, drho_g;
+};
+
+// soft particles: RK3 update of the solid fraction, phi^k = phi^{k-1} + dt (zeta R
+// + xi R_hist) with R = -u^{k-1}.grad phi^{k-1} (WENO5)
+template <typename T>
+struct PhisArgs {
+    const T* U;
+    const T* V;
+    const T* W;
+    const T* phi;      // level k-1
+    T* phin;           // level k
+    T* hist;           // R of the previous substep (in / out)
+    T dt_zeta, dt_xi;
+    int read_hist, write_hist;
 };
 
 // discrete-forcing IBM of rigid particles (k_ibm.cu); Lagrangian points of
@@ -471,6 +487,9 @@ cudaError_t launch_interface(const Geo<T>& g, const IfaceArgs<T>& a, cudaStream_
 // the whole particle coupling of one substep: inner integrals of u^{k-1} (free
 // particles), the multi-direct forcing of u* (in a.U), force and torque, inner
 // integrals of u**, particle update
+template <typename T>
+cudaError_t launch_phis(const Geo<T>& g, const PhisArgs<T>& a, cudaStream_t st, const TimingHook& th);
+
 template <typename T>
 cudaError_t launch_ibm(const IbmArgs<T>& a, const T* const uold[3], int iters, cudaStream_t st,
                        const TimingHook& th);

@@ -148,11 +148,12 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
             voff[q][r] = 0;
             vfac[q][r] = 0;
         }
-        if (VEC || e >= SW * VH) continue;
+        if (e >= SW * VH) continue;
         const int gx = pmod(i0 + vx - 1, g.nx);
         int src;
         row_rule(j0 + vy - 1, 3, src);
-        coff[r] = (size_t)src * g.nx + gx;
+        coff[r] = (size_t)src * g.nx + gx;        // also the soft particles' solid-fraction reads
+        if (VEC) continue;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             vfac[q][r] = (signed char)row_rule(j0 + vy - 1, q, src);
@@ -257,9 +258,20 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
                                        + gm * (Fo * Br[c][e] - (d ? av : T(0)));
                 }
             } else if (MODEL == EVP_NEO_HOOKEAN) {
-                // Table 1: tau = G B
+                if (a.phis_o) {
+                    // soft particles: tau = phi_s G (B - I) at both levels
+                    const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
+                    const T po = gm * __ldg(a.phis_o + pb + coff[r]), pn = gm * __ldg(a.phis_n + pb + coff[r]);
 #pragma unroll
-                for (int c = 0; c < 6; ++c) sm.S[c][slot][e] = gm * Br[6 + c][e] + gm * Br[c][e];
+                    for (int c = 0; c < 6; ++c) {
+                        const T d = (c == 0 || c == 3 || c == 5) ? T(1) : T(0);
+                        sm.S[c][slot][e] = pn * (Br[6 + c][e] - d) + po * (Br[c][e] - d);
+                    }
+                } else {
+                    // Table 1: tau = G B
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) sm.S[c][slot][e] = gm * Br[6 + c][e] + gm * Br[c][e];
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {

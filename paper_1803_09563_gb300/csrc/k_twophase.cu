@@ -131,6 +131,37 @@ __global__ void __launch_bounds__(256) k_sum_partials(const double* partials, in
     if (threadIdx.x == 0) *out = red[0] * scale;
 }
 
+// Soft particles: the solid fraction advected like B, one thread per cell
+template <typename T>
+__global__ void __launch_bounds__(256) k_phis(const Geo<T> g, const PhisArgs<T> a) {
+    pdl_wait();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const size_t c0 = lin(g, i, j, k);
+    // centre velocity: mean of the two faces of the cell
+    const T uc = T(0.5) * (__ldg(a.U + c0) + ld_uw(g, a.U, i - 1, j, k));
+    const T vc = T(0.5) * (__ldg(a.V + c0) + ld_v(g, a.V, i, j - 1, k));
+    const T wc = T(0.5) * (__ldg(a.W + c0) + ld_uw(g, a.W, i, j, k - 1));
+    const int sx = uc > T(0) ? 1 : -1, sy = vc > T(0) ? 1 : -1, sz = wc > T(0) ? 1 : -1;
+    T p[3][6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        p[0][m] = ld_c(g, a.phi, i + (m - 3) * sx, j, k);
+        p[1][m] = ld_c(g, a.phi, i, j + (m - 3) * sy, k);
+        p[2][m] = ld_c(g, a.phi, i, j, k + (m - 3) * sz);
+    }
+    const T adv = upwind_term(fabs(uc) * g.idx, p[0][0], p[0][1], p[0][2], p[0][3], p[0][4], p[0][5])
+                  + upwind_term(fabs(vc) * g.idy, p[1][0], p[1][1], p[1][2], p[1][3], p[1][4], p[1][5])
+                  + upwind_term(fabs(wc) * g.idz, p[2][0], p[2][1], p[2][2], p[2][3], p[2][4], p[2][5]);
+    const T R = -adv;
+    T inc = a.dt_zeta * R;
+    if (a.read_hist) inc += a.dt_xi * a.hist[c0];
+    a.phin[c0] = __ldg(a.phi + c0) + inc;
+    if (a.write_hist) a.hist[c0] = R;
+}
+
 // Mass correction: per-block FP64 sums of 1 - H(phi + d) and delta(phi + d)
 template <typename T>
 __global__ void __launch_bounds__(256) k_mass_partials(const Geo<T> g, const MassArgs<T> a, int np) {
@@ -521,6 +552,15 @@ cudaError_t launch_interface(const Geo<T>& g, const IfaceArgs<T>& a, cudaStream_
 }
 
 template <typename T>
+cudaError_t launch_phis(const Geo<T>& g, const PhisArgs<T>& a, cudaStream_t st, const TimingHook& th) {
+    dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    th.b(K_LEVELSET);
+    k_phis<T><<<grid, block, 0, st>>>(g, a);
+    th.e(K_LEVELSET);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_mass_correct(const Geo<T>& g, const MassArgs<T>& a, int mode, int iters, cudaStream_t st,
                                 const TimingHook& th) {
     dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
@@ -568,6 +608,7 @@ cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>&
                                              const TimingHook&);                                              \
     template cudaError_t launch_mass_correct<T>(const Geo<T>&, const MassArgs<T>&, int, int, cudaStream_t,    \
                                                 const TimingHook&);                                           \
+    template cudaError_t launch_phis<T>(const Geo<T>&, const PhisArgs<T>&, cudaStream_t, const TimingHook&);  \
     template cudaError_t launch_momentum_ab2<T>(const Geo<T>&, int, const MomAB2Args<T>&, cudaStream_t,       \
                                                 const TimingHook&);                                           \
     template cudaError_t launch_split_rhs<T>(const Geo<T>&, const SplitArgs<T>&, cudaStream_t, const TimingHook&); \
