@@ -602,3 +602,54 @@ def test_soft_particles(evp, shape, prec):
             continue    # FP32 pressure: see test_rk3_step_fp32
         assert rel(got, ref) < tol, (q, rel(got, ref))
     assert rel(sim.get(evp.EVP_PHI), st.phis) < tol
+
+
+ODD_SHAPES = [(24, 9, 27, False), (16, 7, 9, True)]
+
+
+@pytest.mark.parametrize("shape", ODD_SHAPES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rk3_step_odd_sizes(evp, shape, prec):
+    """Odd counts: a periodic ny = 9 and nz = 27 (radix-3 FFTs, an unpaired real
+    line in the x transforms), and a wall-bounded ny = 7 with nz = 9."""
+    sim, st, g, prm = setup_case(evp, shape, 'saramito', {'Bi': 0.4}, prec)
+    dt = 2e-3
+    for _ in range(2):
+        sim.step(dt)
+        st = oracle.rk3_step(st, dt, g, prm)
+    sim.sync()
+    for q, (got, ref) in enumerate(zip(fields(sim, evp), oracle_fields(st))):
+        if prec == 1 and q == 3:
+            continue    # FP32 pressure: see test_rk3_step_fp32
+        assert rel(got, ref) < (1e-10 if prec == 0 else 1e-5), (q, rel(got, ref))
+
+
+@pytest.mark.parametrize("shape", ODD_SHAPES)
+def test_poisson_solve_odd_sizes(evp, shape):
+    import torch
+    nx, ny, nz, walls = shape
+    sim, st, g, prm = setup_case(evp, shape, 'oldroyd_b', {}, evp.EVP_FP64)
+    r = np.random.default_rng(12).standard_normal((nz, ny, nx))
+    r -= r.mean()
+    rd = torch.tensor(r, dtype=torch.float64, device='cuda')
+    psi = torch.empty_like(rd)
+    evp.evp_poisson_solve(sim.handle, rd, psi)
+    sim.sync()
+    ref = oracle.solve_poisson(r, g)
+    got = psi.cpu().numpy()
+    if not walls:
+        got, ref = got - got.mean(), ref - ref.mean()
+    assert rel(got, ref) < 1e-12
+
+
+def test_fene_p_trace_limit_is_reported(evp):
+    """A FENE-P state stretched beyond L^2 raises EVP_BIT_TRACE_LIMIT and evp_sync
+    returns EVP_ERR_UNPHYSICAL (no clamping, no fault)."""
+    n, L2 = 16, 30.0
+    sim = evp.Simulation(evp.make_grid(n, n, n, 1.0, 1.0, 1.0), 'fene_p', evp.make_params(Re=1.0, L2=L2))
+    big = np.full((n, n, n), 1.02 * L2 / 3.0)
+    zero = np.zeros((n, n, n))
+    sim.set_state(B=[big, zero, zero, big, zero, big])
+    sim.step(1e-4)
+    code, bits, _ = sim.sync(raise_on_error=False)
+    assert code == evp.EVP_ERR_UNPHYSICAL and bits & evp.EVP_BIT_TRACE_LIMIT
