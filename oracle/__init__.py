@@ -35,6 +35,19 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   level set (Eqs. ls-adv, normal, curv, reinit) .... pinned (translation, sphere
                                                      curvature, Heaviside volume)
   AB2 (Eqs. ab2tau, ab2) ........................... pinned (2nd-order convergence)
+  density-contrast split projection ................ pinned (div-free, uniform-density limit,
+                                                     fixed point = sparse variable solve)
+  mass-preserving level-set shift .................. pinned (exact undo of a shift,
+                                                     volume conservation)
+  implicit viscous option (Helmholtz) .............. pinned (operator residual, closed-form
+                                                     shear-mode decay, dt^3 local error)
+  volume penalisation .............................. pinned (alpha = 0 bitwise, alpha = 1,
+                                                     solid block)
+  rigid-particle IBM, free motion .................. pinned (Roma moments, linear exactness,
+                                                     conservation, convergence, integrals,
+                                                     first substep under gravity)
+  soft particles ................................... pinned (all-solid and all-fluid limits,
+                                                     transport order)
 """
 
 from .grid import Grid, at  # noqa: F401
@@ -46,3 +59,4 @@ from .poisson import divergence, eigenvalues, solve_poisson, project  # noqa: F4
 from .step import State, rk3_step, rk3_substep, RK3_ALPHA, RK3_ZETA, RK3_XI  # noqa: F401
 from . import levelset  # noqa: F401,E402
 from .ab2 import TwoPhase, ab2_step  # noqa: F401,E402
+from . import ibm  # noqa: F401,E402
