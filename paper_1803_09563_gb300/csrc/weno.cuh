@@ -15,8 +15,19 @@ namespace evp {
 //  * in double precision the weights alpha_k = d_k/e_k^2 are multiplied through by
 //    10 e_1^2 e_2^2 e_3^2, which leaves one division;
 //  * in single precision those products could overflow, so the weights are formed
-//    from three fast reciprocals of the squared indicators (no branch; an
+//    from three approximate reciprocals of the squared indicators (no branch; an
 //    indicator beyond ~1e19 gets a zero weight).
+// Approximate single-precision reciprocal (PTX rcp.approx.ftz.f32, about one ulp;
+// a subnormal result flushes to zero, 1/inf = 0).  The WENO weights below use it
+// directly: their operands are at least the squared epsilon term (~8.5e-13) or
+// overflowed indicators, which should get weight zero anyway, so the operand range
+// handling of the general fast division is not needed.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5, T scale) {
     const T eps = T(1.0e-6 * 12.0 / 13.0), r = T(3.0 / 13.0);
@@ -35,11 +46,10 @@ __device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5, T scale) {
     s2 *= s2;
     s3 *= s3;
     if (sizeof(T) == 4) {
-        const float x1 = __fdividef(1.0f, float(s1)), x2 = __fdividef(1.0f, float(s2)),
-                    x3 = __fdividef(1.0f, float(s3));
+        const float x1 = rcp_approx(float(s1)), x2 = rcp_approx(float(s2)), x3 = rcp_approx(float(s3));
         const float num = fmaf(x3, float(q3), fmaf(x2, float(q2), x1 * float(q1))) * float(scale);
         const float den = fmaf(3.0f, x3, fmaf(6.0f, x2, x1));
-        return T(__fdividef(num, den));
+        return T(num * rcp_approx(den));
     }
     const T w1 = s2 * s3, w2 = s1 * s3, w3 = s1 * s2;
     const T den = fma(T(3), w3, fma(T(6), w2, w1));
