@@ -425,7 +425,8 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             av = T(0);
         } else if (MODEL == EVP_FENE_P) {
             const T tr = w[0][3] + w[3][3] + w[5][3];
-            F = kL2 / (kL2 - tr);
+            if (sizeof(T) == 4) F = kL2 * T(rcp_approx(float(kL2 - tr)));
+            else F = kL2 / (kL2 - tr);
             av = kaf;
         } else if (MODEL == EVP_SARAMITO) {
             T gm = kgm;
@@ -439,10 +440,17 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             for (int c = 0; c < 6; ++c) t[c] = gm * (w[c][3] - ((c == 0 || c == 3 || c == 5) ? T(1) : T(0)));
             const T tr3 = (t[0] + t[3] + t[5]) * T(1.0 / 3.0);
             const T d0 = t[0] - tr3, d3 = t[3] - tr3, d5 = t[5] - tr3;
-            const T mag = sqrt(T(0.5) * (d0 * d0 + d3 * d3 + d5 * d5) + t[1] * t[1] + t[2] * t[2] + t[4] * t[4]);
+            const T mag2 = T(0.5) * (d0 * d0 + d3 * d3 + d5 * d5) + t[1] * t[1] + t[2] * t[2] + t[4] * t[4];
             const T tyv = kty;
-            if (mag > T(0)) {
-                const T f = T(1) - tyv / mag;
+            if (sizeof(T) == 4) {
+                // F = max(0, 1 - tau_y/|tau^d|) with the approximate reciprocal square
+                // root instruction; tau_y = 0 is exactly Oldroyd-B (F = 1)
+                float rs;
+                asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(float(mag2)));
+                const T f = T(1) - tyv * T(rs);
+                F = tyv > T(0) ? (mag2 > T(0) && f > T(0) ? f : T(0)) : T(1);
+            } else if (mag2 > T(0)) {
+                const T f = T(1) - tyv / sqrt(mag2);
                 F = f > T(0) ? f : T(0);
             } else {
                 F = tyv > T(0) ? T(0) : T(1);
