@@ -475,16 +475,40 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         const size_t cell = (size_t)k * plane + (size_t)j * g.nx + i;
         const T* Bk = sm.B[k & 1][0];
         const T vx_ = fabs(uc) * g.idx, vy_ = fabs(vc) * g.idy, vz_ = fabs(wc) * g.idz;
-        T bn[6];
+        T bn[6], advc[6];
+        if constexpr (sizeof(T) == 4) {
+            // single precision: the components in pairs (xx, xy), (xz, yy), (yz, zz),
+            // which share the upwind side and |u|/h, on the packed f32x2 instructions
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const float* P0 = Bk + (2 * p) * BPL;
+                const float* P1 = P0 + BPL;
+                auto at = [&](int off) { return make_float2(P0[ob + off], P1[ob + off]); };
+                auto wz = [&](int m) { return make_float2(w[2 * p][m], w[2 * p + 1][m]); };
+                float2 s = upwind_term2(splat2(vx_), at(-3 * sx), at(-2 * sx), at(-sx), at(0), at(sx), at(2 * sx));
+                s = add2(s, upwind_term2(splat2(vy_), at(-3 * syw), at(-2 * syw), at(-syw), at(0), at(syw), at(2 * syw)));
+                // z stencil from the register window, mirrored for a non-positive w
+                s = add2(s, upwind_term2(splat2(vz_), zpos ? wz(0) : wz(6), zpos ? wz(1) : wz(5), zpos ? wz(2) : wz(4),
+                                         wz(3), zpos ? wz(4) : wz(2), zpos ? wz(5) : wz(1)));
+                advc[2 * p] = s.x;
+                advc[2 * p + 1] = s.y;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const T* P = Bk + c * BPL;
+                T adv = upwind_term(vx_, P[ob - 3 * sx], P[ob - 2 * sx], P[ob - sx], P[ob], P[ob + sx], P[ob + 2 * sx]);
+                adv += upwind_term(vy_, P[ob - 3 * syw], P[ob - 2 * syw], P[ob - syw], P[ob], P[ob + syw], P[ob + 2 * syw]);
+                // z stencil from the register window, mirrored for a non-positive w
+                const T z0 = zpos ? w[c][0] : w[c][6], z1 = zpos ? w[c][1] : w[c][5], z2 = zpos ? w[c][2] : w[c][4];
+                const T z4 = zpos ? w[c][4] : w[c][2], z5 = zpos ? w[c][5] : w[c][1];
+                advc[c] = adv + upwind_term(vz_, z0, z1, z2, w[c][3], z4, z5);
+            }
+        }
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const T* P = Bk + c * BPL;
-            T adv = upwind_term(vx_, P[ob - 3 * sx], P[ob - 2 * sx], P[ob - sx], P[ob], P[ob + sx], P[ob + 2 * sx]);
-            adv += upwind_term(vy_, P[ob - 3 * syw], P[ob - 2 * syw], P[ob - syw], P[ob], P[ob + syw], P[ob + 2 * syw]);
-            // z stencil from the register window, mirrored for a non-positive w
-            const T z0 = zpos ? w[c][0] : w[c][6], z1 = zpos ? w[c][1] : w[c][5], z2 = zpos ? w[c][2] : w[c][4];
-            const T z4 = zpos ? w[c][4] : w[c][2], z5 = zpos ? w[c][5] : w[c][1];
-            adv += upwind_term(vz_, z0, z1, z2, w[c][3], z4, z5);
+            const T adv = advc[c];
             const int ra = row_of(c), cb = col_of(c);
             T ucd = T(0);
 #pragma unroll

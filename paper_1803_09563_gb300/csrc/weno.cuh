@@ -57,6 +57,44 @@ __device__ __forceinline__ T weno5(T v1, T v2, T v3, T v4, T v5, T scale) {
     return num / den;
 }
 
+// Packed single-precision pairs (Blackwell f32x2 add / mul / fma: one instruction
+// for both lanes, each lane rounded exactly as the scalar instruction).
+__device__ __forceinline__ float2 splat2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+
+// weno5<float> on two independent stencils at once (the lanes of each argument),
+// with the same operations in the same order.
+__device__ __forceinline__ float2 weno5x2(float2 v1, float2 v2, float2 v3, float2 v4, float2 v5, float2 scale) {
+    const float2 eps = splat2(float(1.0e-6 * 12.0 / 13.0)), r = splat2(float(3.0 / 13.0));
+    const float2 q1 = fma2(v3, splat2(float(11.0 / 6.0)), fma2(v2, splat2(float(-7.0 / 6.0)), mul2(v1, splat2(float(1.0 / 3.0)))));
+    const float2 q2 = fma2(v4, splat2(2.0f), fma2(v3, splat2(5.0f), neg2(v2)));
+    const float2 q3 = fma2(v5, splat2(-0.5f), fma2(v4, splat2(2.5f), v3));
+    const float2 e12 = sub2(v1, v2), e23 = sub2(v2, v3), e34 = sub2(v3, v4), e45 = sub2(v4, v5);
+    const float2 a1 = sub2(e12, e23), a2 = sub2(e23, e34), a3 = sub2(e34, e45);
+    const float2 b1 = fma2(e23, splat2(-2.0f), a1), b2 = add2(e23, e34), b3 = fma2(e34, splat2(2.0f), a3);
+    float2 s1 = fma2(mul2(b1, r), b1, fma2(a1, a1, eps));
+    float2 s2 = fma2(mul2(b2, r), b2, fma2(a2, a2, eps));
+    float2 s3 = fma2(mul2(b3, r), b3, fma2(a3, a3, eps));
+    s1 = mul2(s1, s1);
+    s2 = mul2(s2, s2);
+    s3 = mul2(s3, s3);
+    const float2 x1 = rcp2(s1), x2 = rcp2(s2), x3 = rcp2(s3);
+    const float2 num = mul2(fma2(x3, q3, fma2(x2, q2, mul2(x1, q1))), scale);
+    const float2 den = fma2(splat2(3.0f), x3, fma2(splat2(6.0f), x2, x1));
+    return mul2(num, rcp2(den));
+}
+
+// upwind_term on two stencils at once.
+__device__ __forceinline__ float2 upwind_term2(float2 vih, float2 pm3, float2 pm2, float2 pm1, float2 p0, float2 pp1,
+                                               float2 pp2) {
+    return weno5x2(sub2(pm2, pm3), sub2(pm1, pm2), sub2(p0, pm1), sub2(pp1, p0), sub2(pp2, pp1), vih);
+}
+
 // |u| * (upwind WENO5 derivative) of a centred field along one axis, from the
 // six values phi(c + m*sig*step), m = -3..2, where sig = +1 for a positive
 // velocity (left-biased stencil) and -1 otherwise (right-biased, mirrored; the
