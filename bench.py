@@ -132,12 +132,12 @@ def algorithmic_bytes(kernel, w, elt, walls):
     nxh = w['nx'] // 2 + 1
     spec = 2 * nxh * w['ny'] * w['nz'] * elt     # complex spectral buffer, bytes
     if kernel == 'stress_weno_update':
-        # read u(3) B(6) [+RT(6)], write B(6) [+RT(6)]
-        words = (3 + 6 + 6 + 6) + (3 + 6 + 6 + 6 + 6) + (3 + 6 + 6 + 6)
+        # read u(3) B(6) [+RT(6)], write B(6) [+RT(6)] and the summed stress S(6)
+        words = (3 + 6 + 6 + 6 + 6) + (3 + 6 + 6 + 6 + 6 + 6) + (3 + 6 + 6 + 6 + 6)
         return words * N * elt, 3
     if kernel == 'momentum_predictor':
-        # read u(3) p(1) B^{k-1}(6) B^k(6) [+N(3)], write u*(3) [+N(3)]
-        words = (3 + 1 + 12 + 3 + 3) + (3 + 1 + 12 + 3 + 3 + 3) + (3 + 1 + 12 + 3 + 3)
+        # read u(3) p(1) S(6) [+N(3)], write u*(3) [+N(3)]
+        words = (3 + 1 + 6 + 3 + 3) + (3 + 1 + 6 + 3 + 3 + 3) + (3 + 1 + 6 + 3 + 3)
         return words * N * elt, 3
     if kernel == 'div_fft_x':
         return 3 * (3 * N * elt + spec), 3

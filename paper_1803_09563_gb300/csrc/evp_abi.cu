@@ -78,6 +78,7 @@ struct evp_state_s {
     void* B[2][6];
     void* RT[6];
     void* NH[3];
+    void* S[6];          // RK3 with a stress (not soft particles): tau^k + tau^{k-1}, stress -> momentum
     void* P;
     void* PSI;
     void* spec;
@@ -272,6 +273,11 @@ size_t plan(evp_state* s, char* base) {
         }
     for (int c = 0; c < 6; ++c) { void* p = P(N * e); if (base) s->RT[c] = p; }
     for (int c = 0; c < 3; ++c) { void* p = P(N * e); if (base) s->NH[c] = p; }
+    const bool sum_stress = s->model != EVP_NEWTONIAN && s->prm.integrator != EVP_AB2 && !s->prm.soft_particles;
+    for (int c = 0; c < 6; ++c) {
+        void* p = sum_stress ? P(N * e) : nullptr;
+        if (base) s->S[c] = p;
+    }
     void* p = P(N * e);
     void* psi = P(N * e);
     void* spec = P((size_t)nxh * g.ny * g.nz * 2 * e);
@@ -555,6 +561,7 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
         a.status = s->d_status;
         a.H = nullptr;
         a.mu_p1 = a.mu_p2 = T(0);
+        for (int c = 0; c < 6; ++c) a.S[c] = static_cast<T*>(s->S[c]);
         cudaError_t e = launch_stress<T>(g, s->mc, a, s->st, th);
         if (e != cudaSuccess) return cuda_fail(e, "stress kernel");
     }
@@ -584,6 +591,8 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
         a.trig = s->prm.abc_amp != 0.0 ? static_cast<const T*>(s->trig) : nullptr;
         for (int q = 0; q < 3; ++q) a.solid[q] = static_cast<const T*>(s->SOL[q]);
         a.cn = s->prm.viscous_implicit ? 1 : 0;
+        if (stress)
+            for (int c = 0; c < 6; ++c) a.S[c] = static_cast<const T*>(s->S[c]);
         if (s->prm.soft_particles) {
             // solid fraction phi^k from phi^{k-1} with u^{k-1}, then tau = phi_s G (B - I)
             PhisArgs<T> f;
@@ -912,6 +921,7 @@ size_t evp_state_bytes(const evp_grid* grid, evp_model model, const evp_params* 
     if (validate(grid, model, params) != EVP_OK) return 0;
     evp_state tmp;
     tmp.g = *grid;
+    tmp.model = model;
     tmp.prm = *params;
     tmp.elt = params->precision == EVP_FP32 ? 4 : 8;
     return plan(&tmp, nullptr);

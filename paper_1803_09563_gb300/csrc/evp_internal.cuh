@@ -156,6 +156,9 @@ struct StressArgs {
     unsigned* status;
     const T* H;        // two-phase: Heaviside of the level set (null: single phase)
     T mu_p1, mu_p2;    // two-phase: polymer viscosity of fluid 1 (H = 1) and fluid 2
+    // update modes: summed polymer stress tau(B^k) + tau(B^{k-1}) out for the
+    // momentum step (Table 1 with the state's G); null: not written
+    T* S[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 template <typename T>
@@ -178,6 +181,9 @@ struct MomentumArgs {
     const T* phis_n = nullptr;   //   tau = phi_s G (B - I) (neo-Hookean model)
     const T* trig;     // ABC force tables: sin/cos of k x_i, k y_j, k z_k (6 arrays)
     const T* solid[3]; // volume penalisation: solid fractions at u, v, w nodes (null: off)
+    // summed polymer stress tau^k + tau^{k-1} written by the stress kernel; null:
+    // built here from Bo and Bn
+    const T* S[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 template <typename T>

@@ -19,6 +19,8 @@
 // 16 bytes' worth of elements every row is staged in 16-byte cp.async chunks
 // (x = i0-4 .. i0+35, wrapped periodically chunk by chunk); other grids stage
 // element by element.
+#include <type_traits>
+
 #include "evp_internal.cuh"
 
 namespace evp {
@@ -70,16 +72,28 @@ struct MomSmem {
     T P[4][VPL];         // pressure planes k .. k+3
     T H[4][3][NT];       // momentum history of the tile's cells, planes k .. k+2
 };
+// The summed stress written by the stress kernel is staged like the velocity:
+// ring slots for planes k-1 .. k+3, no raw B and no build phase.
+template <typename T>
+struct MomSmemS {
+    T V[3][5][VPL];
+    T S[6][5][VPL];
+    T P[4][VPL];
+    T H[4][3][NT];
+};
+template <typename T, bool SPRE>
+using MomSmemOf = std::conditional_t<SPRE, MomSmemS<T>, MomSmem<T>>;
 __device__ __forceinline__ int vslot(int kk) { return (kk + 5) % 5; }   // kk >= -5
 
 // VEC: rows are staged in 16-byte chunks (needs nx * sizeof(T) % 16 == 0)
-template <typename T, int MODEL, bool VEC>
+// SPRE: the summed stress comes precomputed (MomentumArgs::S); MODEL is then unused
+template <typename T, int MODEL, bool VEC, bool SPRE>
 __global__ void __launch_bounds__(NT, 1)
 k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_chunk) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
-    MomSmem<T>& sm = *reinterpret_cast<MomSmem<T>*>(smraw);
+    MomSmemOf<T, SPRE>& sm = *reinterpret_cast<MomSmemOf<T, SPRE>*>(smraw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
@@ -216,6 +230,7 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
             if (psm[r] >= 0) cp_async(&sm.P[slot][psm[r]], a.P + pp + coff[r]);
     };
     auto fetch_braw = [&](int kk) {
+        if constexpr (!SPRE) {
         if (!stress) return;
         const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
         if (VEC) {
@@ -235,10 +250,30 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
                     cp_async(&sm.Braw[kk & 1][c][psm[r]], a.Bo[c] + pb + coff[r]);
                     cp_async(&sm.Braw[kk & 1][6 + c][psm[r]], a.Bn[c] + pb + coff[r]);
                 }
+        }
+    };
+    // precomputed summed stress plane kk into ring slot kk mod 5 (a centred field)
+    auto fetch_s = [&](int kk) {
+        if constexpr (SPRE) {
+            const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
+            const int slot = vslot(kk);
+            if (VEC) {
+                if (csm < 0) return;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) cp_async16(&sm.S[c][slot][csm], a.S[c] + pb + ccoff);
+                return;
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+#pragma unroll
+                for (int r = 0; r < NV; ++r)
+                    if (psm[r] >= 0) cp_async(&sm.S[c][slot][psm[r]], a.S[c] + pb + coff[r]);
+        }
     };
     const T kgm = T(mc.gmod), kL2 = T(mc.L2), kaf = T(mc.a_fene);
     // staged raw B -> summed stress S in ring slot kk mod 3 (Table 1 inverted)
     auto build_s = [&](int kk) {
+        if constexpr (!SPRE) {
         if (!stress) return;
         const T gm = kgm;
         const int slot = pmod(kk, 3);
@@ -281,6 +316,7 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
                 }
             }
         }
+        }
     };
     const size_t cell0 = (size_t)min(j, g.ny - 1) * g.nx + min(i, g.nx - 1);
     // history chunk of this thread (own cells of row hr, columns hq .. hq+E-1)
@@ -310,16 +346,24 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     fetch_p(k0);
     fetch_p(k0 + 1);
     fetch_hist(k0);
-    for (int d = -1; d <= 1; ++d) {
-        fetch_braw(k0 + d);
+    if constexpr (SPRE) {
+        for (int d = -1; d <= 1; ++d) fetch_s(k0 + d);
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
-        build_s(k0 + d);
-        __syncthreads();
+    } else {
+        for (int d = -1; d <= 1; ++d) {
+            fetch_braw(k0 + d);
+            cp_async_commit();
+            cp_async_wait_all();
+            __syncthreads();
+            build_s(k0 + d);
+            __syncthreads();
+        }
     }
     fetch_vel(k0 + 2);
     fetch_braw(k0 + 2);
+    fetch_s(k0 + 2);
     fetch_p(k0 + 2);
     fetch_hist(k0 + 1);
     cp_async_commit();
@@ -335,6 +379,7 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         // ---- asynchronous request of plane k+3 (velocity, raw B, p) and the history of k+2
         fetch_vel(k + 3);
         fetch_braw(k + 3);
+        fetch_s(k + 3);
         fetch_p(k + 3);
         fetch_hist(k + 2);
         cp_async_commit();
@@ -421,7 +466,8 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
             iz += am * Lw;
         }
         if (stress) {
-            const int s0 = pmod(k, 3), sm1 = pmod(k - 1, 3), sp1 = pmod(k + 1, 3);
+            const int s0 = SPRE ? vslot(k) : pmod(k, 3), sm1 = SPRE ? vslot(k - 1) : pmod(k - 1, 3);
+            const int sp1 = SPRE ? vslot(k + 1) : pmod(k + 1, 3);
             auto S = [&](int c, int slot, int di, int dj) { return sm.S[c][slot][o + dj * VW + di]; };
             // 4-point average over centres (0 or di) x (0 or dj) in one plane
             auto e4 = [&](int c, int slot, int di, int dj) {
@@ -464,11 +510,15 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         }
 
         // ---- advance: plane k+2 has landed (only plane k+3 may be in flight); its
-        // raw B becomes S plane k+2 (slot of plane k-1)
+        // raw B becomes S plane k+2 (slot of plane k-1).  With the precomputed
+        // stress every ring slot written at the next plane was last read before
+        // this barrier, which is the only one per plane.
         cp_async_wait_prev();
         __syncthreads();
-        build_s(k + 2);
-        __syncthreads();
+        if constexpr (!SPRE) {
+            build_s(k + 2);
+            __syncthreads();
+        }
     }
 }
 
@@ -486,15 +536,26 @@ cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const Momentu
     chunks = (g.nz + kz - 1) / kz;
     dim3 block(TX, TY, 1);
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
+    const bool vec = (g.nx * sizeof(T)) % 16 == 0;
+    if (a.S[0]) {
+        // summed stress precomputed by the stress kernel
+        if (mc.model == EVP_NEWTONIAN) return cudaErrorInvalidValue;
+        const size_t smem = sizeof(MomSmemS<T>);
+        th.b(K_MOMENTUM);
+        auto kern = vec ? k_momentum<T, EVP_OLDROYD_B, true, true> : k_momentum<T, EVP_OLDROYD_B, false, true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaError_t e = launch_k(kern, grid, block, smem, st, th.pdl, g, mc, a, kz)) return e;
+        th.e(K_MOMENTUM);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(MomSmem<T>);
     th.b(K_MOMENTUM);
-    const bool vec = (g.nx * sizeof(T)) % 16 == 0;
     switch (mc.model * 2 + (vec ? 1 : 0)) {
-#define EVP_LAUNCH_MOM_V(M, V)                                                                                \
-    case M * 2 + V:                                                                                           \
-        cudaFuncSetAttribute(k_momentum<T, M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-        if (cudaError_t e = launch_k(k_momentum<T, M, V>, grid, block, smem, st, th.pdl, g, mc, a, kz))     \
-            return e;                                                                                          \
+#define EVP_LAUNCH_MOM_V(M, V)                                                                                       \
+    case M * 2 + V:                                                                                                  \
+        cudaFuncSetAttribute(k_momentum<T, M, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        if (cudaError_t e = launch_k(k_momentum<T, M, V, false>, grid, block, smem, st, th.pdl, g, mc, a, kz))     \
+            return e;                                                                                                 \
         break;
 #define EVP_LAUNCH_MOM(M) EVP_LAUNCH_MOM_V(M, false) EVP_LAUNCH_MOM_V(M, true)
         EVP_LAUNCH_MOM(EVP_NEWTONIAN)

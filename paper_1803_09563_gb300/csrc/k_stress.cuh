@@ -541,6 +541,29 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             const T det = bn[0] * (bn[3] * bn[5] - bn[4] * bn[4]) - bn[1] * (bn[1] * bn[5] - bn[4] * bn[2])
                           + bn[2] * (bn[1] * bn[4] - bn[3] * bn[2]);
             if (det < T(0)) bits |= EVP_BIT_DET_NEG;
+            if (a.S[0]) {
+                // summed polymer stress tau(B^k) + tau(B^{k-1}) of the cell (Table 1),
+                // the divergence term of the momentum step
+                const T gm = kgm;
+                if (MODEL == EVP_FENE_P) {
+                    const T Fo = kL2 / (kL2 - (w[0][3] + w[3][3] + w[5][3]));
+                    const T Fn = kL2 / (kL2 - (bn[0] + bn[3] + bn[5]));
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        const bool d = (c == 0 || c == 3 || c == 5);
+                        a.S[c][cell] = gm * (Fn * bn[c] - (d ? kaf : T(0))) + gm * (Fo * w[c][3] - (d ? kaf : T(0)));
+                    }
+                } else if (MODEL == EVP_NEO_HOOKEAN) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) a.S[c][cell] = gm * bn[c] + gm * w[c][3];
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        const bool d = (c == 0 || c == 3 || c == 5);
+                        a.S[c][cell] = gm * (bn[c] - (d ? T(1) : T(0))) + gm * (w[c][3] - (d ? T(1) : T(0)));
+                    }
+                }
+            }
         }
 
         // ---- advance the window; publish the interior of plane k+1
