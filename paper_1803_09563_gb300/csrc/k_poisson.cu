@@ -295,6 +295,126 @@ k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axi
         }
 }
 
+// ---- register-resident column FFTs for n = R1 * R2 (powers of two, n <= 256)
+//
+// Cooley-Tukey in two passes with one shared-memory exchange:
+//   X[k1 + R1 k2] = sum_j2 W_R2^(j2 k2) W_n^(j2 k1) sum_j1 x[R2 j1 + j2] W_R1^(j1 k1)
+// pass 1: one thread per (column, j2) takes the R1-point DFT over j1 in registers,
+// multiplies by W_n^(j2 k1) and stores to shared memory; pass 2: one thread per
+// (column, k1) takes the R2-point DFT over j2.  The inverse transform (conjugate
+// twiddles) has the same structure.  Twiddles come from the table exp(-2 pi i m/n).
+
+template <int R>
+__device__ __forceinline__ constexpr int bitrev(int i) {
+    int r = 0;
+    for (int b = 1; b < R; b <<= 1) {
+        r = (r << 1) | (i & 1);
+        i >>= 1;
+    }
+    return r;
+}
+
+// In-register R-point DFT (R a power of two), natural order in and out: radix-2
+// decimation in time over the bit-reversed input.  tw[m * ts] = exp(-2 pi i m/R)
+// (conjugated for INV).
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft_reg(C<T> (&x)[R], const C<T>* __restrict__ tw, int ts) {
+    C<T> y[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) y[bitrev<R>(i)] = x[i];
+#pragma unroll
+    for (int h = 1; h < R; h *= 2) {
+#pragma unroll
+        for (int g0 = 0; g0 < R; g0 += 2 * h) {
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                const int m = k * (R / (2 * h));        // W_2h^k = W_R^m
+                C<T> b = y[g0 + k + h];
+                if (R >= 4 && m == R / 4) b = rot<T, INV>(b);   // W_R^(R/4) = -i
+                else if (m != 0) b = twmul<T, INV>(b, __ldg(tw + m * ts));
+                y[g0 + k + h] = sub<T>(y[g0 + k], b);
+                y[g0 + k] = add<T>(y[g0 + k], b);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) x[i] = y[i];
+}
+
+// Column FFT along z (or y) over tk consecutive kx, as k_fft_col, for n = R1 R2.
+// Threads: (tk, max(R1, R2)).  SOLVE: forward, modal division, inverse (the
+// inverse runs the two passes in reverse order, so its input is the forward
+// output as each thread holds it).
+template <typename T, bool INV, bool SOLVE, int R1, int R2>
+__global__ void __launch_bounds__(256)
+k_fft_col_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axis_y, size_t estride,
+            size_t ostride, int tk) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C<T>* Y = reinterpret_cast<C<T>*>(smraw);           // [R2][R1][tk]
+    const C<T>* tw = axis_y ? tb.twy : tb.twz;
+    const int nxh = g.nx / 2 + 1;
+    const int t = threadIdx.x, q = threadIdx.y;
+    const int kx = blockIdx.x * tk + t;
+    const bool ok = kx < nxh;
+    const size_t base = blockIdx.y * ostride + (ok ? kx : 0);
+    if (q < R2) {
+        C<T> x[R1];
+#pragma unroll
+        for (int j1 = 0; j1 < R1; ++j1)
+            x[j1] = ok ? a.spec[base + (size_t)(R2 * j1 + q) * estride] : mk<T>(T(0), T(0));
+        dft_reg<T, R1, INV>(x, tw, R2);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+            Y[(q * R1 + k1) * tk + t] = k1 == 0 ? x[k1] : twmul<T, INV>(x[k1], __ldg(tw + q * k1));
+    }
+    __syncthreads();
+    // every thread of the block reaches each barrier below: idle threads skip work, not barriers
+    const bool p2 = q < R1;
+    C<T> y[R2];
+    if (p2) {
+#pragma unroll
+        for (int j2 = 0; j2 < R2; ++j2) y[j2] = Y[(j2 * R1 + q) * tk + t];
+        dft_reg<T, R2, INV>(y, tw, R1);                  // y[k2] = X[q + R1 k2]
+        if (!SOLVE && ok) {
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) a.spec[base + (size_t)(q + R1 * k2) * estride] = y[k2];
+        }
+    }
+    if (!SOLVE) return;
+    if (p2) {
+        // modal division: -norm/(lx+ly+lz) (zero mode -> 0), or norm/(1 + hcoef lam)
+        const T lz = __ldg(tb.lamz + blockIdx.y);
+        const T lx = ok ? __ldg(tb.lamx + kx) : T(0);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+            const T lam = lx + __ldg(tb.lamy + q + R1 * k2) + lz;
+            const T f = a.hcoef > T(0) ? T(a.norm) / (T(1) + a.hcoef * lam)
+                                       : (lam == T(0) ? T(0) : T(-a.norm) / lam);
+            y[k2] = mk<T>(y[k2].x * f, y[k2].y * f);
+        }
+        // inverse: R2-point DFT over k2, twiddle W_n^-(j2 q), exchange, R1-point DFT over k1
+        dft_reg<T, R2, true>(y, tw, R1);
+    }
+    __syncthreads();                                     // every thread has read Y
+    if (p2) {
+#pragma unroll
+        for (int j2 = 0; j2 < R2; ++j2)
+            Y[(j2 * R1 + q) * tk + t] = j2 == 0 ? y[j2] : twmul<T, true>(y[j2], __ldg(tw + j2 * q));
+    }
+    __syncthreads();
+    if (q >= R2) return;
+    C<T> x[R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) x[k1] = Y[(q * R1 + k1) * tk + t];
+    dft_reg<T, R1, true>(x, tw, R2);                     // x[j1] = x_(R2 j1 + q)
+    if (ok) {
+#pragma unroll
+        for (int j1 = 0; j1 < R1; ++j1) a.spec[base + (size_t)(R2 * j1 + q) * estride] = x[j1];
+    }
+}
+
 // S6 with walls: for each (kx, kz) solve
 //   psi_{j-1}/dy^2 - (2/dy^2 + lx + lz) psi_j + psi_{j+1}/dy^2 = r_j
 // with Neumann rows at j = 0 and ny-1 and the (0, 0) system pinned by psi_0 = 0,
@@ -547,6 +667,33 @@ void set_smem(const void* f, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Column FFT pass of length n along z (axis_y 0) or y (1) over tk consecutive kx
+// per block and one block row per grid.y: the register-resident two-pass kernel
+// for n = 16 .. 256 (powers of two), else the Stockham kernel.
+template <typename T, bool INV, bool SOLVE>
+cudaError_t launch_col(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a, int n, int axis_y,
+                       size_t estride, size_t ostride, int tk, unsigned rows, cudaStream_t st, bool pdl) {
+    const int nxh = g.nx / 2 + 1;
+    const dim3 grid((nxh + tk - 1) / tk, rows);
+    auto go = [&](auto kern, int r1, int r2) {
+        const size_t sm = (size_t)n * tk * sizeof(C<T>);
+        set_smem<T>((const void*)kern, sm);
+        return launch_k(kern, grid, dim3(tk, r1 > r2 ? r1 : r2), sm, st, pdl, g, tb, a, axis_y, estride, ostride, tk);
+    };
+    switch (n) {
+        case 16: return go(k_fft_col_r<T, INV, SOLVE, 4, 4>, 4, 4);
+        case 32: return go(k_fft_col_r<T, INV, SOLVE, 4, 8>, 4, 8);
+        case 64: return go(k_fft_col_r<T, INV, SOLVE, 8, 8>, 8, 8);
+        case 128: return go(k_fft_col_r<T, INV, SOLVE, 8, 16>, 8, 16);
+        case 256: return go(k_fft_col_r<T, INV, SOLVE, 16, 16>, 16, 16);
+        default: break;
+    }
+    const size_t sm = col_smem<T>(n, tk);
+    set_smem<T>((const void*)k_fft_col<T, INV, SOLVE>, sm);
+    return launch_k(k_fft_col<T, INV, SOLVE>, grid, dim3(tk, 256 / tk), sm, st, pdl, g, tb, a, axis_y, estride,
+                    ostride, tk);
+}
+
 }  // namespace
 
 int fft_radices(int n, int* rad) {
@@ -577,25 +724,15 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
     th.e(K_DIV_FFTX);
 
     const int tk = sizeof(T) == 4 ? 16 : 8;
-    dim3 bc(tk, 256 / tk);
     // ---- forward z
-    {
-        dim3 gc((nxh + tk - 1) / tk, ny);
-        const size_t sm = col_smem<T>(nz, tk);
-        set_smem<T>((const void*)k_fft_col<T, false, false>, sm);
-        th.b(K_FFT_Z_FWD);
-        if (cudaError_t e = launch_k(k_fft_col<T, false, false>, gc, bc, sm, st, th.pdl, g, tb, a, 0, (size_t)ny * nxh,
-                                     (size_t)nxh, tk))
-            return e;
-        th.e(K_FFT_Z_FWD);
-    }
+    th.b(K_FFT_Z_FWD);
+    if (cudaError_t e = launch_col<T, false, false>(g, tb, a, nz, 0, (size_t)ny * nxh, (size_t)nxh, tk, ny, st, th.pdl))
+        return e;
+    th.e(K_FFT_Z_FWD);
     if (!g.walls) {
-        dim3 gc((nxh + tk - 1) / tk, nz);
-        const size_t sm = col_smem<T>(ny, tk);
-        set_smem<T>((const void*)k_fft_col<T, false, true>, sm);
         th.b(K_SOLVE_Y);
-        if (cudaError_t e = launch_k(k_fft_col<T, false, true>, gc, bc, sm, st, th.pdl, g, tb, a, 1, (size_t)nxh,
-                                     (size_t)ny * nxh, tk))
+        if (cudaError_t e = launch_col<T, false, true>(g, tb, a, ny, 1, (size_t)nxh, (size_t)ny * nxh, tk, nz, st,
+                                                       th.pdl))
             return e;
         th.e(K_SOLVE_Y);
     } else {
@@ -608,16 +745,10 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
         th.e(K_THOMAS);
     }
     // ---- inverse z
-    {
-        dim3 gc((nxh + tk - 1) / tk, ny);
-        const size_t sm = col_smem<T>(nz, tk);
-        set_smem<T>((const void*)k_fft_col<T, true, false>, sm);
-        th.b(K_FFT_Z_INV);
-        if (cudaError_t e = launch_k(k_fft_col<T, true, false>, gc, bc, sm, st, th.pdl, g, tb, a, 0, (size_t)ny * nxh,
-                                     (size_t)nxh, tk))
-            return e;
-        th.e(K_FFT_Z_INV);
-    }
+    th.b(K_FFT_Z_INV);
+    if (cudaError_t e = launch_col<T, true, false>(g, tb, a, nz, 0, (size_t)ny * nxh, (size_t)nxh, tk, ny, st, th.pdl))
+        return e;
+    th.e(K_FFT_Z_INV);
     set_smem<T>((const void*)k_ifftx<T>, smx);
     th.b(K_IFFTX);
     if (cudaError_t e = launch_k(k_ifftx<T>, gx, bx, smx, st, th.pdl, g, tb, a, np)) return e;
