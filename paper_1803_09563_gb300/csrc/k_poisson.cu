@@ -415,6 +415,120 @@ k_fft_col_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int a
     }
 }
 
+// S4 + S5(x) for nx = R1 R2 (powers of two, 16 .. 256), as k_div_fftx with the
+// two-pass register-resident FFT: threadIdx.y picks one of the block's complex lines
+// (real lines 2L and 2L+1), threadIdx.x = j2 (pass 1), k1 (pass 2), then m (split).
+// The exchange buffer of a line is R1 rows of R2+1 (padded against bank conflicts).
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(256)
+k_div_fftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int n = R1 * R2, RM = R1 > R2 ? R1 : R2, LW = R1 * (R2 + 1);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int q = threadIdx.x;
+    C<T>* Y = reinterpret_cast<C<T>*>(smraw) + (size_t)threadIdx.y * LW;
+    const int NL = g.ny * g.nz, nxh = n / 2 + 1;
+    const int L0 = 2 * (blockIdx.x * blockDim.y + threadIdx.y), L1 = L0 + 1;
+    const bool ok0 = L0 < NL, ok1 = L1 < NL;
+    const C<T>* tw = tb.twx;
+    if (q < R2) {
+        C<T> x[R1];
+        if (a.rhs) {
+#pragma unroll
+            for (int j1 = 0; j1 < R1; ++j1) {
+                const int i = R2 * j1 + q;
+                x[j1] = mk<T>(ok0 ? __ldg(a.rhs + (size_t)L0 * n + i) : T(0), ok1 ? __ldg(a.rhs + (size_t)L1 * n + i) : T(0));
+            }
+        } else {
+            const DivRows<T> r0 = div_rows(g, a, ok0 ? L0 : 0), r1 = div_rows(g, a, ok1 ? L1 : 0);
+#pragma unroll
+            for (int j1 = 0; j1 < R1; ++j1) {
+                const int i = R2 * j1 + q;
+                x[j1] = mk<T>(ok0 ? div_value(g, a, r0, i) : T(0), ok1 ? div_value(g, a, r1, i) : T(0));
+            }
+        }
+        dft_reg<T, R1, false>(x, tw, R2);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+            Y[k1 * (R2 + 1) + q] = k1 == 0 ? x[k1] : twmul<T, false>(x[k1], __ldg(tw + q * k1));
+    }
+    __syncthreads();
+    C<T> y[R2];
+    if (q < R1) {
+#pragma unroll
+        for (int j2 = 0; j2 < R2; ++j2) y[j2] = Y[q * (R2 + 1) + j2];
+        dft_reg<T, R2, false>(y, tw, R1);                // y[k2] = Z[q + R1 k2]
+    }
+    __syncthreads();
+    if (q < R1) {
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) Y[q + R1 * k2] = y[k2];
+    }
+    __syncthreads();
+    // split the packed pair: A_m = (Z_m + conj Z_{n-m})/2, B_m = (Z_m - conj Z_{n-m})/(2i)
+    if (!ok0) return;
+    for (int m = q; m < nxh; m += RM) {
+        const C<T> Z = Y[m];
+        const C<T> Zr = Y[m == 0 ? 0 : n - m];
+        a.spec[(size_t)L0 * nxh + m] = mk<T>(T(0.5) * (Z.x + Zr.x), T(0.5) * (Z.y - Zr.y));
+        if (ok1) a.spec[(size_t)L1 * nxh + m] = mk<T>(T(0.5) * (Z.y + Zr.y), T(0.5) * (Zr.x - Z.x));
+    }
+}
+
+// S7(x) for nx = R1 R2, as k_ifftx with the two-pass register-resident FFT.
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(256)
+k_ifftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int n = R1 * R2, LW = R1 * (R2 + 1), half = n / 2, nxh = n / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int q = threadIdx.x;
+    C<T>* Y = reinterpret_cast<C<T>*>(smraw) + (size_t)threadIdx.y * LW;
+    const int NL = g.ny * g.nz;
+    const int L0 = 2 * (blockIdx.x * blockDim.y + threadIdx.y), L1 = L0 + 1;
+    const bool ok0 = L0 < NL, ok1 = L1 < NL;
+    const C<T>* tw = tb.twx;
+    if (q < R2) {
+        C<T> x[R1];
+#pragma unroll
+        for (int j1 = 0; j1 < R1; ++j1) {
+            // packed pair at m: A_m + i B_m with the Hermitian extension of both lines
+            const int m = R2 * j1 + q;
+            const int mm = m <= half ? m : n - m;
+            C<T> A = mk<T>(T(0), T(0)), B = mk<T>(T(0), T(0));
+            if (ok0) A = a.spec[(size_t)L0 * nxh + mm];
+            if (ok1) B = a.spec[(size_t)L1 * nxh + mm];
+            if (mm == 0 || mm == half) {   // DC and Nyquist of a real line are real
+                A.y = T(0);
+                B.y = T(0);
+            }
+            if (m > half) {
+                A.y = -A.y;
+                B.y = -B.y;
+            }
+            x[j1] = mk<T>(A.x - B.y, A.y + B.x);
+        }
+        dft_reg<T, R1, true>(x, tw, R2);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+            Y[k1 * (R2 + 1) + q] = k1 == 0 ? x[k1] : twmul<T, true>(x[k1], __ldg(tw + q * k1));
+    }
+    __syncthreads();
+    if (q >= R1 || !ok0) return;
+    C<T> y[R2];
+#pragma unroll
+    for (int j2 = 0; j2 < R2; ++j2) y[j2] = Y[q * (R2 + 1) + j2];
+    dft_reg<T, R2, true>(y, tw, R1);                     // y[k2] = z[q + R1 k2]
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+        const size_t i = q + R1 * k2;
+        a.psi[(size_t)L0 * n + i] = y[k2].x * a.out_scale;
+        if (ok1) a.psi[(size_t)L1 * n + i] = y[k2].y * a.out_scale;
+    }
+}
+
 // S6 with walls: for each (kx, kz) solve
 //   psi_{j-1}/dy^2 - (2/dy^2 + lx + lz) psi_j + psi_{j+1}/dy^2 = r_j
 // with Neumann rows at j = 0 and ny-1 and the (0, 0) system pinned by psi_0 = 0,
@@ -718,9 +832,39 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
     dim3 bx(tx, 256 / tx);
     dim3 gx((npairs + np - 1) / np);
     const size_t smx = 2 * (size_t)np * nx * sizeof(C<T>);
-    set_smem<T>((const void*)k_div_fftx<T>, smx);
+    // the register-resident x passes for nx = 16 .. 256 (powers of two)
+    int xr1 = 0, xr2 = 0;
+    switch (nx) {
+        case 16: xr1 = 4; xr2 = 4; break;
+        case 32: xr1 = 4; xr2 = 8; break;
+        case 64: xr1 = 8; xr2 = 8; break;
+        case 128: xr1 = 8; xr2 = 16; break;
+        case 256: xr1 = 16; xr2 = 16; break;
+        default: break;
+    }
+    const int xrm = xr1 > xr2 ? xr1 : xr2;
+    const int xlines = xr1 ? (sizeof(T) == 4 ? 256 : 128) / xrm : 0;          // complex lines per block
+    const dim3 bxr(xrm, xlines ? xlines : 1), gxr(xlines ? (npairs + xlines - 1) / xlines : 1);
+    const size_t smxr = (size_t)xlines * xr1 * (xr2 + 1) * sizeof(C<T>);
+    auto go_x = [&](auto kern) {
+        set_smem<T>((const void*)kern, smxr);
+        return launch_k(kern, gxr, bxr, smxr, st, th.pdl, g, tb, a);
+    };
     th.b(K_DIV_FFTX);
-    if (cudaError_t e = launch_k(k_div_fftx<T>, gx, bx, smx, st, th.pdl, g, tb, a, np)) return e;
+    {
+        cudaError_t e;
+        switch (nx) {
+            case 16: e = go_x(k_div_fftx_r<T, 4, 4>); break;
+            case 32: e = go_x(k_div_fftx_r<T, 4, 8>); break;
+            case 64: e = go_x(k_div_fftx_r<T, 8, 8>); break;
+            case 128: e = go_x(k_div_fftx_r<T, 8, 16>); break;
+            case 256: e = go_x(k_div_fftx_r<T, 16, 16>); break;
+            default:
+                set_smem<T>((const void*)k_div_fftx<T>, smx);
+                e = launch_k(k_div_fftx<T>, gx, bx, smx, st, th.pdl, g, tb, a, np);
+        }
+        if (e) return e;
+    }
     th.e(K_DIV_FFTX);
 
     const int tk = sizeof(T) == 4 ? 16 : 8;
@@ -749,9 +893,21 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
     if (cudaError_t e = launch_col<T, true, false>(g, tb, a, nz, 0, (size_t)ny * nxh, (size_t)nxh, tk, ny, st, th.pdl))
         return e;
     th.e(K_FFT_Z_INV);
-    set_smem<T>((const void*)k_ifftx<T>, smx);
     th.b(K_IFFTX);
-    if (cudaError_t e = launch_k(k_ifftx<T>, gx, bx, smx, st, th.pdl, g, tb, a, np)) return e;
+    {
+        cudaError_t e;
+        switch (nx) {
+            case 16: e = go_x(k_ifftx_r<T, 4, 4>); break;
+            case 32: e = go_x(k_ifftx_r<T, 4, 8>); break;
+            case 64: e = go_x(k_ifftx_r<T, 8, 8>); break;
+            case 128: e = go_x(k_ifftx_r<T, 8, 16>); break;
+            case 256: e = go_x(k_ifftx_r<T, 16, 16>); break;
+            default:
+                set_smem<T>((const void*)k_ifftx<T>, smx);
+                e = launch_k(k_ifftx<T>, gx, bx, smx, st, th.pdl, g, tb, a, np);
+        }
+        if (e) return e;
+    }
     th.e(K_IFFTX);
     return cudaGetLastError();
 }
