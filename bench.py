@@ -4,8 +4,9 @@ Workload (default): Saramito EVP channel, 256 x 128 x 128 (x, y, z), periodic in
 and z, no-slip walls at y = +-1, Re = 100, Wi = 1, Bi = 0.5, beta = 0.5, body force
 dp/dx = 2/Re, dt = 2e-3, laminar Poiseuille base flow plus a seeded solenoidal
 perturbation of max-norm 1e-2 with |k| <= 8.  FP32 fields and stencils, FP64 Thomas
-sweeps and divergence residual ("FP32-served"), with the same run in FP64 ("FP64
-plain") beside it.
+sweeps ("FP32-served"), with the same run in FP64 ("FP64 plain") beside it.  The
+FP64 divergence residual of the final state is evaluated at sync, after the timed
+steps (the steps compute none).
 
 A step is one full RK3 step (three substeps: stress update, momentum predictor,
 Poisson solve, projection).  Metric: Mcell-steps/s = cells * steps / time.
@@ -346,7 +347,7 @@ def run_gpu(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": "Mcell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 Thomas + residual)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 Thomas; FP64 divergence residual of the final state at sync)",
         "data": "synthetic (seeded Poiseuille + solenoidal perturbation)",
         "config": {"workload": w['name'], "grid": [w['nx'], w['ny'], w['nz']], "model": w['model'],
                    "Re": w['Re'], "Wi": w['Wi'], "Bi": w['Bi'], "beta": w['beta'], "dt": w['dt'],

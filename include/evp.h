@@ -276,8 +276,12 @@ int evp_stress_rhs(evp_state* s, void* rt);
 /* Wait for the state's stream.  Returns EVP_ERR_NONFINITE / EVP_ERR_UNPHYSICAL
  * when kernels raised the matching bits since the last sync (bits in *bits),
  * else EVP_OK.  With art_diff > 0, EVP_BIT_DET_NEG is reported in *bits but is
- * not an error: det B < 0 is then the condition the diffusion treats.  *max_div (may be NULL) receives max |div u| of the last
- * projection, computed in FP64.  Bits and residual are cleared afterwards.     */
+ * not an error: det B < 0 is then the condition the diffusion treats.
+ * max_div (may be NULL): when given, a kernel evaluates max |div u| of the
+ * state's current velocity (after a step or evp_project, the last projection's
+ * output) in FP64 on the stored values, which *max_div receives; a non-finite
+ * divergence sets EVP_BIT_NONFINITE.  The steps themselves compute no residual.
+ * Bits are cleared afterwards.                                                 */
 int evp_sync(evp_state* s, unsigned* bits, double* max_div);
 
 /* Self-test of the current device (the paper has no counterpart): checks the

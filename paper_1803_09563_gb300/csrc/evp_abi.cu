@@ -510,7 +510,7 @@ int prepare_helmholtz(evp_state* s, double dt) {
 
 template <typename T>
 int run_correct(evp_state* s, const T* Us, const T* Vs, const T* Ws, T* U, T* V, T* W, T* P, double coef,
-                bool residual, bool p_replace = false) {
+                bool p_replace = false) {
     CorrectArgs<T> a;
     a.Us = Us;
     a.Vs = Vs;
@@ -522,21 +522,14 @@ int run_correct(evp_state* s, const T* Us, const T* Vs, const T* Ws, T* U, T* V,
     a.P = P;
     a.p_replace = p_replace ? 1 : 0;
     a.coef = T(coef);
-    a.maxdiv = residual ? s->d_maxdiv : nullptr;
     a.status = s->d_status;
-    a.idx_d = s->g.nx / s->g.lx;
-    a.idy_d = s->g.ny / s->g.ly;
-    a.idz_d = s->g.nz / s->g.lz;
-    // residual of this projection only
-    if (residual) CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
     cudaError_t e = launch_correct<T>(geo_of<T>(s), a, s->st, hook_of(s));
     return e == cudaSuccess ? EVP_OK : cuda_fail(e, "correct");
 }
 
-// One RK3 substep.  in_step: part of evp_step (then the FP64 residual, which
-// evp_sync reports for the last projection, is evaluated on the third substep only).
+// One RK3 substep; last_in_step: the third substep of evp_step (no history written).
 template <typename T>
-int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
+int substep_t(evp_state* s, double dt, int k, bool last_in_step) {
     const double al = RK_ALPHA[k], ze = RK_ZETA[k], xi = RK_XI[k];
     const bool stress = s->model != EVP_NEWTONIAN;
     const int cu = s->cu, cb = s->cb;
@@ -669,7 +662,7 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step, bool in_step) {
     if (r) return r;
     r = run_correct<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
                        static_cast<const T*>(s->W[1 - cu]), static_cast<T*>(s->U[cu]), static_cast<T*>(s->V[cu]),
-                       static_cast<T*>(s->W[cu]), static_cast<T*>(s->P), coef, !in_step || k == 2);
+                       static_cast<T*>(s->W[cu]), static_cast<T*>(s->P), coef);
     if (r) return r;
     if (stress) s->cb = 1 - cb;
     return EVP_OK;
@@ -821,15 +814,10 @@ int ab2_step_t(evp_state* s, double dt) {
         q.rho_ratio = T(p.rho_ratio);
         q.rho0 = T(p.rho_ratio < 1.0 ? p.rho_ratio : 1.0);
         q.dt = T(dt);
-        q.maxdiv = s->d_maxdiv;
         q.status = s->d_status;
-        q.idx_d = s->g.nx / s->g.lx;
-        q.idy_d = s->g.ny / s->g.ly;
-        q.idz_d = s->g.nz / s->g.lz;
         if ((e = launch_split_rhs<T>(g, q, s->st, th)) != cudaSuccess) return cuda_fail(e, "split rhs");
         int r = run_poisson<T>(s, nullptr, nullptr, nullptr, static_cast<const T*>(s->PSI), 1.0, static_cast<T*>(s->PSI));
         if (r) return r;
-        CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
         if ((e = launch_split_correct<T>(g, q, s->st, th)) != cudaSuccess) return cuda_fail(e, "split correct");
         // rotate: p^{n-1} <- p^n, p^n <- p^{n+1}; the old p^{n-1} buffer becomes scratch
         void* old = s->POLD;
@@ -846,7 +834,7 @@ int ab2_step_t(evp_state* s, double dt) {
     if (r) return r;
     r = run_correct<T>(s, static_cast<const T*>(s->U[1 - cu]), static_cast<const T*>(s->V[1 - cu]),
                        static_cast<const T*>(s->W[1 - cu]), static_cast<T*>(s->U[cu]), static_cast<T*>(s->V[cu]),
-                       static_cast<T*>(s->W[cu]), static_cast<T*>(s->P), dt, true, true);
+                       static_cast<T*>(s->W[cu]), static_cast<T*>(s->P), dt, true);
     if (r) return r;
     if (stress) s->cb = 1 - cb;
     s->nstep += 1;
@@ -1066,13 +1054,13 @@ int evp_substep(evp_state* s, double dt, int k) {
     if (k < 0 || k > 2) return fail(EVP_ERR_ARG, "substep index must be 0, 1 or 2");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
     if (int r = prepare_helmholtz(s, dt)) return r;
-    return s->fp32 ? substep_t<float>(s, dt, k, false, false) : substep_t<double>(s, dt, k, false, false);
+    return s->fp32 ? substep_t<float>(s, dt, k, false) : substep_t<double>(s, dt, k, false);
 }
 
 namespace {
 int rk3_step_direct(evp_state* s, double dt) {
     for (int k = 0; k < 3; ++k) {
-        int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2, true) : substep_t<double>(s, dt, k, k == 2, true);
+        int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2) : substep_t<double>(s, dt, k, k == 2);
         if (r) return r;
     }
     return EVP_OK;
@@ -1268,7 +1256,7 @@ extern "C" int evp_step(evp_state* s, double dt) {
     if (s->ab2) return s->fp32 ? ab2_step_t<float>(s, dt) : ab2_step_t<double>(s, dt);
     if (s->use_graph && !s->timing) return rk3_step_graph(s, dt);
     for (int k = 0; k < 3; ++k) {
-        int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2, true) : substep_t<double>(s, dt, k, k == 2, true);
+        int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2) : substep_t<double>(s, dt, k, k == 2);
         if (r) return r;
     }
     return EVP_OK;
@@ -1283,14 +1271,14 @@ int evp_project(evp_state* s) {
                                1.0, (float*)s->PSI);
         if (!r)
             r = run_correct<float>(s, (const float*)s->U[cu], (const float*)s->V[cu], (const float*)s->W[cu],
-                                   (float*)s->U[1 - cu], (float*)s->V[1 - cu], (float*)s->W[1 - cu], nullptr, 1.0, true);
+                                   (float*)s->U[1 - cu], (float*)s->V[1 - cu], (float*)s->W[1 - cu], nullptr, 1.0);
     } else {
         r = run_poisson<double>(s, (const double*)s->U[cu], (const double*)s->V[cu], (const double*)s->W[cu],
                                 nullptr, 1.0, (double*)s->PSI);
         if (!r)
             r = run_correct<double>(s, (const double*)s->U[cu], (const double*)s->V[cu], (const double*)s->W[cu],
-                                    (double*)s->U[1 - cu], (double*)s->V[1 - cu], (double*)s->W[1 - cu], nullptr, 1.0,
-                                    true);
+                                    (double*)s->U[1 - cu], (double*)s->V[1 - cu], (double*)s->W[1 - cu], nullptr,
+                                    1.0);
     }
     if (!r) s->cu = 1 - cu;
     return r;
@@ -1333,6 +1321,18 @@ int evp_stress_rhs(evp_state* s, void* rt) {
 
 int evp_sync(evp_state* s, unsigned* bits, double* max_div) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (max_div) {
+        // FP64 max |div u| of the current (last projected) velocity
+        CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
+        const int cu = s->cu;
+        const double ix = s->g.nx / s->g.lx, iy = s->g.ny / s->g.ly, iz = s->g.nz / s->g.lz;
+        const cudaError_t e = s->fp32
+            ? launch_div_residual<float>(geo_of<float>(s), (const float*)s->U[cu], (const float*)s->V[cu],
+                                         (const float*)s->W[cu], ix, iy, iz, s->d_maxdiv, s->d_status, s->st)
+            : launch_div_residual<double>(geo_of<double>(s), (const double*)s->U[cu], (const double*)s->V[cu],
+                                          (const double*)s->W[cu], ix, iy, iz, s->d_maxdiv, s->d_status, s->st);
+        if (e != cudaSuccess) return cuda_fail(e, "divergence residual");
+    }
     CK(cudaStreamSynchronize(s->st));
     unsigned st = 0;
     unsigned long long md = 0;

@@ -234,9 +234,7 @@ struct CorrectArgs {
     T* P;              // p += psi if non-null (p = psi with p_replace)
     int p_replace;     // AB2 step: the pressure is psi itself (Eq. projection)
     T coef;            // 2 alpha dt (or 1 for a plain projection)
-    unsigned long long* maxdiv;   // FP64 bits of max |div u|
     unsigned* status;
-    double idx_d, idy_d, idz_d;   // FP64 reciprocal spacings for the residual
 };
 
 // two-phase step (level set, interface force, AB2 momentum)
@@ -352,9 +350,7 @@ struct SplitArgs {
     T* V;
     T* W;              // u^{n+1} out
     T rho_ratio, rho0, dt;
-    unsigned long long* maxdiv;
     unsigned* status;
-    double idx_d, idy_d, idz_d;
 };
 
 // ----------------------------------------------------------- launch functions
@@ -479,6 +475,11 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
 template <typename T>
 cudaError_t launch_correct(const Geo<T>& g, const CorrectArgs<T>& a, cudaStream_t st,
                            const TimingHook& th);
+// FP64 max |div u| of the stored velocity (U, V, W) into *maxdiv (bits of a
+// non-negative double, atomic max: the caller zeroes it); non-finite -> status
+template <typename T>
+cudaError_t launch_div_residual(const Geo<T>& g, const T* U, const T* V, const T* W, double idx, double idy,
+                                double idz, unsigned long long* maxdiv, unsigned* status, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_ls_stage(const Geo<T>& g, const LsArgs<T>& a, bool reinit, cudaStream_t st,

@@ -651,21 +651,18 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
     }
 }
 
-// S8: u^k = u* - c grad psi at the faces, p += psi, FP64 max |div u^k|.
-// A 32 x 8 tile walks a chunk of z planes; psi and w* of the column below are
-// carried from the previous plane.  One FP64 atomic max per block.
-template <typename T, bool RESID>
+// S8: u^k = u* - c grad psi at the faces, p += psi; non-finite results raise
+// EVP_BIT_NONFINITE.  A 32 x 8 tile walks a chunk of z planes; psi of the column
+// below is carried from the previous plane.
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, double idz_d, int kz_chunk) {
+k_correct(const Geo<T> g, const CorrectArgs<T> a, int kz_chunk) {
     pdl_wait();
     pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
     const bool active = i < g.nx && j < g.ny;
-    // max |div u| kept as the bit pattern of a non-negative double (ordered like
-    // the unsigned integer)
-    unsigned long long dmax_b = 0ull;
     unsigned bits = 0;
     if (active) {
         const T c = a.coef;
@@ -679,36 +676,27 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, do
         T* __restrict__ P = a.P;
         const size_t plane = (size_t)g.nx * g.ny;
         const size_t cj = (size_t)j * g.nx + i;
-        const int ip = wrap(i + 1, g.nx), im = wrap(i - 1, g.nx);
-        const int jp = ycen(g, j + 1), jm = ycen(g, j - 1);
-        const bool top = g.walls && j == g.ny - 1, bottom = g.walls && j == 0;
-        const size_t cxp = (size_t)j * g.nx + ip, cxm = (size_t)j * g.nx + im;
-        const size_t cyp = (size_t)jp * g.nx + i, cym = (size_t)jm * g.nx + i;
-        // values of plane k-1 carried along z; the loads of plane k+1 are issued
-        // while plane k is being computed
+        const int ip = wrap(i + 1, g.nx), jp = ycen(g, j + 1);
+        const bool top = g.walls && j == g.ny - 1;
+        const size_t cxp = (size_t)j * g.nx + ip, cyp = (size_t)jp * g.nx + i;
+        // psi of plane k carried from the previous plane; the loads of plane k+1
+        // are issued while plane k is being computed
         struct Pl {
-            T pz, px, pxm, py, pym, us, usm, vs, vsm, ws, pold;
+            T pz, px, py, us, vs, ws, pold;
         };
         auto load = [&](int k) {
             Pl v;
             const size_t o = (size_t)k * plane;
             v.pz = __ldg(Psi + (size_t)wrap(k + 1, g.nz) * plane + cj);
             v.px = __ldg(Psi + o + cxp);
-            v.pxm = __ldg(Psi + o + cxm);
             v.py = __ldg(Psi + o + cyp);
-            v.pym = __ldg(Psi + o + cym);
             v.us = __ldg(Us + o + cj);
-            v.usm = __ldg(Us + o + cxm);
             v.vs = __ldg(Vs + o + cj);
-            v.vsm = bottom ? T(0) : __ldg(Vs + o + cym);
             v.ws = __ldg(Ws + o + cj);
             v.pold = (P && !a.p_replace) ? P[o + cj] : T(0);
             return v;
         };
-        const int km = wrap(k0 - 1, g.nz);
-        T psi_m = __ldg(Psi + km * plane + cj);
         T pc = __ldg(Psi + (size_t)k0 * plane + cj);
-        T ws_m = __ldg(Ws + km * plane + cj);
         Pl cur = load(k0);
         for (int k = k0; k < k1; ++k) {
             const size_t o = (size_t)k * plane;
@@ -721,25 +709,55 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, do
             V[o + cj] = Vn;
             W[o + cj] = Wn;
             if (P) P[o + cj] = a.p_replace ? pc : cur.pold + pc;
-            if (RESID) {
-                // the faces below the cell, recomputed the way their owners write them
-                const T Ul = cur.usm - c * ((pc - cur.pxm) * g.idx);
-                const T Vl = bottom ? T(0) : cur.vsm - c * ((pc - cur.pym) * g.idy);
-                const T Wl = ws_m - c * ((pc - psi_m) * g.idz);
-                const double dv = (widen_f32(Un) - widen_f32(Ul)) * idx_d + (widen_f32(Vn) - widen_f32(Vl)) * idy_d
-                                  + (widen_f32(Wn) - widen_f32(Wl)) * idz_d;
-                const unsigned long long ab = (unsigned long long)__double_as_longlong(dv) & 0x7fffffffffffffffull;
-                // |dv| finite <=> its exponent field is not all ones
-                if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn) || ab >= 0x7ff0000000000000ull)
-                    bits |= EVP_BIT_NONFINITE;
-                else dmax_b = ab > dmax_b ? ab : dmax_b;
-            } else if (!isfinite(Un + Vn + Wn)) {
-                bits |= EVP_BIT_NONFINITE;
-            }
-            psi_m = pc;
+            if (!isfinite(Un + Vn + Wn)) bits |= EVP_BIT_NONFINITE;
             pc = cur.pz;
-            ws_m = cur.ws;
             cur = nxt;
+        }
+    }
+    bits = __reduce_or_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && bits) atomicOr(a.status, bits);
+}
+
+// FP64 max |div u| of a stored staggered velocity: per cell
+// (u_i - u_{i-1})/dx + (v_j - v_{j-1})/dy + (w_k - w_{k-1})/dz, the FP32 values
+// widened exactly by integer operations (widen_f32), periodic in x and z, in y
+// periodic or with v = 0 below the first row (walls).  A non-finite divergence
+// raises EVP_BIT_NONFINITE and stays out of the maximum, which is kept as the bit
+// pattern of a non-negative double (ordered like the unsigned integer); one
+// atomic max per block.  A 32 x 8 tile walks a chunk of z planes, carrying w of
+// the plane below.
+template <typename T>
+__device__ __forceinline__ double wide(T x) {
+    if constexpr (sizeof(T) == 4) return widen_f32(x);
+    else return x;
+}
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_div_residual(const Geo<T> g, const T* __restrict__ U, const T* __restrict__ V, const T* __restrict__ W,
+               double idx_d, double idy_d, double idz_d, int kz_chunk, unsigned long long* maxdiv, unsigned* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
+    unsigned long long dmax_b = 0ull;
+    unsigned bits = 0;
+    if (i < g.nx && j < g.ny) {
+        const size_t plane = (size_t)g.nx * g.ny;
+        const size_t cj = (size_t)j * g.nx + i;
+        const int im = wrap(i - 1, g.nx);
+        const int jm = j > 0 ? j - 1 : (g.walls ? -1 : g.ny - 1);
+        const size_t cxm = (size_t)j * g.nx + im, cym = (size_t)(jm < 0 ? 0 : jm) * g.nx + i;
+        double wm = wide(__ldg(W + (size_t)wrap(k0 - 1, g.nz) * plane + cj));
+        for (int k = k0; k < k1; ++k) {
+            const size_t o = (size_t)k * plane;
+            const double w0 = wide(__ldg(W + o + cj));
+            const double vm = jm < 0 ? 0.0 : wide(__ldg(V + o + cym));
+            const double dv = (wide(__ldg(U + o + cj)) - wide(__ldg(U + o + cxm))) * idx_d
+                              + (wide(__ldg(V + o + cj)) - vm) * idy_d + (w0 - wm) * idz_d;
+            wm = w0;
+            const unsigned long long ab = (unsigned long long)__double_as_longlong(dv) & 0x7fffffffffffffffull;
+            // |dv| finite <=> its exponent field is not all ones
+            if (ab >= 0x7ff0000000000000ull) bits |= EVP_BIT_NONFINITE;
+            else dmax_b = ab > dmax_b ? ab : dmax_b;
         }
     }
     __shared__ unsigned long long red[8];
@@ -767,8 +785,8 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a, double idx_d, double idy_d, do
             bits |= __shfl_xor_sync(0xffffffffu, bits, o);
         }
         if (lane == 0) {
-            if (RESID && dmax_b > 0ull) atomicMax(a.maxdiv, dmax_b);
-            if (bits) atomicOr(a.status, bits);
+            if (dmax_b > 0ull) atomicMax(maxdiv, dmax_b);
+            if (bits) atomicOr(status, bits);
         }
     }
 }
@@ -921,14 +939,29 @@ cudaError_t launch_correct(const Geo<T>& g, const CorrectArgs<T>& a, cudaStream_
     chunks = (g.nz + kz - 1) / kz;
     dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, chunks);
     th.b(K_CORRECT);
-    const cudaError_t e = a.maxdiv
-        ? launch_k(k_correct<T, true>, grid, block, 0, st, th.pdl, g, a, a.idx_d, a.idy_d, a.idz_d, kz)
-        : launch_k(k_correct<T, false>, grid, block, 0, st, th.pdl, g, a, a.idx_d, a.idy_d, a.idz_d, kz);
+    const cudaError_t e = launch_k(k_correct<T>, grid, block, 0, st, th.pdl, g, a, kz);
     if (e != cudaSuccess) return e;
     th.e(K_CORRECT);
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_div_residual(const Geo<T>& g, const T* U, const T* V, const T* W, double idx, double idy,
+                                double idz, unsigned long long* maxdiv, unsigned* status, cudaStream_t st) {
+    dim3 block(32, 8, 1);
+    const int tiles = ((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+    int chunks = (8 * 152 + tiles - 1) / tiles;
+    int kz = (g.nz + chunks - 1) / chunks;
+    chunks = (g.nz + kz - 1) / kz;
+    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, chunks);
+    k_div_residual<T><<<grid, block, 0, st>>>(g, U, V, W, idx, idy, idz, kz, maxdiv, status);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_div_residual<float>(const Geo<float>&, const float*, const float*, const float*, double,
+                                               double, double, unsigned long long*, unsigned*, cudaStream_t);
+template cudaError_t launch_div_residual<double>(const Geo<double>&, const double*, const double*, const double*,
+                                                double, double, double, unsigned long long*, unsigned*, cudaStream_t);
 template cudaError_t launch_poisson<float>(const Geo<float>&, const FFTTables<float>&, const PoissonArgs<float>&,
                                            cudaStream_t, const TimingHook&);
 template cudaError_t launch_poisson<double>(const Geo<double>&, const FFTTables<double>&,

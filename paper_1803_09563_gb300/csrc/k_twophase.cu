@@ -453,13 +453,11 @@ __global__ void __launch_bounds__(256) k_split_rhs(const Geo<T> g, const SplitAr
 }
 
 // u^{n+1} = u* - dt [grad p^{n+1}/rho_0 + (1/rho_f - 1/rho_0) grad p_hat]   (Eq. projection-LS)
-// and the FP64 max |div u^{n+1}|
 template <typename T>
 __global__ void __launch_bounds__(256) k_split_correct(const Geo<T> g, const SplitArgs<T> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
-    double dmax = 0.0;
     unsigned bits = 0;
     if (i < g.nx && j < g.ny) {
         const size_t c0 = lin(g, i, j, k);
@@ -481,24 +479,10 @@ __global__ void __launch_bounds__(256) k_split_correct(const Geo<T> g, const Spl
         a.U[c0] = Un;
         a.V[c0] = Vn;
         a.W[c0] = Wn;
-        const T Ul = face(0, i - 1, j, k), Vl = face(1, i, j - 1, k), Wl = face(2, i, j, k - 1);
-        const double dv = (double(Un) - double(Ul)) * a.idx_d + (double(Vn) - double(Vl)) * a.idy_d
-                          + (double(Wn) - double(Wl)) * a.idz_d;
-        dmax = fabs(dv);
-        if (!isfinite(Un) || !isfinite(Vn) || !isfinite(Wn) || !(dmax <= DBL_MAX)) {
-            bits |= EVP_BIT_NONFINITE;
-            dmax = 0.0;
-        }
+        if (!isfinite(Un + Vn + Wn)) bits |= EVP_BIT_NONFINITE;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        bits |= __shfl_xor_sync(0xffffffffu, bits, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (dmax > 0.0) atomicMax(a.maxdiv, (unsigned long long)__double_as_longlong(dmax));
-        if (bits) atomicOr(a.status, bits);
-    }
+    bits = __reduce_or_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && bits) atomicOr(a.status, bits);
 }
 
 }  // namespace

@@ -236,7 +236,8 @@ def evp_stress_rhs(state, rt):
 
 
 def evp_sync(state, raise_on_error=True):
-    """Returns (code, status bits, max |div u| of the last projection)."""
+    """Returns (code, status bits, FP64 max |div u| of the current velocity, which
+    after a step is the last projection's output)."""
     bits = c_uint(0)
     md = c_double(0.0)
     code = load().evp_sync(state, ctypes.byref(bits), ctypes.byref(md))
