@@ -951,6 +951,7 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
     s->mc.a_fene = model == EVP_FENE_P ? params->L2 / (params->L2 - 3.0) : 1.0;
     s->mc.mu_s = params->beta * mu0;
     s->mc.art_diff = model == EVP_NEWTONIAN ? 0.0 : params->art_diff;
+    s->mc.set_single();
     if (stream) {
         s->st = static_cast<cudaStream_t>(stream);
         s->own_stream = false;

@@ -95,7 +95,28 @@ struct ModelConst {
     double L2, a_fene;  // FENE-P L^2 and a = L^2/(L^2-3)
     double mu_s;        // solvent viscosity
     double art_diff;    // local artificial diffusivity of B (0: off)
+    // the same constants rounded to single precision on the host (set_single)
+    float f_inv_lam, f_gmod, f_tau_y, f_L2, f_a_fene, f_mu_s, f_art_diff;
+    void set_single() {
+        f_inv_lam = float(inv_lam);
+        f_gmod = float(gmod);
+        f_tau_y = float(tau_y);
+        f_L2 = float(L2);
+        f_a_fene = float(a_fene);
+        f_mu_s = float(mu_s);
+        f_art_diff = float(art_diff);
+    }
 };
+
+// A model constant in the kernel's precision T: single-precision kernels read the
+// host-rounded copy, so that no kernel converts a double (on GB300 a conversion
+// instruction runs on the narrow FP64 pipe, and the compiler may recompute such a
+// conversion inside a loop rather than keep it in a register).
+template <typename T>
+__device__ __forceinline__ T kconst(double d, float f) {
+    if constexpr (sizeof(T) == 4) return f;
+    else return d;
+}
 
 // Conversions between binary32 and binary64 (IEEE 754) done branch-free with
 // integer operations, so that FP64 work on FP32 data leaves the (narrow) FP64 pipe

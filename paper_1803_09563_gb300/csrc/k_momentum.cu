@@ -270,7 +270,8 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
                     if (psm[r] >= 0) cp_async(&sm.S[c][slot][psm[r]], a.S[c] + pb + coff[r]);
         }
     };
-    const T kgm = T(mc.gmod), kL2 = T(mc.L2), kaf = T(mc.a_fene);
+    const T kgm = kconst<T>(mc.gmod, mc.f_gmod), kL2 = kconst<T>(mc.L2, mc.f_L2);
+    const T kaf = kconst<T>(mc.a_fene, mc.f_a_fene);
     // staged raw B -> summed stress S in ring slot kk mod 3 (Table 1 inverted)
     auto build_s = [&](int kk) {
         if constexpr (!SPRE) {
@@ -370,7 +371,7 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
 
     const T h = T(0.5);
     const T idx2 = g.idx * g.idx, idy2 = g.idy * g.idy, idz2 = g.idz * g.idz;
-    const T mu = T(mc.mu_s);
+    const T mu = kconst<T>(mc.mu_s, mc.f_mu_s);
     const T two_a = T(2) * a.alpha;
     const int o = (ty + 1) * VW + tx + XO;
     const T* sx_ = a.trig;

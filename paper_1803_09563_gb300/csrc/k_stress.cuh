@@ -377,8 +377,9 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     cp_async_wait_all();
     __syncthreads();
 
-    const T inv_lam = T(mc.inv_lam);
-    const T kL2 = T(mc.L2), kaf = T(mc.a_fene), kgm = T(mc.gmod), kty = T(mc.tau_y);
+    const T inv_lam = kconst<T>(mc.inv_lam, mc.f_inv_lam);
+    const T kL2 = kconst<T>(mc.L2, mc.f_L2), kaf = kconst<T>(mc.a_fene, mc.f_a_fene);
+    const T kgm = kconst<T>(mc.gmod, mc.f_gmod), kty = kconst<T>(mc.tau_y, mc.f_tau_y);
     const T dtz = a.dt_zeta, dtx = a.dt_xi;
     const T hx = T(0.5) * g.idx, hy = T(0.5) * g.idy, hz = T(0.5) * g.idz;
     const int o = (ty + 1) * VW + tx + XO;    // this cell in a velocity plane
@@ -466,7 +467,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
                            + w[2][3] * (w[1][3] * w[4][3] - w[3][3] * w[2][3]);
             bool hit = det0 < T(0);
             if (MODEL == EVP_FENE_P) hit = hit || (w[0][3] + w[3][3] + w[5][3] >= T(0.95) * kL2);
-            kad = hit ? T(mc.art_diff) : T(0);
+            kad = hit ? kconst<T>(mc.art_diff, mc.f_art_diff) : T(0);
         }
 
         // ---- WENO5 advection (stencil direction +1 for a positive velocity), UCD, update
