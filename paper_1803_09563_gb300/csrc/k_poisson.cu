@@ -652,67 +652,37 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
 }
 
 // S8: u^k = u* - c grad psi at the faces, p += psi; non-finite results raise
-// EVP_BIT_NONFINITE.  A 32 x 8 tile walks a chunk of z planes; psi of the column
-// below is carried from the previous plane.
+// EVP_BIT_NONFINITE.  One thread per cell: its eight loads (psi at the cell and
+// its +x, +y, +z neighbours, u*, v*, w*, p) are independent, so each warp keeps
+// them all in flight; neighbours' psi come from L1/L2.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_correct(const Geo<T> g, const CorrectArgs<T> a, int kz_chunk) {
+k_correct(const Geo<T> g, const CorrectArgs<T> a) {
     pdl_wait();
     pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
-    const bool active = i < g.nx && j < g.ny;
+    const int k = blockIdx.z;
     unsigned bits = 0;
-    if (active) {
+    if (i < g.nx && j < g.ny) {
         const T c = a.coef;
-        const T* __restrict__ Psi = a.psi;
-        const T* __restrict__ Us = a.Us;
-        const T* __restrict__ Vs = a.Vs;
-        const T* __restrict__ Ws = a.Ws;
-        T* __restrict__ U = a.U;
-        T* __restrict__ V = a.V;
-        T* __restrict__ W = a.W;
-        T* __restrict__ P = a.P;
         const size_t plane = (size_t)g.nx * g.ny;
-        const size_t cj = (size_t)j * g.nx + i;
-        const int ip = wrap(i + 1, g.nx), jp = ycen(g, j + 1);
+        const size_t o = (size_t)k * plane, cj = (size_t)j * g.nx + i, c0 = o + cj;
         const bool top = g.walls && j == g.ny - 1;
-        const size_t cxp = (size_t)j * g.nx + ip, cyp = (size_t)jp * g.nx + i;
-        // psi of plane k carried from the previous plane; the loads of plane k+1
-        // are issued while plane k is being computed
-        struct Pl {
-            T pz, px, py, us, vs, ws, pold;
-        };
-        auto load = [&](int k) {
-            Pl v;
-            const size_t o = (size_t)k * plane;
-            v.pz = __ldg(Psi + (size_t)wrap(k + 1, g.nz) * plane + cj);
-            v.px = __ldg(Psi + o + cxp);
-            v.py = __ldg(Psi + o + cyp);
-            v.us = __ldg(Us + o + cj);
-            v.vs = __ldg(Vs + o + cj);
-            v.ws = __ldg(Ws + o + cj);
-            v.pold = (P && !a.p_replace) ? P[o + cj] : T(0);
-            return v;
-        };
-        T pc = __ldg(Psi + (size_t)k0 * plane + cj);
-        Pl cur = load(k0);
-        for (int k = k0; k < k1; ++k) {
-            const size_t o = (size_t)k * plane;
-            Pl nxt = cur;
-            if (k + 1 < k1) nxt = load(k + 1);
-            const T Un = cur.us - c * ((cur.px - pc) * g.idx);
-            const T Vn = top ? T(0) : cur.vs - c * ((cur.py - pc) * g.idy);
-            const T Wn = cur.ws - c * ((cur.pz - pc) * g.idz);
-            U[o + cj] = Un;
-            V[o + cj] = Vn;
-            W[o + cj] = Wn;
-            if (P) P[o + cj] = a.p_replace ? pc : cur.pold + pc;
-            if (!isfinite(Un + Vn + Wn)) bits |= EVP_BIT_NONFINITE;
-            pc = cur.pz;
-            cur = nxt;
-        }
+        const T pc = __ldg(a.psi + c0);
+        const T px = __ldg(a.psi + o + (size_t)j * g.nx + wrap(i + 1, g.nx));
+        const T py = __ldg(a.psi + o + (size_t)ycen(g, j + 1) * g.nx + i);
+        const T pz = __ldg(a.psi + (size_t)wrap(k + 1, g.nz) * plane + cj);
+        const T us = __ldg(a.Us + c0), vs = __ldg(a.Vs + c0), ws = __ldg(a.Ws + c0);
+        const T pold = (a.P && !a.p_replace) ? a.P[c0] : T(0);
+        const T Un = us - c * ((px - pc) * g.idx);
+        const T Vn = top ? T(0) : vs - c * ((py - pc) * g.idy);
+        const T Wn = ws - c * ((pz - pc) * g.idz);
+        a.U[c0] = Un;
+        a.V[c0] = Vn;
+        a.W[c0] = Wn;
+        if (a.P) a.P[c0] = a.p_replace ? pc : pold + pc;
+        if (!isfinite(Un + Vn + Wn)) bits |= EVP_BIT_NONFINITE;
     }
     bits = __reduce_or_sync(0xffffffffu, bits);
     if ((threadIdx.x & 31) == 0 && bits) atomicOr(a.status, bits);
@@ -933,13 +903,9 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
 template <typename T>
 cudaError_t launch_correct(const Geo<T>& g, const CorrectArgs<T>& a, cudaStream_t st, const TimingHook& th) {
     dim3 block(32, 8, 1);
-    const int tiles = ((g.nx + 31) / 32) * ((g.ny + 7) / 8);
-    int chunks = (8 * 152 + tiles - 1) / tiles;
-    int kz = (g.nz + chunks - 1) / chunks;
-    chunks = (g.nz + kz - 1) / kz;
-    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, chunks);
+    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
     th.b(K_CORRECT);
-    const cudaError_t e = launch_k(k_correct<T>, grid, block, 0, st, th.pdl, g, a, kz);
+    const cudaError_t e = launch_k(k_correct<T>, grid, block, 0, st, th.pdl, g, a);
     if (e != cudaSuccess) return e;
     th.e(K_CORRECT);
     return cudaGetLastError();

@@ -645,6 +645,33 @@ def test_poisson_solve_odd_sizes(evp, shape):
     assert rel(got, ref) < 1e-12
 
 
+# power-of-two sizes 16 .. 256 in each role (x pass, z pass, periodic y solve) of the
+# register-resident FFT kernels, with walls and periodic
+POW2_SHAPES = [(256, 16, 128, False), (16, 256, 64, False), (128, 64, 256, False), (64, 128, 16, False),
+               (256, 24, 128, True), (128, 16, 256, True), (16, 8, 64, True)]
+
+
+@pytest.mark.parametrize("shape", POW2_SHAPES)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-6)])
+def test_poisson_solve_power_of_two_sizes(evp, shape, prec, tol):
+    import torch
+    nx, ny, nz, walls = shape
+    sim, st, g, prm = setup_case(evp, shape, 'oldroyd_b', {}, prec)
+    r = np.random.default_rng(13).standard_normal((nz, ny, nx))
+    r -= r.mean()
+    if prec == 1:
+        r = r.astype(np.float32).astype(np.float64)
+    rd = torch.tensor(r, dtype=torch.float32 if prec else torch.float64, device='cuda')
+    psi = torch.empty_like(rd)
+    evp.evp_poisson_solve(sim.handle, rd, psi)
+    sim.sync()
+    ref = oracle.solve_poisson(r, g)
+    got = psi.cpu().numpy().astype(np.float64)
+    if not walls:
+        got, ref = got - got.mean(), ref - ref.mean()
+    assert rel(got, ref) < tol, (shape, prec, rel(got, ref))
+
+
 def test_fene_p_trace_limit_is_reported(evp):
     """A FENE-P state stretched beyond L^2 raises EVP_BIT_TRACE_LIMIT and evp_sync
     returns EVP_ERR_UNPHYSICAL (no clamping, no fault)."""
