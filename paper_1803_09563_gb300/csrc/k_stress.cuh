@@ -26,9 +26,10 @@ __device__ __forceinline__ constexpr int col_of(int c) { return c == 0 ? 0 : ((c
 
 
 // Tile geometry of the z-marching kernel: a 32 x 8 tile of cells in x-y walks
-// through a chunk of z planes.  B of the tile's own column lives in a 7-plane
-// register window (z stencils); the current plane of B with a 3-cell x-y halo
-// and three planes of u, v, w with a 1-cell halo live in shared memory.  Plane
+// through a chunk of z planes.  B of the tile's own columns lives in an 8-plane
+// shared-memory ring (planes k-3 .. k+3 for the z stencils, k+4 arriving); the
+// current plane of B with a 3-cell x-y halo and three planes of u, v, w with a
+// 1-cell halo live in shared memory too.  Plane
 // rows are 40 wide with the tile's i0 at column 4 (x = i0-4 .. i0+35), so that
 // when nx is a whole number of 16-byte chunks every row is staged in 16-byte
 // cp.async chunks; other grids stage element by element.
@@ -95,7 +96,7 @@ template <typename T>
 struct StressSmem {
     T B[2][6][BPL];     // plane k (being used) and plane k+1 (arriving) of B, 3-cell halo
     T V[3][4][VPL];     // [u, v, w][ring slot: planes k-1 .. k+2][plane with 1-cell halo]
-    T N[6][NT];         // plane k+4 of B for the tile's own columns (arriving)
+    T N[8][6][NT];      // ring of B planes k-3 .. k+4 for the tile's own columns (slot = plane & 7)
     T H[2][6][NT];      // RK3 history RT^{k-2} of planes k and k+1 for the tile's cells
 };
 
@@ -324,28 +325,27 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             for (int r = 0; r < NBH; ++r)
                 if (hsm[r] >= 0) cp_async(&sm.B[buf][c][hsm[r]], a.B[c] + ph + hoff[r]);
     };
-    // plane kk+4 of B for the tile's own columns (the window's next plane)
+    // plane kk of B for the tile's own columns into ring slot kk & 7 (kk >= -nz)
     auto fetch_next = [&](int kk) {
         const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
+        T* slot = &sm.N[kk & 7][0][0];
         if (VEC) {
 #pragma unroll
             for (int r = 0; r < NOC; ++r)
                 if (oc_sm[r] >= 0) {
                     const int c = oc_sm[r] / NT;
-                    cp_async16(&sm.N[0][0] + oc_sm[r], a.B[c] + pb + oc_off[r]);
+                    cp_async16(slot + oc_sm[r], a.B[c] + pb + oc_off[r]);
                 }
             return;
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) cp_async(&sm.N[c][tid], a.B[c] + pb + col);
+        for (int c = 0; c < 6; ++c) cp_async(slot + c * NT + tid, a.B[c] + pb + col);
     };
 
-    // ---- prologue: B window (planes k0-3 .. k0+3), velocity planes k0-1 .. k0+1, plane k0 of B
-    T w[6][7];
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-#pragma unroll
-        for (int m = 0; m < 7; ++m) w[c][m] = __ldg(a.B[c] + (size_t)pmod(k0 + m - 3, g.nz) * plane + col);
+    // ---- prologue: the own-column ring (planes k0-3 .. k0+3), velocity planes
+    // k0-1 .. k0+1, the halo of plane k0; then its interior from the ring
+#pragma unroll 1
+    for (int m = -3; m <= 3; ++m) fetch_next(k0 + m);
     fetch_vel(k0 - 1);
     fetch_vel(k0);
     fetch_vel(k0 + 1);
@@ -371,10 +371,11 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     };
     fetch_hist(k0);
     const int ob = (ty + 3) * BW + tx + XO;   // this cell in a B plane
-#pragma unroll
-    for (int c = 0; c < 6; ++c) sm.B[k0 & 1][c][ob] = w[c][3];
     cp_async_commit();
     cp_async_wait_all();
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sm.B[k0 & 1][c][ob] = sm.N[k0 & 7][c][tid];
     __syncthreads();
 
     const T inv_lam = kconst<T>(mc.inv_lam, mc.f_inv_lam);
@@ -386,8 +387,13 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     unsigned bits = 0;
 
     for (int k = k0; k < k1; ++k) {
-        // ---- asynchronous prefetch: plane k+4 of B (own column), halo of plane k+1, velocity plane k+2
+        // ---- plane k+1 of B: the interior from the ring, the halo by asynchronous
+        // copy; asynchronous prefetch of plane k+4 (own columns), velocity plane k+2
+        // and history plane k+1.  Every buffer written here was last read before
+        // the previous plane's barrier, the only one per plane.
         {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sm.B[(k + 1) & 1][c][ob] = sm.N[(k + 1) & 7][c][tid];
             fetch_next(k + 4);
             fetch_halo(k + 1);
             fetch_vel(k + 2);
@@ -419,13 +425,19 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         L[2][0] = (T(0.5) * (Wp_[o + 1] + Wc_[o + 1]) - T(0.5) * (Wp_[o - 1] + Wc_[o - 1])) * hx;
         L[2][1] = (T(0.5) * (Wp_[o + VW] + Wc_[o + VW]) - T(0.5) * (Wp_[o - VW] + Wc_[o - VW])) * hy;
 
+        // ---- B^{k-1} of the cell (ring slot of plane k)
+        const T* Nf = &sm.N[0][0][0];
+        T b0[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) b0[c] = sm.N[k & 7][c][tid];
+
         // ---- Table 1 closure at the cell
         T F = T(1), av = T(1);
         if (MODEL == EVP_NEO_HOOKEAN) {
             F = T(0);
             av = T(0);
         } else if (MODEL == EVP_FENE_P) {
-            const T tr = w[0][3] + w[3][3] + w[5][3];
+            const T tr = b0[0] + b0[3] + b0[5];
             if (sizeof(T) == 4) F = kL2 * T(rcp_approx(float(kL2 - tr)));
             else F = kL2 / (kL2 - tr);
             av = kaf;
@@ -438,7 +450,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             }
             T t[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) t[c] = gm * (w[c][3] - ((c == 0 || c == 3 || c == 5) ? T(1) : T(0)));
+            for (int c = 0; c < 6; ++c) t[c] = gm * (b0[c] - ((c == 0 || c == 3 || c == 5) ? T(1) : T(0)));
             const T tr3 = (t[0] + t[3] + t[5]) * T(1.0 / 3.0);
             const T d0 = t[0] - tr3, d3 = t[3] - tr3, d5 = t[5] - tr3;
             const T mag2 = T(0.5) * (d0 * d0 + d3 * d3 + d5 * d5) + t[1] * t[1] + t[2] * t[2] + t[4] * t[4];
@@ -462,11 +474,10 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         // ---- local artificial diffusion (Sec. 3.1): selected from B^{k-1} of the cell
         T kad = T(0);
         if constexpr (DIFF) {
-            const T det0 = w[0][3] * (w[3][3] * w[5][3] - w[4][3] * w[4][3])
-                           - w[1][3] * (w[1][3] * w[5][3] - w[4][3] * w[2][3])
-                           + w[2][3] * (w[1][3] * w[4][3] - w[3][3] * w[2][3]);
+            const T det0 = b0[0] * (b0[3] * b0[5] - b0[4] * b0[4]) - b0[1] * (b0[1] * b0[5] - b0[4] * b0[2])
+                           + b0[2] * (b0[1] * b0[4] - b0[3] * b0[2]);
             bool hit = det0 < T(0);
-            if (MODEL == EVP_FENE_P) hit = hit || (w[0][3] + w[3][3] + w[5][3] >= T(0.95) * kL2);
+            if (MODEL == EVP_FENE_P) hit = hit || (b0[0] + b0[3] + b0[5] >= T(0.95) * kL2);
             kad = hit ? kconst<T>(mc.art_diff, mc.f_art_diff) : T(0);
         }
 
@@ -476,6 +487,11 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         const size_t cell = (size_t)k * plane + (size_t)j * g.nx + i;
         const T* Bk = sm.B[k & 1][0];
         const T vx_ = fabs(uc) * g.idx, vy_ = fabs(vc) * g.idy, vz_ = fabs(wc) * g.idz;
+        // ring offsets of the z stencil of this cell, far upwind first: planes
+        // k-3 .. k+2 for a positive w, mirrored (k+3 .. k-2) otherwise
+        int zo[6];
+#pragma unroll
+        for (int n = 0; n < 6; ++n) zo[n] = ((zpos ? k - 3 + n : k + 3 - n) & 7) * (6 * NT) + tid;
         T bn[6], advc[6];
         if constexpr (sizeof(T) == 4) {
             // single precision: the components in pairs (xx, xy), (xz, yy), (yz, zz),
@@ -485,12 +501,11 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
                 const float* P0 = Bk + (2 * p) * BPL;
                 const float* P1 = P0 + BPL;
                 auto at = [&](int off) { return make_float2(P0[ob + off], P1[ob + off]); };
-                auto wz = [&](int m) { return make_float2(w[2 * p][m], w[2 * p + 1][m]); };
+                auto zz = [&](int n) { return make_float2(Nf[zo[n] + (2 * p) * NT], Nf[zo[n] + (2 * p + 1) * NT]); };
                 float2 s = upwind_term2(splat2(vx_), at(-3 * sx), at(-2 * sx), at(-sx), at(0), at(sx), at(2 * sx));
                 s = add2(s, upwind_term2(splat2(vy_), at(-3 * syw), at(-2 * syw), at(-syw), at(0), at(syw), at(2 * syw)));
-                // z stencil from the register window, mirrored for a non-positive w
-                s = add2(s, upwind_term2(splat2(vz_), zpos ? wz(0) : wz(6), zpos ? wz(1) : wz(5), zpos ? wz(2) : wz(4),
-                                         wz(3), zpos ? wz(4) : wz(2), zpos ? wz(5) : wz(1)));
+                // z stencil from the ring
+                s = add2(s, upwind_term2(splat2(vz_), zz(0), zz(1), zz(2), zz(3), zz(4), zz(5)));
                 advc[2 * p] = s.x;
                 advc[2 * p + 1] = s.y;
             }
@@ -500,10 +515,9 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
                 const T* P = Bk + c * BPL;
                 T adv = upwind_term(vx_, P[ob - 3 * sx], P[ob - 2 * sx], P[ob - sx], P[ob], P[ob + sx], P[ob + 2 * sx]);
                 adv += upwind_term(vy_, P[ob - 3 * syw], P[ob - 2 * syw], P[ob - syw], P[ob], P[ob + syw], P[ob + 2 * syw]);
-                // z stencil from the register window, mirrored for a non-positive w
-                const T z0 = zpos ? w[c][0] : w[c][6], z1 = zpos ? w[c][1] : w[c][5], z2 = zpos ? w[c][2] : w[c][4];
-                const T z4 = zpos ? w[c][4] : w[c][2], z5 = zpos ? w[c][5] : w[c][1];
-                advc[c] = adv + upwind_term(vz_, z0, z1, z2, w[c][3], z4, z5);
+                // z stencil from the ring
+                advc[c] = adv + upwind_term(vz_, Nf[zo[0] + c * NT], Nf[zo[1] + c * NT], Nf[zo[2] + c * NT], b0[c],
+                                            Nf[zo[4] + c * NT], Nf[zo[5] + c * NT]);
             }
         }
 #pragma unroll
@@ -513,22 +527,23 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             const int ra = row_of(c), cb = col_of(c);
             T ucd = T(0);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) ucd += L[ra][q] * w[symi(q, cb)][3] + w[symi(ra, q)][3] * L[cb][q];
+            for (int q = 0; q < 3; ++q) ucd += L[ra][q] * b0[symi(q, cb)] + b0[symi(ra, q)] * L[cb][q];
             const bool diag = (c == 0 || c == 3 || c == 5);
-            const T src = ((diag ? av : T(0)) - F * w[c][3]) * inv_lam;
+            const T src = ((diag ? av : T(0)) - F * b0[c]) * inv_lam;
             T rt = src + ucd - adv;
             if (DIFF && kad != T(0)) {
-                const T b0 = w[c][3];
-                rt += kad * ((P[ob - 1] + P[ob + 1] - T(2) * b0) * (g.idx * g.idx)
-                             + (P[ob - BW] + P[ob + BW] - T(2) * b0) * (g.idy * g.idy)
-                             + (w[c][2] + w[c][4] - T(2) * b0) * (g.idz * g.idz));
+                const T bc = b0[c];
+                const T zm = sm.N[(k - 1) & 7][c][tid], zp = sm.N[(k + 1) & 7][c][tid];
+                rt += kad * ((P[ob - 1] + P[ob + 1] - T(2) * bc) * (g.idx * g.idx)
+                             + (P[ob - BW] + P[ob + BW] - T(2) * bc) * (g.idy * g.idy)
+                             + (zm + zp - T(2) * bc) * (g.idz * g.idz));
             }
             if (RHS_ONLY) {
                 if (active) a.RT[c][cell] = rt;
             } else {
                 T inc = dtz * rt;
                 if (READ_H) inc += dtx * sm.H[k & 1][c][tid];
-                bn[c] = w[c][3] + inc;
+                bn[c] = b0[c] + inc;
                 if (active) {
                     a.Bn[c][cell] = bn[c];
                     if (WRITE_H) a.RT[c][cell] = rt;
@@ -547,36 +562,29 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
                 // the divergence term of the momentum step
                 const T gm = kgm;
                 if (MODEL == EVP_FENE_P) {
-                    const T Fo = kL2 / (kL2 - (w[0][3] + w[3][3] + w[5][3]));
+                    const T Fo = kL2 / (kL2 - (b0[0] + b0[3] + b0[5]));
                     const T Fn = kL2 / (kL2 - (bn[0] + bn[3] + bn[5]));
 #pragma unroll
                     for (int c = 0; c < 6; ++c) {
                         const bool d = (c == 0 || c == 3 || c == 5);
-                        a.S[c][cell] = gm * (Fn * bn[c] - (d ? kaf : T(0))) + gm * (Fo * w[c][3] - (d ? kaf : T(0)));
+                        a.S[c][cell] = gm * (Fn * bn[c] - (d ? kaf : T(0))) + gm * (Fo * b0[c] - (d ? kaf : T(0)));
                     }
                 } else if (MODEL == EVP_NEO_HOOKEAN) {
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) a.S[c][cell] = gm * bn[c] + gm * w[c][3];
+                    for (int c = 0; c < 6; ++c) a.S[c][cell] = gm * bn[c] + gm * b0[c];
                 } else {
 #pragma unroll
                     for (int c = 0; c < 6; ++c) {
                         const bool d = (c == 0 || c == 3 || c == 5);
-                        a.S[c][cell] = gm * (bn[c] - (d ? T(1) : T(0))) + gm * (w[c][3] - (d ? T(1) : T(0)));
+                        a.S[c][cell] = gm * (bn[c] - (d ? T(1) : T(0))) + gm * (b0[c] - (d ? T(1) : T(0)));
                     }
                 }
             }
         }
 
-        // ---- advance the window; publish the interior of plane k+1
+        // ---- plane k+1 (halo) and ring slot k+4 have landed; after the barrier
+        // they are visible to every thread
         cp_async_wait_all();
-        __syncthreads();
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-#pragma unroll
-            for (int m = 0; m < 6; ++m) w[c][m] = w[c][m + 1];
-            w[c][6] = sm.N[c][tid];
-            sm.B[(k + 1) & 1][c][ob] = w[c][3];
-        }
         __syncthreads();
     }
     if (bits) atomicOr(a.status, bits);
