@@ -298,12 +298,11 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    host_np = [h.numpy() for h in host]
     for _ in range(e2e_steps):
-        for f, h in zip(fields_io, host):
-            evp.evp_set_field(sim.handle, f, h.numpy())
+        evp.evp_set_fields(sim.handle, fields_io, host_np)
         sim.step(w['dt'])
-        for f, h in zip(fields_io, host):
-            evp.evp_get_field(sim.handle, f, h.numpy())
+        evp.evp_get_fields(sim.handle, fields_io, host_np)
     torch.cuda.synchronize()
     e2e_s = max_ranks(time.perf_counter() - t0)
     e2e_value = job_rate(N, e2e_steps, world, e2e_s)

@@ -176,6 +176,16 @@ int evp_destroy(evp_state* s);
 int evp_set_field(evp_state* s, int field, const void* src, int src_on_device);
 int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device);
 
+/* Several fields at once: n copies as evp_set_field / evp_get_field would make
+ * (fields[i] <-> bufs[i], each nx*ny*nz elements of the state's precision), all
+ * enqueued on the state's stream, then one synchronisation.  Host buffers that
+ * are page-locked (cudaHostAlloc / pinned) copy asynchronously at full link
+ * speed.  The arrays fields and bufs (n entries) are read during the call only.
+ * Errors: EVP_ERR_ARG (n < 0, null arrays or buffers, unknown field, EVP_PSI in
+ * evp_set_fields), in which case nothing is copied.                          */
+int evp_set_fields(evp_state* s, int n, const int* fields, const void* const* srcs, int src_on_device);
+int evp_get_fields(evp_state* s, int n, const int* fields, void* const* dsts, int dst_on_device);
+
 /* One full RK3 time step of size dt (Sec. 3.3.1, Eqs. RK-rt..NS-num3, RK):
  * three substeps, each B update (Eq. rk3tau), momentum predictor (Eq. rk3),
  * Poisson solve (Eq. NS-num2) and correction (Eq. NS-num3).  Asynchronous.   */

@@ -1022,29 +1022,65 @@ int evp_destroy(evp_state* s) {
     return EVP_OK;
 }
 
-int evp_set_field(evp_state* s, int field, const void* src, int src_on_device) {
-    if (!s || !src) return fail(EVP_ERR_ARG, "null state or source");
-    if (field == EVP_PSI) return fail(EVP_ERR_ARG, "EVP_PSI is read only");
+namespace {
+// enqueue the copy of one field into the state on stream st (no synchronisation)
+int put_field(evp_state* s, int field, const void* src, int src_on_device, cudaStream_t st) {
     void* dst = field_ptr(s, field);
-    if (!dst) return fail(EVP_ERR_ARG, "unknown field id");
     const size_t bytes = s->N * s->elt;
-    CK(cudaMemcpyAsync(dst, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(dst, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     if (field == EVP_V && s->g.walls_y) {
         // the stored top face is the wall: v = 0
         const size_t row = (size_t)s->g.nx * s->elt;
         CK(cudaMemset2DAsync(static_cast<char*>(dst) + (size_t)(s->g.ny - 1) * row, (size_t)s->g.ny * row, 0, row,
-                             s->g.nz, s->st));
+                             s->g.nz, st));
     }
+    return EVP_OK;
+}
+int take_field(evp_state* s, int field, void* dst, int dst_on_device, cudaStream_t st) {
+    CK(cudaMemcpyAsync(dst, field_ptr(s, field), s->N * s->elt,
+                       dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    return EVP_OK;
+}
+}  // namespace
+
+int evp_set_field(evp_state* s, int field, const void* src, int src_on_device) {
+    if (!s || !src) return fail(EVP_ERR_ARG, "null state or source");
+    if (field == EVP_PSI) return fail(EVP_ERR_ARG, "EVP_PSI is read only");
+    if (!field_ptr(s, field)) return fail(EVP_ERR_ARG, "unknown field id");
+    if (int r = put_field(s, field, src, src_on_device, s->st)) return r;
     CK(cudaStreamSynchronize(s->st));
     return EVP_OK;
 }
 
 int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device) {
     if (!s || !dst) return fail(EVP_ERR_ARG, "null state or destination");
-    const void* src = field_ptr(s, field);
-    if (!src) return fail(EVP_ERR_ARG, "unknown field id");
-    CK(cudaMemcpyAsync(dst, src, s->N * s->elt, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       s->st));
+    if (!field_ptr(s, field)) return fail(EVP_ERR_ARG, "unknown field id");
+    if (int r = take_field(s, field, dst, dst_on_device, s->st)) return r;
+    CK(cudaStreamSynchronize(s->st));
+    return EVP_OK;
+}
+
+int evp_set_fields(evp_state* s, int n, const int* fields, const void* const* srcs, int src_on_device) {
+    if (!s || n < 0 || (n > 0 && (!fields || !srcs))) return fail(EVP_ERR_ARG, "null state or arrays, or n < 0");
+    for (int i = 0; i < n; ++i) {
+        if (!srcs[i]) return fail(EVP_ERR_ARG, "null source buffer");
+        if (fields[i] == EVP_PSI) return fail(EVP_ERR_ARG, "EVP_PSI is read only");
+        if (!field_ptr(s, fields[i])) return fail(EVP_ERR_ARG, "unknown field id");
+    }
+    for (int i = 0; i < n; ++i)
+        if (int r = put_field(s, fields[i], srcs[i], src_on_device, s->st)) return r;
+    CK(cudaStreamSynchronize(s->st));
+    return EVP_OK;
+}
+
+int evp_get_fields(evp_state* s, int n, const int* fields, void* const* dsts, int dst_on_device) {
+    if (!s || n < 0 || (n > 0 && (!fields || !dsts))) return fail(EVP_ERR_ARG, "null state or arrays, or n < 0");
+    for (int i = 0; i < n; ++i) {
+        if (!dsts[i]) return fail(EVP_ERR_ARG, "null destination buffer");
+        if (!field_ptr(s, fields[i])) return fail(EVP_ERR_ARG, "unknown field id");
+    }
+    for (int i = 0; i < n; ++i)
+        if (int r = take_field(s, fields[i], dsts[i], dst_on_device, s->st)) return r;
     CK(cudaStreamSynchronize(s->st));
     return EVP_OK;
 }

@@ -76,6 +76,8 @@ def load(path=None):
         'evp_destroy': (c_int, [c_void_p]),
         'evp_set_field': (c_int, [c_void_p, c_int, c_void_p, c_int]),
         'evp_get_field': (c_int, [c_void_p, c_int, c_void_p, c_int]),
+        'evp_set_fields': (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_void_p), c_int]),
+        'evp_get_fields': (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_void_p), c_int]),
         'evp_step': (c_int, [c_void_p, c_double]),
         'evp_set_graph': (c_int, [c_void_p, c_int]),
         'evp_set_pdl': (c_int, [c_void_p, c_int]),
@@ -107,7 +109,8 @@ def exported_symbols():
     return ['evp_state_bytes', 'evp_init', 'evp_destroy', 'evp_set_field', 'evp_get_field', 'evp_step',
             'evp_substep', 'evp_project', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_sync', 'evp_kernel_timing',
             'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error', 'evp_poisson_solve_static',
-            'evp_set_graph', 'evp_selftest', 'evp_set_pdl', 'evp_set_particles', 'evp_get_particles']
+            'evp_set_graph', 'evp_selftest', 'evp_set_pdl', 'evp_set_particles', 'evp_get_particles',
+            'evp_set_fields', 'evp_get_fields']
 
 
 def _check(code):
@@ -178,6 +181,31 @@ def evp_set_field(state, field, src):
 def evp_get_field(state, field, dst):
     p, dev, _ = _ptr(dst)
     return _check(load().evp_get_field(state, int(field), p, dev))
+
+
+def _field_arrays(fields, bufs):
+    if len(fields) != len(bufs):
+        raise ValueError('one buffer per field')
+    ptrs = [_ptr(b) for b in bufs]
+    devs = {d for _, d, _ in ptrs}
+    if len(devs) > 1:
+        raise ValueError('all buffers on the host or all on the device')
+    n = len(fields)
+    ids = (c_int * n)(*[int(f) for f in fields])
+    ps = (c_void_p * n)(*[p for p, _, _ in ptrs])
+    return n, ids, ps, (devs.pop() if devs else 0)
+
+
+def evp_set_fields(state, fields, srcs):
+    """Copy several fields into the state with one synchronisation."""
+    n, ids, ps, dev = _field_arrays(fields, srcs)
+    return _check(load().evp_set_fields(state, n, ids, ps, dev))
+
+
+def evp_get_fields(state, fields, dsts):
+    """Copy several fields out of the state with one synchronisation."""
+    n, ids, ps, dev = _field_arrays(fields, dsts)
+    return _check(load().evp_get_fields(state, n, ids, ps, dev))
 
 
 def evp_step(state, dt):

@@ -210,6 +210,39 @@ def test_nonfinite_input_raises_status(evp):
     assert code == 0 and bits == 0 and maxdiv == 0.0
 
 
+def test_batched_field_copies(evp):
+    """evp_set_fields / evp_get_fields move the same data as the single-field
+    calls (host and device buffers), apply the wall rule to v, and reject the
+    read-only field before copying anything."""
+    import torch
+    shape = (32, 16, 8, True)
+    sim, st, g, prm = setup_case(evp, shape, 'saramito', {'Bi': 0.4}, evp.EVP_FP32)
+    rng = np.random.default_rng(21)
+    fields = [evp.EVP_U, evp.EVP_V, evp.EVP_P, evp.EVP_BXY]
+    vals = [rng.standard_normal(sim.shape).astype(np.float32) for _ in fields]
+    evp.evp_set_fields(sim.handle, fields, vals)
+    out = [np.empty(sim.shape, np.float32) for _ in fields]
+    evp.evp_get_fields(sim.handle, fields, out)
+    for f, v, o in zip(fields, vals, out):
+        ref = v.copy()
+        if f == evp.EVP_V:
+            ref[:, -1] = 0.0        # the stored top face is the wall
+        assert np.array_equal(o, ref), f
+        single = np.empty(sim.shape, np.float32)
+        evp.evp_get_field(sim.handle, f, single)
+        assert np.array_equal(single, o)
+    dev = [torch.zeros(sim.shape, dtype=torch.float32, device='cuda') for _ in fields]
+    evp.evp_get_fields(sim.handle, fields, dev)
+    for d, o in zip(dev, out):
+        assert np.array_equal(d.cpu().numpy(), o)
+    with pytest.raises(evp.EvpError):
+        evp.evp_set_fields(sim.handle, [evp.EVP_U, evp.EVP_PSI], [vals[0], vals[0]])
+    got = np.empty(sim.shape, np.float32)
+    evp.evp_get_field(sim.handle, evp.EVP_U, got)
+    assert np.array_equal(got, out[0])          # nothing copied by the rejected call
+    evp.evp_set_fields(sim.handle, [], [])      # an empty batch is a no-op
+
+
 def test_bad_arguments_rejected(evp):
     with pytest.raises(evp.EvpError):
         evp.Simulation(evp.make_grid(20, 16, 16, 1.0, 1.0, 1.0), 'oldroyd_b', evp.make_params(Re=1.0))
