@@ -11,7 +11,7 @@
 // faces (i+1/2, j, k), (i, j+1/2, k), (i, j, k+1/2) of its cell; with walls the
 // top y-face stays zero.
 //
-// A 32 x 8 tile walks a chunk of z planes.  Shared memory holds planes k-1..k+1
+// A 32 x 4 tile walks a chunk of z planes.  Shared memory holds planes k-1..k+1
 // (1-cell x-y halo) of u, v, w (4-slot ring, refilled by cp.async), of the summed
 // stress S = tau^k + tau^{k-1} (3-slot ring, built from raw B planes staged by
 // cp.async) and of p, plus the cell's momentum history.  A plane row is 40 wide
@@ -27,9 +27,9 @@ namespace evp {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int TX = 32, TY = 4, NT = TX * TY;
 constexpr int VW = TX + 8, XO = 4;                       // plane row width; column of the tile's i0
-constexpr int VH = TY + 2, VPL = VW * VH;                // rows j0-1 .. j0+8
+constexpr int VH = TY + 2, VPL = VW * VH;                // rows j0-1 .. j0+TY
 constexpr int SW = TX + 2;                               // columns the stencils use: XO-1 .. XO+TX
 constexpr int NV = (SW * VH + NT - 1) / NT;              // used plane cells per thread (2)
 
@@ -88,7 +88,7 @@ __device__ __forceinline__ int vslot(int kk) { return (kk + 5) % 5; }   // kk >=
 // VEC: rows are staged in 16-byte chunks (needs nx * sizeof(T) % 16 == 0)
 // SPRE: the summed stress comes precomputed (MomentumArgs::S); MODEL is then unused
 template <typename T, int MODEL, bool VEC, bool SPRE>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2)
 k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_chunk) {
     pdl_wait();
     pdl_trigger();
@@ -530,7 +530,7 @@ cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const Momentu
                             cudaStream_t st, const TimingHook& th) {
     // z chunks: about four waves of CTAs; small grids go down to one plane per CTA
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-    const int per_sm = sizeof(T) == 4 ? 2 : 1;
+    const int per_sm = sizeof(T) == 4 ? 4 : 2;
     int chunks = (4 * 152 * per_sm + tiles - 1) / tiles;
     chunks = chunks > g.nz ? g.nz : chunks;
     const int kz = (g.nz + chunks - 1) / chunks;
