@@ -281,30 +281,37 @@ def test_volume_penalisation_channel(evp, prec, tol):
         assert rel(got, ref) < tol, (q, rel(got, ref))
 
 
-def test_abc_forcing_fene_p_fp64(evp):
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-5)])
+def test_abc_forcing_fene_p(evp, prec, tol):
     """ABC body force A(sin kz + cos ky, sin kx + cos kz, sin ky + cos kx) on a
     FENE-P box (the forced-turbulence setting): two RK3 steps against the oracle,
-    the force sampled at the faces from its definition."""
+    the force sampled at the faces from its definition.  In FP32 (nx a multiple of
+    4) the momentum kernel computes two cells per thread and reads the force tables
+    in pairs."""
     nx, ny, nz = 48, 24, 18
     L = 2 * np.pi
     geo = inputs.geometry(nx, ny, nz, L, L, L)
     g = oracle.Grid(nx, ny, nz, L, L, L)
     U, V, W = inputs.scale_max(*inputs.random_solenoidal(geo, 21, 3), 1.0)
+    if prec == 1:
+        U, V, W = (a.astype(np.float32).astype(np.float64) for a in (U, V, W))
     A, k = 0.7, 2.0
     xc, yc, zc = g.xc(), g.yc(), g.zc()
     force = (A * (np.sin(k * zc) + np.cos(k * yc)) + 0 * g.zeros(), A * (np.sin(k * xc) + np.cos(k * zc)) + 0 * g.zeros(),
              A * (np.sin(k * yc) + np.cos(k * xc)) + 0 * g.zeros())
     prm = oracle.Params.from_groups('fene_p', 200.0, 5.0, 0.9, L2=900.0)
     sim = evp.Simulation(evp.make_grid(nx, ny, nz, L, L, L), 'fene_p',
-                         evp.make_params(Re=200.0, Wi=5.0, beta=0.9, L2=900.0, abc_amp=A, abc_k=k, precision=0))
+                         evp.make_params(Re=200.0, Wi=5.0, beta=0.9, L2=900.0, abc_amp=A, abc_k=k, precision=prec))
     sim.set_state(U, V, W)
     st = oracle.State.rest(g, U, V, W)
     for _ in range(2):
         sim.step(1e-3)
         st = oracle.rk3_step(st, 1e-3, g, prm, force)
     sim.sync()
-    for got, ref in zip(fields(sim, evp), oracle_fields(st)):
-        assert rel(got, ref) < 1e-10
+    for q, (got, ref) in enumerate(zip(fields(sim, evp), oracle_fields(st))):
+        if prec == 1 and q == 3:
+            continue    # FP32 pressure: see test_rk3_step_fp32
+        assert rel(got, ref) < tol, (q, rel(got, ref))
 
 
 def defect_conformation(geo, seed, L2):
