@@ -652,15 +652,27 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
 }
 
 // S8: u^k = u* - c grad psi at the faces, p += psi; non-finite results raise
-// EVP_BIT_NONFINITE.  One thread per cell: its eight loads (psi at the cell and
-// its +x, +y, +z neighbours, u*, v*, w*, p) are independent, so each warp keeps
-// them all in flight; neighbours' psi come from L1/L2.
+// EVP_BIT_NONFINITE.  One thread per pair of x-adjacent cells (nx is even): its
+// loads (psi at the pair, the next x cell, the +y and +z pairs; u*, v*, w*, p)
+// are independent 8- or 16-byte accesses, so each warp keeps them all in flight;
+// neighbours' psi come from L1/L2.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_correct(const Geo<T> g, const CorrectArgs<T> a) {
+    using V = typename Pair<T>::type;
     pdl_wait();
     pdl_trigger();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     unsigned bits = 0;
@@ -669,20 +681,32 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a) {
         const size_t plane = (size_t)g.nx * g.ny;
         const size_t o = (size_t)k * plane, cj = (size_t)j * g.nx + i, c0 = o + cj;
         const bool top = g.walls && j == g.ny - 1;
-        const T pc = __ldg(a.psi + c0);
-        const T px = __ldg(a.psi + o + (size_t)j * g.nx + wrap(i + 1, g.nx));
-        const T py = __ldg(a.psi + o + (size_t)ycen(g, j + 1) * g.nx + i);
-        const T pz = __ldg(a.psi + (size_t)wrap(k + 1, g.nz) * plane + cj);
-        const T us = __ldg(a.Us + c0), vs = __ldg(a.Vs + c0), ws = __ldg(a.Ws + c0);
-        const T pold = (a.P && !a.p_replace) ? a.P[c0] : T(0);
-        const T Un = us - c * ((px - pc) * g.idx);
-        const T Vn = top ? T(0) : vs - c * ((py - pc) * g.idy);
-        const T Wn = ws - c * ((pz - pc) * g.idz);
-        a.U[c0] = Un;
-        a.V[c0] = Vn;
-        a.W[c0] = Wn;
-        if (a.P) a.P[c0] = a.p_replace ? pc : pold + pc;
-        if (!isfinite(Un + Vn + Wn)) bits |= EVP_BIT_NONFINITE;
+        auto ld = [](const T* p) { return __ldg(reinterpret_cast<const V*>(p)); };
+        const V pc = ld(a.psi + c0);
+        const T px1 = __ldg(a.psi + o + (size_t)j * g.nx + wrap(i + 2, g.nx));
+        const V py = ld(a.psi + o + (size_t)ycen(g, j + 1) * g.nx + i);
+        const V pz = ld(a.psi + (size_t)wrap(k + 1, g.nz) * plane + cj);
+        const V us = ld(a.Us + c0), vs = ld(a.Vs + c0), ws = ld(a.Ws + c0);
+        V Un, Vn, Wn;
+        Un.x = us.x - c * ((pc.y - pc.x) * g.idx);
+        Un.y = us.y - c * ((px1 - pc.y) * g.idx);
+        Vn.x = top ? T(0) : vs.x - c * ((py.x - pc.x) * g.idy);
+        Vn.y = top ? T(0) : vs.y - c * ((py.y - pc.y) * g.idy);
+        Wn.x = ws.x - c * ((pz.x - pc.x) * g.idz);
+        Wn.y = ws.y - c * ((pz.y - pc.y) * g.idz);
+        *reinterpret_cast<V*>(a.U + c0) = Un;
+        *reinterpret_cast<V*>(a.V + c0) = Vn;
+        *reinterpret_cast<V*>(a.W + c0) = Wn;
+        if (a.P) {
+            V pn = pc;
+            if (!a.p_replace) {
+                const V pold = *reinterpret_cast<const V*>(a.P + c0);
+                pn.x = pold.x + pc.x;
+                pn.y = pold.y + pc.y;
+            }
+            *reinterpret_cast<V*>(a.P + c0) = pn;
+        }
+        if (!isfinite(Un.x + Vn.x + Wn.x + Un.y + Vn.y + Wn.y)) bits |= EVP_BIT_NONFINITE;
     }
     bits = __reduce_or_sync(0xffffffffu, bits);
     if ((threadIdx.x & 31) == 0 && bits) atomicOr(a.status, bits);
@@ -903,7 +927,7 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
 template <typename T>
 cudaError_t launch_correct(const Geo<T>& g, const CorrectArgs<T>& a, cudaStream_t st, const TimingHook& th) {
     dim3 block(32, 8, 1);
-    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    dim3 grid((g.nx / 2 + 31) / 32, (g.ny + 7) / 8, g.nz);
     th.b(K_CORRECT);
     const cudaError_t e = launch_k(k_correct<T>, grid, block, 0, st, th.pdl, g, a);
     if (e != cudaSuccess) return e;
