@@ -26,7 +26,7 @@ enum KernelId {
     K_THOMAS,         // S6, walls: FP64 tridiagonal solve per (kx, kz)
     K_FFT_Z_INV,      // S7(z): inverse complex FFT along z
     K_IFFTX,          // S7(x): complex-to-real inverse FFT along x -> psi
-    K_CORRECT,        // S8: u = u* - c grad psi, p += psi, FP64 divergence residual
+    K_CORRECT,        // S8: u = u* - c grad psi, p += psi (the FP64 residual runs at evp_sync)
     K_LEVELSET,       // S9: TVD-RK3 stage of level-set advection or re-distancing
     K_INTERFACE,      // S9: H, normals, curvature, CSF and buoyancy force
     K_IBM,            // discrete-forcing IBM of rigid particles (multi-direct iterations)

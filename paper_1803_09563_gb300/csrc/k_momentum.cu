@@ -12,9 +12,11 @@
 // top y-face stays zero.
 //
 // A 32 x 4 tile walks a chunk of z planes.  Shared memory holds planes k-1..k+1
-// (1-cell x-y halo) of u, v, w (4-slot ring, refilled by cp.async), of the summed
-// stress S = tau^k + tau^{k-1} (3-slot ring, built from raw B planes staged by
-// cp.async) and of p, plus the cell's momentum history.  A plane row is 40 wide
+// (1-cell x-y halo) of u, v, w and p, and of the summed stress S = tau^k + tau^{k-1},
+// plus the cell's momentum history; planes are staged two ahead by cp.async.  S is
+// either written by the stress kernel and staged like the velocity (5-slot rings,
+// one barrier per plane) or built here from the staged raw B^{k-1} and B^k planes
+// (3-slot ring, a build phase between two barriers).  A plane row is 40 wide
 // with the tile's interior at columns 4..35, so that when nx is a multiple of
 // 16 bytes' worth of elements every row is staged in 16-byte cp.async chunks
 // (x = i0-4 .. i0+35, wrapped periodically chunk by chunk); other grids stage
