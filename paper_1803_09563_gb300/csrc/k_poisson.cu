@@ -442,10 +442,20 @@ k_div_fftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
             }
         } else {
             const DivRows<T> r0 = div_rows(g, a, ok0 ? L0 : 0), r1 = div_rows(g, a, ok1 ? L1 : 0);
+            // the second line's v row below is the first line's v row (same plane, the
+            // next row): reuse its loads
+            const bool share = r1.vm == r0.v;
 #pragma unroll
             for (int j1 = 0; j1 < R1; ++j1) {
-                const int i = R2 * j1 + q;
-                x[j1] = mk<T>(ok0 ? div_value(g, a, r0, i) : T(0), ok1 ? div_value(g, a, r1, i) : T(0));
+                const int i = R2 * j1 + q, im = i > 0 ? i - 1 : n - 1;
+                const T v0 = __ldg(r0.v + i);
+                const T d0 = (__ldg(r0.u + i) - __ldg(r0.u + im)) * g.idx
+                             + (v0 - (r0.vm ? __ldg(r0.vm + i) : T(0))) * g.idy
+                             + (__ldg(r0.w + i) - __ldg(r0.wm + i)) * g.idz;
+                const T vm1 = share ? v0 : (r1.vm ? __ldg(r1.vm + i) : T(0));
+                const T d1 = (__ldg(r1.u + i) - __ldg(r1.u + im)) * g.idx + (__ldg(r1.v + i) - vm1) * g.idy
+                             + (__ldg(r1.w + i) - __ldg(r1.wm + i)) * g.idz;
+                x[j1] = mk<T>(ok0 ? d0 * a.rscale : T(0), ok1 ? d1 * a.rscale : T(0));
             }
         }
         dft_reg<T, R1, false>(x, tw, R2);
