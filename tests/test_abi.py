@@ -59,6 +59,29 @@ def test_state_bytes_validates_without_a_gpu(libpath):
     assert evp.evp_state_bytes(bad, evp.EVP_SARAMITO, p) == 0
 
 
+def test_state_bytes_count_the_summed_stress(libpath):
+    """An RK3 state with a stress model holds six more fields than a Newtonian one:
+    the summed stress tau^k + tau^{k-1} that the stress kernel hands to the momentum
+    kernel (N * 4 bytes is a multiple of the 256-byte arena alignment here)."""
+    from paper_1803_09563_gb300 import evp
+    evp.load(libpath)
+    g = evp.make_grid(64, 32, 32, 6.283185307179586, 2.0, 6.283185307179586, True)
+    p = evp.make_params(Re=100, Wi=1, beta=0.5, Bi=0.5, precision=evp.EVP_FP32)
+    N = 64 * 32 * 32
+    assert evp.evp_state_bytes(g, evp.EVP_SARAMITO, p) - evp.evp_state_bytes(g, evp.EVP_NEWTONIAN, p) == 6 * N * 4
+
+
+def test_batched_copies_reject_a_null_state(libpath):
+    """evp_set_fields / evp_get_fields check their arguments before any CUDA call."""
+    from paper_1803_09563_gb300 import evp
+    lib = evp.load(libpath)
+    ids = (ctypes.c_int * 1)(evp.EVP_U)
+    bufs = (ctypes.c_void_p * 1)(None)
+    assert lib.evp_set_fields(None, 1, ids, bufs, 0) == evp.EVP_ERR_ARG
+    assert lib.evp_get_fields(None, 1, ids, bufs, 0) == evp.EVP_ERR_ARG
+    assert b'null' in lib.evp_last_error()
+
+
 def test_binding_structs_match_the_header(tmp_path):
     """The ctypes mirrors of evp_grid and evp_params have the C layout: a small C
     program compiled against include/evp.h prints sizeof and every offsetof."""
