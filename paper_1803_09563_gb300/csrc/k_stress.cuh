@@ -173,14 +173,16 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     size_t voff[3][NVH];
     signed char vfac[3][NVH];
     int vsm[NVH];
-    // chunk staging (VEC true): ring copies (field, plane offset, shared offset),
-    // the velocity chunk, and the own-cell chunks (field, row, column)
-    unsigned rc_off[NRC];
+    // chunk staging (VEC true): the source of each copy in plane 0 (a plane's copy
+    // adds its plane offset) and its shared-memory offset, for the ring copies, the
+    // velocity chunk and the own-cell chunks of B and of the history
+    const T* rc_src[NRC];
     int rc_sm[NRC];
     int csm = -1;
-    size_t cvoff[3] = {0, 0, 0};
+    const T* cv_src[3] = {a.U, a.V, a.W};
     signed char cvfac[3] = {0, 0, 0};
-    unsigned oc_off[NOC], oc_hoff[NOC];
+    const T* oc_src[NOC];
+    const T* oc_hsrc[NOC];
     int oc_sm[NOC];
     bool oc_act[NOC];
     if (VEC) {
@@ -188,14 +190,14 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         for (int r = 0; r < NRC; ++r) {
             const int idx = tid + r * NT;
             rc_sm[r] = -1;
-            rc_off[r] = 0;
+            rc_src[r] = a.B[0];
             if (idx < 6 * RING) {
                 const int c = idx / RING, h = idx - c * RING;
                 int row, colq;
                 bring_pos<E>(h, row, colq);
                 int src;
                 row_rule(j0 + row - 3, 3, src);
-                rc_off[r] = (unsigned)((size_t)src * g.nx + pmod(i0 - XO + colq, g.nx));
+                rc_src[r] = a.B[c] + (size_t)src * g.nx + pmod(i0 - XO + colq, g.nx);
                 rc_sm[r] = c * BPL + row * BW + colq;
             }
         }
@@ -207,24 +209,25 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 cvfac[q] = (signed char)row_rule(j0 - 1 + r, q, src);
-                cvoff[q] = (size_t)src * g.nx + gx;
+                cv_src[q] += (size_t)src * g.nx + gx;
             }
         }
 #pragma unroll
         for (int r = 0; r < NOC; ++r) {
             const int idx = tid + r * NT;
             oc_sm[r] = -1;
-            oc_off[r] = oc_hoff[r] = 0;
+            oc_src[r] = a.B[0];
+            oc_hsrc[r] = a.RT[0];
             oc_act[r] = false;
             if (idx < 6 * OCH) {
                 const int c = idx / OCH, h = idx - c * OCH;
                 const int row = h / (TX / E), q0 = (h - row * (TX / E)) * E;
                 int src;
                 row_rule(j0 + row, 3, src);
-                oc_off[r] = (unsigned)((size_t)src * g.nx + pmod(i0 + q0, g.nx));
+                oc_src[r] = a.B[c] + (size_t)src * g.nx + pmod(i0 + q0, g.nx);
                 oc_sm[r] = c * NT + row * TX + q0;
                 oc_act[r] = j0 + row < g.ny && i0 + q0 < g.nx;
-                oc_hoff[r] = (unsigned)((size_t)(j0 + row) * g.nx + i0 + q0);
+                oc_hsrc[r] = a.RT[c] + (size_t)(j0 + row) * g.nx + i0 + q0;
             }
         }
     }
@@ -289,8 +292,8 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 T* dst = &sm.V[q][slot][csm];
-                if (cvfac[q] == 1) cp_async16(dst, vel[q] + pv + cvoff[q]);
-                else copy_scaled(dst, vel[q] + pv + cvoff[q], cvfac[q]);
+                if (cvfac[q] == 1) cp_async16(dst, cv_src[q] + pv);
+                else copy_scaled(dst, cv_src[q] + pv, cvfac[q]);
             }
             return;
         }
@@ -313,10 +316,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         if (VEC) {
 #pragma unroll
             for (int r = 0; r < NRC; ++r)
-                if (rc_sm[r] >= 0) {
-                    const int c = rc_sm[r] / BPL;
-                    cp_async16(&sm.B[buf][0][0] + rc_sm[r], a.B[c] + ph + rc_off[r]);
-                }
+                if (rc_sm[r] >= 0) cp_async16(&sm.B[buf][0][0] + rc_sm[r], rc_src[r] + ph);
             return;
         }
 #pragma unroll
@@ -332,10 +332,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
         if (VEC) {
 #pragma unroll
             for (int r = 0; r < NOC; ++r)
-                if (oc_sm[r] >= 0) {
-                    const int c = oc_sm[r] / NT;
-                    cp_async16(slot + oc_sm[r], a.B[c] + pb + oc_off[r]);
-                }
+                if (oc_sm[r] >= 0) cp_async16(slot + oc_sm[r], oc_src[r] + pb);
             return;
         }
 #pragma unroll
@@ -358,10 +355,8 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
             if (VEC) {
 #pragma unroll
                 for (int r = 0; r < NOC; ++r)
-                    if (oc_sm[r] >= 0 && oc_act[r]) {
-                        const int c = oc_sm[r] / NT;
-                        cp_async16(&sm.H[kk & 1][0][0] + oc_sm[r], a.RT[c] + (size_t)kk * plane + oc_hoff[r]);
-                    }
+                    if (oc_sm[r] >= 0 && oc_act[r])
+                        cp_async16(&sm.H[kk & 1][0][0] + oc_sm[r], oc_hsrc[r] + (size_t)kk * plane);
                 return;
             }
             if (!active) return;
