@@ -351,7 +351,7 @@ def run_gpu(args, rank, world, local_rank):
         "config": {"workload": w['name'], "grid": [w['nx'], w['ny'], w['nz']], "model": w['model'],
                    "Re": w['Re'], "Wi": w['Wi'], "Bi": w['Bi'], "beta": w['beta'], "dt": w['dt'],
                    "walls_y": True, "integrator": "RK3", "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (state 0.5 GB per replica vs 129 MB L2)"},
+                   "l2": "inputs larger than L2 (state 0.66 GB per replica vs 129 MB L2)"},
         "p50_ms": p50, "p99_ms": p99,
         "fp64_plain": {"value": value64, "unit": "Mcell-steps/s", "steps": n64, "ms_per_step": ms64 / n64},
         "fp32_vs_fp64_rel_err": {names[int(k)]: v for k, v in errs.items()},
