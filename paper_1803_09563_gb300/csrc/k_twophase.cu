@@ -34,12 +34,15 @@ __global__ void __launch_bounds__(256) k_ls_stage(const Geo<T> g, const LsArgs<T
     if (i >= g.nx || j >= g.ny) return;
     const size_t c0 = lin(g, i, j, k);
     const T* P = a.phis;
+    // the 7-point stencils along x, y, z: wrapped or clamped neighbour indices formed
+    // once, as 32-bit offsets (a grid has fewer than 2^31 cells)
+    const int row = (k * g.ny + j) * g.nx, col = j * g.nx + i, plane = g.nx * g.ny;
     T p[3][7];
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
-        p[0][m] = ld_c(g, P, i + m - 3, j, k);
-        p[1][m] = ld_c(g, P, i, j + m - 3, k);
-        p[2][m] = ld_c(g, P, i, j, k + m - 3);
+        p[0][m] = __ldg(P + (row + wrap(i + m - 3, g.nx)));
+        p[1][m] = __ldg(P + ((k * g.ny + ycen(g, j + m - 3)) * g.nx + i));
+        p[2][m] = __ldg(P + (wrap(k + m - 3, g.nz) * plane + col));
     }
     const T ih[3] = {g.idx, g.idy, g.idz};
     T rhs;
@@ -262,8 +265,10 @@ __global__ void __launch_bounds__(256) k_iface_b(const Geo<T> g, const IfaceArgs
 
 // tau component c at a centre from B^n with the mixture polymer viscosity mu_p(H)
 template <typename T, int MODEL>
-__device__ __forceinline__ T tau_mix(const Geo<T>& g, const MomAB2Args<T>& a, int c, int i, int j, int k) {
-    const size_t o = lin(g, wrap(i, g.nx), ycen(g, j), wrap(k, g.nz));
+__device__ __forceinline__ T tau_mix(const Geo<T>& g, const MomAB2Args<T>& a, int c, int i, int j, int k,
+                                     bool fast = false) {
+    // fast: (i, j, k) is inside the grid, so no wrap or ghost rule applies
+    const size_t o = fast ? ((size_t)k * g.ny + j) * g.nx + i : lin(g, wrap(i, g.nx), ycen(g, j), wrap(k, g.nz));
     const T H = __ldg(a.H + o);
     const T gm = (a.mu_p1 * H + a.mu_p2 * (T(1) - H)) * a.inv_lam;
     const bool diag = (c == 0 || c == 3 || c == 5);
@@ -280,7 +285,7 @@ __device__ __forceinline__ T tau_mix(const Geo<T>& g, const MomAB2Args<T>& a, in
 // average of tau_c over (0 or d1) x (0 or d2) around (i, j, k); offsets as in the RK3 kernel
 template <typename T, int MODEL>
 __device__ __forceinline__ T tau_e4(const Geo<T>& g, const MomAB2Args<T>& a, int c, int i, int j, int k, int di,
-                                    int dj, int dk) {
+                                    int dj, int dk, bool fast = false) {
     int a1i = 0, a1j = 0, a1k = 0, a2i = 0, a2j = 0, a2k = 0;
     if (di) {
         a1i = di;
@@ -289,23 +294,26 @@ __device__ __forceinline__ T tau_e4(const Geo<T>& g, const MomAB2Args<T>& a, int
         a1j = dj;
         a2k = dk;
     }
-    return T(0.25) * (tau_mix<T, MODEL>(g, a, c, i, j, k) + tau_mix<T, MODEL>(g, a, c, i + a2i, j + a2j, k + a2k)
-                      + tau_mix<T, MODEL>(g, a, c, i + a1i, j + a1j, k + a1k)
-                      + tau_mix<T, MODEL>(g, a, c, i + a1i + a2i, j + a1j + a2j, k + a1k + a2k));
+    return T(0.25) * (tau_mix<T, MODEL>(g, a, c, i, j, k, fast) + tau_mix<T, MODEL>(g, a, c, i + a2i, j + a2j, k + a2k, fast)
+                      + tau_mix<T, MODEL>(g, a, c, i + a1i, j + a1j, k + a1k, fast)
+                      + tau_mix<T, MODEL>(g, a, c, i + a1i + a2i, j + a1j + a2j, k + a1k + a2k, fast));
 }
 
-template <typename T, int MODEL>
-__global__ void __launch_bounds__(256) k_momentum_ab2(const Geo<T> g, const MomAB2Args<T> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
+// One cell of k_momentum_ab2.  FAST: every stencil point (offsets within one cell
+// in each direction) lies inside the grid, so the loads index directly; otherwise
+// they apply the periodic wraps and wall ghost rules.  Both read the same values.
+template <typename T, int MODEL, bool FAST>
+__device__ __forceinline__ void momentum_ab2_cell(const Geo<T>& g, const MomAB2Args<T>& a, int i, int j, int k) {
     const size_t c0 = lin(g, i, j, k);
-    auto u = [&](int di, int dj, int dk) { return ld_uw(g, a.U, i + di, j + dj, k + dk); };
-    auto v = [&](int di, int dj, int dk) { return ld_v(g, a.V, i + di, j + dj, k + dk); };
-    auto w = [&](int di, int dj, int dk) { return ld_uw(g, a.W, i + di, j + dj, k + dk); };
+    const size_t plane = (size_t)g.nx * g.ny;
+    auto at = [&](const T* F, int di, int dj, int dk) {
+        return __ldg(F + (c0 + (ptrdiff_t)di + (ptrdiff_t)dj * g.nx + (ptrdiff_t)dk * (ptrdiff_t)plane));
+    };
+    auto u = [&](int di, int dj, int dk) { return FAST ? at(a.U, di, dj, dk) : ld_uw(g, a.U, i + di, j + dj, k + dk); };
+    auto v = [&](int di, int dj, int dk) { return FAST ? at(a.V, di, dj, dk) : ld_v(g, a.V, i + di, j + dj, k + dk); };
+    auto w = [&](int di, int dj, int dk) { return FAST ? at(a.W, di, dj, dk) : ld_uw(g, a.W, i + di, j + dj, k + dk); };
     auto mu = [&](int di, int dj, int dk) {
-        const T H = ld_c(g, a.H, i + di, j + dj, k + dk);
+        const T H = FAST ? at(a.H, di, dj, dk) : ld_c(g, a.H, i + di, j + dj, k + dk);
         return a.mu_s1 * H + a.mu_s2 * (T(1) - H);
     };
     // viscosity averaged over the 4 centres (0 or d1) x (0 or d2), shifted by (si, sj, sk)
@@ -357,27 +365,27 @@ __global__ void __launch_bounds__(256) k_momentum_ab2(const Geo<T> g, const MomA
     // ---- div tau^n with mu_p(H)
     T dtx = T(0), dty = T(0), dtz = T(0);
     if (MODEL != EVP_NEWTONIAN) {
-        dtx = (tau_mix<T, MODEL>(g, a, 0, i + 1, j, k) - tau_mix<T, MODEL>(g, a, 0, i, j, k)) * ix
-              + (tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, 1, 0) - tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, -1, 0)) * iy
-              + (tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, 1) - tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, -1)) * iz;
-        dty = (tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, 1, 0) - tau_e4<T, MODEL>(g, a, 1, i, j, k, -1, 1, 0)) * ix
-              + (tau_mix<T, MODEL>(g, a, 3, i, j + 1, k) - tau_mix<T, MODEL>(g, a, 3, i, j, k)) * iy
-              + (tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, 1) - tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, -1)) * iz;
-        dtz = (tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, 1) - tau_e4<T, MODEL>(g, a, 2, i, j, k, -1, 0, 1)) * ix
-              + (tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, 1) - tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, -1, 1)) * iy
-              + (tau_mix<T, MODEL>(g, a, 5, i, j, k + 1) - tau_mix<T, MODEL>(g, a, 5, i, j, k)) * iz;
+        dtx = (tau_mix<T, MODEL>(g, a, 0, i + 1, j, k, FAST) - tau_mix<T, MODEL>(g, a, 0, i, j, k, FAST)) * ix
+              + (tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, 1, 0, FAST) - tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, -1, 0, FAST)) * iy
+              + (tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, 1, FAST) - tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, -1, FAST)) * iz;
+        dty = (tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, 1, 0, FAST) - tau_e4<T, MODEL>(g, a, 1, i, j, k, -1, 1, 0, FAST)) * ix
+              + (tau_mix<T, MODEL>(g, a, 3, i, j + 1, k, FAST) - tau_mix<T, MODEL>(g, a, 3, i, j, k, FAST)) * iy
+              + (tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, 1, FAST) - tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, -1, FAST)) * iz;
+        dtz = (tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, 1, FAST) - tau_e4<T, MODEL>(g, a, 2, i, j, k, -1, 0, 1, FAST)) * ix
+              + (tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, 1, FAST) - tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, -1, 1, FAST)) * iy
+              + (tau_mix<T, MODEL>(g, a, 5, i, j, k + 1, FAST) - tau_mix<T, MODEL>(g, a, 5, i, j, k, FAST)) * iz;
     }
 
     // ---- interface force: mean of the two centres next to each face
-    const T Fx = h * (__ldg(a.f[0] + c0) + ld_c(g, a.f[0], i + 1, j, k));
-    const T Fy = h * (__ldg(a.f[1] + c0) + ld_c(g, a.f[1], i, j + 1, k));
-    const T Fz = h * (__ldg(a.f[2] + c0) + ld_c(g, a.f[2], i, j, k + 1));
+    const T Fx = h * (__ldg(a.f[0] + c0) + (FAST ? at(a.f[0], 1, 0, 0) : ld_c(g, a.f[0], i + 1, j, k)));
+    const T Fy = h * (__ldg(a.f[1] + c0) + (FAST ? at(a.f[1], 0, 1, 0) : ld_c(g, a.f[1], i, j + 1, k)));
+    const T Fz = h * (__ldg(a.f[2] + c0) + (FAST ? at(a.f[2], 0, 0, 1) : ld_c(g, a.f[2], i, j, k + 1)));
 
     T Nx, Ny, Nz;
     if (a.rho_ratio > T(0)) {
         // density contrast: 1/rho on the stress terms, (1 - rho_bar/rho) g per unit mass
         auto rho = [&](int di, int dj, int dk) {
-            const T Hc = ld_c(g, a.H, i + di, j + dj, k + dk);
+            const T Hc = FAST ? at(a.H, di, dj, dk) : ld_c(g, a.H, i + di, j + dj, k + dk);
             return Hc + a.rho_ratio * (T(1) - Hc);
         };
         const T r0 = rho(0, 0, 0);
@@ -404,6 +412,17 @@ __global__ void __launch_bounds__(256) k_momentum_ab2(const Geo<T> g, const MomA
     a.NH[0][c0] = Nx;
     a.NH[1][c0] = Ny;
     a.NH[2][c0] = Nz;
+}
+
+template <typename T, int MODEL>
+__global__ void __launch_bounds__(256) k_momentum_ab2(const Geo<T> g, const MomAB2Args<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const bool inside = i >= 1 && i < g.nx - 1 && j >= 1 && j < g.ny - 1 && k >= 1 && k < g.nz - 1;
+    if (inside) momentum_ab2_cell<T, MODEL, true>(g, a, i, j, k);
+    else momentum_ab2_cell<T, MODEL, false>(g, a, i, j, k);
 }
 
 // density at a centre from the Heaviside: rho_1 = 1 (H = 1), rho_2 = rho_ratio
