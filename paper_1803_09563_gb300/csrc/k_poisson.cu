@@ -10,14 +10,18 @@
 //   k_div_fftx    divergence of u* (scaled) fused into the x real-to-complex FFT;
 //                 two real lines are packed into one complex FFT and split after.
 //   k_fft_col     forward complex FFT along z (columns of TK consecutive kx).
-//   k_fft_col     periodic y: forward FFT along y, modal division, inverse FFT,
-//                 all in shared memory (one pass).
+//   k_fft_col     periodic y: forward FFT along y, modal division, inverse FFT
+//                 (one pass).
 //   k_thomas      walls: FP64 Thomas sweep along y per (kx, kz), pivots from a table.
 //   k_fft_col     inverse FFT along z.
 //   k_ifftx       x complex-to-real inverse FFT -> psi.
-//   k_correct     u = u* - c grad psi, p += psi, FP64 max |div u|.
+//   k_correct     u = u* - c grad psi, p += psi (non-finite -> status).
+//   k_div_residual  FP64 max |div u| of a stored velocity (run by evp_sync).
+// For power-of-two lengths 16 .. 256 the x and column passes use the register-
+// resident two-pass kernels (k_div_fftx_r, k_fft_col_r, k_ifftx_r); other lengths
+// use the shared-memory kernels below.
 //
-// The FFT is a Stockham auto-sort transform in shared memory with radix-4, -3 and
+// The shared-memory FFT is a Stockham auto-sort transform with radix-4, -3 and
 // -2 stages (n = 2^a 3^b), twiddles read from a table exp(-2 pi i m/n).
 #include <cfloat>
 
