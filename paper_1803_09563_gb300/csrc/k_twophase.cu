@@ -53,13 +53,26 @@ __global__ void __launch_bounds__(256) k_ls_stage(const Geo<T> g, const LsArgs<T
         const T wc = T(0.5) * (ld_uw(g, a.W, i, j, k - 1) + __ldg(a.W + c0));
         const T vel[3] = {uc, vc, wc};
         T adv = T(0);
+        if constexpr (sizeof(T) == 4) {
+            // single precision: the x and y reconstructions in the two lanes of the
+            // packed f32x2 WENO5 (each lane picks its upwind side), z on its own
+            auto side = [&](int d, int m) { return vel[d] > T(0) ? p[d][m] : p[d][6 - m]; };
+            auto xy = [&](int m) { return make_float2(side(0, m), side(1, m)); };
+            const float2 sxy = upwind_term2(make_float2(fabs(uc) * ih[0], fabs(vc) * ih[1]), xy(0), xy(1), xy(2),
+                                            xy(3), xy(4), xy(5));
+            const T sz = fabs(wc) * ih[2];
+            const T az = wc > T(0) ? upwind_term(sz, p[2][0], p[2][1], p[2][2], p[2][3], p[2][4], p[2][5])
+                                   : upwind_term(sz, p[2][6], p[2][5], p[2][4], p[2][3], p[2][2], p[2][1]);
+            adv = (sxy.x + sxy.y) + az;
+        } else {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const T s = fabs(vel[d]) * ih[d];
-            if (vel[d] > T(0))
-                adv += upwind_term(s, p[d][0], p[d][1], p[d][2], p[d][3], p[d][4], p[d][5]);
-            else
-                adv += upwind_term(s, p[d][6], p[d][5], p[d][4], p[d][3], p[d][2], p[d][1]);
+            for (int d = 0; d < 3; ++d) {
+                const T s = fabs(vel[d]) * ih[d];
+                if (vel[d] > T(0))
+                    adv += upwind_term(s, p[d][0], p[d][1], p[d][2], p[d][3], p[d][4], p[d][5]);
+                else
+                    adv += upwind_term(s, p[d][6], p[d][5], p[d][4], p[d][3], p[d][2], p[d][1]);
+            }
         }
         rhs = -adv;
     } else {
