@@ -169,11 +169,12 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         int src;
         row_rule(j0 + vy - 1, 3, src);
         coff[r] = (size_t)src * g.nx + gx;        // also the soft particles' solid-fraction reads
-        if (VEC) continue;
+        if constexpr (!VEC) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            vfac[q][r] = (signed char)row_rule(j0 + vy - 1, q, src);
-            voff[q][r] = (size_t)src * g.nx + gx;
+            for (int q = 0; q < 3; ++q) {
+                vfac[q][r] = (signed char)row_rule(j0 + vy - 1, q, src);
+                voff[q][r] = (size_t)src * g.nx + gx;
+            }
         }
     }
     const T* vel[3] = {a.U, a.V, a.W};
@@ -198,7 +199,7 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     auto fetch_vel = [&](int kk) {
         const size_t pv = (size_t)wrap1(kk, g.nz) * plane;
         const int slot = vslot(kk);
-        if (VEC) {
+        if constexpr (VEC) {
             if (csm < 0) return;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -206,52 +207,52 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
                 if (cvfac[q] == 1) cp_async16(dst, vel[q] + pv + cvoff[q]);
                 else copy_scaled(dst, vel[q] + pv + cvoff[q], cvfac[q]);
             }
-            return;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int r = 0; r < NV; ++r) {
+                    if (psm[r] < 0) continue;
+                    T* dst = &sm.V[q][slot][psm[r]];
+                    if (vfac[q][r] == 1)
+                        cp_async(dst, vel[q] + pv + voff[q][r]);
+                    else
+                        *dst = vfac[q][r] == 0 ? T(0) : -__ldg(vel[q] + pv + voff[q][r]);
+                }
         }
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-#pragma unroll
-            for (int r = 0; r < NV; ++r) {
-                if (psm[r] < 0) continue;
-                T* dst = &sm.V[q][slot][psm[r]];
-                if (vfac[q][r] == 1)
-                    cp_async(dst, vel[q] + pv + voff[q][r]);
-                else
-                    *dst = vfac[q][r] == 0 ? T(0) : -__ldg(vel[q] + pv + voff[q][r]);
-            }
     };
     auto fetch_p = [&](int kk) {
         const size_t pp = (size_t)wrap1(kk, g.nz) * plane;
         const int slot = kk & 3;
-        if (VEC) {
+        if constexpr (VEC) {
             if (csm >= 0) cp_async16(&sm.P[slot][csm], a.P + pp + ccoff);
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int r = 0; r < NV; ++r)
-            if (psm[r] >= 0) cp_async(&sm.P[slot][psm[r]], a.P + pp + coff[r]);
+            for (int r = 0; r < NV; ++r)
+                if (psm[r] >= 0) cp_async(&sm.P[slot][psm[r]], a.P + pp + coff[r]);
+        }
     };
     auto fetch_braw = [&](int kk) {
         if constexpr (!SPRE) {
         if (!stress) return;
         const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
-        if (VEC) {
+        if constexpr (VEC) {
             if (csm < 0) return;
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 cp_async16(&sm.Braw[kk & 1][c][csm], a.Bo[c] + pb + ccoff);
                 cp_async16(&sm.Braw[kk & 1][6 + c][csm], a.Bn[c] + pb + ccoff);
             }
-            return;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+#pragma unroll
+                for (int r = 0; r < NV; ++r)
+                    if (psm[r] >= 0) {
+                        cp_async(&sm.Braw[kk & 1][c][psm[r]], a.Bo[c] + pb + coff[r]);
+                        cp_async(&sm.Braw[kk & 1][6 + c][psm[r]], a.Bn[c] + pb + coff[r]);
+                    }
         }
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-#pragma unroll
-            for (int r = 0; r < NV; ++r)
-                if (psm[r] >= 0) {
-                    cp_async(&sm.Braw[kk & 1][c][psm[r]], a.Bo[c] + pb + coff[r]);
-                    cp_async(&sm.Braw[kk & 1][6 + c][psm[r]], a.Bn[c] + pb + coff[r]);
-                }
         }
     };
     // precomputed summed stress plane kk into ring slot kk mod 5 (a centred field)
@@ -259,17 +260,17 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
         if constexpr (SPRE) {
             const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
             const int slot = vslot(kk);
-            if (VEC) {
+            if constexpr (VEC) {
                 if (csm < 0) return;
 #pragma unroll
                 for (int c = 0; c < 6; ++c) cp_async16(&sm.S[c][slot][csm], a.S[c] + pb + ccoff);
-                return;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c)
+#pragma unroll
+                    for (int r = 0; r < NV; ++r)
+                        if (psm[r] >= 0) cp_async(&sm.S[c][slot][psm[r]], a.S[c] + pb + coff[r]);
             }
-#pragma unroll
-            for (int c = 0; c < 6; ++c)
-#pragma unroll
-                for (int r = 0; r < NV; ++r)
-                    if (psm[r] >= 0) cp_async(&sm.S[c][slot][psm[r]], a.S[c] + pb + coff[r]);
         }
     };
     const T kgm = kconst<T>(mc.gmod, mc.f_gmod), kL2 = kconst<T>(mc.L2, mc.f_L2);
@@ -329,16 +330,16 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     const size_t hoff = (size_t)(j0 + hr) * g.nx + i0 + hq;
     auto fetch_hist = [&](int kk) {
         if (!a.read_hist || kk >= k1) return;
-        if (VEC) {
+        if constexpr (VEC) {
             if (hch) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
                     cp_async16(&sm.H[kk & 3][q][hr * TX + hq], a.NH[q] + (size_t)kk * plane + hoff);
             }
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) cp_async(&sm.H[kk & 3][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
+            for (int q = 0; q < 3; ++q) cp_async(&sm.H[kk & 3][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
+        }
     };
 
     // ---- prologue: velocity k0-1 .. k0+1, p k0 .. k0+1, S k0-1 .. k0+1, history k0

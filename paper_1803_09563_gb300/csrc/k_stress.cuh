@@ -287,7 +287,7 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     auto fetch_vel = [&](int kk) {
         const size_t pv = (size_t)wrap1(kk, g.nz) * plane;
         const int slot = kk & 3;
-        if (VEC) {
+        if constexpr (VEC) {
             if (csm < 0) return;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -295,48 +295,48 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
                 if (cvfac[q] == 1) cp_async16(dst, cv_src[q] + pv);
                 else copy_scaled(dst, cv_src[q] + pv, cvfac[q]);
             }
-            return;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int r = 0; r < NVH; ++r) {
+                    if (vsm[r] < 0) continue;
+                    T* dst = &sm.V[q][slot][vsm[r]];
+                    if (vfac[q][r] == 1)
+                        cp_async(dst, vel[q] + pv + voff[q][r]);
+                    else
+                        *dst = vfac[q][r] == 0 ? T(0) : -__ldg(vel[q] + pv + voff[q][r]);
+                }
         }
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-#pragma unroll
-            for (int r = 0; r < NVH; ++r) {
-                if (vsm[r] < 0) continue;
-                T* dst = &sm.V[q][slot][vsm[r]];
-                if (vfac[q][r] == 1)
-                    cp_async(dst, vel[q] + pv + voff[q][r]);
-                else
-                    *dst = vfac[q][r] == 0 ? T(0) : -__ldg(vel[q] + pv + voff[q][r]);
-            }
     };
     // halo ring of B plane kk into buffer kk & 1
     auto fetch_halo = [&](int kk) {
         const size_t ph = (size_t)wrap1(kk, g.nz) * plane;
         const int buf = kk & 1;
-        if (VEC) {
+        if constexpr (VEC) {
 #pragma unroll
             for (int r = 0; r < NRC; ++r)
                 if (rc_sm[r] >= 0) cp_async16(&sm.B[buf][0][0] + rc_sm[r], rc_src[r] + ph);
-            return;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+#pragma unroll
+                for (int r = 0; r < NBH; ++r)
+                    if (hsm[r] >= 0) cp_async(&sm.B[buf][c][hsm[r]], a.B[c] + ph + hoff[r]);
         }
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-#pragma unroll
-            for (int r = 0; r < NBH; ++r)
-                if (hsm[r] >= 0) cp_async(&sm.B[buf][c][hsm[r]], a.B[c] + ph + hoff[r]);
     };
     // plane kk of B for the tile's own columns into ring slot kk & 7 (kk >= -nz)
     auto fetch_next = [&](int kk) {
         const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
         T* slot = &sm.N[kk & 7][0][0];
-        if (VEC) {
+        if constexpr (VEC) {
 #pragma unroll
             for (int r = 0; r < NOC; ++r)
                 if (oc_sm[r] >= 0) cp_async16(slot + oc_sm[r], oc_src[r] + pb);
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) cp_async(slot + c * NT + tid, a.B[c] + pb + col);
+            for (int c = 0; c < 6; ++c) cp_async(slot + c * NT + tid, a.B[c] + pb + col);
+        }
     };
 
     // ---- prologue: the own-column ring (planes k0-3 .. k0+3), velocity planes
@@ -352,16 +352,16 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     auto fetch_hist = [&](int kk) {
         if constexpr (READ_H) {
             if (kk >= k1) return;
-            if (VEC) {
+            if constexpr (VEC) {
 #pragma unroll
                 for (int r = 0; r < NOC; ++r)
                     if (oc_sm[r] >= 0 && oc_act[r])
                         cp_async16(&sm.H[kk & 1][0][0] + oc_sm[r], oc_hsrc[r] + (size_t)kk * plane);
-                return;
-            }
-            if (!active) return;
+            } else {
+                if (!active) return;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) cp_async(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0);
+                for (int c = 0; c < 6; ++c) cp_async(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0);
+            }
         }
     };
     fetch_hist(k0);
