@@ -91,13 +91,19 @@ class State:
                      cp(self.phis_hist))
 
 
-def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3, gravity=0.0):
+def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False, ibm_iters=3, gravity=0.0,
+                predictor_only=False):
     """Substep k (0-based index into Eq. RK) of the RK3 scheme; returns a new State.
 
     ``solid`` (optional triple of face arrays alpha) switches on the volume-penalisation
     IBM for fixed obstacles (Sec. 3.3.2, Eqs. Vol, forceAdded): the predicted
     velocity becomes u** = (1 - alpha) u* before the projection, alpha being the
-    solid volume fraction of the control volume around each velocity node."""
+    solid volume fraction of the control volume around each velocity node.
+
+    ``predictor_only`` stops before the projection and returns (u*, B^k): the
+    predicted face velocities (with every option above applied) and the updated
+    conformation.  Both are local in the fields of level k-1, unlike the
+    projection, which is a global solve."""
     alpha, zeta, xi = RK3_ALPHA[k], RK3_ZETA[k], RK3_XI[k]
     has_stress = prm.model != 'newtonian'
     soft = s.phis is not None
@@ -163,6 +169,8 @@ def rk3_substep(s, k, dt, g, prm, force=None, solid=None, implicit_viscous=False
               if q.get('rho', 0.0) > 0.0 else None for q in s.particles]
     if g.walls:
         star[1][:, g.ny - 1, :] = 0.0
+    if predictor_only:
+        return star, Bn
     # projection, Eqs. NS-num2 and NS-num3
     U, V, W, psi = project(star[0], star[1], star[2], g, 2.0 * alpha * dt)
     parts = None

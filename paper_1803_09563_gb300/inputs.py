@@ -202,6 +202,24 @@ def random_conformation(geo, seed, amp=0.2):
     return B
 
 
+def spd_conformation(geo, seed, amp=0.5, scale=1.0):
+    """A smooth symmetric positive-definite B field with large deviations, for tests:
+    B = scale * M M with M = I + amp * S (S as in ``random_conformation``), components
+    in the order xx, xy, xz, yy, yz, zz.  B is positive definite wherever M is
+    nonsingular; ``scale`` multiplies its deviatoric part (and its determinant by
+    scale^3)."""
+    S = random_conformation(geo, seed, amp=1.0)
+    m = [S[c] - (1.0 if c in (0, 3, 5) else 0.0) for c in range(6)]
+    m = [(1.0 if c in (0, 3, 5) else 0.0) + amp * m[c] for c in range(6)]
+    m0, m1, m2, m3, m4, m5 = m
+    return [scale * (m0 * m0 + m1 * m1 + m2 * m2),
+            scale * (m0 * m1 + m1 * m3 + m2 * m4),
+            scale * (m0 * m2 + m1 * m4 + m2 * m5),
+            scale * (m1 * m1 + m3 * m3 + m4 * m4),
+            scale * (m1 * m2 + m3 * m4 + m4 * m5),
+            scale * (m2 * m2 + m4 * m4 + m5 * m5)]
+
+
 def solid_fractions(geo, inside, samples=4):
     """Solid volume fraction of the control volume around every u, v and w node
     (the cell shifted by half a cell along that component's axis), by sub-sampling

@@ -1,0 +1,150 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch configuration
+that the benchmark times: FP32 storage and the kernels of one RK3 substep exactly as
+the step graph captures them (the graph replays these substep launches; graph and
+direct launches are compared bit for bit in test_gpu_parity).
+
+The oracle takes about half a minute per substep at 256x128x128, so the local parts
+of the substep are checked on sampled outputs (windows, see oracle_windows; the
+method is pinned by test_oracle_windows):
+  * B^k (Eq. rk3tau) at every cell of each window's interior;
+  * u* (Eqs. NS-num1, rk3), recovered from the GPU's projected velocity and pressure
+    as u* = u^k + 2 alpha dt grad(p^k - p^{k-1}) (Eqs. NS-num2/3 with
+    p^k = p^{k-1} + psi), at every face of each window's interior.
+The projection itself is a global solve; it is checked through a property that holds
+at any size: the discrete divergence of u^k, in FP64 on the host from the stored
+FP32 fields, is at the FP32 rounding level of the velocity.  Together with the u*
+check, u^k - u* is then a discrete gradient that removes the divergence of u*.
+
+Inputs: the benchmark's velocity recipe for each workload, a random pressure and a
+large-deformation SPD conformation B = s (I + a S)^2 in place of B = I, so that the
+advection, the upper-convected terms and (Saramito) both sides of the yield
+surface are exercised from the first substep.  Tolerance: 1e-5 relative per field
+(FP32 path, per step), as in the small-size tests.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_09563_gb300 import inputs
+from oracle_windows import predictor
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+def rd(a):
+    return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def run_first_substep(evp, grid, model, params, U, V, W, p, B, dt):
+    sim = evp.Simulation(grid, model, params)
+    evp.evp_set_graph(sim.handle, True)
+    sim.set_state(U, V, W, p, B)
+    sim.substep(dt, 0)
+    code, bits, maxdiv = sim.sync()
+    out = [sim.get(f).astype(np.float64) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P)]
+    Bn = [sim.get(evp.EVP_BXX + c).astype(np.float64) for c in range(6)]
+    sim.close()
+    return out, Bn, maxdiv
+
+
+def check_windows(g, prm, dt, force, state0, out, Bn, starts_list, widths, tol=1e-5):
+    """Compare B^1 and the recovered u* with the oracle on each window; returns the
+    window B^0 of the compared cells (for coverage checks)."""
+    U, V, W, p, B = state0
+    U1, V1, W1, p1 = out
+    coef = 2.0 * oracle.RK3_ALPHA[0] * dt
+    gp = oracle.grad_p(p1 - p, g)
+    star_gpu = (U1 + coef * gp[0], V1 + coef * gp[1], W1 + coef * gp[2])
+    seen = []
+    from oracle_windows import cut
+    for starts in starts_list:
+        idx, star_o, Bn_o, B0_w = predictor(g, prm, dt, 0, U, V, W, p, B, starts, widths, force)
+        for q in range(3):
+            got = cut(star_gpu[q], starts, widths)[idx]
+            ref = star_o[q][idx]
+            err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+            assert err < tol, ('u*', q, starts, err)
+        for c in range(6):
+            got = cut(Bn[c], starts, widths)[idx]
+            ref = Bn_o[c][idx]
+            err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+            assert err < tol, ('B', c, starts, err)
+        seen.append([b[idx] for b in B0_w])
+    return seen
+
+
+def divergence_bound(g, U, V, W):
+    """FP32 rounding of a face velocity moves the discrete divergence of a cell by at
+    most eps32 |u|_max (1/dx + 1/dy + 1/dz)."""
+    umax = max(np.abs(U).max(), np.abs(V).max(), np.abs(W).max())
+    return EPS32 * umax * (1.0 / g.dx + 1.0 / g.dy + 1.0 / g.dz)
+
+
+def test_saramito_channel_256x128x128_first_substep(evp):
+    """Saramito EVP channel, 256x128x128, walls at y = +-1, Re 100, Wi 1, Bi 0.5,
+    beta 0.5, the Poiseuille body force 2/Re, dt 2e-3: the benchmark workload."""
+    nx, ny, nz = 256, 128, 128
+    lx, ly, lz = 4 * np.pi, 2.0, 2 * np.pi
+    Re, Wi, Bi, beta, dt = 100.0, 1.0, 0.5, 0.5, 2e-3
+    geo = inputs.geometry(nx, ny, nz, lx, ly, lz, True)
+    U, V, W = inputs.poiseuille(geo)
+    u2, v2, w2 = inputs.scale_max(*inputs.random_solenoidal(geo, 1, 8), 1e-2)
+    U, V, W = rd(U + u2), rd(v2), rd(w2)
+    V[:, -1] = 0.0
+    B = [rd(b) for b in inputs.spd_conformation(geo, 7, 0.6, scale=3.0)]
+    p = rd(np.random.default_rng(9).standard_normal((nz, ny, nx)) * 0.05)
+    grid = evp.make_grid(nx, ny, nz, lx, ly, lz, True)
+    params = evp.make_params(Re=Re, Wi=Wi, beta=beta, Bi=Bi, dpdx=2.0 / Re, precision=evp.EVP_FP32)
+    out, Bn, maxdiv = run_first_substep(evp, grid, 'saramito', params, U, V, W, p, B, dt)
+
+    g = oracle.Grid(nx, ny, nz, lx, ly, lz, True)
+    prm = oracle.Params.from_groups('saramito', Re, Wi, beta, Bi=Bi)
+    force = (2.0 / Re, 0.0, 0.0)
+    # windows across the periodic seams in x and in z, and one inside
+    starts = [(244, 0, 50), (100, 0, 116), (17, 0, 3)]
+    seen = check_windows(g, prm, dt, force, (U, V, W, p, B), out, Bn, starts, (24, None, 24))
+    # both sides of the yield surface were compared (F = 0 and F > 0 of Table 1)
+    F = np.concatenate([np.ravel(oracle.closure(b0, prm)[0]) for b0 in seen])
+    assert (F == 0.0).sum() > 1000 and (F > 0.0).sum() > 1000
+    # projection: the FP64 divergence of the stored FP32 velocity, and the GPU's own
+    # FP64 residual of the same fields
+    div = oracle.divergence(out[0], out[1], out[2], g)
+    bound = divergence_bound(g, *out[:3])
+    assert np.abs(div).max() < bound
+    assert maxdiv < bound
+    assert abs(np.abs(div).max() - maxdiv) <= 1e-3 * bound + 1e-9 * maxdiv
+
+
+def test_fene_p_turbulence_256cubed_first_substep(evp):
+    """FENE-P forced turbulence, 256^3 periodic box 2 pi, Re 200, Wi 5, beta 0.9,
+    L^2 900, ABC forcing A = 1 at k = 2, dt 1e-3: the benchmark workload."""
+    n, L = 256, 2 * np.pi
+    Re, Wi, beta, L2, dt = 200.0, 5.0, 0.9, 900.0, 1e-3
+    A, kf = 1.0, 2.0
+    geo = inputs.geometry(n, n, n, L, L, L)
+    U, V, W = (rd(a) for a in inputs.scale_rms(*inputs.random_solenoidal(geo, 2, 16, spectrum='k-5/3',
+                                                                          periodic_fft=True), 1.0))
+    B = [rd(b) for b in inputs.spd_conformation(geo, 8, 0.5)]
+    p = rd(np.random.default_rng(10).standard_normal((n, n, n)) * 0.1)
+    grid = evp.make_grid(n, n, n, L, L, L)
+    params = evp.make_params(Re=Re, Wi=Wi, beta=beta, L2=L2, abc_amp=A, abc_k=kf, precision=evp.EVP_FP32)
+    out, Bn, maxdiv = run_first_substep(evp, grid, 'fene_p', params, U, V, W, p, B, dt)
+
+    g = oracle.Grid(n, n, n, L, L, L)
+    prm = oracle.Params.from_groups('fene_p', Re, Wi, beta, L2=L2)
+    # the ABC force at the faces from its definition (each component is constant
+    # along its own direction, so the centre coordinates are the face coordinates)
+    xc, yc, zc = g.xc(), g.yc(), g.zc()
+    shp = (n, n, n)
+    force = (np.broadcast_to(A * (np.sin(kf * zc) + np.cos(kf * yc)), shp),
+             np.broadcast_to(A * (np.sin(kf * xc) + np.cos(kf * zc)), shp),
+             np.broadcast_to(A * (np.sin(kf * yc) + np.cos(kf * xc)), shp))
+    starts = [(244, 250, 3), (100, 17, 240), (0, 128, 60)]
+    check_windows(g, prm, dt, force, (U, V, W, p, B), out, Bn, starts, (24, 24, 24))
+    div = oracle.divergence(out[0], out[1], out[2], g)
+    bound = divergence_bound(g, *out[:3])
+    assert np.abs(div).max() < bound
+    assert maxdiv < bound
