@@ -92,11 +92,10 @@ def split_projection(star, p_n, p_nm1, rho, dt, g, rho0):
     return out[0], out[1], out[2], p_new
 
 
-def ab2_step(s, phi, dt, g, tp, nstep):
-    """One AB2 step; ``nstep`` counts completed steps (0 for the first).
-    ``s.RT_hist`` / ``s.N_hist`` carry RT^{n-1} / RU^{n-1}.  Returns (State, phi)."""
+def ab2_levelset(phi, s, dt, g, tp, nstep):
+    """Step 1: phi^{n+1} from phi^n and u^n (TVD-RK3 + WENO5 advection, re-distancing
+    every ``reinit_every`` steps, the mass-preserving shift of Reading 17)."""
     eps = tp.eps_cells * g.dx
-    # 1. level set (Reading 17: the drop volume of the first step is kept)
     if tp.mass_iters > 0 and nstep == 0:
         tp.v0 = ls.drop_volume(phi, g, eps)
     phi = ls.advect(phi, s.U, s.V, s.W, g, dt)
@@ -104,6 +103,16 @@ def ab2_step(s, phi, dt, g, tp, nstep):
         phi = ls.reinitialise(phi, g, tp.reinit_iters)
     if tp.mass_iters > 0:
         phi = ls.mass_correct(phi, g, eps, tp.v0, tp.mass_iters)
+    return phi
+
+
+def ab2_predictor(s, phi, dt, g, tp, nstep, b_mean=None):
+    """Steps 2-4 with ``phi`` = phi^{n+1}.  Returns (u*, B^{n+1}, RT^n, RU^n, rho),
+    rho being the centre density with a density contrast and None without one.
+    Everything here is local in (u^n, B^n, phi^{n+1}) and the histories, except the
+    domain mean that makes the Boussinesq buoyancy mean-free (``b_mean``, see
+    ``levelset.interface_force_centres``)."""
+    eps = tp.eps_cells * g.dx
     # 2. mixture properties at n+1
     H = ls.heaviside(phi, eps)
     mu_s, mu_p = tp.mixture(H)
@@ -117,8 +126,9 @@ def ab2_step(s, phi, dt, g, tp, nstep):
     Vv = viscous(s.U, s.V, s.W, g, mu_s)
     dtau = div_tau(tau_from_B(s.B, prm), g)
     dens = tp.rho_ratio is not None
-    fc = ls.interface_force_centres(phi, g, tp.sigma, eps, 0.0 if dens else tp.drho_g)
+    fc = ls.interface_force_centres(phi, g, tp.sigma, eps, 0.0 if dens else tp.drho_g, b_mean)
     F = ls.centres_to_faces(fc, g)
+    rho = None
     if dens:
         rho = H + tp.rho_ratio * (1.0 - H)
         rf = face_mean(rho, g)
@@ -131,8 +141,16 @@ def ab2_step(s, phi, dt, g, tp, nstep):
     star = [vel[d] + dt * (w1 * RU[d] + (w0 * s.N_hist[d] if w0 else 0.0)) for d in range(3)]
     if g.walls:
         star[1][:, g.ny - 1, :] = 0.0
+    return star, Bn, RT, RU, rho
+
+
+def ab2_step(s, phi, dt, g, tp, nstep):
+    """One AB2 step; ``nstep`` counts completed steps (0 for the first).
+    ``s.RT_hist`` / ``s.N_hist`` carry RT^{n-1} / RU^{n-1}.  Returns (State, phi)."""
+    phi = ab2_levelset(phi, s, dt, g, tp, nstep)
+    star, Bn, RT, RU, rho = ab2_predictor(s, phi, dt, g, tp, nstep)
     # 5. projection with dt
-    if dens:
+    if rho is not None:
         p_nm1 = s.p if s.psi is None or nstep == 0 else s.psi
         U, V, W, p_new = split_projection(star, s.p, p_nm1, rho, dt, g, min(1.0, tp.rho_ratio))
         # psi carries p^{n} to the next step as its p^{n-1}

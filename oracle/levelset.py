@@ -106,9 +106,11 @@ def curvature(n, g):
              + (at(nz, g, 'c', k=1) - at(nz, g, 'c', k=-1)) / (2.0 * g.dz))
 
 
-def interface_force_centres(phi, g, sigma, eps, drho_g):
+def interface_force_centres(phi, g, sigma, eps, drho_g, b_mean=None):
     """CSF force sigma kappa delta(phi) n (Eq. fLS) plus the mean-free Boussinesq
-    buoyancy (1 - H) drho_g e_y, at cell centres."""
+    buoyancy (1 - H) drho_g e_y, at cell centres.  ``b_mean`` (default: the mean over
+    ``phi``'s cells) is the domain mean of (1 - H) drho_g that makes it mean-free;
+    a caller passing a window of a larger field passes the larger field's mean."""
     n = normals(phi, g)
     kap = curvature(n, g)
     dl = delta(phi, eps)
@@ -116,7 +118,7 @@ def interface_force_centres(phi, g, sigma, eps, drho_g):
     fy = sigma * kap * dl * n[1]
     fz = sigma * kap * dl * n[2]
     b = (1.0 - heaviside(phi, eps)) * drho_g
-    fy = fy + b - b.mean()
+    fy = fy + b - (b.mean() if b_mean is None else b_mean)
     return fx, fy, fz
 
 

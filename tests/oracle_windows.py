@@ -63,3 +63,28 @@ def predictor(g, prm, dt, k, U, V, W, p, B, starts, widths, force=None):
     fw = None if force is None else tuple(c(f) for f in force)
     star, Bn = oracle.rk3_substep(st, k, dt, gw, prm, fw, predictor_only=True)
     return interior(widths, st.U.shape), star, Bn, st.B
+
+
+def ab2_predictor(g, tp, dt, U, V, W, p, B, phi_next, starts, widths):
+    """Oracle (u*, B^{n+1}) of the first AB2 step (steps 2-4 of ``oracle.ab2``: no
+    history) on the window at ``starts``, from the full-size level set phi^{n+1}
+    (the level set's own advection reaches 9 cells, and a mass shift is global, so
+    phi^{n+1} is computed on the full fields and only cut here).  The mixture
+    properties, the interface force and the AB2 predictor reach 3 cells of
+    phi^{n+1} and the same distances as the RK3 predictor in (u, p, B); the one
+    global quantity, the mean that makes the buoyancy mean-free, is taken from the
+    full phi^{n+1}.  Returns
+    (compared index, u* triple, B^{n+1} list, B^n list, phi^{n+1}), all on the
+    window."""
+    from oracle.ab2 import ab2_predictor as predict
+    from oracle import levelset as ls
+    # the buoyancy is made mean-free with the mean over the whole domain
+    b_mean = float((1.0 - ls.heaviside(phi_next, tp.eps_cells * g.dx)).mean()) * tp.drho_g
+    gw = window_grid(g, widths)
+    c = lambda a: cut(a, starts, widths)
+    st = oracle.State.rest(gw, c(U), c(V), c(W))
+    st.p = c(p)
+    st.B = [c(b) for b in B]
+    phw = c(phi_next)
+    star, Bn, _, _, _ = predict(st, phw, dt, gw, tp, 0, b_mean)
+    return interior(widths, st.U.shape), star, Bn, st.B, phw

@@ -10,8 +10,10 @@ method is pinned by test_oracle_windows):
   * u* (Eqs. NS-num1, rk3), recovered from the GPU's projected velocity and pressure
     as u* = u^k + 2 alpha dt grad(p^k - p^{k-1}) (Eqs. NS-num2/3 with
     p^k = p^{k-1} + psi), at every face of each window's interior.
-The projection itself is a global solve; it is checked through a property that holds
-at any size: the discrete divergence of u^k, in FP64 on the host from the stored
+For the two-phase drop (AB2) the level set phi^{n+1} is compared at every cell with
+the oracle's level-set update of the full fields, and B^{n+1} and u* on windows as
+above.  The projection itself is a global solve; it is checked through a property
+that holds at any size: the discrete divergence of u^k, in FP64 on the host from the stored
 FP32 fields, is at the FP32 rounding level of the velocity.  Together with the u*
 check, u^k - u* is then a discrete gradient that removes the divergence of u*.
 
@@ -27,7 +29,7 @@ import pytest
 
 import oracle
 from paper_1803_09563_gb300 import inputs
-from oracle_windows import predictor
+from oracle_windows import cut, predictor
 
 pytestmark = pytest.mark.gpu
 
@@ -59,7 +61,7 @@ def check_windows(g, prm, dt, force, state0, out, Bn, starts_list, widths, tol=1
     gp = oracle.grad_p(p1 - p, g)
     star_gpu = (U1 + coef * gp[0], V1 + coef * gp[1], W1 + coef * gp[2])
     seen = []
-    from oracle_windows import cut
+    worst = {'u*': 0.0, 'B': 0.0}
     for starts in starts_list:
         idx, star_o, Bn_o, B0_w = predictor(g, prm, dt, 0, U, V, W, p, B, starts, widths, force)
         for q in range(3):
@@ -67,12 +69,15 @@ def check_windows(g, prm, dt, force, state0, out, Bn, starts_list, widths, tol=1
             ref = star_o[q][idx]
             err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
             assert err < tol, ('u*', q, starts, err)
+            worst['u*'] = max(worst['u*'], err)
         for c in range(6):
             got = cut(Bn[c], starts, widths)[idx]
             ref = Bn_o[c][idx]
             err = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
             assert err < tol, ('B', c, starts, err)
+            worst['B'] = max(worst['B'], err)
         seen.append([b[idx] for b in B0_w])
+    print('max relative error over the windows:', worst)
     return seen
 
 
@@ -113,6 +118,7 @@ def test_saramito_channel_256x128x128_first_substep(evp):
     # FP64 residual of the same fields
     div = oracle.divergence(out[0], out[1], out[2], g)
     bound = divergence_bound(g, *out[:3])
+    print('max|div u|:', np.abs(div).max(), 'GPU FP64 residual:', maxdiv, 'bound:', bound)
     assert np.abs(div).max() < bound
     assert maxdiv < bound
     assert abs(np.abs(div).max() - maxdiv) <= 1e-3 * bound + 1e-9 * maxdiv
@@ -146,5 +152,90 @@ def test_fene_p_turbulence_256cubed_first_substep(evp):
     check_windows(g, prm, dt, force, (U, V, W, p, B), out, Bn, starts, (24, 24, 24))
     div = oracle.divergence(out[0], out[1], out[2], g)
     bound = divergence_bound(g, *out[:3])
+    print('max|div u|:', np.abs(div).max(), 'GPU FP64 residual:', maxdiv, 'bound:', bound)
+    assert np.abs(div).max() < bound
+    assert maxdiv < bound
+
+
+def test_evp_drop_128x256x128_first_step(evp):
+    """Two-phase buoyancy-driven drop in a Saramito fluid, 128x256x128 periodic box
+    4 x 8 x 4, FP32, AB2 with the level set: drop of radius 0.5 at (2, 2, 2), Heaviside
+    over 1.5 cells, Re 10, Wi 1, Bi 0.2 (tau_y = Bi), beta 0.5, viscosity ratio 1,
+    surface tension 0.1 and drho g = 1 (Bond 10), re-distancing every 10 steps,
+    dt 1e-3: the benchmark workload, one step from a moving, stressed state.
+
+    * phi^{n+1} (Sec. 3.2.1: TVD-RK3 + WENO5 advection) at every cell, against the
+      oracle's level-set update on the full fields;
+    * B^{n+1} (Eq. ab2tau) and u* (Eq. ab2 with the CSF force and buoyancy),
+      recovered as u^{n+1} + dt grad p^{n+1} (Eq. projection), on windows across the
+      drop's interface and across the periodic seams;
+    * the divergence of u^{n+1} at the FP32 rounding level."""
+    from oracle.ab2 import TwoPhase, ab2_levelset
+    from oracle import levelset as ls
+    from oracle_windows import ab2_predictor
+    nx, ny, nz = 128, 256, 128
+    lx, ly, lz = 4.0, 8.0, 4.0
+    dt = 1e-3
+    geo = inputs.geometry(nx, ny, nz, lx, ly, lz)
+    phi = rd(inputs.sphere_distance(geo, (2.0, 2.0, 2.0), 0.5))
+    U, V, W = (rd(a) for a in inputs.scale_max(*inputs.random_solenoidal(geo, 3, 4), 0.5))
+    B = [rd(b) for b in inputs.spd_conformation(geo, 11, 0.6, scale=12.0)]
+    params = evp.make_params(Re=10.0, Wi=1.0, beta=0.5, Bi=0.2, bi_def=1, precision=evp.EVP_FP32,
+                             integrator=evp.EVP_AB2, mu_ratio=1.0, ls_eps_cells=1.5, sigma=0.1, drho_g=1.0,
+                             reinit_every=10, reinit_iters=2)
+    sim = evp.Simulation(evp.make_grid(nx, ny, nz, lx, ly, lz), 'saramito', params)
+    sim.set_state(U, V, W, None, B)
+    sim.set(evp.EVP_PHI, phi)
+    sim.step(dt)
+    code, bits, maxdiv = sim.sync()
+    U1, V1, W1, p1, phi1 = (sim.get(f).astype(np.float64)
+                            for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P, evp.EVP_PHI))
+    Bn = [sim.get(evp.EVP_BXX + c).astype(np.float64) for c in range(6)]
+    sim.close()
+
+    g = oracle.Grid(nx, ny, nz, lx, ly, lz)
+    tp = TwoPhase('saramito', Re=10.0, Wi=1.0, beta=0.5, tau_y=0.2, mu_ratio=1.0, eps_cells=1.5, sigma=0.1,
+                  drho_g=1.0, reinit_every=10, reinit_iters=2)
+    st = oracle.State.rest(g, U, V, W)
+    st.B = B
+    phi1_o = ab2_levelset(phi, st, dt, g, tp, 0)
+    err_phi = np.abs(phi1 - phi1_o).max() / np.abs(phi1_o).max()
+    assert err_phi < 1e-5
+    worst = {'phi': err_phi, 'u*': 0.0, 'B': 0.0}
+
+    gp = oracle.grad_p(p1, g)
+    star_gpu = (U1 + dt * gp[0], V1 + dt * gp[1], W1 + dt * gp[2])
+    widths = (24, 24, 24)
+    band = yielded = unyielded = 0
+    eps = tp.eps_cells * g.dx
+    # across the drop's lower interface (y = 1.5), its side (x = 2.5), and the seams
+    for starts in ((52, 36, 52), (68, 52, 52), (120, 250, 120)):
+        idx, star_o, Bn_o, B0_w, phw = ab2_predictor(g, tp, dt, U, V, W, np.zeros_like(U), B, phi1_o, starts,
+                                                     widths)
+        for q in range(3):
+            got = cut(star_gpu[q], starts, widths)[idx]
+            ref = star_o[q][idx]
+            err = np.abs(got - ref).max() / np.abs(ref).max()
+            assert err < 1e-5, ('u*', q, starts, err)
+            worst['u*'] = max(worst['u*'], err)
+        for c in range(6):
+            got = cut(Bn[c], starts, widths)[idx]
+            ref = Bn_o[c][idx]
+            err = np.abs(got - ref).max() / np.abs(ref).max()
+            assert err < 1e-5, ('B', c, starts, err)
+            worst['B'] = max(worst['B'], err)
+        H = ls.heaviside(phw[idx], eps)
+        band += ((H > 0.01) & (H < 0.99)).sum()
+        mu_s, mu_p = tp.mixture(H)
+        F = oracle.closure([b[idx] for b in B0_w],
+                           oracle.Params('saramito', mu_s=mu_s, mu_p=mu_p, lam=tp.Wi, tau_y=tp.tau_y))[0]
+        yielded += ((F > 0.0) & (H > 0.99)).sum()
+        unyielded += ((F == 0.0) & (H > 0.99)).sum()
+    # the interface band and both sides of the yield surface were compared
+    assert band > 100 and yielded > 50 and unyielded > 50
+    div = oracle.divergence(U1, V1, W1, g)
+    bound = divergence_bound(g, U1, V1, W1)
+    print('max relative error:', worst, 'band/yielded/unyielded cells:', band, yielded, unyielded)
+    print('max|div u|:', np.abs(div).max(), 'GPU FP64 residual:', maxdiv, 'bound:', bound)
     assert np.abs(div).max() < bound
     assert maxdiv < bound

@@ -66,3 +66,36 @@ def test_predictor_recovered_from_projected_fields(walls):
     for q, vel in enumerate((s1.U, s1.V, s1.W)):
         assert np.abs(vel + coef * gp[q] - star[q]).max() < 1e-12 * np.abs(star[q]).max() + 1e-15
     assert np.abs(oracle.divergence(s1.U, s1.V, s1.W, g)).max() < 1e-11
+
+
+def test_ab2_window_interior_equals_full_predictor():
+    """The same for the two-phase AB2 predictor (mixture properties from H(phi^{n+1}),
+    CSF force and buoyancy, stress and momentum), phi^{n+1} taken from the full
+    fields."""
+    from oracle.ab2 import TwoPhase, ab2_levelset, ab2_predictor as full_predictor
+    from oracle_windows import ab2_predictor
+    nx, ny, nz = 40, 48, 36
+    geo = inputs.geometry(nx, ny, nz, 1.25, 1.5, 1.125)
+    g = oracle.Grid(nx, ny, nz, 1.25, 1.5, 1.125)
+    phi = inputs.sphere_distance(geo, (0.6, 0.7, 0.55), 0.3)
+    U, V, W = inputs.scale_max(*inputs.random_solenoidal(geo, 4, 3), 0.5)
+    B = inputs.spd_conformation(geo, 6, 0.6, scale=5.0)
+    p = np.random.default_rng(8).standard_normal((nz, ny, nx)) * 0.1
+    tp = TwoPhase('saramito', Re=10.0, Wi=1.0, beta=0.5, tau_y=0.2, mu_ratio=0.5, sigma=0.1, drho_g=1.0)
+    st = oracle.State.rest(g, U, V, W)
+    st.p = p
+    st.B = B
+    dt = 1e-3
+    phi1 = ab2_levelset(phi, st, dt, g, tp, 0)
+    star, Bn, _, _, _ = full_predictor(st, phi1, dt, g, tp, 0)
+    widths = (24, 24, 24)
+    band = 0
+    # one window across the drop's interface (x = 0.9), one across the periodic seams
+    for starts in ((18, 10, 6), (30, 40, 25)):
+        idx, star_w, Bn_w, _, phw = ab2_predictor(g, tp, dt, U, V, W, p, B, phi1, starts, widths)
+        band += (np.abs(phw[idx]) < 1.5 * g.dx).sum()
+        for full, win in zip(list(star) + list(Bn), list(star_w) + list(Bn_w)):
+            ref = cut(full, starts, widths)
+            assert np.array_equal(win[idx], ref[idx])
+            assert not np.array_equal(win[:, :, :1], ref[:, :, :1])
+    assert band > 0
