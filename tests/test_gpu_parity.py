@@ -774,3 +774,53 @@ def test_fene_p_trace_limit_is_reported(evp):
     sim.step(1e-4)
     code, bits, _ = sim.sync(raise_on_error=False)
     assert code == evp.EVP_ERR_UNPHYSICAL and bits & evp.EVP_BIT_TRACE_LIMIT
+
+
+# the longest transform in each role (512: x pass, periodic y solve, z pass, and a
+# wall-normal y of 512 for the Thomas solve), with the other axes at their minimum,
+# and the smallest grid the library accepts (nx = nz = 8, ny = 4 between walls)
+EXTREME_SHAPES = [(512, 8, 8, False), (8, 512, 8, False), (8, 8, 512, False), (16, 512, 8, True), (8, 4, 8, True)]
+
+
+@pytest.mark.parametrize("shape", EXTREME_SHAPES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_poisson_solve_extreme_lengths(evp, shape, prec):
+    """FP64 1e-12; FP32 2e-6 for transforms of up to 256 points (8 radix-2 stages,
+    as above) scaled by the stage count log2(n) / 8, the growth of the FFT's rounding
+    error with its length."""
+    import torch
+    nx, ny, nz, walls = shape
+    sim, st, g, prm = setup_case(evp, shape, 'oldroyd_b', {}, prec)
+    r = np.random.default_rng(14).standard_normal((nz, ny, nx))
+    r -= r.mean()
+    if prec == 1:
+        r = r.astype(np.float32).astype(np.float64)
+    rd = torch.tensor(r, dtype=torch.float32 if prec else torch.float64, device='cuda')
+    psi = torch.empty_like(rd)
+    evp.evp_poisson_solve(sim.handle, rd, psi)
+    sim.sync()
+    ref = oracle.solve_poisson(r, g)
+    got = psi.cpu().numpy().astype(np.float64)
+    if not walls:
+        got, ref = got - got.mean(), ref - ref.mean()
+    tol = 1e-12 if prec == 0 else 2e-6 * max(1.0, np.log2(max(nx, nz, 8 if walls else ny)) / 8.0)
+    print('poisson', shape, prec, rel(got, ref))
+    assert rel(got, ref) < tol, (shape, prec, rel(got, ref))
+
+
+@pytest.mark.parametrize("shape", EXTREME_SHAPES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rk3_step_extreme_lengths(evp, shape, prec):
+    """One Saramito RK3 step on the extreme grids: FP64 1e-10, FP32 1e-5."""
+    sim, st, g, prm = setup_case(evp, shape, 'saramito', {'Bi': 0.4}, prec)
+    dt = 2e-3
+    sim.step(dt)
+    st = oracle.rk3_step(st, dt, g, prm)
+    sim.sync()
+    worst = 0.0
+    for q, (got, ref) in enumerate(zip(fields(sim, evp), oracle_fields(st))):
+        if prec == 1 and q == 3:
+            continue    # FP32 pressure: see test_rk3_step_fp32
+        worst = max(worst, rel(got, ref))
+        assert rel(got, ref) < (1e-10 if prec == 0 else 1e-5), (q, rel(got, ref))
+    print('rk3 step', shape, prec, worst)
