@@ -48,6 +48,12 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                                                      first substep under gravity)
   soft particles ................................... pinned (all-solid and all-fluid limits,
                                                      transport order)
+
+The substep predictors (``rk3_substep(..., predictor_only=True)``,
+``ab2.ab2_predictor``) return u* and the updated conformation before the global
+projection; the full-size GPU tests evaluate them on windows of the full fields
+(``tests/oracle_windows.py``; the window interior equals the full-field result bit
+for bit, ``tests/test_oracle_windows.py``).
 """
 
 from .grid import Grid, at  # noqa: F401

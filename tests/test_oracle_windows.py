@@ -99,3 +99,23 @@ def test_ab2_window_interior_equals_full_predictor():
             assert np.array_equal(win[idx], ref[idx])
             assert not np.array_equal(win[:, :, :1], ref[:, :, :1])
     assert band > 0
+
+
+def test_spd_conformation_is_symmetric_positive_definite():
+    """The large-deformation input B = s (I + a S)^2 is positive definite (its
+    eigenvalues are s times the squares of those of I + a S) and its deviator
+    scales with s."""
+    geo = inputs.geometry(16, 12, 10, 2 * np.pi, 2.0, 2 * np.pi, True)
+    B = inputs.spd_conformation(geo, 7, 0.6, scale=3.0)
+    M = np.stack([np.stack([B[0], B[1], B[2]], -1), np.stack([B[1], B[3], B[4]], -1),
+                  np.stack([B[2], B[4], B[5]], -1)], -2)
+    assert np.linalg.eigvalsh(M).min() > 0.0
+    B1 = inputs.spd_conformation(geo, 7, 0.6, scale=1.0)
+    for c in range(6):
+        assert np.allclose(B[c], 3.0 * B1[c], rtol=1e-15, atol=0.0)
+    S = inputs.random_conformation(geo, 7, amp=1.0)
+    m = [(1.0 if c in (0, 3, 5) else 0.0) + 0.6 * (S[c] - (1.0 if c in (0, 3, 5) else 0.0)) for c in range(6)]
+    Mm = np.stack([np.stack([m[0], m[1], m[2]], -1), np.stack([m[1], m[3], m[4]], -1),
+                   np.stack([m[2], m[4], m[5]], -1)], -2)
+    sq = Mm @ Mm
+    assert np.allclose(M, 3.0 * sq, rtol=1e-14, atol=1e-14)
