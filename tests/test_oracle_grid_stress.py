@@ -152,3 +152,113 @@ def test_wall_ghost_rules():
     np.testing.assert_array_equal(oracle.at(a, g, 'u', j=1)[:, -1], -a[:, -1])
     np.testing.assert_array_equal(oracle.at(a, g, 'v', j=-1)[:, 0], 0.0)
     np.testing.assert_array_equal(oracle.at(a, g, 'c', j=3)[:, -1], a[:, -1])
+
+
+def solenoidal_case(walls, seed=5, shape=(12, 10, 14)):
+    nx, ny, nz = shape
+    geo = inputs.geometry(nx, ny, nz, 2 * np.pi, 2.0 if walls else 2 * np.pi, 2 * np.pi, walls)
+    g = oracle.Grid(nx, ny, nz, geo['lx'], geo['ly'], geo['lz'], walls)
+    U, V, W = inputs.random_solenoidal(geo, seed, 3)
+    if walls:
+        U = U + inputs.poiseuille(geo)[0]
+    return geo, g, U, V, W
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_advection_conserves_kinetic_energy_of_solenoidal_fields(walls):
+    """The divergence form of div(uu) on the staggered grid with central averages
+    (Sec. 3) is energy-conserving when the discrete continuity equation holds:
+    sum over the faces of u.div(uu) = 0 for a discretely divergence-free field
+    (periodic, or with no-penetration walls).  Every term of the three face
+    components enters this sum, so a wrong neighbour, sign or spacing in any of
+    them leaves a residual of order one."""
+    geo, g, U, V, W = solenoidal_case(walls)
+    assert np.abs(oracle.divergence(U, V, W, g)).max() < 1e-12
+    A = oracle.advection(U, V, W, g)
+    terms = [U * A[0], V * A[1], W * A[2]]
+    total = sum(t.sum() for t in terms)
+    scale = sum(np.abs(t).sum() for t in terms)
+    assert abs(total) < 1e-13 * scale
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_div_tau_is_minus_the_adjoint_of_the_velocity_gradient(walls):
+    """Summation by parts on the staggered grid: for any symmetric centre stress tau,
+    sum over the faces of u.div(tau) = -sum over the cells of L:tau, with div(tau)
+    from the edge averages of Reading 5 and L from the centre velocity gradient of
+    Reading 5 (periodic, or no-slip walls with their ghost rules).  It ties the two
+    discretisations to each other: a wrong sign, neighbour or spacing in either
+    breaks it (a transposed L does not, tau being symmetric; that case has its own
+    pin above)."""
+    geo, g, U, V, W = solenoidal_case(walls)
+    B = inputs.random_conformation(geo, 3, amp=0.5)
+    tau = [b - (1.0 if c in (0, 3, 5) else 0.0) for c, b in enumerate(B)]
+    f = oracle.div_tau(tau, g)
+    lhs = (U * f[0]).sum() + (V * f[1]).sum() + (W * f[2]).sum()
+    L = oracle.velocity_gradient(U, V, W, g)
+    comp = {(0, 0): 0, (0, 1): 1, (0, 2): 2, (1, 1): 3, (1, 2): 4, (2, 2): 5}
+    rhs = -sum((L[i][j] * tau[comp[(min(i, j), max(i, j))]]).sum() for i in range(3) for j in range(3))
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_variable_viscosity_form_is_symmetric_and_dissipative(walls):
+    """div[mu(grad u + grad u^T)] in divergence form with centre normal stresses and
+    edge shear stresses (Sec. 3.2.1 mixture viscosity): the bilinear form
+    sum a.V(b) is symmetric and sum a.V(a) < 0 for any positive mu field, periodic
+    or with no-slip walls (wall faces of v held at zero)."""
+    g = box(12, 10, 14, walls)
+    rng = np.random.default_rng(1)
+    a = [rng.standard_normal(g.shape) for _ in range(3)]
+    b = [rng.standard_normal(g.shape) for _ in range(3)]
+    if walls:
+        a[1][:, -1] = 0.0
+        b[1][:, -1] = 0.0
+    mu = 0.3 + 0.2 * rng.random(g.shape)
+    Va = oracle.momentum.viscous(*a, g, mu)
+    Vb = oracle.momentum.viscous(*b, g, mu)
+    ab = sum((a[q] * Vb[q]).sum() for q in range(3))
+    ba = sum((b[q] * Va[q]).sum() for q in range(3))
+    assert abs(ab - ba) < 1e-13 * abs(ab)
+    assert sum((a[q] * Va[q]).sum() for q in range(3)) < 0.0
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_variable_viscosity_one_dimensional_fluxes(q, d):
+    """Brute force on a periodic box: velocity component q and the viscosity vary
+    along direction d only.  The form reduces to a 1-D flux difference, written
+    out here cell by cell: for d != q the shear flux mu_e (f[n+1] - f[n]) / h with
+    the edge viscosity mu_e = (m[n] + m[n+1]) / 2; for d == q the normal flux
+    2 m[n+1] (f[n+1] - f[n]) / h with the viscosity of the centre between the two
+    faces.  The other two components vanish."""
+    shape = [6, 8, 10]                       # x, y, z
+    g = box(*shape)
+    h = (g.dx, g.dy, g.dz)[d]
+    n = shape[d]
+    rng = np.random.default_rng(10 * q + d)
+    f = rng.standard_normal(n)
+    m = 0.5 + rng.random(n)
+
+    def along(v):
+        s = [1, 1, 1]
+        s[d] = n
+        return np.broadcast_to(np.asarray(v).reshape(s[::-1]), g.shape).copy()
+
+    vel = [g.zeros(), g.zeros(), g.zeros()]
+    vel[q] = along(f)
+    out = oracle.momentum.viscous(*vel, g, along(m))
+    exp = np.zeros(n)
+    for i in range(n):
+        ip, im = (i + 1) % n, (i - 1) % n
+        if d != q:
+            up = 0.5 * (m[i] + m[ip]) * (f[ip] - f[i]) / h
+            lo = 0.5 * (m[im] + m[i]) * (f[i] - f[im]) / h
+        else:
+            up = 2.0 * m[ip] * (f[ip] - f[i]) / h
+            lo = 2.0 * m[i] * (f[i] - f[im]) / h
+        exp[i] = (up - lo) / h
+    np.testing.assert_allclose(out[q], along(exp), rtol=0, atol=1e-12 * np.abs(exp).max())
+    for r in range(3):
+        if r != q:
+            assert np.abs(out[r]).max() < 1e-12 * np.abs(exp).max()
