@@ -262,3 +262,41 @@ def test_variable_viscosity_one_dimensional_fluxes(q, d):
     for r in range(3):
         if r != q:
             assert np.abs(out[r]).max() < 1e-12 * np.abs(exp).max()
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_grad_p_is_minus_the_adjoint_of_the_divergence(walls):
+    """Summation by parts between the face gradient of a centre field and the centre
+    divergence of a face field (Eqs. NS-num2/3): sum u.grad p = -sum p div u for any
+    p and any u (wall faces of v at zero; the pressure's zero-gradient wall ghost
+    makes its wall-face gradient vanish)."""
+    g = box(12, 10, 14, walls)
+    rng = np.random.default_rng(2)
+    u = [rng.standard_normal(g.shape) for _ in range(3)]
+    if walls:
+        u[1][:, -1] = 0.0
+    p = rng.standard_normal(g.shape)
+    gp = oracle.grad_p(p, g)
+    lhs = sum((u[q] * gp[q]).sum() for q in range(3))
+    rhs = -(p * oracle.divergence(*u, g)).sum()
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_laplacian_is_symmetric_and_negative(walls):
+    """The uniform-viscosity Laplacian of the three face components (with the no-slip
+    ghosts of u, w and the zero wall face of v) is a symmetric, negative definite
+    operator: sum a.lap(b) = sum b.lap(a), sum a.lap(a) < 0."""
+    g = box(12, 10, 14, walls)
+    rng = np.random.default_rng(3)
+    a = [rng.standard_normal(g.shape) for _ in range(3)]
+    b = [rng.standard_normal(g.shape) for _ in range(3)]
+    if walls:
+        a[1][:, -1] = 0.0
+        b[1][:, -1] = 0.0
+    La = oracle.momentum.viscous(*a, g, 0.3)
+    Lb = oracle.momentum.viscous(*b, g, 0.3)
+    ab = sum((a[q] * Lb[q]).sum() for q in range(3))
+    ba = sum((b[q] * La[q]).sum() for q in range(3))
+    assert abs(ab - ba) < 1e-13 * abs(ab)
+    assert sum((a[q] * La[q]).sum() for q in range(3)) < 0.0
