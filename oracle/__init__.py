@@ -27,13 +27,21 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                                                      stencil, trigger thresholds, wall
                                                      row, conservation)
   momentum RHS (Eq. NS-num1) ....................... pinned (Taylor-Green decay order,
-                                                     steady Oldroyd-B Poiseuille)
+                                                     steady Oldroyd-B Poiseuille, kinetic
+                                                     energy conserved by the advection
+                                                     form, summation by parts of div tau
+                                                     with the velocity gradient and of
+                                                     grad p with the divergence, symmetric
+                                                     negative viscous forms, 1-D
+                                                     variable-viscosity fluxes)
   Poisson solve + projection (Eqs. NS-num2/3) ...... pinned (sine modes, sparse direct
                                                      solve, divergence <= 1e-12)
   RK3 constants (Eq. RK) ........................... pinned (3rd-order convergence on
                                                      a linear ODE closed form)
   level set (Eqs. ls-adv, normal, curv, reinit) .... pinned (translation, sphere
-                                                     curvature, Heaviside volume)
+                                                     curvature, Heaviside volume, Laplace
+                                                     pressure jump of the CSF force,
+                                                     mean-free buoyancy)
   AB2 (Eqs. ab2tau, ab2) ........................... pinned (2nd-order convergence)
   density-contrast split projection ................ pinned (div-free, uniform-density limit,
                                                      fixed point = sparse variable solve)

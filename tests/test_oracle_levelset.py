@@ -265,3 +265,36 @@ def test_mass_correction_keeps_the_drop_volume_over_ab2_steps():
             st, phi = ab2_step(st, phi, 2e-2, g, tp, it)
         drift[iters] = abs(ls.drop_volume(phi, g, eps) - v0) / v0
     assert drift[4] < 1e-12 and drift[0] > 1e-6, drift
+
+
+def test_csf_force_of_a_drop_at_rest_gives_the_laplace_jump():
+    """Laplace's law for the CSF force sigma kappa delta(phi) n (Eq. fLS): the
+    pressure that balances it (lap p = div F, the projection of F) is uniform inside
+    and outside a spherical drop and higher inside by 2 sigma / R.  This fixes the
+    sign of kappa and n and the magnitude of delta together."""
+    n, L, R, sigma = 32, 2.0, 0.5, 0.1
+    g = box(n, L)
+    phi = sphere(g, (1.0, 1.0, 1.0), R)
+    eps = 1.5 * g.dx
+    F = ls.centres_to_faces(ls.interface_force_centres(phi, g, sigma, eps, 0.0), g)
+    p = oracle.solve_poisson(oracle.divergence(*F, g), g)
+    inside, outside = phi < -3 * eps, phi > 3 * eps
+    jump = p[inside].mean() - p[outside].mean()
+    assert abs(jump / (2.0 * sigma / R) - 1.0) < 0.01
+    assert p[inside].std() < 1e-3 * jump and p[outside].std() < 1e-3 * jump
+
+
+def test_buoyancy_is_mean_free_and_lifts_the_drop():
+    """Boussinesq buoyancy (1 - H) drho_g e_y minus its domain mean: zero net force,
+    x and z parts zero, and a difference of exactly drho_g between the drop
+    (phi < -eps, 1 - H = 1) and the outer fluid (phi > eps)."""
+    g = box(24)
+    phi = sphere(g, (1.0, 0.8, 1.0), 0.45)
+    eps = 1.5 * g.dx
+    fx, fy, fz = ls.interface_force_centres(phi, g, 0.0, eps, 0.7)
+    assert np.abs(fx).max() == 0.0 and np.abs(fz).max() == 0.0
+    assert abs(fy.sum()) < 1e-12 * np.abs(fy).sum()
+    inside, outside = phi < -eps, phi > eps
+    assert np.allclose(fy[inside], fy[inside][0]) and np.allclose(fy[outside], fy[outside][0])
+    assert abs(fy[inside][0] - fy[outside][0] - 0.7) < 1e-14
+    assert fy[inside][0] > 0.0
