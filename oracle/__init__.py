@@ -22,7 +22,8 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                                                      convergence order)
   closures (Table 1), stress RHS (Eq. SRM2) ........ pinned (start-up / oscillatory
                                                      shear closed forms, Saramito yield
-                                                     time, steady yielded shear)
+                                                     time, steady yielded shear, axis
+                                                     swaps and mirrors of the cube)
   local artificial diffusion (Sec. 3.1) ............ pinned (sine-mode eigenvalues of the
                                                      stencil, trigger thresholds, wall
                                                      row, conservation)

@@ -300,3 +300,89 @@ def test_laplacian_is_symmetric_and_negative(walls):
     ba = sum((b[q] * La[q]).sum() for q in range(3))
     assert abs(ab - ba) < 1e-13 * abs(ab)
     assert sum((a[q] * La[q]).sum() for q in range(3)) < 0.0
+
+
+# ---- discrete symmetries of the periodic staggered cube: an axis swap or a mirror
+# maps the grid onto itself, so every operator must commute with it.  Array axis
+# of direction d (x 0, y 1, z 2) in [z][y][x] storage:
+_AX = (2, 1, 0)
+_COMP = {(0, 0): 0, (0, 1): 1, (0, 2): 2, (1, 1): 3, (1, 2): 4, (2, 2): 5}
+
+
+def _comp(i, j):
+    return _COMP[(min(i, j), max(i, j))]
+
+
+def _swap(a, b):
+    """(vector map, tensor map) of the swap of directions a and b."""
+    s = [0, 1, 2]
+    s[a], s[b] = b, a
+    sw = lambda f: np.swapaxes(f, _AX[a], _AX[b]).copy()
+    vec = lambda v: [sw(v[s[q]]) for q in range(3)]
+    ten = lambda t: [sw(t[_comp(s[i], s[j])]) for (i, j) in _COMP]
+    return vec, ten, sw
+
+
+def _mirror(a):
+    """(vector map, tensor map, centre map) of the reflection x_a -> -x_a: centre
+    values and the other components reverse along a; the a-face component also
+    changes sign and moves from face i+1/2 to face n-1-i-1/2; tensor components
+    with one index a change sign."""
+    ax = _AX[a]
+    rc = lambda f: np.flip(f, ax).copy()
+    rf = lambda f: -np.roll(np.flip(f, ax), -1, axis=ax)
+    vec = lambda v: [rf(v[q]) if q == a else rc(v[q]) for q in range(3)]
+    ten = lambda t: [(-1.0 if (i == a) != (j == a) else 1.0) * rc(t[_comp(i, j)]) for (i, j) in _COMP]
+    return vec, ten, rc
+
+
+def _sym_case():
+    n, L = 12, 2 * np.pi
+    geo = inputs.geometry(n, n, n, L, L, L)
+    g = oracle.Grid(n, n, n, L, L, L)
+    vel = list(inputs.scale_max(*inputs.random_solenoidal(geo, 5, 3), 1.0))
+    B = inputs.spd_conformation(geo, 3, 0.5, scale=2.0)
+    mu = 0.3 + 0.2 * np.random.default_rng(4).random(g.shape)
+    return g, vel, B, mu
+
+
+def _maps():
+    out = []
+    for a, b in ((0, 1), (1, 2), (0, 2)):
+        out.append(('swap%d%d' % (a, b),) + _swap(a, b))
+    for a in range(3):
+        out.append(('mirror%d' % a,) + _mirror(a))
+    return out
+
+
+@pytest.mark.parametrize("name,vec,ten,cen", _maps(), ids=[m[0] for m in _maps()])
+@pytest.mark.parametrize("model,extra", [('saramito', {'Bi': 0.4}), ('fene_p', {'L2': 30.0}), ('oldroyd_b', {})])
+def test_stress_rhs_commutes_with_the_cube_symmetries(name, vec, ten, cen, model, extra):
+    """Stress RHS (Eq. rt: WENO5 advection, upper-convected terms, Table 1 closure):
+    RT(S u, S B) = S RT(u, B) for the axis swaps and mirrors S of the cube.  A typo
+    confined to one direction's stencil, or to the upwind side of a negative
+    velocity, breaks it."""
+    g, vel, B, _ = _sym_case()
+    prm = oracle.Params.from_groups(model, Re=2.0, Wi=0.8, beta=0.4, **extra)
+    R = oracle.stress_rhs(*vel, B, g, prm)
+    Rs = oracle.stress_rhs(*vec(vel), ten(B), g, prm)
+    scale = max(np.abs(r).max() for r in R)
+    for got, ref in zip(Rs, ten(R)):
+        assert np.abs(got - ref).max() < 1e-13 * scale
+
+
+@pytest.mark.parametrize("name,vec,ten,cen", _maps(), ids=[m[0] for m in _maps()])
+def test_momentum_operators_commute_with_the_cube_symmetries(name, vec, ten, cen):
+    """Advection, the uniform and the variable-viscosity viscous forms, and div tau:
+    each maps S-transformed inputs to the S-transformed result."""
+    g, vel, B, mu = _sym_case()
+    tau = [b - (1.0 if c in (0, 3, 5) else 0.0) for c, b in enumerate(B)]
+    pairs = [
+        (oracle.momentum_rhs_n(*vel, g, 0.3), oracle.momentum_rhs_n(*vec(vel), g, 0.3)),
+        (oracle.momentum.viscous(*vel, g, mu), oracle.momentum.viscous(*vec(vel), g, cen(mu))),
+        (oracle.div_tau(tau, g), oracle.div_tau(ten(tau), g)),
+    ]
+    for ref, got in pairs:
+        scale = max(np.abs(r).max() for r in ref)
+        for a, b in zip(got, vec(list(ref))):
+            assert np.abs(a - b).max() < 1e-13 * scale
