@@ -298,3 +298,54 @@ def test_buoyancy_is_mean_free_and_lifts_the_drop():
     assert np.allclose(fy[inside], fy[inside][0]) and np.allclose(fy[outside], fy[outside][0])
     assert abs(fy[inside][0] - fy[outside][0] - 0.7) < 1e-14
     assert fy[inside][0] > 0.0
+
+
+def _cube_maps():
+    """Axis swaps and mirrors of a periodic cube as maps of (face vector, centre
+    scalar, centre vector) fields, [z][y][x] storage."""
+    AX = (2, 1, 0)
+    maps = []
+    for a, b in ((0, 1), (1, 2), (0, 2)):
+        s = [0, 1, 2]
+        s[a], s[b] = b, a
+        sw = (lambda a_, b_: (lambda f: np.swapaxes(f, AX[a_], AX[b_]).copy()))(a, b)
+        vec = (lambda sw_, s_: (lambda v: [sw_(v[s_[q]]) for q in range(3)]))(sw, s)
+        maps.append(('swap%d%d' % (a, b), vec, sw, vec))
+    for a in range(3):
+        ax = AX[a]
+        rc = (lambda ax_: (lambda f: np.flip(f, ax_).copy()))(ax)
+        rf = (lambda ax_: (lambda f: -np.roll(np.flip(f, ax_), -1, axis=ax_)))(ax)
+        fvec = (lambda a_, rc_, rf_: (lambda v: [rf_(v[q]) if q == a_ else rc_(v[q]) for q in range(3)]))(a, rc, rf)
+        cvec = (lambda a_, rc_: (lambda v: [-rc_(v[q]) if q == a_ else rc_(v[q]) for q in range(3)]))(a, rc)
+        maps.append(('mirror%d' % a, fvec, rc, cvec))
+    return maps
+
+
+@pytest.mark.parametrize("name,fvec,cen,cvec", _cube_maps(), ids=[m[0] for m in _cube_maps()])
+def test_level_set_operators_commute_with_the_cube_symmetries(name, fvec, cen, cvec):
+    """Level-set advection (WENO5, Eq. ls-adv), the re-distancing right-hand side
+    (Godunov upwinding, Eq. reinit), the normals and curvature and the CSF force
+    (Eqs. normal, curv, fLS): each maps transformed inputs to the transformed
+    result.  The drop is off-centre, the velocity random, so no symmetry of the
+    data hides a one-direction typo."""
+    n, L = 16, 2.0
+    g = box(n, L)
+    geo = inputs.geometry(n, n, n, L, L, L)
+    phi = sphere(g, (0.9, 1.1, 1.05), 0.45) * (1.0 + 0.2 * np.sin(np.pi * g.xc()) * np.cos(np.pi * g.zc()))
+    vel = list(inputs.scale_max(*inputs.random_solenoidal(geo, 7, 3), 1.0))
+    eps = 1.5 * g.dx
+    ref = ls.advection_rhs(phi, *vel, g)
+    got = ls.advection_rhs(cen(phi), *fvec(vel), g)
+    assert np.abs(got - cen(ref)).max() < 1e-13 * np.abs(ref).max()
+    phi0 = sphere(g, (0.9, 1.1, 1.05), 0.45)
+    ref = ls.reinit_rhs(phi, phi0, g)
+    got = ls.reinit_rhs(cen(phi), cen(phi0), g)
+    assert np.abs(got - cen(ref)).max() < 1e-13 * np.abs(ref).max()
+    ref = ls.curvature(ls.normals(phi, g), g)
+    got = ls.curvature(ls.normals(cen(phi), g), g)
+    assert np.abs(got - cen(ref)).max() < 1e-12 * np.abs(ref).max()
+    ref = ls.interface_force_centres(phi, g, 0.1, eps, 0.0)
+    got = ls.interface_force_centres(cen(phi), g, 0.1, eps, 0.0)
+    scale = max(np.abs(r).max() for r in ref)
+    for a, b in zip(got, cvec(list(ref))):
+        assert np.abs(a - b).max() < 1e-12 * scale
