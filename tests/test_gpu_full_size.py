@@ -239,3 +239,35 @@ def test_evp_drop_128x256x128_first_step(evp):
     print('max|div u|:', np.abs(div).max(), 'GPU FP64 residual:', maxdiv, 'bound:', bound)
     assert np.abs(div).max() < bound
     assert maxdiv < bound
+
+
+def test_saramito_channel_graph_replay_equals_direct_launches(evp):
+    """The benchmark's own launch path at its own size: the channel workload exactly
+    as the benchmark sets it up (velocity recipe, B = I, a torch stream), two RK3
+    steps replayed from the captured step graphs (one per B buffer parity) against
+    the same steps launched directly, all fields bit for bit.  The windows above
+    check the direct launches against the oracle."""
+    import torch
+    nx, ny, nz = 256, 128, 128
+    lx, ly, lz = 4 * np.pi, 2.0, 2 * np.pi
+    Re, dt = 100.0, 2e-3
+    geo = inputs.geometry(nx, ny, nz, lx, ly, lz, True)
+    U, V, W = inputs.poiseuille(geo)
+    u2, v2, w2 = inputs.scale_max(*inputs.random_solenoidal(geo, 1, 8), 1e-2)
+    U, V, W = U + u2, v2, w2
+    names = [evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P] + [evp.EVP_BXX + c for c in range(6)]
+    out = []
+    for graph in (True, False):
+        stream = torch.cuda.Stream()
+        sim = evp.Simulation(evp.make_grid(nx, ny, nz, lx, ly, lz, True), 'saramito',
+                             evp.make_params(Re=Re, Wi=1.0, beta=0.5, Bi=0.5, dpdx=2.0 / Re,
+                                             precision=evp.EVP_FP32), stream=stream.cuda_stream)
+        sim.set_state(U, V, W)
+        evp.evp_set_graph(sim.handle, graph)
+        for _ in range(3):
+            sim.step(dt)
+        sim.sync()
+        out.append([sim.get(f) for f in names])
+        sim.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
