@@ -137,3 +137,35 @@ def test_solid_fractions_of_a_block():
         vol = a.sum() * (2.0 / 16) ** 3
         assert abs(vol - 0.8 * 0.6 * 1.0) < 0.02
         assert set(np.unique(a[(a > 0) & (a < 1)]).round(6)) <= set((np.arange(1, 512) / 512).round(6))
+
+
+@pytest.mark.parametrize("walls,m,dt", [(False, 2, 0.01), (False, 3, 0.002), (True, 1, 5e-4), (True, 3, 1e-4)])
+def test_shear_mode_decays_by_the_rk3_stability_polynomial(walls, m, dt):
+    """A shear mode u = f(y) e_x is an exact Navier-Stokes solution (no advection,
+    no pressure) whose discrete form decays as u' = -nu lambda u, lambda the
+    eigenvalue of the discrete Laplacian: (2 - 2 cos(m dy)) / dy^2 for sin(m y)
+    (periodic) and (2 - 2 cos(m pi / ny)) / dy^2 for sin(m pi (j + 1/2) / ny) between
+    no-slip walls.  One step of the three-substep scheme of Eq. RK (viscous term
+    explicit with the weights zeta, xi, Reading 3) multiplies it by the stability
+    polynomial of a three-stage third-order method, 1 + z + z^2/2 + z^3/6 with
+    z = -nu lambda dt, to rounding; a wrong RK3 weight changes the polynomial."""
+    nx, ny, nz = 8, 16, 6
+    ly = 2.0 if walls else 2 * np.pi
+    g = oracle.Grid(nx, ny, nz, 2 * np.pi, ly, 2 * np.pi, walls)
+    if walls:
+        prof = np.sin(m * np.pi * (np.arange(ny) + 0.5) / ny)
+        lam = (2.0 - 2.0 * np.cos(m * np.pi / ny)) / g.dy ** 2
+    else:
+        prof = np.sin(m * g.yc()).ravel()
+        lam = (2.0 - 2.0 * np.cos(m * g.dy)) / g.dy ** 2
+    U = np.broadcast_to(prof[None, :, None], g.shape).copy()
+    prm = oracle.Params('newtonian', mu_s=2.0, mu_p=0.0, lam=1.0)
+    s1 = oracle.rk3_step(oracle.State.rest(g, U), dt, g, prm)
+    z = -prm.mu_s * lam * dt
+    amp = 1.0 + z + z * z / 2.0 + z ** 3 / 6.0
+    assert abs(z) > 1e-4
+    assert np.abs(s1.U - amp * U).max() < 1e-14
+    assert np.abs(s1.V).max() == 0.0 and np.abs(s1.W).max() == 0.0
+    # third order, not the exponential: the z^4 / 24 term is visible when |z| is large
+    if abs(z) > 0.05:
+        assert abs(np.exp(z) - amp) > 100 * 1e-14
