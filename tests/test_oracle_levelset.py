@@ -349,3 +349,25 @@ def test_level_set_operators_commute_with_the_cube_symmetries(name, fvec, cen, c
     scale = max(np.abs(r).max() for r in ref)
     for a, b in zip(got, cvec(list(ref))):
         assert np.abs(a - b).max() < 1e-12 * scale
+
+
+def test_ab2_shear_mode_follows_the_ab2_recurrence():
+    """One fluid everywhere (phi = 5, H = 1, no interface force, zero mean-free
+    buoyancy; beta = 1 so tau = 0): a shear mode u = sin(m y) e_x decays under
+    u' = -nu lambda u with lambda the discrete Laplacian eigenvalue, and the AB2 step
+    of Eqs. ab2 / ru (forward Euler first, Reading 11; the variable-viscosity form
+    with the mixture viscosity) gives exactly u^1 = (1 + z) u^0 and
+    u^{n+1} = u^n + z (3/2 u^n - 1/2 u^{n-1}), z = -nu lambda dt."""
+    g = oracle.Grid(8, 16, 6, 2 * np.pi, 2 * np.pi, 2 * np.pi)
+    m, dt = 2, 0.01
+    U = np.broadcast_to(np.sin(m * g.yc()), g.shape).copy()
+    tp = TwoPhase('oldroyd_b', Re=0.5, Wi=1.0, beta=1.0, tau_y=0.0, sigma=0.1, drho_g=1.0, reinit_every=0)
+    z = -(tp.beta / tp.Re) * (2.0 - 2.0 * np.cos(m * g.dy)) / g.dy ** 2 * dt
+    s, phi = oracle.State.rest(g, U), np.full(g.shape, 5.0)
+    ref = [U, (1.0 + z) * U]
+    for n in range(4):
+        s, phi = ab2_step(s, phi, dt, g, tp, n)
+        if n >= 1:
+            ref.append(ref[-1] + z * (1.5 * ref[-1] - 0.5 * ref[-2]))
+        assert np.abs(s.U - ref[n + 1]).max() < 1e-14
+        assert np.abs(s.V).max() == 0.0 and np.abs(s.W).max() == 0.0
