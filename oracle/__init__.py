@@ -38,12 +38,17 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   Poisson solve + projection (Eqs. NS-num2/3) ...... pinned (sine modes, sparse direct
                                                      solve, divergence <= 1e-12)
   RK3 constants (Eq. RK) ........................... pinned (3rd-order convergence on
-                                                     a linear ODE closed form)
+                                                     a linear ODE closed form; a whole
+                                                     step multiplies a shear mode and a
+                                                     relaxing uniform conformation by
+                                                     the RK3 stability polynomial)
   level set (Eqs. ls-adv, normal, curv, reinit) .... pinned (translation, sphere
                                                      curvature, Heaviside volume, Laplace
                                                      pressure jump of the CSF force,
                                                      mean-free buoyancy)
-  AB2 (Eqs. ab2tau, ab2) ........................... pinned (2nd-order convergence)
+  AB2 (Eqs. ab2tau, ab2) ........................... pinned (2nd-order convergence; a
+                                                     shear mode follows the AB2
+                                                     recurrence exactly)
   density-contrast split projection ................ pinned (div-free, uniform-density limit,
                                                      fixed point = sparse variable solve)
   mass-preserving level-set shift .................. pinned (exact undo of a shift,

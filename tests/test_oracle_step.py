@@ -169,3 +169,25 @@ def test_shear_mode_decays_by_the_rk3_stability_polynomial(walls, m, dt):
     # third order, not the exponential: the z^4 / 24 term is visible when |z| is large
     if abs(z) > 0.05:
         assert abs(np.exp(z) - amp) > 100 * 1e-14
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_uniform_conformation_relaxes_by_the_rk3_stability_polynomial(walls):
+    """Fluid at rest with a uniform Oldroyd-B conformation: div tau = 0 keeps it at
+    rest, and B - I obeys dB/dt = -(B - I)/lambda exactly (Eq. SRM2, Table 1 with
+    F = a = 1).  One step of Eq. rk3tau with the weights of Eq. RK multiplies B - I by
+    1 + z + z^2/2 + z^3/6, z = -dt/lambda, in every cell and component."""
+    ly = 2.0 if walls else 2 * np.pi
+    g = oracle.Grid(8, 6, 10, 2 * np.pi, ly, 2 * np.pi, walls)
+    prm = oracle.Params.from_groups('oldroyd_b', Re=2.0, Wi=0.3, beta=0.4)
+    B0 = [1.7, 0.3, -0.2, 1.2, 0.1, 0.9]
+    eye = [1.0, 0.0, 0.0, 1.0, 0.0, 1.0]
+    s = oracle.State.rest(g)
+    s.B = [np.full(g.shape, b) for b in B0]
+    dt = 0.05
+    s1 = oracle.rk3_step(s, dt, g, prm)
+    z = -dt / prm.lam
+    amp = 1.0 + z + z * z / 2.0 + z ** 3 / 6.0
+    for c in range(6):
+        assert np.abs(s1.B[c] - (eye[c] + amp * (B0[c] - eye[c]))).max() < 1e-15
+    assert max(np.abs(a).max() for a in (s1.U, s1.V, s1.W)) == 0.0
