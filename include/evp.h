@@ -268,13 +268,18 @@ int evp_poisson_solve(evp_state* s, const void* rhs, void* psi);
  *   precision: EVP_FP64 or EVP_FP32 (element type of rhs and psi).
  *   rhs, psi:  device buffers of nx*ny*nz elements, caller-owned; rhs may equal psi.
  *   stream:    cudaStream_t to run on (NULL = legacy default stream).
- * The result is that of evp_poisson_solve on the same grid.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current, and every call whose grid or precision differs from the
- * previous call's on that device uploads its tables into the array; make such
- * calls before any stream capture.  All calls on a device share the array and
- * it keeps the last call's contents (nothing in it needs to start at zero):
- * calls that overlap on the GPU, on any streams, race and give wrong results.
+ * The result is that of evp_poisson_solve on the same grid.  Calls that are not
+ * being captured look up the array's device address (cudaGetSymbolAddress) with
+ * the current device; the first call on a device may load the module there.  A
+ * call whose grid or precision differs from the previous call's on that device
+ * (or that finds the array moved, after cudaDeviceReset) uploads its tables into
+ * the array.  Make the first call and such calls before any stream capture: a
+ * captured call that would need the lookup or an upload returns EVP_ERR_STATE.  All calls on a
+ * device share the array and it keeps the last call's contents (nothing in it
+ * needs to start at zero): calls that overlap on the GPU, on any streams, race
+ * and give wrong results.  A CUDA graph that holds this call reads the tables in
+ * place, so it stays valid only until the next call on that device with another
+ * grid or precision, even when the calls never overlap.
  * Asynchronous on ``stream``.                                                    */
 int evp_poisson_solve_static(const evp_grid* grid, int precision, const void* rhs, void* psi, void* stream);
 

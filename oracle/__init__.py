@@ -13,7 +13,7 @@ Everything is numpy float64, vectorised over whole arrays with no blocking or
 fusion.  Library primitives used as steps: ``numpy.fft`` (the FFTs of the fast
 Poisson solver).  Each function cites the section / equation / table of the paper
 it restates.  Where the paper is silent the reading taken is stated in the
-docstring ("Reading n"); the same readings are listed in the design notes.
+docstring ("Reading n"); the CUDA path takes the same numbered readings.
 
 Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   grid shifts, centre velocity, velocity gradient ... pinned (brute force, closed forms)
@@ -24,6 +24,15 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                                                      shear closed forms, Saramito yield
                                                      time, steady yielded shear, axis
                                                      swaps and mirrors of the cube)
+  stress from B (Table 1 inverted) ................. pinned (Oldroyd-B start-up shear,
+                                                     FENE-P steady shear: tau_yy = 0,
+                                                     tau_xy = mu_p gdot a/F, N1; planted
+                                                     slips fail)
+  Saramito channel (Sec. 4.1.1, Table 1) ........... pinned (plug half-width y0 of the
+                                                     closed form, steady-shear relations
+                                                     of the yielded cells, force balance,
+                                                     velocity profile of a 1-D root find;
+                                                     planted slips fail)
   local artificial diffusion (Sec. 3.1) ............ pinned (sine-mode eigenvalues of the
                                                      stencil, trigger thresholds, wall
                                                      row, conservation)

@@ -33,8 +33,8 @@ constexpr int MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[EVP_STATIC_SCRATCH_BYTES];
 
-// Per device: the array's device address (looked up once, with that device
-// current) and the configuration whose tables the array currently holds.
+// Per device: the array's device address (looked up with that device current)
+// and the configuration whose tables the array currently holds.
 struct DeviceSlot {
     bool ready = false;
     unsigned char* base = nullptr;
@@ -196,18 +196,38 @@ extern "C" int evp_poisson_solve_static(const evp_grid* grid, int precision, con
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> lock(g_slots_mutex);
     DeviceSlot& slot = g_slots[dev];
-    if (!slot.ready) {
-        // one-time set-up on this device: the host-side name of the array is not a
-        // device address; ask the runtime for the address on the current device
-        void* p = nullptr;
+    // The host-side name of the array is not a device address: ask the runtime
+    // for the address on the current device.  The first call on a device does
+    // this lookup (and may load the module); later calls that are not being
+    // captured repeat it, which is a table lookup, so that a module reloaded after
+    // cudaDeviceReset, whose array lost its contents and may have moved, gets its
+    // tables uploaded again.  A captured call uses the address already known.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (st) {
+        e = cudaStreamIsCapturing(st, &cap);
+        if (e != cudaSuccess)
+            return static_fail(EVP_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+    }
+    if (cap != cudaStreamCaptureStatusNone && !slot.ready)
+        return static_fail(EVP_ERR_STATE, "the first call on a device must come before any stream capture");
+    void* p = slot.base;
+    if (cap == cudaStreamCaptureStatusNone) {
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess)
             return static_fail(EVP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    }
+    if (!slot.ready || slot.base != static_cast<unsigned char*>(p)) {
         slot.base = static_cast<unsigned char*>(p);
+        slot.tables_valid = false;
         slot.ready = true;
     }
-    const bool same = slot.tables_valid && slot.tables_precision == precision &&
-                      std::memcmp(&slot.tables_grid, &g, sizeof(evp_grid)) == 0;
+    // compared member by member: a caller's struct may carry arbitrary padding bytes
+    const evp_grid& tg = slot.tables_grid;
+    const bool same = slot.tables_valid && slot.tables_precision == precision && tg.nx == g.nx && tg.ny == g.ny &&
+                      tg.nz == g.nz && tg.lx == g.lx && tg.ly == g.ly && tg.lz == g.lz && tg.walls_y == g.walls_y;
+    if (!same && cap != cudaStreamCaptureStatusNone)
+        return static_fail(EVP_ERR_STATE, "a call with a new grid or precision cannot be captured: make one "
+                                          "call with this grid and precision before the capture");
     if (!same) {
         slot.tables_valid = false;
         const int r = precision == EVP_FP32 ? upload_static_tables<float>(g, slot.base, L, st)

@@ -151,15 +151,16 @@ def test_saramito_zero_stress_guard():
     assert F == 1.0 and a == 1.0
 
 
-def test_fene_p_identity_fixed_point_and_steady_shear():
-    """B = I is a fixed point at rest (F(I) = a); steady simple shear satisfies
-    B_yy = B_zz = a/F, B_xy = lam gdot B_yy / F, B_xx = (a + 2 lam gdot B_xy)/F
-    with F = L^2/(L^2 - tr B) (solved here by a scalar root find)."""
-    prm = Params.from_groups('fene_p', Re=1.0, Wi=0.6, beta=0.5, L2=50.0)
-    I6 = [np.array(1.0 if c in (0, 3, 5) else 0.0) for c in range(6)]
-    Z = [[0.0] * 3 for _ in range(3)]
-    assert max(abs(v) for v in rt_local(I6, Z, prm)) < 1e-15
-    gdot, lam, L2 = 2.0, prm.lam, prm.L2
+FENE_P_SHEAR = dict(Re=1.0, Wi=0.6, beta=0.5, L2=50.0, gdot=2.0)
+
+
+def fene_p_steady_shear_root():
+    """Steady simple shear of FENE-P (Table 1, upper-convected B): B_yy = B_zz =
+    a/F, B_xy = lam gdot B_yy / F, B_xx = (a + 2 lam gdot B_xy)/F with
+    F = L^2/(L^2 - tr B), solved here by a scalar root find."""
+    c = FENE_P_SHEAR
+    prm = Params.from_groups('fene_p', Re=c['Re'], Wi=c['Wi'], beta=c['beta'], L2=c['L2'])
+    gdot, lam, L2 = c['gdot'], prm.lam, prm.L2
     a = L2 / (L2 - 3.0)
 
     def parts(F):
@@ -172,10 +173,84 @@ def test_fene_p_identity_fixed_point_and_steady_shear():
         bxx, bxy, byy = parts(F)
         return F - L2 / (L2 - (bxx + 2 * byy))
     F = brentq(resid, 1.0 + 1e-9, 50.0)
+    return prm, gdot, a, F, parts(F)
+
+
+def fene_p_steady_shear_oracle():
+    """The oracle's homogeneous shear integrated to steady state (Eq. RK weights)."""
+    prm, gdot, _, _, _ = fene_p_steady_shear_root()
     ts, Bs = integrate_homogeneous(prm, shear_L(gdot), 20.0, 2e-3)
-    bxx, bxy, byy = parts(F)
-    B = Bs[-1]
+    return Bs[-1]
+
+
+def test_fene_p_identity_fixed_point_and_steady_shear():
+    """B = I is a fixed point at rest (F(I) = a); the oracle's homogeneous shear
+    reaches the steady conformation of the root find."""
+    prm, gdot, a, F, (bxx, bxy, byy) = fene_p_steady_shear_root()
+    I6 = [np.array(1.0 if c in (0, 3, 5) else 0.0) for c in range(6)]
+    Z = [[0.0] * 3 for _ in range(3)]
+    assert max(abs(v) for v in rt_local(I6, Z, prm)) < 1e-15
+    B = fene_p_steady_shear_oracle()
     assert abs(B[0] - bxx) < 1e-7 and abs(B[1] - bxy) < 1e-8 and abs(B[3] - byy) < 1e-9
+
+
+def fene_p_stress_errors(B, tau_fn):
+    """Errors of tau = tau_fn(B) against steady FENE-P shear: tau_yy = tau_zz = 0,
+    tau_xy = mu_p gdot a / F and N1 = tau_xx - tau_yy = 2 mu_p lam gdot^2 a / F^2
+    (from tau = (mu_p/lam)(F B - a I) and the steady balance F B - a I = lam (L B + B L^T)),
+    F from the root find."""
+    prm, gdot, a, F, _ = fene_p_steady_shear_root()
+    tau = tau_fn(B, prm)
+    mu_p, lam = prm.mu_p, prm.lam
+    return {'tau_yy': abs(float(tau[3])), 'tau_zz': abs(float(tau[5])),
+            'tau_xy': abs(float(tau[1]) - mu_p * gdot * a / F) / (mu_p * gdot),
+            'N1': abs(float(tau[0] - tau[3]) - 2 * mu_p * lam * gdot ** 2 * a / F ** 2) / (mu_p * lam * gdot ** 2)}
+
+
+def test_fene_p_stress_from_conformation_in_steady_shear():
+    """The FENE-P branch of the stress-from-B inversion (Table 1): in steady simple
+    shear the normal stresses tau_yy and tau_zz vanish, tau_xy = mu_p gdot a/F and
+    N1 = 2 mu_p lam gdot^2 a/F^2, with F from the independent root find."""
+    import oracle.models as om
+    err = fene_p_stress_errors(fene_p_steady_shear_oracle(), om.tau_from_B)
+    assert err['tau_yy'] < 1e-9 and err['tau_zz'] < 1e-9, err
+    assert err['tau_xy'] < 1e-7 and err['N1'] < 1e-6, err
+
+
+@pytest.mark.parametrize('plant', ['B_minus_aI', 'FB_minus_I', 'modulus_mu_p'])
+def test_fene_p_stress_pin_catches_planted_mistakes(plant, monkeypatch):
+    """Each plausible slip in the FENE-P inversion gives an isotropic or scaled
+    error that the rest state cannot see; the steady-shear pin fails on each."""
+    import oracle.models as om
+    B = fene_p_steady_shear_oracle()
+    diag = (True, False, False, True, False, True)
+
+    def bad(B, prm):
+        g = prm.mu_p / prm.lam
+        F, a = om.closure(B, prm)
+        if plant == 'B_minus_aI':
+            return [g * (B[c] - (a if diag[c] else 0.0)) for c in range(6)]
+        if plant == 'FB_minus_I':
+            return [g * (F * B[c] - (1.0 if diag[c] else 0.0)) for c in range(6)]
+        return [prm.mu_p * (F * B[c] - (a if diag[c] else 0.0)) for c in range(6)]
+    monkeypatch.setattr(om, 'tau_from_B', bad)
+    err = fene_p_stress_errors(B, om.tau_from_B)
+    assert not (err['tau_yy'] < 1e-9 and err['tau_zz'] < 1e-9 and err['tau_xy'] < 1e-7 and err['N1'] < 1e-6), err
+
+
+def test_fene_p_steady_shear_pin_catches_a_planted_closure_mistake(monkeypatch):
+    """A slip in the FENE-P closure itself (a = 1 instead of L^2/(L^2 - 3)) moves the
+    steady conformation away from the root find."""
+    import oracle.models as om
+    orig = om.closure
+
+    def bad(B, prm):
+        F, a = orig(B, prm)
+        return (F, 1.0) if prm.model == 'fene_p' else (F, a)
+    monkeypatch.setattr(om, 'closure', bad)
+    _, _, _, _, (bxx, bxy, byy) = fene_p_steady_shear_root()
+    B = fene_p_steady_shear_oracle()
+    assert not (abs(B[0] - bxx) < 1e-7 and abs(B[1] - bxy) < 1e-8 and abs(B[3] - byy) < 1e-9)
 
 
 def test_oldroyd_b_oscillatory_shear_maxwell_closed_form():

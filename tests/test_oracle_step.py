@@ -191,3 +191,185 @@ def test_uniform_conformation_relaxes_by_the_rk3_stability_polynomial(walls):
     for c in range(6):
         assert np.abs(s1.B[c] - (eye[c] + amp * (B0[c] - eye[c]))).max() < 1e-15
     assert max(np.abs(a).max() for a in (s1.U, s1.V, s1.W)) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Saramito channel (Sec. 4.1.1 geometry, Table 1 Saramito row): plug width and
+# the yielded profile of the steady pressure-driven flow
+
+
+def saramito_channel_closed_form(G, mu_s, mu_p, lam, tau_y):
+    """Steady yielded simple shear of the Saramito model with the velocity
+    gradient du/dy = -gdot: tau_yy = 0, F tau_xy = mu_p gdot, tau_xx =
+    2 lam tau_xy^2 / mu_p and F = 1 - tau_y/|tau^d|, |tau^d|^2 = tau_xy^2 +
+    tau_xx^2/3.  The shear stress T = |tau_xy| parametrises everything: with the
+    momentum balance mu_s gdot + T = G |y| the position of a yielded layer is
+    explicit in T.  The plug edge is where gdot -> 0, |tau^d| = tau_y and T = G y0:
+    (G y0)^2 = 3 mu_p^2 (-1 + sqrt(1 + 16 lam^2 tau_y^2 / (3 mu_p^2))) / (8 lam^2).
+    Returns (y0, gdot(y), u(y)) with u = 0 at the walls y = +-1."""
+    from scipy.integrate import quad
+    from scipy.optimize import brentq
+
+    y0 = np.sqrt(3 * mu_p ** 2 * (-1 + np.sqrt(1 + 16 * lam ** 2 * tau_y ** 2 / (3 * mu_p ** 2)))
+                 / (8 * lam ** 2)) / G
+
+    def F_of(T):
+        return max(0.0, 1.0 - tau_y / np.sqrt(T ** 2 + (2 * lam * T ** 2 / mu_p) ** 2 / 3))
+
+    def gdot(y):
+        y = abs(y)
+        if y <= y0:
+            return 0.0
+        T = brentq(lambda T: mu_s * F_of(T) * T / mu_p + T - G * y, G * y0, G * y, xtol=1e-15)
+        return F_of(T) * T / mu_p
+
+    def u(y):
+        return quad(gdot, max(abs(y), y0), 1.0, epsabs=1e-13, epsrel=1e-12)[0]
+
+    return y0, gdot, u
+
+
+def test_saramito_plug_edge_closed_form_is_the_yield_root():
+    """The plug-edge formula is the root of |tau^d|(T) = tau_y with tau_xx =
+    2 lam T^2 / mu_p, found here by bisection; at the channel workload's values
+    (G = 2/Re = 0.02, mu_p = tau_y = 0.005, lambda = 1) it gives y0 = 0.1885, and
+    the Bingham limit lambda -> 0 gives tau_y / G."""
+    from scipy.optimize import brentq
+    for G, mu_p, lam, ty in ((0.02, 0.005, 1.0, 0.005), (1.0, 0.48, 0.8, 0.4), (3.0, 0.2, 2.5, 1.1)):
+        y0, _, _ = saramito_channel_closed_form(G, 0.1, mu_p, lam, ty)
+        T = brentq(lambda T: T ** 2 + (2 * lam * T ** 2 / mu_p) ** 2 / 3 - ty ** 2, 0.0, ty)
+        assert abs(G * y0 - T) < 1e-12 * max(1.0, T)
+    y0, _, _ = saramito_channel_closed_form(0.02, 0.005, 0.005, 1.0, 0.005)
+    assert abs(y0 - 0.1885) < 5e-5
+    y0, _, _ = saramito_channel_closed_form(0.02, 0.005, 0.005, 1e-3, 0.005)
+    assert abs(y0 - 0.25) < 1e-5
+
+
+SARAMITO_CHANNEL = dict(ny=32, Re=1.25, Wi=0.8, beta=0.4, Bi=0.5, G=1.0, T=3.0)
+
+
+def saramito_channel_errors():
+    """Runs the oracle's RK3 step on a thin wall-bounded channel (1 x 32 x 1, walls
+    at y = +-1, body force G along x) from the closed-form steady state until the
+    discrete flow is steady, and measures it against what the closed form fixes
+    exactly or to O(dy^2).  mu_s, mu_p, lambda and tau_y are all different, so a
+    wrong scaling of any of them shows.  Returns a dict of errors (NaN-safe: a
+    diverging run gives inf)."""
+    c = SARAMITO_CHANNEL
+    ny, G = c['ny'], c['G']
+    g = oracle.Grid(1, ny, 1, 1.0, 2.0, 1.0, True)
+    prm = oracle.Params.from_groups('saramito', c['Re'], c['Wi'], c['beta'], Bi=c['Bi'])
+    mu_s, mu_p, lam, ty = prm.mu_s, prm.mu_p, prm.lam, prm.tau_y
+    y0, gdot, u_of = saramito_channel_closed_form(G, mu_s, mu_p, lam, ty)
+    yc = g.yc()[0, :, 0]
+    ua = np.array([u_of(y) for y in yc])
+    # closed-form start: total shear stress -G y, tau_xx = 2 lam tau_xy^2 / mu_p
+    txy = np.array([-G * y + mu_s * gdot(y) * np.sign(y) for y in yc])
+    gm = mu_p / lam
+    one = np.ones(g.shape)
+    zero = g.zeros()
+    B = [one + (2 * lam * txy ** 2 / mu_p / gm)[None, :, None], one * (txy / gm)[None, :, None], zero.copy(),
+         one.copy(), zero.copy(), one.copy()]
+    s = oracle.State.rest(g, U=one * ua[None, :, None])
+    s.B = B
+    dt = 0.9 * 2.51 / (4 * mu_s * (1 / g.dx ** 2 + 1 / g.dy ** 2 + 1 / g.dz ** 2))
+    for _ in range(int(c['T'] / dt)):
+        s = oracle.rk3_step(s, dt, g, prm, (G, 0.0, 0.0))
+    u = s.U[0, :, 0]
+    tau = [t[0, :, 0] for t in oracle.models.tau_from_B(s.B, prm)]
+    F_or = np.broadcast_to(oracle.models.closure(s.B, prm)[0], g.shape)[0, :, 0]
+    gd = oracle.velocity_gradient(s.U, s.V, s.W, g)[0][1][0, :, 0]
+    # |tau^d| from the 3x3 stress matrix, written independently of the oracle
+    M = np.zeros((ny, 3, 3))
+    for k, (a, b) in enumerate(((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))):
+        M[:, a, b] = M[:, b, a] = tau[k]
+    dev = M - np.trace(M, axis1=1, axis2=2)[:, None, None] / 3 * np.eye(3)
+    mag = np.sqrt(0.5 * np.einsum('nij,nij->n', dev, dev))
+    F_t = np.maximum(0.0, 1.0 - ty / mag)
+    yielded = F_or > 0
+    strong = F_t >= 0.1
+    ay = np.abs(yc)
+    edge_y = 0.5 * (yc[1:] + yc[:-1])
+    bal = mu_s * (u[1:] - u[:-1]) / g.dy + 0.5 * (tau[1][1:] + tau[1][:-1]) + G * edge_y
+
+    def worst(x):
+        x = np.asarray(x, dtype=float)
+        return float(np.max(np.abs(x))) if x.size and np.all(np.isfinite(x)) else np.inf
+
+    return {
+        # the discrete momentum balance: total shear stress = -G y at every y edge
+        'force_balance': worst(bal),
+        # the yield surface: unyielded cells inside y0, yielded cells outside it
+        'plug_inside_y0': float(ay[~yielded].max() - y0) if np.any(~yielded) else np.inf,
+        'yield_outside_y0': float(y0 - ay[yielded].min()) if np.any(yielded) else np.inf,
+        'plug_cells': int(np.sum(~yielded)),
+        # the oracle's F equals 1 - tau_y/|tau^d| from the stress it returns
+        'F_consistent': worst((F_or - F_t)[yielded]),
+        # steady yielded shear: tau_yy = 0, F tau_xy = mu_p gdot, tau_xx = 2 lam tau_xy^2 / mu_p
+        'tau_yy': worst(tau[3][yielded]),
+        'F_tauxy': worst((F_t * tau[1] - mu_p * gd)[strong]),
+        'tau_xx': worst((tau[0] - 2 * lam * tau[1] ** 2 / mu_p)[strong]),
+        # the plug moves rigidly
+        'plug_gdot': worst(gd[~yielded]),
+        # the velocity profile of the closed form, to O(dy^2)
+        'u_rel': worst(u - ua) / ua.max(),
+    }
+
+
+SARAMITO_CHANNEL_TOL = {'force_balance': 5e-4, 'plug_inside_y0': 0.0, 'yield_outside_y0': 0.0,
+                        'F_consistent': 1e-12, 'tau_yy': 1e-12, 'F_tauxy': 1e-3, 'tau_xx': 5e-3,
+                        'plug_gdot': 5e-3, 'u_rel': 1e-2}
+
+
+def saramito_channel_failures(err):
+    fails = [k for k, tol in SARAMITO_CHANNEL_TOL.items() if not (err[k] <= tol)]
+    if err['plug_cells'] < 6:
+        fails.append('plug_cells')
+    return fails
+
+
+def test_saramito_channel_plug_width_and_yielded_profile():
+    """Steady Saramito channel flow (Sec. 4.1.1 geometry, Table 1): the oracle's
+    plug spans |y| < y0 of the closed form to within the cell layout (the edge lies
+    between the last unyielded and the first yielded cell centre; the Bingham
+    value tau_y/G = 0.4 here lies outside that interval), the yielded cells obey the
+    steady-shear relations of the closed form, the total shear stress balances the
+    body force at every edge, and u matches the closed-form profile to O(dy^2)."""
+    err = saramito_channel_errors()
+    assert not saramito_channel_failures(err), err
+
+
+def _saramito_mag_without_half(B, prm):
+    """Planted mistake: |tau^d| without the factor 1/2 of the second invariant."""
+    g = prm.mu_p / prm.lam
+    t = [g * (B[c] - (1.0 if c in (0, 3, 5) else 0.0)) for c in range(6)]
+    tr = t[0] + t[3] + t[5]
+    d = [t[c] - (tr / 3.0 if c in (0, 3, 5) else 0.0) for c in range(6)]
+    mag = np.sqrt(d[0] ** 2 + d[3] ** 2 + d[5] ** 2 + 2 * (d[1] ** 2 + d[2] ** 2 + d[4] ** 2))
+    F = np.where(mag > 0.0, np.maximum(0.0, 1.0 - prm.tau_y / np.where(mag > 0, mag, 1.0)), 0.0)
+    return F, F
+
+
+@pytest.mark.parametrize('plant', ['closure_norm', 'tau_modulus'])
+def test_saramito_channel_pin_catches_planted_mistakes(plant, monkeypatch):
+    """The channel pin fails when a mistake is planted in the oracle's Saramito
+    closure (the second invariant without its factor 1/2) or in its stress from B
+    (mu_p in place of the modulus mu_p/lambda)."""
+    import oracle.models as om
+    import oracle.step as ost
+    if plant == 'closure_norm':
+        orig = om.closure
+        monkeypatch.setattr(om, 'closure', lambda B, prm: _saramito_mag_without_half(B, prm)
+                            if prm.model == 'saramito' else orig(B, prm))
+    else:
+        orig = om.tau_from_B
+
+        def bad(B, prm):
+            if prm.model != 'saramito':
+                return orig(B, prm)
+            return [prm.mu_p * (B[c] - (1.0 if c in (0, 3, 5) else 0.0)) for c in range(6)]
+        monkeypatch.setattr(om, 'tau_from_B', bad)
+        monkeypatch.setattr(ost, 'tau_from_B', bad)
+    with np.errstate(all='ignore'):
+        err = saramito_channel_errors()
+    assert saramito_channel_failures(err), err

@@ -73,3 +73,32 @@ def test_static_scratch_rejects_oversize_grid(evp):
         evp.evp_poisson_solve_static(big, evp.EVP_FP32, r, r, None)
     assert e.value.code == evp.EVP_ERR_ARG
     assert 'too large' in str(e.value)
+
+
+def test_static_scratch_solve_in_a_captured_graph(evp):
+    """The use the entry point exists for: after one call on the grid (tables in
+    the array), a second call on the same grid made while a stream is captured
+    into a CUDA graph.  The replayed graph gives the state solve's result, twice in
+    a row, and nothing is allocated on the device by the captured call."""
+    import torch
+    grid = evp.make_grid(36, 20, 16, 2 * np.pi, 2.0, 2 * np.pi, True)
+    prec = 0
+    r = case(5, (grid.nz, grid.ny, grid.nx))
+    ref = state_solve(evp, grid, prec, r)
+    rd = torch.tensor(r, dtype=torch.float64, device='cuda')
+    out = torch.full_like(rd, float('nan'))
+    static_solve(evp, grid, prec, case(6, (grid.nz, grid.ny, grid.nx)))    # warm call on this grid
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        evp.evp_poisson_solve_static(grid, prec, rd, out, torch.cuda.current_stream().cuda_stream)
+    assert torch.cuda.memory_allocated() == before
+    for _ in range(2):
+        out.fill_(float('nan'))
+        g.replay()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert rel(got, ref) < TOL[prec], rel(got, ref)
