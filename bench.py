@@ -95,9 +95,17 @@ class ClockSampler:
     def end(self):
         self.window[1] = time.monotonic()
 
-    def stop(self):
+    def stop(self, wait_s=3.0):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        # a region shorter than the sampling period may hold no sample: wait for the
+        # first one printed after it ended (it describes the clocks just after the
+        # region, which the region's own work set)
+        if self.window is not None and self.window[1] is not None:
+            t0 = time.monotonic()
+            while (not any(x[0] >= self.window[1] for x in self.lines)
+                   and time.monotonic() - t0 < wait_s and self.proc.poll() is None):
+                time.sleep(0.02)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -109,7 +117,9 @@ class ClockSampler:
         if self.window is not None and self.window[1] is not None:
             inside = [x for x in lines if self.window[0] <= x[0] <= self.window[1]]
             # a region shorter than the sampling period: the first sample after it began
-            lines = inside or [x for x in lines if x[0] >= self.window[0]][:1]
+            after = [x for x in lines if x[0] >= self.window[0]][:1]
+            self.where = "inside the timed region" if inside else "first sample after the region began"
+            lines = inside or after
         for _, l in lines:
             parts = [x.strip() for x in l.split(',')]
             if len(parts) < 7:
@@ -123,7 +133,7 @@ class ClockSampler:
                 if v.lower() == 'active':
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_from": getattr(self, 'where', None)}
 
 
 def algorithmic_bytes(kernel, w, elt, walls):
@@ -133,8 +143,10 @@ def algorithmic_bytes(kernel, w, elt, walls):
     nxh = w['nx'] // 2 + 1
     spec = 2 * nxh * w['ny'] * w['nz'] * elt     # complex spectral buffer, bytes
     if kernel == 'stress_weno_update':
-        # read u(3) B(6) [+RT(6)], write B(6) [+RT(6)] and the summed stress S(6)
-        words = (3 + 6 + 6 + 6 + 6) + (3 + 6 + 6 + 6 + 6 + 6) + (3 + 6 + 6 + 6 + 6)
+        # the method's own words (Eq. rk3tau): read u(3) B(6) [+RT(6)], write B(6)
+        # [+RT(6)]: 21, 27, 21.  The summed stress S (6 words written per substep for
+        # the momentum step) is the fusion's traffic, counted by fusion_bytes()
+        words = (3 + 6 + 6) + (3 + 6 + 6 + 6) + (3 + 6 + 6)
         return words * N * elt, 3
     if kernel == 'momentum_predictor':
         # read u(3) p(1) S(6) [+N(3)], write u*(3) [+N(3)]
@@ -152,6 +164,15 @@ def algorithmic_bytes(kernel, w, elt, walls):
         # read u*(3) psi(1) p(1), write u(3) p(1)
         return 3 * 9 * N * elt, 3
     return 0, 1
+
+
+def fusion_bytes(kernel, w, elt):
+    """Bytes per step a kernel moves beyond the method's own words because of a
+    fusion choice: the stress kernel writes the summed stress tau^k + tau^{k-1}
+    (6 words per substep) that the momentum kernel then reads instead of B^{k-1}
+    and B^k (12 words)."""
+    N = w['nx'] * w['ny'] * w['nz']
+    return 3 * 6 * N * elt if kernel == 'stress_weno_update' else 0
 
 
 # CUDA sources that determine each profiled kernel's code (for the staleness check)
@@ -284,10 +305,20 @@ def run_gpu(args, rank, world, local_rank):
         gbs = b * nsteps / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
         kern[name] = {"ms_per_launch": ms / cnt, "launches": cnt, "share": ms / sum(v[0] for v in ktimes.values()),
                       "algorithmic_GBps": gbs, "frac_of_hbm": gbs / hbm}
+        fb = fusion_bytes(name, w, elt)
+        if fb:
+            # bytes the kernel moves beyond the method's own (the summed stress it writes)
+            kern[name]["fusion_GBps"] = fb * nsteps / (ms * 1e-3) / 1e9
+            kern[name]["with_fusion_frac_of_hbm"] = (b + fb) * nsteps / (ms * 1e-3) / 1e9 / hbm
     b_dom, per_dom = algorithmic_bytes(dom, w, elt, w['walls_y'])
     dom_ms, dom_cnt = ktimes[dom]
     achieved = b_dom * (dom_cnt / per_dom) / (dom_ms * 1e-3) / 1e9
     traffic = ncu_traffic(dom)
+
+    # plain-FMA peaks of this GPU (non-tensor FP32 and FP64), the arithmetic roofline
+    fma = {"fp32_tflops": evp.evp_fma_peak(evp.EVP_FP32) / 1e12, "fp64_tflops": evp.evp_fma_peak(evp.EVP_FP64) / 1e12,
+           "how": "evp_fma_peak: 8 independent FMA chains per thread, 8 blocks of 256 threads per SM, "
+                  "packed f32x2 FMAs in FP32; best of 3 timed launches, an FMA counted as 2 operations"}
 
     # ---------------- e2e through the C ABI with host buffers
     fields_io = [evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P] + [evp.EVP_BXX + c for c in range(6)]
@@ -364,11 +395,59 @@ def run_gpu(args, rank, world, local_rank):
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                      "traffic": traffic},
         "kernels": kern,
+        "fma_peaks": fma,
+        "cufft_reference": cufft_reference(ktimes),
         "kernel_timing": f"adjacent pass of {k_steps} steps with CUDA events around each launch on the library "
                          f"stream (direct launches); the timed region replays a CUDA graph per step",
         "clocks": clk,
     }
     return line
+
+
+def cufft_reference(ktimes):
+    """cuFFT (through torch.fft), timed as a reference point only, on the transforms
+    the hand-written passes of the channel's Poisson solve take: the real-to-complex
+    transform along x of a 128 x 128 x 256 FP32 field, the complex transform along
+    z of its (129-wide) spectrum, and the two inverses; beside it the hand-written
+    chain's x and z passes (div_fft_x + fft_z_forward + fft_z_inverse + ifft_x_psi,
+    per substep, from the instrumented pass).  Also the 256^3 FP32 periodic
+    real-to-complex 3-D transform pair (rfftn + irfftn) of the FENE-P box."""
+    import torch
+    out = {}
+    x = torch.randn(128, 128, 256, device='cuda', dtype=torch.float32)
+
+    def timeit(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def chain():
+        X = torch.fft.rfft(x, dim=2)
+        X = torch.fft.fft(X, dim=0)
+        X = torch.fft.ifft(X, dim=0)
+        return torch.fft.irfft(X, n=256, dim=2)
+    out["channel_x_z_transforms_ms"] = timeit(chain)
+    mine = 0.0
+    for k in ('div_fft_x', 'fft_z_forward', 'fft_z_inverse', 'ifft_x_psi'):
+        ms, cnt = ktimes.get(k, (0.0, 0))
+        if cnt:
+            mine += ms / cnt
+    out["hand_written_x_z_passes_ms"] = mine
+    del x
+    y = torch.randn(256, 256, 256, device='cuda', dtype=torch.float32)
+    out["periodic_256^3_rfftn_irfftn_ms"] = timeit(lambda: torch.fft.irfftn(torch.fft.rfftn(y), s=y.shape), reps=10)
+    out["note"] = ("cuFFT is a reference point only: the hand-written passes also fuse the divergence into the "
+                   "x pass and the scaling into the inverse x pass")
+    del y
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_serving(steps_scale=0.1):
@@ -417,6 +496,18 @@ def run_fene_turbulence(steps=4):
         code, bits, maxdiv = sim.sync(raise_on_error=False)
         out[name] = {"ms_per_step": ms, "Mcell_steps_per_s": n ** 3 / (ms * 1e-3) / 1e6, "max_div": maxdiv,
                      "status": code}
+        if name == 'fp32':
+            # per-kernel times of one instrumented step: the periodic Poisson chain
+            # beside cuFFT's 3-D transform pair of the same box
+            evp.evp_kernel_timing(sim.handle, True)
+            evp.evp_kernel_times(sim.handle)
+            sim.step(1e-3)
+            kt = evp.evp_kernel_times(sim.handle)
+            evp.evp_kernel_timing(sim.handle, False)
+            out[name]["kernels_ms_per_launch"] = {k: t / c for k, (t, c) in kt.items() if c}
+            out[name]["hand_written_periodic_chain_ms"] = sum(
+                kt[k][0] / kt[k][1] for k in ('div_fft_x', 'fft_z_forward', 'fft_y_modal_solve', 'fft_z_inverse',
+                                              'ifft_x_psi') if kt.get(k, (0, 0))[1])
         res[name] = [sim.get(f).astype(np.float64) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_BXX,
                                                                  evp.EVP_BXY)]
         sim.close()
@@ -548,22 +639,73 @@ def run_small_grid():
     return out
 
 
-def run_cpu_baseline(args):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
-    one RK3 step of a 256 x 128 x 64 slab of the channel (z halved)."""
+def _oracle_slab(nz):
+    """Oracle state of a 256 x 128 x nz slab of the channel (inputs only)."""
     import oracle
     w = WORKLOAD
-    nz = 64
     geo, U, V, W = workload_inputs(w, nz=nz)
     g = oracle.Grid(w['nx'], w['ny'], nz, geo['lx'], geo['ly'], geo['lz'], True)
     prm = oracle.Params.from_groups(w['model'], w['Re'], w['Wi'], w['beta'], Bi=w['Bi'])
-    s = oracle.State.rest(g, U, V, W)
+    return g, prm, oracle.State.rest(g, U, V, W)
+
+
+def _oracle_step(g, prm, s):
+    import oracle
+    w = WORKLOAD
+    return oracle.rk3_step(s, w['dt'], g, prm, (2.0 / w['Re'], 0.0, 0.0))
+
+
+def _oracle_worker(nz, barrier, queue):
+    """One host process of the all-core run: build its slab, wait for the others,
+    time one RK3 step of the oracle."""
+    os.environ.setdefault('OMP_NUM_THREADS', '1')
+    g, prm, s = _oracle_slab(nz)
+    barrier.wait()
+    t0 = time.time()
+    _oracle_step(g, prm, s)
+    queue.put((t0, time.time(), g.ncells))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_cpu_baseline(args, all_cores=True):
+    """The FP64 oracle, as it stands, on bounded samples of the same workload.
+    Single core: one RK3 step of a 256 x 128 x 64 slab of the channel (z halved).
+    All cores: one process per host core (spawned, so no process is forked from a
+    CUDA context), each timing one RK3 step of its own 256 x 128 x 32 slab after a
+    barrier; throughput = all slabs' cells / (last end - first start)."""
+    nz = 64
+    g, prm, s = _oracle_slab(nz)
     t0 = time.perf_counter()
-    s = oracle.rk3_step(s, w['dt'], g, prm, (2.0 / w['Re'], 0.0, 0.0))
+    _oracle_step(g, prm, s)
     dt = time.perf_counter() - t0
-    return {"value": w['nx'] * w['ny'] * nz / dt / 1e6, "unit": "Mcell-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"1 RK3 step of a {w['nx']}x{w['ny']}x{nz} slab of the channel (numpy FP64, "
-                      f"single thread), {dt:.1f} s"}
+    single = {"value": g.ncells / dt / 1e6, "unit": "Mcell-steps/s", "cores": 1, "kind": "oracle",
+              "sample": f"1 RK3 step of a {g.nx}x{g.ny}x{nz} slab of the channel (numpy FP64, "
+                        f"single thread), {dt:.1f} s"}
+    del s
+    if not all_cores:
+        return single
+    import multiprocessing as mp
+    n = host_cores()
+    ctx = mp.get_context('spawn')
+    barrier, queue = ctx.Barrier(n), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(32, barrier, queue)) for _ in range(n)]
+    for p in procs:
+        p.start()
+    res = [queue.get(timeout=600) for _ in range(n)]
+    for p in procs:
+        p.join(timeout=60)
+    wall = max(r[1] for r in res) - min(r[0] for r in res)
+    cells = sum(r[2] for r in res)
+    return {"value": cells / wall / 1e6, "unit": "Mcell-steps/s", "cores": n, "kind": "oracle",
+            "sample": f"{n} processes (one per host core), each one RK3 step of its own 256x128x32 slab of "
+                      f"the channel (numpy FP64), {wall:.1f} s from the first start to the last end",
+            "single_core": single}
 
 
 def main():
@@ -585,7 +727,7 @@ def main():
             return
         # untimed warm-up samples, then the timed ones; both capped at 3 so that the
         # run stays within a few minutes of host time
-        warm = max(0, min(args.warmup, 3))
+        warm = max(0, min(args.warmup, 2))
         for _ in range(warm):
             run_cpu_baseline(args)
         vals = []

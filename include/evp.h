@@ -310,6 +310,16 @@ int evp_sync(evp_state* s, unsigned* bits, double* max_div);
  * allocates 16 bytes.                                                          */
 int evp_selftest(unsigned long long* mismatches);
 
+/* Measured peak of the plain (non-tensor) FMA pipe of the current device, the
+ * roofline of arithmetic-bound kernels (the paper has no counterpart): every
+ * thread of 8 blocks per SM runs eight independent chains of fused multiply-adds
+ * (EVP_FP32: the packed two-lane f32x2 instruction the stress kernel uses;
+ * EVP_FP64: the double-precision FMA), timed with CUDA events on the legacy
+ * stream; *flops_per_s receives the best of three timed launches after a
+ * warm-up, counting an FMA as two operations.  Synchronous; about 0.2 s;
+ * allocates 16 bytes.  The rate follows the SM clock at the time.              */
+int evp_fma_peak(int precision, double* flops_per_s);
+
 /* Per-kernel timing with CUDA events on the state's stream (off by default).
  * evp_kernel_times fills up to n entries of accumulated milliseconds and
  * launch counts (synchronises); evp_kernel_name names entry i.              */

@@ -1398,6 +1398,14 @@ int evp_selftest(unsigned long long* mismatches) {
     return EVP_OK;
 }
 
+int evp_fma_peak(int precision, double* flops_per_s) {
+    if (!flops_per_s) return fail(EVP_ERR_ARG, "null output");
+    if (precision != EVP_FP64 && precision != EVP_FP32) return fail(EVP_ERR_ARG, "bad precision");
+    const cudaError_t e = evp::run_fma_peak(precision, flops_per_s);
+    if (e != cudaSuccess) return cuda_fail(e, "peak kernels");
+    return EVP_OK;
+}
+
 int evp_kernel_timing(evp_state* s, int enable) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
     flush_timing(s);

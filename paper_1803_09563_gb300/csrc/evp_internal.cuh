@@ -480,6 +480,8 @@ inline std::vector<double> helmholtz_table(int ny, int nz, int nxh, double dy, c
 
 // device self-test of widen_f32 / narrow_f64 (k_selftest.cu)
 cudaError_t run_selftest(unsigned long long* mismatches);
+// best rate of plain FMAs of the current device, in FLOP/s (k_selftest.cu)
+cudaError_t run_fma_peak(int precision, double* flops);
 
 template <typename T>
 cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a,

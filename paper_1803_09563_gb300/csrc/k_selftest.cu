@@ -2,9 +2,87 @@
 // binary64 (widen_f32, narrow_f64) against the conversion instructions: bit for
 // bit, except that binary32-subnormal values must come out as the signed zero and
 // a NaN as some NaN.
+#include <algorithm>
+
 #include "evp_internal.cuh"
 
 namespace evp {
+
+namespace {
+
+// Plain (non-tensor) FMA throughput: every thread runs NACC independent chains of
+// ``iters`` fused multiply-adds acc = acc * m + c with run-time m and c, so that
+// nothing folds and each chain keeps the pipe busy at full occupancy.  Single
+// precision uses the packed f32x2 instruction (two lanes per instruction), the
+// form the stress kernel issues.  A result equal to ``never`` would be stored, so
+// the chains cannot be removed.
+constexpr int NACC = 8;
+
+__global__ void __launch_bounds__(256) k_peak_f32(float* out, int iters, float m, float c, float never) {
+    float2 acc[NACC];
+#pragma unroll
+    for (int q = 0; q < NACC; ++q) acc[q] = make_float2(threadIdx.x * 1e-3f + q, q * 0.5f);
+    const float2 m2 = make_float2(m, m), c2 = make_float2(c, c);
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int q = 0; q < NACC; ++q) acc[q] = __ffma2_rn(acc[q], m2, c2);
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < NACC; ++q) s += acc[q].x + acc[q].y;
+    if (s == never) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) k_peak_f64(double* out, int iters, double m, double c, double never) {
+    double acc[NACC];
+#pragma unroll
+    for (int q = 0; q < NACC; ++q) acc[q] = threadIdx.x * 1e-3 + q;
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int q = 0; q < NACC; ++q) acc[q] = fma(acc[q], m, c);
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < NACC; ++q) s += acc[q];
+    if (s == never) out[0] = s;
+}
+
+}  // namespace
+
+cudaError_t run_fma_peak(int precision, double* flops) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    void* d = nullptr;
+    e = cudaMalloc(&d, 16);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int threads = 256, blocks = sms * 8;
+    // about 20-40 ms per launch at the expected rates (80 TFLOP/s FP32, ~1.3 FP64)
+    const int iters = precision == EVP_FP32 ? 65536 : 2048;
+    const double per_launch = 2.0 * NACC * (precision == EVP_FP32 ? 2.0 : 1.0) * iters * double(threads) * blocks;
+    double best = 0.0;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(a);
+        if (precision == EVP_FP32)
+            k_peak_f32<<<blocks, threads>>>(static_cast<float*>(d), iters, 0.999999f, 1e-7f, -1.2345e30f);
+        else
+            k_peak_f64<<<blocks, threads>>>(static_cast<double*>(d), iters, 0.999999999, 1e-12, -1.2345e300);
+        cudaEventRecord(b);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        // the first launch is a warm-up
+        if (e == cudaSuccess && rep > 0 && ms > 0.f) best = std::max(best, per_launch / (ms * 1e-3));
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(d);
+    *flops = best;
+    return e;
+}
 
 namespace {
 

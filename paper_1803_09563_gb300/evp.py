@@ -90,6 +90,7 @@ def load(path=None):
         'evp_poisson_solve_static': (c_int, [POINTER(evp_grid), c_int, c_void_p, c_void_p, c_void_p]),
         'evp_sync': (c_int, [c_void_p, POINTER(c_uint), POINTER(c_double)]),
         'evp_selftest': (c_int, [POINTER(c_ulonglong)]),
+        'evp_fma_peak': (c_int, [c_int, POINTER(c_double)]),
         'evp_kernel_timing': (c_int, [c_void_p, c_int]),
         'evp_kernel_times': (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), c_int]),
         'evp_kernel_name': (c_char_p, [c_int]),
@@ -110,7 +111,7 @@ def exported_symbols():
             'evp_substep', 'evp_project', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_sync', 'evp_kernel_timing',
             'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error', 'evp_poisson_solve_static',
             'evp_set_graph', 'evp_selftest', 'evp_set_pdl', 'evp_set_particles', 'evp_get_particles',
-            'evp_set_fields', 'evp_get_fields']
+            'evp_set_fields', 'evp_get_fields', 'evp_fma_peak']
 
 
 def _check(code):
@@ -272,6 +273,14 @@ def evp_sync(state, raise_on_error=True):
     if raise_on_error and code not in (EVP_OK,):
         _check(code)
     return code, bits.value, md.value
+
+
+def evp_fma_peak(precision):
+    """Measured plain-FMA peak of the current device in FLOP/s (EVP_FP32: packed
+    f32x2 FMAs; EVP_FP64: double FMAs)."""
+    r = c_double(0.0)
+    _check(load().evp_fma_peak(int(precision), ctypes.byref(r)))
+    return r.value
 
 
 def evp_selftest():
