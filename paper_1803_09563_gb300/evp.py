@@ -126,8 +126,10 @@ def _ptr(a):
         import torch
         if isinstance(a, torch.Tensor):
             assert a.is_contiguous()
-            if a.is_cuda:
-                # the library works on its own stream: finish torch's pending work on the tensor
+            if a.is_cuda and not torch.cuda.is_current_stream_capturing():
+                # the library works on its own stream: finish torch's pending work on
+                # the tensor (a stream being captured orders the work by the capture
+                # and may not be synchronised)
                 torch.cuda.current_stream(a.device).synchronize()
             return a.data_ptr(), int(a.is_cuda), a.numel() * a.element_size()
     except ImportError:
