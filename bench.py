@@ -450,18 +450,24 @@ def cufft_reference(ktimes):
     return out
 
 
-def run_serving(steps_scale=0.1):
-    """Serving mix: a seeded Poisson stream of 64 periodic Saramito requests, grids
-    from {32, 48, 64, 96, 128}^3, Wi in U[0.5, 4], Bi in U[0, 1], beta in U[0.3, 0.9],
-    random solenoidal velocity (|k| <= 4, max-norm 1), FP32, 120 GB budget, graph
-    replay.  Step counts are the mix's 100-1000 scaled by ``steps_scale``."""
+def run_serving():
+    """Serving mix: a seeded Poisson stream (0.05 requests per ms, seed 3) of 64
+    periodic Saramito requests, grids from {32, 48, 64, 96, 128}^3, Wi in U[0.5, 4],
+    Bi in U[0, 1], beta in U[0.3, 0.9], random solenoidal velocity (|k| <= 4,
+    max-norm 1), 100-1000 FP32 steps each, admitted under a 120 GB budget; one
+    batch per grid size, its tiles autotuned before the run (untimed)."""
     from paper_1803_09563_gb300 import serve
-    lo, hi = max(1, int(100 * steps_scale)), max(2, int(1000 * steps_scale))
-    reqs = serve.mixed_requests(64, seed=3, steps=(lo, hi), rate=0.5)
+    reqs = serve.mixed_requests(64, seed=3, steps=(100, 1000), rate_per_ms=0.05)
     prepared = {r.rid: serve.request_inputs(r) for r in reqs}      # client side, untimed
-    _, rep = serve.Server(budget_bytes=120 * 10 ** 9).run(reqs, prepared=prepared)
-    rep["steps_per_request"] = [lo, hi]
-    rep["workload"] = "serving_mix_64_requests_32-128^3_saramito_fp32"
+    srv = serve.Server(budget_bytes=120 * 10 ** 9, result_fields=(), tune=False)
+    t0 = time.perf_counter()
+    tuned = srv.tune_sizes(reqs)
+    tune_s = time.perf_counter() - t0
+    _, rep = srv.run(reqs, prepared=prepared)
+    rep["tuned_tiles"] = {str(n): {"config": list(c), "ms_per_step": ms} for n, (c, ms) in tuned.items()}
+    rep["tune_seconds"] = tune_s
+    rep["steps_per_request"] = [100, 1000]
+    rep["workload"] = "serving_mix_64_requests_32-128^3_saramito_fp32_100-1000_steps_120GB"
     return rep
 
 

@@ -310,6 +310,77 @@ int evp_sync(evp_state* s, unsigned* bits, double* max_div);
  * allocates 16 bytes.                                                          */
 int evp_selftest(unsigned long long* mismatches);
 
+/* ---------------------------------------------------------------- batches
+ * Many simulations advanced together (the paper has no counterpart: it runs one
+ * simulation per job).  A batch advances every member state by one RK3 step of
+ * that member's dt per evp_batch_step, with one launch per kernel phase for all
+ * members: the stress update and the momentum predictor as persistent kernels
+ * over a device work list of (member, tile) that may mix grid sizes, the
+ * Poisson passes and the correction once per group of members on the same grid
+ * (the FFT kernels are specialised by length).  Every member computes exactly
+ * what evp_step computes for it alone (bit for bit).  Steps replay a CUDA graph
+ * per membership, dt and buffer parity (captured on first use).
+ * Members: RK3 states with a stress (Oldroyd-B, FENE-P, Saramito) of the
+ * batch's precision, without penalisation, particles, soft particles, the
+ * implicit viscous option or artificial diffusion; at most 64 members.  While a
+ * state is a member its evp_step / evp_substep return EVP_ERR_STATE; field
+ * copies and evp_sync on it first wait for the batch's stream.               */
+typedef struct evp_batch_s evp_batch;
+
+/* Tile configuration of the batched kernels for one grid: z planes per work item
+ * of the stress and momentum kernels, resident CTAs per SM of their persistent
+ * grids (at most 2 and 4 in FP32, 1 and 2 in FP64), and kx columns per block of
+ * the column FFT passes (4, 8 or 16; 16 only in FP32).  0 in a field: the
+ * default (the heuristic of the single-state launches).                       */
+typedef struct {
+    int stress_kz, momentum_kz;
+    int stress_ctas_per_sm, momentum_ctas_per_sm;
+    int fft_cols;
+} evp_tile_config;
+
+/* Create an empty batch.  precision: EVP_FP64 or EVP_FP32, of every member.
+ * budget_bytes: admission limit on the sum of the members' evp_state_bytes (0:
+ * none).  stream: a cudaStream_t the batch runs on, or NULL to create one.   */
+int evp_batch_create(int precision, size_t budget_bytes, void* stream, evp_batch** out);
+/* Add a state with its time step dt.  Waits for the state's stream.  Errors:
+ * EVP_ERR_ARG (state not eligible, see above, or already a member of a batch),
+ * EVP_ERR_OOM (budget or member count exceeded; nothing changes).             */
+int evp_batch_admit(evp_batch* b, evp_state* s, double dt);
+/* Remove a member (waits for the batch's stream); the state stays valid and
+ * can step on its own again.  EVP_ERR_ARG if it is not a member.              */
+int evp_batch_evict(evp_batch* b, evp_state* s);
+/* One RK3 step of every member, asynchronous on the batch's stream.           */
+int evp_batch_step(evp_batch* b);
+/* Members and bytes admitted (either pointer may be NULL).                    */
+int evp_batch_info(const evp_batch* b, int* members, size_t* bytes);
+/* Replay steps from CUDA graphs (1, the default) or launch them directly (0). */
+int evp_batch_set_graph(evp_batch* b, int enable);
+/* Evict every member, release the batch (and its stream if it created it).    */
+int evp_batch_destroy(evp_batch* b);
+
+/* Self-written tile autotuner: times batched steps of a scratch state of this
+ * grid, model and parameters (one member, B = I and a smooth solenoidal
+ * velocity) under candidate tile configurations and keeps the fastest in a
+ * process-wide table keyed by (grid, precision, model), which batches use for
+ * members on that grid from their next membership change on.
+ *   exhaustive = 0: coordinate descent over the five fields, each swept with the
+ *   others held, twice round; 1: every combination.  best receives the chosen
+ *   configuration, best_ms its time per step, trials the configurations timed.
+ * Synchronous; allocates a scratch state.                                     */
+int evp_tune(const evp_grid* grid, evp_model model, const evp_params* params, int exhaustive,
+             evp_tile_config* best, double* best_ms, int* trials);
+/* Time per step (ms, median of 3 runs of `steps` graph-replayed steps) of the
+ * scratch one-member batch of evp_tune under one configuration.  Synchronous.  */
+int evp_tile_time(const evp_grid* grid, evp_model model, const evp_params* params, const evp_tile_config* cfg,
+                  int steps, double* ms_per_step);
+/* The configuration batches use for this grid: the tuned (or set) one, else the
+ * default with every field filled in.                                         */
+int evp_tile_config_get(const evp_grid* grid, int precision, evp_model model, evp_tile_config* out);
+/* Put a configuration in the table (zero fields: defaults); all fields zero
+ * removes the grid's entry.  Batches pick it up at their next membership
+ * change.  EVP_ERR_ARG when a field is out of range.                          */
+int evp_tile_config_set(const evp_grid* grid, int precision, evp_model model, const evp_tile_config* cfg);
+
 /* Measured peak of the plain (non-tensor) FMA pipe of the current device, the
  * roofline of arithmetic-bound kernels (the paper has no counterpart): every
  * thread of 8 blocks per SM runs eight independent chains of fused multiply-adds

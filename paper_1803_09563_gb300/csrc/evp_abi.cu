@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "evp_internal.cuh"
+#include "evp_state.cuh"
 
 using namespace evp;
 
@@ -32,10 +33,6 @@ int cuda_fail(cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
     } while (0)
 
-// Wray's low-storage RK3 constants (Eq. RK)
-const double RK_ALPHA[3] = {4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0};
-const double RK_ZETA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
-const double RK_XI[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 
 const char* KERNEL_NAMES[K_COUNT] = {"stress_weno_update", "momentum_predictor", "div_fft_x",
                                      "fft_z_forward",      "fft_y_modal_solve",  "thomas_y_fp64",
@@ -58,91 +55,6 @@ namespace evp {
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace evp
 
-struct evp_state_s {
-    evp_grid g;
-    evp_model model;
-    evp_params prm;
-    bool fp32;
-    size_t elt;          // bytes per element
-    size_t N;            // cells
-    int nxh;
-    cudaStream_t st;
-    bool own_stream;
-    char* arena;
-    size_t arena_bytes;
-    bool own_arena;
-    // field storage (element type = precision)
-    void* U[2];
-    void* V[2];
-    void* W[2];
-    void* B[2][6];
-    void* RT[6];
-    void* NH[3];
-    void* S[6];          // RK3 with a stress (not soft particles): tau^k + tau^{k-1}, stress -> momentum
-    void* P;
-    void* PSI;
-    void* spec;
-    // tables
-    void* twx;
-    void* twy;
-    void* twz;
-    void* lamx;
-    void* lamy;
-    void* lamz;
-    void* trig;
-    double2* thomas_m;
-    double* thomas_d;
-    unsigned* d_status;
-    unsigned long long* d_maxdiv;
-    // two-phase (AB2) fields
-    bool ab2;
-    void* PHI;
-    void* PHI0;
-    void* PHIA;
-    void* PHIB;
-    void* HF;
-    void* NRM[3];
-    void* FC[3];
-    void* SOL[3];        // penalization: solid fractions at the velocity nodes
-    void* POLD;          // AB2 with a density contrast: p^{n-1}
-    double* partials;
-    double* mean_1mH;
-    double* mass;        // mass correction: 2 x block partials, v0, d
-    void* PHS[2];        // soft particles: solid fraction, buffer cb = current level
-    void* PHSH;          // soft particles: history of its right-hand side
-    double2* helm[3][2]; // implicit viscous, walls: Thomas tables per substep, (u/w, v)
-    double helm_dt;      // dt the Helmholtz tables were built for
-    // rigid particles (discrete-forcing IBM): one device block holding the arrays below
-    int n_part, n_lag, ibm_iters;
-    void* ibm_block;
-    double *i_off, *i_dvl, *i_centre, *i_vel, *i_omg, *i_Facc, *i_dF, *i_force, *i_rad, *i_dens, *i_int;
-    int *i_owner, *i_start;
-    int any_free;
-    long long nstep;     // AB2 steps taken
-    int cu, cb;          // current velocity / B buffer
-    // CUDA-graph replay of evp_step: one executable graph per parity of the B
-    // buffer at the start of the step (the three substeps flip it each time)
-    bool use_graph;
-    bool pdl;            // programmatic dependent launch of the step's kernels
-    struct StepGraph {
-        bool valid;
-        double dt;
-        int cb_after;
-        cudaGraphExec_t exec;
-    } graphs[2];
-    ModelConst mc;
-    // timing
-    bool timing;
-    std::vector<cudaEvent_t> ev_free;
-    struct Pend {
-        int kid;
-        cudaEvent_t a, b;
-    };
-    std::vector<Pend> pending;
-    cudaEvent_t cur_start;
-    double ms[K_COUNT];
-    long long launches[K_COUNT];
-};
 
 namespace {
 
@@ -405,43 +317,8 @@ int upload_tables(evp_state* s) {
     return cudaStreamSynchronize(s->st) == cudaSuccess ? EVP_OK : cuda_fail(cudaGetLastError(), "tables");
 }
 
-template <typename T>
-Geo<T> geo_of(const evp_state* s) {
-    Geo<T> g;
-    g.nx = s->g.nx;
-    g.ny = s->g.ny;
-    g.nz = s->g.nz;
-    g.walls = s->g.walls_y;
-    g.idx = T(s->g.nx / s->g.lx);
-    g.idy = T(s->g.ny / s->g.ly);
-    g.idz = T(s->g.nz / s->g.lz);
-    return g;
-}
 
-template <typename T>
-FFTTables<T> tables_of(const evp_state* s) {
-    using CT = typename Cplx<T>::type;
-    FFTTables<T> t;
-    t.twx = static_cast<const CT*>(s->twx);
-    t.twy = static_cast<const CT*>(s->twy);
-    t.twz = static_cast<const CT*>(s->twz);
-    t.nrx = fft_radices(s->g.nx, t.radx);
-    t.nry = s->g.walls_y ? 0 : fft_radices(s->g.ny, t.rady);
-    t.nrz = fft_radices(s->g.nz, t.radz);
-    t.lamx = static_cast<const T*>(s->lamx);
-    t.lamy = static_cast<const T*>(s->lamy);
-    t.lamz = static_cast<const T*>(s->lamz);
-    t.thomas_m = s->thomas_m;
-    const double dy = s->g.ly / s->g.ny;
-    t.idy2 = 1.0 / (dy * dy);
-    return t;
-}
 
-template <typename T>
-double poisson_norm(const evp_state* s) {
-    const evp_grid& g = s->g;
-    return g.walls_y ? 1.0 / (double(g.nx) * g.nz) : 1.0 / (double(g.nx) * g.ny * g.nz);
-}
 
 template <typename T>
 int run_poisson(evp_state* s, const T* Us, const T* Vs, const T* Ws, const T* rhs, double rscale, T* psi) {
@@ -930,6 +807,8 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
     s->elt = s->fp32 ? 4 : 8;
     s->use_graph = false;
     s->pdl = true;
+    s->batch = nullptr;
+    s->batch_st = nullptr;
     s->n_part = s->n_lag = 0;
     s->ibm_iters = 3;
     s->ibm_block = nullptr;
@@ -1007,6 +886,7 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
 
 int evp_destroy(evp_state* s) {
     if (!s) return EVP_OK;
+    if (s->batch) evp_batch_evict(static_cast<evp_batch*>(s->batch), s);
     if (s->st) cudaStreamSynchronize(s->st);
     if (s->ibm_block) cudaFree(s->ibm_block);
     for (auto& p : s->pending) {
@@ -1043,8 +923,18 @@ int take_field(evp_state* s, int field, void* dst, int dst_on_device, cudaStream
 }
 }  // namespace
 
+namespace {
+// a batch member's steps run on the batch's stream: wait for them before touching
+// the state from its own stream
+int wait_batch(evp_state* s) {
+    if (s->batch) CK(cudaStreamSynchronize(s->batch_st));
+    return EVP_OK;
+}
+}  // namespace
+
 int evp_set_field(evp_state* s, int field, const void* src, int src_on_device) {
     if (!s || !src) return fail(EVP_ERR_ARG, "null state or source");
+    if (int r = wait_batch(s)) return r;
     if (field == EVP_PSI) return fail(EVP_ERR_ARG, "EVP_PSI is read only");
     if (!field_ptr(s, field)) return fail(EVP_ERR_ARG, "unknown field id");
     if (int r = put_field(s, field, src, src_on_device, s->st)) return r;
@@ -1054,6 +944,7 @@ int evp_set_field(evp_state* s, int field, const void* src, int src_on_device) {
 
 int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device) {
     if (!s || !dst) return fail(EVP_ERR_ARG, "null state or destination");
+    if (int r = wait_batch(s)) return r;
     if (!field_ptr(s, field)) return fail(EVP_ERR_ARG, "unknown field id");
     if (int r = take_field(s, field, dst, dst_on_device, s->st)) return r;
     CK(cudaStreamSynchronize(s->st));
@@ -1062,6 +953,7 @@ int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device) {
 
 int evp_set_fields(evp_state* s, int n, const int* fields, const void* const* srcs, int src_on_device) {
     if (!s || n < 0 || (n > 0 && (!fields || !srcs))) return fail(EVP_ERR_ARG, "null state or arrays, or n < 0");
+    if (int r = wait_batch(s)) return r;
     for (int i = 0; i < n; ++i) {
         if (!srcs[i]) return fail(EVP_ERR_ARG, "null source buffer");
         if (fields[i] == EVP_PSI) return fail(EVP_ERR_ARG, "EVP_PSI is read only");
@@ -1075,6 +967,7 @@ int evp_set_fields(evp_state* s, int n, const int* fields, const void* const* sr
 
 int evp_get_fields(evp_state* s, int n, const int* fields, void* const* dsts, int dst_on_device) {
     if (!s || n < 0 || (n > 0 && (!fields || !dsts))) return fail(EVP_ERR_ARG, "null state or arrays, or n < 0");
+    if (int r = wait_batch(s)) return r;
     for (int i = 0; i < n; ++i) {
         if (!dsts[i]) return fail(EVP_ERR_ARG, "null destination buffer");
         if (!field_ptr(s, fields[i])) return fail(EVP_ERR_ARG, "unknown field id");
@@ -1087,6 +980,7 @@ int evp_get_fields(evp_state* s, int n, const int* fields, void* const* dsts, in
 
 int evp_substep(evp_state* s, double dt, int k) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (s->batch) return fail(EVP_ERR_STATE, "the state is a member of a batch: it steps with evp_batch_step");
     if (s->ab2) return fail(EVP_ERR_STATE, "evp_substep is an RK3 call; this state integrates with AB2");
     if (k < 0 || k > 2) return fail(EVP_ERR_ARG, "substep index must be 0, 1 or 2");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
@@ -1288,6 +1182,7 @@ extern "C" int evp_get_particles(evp_state* s, int n, double* out) {
 
 extern "C" int evp_step(evp_state* s, double dt) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (s->batch) return fail(EVP_ERR_STATE, "the state is a member of a batch: it steps with evp_batch_step");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
     if (int r = prepare_helmholtz(s, dt)) return r;
     if (s->ab2) return s->fp32 ? ab2_step_t<float>(s, dt) : ab2_step_t<double>(s, dt);
@@ -1301,6 +1196,7 @@ extern "C" int evp_step(evp_state* s, double dt) {
 
 int evp_project(evp_state* s) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (int r = wait_batch(s)) return r;
     const int cu = s->cu;
     int r;
     if (s->fp32) {
@@ -1323,6 +1219,7 @@ int evp_project(evp_state* s) {
 
 int evp_poisson_solve(evp_state* s, const void* rhs, void* psi) {
     if (!s || !rhs || !psi) return fail(EVP_ERR_ARG, "null argument");
+    if (int r = wait_batch(s)) return r;
     if (s->fp32) return run_poisson<float>(s, nullptr, nullptr, nullptr, (const float*)rhs, 1.0, (float*)psi);
     return run_poisson<double>(s, nullptr, nullptr, nullptr, (const double*)rhs, 1.0, (double*)psi);
 }
@@ -1330,6 +1227,7 @@ int evp_poisson_solve(evp_state* s, const void* rhs, void* psi) {
 int evp_stress_rhs(evp_state* s, void* rt) {
     if (!s || !rt) return fail(EVP_ERR_ARG, "null argument");
     if (s->model == EVP_NEWTONIAN) return fail(EVP_ERR_STATE, "a Newtonian state has no stress");
+    if (int r = wait_batch(s)) return r;
     auto go = [&](auto tag) -> int {
         using T = decltype(tag);
         StressArgs<T> a;
@@ -1358,6 +1256,7 @@ int evp_stress_rhs(evp_state* s, void* rt) {
 
 int evp_sync(evp_state* s, unsigned* bits, double* max_div) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
+    if (int r = wait_batch(s)) return r;
     if (max_div) {
         // FP64 max |div u| of the current (last projected) velocity
         CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));

@@ -374,6 +374,47 @@ struct SplitArgs {
     unsigned* status;
 };
 
+// ------------------------------------------------------------------- batches
+// A batch advances several states with one launch per kernel phase.  The members'
+// argument blocks travel in the kernel's parameter space (at most 32 KB), so a
+// launch holds at most EVP_BATCH_MAX members.
+constexpr int EVP_BATCH_MAX = 64;
+
+template <typename T>
+struct StressMember {
+    Geo<T> g;
+    ModelConst mc;
+    StressArgs<T> a;
+    int kz;            // z planes per work item
+};
+template <typename T>
+struct StressBatch {
+    StressMember<T> m[EVP_BATCH_MAX];
+};
+
+template <typename T>
+struct MomentumMember {
+    Geo<T> g;
+    ModelConst mc;
+    MomentumArgs<T> a;
+    int kz;
+};
+template <typename T>
+struct MomentumBatch {
+    MomentumMember<T> m[EVP_BATCH_MAX];
+};
+
+// Poisson passes and correction of members that share one grid (the FFT kernels
+// are specialised by length): member = blockIdx.z of the launch
+template <typename T>
+struct PoissonBatch {
+    PoissonArgs<T> a[EVP_BATCH_MAX];
+};
+template <typename T>
+struct CorrectBatch {
+    CorrectArgs<T> a[EVP_BATCH_MAX];
+};
+
 // ----------------------------------------------------------- launch functions
 // Each returns cudaSuccess or the launch error; ``t`` is a timing hook that
 // records events around the launch when enabled.
@@ -490,6 +531,33 @@ cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArg
 template <typename T>
 cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const MomentumArgs<T>& a,
                             cudaStream_t st, const TimingHook& th);
+
+// Batched launches.  work: device list of int4 (member, tile x, tile y, z chunk);
+// ctas: size of the persistent grid.  The stress batch holds members of one model
+// and one staging kind (vec: nx * sizeof(T) % 16 == 0); mode 1, 2, 3 as the
+// update modes of the stress kernel.  The momentum batch reads the summed stress.
+template <typename T>
+cudaError_t launch_stress_batch(const StressBatch<T>& p, int model, int mode, bool vec, const int4* work, int nwork,
+                                int ctas, cudaStream_t st);
+template <typename T>
+cudaError_t launch_momentum_batch(const MomentumBatch<T>& p, bool vec, const int4* work, int nwork, int ctas,
+                                  cudaStream_t st);
+// tiles and resident CTAs per SM of the z-marching kernels
+int stress_tile_x();
+int stress_tile_y();
+int momentum_tile_x();
+int momentum_tile_y();
+template <typename T>
+int stress_ctas_per_sm();
+template <typename T>
+int momentum_ctas_per_sm();
+// Poisson solve (divergence of u* as right-hand side) and correction of n members
+// that share grid g and tables tb; tk: kx columns per block of the column passes
+template <typename T>
+cudaError_t launch_poisson_batch(const Geo<T>& g, const FFTTables<T>& tb, const PoissonBatch<T>& p, int n, int tk,
+                                 cudaStream_t st);
+template <typename T>
+cudaError_t launch_correct_batch(const Geo<T>& g, const CorrectBatch<T>& p, int n, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a,

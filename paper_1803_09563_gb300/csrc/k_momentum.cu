@@ -89,16 +89,14 @@ __device__ __forceinline__ int vslot(int kk) { return (kk + 5) % 5; }   // kk >=
 
 // VEC: rows are staged in 16-byte chunks (needs nx * sizeof(T) % 16 == 0)
 // SPRE: the summed stress comes precomputed (MomentumArgs::S); MODEL is then unused
+// One tile: the 32 x 4 columns (bx, by) over the z chunk bz of kz_chunk planes.
 template <typename T, int MODEL, bool VEC, bool SPRE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2)
-k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_chunk) {
-    pdl_wait();
-    pdl_trigger();
-    extern __shared__ __align__(16) unsigned char smraw[];
+__device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst& mc, const MomentumArgs<T>& a,
+                                              int kz_chunk, int bx, int by, int bz, unsigned char* smraw) {
     MomSmemOf<T, SPRE>& sm = *reinterpret_cast<MomSmemOf<T, SPRE>*>(smraw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
+    const int i0 = bx * TX, j0 = by * TY;
+    const int k0 = bz * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
     const int i = i0 + tx, j = j0 + ty;
     const bool active = i < g.nx && j < g.ny;
     const size_t plane = (size_t)g.nx * g.ny;
@@ -526,6 +524,31 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     }
 }
 
+template <typename T, int MODEL, bool VEC, bool SPRE>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2)
+k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_chunk) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    momentum_tile<T, MODEL, VEC, SPRE>(g, mc, a, kz_chunk, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
+}
+
+// Batched form (summed stress precomputed): a persistent grid walks a work list
+// of (member, tile x, tile y, z chunk); members' grids may differ.
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2)
+k_momentum_batch(const __grid_constant__ MomentumBatch<T> p, const int4* __restrict__ work, int nwork) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int4 t = __ldg(work + w);
+        const MomentumMember<T>& m = p.m[t.x];
+        momentum_tile<T, EVP_OLDROYD_B, VEC, true>(m.g, m.mc, m.a, m.kz, t.y, t.z, t.w, smraw);
+        // the tile's last request (two planes past its chunk) may still be in flight
+        cp_async_wait_all();
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -574,6 +597,29 @@ cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const Momentu
     th.e(K_MOMENTUM);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_momentum_batch(const MomentumBatch<T>& p, bool vec, const int4* work, int nwork, int ctas,
+                                  cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    const size_t smem = sizeof(MomSmemS<T>);
+    const dim3 grid(ctas < nwork ? ctas : nwork), block(TX, TY, 1);
+    auto kern = vec ? k_momentum_batch<T, true> : k_momentum_batch<T, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return launch_k(kern, grid, block, smem, st, false, p, work, nwork);
+}
+
+int momentum_tile_x() { return TX; }
+int momentum_tile_y() { return TY; }
+template <typename T>
+int momentum_ctas_per_sm() { return sizeof(T) == 4 ? 4 : 2; }
+
+template cudaError_t launch_momentum_batch<float>(const MomentumBatch<float>&, bool, const int4*, int, int,
+                                                  cudaStream_t);
+template cudaError_t launch_momentum_batch<double>(const MomentumBatch<double>&, bool, const int4*, int, int,
+                                                   cudaStream_t);
+template int momentum_ctas_per_sm<float>();
+template int momentum_ctas_per_sm<double>();
 
 template cudaError_t launch_momentum<float>(const Geo<float>&, const ModelConst&, const MomentumArgs<float>&,
                                             cudaStream_t, const TimingHook&);

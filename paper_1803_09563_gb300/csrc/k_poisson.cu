@@ -160,8 +160,7 @@ __device__ __forceinline__ T div_value(const Geo<T>& g, const PoissonArgs<T>& a,
 
 // S4 + S5(x): r = div(u*)/(2 alpha dt) fused into the x real-to-complex FFT.
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_div_fftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
+__device__ __forceinline__ void k_div_fftx_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a, int np) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -201,11 +200,21 @@ k_div_fftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np
         }
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_div_fftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
+    k_div_fftx_body<T>(g, tb, a, np);
+}
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_div_fftx_b(const Geo<T> g, const FFTTables<T> tb, const __grid_constant__ PoissonBatch<T> p, int np) {
+    k_div_fftx_body<T>(g, tb, p.a[blockIdx.z], np);
+}
+
 
 // S7(x): complex-to-real inverse FFT along x of two lines per complex FFT -> psi
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_ifftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
+__device__ __forceinline__ void k_ifftx_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a, int np) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -246,13 +255,22 @@ k_ifftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
         }
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_ifftx(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int np) {
+    k_ifftx_body<T>(g, tb, a, np);
+}
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_ifftx_b(const Geo<T> g, const FFTTables<T> tb, const __grid_constant__ PoissonBatch<T> p, int np) {
+    k_ifftx_body<T>(g, tb, p.a[blockIdx.z], np);
+}
+
 
 // Column FFT along z (or y) over TK consecutive kx.  SOLVE (periodic y pass):
 // forward FFT, multiply by -norm/(lx+ly+lz) (zero mode -> 0), inverse FFT.
 template <typename T, bool INV, bool SOLVE>
-__global__ void __launch_bounds__(256)
-k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axis_y, size_t estride,
-          size_t ostride, int tk) {
+__device__ __forceinline__ void k_fft_col_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a, int axis_y, size_t estride, size_t ostride, int tk) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -298,6 +316,18 @@ k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axi
             if (kx < nxh) a.spec[base + m * estride + kx] = res[(size_t)m * tk + t];
         }
 }
+template <typename T, bool INV, bool SOLVE>
+__global__ void __launch_bounds__(256)
+k_fft_col(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axis_y, size_t estride,
+          size_t ostride, int tk) {
+    k_fft_col_body<T, INV, SOLVE>(g, tb, a, axis_y, estride, ostride, tk);
+}
+template <typename T, bool INV, bool SOLVE>
+__global__ void __launch_bounds__(256)
+k_fft_col_b(const Geo<T> g, const FFTTables<T> tb, const __grid_constant__ PoissonBatch<T> p, int axis_y, size_t estride, size_t ostride, int tk) {
+    k_fft_col_body<T, INV, SOLVE>(g, tb, p.a[blockIdx.z], axis_y, estride, ostride, tk);
+}
+
 
 // ---- register-resident column FFTs for n = R1 * R2 (powers of two, n <= 256)
 //
@@ -350,9 +380,7 @@ __device__ __forceinline__ void dft_reg(C<T> (&x)[R], const C<T>* __restrict__ t
 // inverse runs the two passes in reverse order, so its input is the forward
 // output as each thread holds it).
 template <typename T, bool INV, bool SOLVE, int R1, int R2>
-__global__ void __launch_bounds__(256)
-k_fft_col_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axis_y, size_t estride,
-            size_t ostride, int tk) {
+__device__ __forceinline__ void k_fft_col_r_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a, int axis_y, size_t estride, size_t ostride, int tk) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -418,14 +446,25 @@ k_fft_col_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int a
         for (int j1 = 0; j1 < R1; ++j1) a.spec[base + (size_t)(R2 * j1 + q) * estride] = x[j1];
     }
 }
+template <typename T, bool INV, bool SOLVE, int R1, int R2>
+__global__ void __launch_bounds__(256)
+k_fft_col_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a, int axis_y, size_t estride,
+            size_t ostride, int tk) {
+    k_fft_col_r_body<T, INV, SOLVE, R1, R2>(g, tb, a, axis_y, estride, ostride, tk);
+}
+template <typename T, bool INV, bool SOLVE, int R1, int R2>
+__global__ void __launch_bounds__(256)
+k_fft_col_r_b(const Geo<T> g, const FFTTables<T> tb, const __grid_constant__ PoissonBatch<T> p, int axis_y, size_t estride, size_t ostride, int tk) {
+    k_fft_col_r_body<T, INV, SOLVE, R1, R2>(g, tb, p.a[blockIdx.z], axis_y, estride, ostride, tk);
+}
+
 
 // S4 + S5(x) for nx = R1 R2 (powers of two, 16 .. 256), as k_div_fftx with the
 // two-pass register-resident FFT: threadIdx.y picks one of the block's complex lines
 // (real lines 2L and 2L+1), threadIdx.x = j2 (pass 1), k1 (pass 2), then m (split).
 // The exchange buffer of a line is R1 rows of R2+1 (padded against bank conflicts).
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256)
-k_div_fftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+__device__ __forceinline__ void k_div_fftx_r_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a) {
     pdl_wait();
     pdl_trigger();
     constexpr int n = R1 * R2, RM = R1 > R2 ? R1 : R2, LW = R1 * (R2 + 1);
@@ -489,11 +528,21 @@ k_div_fftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
         if (ok1) a.spec[(size_t)L1 * nxh + m] = mk<T>(T(0.5) * (Z.y + Zr.y), T(0.5) * (Zr.x - Z.x));
     }
 }
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(256)
+k_div_fftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+    k_div_fftx_r_body<T, R1, R2>(g, tb, a);
+}
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(256)
+k_div_fftx_r_b(const Geo<T> g, const FFTTables<T> tb, const __grid_constant__ PoissonBatch<T> p) {
+    k_div_fftx_r_body<T, R1, R2>(g, tb, p.a[blockIdx.z]);
+}
+
 
 // S7(x) for nx = R1 R2, as k_ifftx with the two-pass register-resident FFT.
 template <typename T, int R1, int R2>
-__global__ void __launch_bounds__(256)
-k_ifftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+__device__ __forceinline__ void k_ifftx_r_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a) {
     pdl_wait();
     pdl_trigger();
     constexpr int n = R1 * R2, LW = R1 * (R2 + 1), half = n / 2, nxh = n / 2 + 1;
@@ -542,6 +591,17 @@ k_ifftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
         if (ok1) a.psi[(size_t)L1 * n + i] = y[k2].y * a.out_scale;
     }
 }
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(256)
+k_ifftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+    k_ifftx_r_body<T, R1, R2>(g, tb, a);
+}
+template <typename T, int R1, int R2>
+__global__ void __launch_bounds__(256)
+k_ifftx_r_b(const Geo<T> g, const FFTTables<T> tb, const __grid_constant__ PoissonBatch<T> p) {
+    k_ifftx_r_body<T, R1, R2>(g, tb, p.a[blockIdx.z]);
+}
+
 
 // S6 with walls: for each (kx, kz) solve
 //   psi_{j-1}/dy^2 - (2/dy^2 + lx + lz) psi_j + psi_{j+1}/dy^2 = r_j
@@ -555,8 +615,7 @@ k_ifftx_r(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
 // not wait on a memory round trip per row; rows that do not fill a batch are
 // done one by one.  The FFT normalisation is applied later, in the inverse x pass.
 template <typename T>
-__global__ void __launch_bounds__(32)
-k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+__device__ __forceinline__ void k_thomas_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a) {
     pdl_wait();
     pdl_trigger();
     constexpr int TB = 16;
@@ -664,6 +723,17 @@ k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
         }
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_thomas(const Geo<T> g, const FFTTables<T> tb, const PoissonArgs<T> a) {
+    k_thomas_body<T>(g, tb, a);
+}
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_thomas_b(const Geo<T> g, const FFTTables<T> tb, const __grid_constant__ PoissonBatch<T> p) {
+    k_thomas_body<T>(g, tb, p.a[blockIdx.z]);
+}
+
 
 // S8: u^k = u* - c grad psi at the faces, p += psi; non-finite results raise
 // EVP_BIT_NONFINITE.  One thread per pair of x-adjacent cells (nx is even): its
@@ -681,14 +751,12 @@ struct Pair<double> {
     using type = double2;
 };
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_correct(const Geo<T> g, const CorrectArgs<T> a) {
+__device__ __forceinline__ void k_correct_body(const Geo<T>& g, const CorrectArgs<T>& a, int k) {
     using V = typename Pair<T>::type;
     pdl_wait();
     pdl_trigger();
     const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
     unsigned bits = 0;
     if (i < g.nx && j < g.ny) {
         const T c = a.coef;
@@ -725,6 +793,19 @@ k_correct(const Geo<T> g, const CorrectArgs<T> a) {
     bits = __reduce_or_sync(0xffffffffu, bits);
     if ((threadIdx.x & 31) == 0 && bits) atomicOr(a.status, bits);
 }
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_correct(const Geo<T> g, const CorrectArgs<T> a) {
+    k_correct_body<T>(g, a, blockIdx.z);
+}
+// batch: blockIdx.z = member * nz + plane
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_correct_b(const Geo<T> g, const __grid_constant__ CorrectBatch<T> p) {
+    const int mb = blockIdx.z / g.nz;
+    k_correct_body<T>(g, p.a[mb], blockIdx.z - mb * g.nz);
+}
+
 
 // FP64 max |div u| of a stored staggered velocity: per cell
 // (u_i - u_{i-1})/dx + (v_j - v_{j-1})/dy + (w_k - w_{k-1})/dz, the FP32 values
@@ -807,46 +888,59 @@ void set_smem(const void* f, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Launch of one pass, single or batched.  Single: the state's arguments by value,
+// with programmatic dependent launch when asked.  Batched (pb non-null): the same
+// kernel's batched form with the members' arguments in parameter space and
+// grid.z = members (the single launches use grid.z = 1).
+template <typename T>
+struct PassLaunch {
+    const PoissonArgs<T>* a;
+    const PoissonBatch<T>* pb;
+    int nb;
+    cudaStream_t st;
+    bool pdl;
+    template <typename KS, typename KB, typename... R>
+    cudaError_t go(KS ks, KB kb, dim3 grid, dim3 block, size_t smem, const Geo<T>& g, const FFTTables<T>& tb,
+                   R... rest) const {
+        if (pb) {
+            set_smem<T>((const void*)kb, smem);
+            return launch_k(kb, dim3(grid.x, grid.y, nb), block, smem, st, false, g, tb, *pb, rest...);
+        }
+        set_smem<T>((const void*)ks, smem);
+        return launch_k(ks, grid, block, smem, st, pdl, g, tb, *a, rest...);
+    }
+};
+
 // Column FFT pass of length n along z (axis_y 0) or y (1) over tk consecutive kx
 // per block and one block row per grid.y: the register-resident two-pass kernel
 // for n = 16 .. 256 (powers of two), else the Stockham kernel.
 template <typename T, bool INV, bool SOLVE>
-cudaError_t launch_col(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a, int n, int axis_y,
-                       size_t estride, size_t ostride, int tk, unsigned rows, cudaStream_t st, bool pdl) {
+cudaError_t launch_col(const Geo<T>& g, const FFTTables<T>& tb, const PassLaunch<T>& L, int n, int axis_y,
+                       size_t estride, size_t ostride, int tk, unsigned rows) {
     const int nxh = g.nx / 2 + 1;
     const dim3 grid((nxh + tk - 1) / tk, rows);
-    auto go = [&](auto kern, int r1, int r2) {
-        const size_t sm = (size_t)n * tk * sizeof(C<T>);
-        set_smem<T>((const void*)kern, sm);
-        return launch_k(kern, grid, dim3(tk, r1 > r2 ? r1 : r2), sm, st, pdl, g, tb, a, axis_y, estride, ostride, tk);
-    };
+    const size_t smr = (size_t)n * tk * sizeof(C<T>);
+#define EVP_COL_R(R1, R2)                                                                                      \
+    L.go(k_fft_col_r<T, INV, SOLVE, R1, R2>, k_fft_col_r_b<T, INV, SOLVE, R1, R2>, grid, dim3(tk, R1 > R2 ? R1 : R2), \
+         smr, g, tb, axis_y, estride, ostride, tk)
     switch (n) {
-        case 16: return go(k_fft_col_r<T, INV, SOLVE, 4, 4>, 4, 4);
-        case 32: return go(k_fft_col_r<T, INV, SOLVE, 4, 8>, 4, 8);
-        case 64: return go(k_fft_col_r<T, INV, SOLVE, 8, 8>, 8, 8);
-        case 128: return go(k_fft_col_r<T, INV, SOLVE, 8, 16>, 8, 16);
-        case 256: return go(k_fft_col_r<T, INV, SOLVE, 16, 16>, 16, 16);
+        case 16: return EVP_COL_R(4, 4);
+        case 32: return EVP_COL_R(4, 8);
+        case 64: return EVP_COL_R(8, 8);
+        case 128: return EVP_COL_R(8, 16);
+        case 256: return EVP_COL_R(16, 16);
         default: break;
     }
-    const size_t sm = col_smem<T>(n, tk);
-    set_smem<T>((const void*)k_fft_col<T, INV, SOLVE>, sm);
-    return launch_k(k_fft_col<T, INV, SOLVE>, grid, dim3(tk, 256 / tk), sm, st, pdl, g, tb, a, axis_y, estride,
-                    ostride, tk);
+#undef EVP_COL_R
+    return L.go(k_fft_col<T, INV, SOLVE>, k_fft_col_b<T, INV, SOLVE>, grid, dim3(tk, 256 / tk), col_smem<T>(n, tk), g,
+                tb, axis_y, estride, ostride, tk);
 }
 
-}  // namespace
-
-int fft_radices(int n, int* rad) {
-    int s = 0;
-    while (n % 4 == 0 && n > 2) { rad[s++] = 4; n /= 4; }
-    while (n % 3 == 0) { rad[s++] = 3; n /= 3; }
-    while (n % 2 == 0) { rad[s++] = 2; n /= 2; }
-    return n == 1 ? s : -1;
-}
-
+// The chain of Poisson passes (S4-S7): x pass with the right-hand side, z pass,
+// periodic y solve or FP64 Thomas sweep, inverse z and inverse x passes.
 template <typename T>
-cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a, cudaStream_t st,
-                           const TimingHook& th) {
+cudaError_t poisson_chain(const Geo<T>& g, const FFTTables<T>& tb, const PassLaunch<T>& L, int tk,
+                          const TimingHook& th) {
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = nx / 2 + 1;
     const int NL = ny * nz;
     // ---- x pass: np complex lines (2 np real lines) per block
@@ -872,37 +966,30 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
     const int xlines = xr1 ? (sizeof(T) == 4 ? 256 : 128) / xrm : 0;          // complex lines per block
     const dim3 bxr(xrm, xlines ? xlines : 1), gxr(xlines ? (npairs + xlines - 1) / xlines : 1);
     const size_t smxr = (size_t)xlines * xr1 * (xr2 + 1) * sizeof(C<T>);
-    auto go_x = [&](auto kern) {
-        set_smem<T>((const void*)kern, smxr);
-        return launch_k(kern, gxr, bxr, smxr, st, th.pdl, g, tb, a);
-    };
     th.b(K_DIV_FFTX);
     {
         cudaError_t e;
+#define EVP_X_R(K, R1, R2) L.go(K<T, R1, R2>, K##_b<T, R1, R2>, gxr, bxr, smxr, g, tb)
         switch (nx) {
-            case 16: e = go_x(k_div_fftx_r<T, 4, 4>); break;
-            case 32: e = go_x(k_div_fftx_r<T, 4, 8>); break;
-            case 64: e = go_x(k_div_fftx_r<T, 8, 8>); break;
-            case 128: e = go_x(k_div_fftx_r<T, 8, 16>); break;
-            case 256: e = go_x(k_div_fftx_r<T, 16, 16>); break;
-            default:
-                set_smem<T>((const void*)k_div_fftx<T>, smx);
-                e = launch_k(k_div_fftx<T>, gx, bx, smx, st, th.pdl, g, tb, a, np);
+            case 16: e = EVP_X_R(k_div_fftx_r, 4, 4); break;
+            case 32: e = EVP_X_R(k_div_fftx_r, 4, 8); break;
+            case 64: e = EVP_X_R(k_div_fftx_r, 8, 8); break;
+            case 128: e = EVP_X_R(k_div_fftx_r, 8, 16); break;
+            case 256: e = EVP_X_R(k_div_fftx_r, 16, 16); break;
+            default: e = L.go(k_div_fftx<T>, k_div_fftx_b<T>, gx, bx, smx, g, tb, np);
         }
         if (e) return e;
     }
     th.e(K_DIV_FFTX);
 
-    const int tk = sizeof(T) == 4 ? 16 : 8;
     // ---- forward z
     th.b(K_FFT_Z_FWD);
-    if (cudaError_t e = launch_col<T, false, false>(g, tb, a, nz, 0, (size_t)ny * nxh, (size_t)nxh, tk, ny, st, th.pdl))
+    if (cudaError_t e = launch_col<T, false, false>(g, tb, L, nz, 0, (size_t)ny * nxh, (size_t)nxh, tk, ny))
         return e;
     th.e(K_FFT_Z_FWD);
     if (!g.walls) {
         th.b(K_SOLVE_Y);
-        if (cudaError_t e = launch_col<T, false, true>(g, tb, a, ny, 1, (size_t)nxh, (size_t)ny * nxh, tk, nz, st,
-                                                       th.pdl))
+        if (cudaError_t e = launch_col<T, false, true>(g, tb, L, ny, 1, (size_t)nxh, (size_t)ny * nxh, tk, nz))
             return e;
         th.e(K_SOLVE_Y);
     } else {
@@ -911,31 +998,57 @@ cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const Poisso
         const int chains = 2 * nxh * nz;
         dim3 gt((chains + tt - 1) / tt);
         th.b(K_THOMAS);
-        if (cudaError_t e = launch_k(k_thomas<T>, gt, dim3(tt), 0, st, th.pdl, g, tb, a)) return e;
+        if (cudaError_t e = L.go(k_thomas<T>, k_thomas_b<T>, gt, dim3(tt), 0, g, tb)) return e;
         th.e(K_THOMAS);
     }
     // ---- inverse z
     th.b(K_FFT_Z_INV);
-    if (cudaError_t e = launch_col<T, true, false>(g, tb, a, nz, 0, (size_t)ny * nxh, (size_t)nxh, tk, ny, st, th.pdl))
+    if (cudaError_t e = launch_col<T, true, false>(g, tb, L, nz, 0, (size_t)ny * nxh, (size_t)nxh, tk, ny))
         return e;
     th.e(K_FFT_Z_INV);
     th.b(K_IFFTX);
     {
         cudaError_t e;
         switch (nx) {
-            case 16: e = go_x(k_ifftx_r<T, 4, 4>); break;
-            case 32: e = go_x(k_ifftx_r<T, 4, 8>); break;
-            case 64: e = go_x(k_ifftx_r<T, 8, 8>); break;
-            case 128: e = go_x(k_ifftx_r<T, 8, 16>); break;
-            case 256: e = go_x(k_ifftx_r<T, 16, 16>); break;
-            default:
-                set_smem<T>((const void*)k_ifftx<T>, smx);
-                e = launch_k(k_ifftx<T>, gx, bx, smx, st, th.pdl, g, tb, a, np);
+            case 16: e = EVP_X_R(k_ifftx_r, 4, 4); break;
+            case 32: e = EVP_X_R(k_ifftx_r, 4, 8); break;
+            case 64: e = EVP_X_R(k_ifftx_r, 8, 8); break;
+            case 128: e = EVP_X_R(k_ifftx_r, 8, 16); break;
+            case 256: e = EVP_X_R(k_ifftx_r, 16, 16); break;
+            default: e = L.go(k_ifftx<T>, k_ifftx_b<T>, gx, bx, smx, g, tb, np);
         }
+#undef EVP_X_R
         if (e) return e;
     }
     th.e(K_IFFTX);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+int fft_radices(int n, int* rad) {
+    int s = 0;
+    while (n % 4 == 0 && n > 2) { rad[s++] = 4; n /= 4; }
+    while (n % 3 == 0) { rad[s++] = 3; n /= 3; }
+    while (n % 2 == 0) { rad[s++] = 2; n /= 2; }
+    return n == 1 ? s : -1;
+}
+
+template <typename T>
+cudaError_t launch_poisson(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a, cudaStream_t st,
+                           const TimingHook& th) {
+    const PassLaunch<T> L{&a, nullptr, 1, st, th.pdl};
+    return poisson_chain<T>(g, tb, L, sizeof(T) == 4 ? 16 : 8, th);
+}
+
+template <typename T>
+cudaError_t launch_poisson_batch(const Geo<T>& g, const FFTTables<T>& tb, const PoissonBatch<T>& p, int n, int tk,
+                                 cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (n > EVP_BATCH_MAX) return cudaErrorInvalidValue;
+    const PassLaunch<T> L{nullptr, &p, n, st, false};
+    const TimingHook none{nullptr, nullptr, nullptr};
+    return poisson_chain<T>(g, tb, L, tk, none);
 }
 
 template <typename T>
@@ -970,6 +1083,21 @@ template cudaError_t launch_poisson<float>(const Geo<float>&, const FFTTables<fl
                                            cudaStream_t, const TimingHook&);
 template cudaError_t launch_poisson<double>(const Geo<double>&, const FFTTables<double>&,
                                             const PoissonArgs<double>&, cudaStream_t, const TimingHook&);
+template <typename T>
+cudaError_t launch_correct_batch(const Geo<T>& g, const CorrectBatch<T>& p, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    dim3 block(32, 8, 1);
+    dim3 grid((g.nx / 2 + 31) / 32, (g.ny + 7) / 8, g.nz * n);
+    return launch_k(k_correct_b<T>, grid, block, 0, st, false, g, p);
+}
+
+template cudaError_t launch_poisson_batch<float>(const Geo<float>&, const FFTTables<float>&,
+                                                 const PoissonBatch<float>&, int, int, cudaStream_t);
+template cudaError_t launch_poisson_batch<double>(const Geo<double>&, const FFTTables<double>&,
+                                                  const PoissonBatch<double>&, int, int, cudaStream_t);
+template cudaError_t launch_correct_batch<float>(const Geo<float>&, const CorrectBatch<float>&, int, cudaStream_t);
+template cudaError_t launch_correct_batch<double>(const Geo<double>&, const CorrectBatch<double>&, int,
+                                                  cudaStream_t);
 template cudaError_t launch_correct<float>(const Geo<float>&, const CorrectArgs<float>&, cudaStream_t,
                                            const TimingHook&);
 template cudaError_t launch_correct<double>(const Geo<double>&, const CorrectArgs<double>&, cudaStream_t,

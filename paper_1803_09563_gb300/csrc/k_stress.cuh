@@ -117,17 +117,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // 3 = update reading the history without writing it (last RK3 substep).
 // DIFF: the local artificial diffusion is on (ModelConst::art_diff > 0).
 // VEC: planes are staged in 16-byte chunks (needs nx * sizeof(T) % 16 == 0).
+// One tile: the 32 x 8 columns (bx, by) over the z chunk bz of kz_chunk planes.
 template <typename T, int MODEL, int MODE, bool DIFF, bool VEC>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
-k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chunk) {
+__device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a,
+                                            int kz_chunk, int bx, int by, int bz, unsigned char* smraw) {
     constexpr bool RHS_ONLY = MODE == 0, READ_H = MODE >= 2, WRITE_H = MODE == 1 || MODE == 2;
-    pdl_wait();
-    pdl_trigger();
-    extern __shared__ __align__(16) unsigned char smraw[];
     StressSmem<T>& sm = *reinterpret_cast<StressSmem<T>*>(smraw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int k0 = blockIdx.z * kz_chunk;
+    const int i0 = bx * TX, j0 = by * TY;
+    const int k0 = bz * kz_chunk;
     const int k1 = min(k0 + kz_chunk, g.nz);
     const int i = i0 + tx, j = j0 + ty;
     const bool active = (i < g.nx) && (j < g.ny);
@@ -585,6 +583,30 @@ k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chun
     if (bits) atomicOr(a.status, bits);
 }
 
+template <typename T, int MODEL, int MODE, bool DIFF, bool VEC>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+k_stress(const Geo<T> g, const ModelConst mc, const StressArgs<T> a, int kz_chunk) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    stress_tile<T, MODEL, MODE, DIFF, VEC>(g, mc, a, kz_chunk, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
+}
+
+// Batched form: a persistent grid walks a work list of (member, tile x, tile y,
+// z chunk) over the members of a batch, whose grids may differ; the members'
+// arguments sit in the kernel's parameter space.
+template <typename T, int MODEL, int MODE, bool DIFF, bool VEC>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+k_stress_batch(const __grid_constant__ StressBatch<T> p, const int4* __restrict__ work, int nwork) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int4 t = __ldg(work + w);
+        const StressMember<T>& m = p.m[t.x];
+        stress_tile<T, MODEL, MODE, DIFF, VEC>(m.g, m.mc, m.a, m.kz, t.y, t.z, t.w, smraw);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 template <typename T, bool VEC>
@@ -625,6 +647,41 @@ cudaError_t launch_stress_v(const Geo<T>& g, const ModelConst& mc, const StressA
     }
     return cudaSuccess;
 }
+
+// Batched stress update: one persistent launch over the work list (members of one
+// model, one mode and one staging kind, the caller groups them so).
+template <typename T>
+cudaError_t launch_stress_batch(const StressBatch<T>& p, int model, int mode, bool vec, const int4* work, int nwork,
+                                int ctas, cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    dim3 block(TX, TY, 1);
+    const size_t smem = sizeof(StressSmem<T>);
+    const dim3 grid(ctas < nwork ? ctas : nwork);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return launch_k(kern, grid, block, smem, st, false, p, work, nwork);
+    };
+    switch ((model * 4 + mode) * 2 + (vec ? 1 : 0)) {
+#define EVP_LAUNCH_STRESS_B(M, MD)                                            \
+    case (M * 4 + MD) * 2 + 0: return go(k_stress_batch<T, M, MD, false, false>); \
+    case (M * 4 + MD) * 2 + 1: return go(k_stress_batch<T, M, MD, false, true>);
+        EVP_LAUNCH_STRESS_B(EVP_OLDROYD_B, 1)
+        EVP_LAUNCH_STRESS_B(EVP_OLDROYD_B, 2)
+        EVP_LAUNCH_STRESS_B(EVP_OLDROYD_B, 3)
+        EVP_LAUNCH_STRESS_B(EVP_FENE_P, 1)
+        EVP_LAUNCH_STRESS_B(EVP_FENE_P, 2)
+        EVP_LAUNCH_STRESS_B(EVP_FENE_P, 3)
+        EVP_LAUNCH_STRESS_B(EVP_SARAMITO, 1)
+        EVP_LAUNCH_STRESS_B(EVP_SARAMITO, 2)
+        EVP_LAUNCH_STRESS_B(EVP_SARAMITO, 3)
+#undef EVP_LAUNCH_STRESS_B
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// resident CTAs of the stress kernel per SM (shared memory and registers)
+template <typename T>
+int stress_ctas_per_sm() { return sizeof(T) == 4 ? 2 : 1; }
 
 template <typename T>
 cudaError_t launch_stress(const Geo<T>& g, const ModelConst& mc, const StressArgs<T>& a,

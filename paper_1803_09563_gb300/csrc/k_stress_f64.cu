@@ -5,5 +5,8 @@ namespace evp {
 
 template cudaError_t launch_stress<double>(const Geo<double>&, const ModelConst&, const StressArgs<double>&,
                                         cudaStream_t, const TimingHook&);
+template cudaError_t launch_stress_batch<double>(const StressBatch<double>&, int, int, bool, const int4*, int, int,
+                                               cudaStream_t);
+template int stress_ctas_per_sm<double>();
 
 }  // namespace evp

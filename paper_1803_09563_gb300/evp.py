@@ -25,6 +25,7 @@ EVP_NEWTONIAN, EVP_OLDROYD_B, EVP_FENE_P, EVP_SARAMITO, EVP_NEO_HOOKEAN = range(
 MODEL_IDS = {'newtonian': 0, 'oldroyd_b': 1, 'fene_p': 2, 'saramito': 3, 'neo_hookean': 4}
 EVP_FP64, EVP_FP32 = 0, 1
 EVP_RK3, EVP_AB2 = 0, 1
+EVP_BATCH_MAX = 64   # members of one batch
 # evp_field
 EVP_U, EVP_V, EVP_W, EVP_P = 0, 1, 2, 3
 EVP_BXX, EVP_BXY, EVP_BXZ, EVP_BYY, EVP_BYZ, EVP_BZZ = range(4, 10)
@@ -54,6 +55,14 @@ class EvpError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f'libevp error {code}: {msg}')
         self.code = code
+
+
+class evp_tile_config(ctypes.Structure):
+    _fields_ = [('stress_kz', c_int), ('momentum_kz', c_int), ('stress_ctas_per_sm', c_int),
+                ('momentum_ctas_per_sm', c_int), ('fft_cols', c_int)]
+
+    def as_tuple(self):
+        return (self.stress_kz, self.momentum_kz, self.stress_ctas_per_sm, self.momentum_ctas_per_sm, self.fft_cols)
 
 
 _lib = None
@@ -91,6 +100,19 @@ def load(path=None):
         'evp_sync': (c_int, [c_void_p, POINTER(c_uint), POINTER(c_double)]),
         'evp_selftest': (c_int, [POINTER(c_ulonglong)]),
         'evp_fma_peak': (c_int, [c_int, POINTER(c_double)]),
+        'evp_batch_create': (c_int, [c_int, c_size_t, c_void_p, POINTER(c_void_p)]),
+        'evp_batch_admit': (c_int, [c_void_p, c_void_p, c_double]),
+        'evp_batch_evict': (c_int, [c_void_p, c_void_p]),
+        'evp_batch_step': (c_int, [c_void_p]),
+        'evp_batch_info': (c_int, [c_void_p, POINTER(c_int), POINTER(c_size_t)]),
+        'evp_batch_set_graph': (c_int, [c_void_p, c_int]),
+        'evp_batch_destroy': (c_int, [c_void_p]),
+        'evp_tune': (c_int, [POINTER(evp_grid), c_int, POINTER(evp_params), c_int, POINTER(evp_tile_config),
+                             POINTER(c_double), POINTER(c_int)]),
+        'evp_tile_time': (c_int, [POINTER(evp_grid), c_int, POINTER(evp_params), POINTER(evp_tile_config), c_int,
+                                  POINTER(c_double)]),
+        'evp_tile_config_get': (c_int, [POINTER(evp_grid), c_int, c_int, POINTER(evp_tile_config)]),
+        'evp_tile_config_set': (c_int, [POINTER(evp_grid), c_int, c_int, POINTER(evp_tile_config)]),
         'evp_kernel_timing': (c_int, [c_void_p, c_int]),
         'evp_kernel_times': (c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong), c_int]),
         'evp_kernel_name': (c_char_p, [c_int]),
@@ -111,7 +133,9 @@ def exported_symbols():
             'evp_substep', 'evp_project', 'evp_poisson_solve', 'evp_stress_rhs', 'evp_sync', 'evp_kernel_timing',
             'evp_kernel_times', 'evp_kernel_name', 'evp_num_kernels', 'evp_last_error', 'evp_poisson_solve_static',
             'evp_set_graph', 'evp_selftest', 'evp_set_pdl', 'evp_set_particles', 'evp_get_particles',
-            'evp_set_fields', 'evp_get_fields', 'evp_fma_peak']
+            'evp_set_fields', 'evp_get_fields', 'evp_fma_peak', 'evp_batch_create', 'evp_batch_admit',
+            'evp_batch_evict', 'evp_batch_step', 'evp_batch_info', 'evp_batch_set_graph', 'evp_batch_destroy',
+            'evp_tune', 'evp_tile_time', 'evp_tile_config_get', 'evp_tile_config_set']
 
 
 def _check(code):
@@ -285,6 +309,72 @@ def evp_fma_peak(precision):
     return r.value
 
 
+def evp_batch_create(precision, budget_bytes=0, stream=None):
+    h = c_void_p()
+    _check(load().evp_batch_create(int(precision), int(budget_bytes), stream, ctypes.byref(h)))
+    return h
+
+
+def evp_batch_admit(batch, state, dt):
+    return _check(load().evp_batch_admit(batch, state, float(dt)))
+
+
+def evp_batch_evict(batch, state):
+    return _check(load().evp_batch_evict(batch, state))
+
+
+def evp_batch_step(batch):
+    return _check(load().evp_batch_step(batch))
+
+
+def evp_batch_info(batch):
+    """(members, bytes admitted)"""
+    n, b = c_int(0), c_size_t(0)
+    _check(load().evp_batch_info(batch, ctypes.byref(n), ctypes.byref(b)))
+    return n.value, b.value
+
+
+def evp_batch_set_graph(batch, enable):
+    return _check(load().evp_batch_set_graph(batch, int(bool(enable))))
+
+
+def evp_batch_destroy(batch):
+    return _check(load().evp_batch_destroy(batch))
+
+
+def evp_tune(grid, model, params, exhaustive=False):
+    """(config, ms per step, trials) chosen by the library's autotuner for this grid."""
+    cfg, ms, n = evp_tile_config(), c_double(0.0), c_int(0)
+    m = MODEL_IDS[model] if isinstance(model, str) else int(model)
+    _check(load().evp_tune(ctypes.byref(grid), m, ctypes.byref(params), int(bool(exhaustive)), ctypes.byref(cfg),
+                           ctypes.byref(ms), ctypes.byref(n)))
+    return cfg, ms.value, n.value
+
+
+def evp_tile_time(grid, model, params, cfg, steps=20):
+    ms = c_double(0.0)
+    m = MODEL_IDS[model] if isinstance(model, str) else int(model)
+    if not isinstance(cfg, evp_tile_config):
+        cfg = evp_tile_config(*cfg)
+    _check(load().evp_tile_time(ctypes.byref(grid), m, ctypes.byref(params), ctypes.byref(cfg), int(steps),
+                                ctypes.byref(ms)))
+    return ms.value
+
+
+def evp_tile_config_get(grid, precision, model):
+    cfg = evp_tile_config()
+    m = MODEL_IDS[model] if isinstance(model, str) else int(model)
+    _check(load().evp_tile_config_get(ctypes.byref(grid), int(precision), m, ctypes.byref(cfg)))
+    return cfg
+
+
+def evp_tile_config_set(grid, precision, model, cfg):
+    m = MODEL_IDS[model] if isinstance(model, str) else int(model)
+    if not isinstance(cfg, evp_tile_config):
+        cfg = evp_tile_config(*cfg)
+    return _check(load().evp_tile_config_set(ctypes.byref(grid), int(precision), m, ctypes.byref(cfg)))
+
+
 def evp_selftest():
     """Failures of the integer-operation FP32 <-> FP64 conversions against the
     device's conversion instructions (0 expected)."""
@@ -371,3 +461,38 @@ class Simulation:
 
     def sync(self, raise_on_error=True):
         return evp_sync(self.handle, raise_on_error)
+
+
+class Batch:
+    """A libevp batch: member Simulations advance together, one RK3 step of each
+    member's dt per ``step()``."""
+
+    def __init__(self, precision, budget_bytes=0, stream=None):
+        self.handle = evp_batch_create(precision, budget_bytes, stream)
+        self.members = []
+
+    def admit(self, sim, dt):
+        evp_batch_admit(self.handle, sim.handle, dt)
+        self.members.append(sim)
+
+    def evict(self, sim):
+        evp_batch_evict(self.handle, sim.handle)
+        self.members.remove(sim)
+
+    def step(self):
+        evp_batch_step(self.handle)
+
+    def info(self):
+        return evp_batch_info(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            evp_batch_destroy(self.handle)
+            self.handle = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

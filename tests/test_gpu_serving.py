@@ -1,7 +1,8 @@
 """Serving form: continuous batching of simulations of different sizes and
-parameters.  Each request's result must be the same alone and in the mix
-(bitwise: the kernels are deterministic and share no state), admission must
-respect the HBM budget, and CUDA-graph replay must give the direct result."""
+parameters (one libevp batch per grid size, stepped as its previous step ends).
+Each request's result must be the same alone and in the mix (bitwise: every
+member's arithmetic is its own), admission must respect the HBM budget, and
+CUDA-graph replay must give the direct result."""
 
 import numpy as np
 import pytest
@@ -11,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 def small_mix():
     from paper_1803_09563_gb300 import serve
-    return serve.mixed_requests(6, seed=3, grids=(32, 48), steps=(4, 9), rate=2.0)
+    return serve.mixed_requests(8, seed=3, grids=(32, 48), steps=(4, 9), rate_per_ms=2.0)
 
 
 def test_result_alone_equals_result_in_the_mix(evp):
@@ -20,7 +21,7 @@ def test_result_alone_equals_result_in_the_mix(evp):
     mixed, rep = serve.Server(budget_bytes=8 << 30).run(reqs)
     assert rep['requests'] == len(reqs) and rep['max_resident'] > 1
     for r in reqs:
-        r0 = serve.Request(arrival_tick=0, rid=r.rid, n=r.n, Wi=r.Wi, Bi=r.Bi, beta=r.beta, steps=r.steps,
+        r0 = serve.Request(arrival_ms=0.0, rid=r.rid, n=r.n, Wi=r.Wi, Bi=r.Bi, beta=r.beta, steps=r.steps,
                            seed=r.seed)
         alone, _ = serve.Server(budget_bytes=8 << 30).run([r0])
         for f, a in alone[r.rid]['fields'].items():
@@ -31,7 +32,7 @@ def test_result_alone_equals_result_in_the_mix(evp):
 
 def test_admission_respects_the_budget(evp):
     from paper_1803_09563_gb300 import serve
-    reqs = [serve.Request(arrival_tick=0, rid=i, n=32, Wi=1.0, Bi=0.2, beta=0.5, steps=3, seed=i) for i in range(5)]
+    reqs = [serve.Request(arrival_ms=0.0, rid=i, n=32, Wi=1.0, Bi=0.2, beta=0.5, steps=3, seed=i) for i in range(5)]
     L = 2 * np.pi
     one = evp.evp_state_bytes(evp.make_grid(32, 32, 32, L, L, L), evp.EVP_SARAMITO,
                               evp.make_params(Re=100.0, Wi=1.0, beta=0.5, Bi=0.2, precision=evp.EVP_FP32))
@@ -60,3 +61,18 @@ def test_graph_replay_equals_direct_launches(evp):
         sim.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+def test_small_requests_do_not_wait_for_large_grids(evp):
+    """Each size class steps as soon as its own previous step ends: 32^3 requests
+    served beside a long 96^3 one see step latencies far below the 96^3 steps."""
+    from paper_1803_09563_gb300 import serve
+    reqs = [serve.Request(arrival_ms=0.0, rid=0, n=96, Wi=1.0, Bi=0.3, beta=0.5, steps=60, seed=1)]
+    reqs += [serve.Request(arrival_ms=0.5 * i, rid=1 + i, n=32, Wi=1.0, Bi=0.3, beta=0.5, steps=20, seed=2 + i)
+             for i in range(6)]
+    _, rep = serve.Server(budget_bytes=8 << 30, result_fields=()).run(reqs)
+    assert rep['requests'] == 7
+    small, big = rep['by_size']['32'], rep['by_size']['96']
+    assert small['request_steps'] == 6 * 20 and big['request_steps'] == 60
+    assert small['p50_ms'] < 0.5 * big['p50_ms'], rep['by_size']
+    assert rep['queue_p99_ms'] is not None
