@@ -166,6 +166,19 @@ def algorithmic_bytes(kernel, w, elt, walls):
     return 0, 1
 
 
+# Arithmetic of the method counted from its formulas (an FMA counts as two
+# operations, a division or square root as one), per cell:
+#  stress update, one substep: centre velocity and gradient 48, 18 WENO5
+#  reconstructions of 62 (5 differences, 3 candidates 13, smoothness indicators 30,
+#  weights and combination 14) = 1116, |u|/h 6, advection sums 12, upper-convected
+#  terms 66, Saramito closure 33, source and right-hand side 27, RK3 update 24:
+#  1332 in all;
+#  whole RK3 step: three times (stress 1332 + momentum predictor about 260 +
+#  Poisson chain and correction about 95) = about 5060.
+STRESS_FLOPS_PER_CELL = 1332
+STEP_FLOPS_PER_CELL = 5060
+
+
 def fusion_bytes(kernel, w, elt):
     """Bytes per step a kernel moves beyond the method's own words because of a
     fusion choice: the stress kernel writes the summed stress tau^k + tau^{k-1}
@@ -396,6 +409,19 @@ def run_gpu(args, rank, world, local_rank):
                      "traffic": traffic},
         "kernels": kern,
         "fma_peaks": fma,
+        "alu_roofline": {
+            "stress_weno_update": {"bound": "alu", "flops_per_cell": STRESS_FLOPS_PER_CELL,
+                                   "achieved": STRESS_FLOPS_PER_CELL * N / (kern['stress_weno_update']['ms_per_launch'] * 1e-3) / 1e12,
+                                   "peak": fma["fp32_tflops"], "unit": "TFLOP/s",
+                                   "frac": STRESS_FLOPS_PER_CELL * N / (kern['stress_weno_update']['ms_per_launch'] * 1e-3) / 1e12 / fma["fp32_tflops"],
+                                   "peak_kind": "measured FP32 FMA (evp_fma_peak)"}
+            if 'stress_weno_update' in kern else None,
+            "fp64_plain_step": {"bound": "alu", "flops_per_cell_step": STEP_FLOPS_PER_CELL,
+                                "achieved": STEP_FLOPS_PER_CELL * value64 * 1e6 / world / 1e12,
+                                "peak": fma["fp64_tflops"], "unit": "TFLOP/s",
+                                "frac": STEP_FLOPS_PER_CELL * value64 * 1e6 / world / 1e12 / fma["fp64_tflops"],
+                                "peak_kind": "measured FP64 FMA (evp_fma_peak)"},
+            "note": "operation counts from the method's formulas (FMA = 2), not from the instructions executed"},
         "cufft_reference": cufft_reference(ktimes),
         "kernel_timing": f"adjacent pass of {k_steps} steps with CUDA events around each launch on the library "
                          f"stream (direct launches); the timed region replays a CUDA graph per step",

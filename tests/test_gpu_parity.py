@@ -169,6 +169,39 @@ def test_rk3_step_fp32(evp, shape, model, extra):
     assert np.abs(got[3] - ref[3]).max() < bound
 
 
+# rows of 128 cells or more (several 32-wide tiles per row, 144 = 4.5 tiles)
+ROW_SHAPES = [(128, 12, 12, True), (128, 16, 8, False), (144, 10, 8, True)]
+
+
+@pytest.mark.parametrize("shape", ROW_SHAPES)
+@pytest.mark.parametrize("model,extra", [MODELS[2], MODELS[1]])
+def test_rk3_step_long_rows_fp64(evp, shape, model, extra):
+    """Two RK3 steps on long rows (walls: both wall rows and their ghost rules;
+    periodic: the seams) within 1e-10 of the oracle."""
+    dpdx = 0.05 if shape[3] else 0.0
+    force = (dpdx, 0.0, 0.0) if dpdx else None
+    sim, st, g, prm = setup_case(evp, shape, model, extra, evp.EVP_FP64, dpdx=dpdx)
+    dt = 2e-3
+    for _ in range(2):
+        sim.step(dt)
+        st = oracle.rk3_step(st, dt, g, prm, force)
+    sim.sync()
+    for got, ref in zip(fields(sim, evp), oracle_fields(st)):
+        assert rel(got, ref) < 1e-10
+
+
+@pytest.mark.parametrize("shape", ROW_SHAPES)
+def test_rk3_step_long_rows_fp32(evp, shape):
+    sim, st0, g, prm = setup_case(evp, shape, 'saramito', {'Bi': 0.4}, evp.EVP_FP32)
+    dt = 2e-3
+    sim.step(dt)
+    st = oracle.rk3_step(st0, dt, g, prm)
+    sim.sync()
+    for q, (a, b) in enumerate(zip(fields(sim, evp), oracle_fields(st))):
+        if q != 3:
+            assert rel(a, b) < 1e-5, (q, rel(a, b))
+
+
 def test_c1_ten_steps_fp64(evp):
     """Single-phase Oldroyd-B Taylor-Green box, 32^3, Re = 1, Wi = 1, beta = 0.5,
     10 RK3 steps of dt = 1e-3: every field within 1e-10 of the oracle."""
@@ -830,3 +863,27 @@ def test_rk3_step_extreme_lengths(evp, shape, prec):
         worst = max(worst, rel(got, ref))
         assert rel(got, ref) < (1e-10 if prec == 0 else 1e-5), (q, rel(got, ref))
     print('rk3 step', shape, prec, worst)
+
+
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[1]])
+def test_checkpoint_and_resume_bitwise_fp64(evp, shape):
+    """Checkpoint / resume of an RK3 state through the field copies: every field a
+    state holds (velocity, pressure, conformation, both histories) read after two
+    steps and written into a fresh state; both then take three more steps and agree
+    bit for bit."""
+    sim, st, g, prm = setup_case(evp, shape, 'saramito', {'Bi': 0.4}, evp.EVP_FP64, dpdx=0.05 if shape[3] else 0.0)
+    for _ in range(2):
+        sim.step(2e-3)
+    ids = [evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P] + [evp.EVP_BXX + c for c in range(6)]
+    ids += [evp.EVP_RT_XX + c for c in range(6)] + [evp.EVP_NH_X + c for c in range(3)]
+    saved = [sim.get(f) for f in ids]
+    twin = evp.Simulation(sim.grid, 'saramito', sim.params)
+    for f, a in zip(ids, saved):
+        twin.set(f, a)
+    for _ in range(3):
+        sim.step(2e-3)
+        twin.step(2e-3)
+    for f in ids:
+        assert np.array_equal(sim.get(f), twin.get(f)), f
+    twin.close()
+    sim.close()
