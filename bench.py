@@ -476,14 +476,14 @@ def cufft_reference(ktimes):
     return out
 
 
-def run_serving():
+def run_serving(requests=64):
     """Serving mix: a seeded Poisson stream (0.05 requests per ms, seed 3) of 64
     periodic Saramito requests, grids from {32, 48, 64, 96, 128}^3, Wi in U[0.5, 4],
     Bi in U[0, 1], beta in U[0.3, 0.9], random solenoidal velocity (|k| <= 4,
     max-norm 1), 100-1000 FP32 steps each, admitted under a 120 GB budget; one
     batch per grid size, its tiles autotuned before the run (untimed)."""
     from paper_1803_09563_gb300 import serve
-    reqs = serve.mixed_requests(64, seed=3, steps=(100, 1000), rate_per_ms=0.05)
+    reqs = serve.mixed_requests(64, seed=3, steps=(100, 1000), rate_per_ms=0.05)[:requests]
     prepared = {r.rid: serve.request_inputs(r) for r in reqs}      # client side, untimed
     srv = serve.Server(budget_bytes=120 * 10 ** 9, result_fields=(), tune=False)
     t0 = time.perf_counter()
@@ -748,6 +748,10 @@ def main():
     ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-extras', action='store_true', help='skip the serving-mix and small-grid sections')
+    ap.add_argument('--profile-case', default=None,
+                    help='profiling runs only: "channel-nz=<n>" (the channel workload with n z planes, no '
+                         'extras) or "serving=<n>" (the first n requests of the serving mix alone); prints the '
+                         'section\'s JSON')
     args = ap.parse_args()
     rank = int(os.environ.get('RANK', 0))
     world = int(os.environ.get('WORLD_SIZE', 1))
@@ -774,6 +778,21 @@ def main():
                 "config": {"workload": WORKLOAD['name']}, "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": "Mcell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
+        return
+
+    if args.profile_case:
+        # smaller cases for ncu captures (not bench lines)
+        kind, _, n = args.profile_case.partition('=')
+        if kind == 'serving':
+            print(json.dumps({"profile_case": args.profile_case, "serving": run_serving(requests=int(n))}))
+        elif kind == 'channel-nz':
+            WORKLOAD['nz'] = int(n)
+            WORKLOAD['lz'] = 2 * np.pi * int(n) / 128
+            WORKLOAD['name'] = f"saramito_channel_256x128x{int(n)}"
+            line = run_gpu(args, 0, 1, 0)
+            print(json.dumps({"profile_case": args.profile_case, "kernels": line['kernels']}))
+        else:
+            raise SystemExit(f'unknown profile case {args.profile_case}')
         return
 
     if world > 1:
