@@ -13,7 +13,9 @@
 //                   the mean-free Boussinesq buoyancy, at cell centres
 //   k_momentum_ab2  RU = -div(uu) + div[mu_s(H)(grad u + grad u^T)] + div tau(mu_p(H)) + f
 //                   and u* = u + dt (w1 RU^n + w0 RU^{n-1})   (Eqs. ru, ab2)
-// One thread per cell; neighbours through the read-only cache.
+// The level-set and interface kernels take one thread per cell with neighbours
+// through the read-only cache; the AB2 momentum kernel marches z-planes of tiles
+// staged in shared memory.
 #include <cfloat>
 
 #include "evp_internal.cuh"
@@ -276,57 +278,33 @@ __global__ void __launch_bounds__(256) k_iface_b(const Geo<T> g, const IfaceArgs
     a.f[2][c0] = s * __ldg(a.n[2] + c0);
 }
 
-// tau component c at a centre from B^n with the mixture polymer viscosity mu_p(H)
+// tau component c at a centre from B^n (b: the six components there) with the
+// mixture polymer viscosity mu_p(H) (Table 1 inverted)
 template <typename T, int MODEL>
-__device__ __forceinline__ T tau_mix(const Geo<T>& g, const MomAB2Args<T>& a, int c, int i, int j, int k,
-                                     bool fast = false) {
-    // fast: (i, j, k) is inside the grid, so no wrap or ghost rule applies
-    const size_t o = fast ? ((size_t)k * g.ny + j) * g.nx + i : lin(g, wrap(i, g.nx), ycen(g, j), wrap(k, g.nz));
-    const T H = __ldg(a.H + o);
+__device__ __forceinline__ T tau_value(const MomAB2Args<T>& a, int c, const T* b, T H) {
     const T gm = (a.mu_p1 * H + a.mu_p2 * (T(1) - H)) * a.inv_lam;
     const bool diag = (c == 0 || c == 3 || c == 5);
-    const T bc = __ldg(a.B[c] + o);
     if (MODEL == EVP_FENE_P) {
-        const T tr = __ldg(a.B[0] + o) + __ldg(a.B[3] + o) + __ldg(a.B[5] + o);
+        const T tr = b[0] + b[3] + b[5];
         const T F = a.L2 / (a.L2 - tr);
-        return gm * (F * bc - (diag ? a.a_fene : T(0)));
+        return gm * (F * b[c] - (diag ? a.a_fene : T(0)));
     }
-    if (MODEL == EVP_NEO_HOOKEAN) return gm * bc;
-    return gm * (bc - (diag ? T(1) : T(0)));
+    if (MODEL == EVP_NEO_HOOKEAN) return gm * b[c];
+    return gm * (b[c] - (diag ? T(1) : T(0)));
 }
 
-// average of tau_c over (0 or d1) x (0 or d2) around (i, j, k); offsets as in the RK3 kernel
-template <typename T, int MODEL>
-__device__ __forceinline__ T tau_e4(const Geo<T>& g, const MomAB2Args<T>& a, int c, int i, int j, int k, int di,
-                                    int dj, int dk, bool fast = false) {
-    int a1i = 0, a1j = 0, a1k = 0, a2i = 0, a2j = 0, a2k = 0;
-    if (di) {
-        a1i = di;
-        if (dj) a2j = dj; else a2k = dk;
-    } else {
-        a1j = dj;
-        a2k = dk;
-    }
-    return T(0.25) * (tau_mix<T, MODEL>(g, a, c, i, j, k, fast) + tau_mix<T, MODEL>(g, a, c, i + a2i, j + a2j, k + a2k, fast)
-                      + tau_mix<T, MODEL>(g, a, c, i + a1i, j + a1j, k + a1k, fast)
-                      + tau_mix<T, MODEL>(g, a, c, i + a1i + a2i, j + a1j + a2j, k + a1k + a2k, fast));
-}
-
-// One cell of k_momentum_ab2.  FAST: every stencil point (offsets within one cell
-// in each direction) lies inside the grid, so the loads index directly; otherwise
-// they apply the periodic wraps and wall ghost rules.  Both read the same values.
-template <typename T, int MODEL, bool FAST>
-__device__ __forceinline__ void momentum_ab2_cell(const Geo<T>& g, const MomAB2Args<T>& a, int i, int j, int k) {
+// One cell (i, j, k) of the AB2 momentum step.  S gives the staged values around
+// the cell at offsets (di, dj, dk) in -1 .. 1: S.u, S.v, S.w (faces), S.H, S.tau(c)
+// and S.f(q) (centres); the wraps and wall ghost rules were applied when staging.
+template <typename T, int MODEL, typename Src>
+__device__ __forceinline__ void momentum_ab2_cell(const Geo<T>& g, const MomAB2Args<T>& a, int i, int j, int k,
+                                                  const Src& S) {
     const size_t c0 = lin(g, i, j, k);
-    const size_t plane = (size_t)g.nx * g.ny;
-    auto at = [&](const T* F, int di, int dj, int dk) {
-        return __ldg(F + (c0 + (ptrdiff_t)di + (ptrdiff_t)dj * g.nx + (ptrdiff_t)dk * (ptrdiff_t)plane));
-    };
-    auto u = [&](int di, int dj, int dk) { return FAST ? at(a.U, di, dj, dk) : ld_uw(g, a.U, i + di, j + dj, k + dk); };
-    auto v = [&](int di, int dj, int dk) { return FAST ? at(a.V, di, dj, dk) : ld_v(g, a.V, i + di, j + dj, k + dk); };
-    auto w = [&](int di, int dj, int dk) { return FAST ? at(a.W, di, dj, dk) : ld_uw(g, a.W, i + di, j + dj, k + dk); };
+    auto u = [&](int di, int dj, int dk) { return S.u(di, dj, dk); };
+    auto v = [&](int di, int dj, int dk) { return S.v(di, dj, dk); };
+    auto w = [&](int di, int dj, int dk) { return S.w(di, dj, dk); };
     auto mu = [&](int di, int dj, int dk) {
-        const T H = FAST ? at(a.H, di, dj, dk) : ld_c(g, a.H, i + di, j + dj, k + dk);
+        const T H = S.H(di, dj, dk);
         return a.mu_s1 * H + a.mu_s2 * (T(1) - H);
     };
     // viscosity averaged over the 4 centres (0 or d1) x (0 or d2), shifted by (si, sj, sk)
@@ -341,6 +319,20 @@ __device__ __forceinline__ void momentum_ab2_cell(const Geo<T>& g, const MomAB2A
         }
         return T(0.25) * (mu(si, sj, sk) + mu(si + a2i, sj + a2j, sk + a2k) + mu(si + a1i, sj + a1j, sk + a1k)
                           + mu(si + a1i + a2i, sj + a1j + a2j, sk + a1k + a2k));
+    };
+    auto tau = [&](int c, int di, int dj, int dk) { return S.tau(c, di, dj, dk); };
+    // average of tau_c over (0 or d1) x (0 or d2) around the cell; offsets as in the RK3 kernel
+    auto tau_e4 = [&](int c, int di, int dj, int dk) {
+        int a1i = 0, a1j = 0, a1k = 0, a2i = 0, a2j = 0, a2k = 0;
+        if (di) {
+            a1i = di;
+            if (dj) a2j = dj; else a2k = dk;
+        } else {
+            a1j = dj;
+            a2k = dk;
+        }
+        return T(0.25) * (tau(c, 0, 0, 0) + tau(c, a2i, a2j, a2k) + tau(c, a1i, a1j, a1k)
+                          + tau(c, a1i + a2i, a1j + a2j, a1k + a2k));
     };
     const T h = T(0.5);
     const T u0 = u(0, 0, 0), v0 = v(0, 0, 0), w0 = w(0, 0, 0);
@@ -378,27 +370,24 @@ __device__ __forceinline__ void momentum_ab2_cell(const Geo<T>& g, const MomAB2A
     // ---- div tau^n with mu_p(H)
     T dtx = T(0), dty = T(0), dtz = T(0);
     if (MODEL != EVP_NEWTONIAN) {
-        dtx = (tau_mix<T, MODEL>(g, a, 0, i + 1, j, k, FAST) - tau_mix<T, MODEL>(g, a, 0, i, j, k, FAST)) * ix
-              + (tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, 1, 0, FAST) - tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, -1, 0, FAST)) * iy
-              + (tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, 1, FAST) - tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, -1, FAST)) * iz;
-        dty = (tau_e4<T, MODEL>(g, a, 1, i, j, k, 1, 1, 0, FAST) - tau_e4<T, MODEL>(g, a, 1, i, j, k, -1, 1, 0, FAST)) * ix
-              + (tau_mix<T, MODEL>(g, a, 3, i, j + 1, k, FAST) - tau_mix<T, MODEL>(g, a, 3, i, j, k, FAST)) * iy
-              + (tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, 1, FAST) - tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, -1, FAST)) * iz;
-        dtz = (tau_e4<T, MODEL>(g, a, 2, i, j, k, 1, 0, 1, FAST) - tau_e4<T, MODEL>(g, a, 2, i, j, k, -1, 0, 1, FAST)) * ix
-              + (tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, 1, 1, FAST) - tau_e4<T, MODEL>(g, a, 4, i, j, k, 0, -1, 1, FAST)) * iy
-              + (tau_mix<T, MODEL>(g, a, 5, i, j, k + 1, FAST) - tau_mix<T, MODEL>(g, a, 5, i, j, k, FAST)) * iz;
+        dtx = (tau(0, 1, 0, 0) - tau(0, 0, 0, 0)) * ix + (tau_e4(1, 1, 1, 0) - tau_e4(1, 1, -1, 0)) * iy
+              + (tau_e4(2, 1, 0, 1) - tau_e4(2, 1, 0, -1)) * iz;
+        dty = (tau_e4(1, 1, 1, 0) - tau_e4(1, -1, 1, 0)) * ix + (tau(3, 0, 1, 0) - tau(3, 0, 0, 0)) * iy
+              + (tau_e4(4, 0, 1, 1) - tau_e4(4, 0, 1, -1)) * iz;
+        dtz = (tau_e4(2, 1, 0, 1) - tau_e4(2, -1, 0, 1)) * ix + (tau_e4(4, 0, 1, 1) - tau_e4(4, 0, -1, 1)) * iy
+              + (tau(5, 0, 0, 1) - tau(5, 0, 0, 0)) * iz;
     }
 
     // ---- interface force: mean of the two centres next to each face
-    const T Fx = h * (__ldg(a.f[0] + c0) + (FAST ? at(a.f[0], 1, 0, 0) : ld_c(g, a.f[0], i + 1, j, k)));
-    const T Fy = h * (__ldg(a.f[1] + c0) + (FAST ? at(a.f[1], 0, 1, 0) : ld_c(g, a.f[1], i, j + 1, k)));
-    const T Fz = h * (__ldg(a.f[2] + c0) + (FAST ? at(a.f[2], 0, 0, 1) : ld_c(g, a.f[2], i, j, k + 1)));
+    const T Fx = h * (S.f(0, 0, 0, 0) + S.f(0, 1, 0, 0));
+    const T Fy = h * (S.f(1, 0, 0, 0) + S.f(1, 0, 1, 0));
+    const T Fz = h * (S.f(2, 0, 0, 0) + S.f(2, 0, 0, 1));
 
     T Nx, Ny, Nz;
     if (a.rho_ratio > T(0)) {
         // density contrast: 1/rho on the stress terms, (1 - rho_bar/rho) g per unit mass
         auto rho = [&](int di, int dj, int dk) {
-            const T Hc = FAST ? at(a.H, di, dj, dk) : ld_c(g, a.H, i + di, j + dj, k + dk);
+            const T Hc = S.H(di, dj, dk);
             return Hc + a.rho_ratio * (T(1) - Hc);
         };
         const T r0 = rho(0, 0, 0);
@@ -427,15 +416,112 @@ __device__ __forceinline__ void momentum_ab2_cell(const Geo<T>& g, const MomAB2A
     a.NH[2][c0] = Nz;
 }
 
+// z-marching tiles of the AB2 momentum step: a 32 x 4 tile walks a chunk of z
+// planes.  Planes k-1, k, k+1 of u, v, w, H and tau (built once per staged cell
+// from B^n and H, instead of once per stencil use) and planes k, k+1 of the
+// interface force sit in shared memory with a one-cell halo in x and y, staged
+// with the periodic wraps and the wall ghost rules; the raw values of plane k+2
+// are loaded into registers before plane k is computed.
+constexpr int AB_TX = 32, AB_TY = 4, AB_NT = AB_TX * AB_TY;
+constexpr int AB_W = AB_TX + 2, AB_H = AB_TY + 2, AB_PL = AB_W * AB_H;
+constexpr int AB_NE = (AB_PL + AB_NT - 1) / AB_NT;          // staged cells per thread
+
+template <typename T>
+struct Ab2Smem {
+    T U[3][AB_PL], V[3][AB_PL], W[3][AB_PL], H[3][AB_PL];    // ring slot = plane mod 3
+    T TAU[6][3][AB_PL];
+    T F[3][2][AB_PL];                                       // slot = plane mod 2
+};
+
+template <typename T>
+struct Ab2Src {
+    const Ab2Smem<T>* sm;
+    int o;          // the cell in a plane tile
+    int sl[3];      // slots of planes k-1, k, k+1
+    int fs[2];      // force slots of planes k, k+1
+    __device__ __forceinline__ int at(int di, int dj) const { return o + dj * AB_W + di; }
+    __device__ __forceinline__ T u(int di, int dj, int dk) const { return sm->U[sl[1 + dk]][at(di, dj)]; }
+    __device__ __forceinline__ T v(int di, int dj, int dk) const { return sm->V[sl[1 + dk]][at(di, dj)]; }
+    __device__ __forceinline__ T w(int di, int dj, int dk) const { return sm->W[sl[1 + dk]][at(di, dj)]; }
+    __device__ __forceinline__ T H(int di, int dj, int dk) const { return sm->H[sl[1 + dk]][at(di, dj)]; }
+    __device__ __forceinline__ T tau(int c, int di, int dj, int dk) const {
+        return sm->TAU[c][sl[1 + dk]][at(di, dj)];
+    }
+    __device__ __forceinline__ T f(int q, int di, int dj, int dk) const { return sm->F[q][fs[dk]][at(di, dj)]; }
+};
+
 template <typename T, int MODEL>
-__global__ void __launch_bounds__(256) k_momentum_ab2(const Geo<T> g, const MomAB2Args<T> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const bool inside = i >= 1 && i < g.nx - 1 && j >= 1 && j < g.ny - 1 && k >= 1 && k < g.nz - 1;
-    if (inside) momentum_ab2_cell<T, MODEL, true>(g, a, i, j, k);
-    else momentum_ab2_cell<T, MODEL, false>(g, a, i, j, k);
+__global__ void __launch_bounds__(AB_NT) k_momentum_ab2(const Geo<T> g, const MomAB2Args<T> a, int kz_chunk) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Ab2Smem<T>& sm = *reinterpret_cast<Ab2Smem<T>*>(smraw);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * AB_TX + tx;
+    const int i0 = blockIdx.x * AB_TX, j0 = blockIdx.y * AB_TY;
+    const int k0 = blockIdx.z * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = i < g.nx && j < g.ny;
+    constexpr bool STRESS = MODEL != EVP_NEWTONIAN;
+    // raw values of one staged plane for this thread's cells
+    T ru[AB_NE], rv[AB_NE], rw[AB_NE], rH[AB_NE], rB[6][AB_NE], rf[3][AB_NE];
+    auto load = [&](int q) {
+#pragma unroll
+        for (int r = 0; r < AB_NE; ++r) {
+            const int e = tid + r * AB_NT;
+            if (e >= AB_PL) continue;
+            const int ly = e / AB_W, lx = e - ly * AB_W;
+            // the halo of a ragged tile may reach past one period of a short x
+            const int gi = ((i0 - 1 + lx) % g.nx + g.nx) % g.nx, gj = j0 - 1 + ly;
+            ru[r] = ld_uw(g, a.U, gi, gj, q);
+            rv[r] = ld_v(g, a.V, gi, gj, q);
+            rw[r] = ld_uw(g, a.W, gi, gj, q);
+            rH[r] = ld_c(g, a.H, gi, gj, q);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) rB[c][r] = STRESS ? ld_c(g, a.B[c], gi, gj, q) : T(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) rf[c][r] = ld_c(g, a.f[c], gi, gj, q);
+        }
+    };
+    auto store = [&](int q) {
+        const int s3 = (q + 3) % 3, s2 = q & 1;
+#pragma unroll
+        for (int r = 0; r < AB_NE; ++r) {
+            const int e = tid + r * AB_NT;
+            if (e >= AB_PL) continue;
+            sm.U[s3][e] = ru[r];
+            sm.V[s3][e] = rv[r];
+            sm.W[s3][e] = rw[r];
+            sm.H[s3][e] = rH[r];
+            if (STRESS) {
+                T b[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) b[c] = rB[c][r];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) sm.TAU[c][s3][e] = tau_value<T, MODEL>(a, c, b, rH[r]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sm.F[c][s2][e] = rf[c][r];
+        }
+    };
+    for (int q = k0 - 1; q <= k0 + 1; ++q) {
+        load(q);
+        store(q);
+    }
+    __syncthreads();
+    Ab2Src<T> src;
+    src.sm = &sm;
+    src.o = (ty + 1) * AB_W + tx + 1;
+    for (int k = k0; k < k1; ++k) {
+        const bool more = k + 2 <= k1;
+        if (more) load(k + 2);
+        src.sl[0] = (k + 2) % 3;
+        src.sl[1] = k % 3;
+        src.sl[2] = (k + 1) % 3;
+        src.fs[0] = k & 1;
+        src.fs[1] = (k + 1) & 1;
+        if (active) momentum_ab2_cell<T, MODEL>(g, a, i, j, k, src);
+        __syncthreads();
+        if (more) store(k + 2);
+        __syncthreads();
+    }
 }
 
 // density at a centre from the Heaviside: rho_1 = 1 (H = 1), rho_2 = rho_ratio
@@ -602,14 +688,25 @@ cudaError_t launch_mass_correct(const Geo<T>& g, const MassArgs<T>& a, int mode,
 template <typename T>
 cudaError_t launch_momentum_ab2(const Geo<T>& g, int model, const MomAB2Args<T>& a, cudaStream_t st,
                                 const TimingHook& th) {
-    dim3 block(32, 8, 1), grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    // z chunks: about four waves of four CTAs per SM; small grids down to one plane
+    const int tiles = ((g.nx + AB_TX - 1) / AB_TX) * ((g.ny + AB_TY - 1) / AB_TY);
+    int chunks = (4 * 152 * 4 + tiles - 1) / tiles;
+    chunks = chunks > g.nz ? g.nz : chunks;
+    const int kz = (g.nz + chunks - 1) / chunks;
+    chunks = (g.nz + kz - 1) / kz;
+    const dim3 block(AB_TX, AB_TY, 1), grid((g.nx + AB_TX - 1) / AB_TX, (g.ny + AB_TY - 1) / AB_TY, chunks);
+    const size_t smem = sizeof(Ab2Smem<T>);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, block, smem, st>>>(g, a, kz);
+    };
     th.b(K_MOMENTUM);
     switch (model) {
-        case EVP_NEWTONIAN: k_momentum_ab2<T, EVP_NEWTONIAN><<<grid, block, 0, st>>>(g, a); break;
-        case EVP_OLDROYD_B: k_momentum_ab2<T, EVP_OLDROYD_B><<<grid, block, 0, st>>>(g, a); break;
-        case EVP_FENE_P: k_momentum_ab2<T, EVP_FENE_P><<<grid, block, 0, st>>>(g, a); break;
-        case EVP_SARAMITO: k_momentum_ab2<T, EVP_SARAMITO><<<grid, block, 0, st>>>(g, a); break;
-        case EVP_NEO_HOOKEAN: k_momentum_ab2<T, EVP_NEO_HOOKEAN><<<grid, block, 0, st>>>(g, a); break;
+        case EVP_NEWTONIAN: go(k_momentum_ab2<T, EVP_NEWTONIAN>); break;
+        case EVP_OLDROYD_B: go(k_momentum_ab2<T, EVP_OLDROYD_B>); break;
+        case EVP_FENE_P: go(k_momentum_ab2<T, EVP_FENE_P>); break;
+        case EVP_SARAMITO: go(k_momentum_ab2<T, EVP_SARAMITO>); break;
+        case EVP_NEO_HOOKEAN: go(k_momentum_ab2<T, EVP_NEO_HOOKEAN>); break;
         default: return cudaErrorInvalidValue;
     }
     th.e(K_MOMENTUM);
