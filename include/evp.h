@@ -186,6 +186,19 @@ int evp_get_field(evp_state* s, int field, void* dst, int dst_on_device);
 int evp_set_fields(evp_state* s, int n, const int* fields, const void* const* srcs, int src_on_device);
 int evp_get_fields(evp_state* s, int n, const int* fields, void* const* dsts, int dst_on_device);
 
+/* One step with its inputs and outputs on the host, nothing waited for: the n_in
+ * copies into the state (as evp_set_fields), one evp_step of size dt, then the
+ * n_out copies out of the state (as evp_get_fields), all enqueued in this order
+ * on the state's stream and left running.  Host buffers should be page-locked
+ * (then the copies are asynchronous; pageable buffers make the call wait for
+ * them); the caller keeps them untouched until the stream is synchronised
+ * (evp_sync).  Several states on different streams overlap one state's copies
+ * with another's step (the paper has no counterpart).
+ * Errors: as evp_set_fields / evp_step / evp_get_fields, found before anything
+ * is enqueued when they concern the arguments.                               */
+int evp_step_io(evp_state* s, double dt, int n_in, const int* in_fields, const void* const* in_srcs, int n_out,
+                const int* out_fields, void* const* out_dsts);
+
 /* One full RK3 time step of size dt (Sec. 3.3.1, Eqs. RK-rt..NS-num3, RK):
  * three substeps, each B update (Eq. rk3tau), momentum predictor (Eq. rk3),
  * Poisson solve (Eq. NS-num2) and correction (Eq. NS-num3).  Asynchronous.   */

@@ -1194,6 +1194,30 @@ extern "C" int evp_step(evp_state* s, double dt) {
     return EVP_OK;
 }
 
+int evp_step_io(evp_state* s, double dt, int n_in, const int* in_fields, const void* const* in_srcs, int n_out,
+                const int* out_fields, void* const* out_dsts) {
+    if (!s || n_in < 0 || n_out < 0 || (n_in > 0 && (!in_fields || !in_srcs)) ||
+        (n_out > 0 && (!out_fields || !out_dsts)))
+        return fail(EVP_ERR_ARG, "null state or arrays, or a negative count");
+    if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
+    for (int i = 0; i < n_in; ++i) {
+        if (!in_srcs[i]) return fail(EVP_ERR_ARG, "null source buffer");
+        if (in_fields[i] == EVP_PSI) return fail(EVP_ERR_ARG, "EVP_PSI is read only");
+        if (!field_ptr(s, in_fields[i])) return fail(EVP_ERR_ARG, "unknown field id");
+    }
+    for (int i = 0; i < n_out; ++i) {
+        if (!out_dsts[i]) return fail(EVP_ERR_ARG, "null destination buffer");
+        if (!field_ptr(s, out_fields[i])) return fail(EVP_ERR_ARG, "unknown field id");
+    }
+    if (s->batch) return fail(EVP_ERR_STATE, "the state is a member of a batch: it steps with evp_batch_step");
+    for (int i = 0; i < n_in; ++i)
+        if (int r = put_field(s, in_fields[i], in_srcs[i], 0, s->st)) return r;
+    if (int r = evp_step(s, dt)) return r;
+    for (int i = 0; i < n_out; ++i)
+        if (int r = take_field(s, out_fields[i], out_dsts[i], 0, s->st)) return r;
+    return EVP_OK;
+}
+
 int evp_project(evp_state* s) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
     if (int r = wait_batch(s)) return r;

@@ -88,6 +88,8 @@ def load(path=None):
         'evp_set_fields': (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_void_p), c_int]),
         'evp_get_fields': (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_void_p), c_int]),
         'evp_step': (c_int, [c_void_p, c_double]),
+        'evp_step_io': (c_int, [c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_void_p), c_int, POINTER(c_int),
+                                POINTER(c_void_p)]),
         'evp_set_graph': (c_int, [c_void_p, c_int]),
         'evp_set_pdl': (c_int, [c_void_p, c_int]),
         'evp_set_particles': (c_int, [c_void_p, c_int, c_void_p, c_int]),
@@ -135,7 +137,7 @@ def exported_symbols():
             'evp_set_graph', 'evp_selftest', 'evp_set_pdl', 'evp_set_particles', 'evp_get_particles',
             'evp_set_fields', 'evp_get_fields', 'evp_fma_peak', 'evp_batch_create', 'evp_batch_admit',
             'evp_batch_evict', 'evp_batch_step', 'evp_batch_info', 'evp_batch_set_graph', 'evp_batch_destroy',
-            'evp_tune', 'evp_tile_time', 'evp_tile_config_get', 'evp_tile_config_set']
+            'evp_tune', 'evp_tile_time', 'evp_tile_config_get', 'evp_tile_config_set', 'evp_step_io']
 
 
 def _check(code):
@@ -237,6 +239,26 @@ def evp_get_fields(state, fields, dsts):
 
 def evp_step(state, dt):
     return _check(load().evp_step(state, float(dt)))
+
+
+class StepIO:
+    """Marshalled argument arrays of evp_step_io for fixed host buffers (built
+    once, reused every step; the buffers are numpy arrays or CPU tensors, pinned
+    for asynchronous copies)."""
+
+    def __init__(self, in_fields, in_bufs, out_fields, out_bufs):
+        self.n_in, self.in_ids, self.in_ps, dev_in = _field_arrays(in_fields, in_bufs)
+        self.n_out, self.out_ids, self.out_ps, dev_out = _field_arrays(out_fields, out_bufs)
+        if dev_in or dev_out:
+            raise ValueError('evp_step_io copies from and to host buffers')
+        self.keep = (in_bufs, out_bufs)
+
+
+def evp_step_io(state, dt, io):
+    """One step with host inputs and outputs (see StepIO), enqueued on the state's
+    stream without waiting."""
+    return _check(load().evp_step_io(state, float(dt), io.n_in, io.in_ids, io.in_ps, io.n_out, io.out_ids,
+                                     io.out_ps))
 
 
 def evp_set_graph(state, enable):

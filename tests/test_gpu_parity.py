@@ -887,3 +887,37 @@ def test_checkpoint_and_resume_bitwise_fp64(evp, shape):
         assert np.array_equal(sim.get(f), twin.get(f)), f
     twin.close()
     sim.close()
+
+
+def test_step_io_equals_copies_and_step(evp):
+    """evp_step_io (copies in, one step, copies out, nothing waited for) gives what
+    evp_set_fields + evp_step + evp_get_fields give, bit for bit, with two states on
+    two streams stepping in turn and sharing nothing."""
+    import torch
+    shape = SHAPES[1]
+    ids = [evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P] + [evp.EVP_BXX + c for c in range(6)]
+    ref, _, _, _ = setup_case(evp, shape, 'saramito', {'Bi': 0.4}, evp.EVP_FP32, dpdx=0.05)
+    start = [ref.get(f) for f in ids]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    sims, ios, bufs = [], [], []
+    for st in streams:
+        sim = evp.Simulation(ref.grid, 'saramito', ref.params, stream=st.cuda_stream)
+        b = [torch.from_numpy(a.copy()).pin_memory() for a in start]
+        outs = [torch.empty_like(x).pin_memory() for x in b]
+        ios.append(evp.StepIO(ids, [x.numpy() for x in b], ids, [x.numpy() for x in outs]))
+        sims.append(sim)
+        bufs.append((b, outs))
+    for k in range(6):
+        evp.evp_step_io(sims[k & 1].handle, 2e-3, ios[k & 1])
+    torch.cuda.synchronize()
+    for sim, (b, outs) in zip(sims, bufs):
+        # each state restarted from `start` every step: its outputs are one step from it
+        one = [sim.get(f) for f in ids]
+        for a, o in zip(one, outs):
+            assert np.array_equal(a, o.numpy())
+    ref.set_state(*start[:4], B=start[4:])
+    ref.step(2e-3)
+    for f, o in zip(ids, bufs[0][1]):
+        assert np.array_equal(ref.get(f), o.numpy()), f
+    for s in sims + [ref]:
+        s.close()
