@@ -333,43 +333,49 @@ def run_gpu(args, rank, world, local_rank):
            "how": "evp_fma_peak: 8 independent FMA chains per thread, 8 blocks of 256 threads per SM, "
                   "packed f32x2 FMAs in FP32; best of 3 timed launches, an FMA counted as 2 operations"}
 
-    # ---------------- e2e through the C ABI with host buffers: two replicas of the
+    # ---------------- e2e through the C ABI with host buffers: replicas of the
     # state, each on its own stream, stepping in turn with evp_step_io: every step
     # copies its 10 fields in from pinned host memory, takes one RK3 step and copies
     # the 10 fields back out to the same host buffers (the state makes the round
-    # trip through host memory every step); one replica's copies overlap the other's
+    # trip through host memory every step); one replica's copies overlap another's
     # step, nothing is waited for until the end
     fields_io = [evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P] + [evp.EVP_BXX + c for c in range(6)]
     host_a = [torch.empty(sim.shape, dtype=torch.float32).pin_memory() for _ in fields_io]
     for f, h in zip(fields_io, host_a):
         evp.evp_get_field(sim.handle, f, h.numpy())
-    host_b = [h.clone().pin_memory() for h in host_a]
-    stream2 = torch.cuda.Stream()
-    sim2 = evp.Simulation(evp.make_grid(w['nx'], w['ny'], w['nz'], w['lx'], w['ly'], w['lz'], w['walls_y']),
-                          w['model'], evp.make_params(Re=w['Re'], Wi=w['Wi'], beta=w['beta'], Bi=w['Bi'],
-                                                      dpdx=2.0 / w['Re'], precision=evp.EVP_FP32),
-                          stream=stream2.cuda_stream)
-    evp.evp_set_graph(sim2.handle, True)
-    host_b_np = [h.numpy() for h in host_b]
-    for _ in range(2):                   # capture the second replica's graphs (both parities)
-        sim2.step(w['dt'])
-    evp.evp_set_fields(sim2.handle, fields_io, host_b_np)
-    io = [evp.StepIO(fields_io, [h.numpy() for h in host_a], fields_io, [h.numpy() for h in host_a]),
-          evp.StepIO(fields_io, host_b_np, fields_io, host_b_np)]
-    pair = [sim, sim2]
-    e2e_steps = 2 * max(1, args.steps // 4)
+    # further replicas start from the same state, each on its own stream
+    NREP = 3
+    pair = [sim]
+    host = [host_a]
+    grid_w = evp.make_grid(w['nx'], w['ny'], w['nz'], w['lx'], w['ly'], w['lz'], w['walls_y'])
+    prm_w = evp.make_params(Re=w['Re'], Wi=w['Wi'], beta=w['beta'], Bi=w['Bi'], dpdx=2.0 / w['Re'],
+                            precision=evp.EVP_FP32)
+    rep_streams = []
+    for _ in range(NREP - 1):
+        hb = [h.clone().pin_memory() for h in host_a]
+        st_r = torch.cuda.Stream()
+        rep_streams.append(st_r)
+        sr = evp.Simulation(grid_w, w['model'], prm_w, stream=st_r.cuda_stream)
+        evp.evp_set_graph(sr.handle, True)
+        for _ in range(2):               # capture the replica's graphs (both parities)
+            sr.step(w['dt'])
+        evp.evp_set_fields(sr.handle, fields_io, [h.numpy() for h in hb])
+        pair.append(sr)
+        host.append(hb)
+    io = [evp.StepIO(fields_io, [h.numpy() for h in hb], fields_io, [h.numpy() for h in hb]) for hb in host]
+    e2e_steps = NREP * max(1, args.steps // (2 * NREP))
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        evp.evp_step_io(pair[k & 1].handle, w['dt'], io[k & 1])
+        evp.evp_step_io(pair[k % NREP].handle, w['dt'], io[k % NREP])
     torch.cuda.synchronize()
     e2e_s = max_ranks(time.perf_counter() - t0)
     e2e_value = job_rate(N, e2e_steps, world, e2e_s)
     io_bytes = len(fields_io) * N * 4
     fp32_fields = [sim.get(f) for f in fields_io]
-    sim.close()
-    sim2.close()
+    for sr in pair:
+        sr.close()
 
     # ---------------- FP64 plain on the same workload and the same steps
     sim64 = make(evp.EVP_FP64)
@@ -387,7 +393,7 @@ def run_gpu(args, rank, world, local_rank):
     ms64 = max_ranks(e0.elapsed_time(e1))
     value64 = job_rate(N, n64, world, ms64 * 1e-3)
     # accuracy of FP32-served against FP64 plain after the same number of steps
-    steps_done = args.warmup + args.steps + k_steps + e2e_steps // 2
+    steps_done = args.warmup + args.steps + k_steps + e2e_steps // NREP
     sim64.close()
     sim64 = make(evp.EVP_FP64)
     for _ in range(steps_done):
@@ -420,10 +426,10 @@ def run_gpu(args, rank, world, local_rank):
         "max_div_fp64_residual": maxdiv, "status_bits": bits,
         "e2e": {"value": e2e_value, "unit": "Mcell-steps/s", "h2d_bytes_per_step": io_bytes,
                 "d2h_bytes_per_step": io_bytes, "steps": e2e_steps,
-                "how": "evp_step_io: two replicas of the state on two streams step in turn; each step copies its "
-                       "10 fields in from pinned host memory, takes one RK3 step and copies them back out, so one "
-                       "replica's copies overlap the other's step; host-clock time from the first call to the "
-                       "final synchronisation"},
+                "how": f"evp_step_io: {NREP} replicas of the state on their own streams step in turn; each step "
+                       "copies its 10 fields in from pinned host memory, takes one RK3 step and copies them back "
+                       "out, so one replica's copies overlap another's step; host-clock time from the first call "
+                       "to the final synchronisation"},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
