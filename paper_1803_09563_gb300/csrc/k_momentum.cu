@@ -64,8 +64,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // all but the most recently committed group have landed
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// Planes are staged two ahead: while plane k is computed, plane k+2 has landed
-// (or is landing) and plane k+3 is being requested.
+// Planes are staged two ahead (the forms that build the summed stress here, and the
+// batched kernel): while plane k is computed, plane k+2 has landed (or is landing)
+// and plane k+3 is being requested.
 template <typename T>
 struct MomSmem {
     T V[3][5][VPL];      // u, v, w: ring slots for planes k-1 .. k+3
@@ -83,17 +84,33 @@ struct MomSmemS {
     T P[4][VPL];
     T H[4][3][NT];
 };
-template <typename T, bool SPRE>
-using MomSmemOf = std::conditional_t<SPRE, MomSmemS<T>, MomSmem<T>>;
-__device__ __forceinline__ int vslot(int kk) { return (kk + 5) % 5; }   // kk >= -5
+// Staged one plane ahead (D1): while plane k is computed, plane k+2 is being
+// requested; fewer slots, so five CTAs fit on an SM in FP32.
+template <typename T>
+struct MomSmemS1 {
+    T V[3][4][VPL];      // planes k-1 .. k+2
+    T S[6][4][VPL];
+    T P[3][VPL];         // planes k .. k+2
+    T H[2][3][NT];       // planes k, k+1
+};
+template <typename T, bool SPRE, bool D1>
+using MomSmemOf = std::conditional_t<SPRE, std::conditional_t<D1, MomSmemS1<T>, MomSmemS<T>>, MomSmem<T>>;
+// ring slots of velocity / stress, pressure and history planes (kk >= -1)
+template <bool D1>
+__device__ __forceinline__ int vs_of(int kk) { return D1 ? (kk + 4) % 4 : (kk + 5) % 5; }
+template <bool D1>
+__device__ __forceinline__ int ps_of(int kk) { return D1 ? (kk + 3) % 3 : (kk & 3); }
+template <bool D1>
+__device__ __forceinline__ int hs_of(int kk) { return D1 ? (kk & 1) : (kk & 3); }
 
 // VEC: rows are staged in 16-byte chunks (needs nx * sizeof(T) % 16 == 0)
 // SPRE: the summed stress comes precomputed (MomentumArgs::S); MODEL is then unused
 // One tile: the 32 x 4 columns (bx, by) over the z chunk bz of kz_chunk planes.
-template <typename T, int MODEL, bool VEC, bool SPRE>
+template <typename T, int MODEL, bool VEC, bool SPRE, bool D1 = false>
 __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst& mc, const MomentumArgs<T>& a,
                                               int kz_chunk, int bx, int by, int bz, unsigned char* smraw) {
-    MomSmemOf<T, SPRE>& sm = *reinterpret_cast<MomSmemOf<T, SPRE>*>(smraw);
+    static_assert(!D1 || SPRE, "one-ahead staging is a form of the precomputed-stress kernel");
+    MomSmemOf<T, SPRE, D1>& sm = *reinterpret_cast<MomSmemOf<T, SPRE, D1>*>(smraw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int i0 = bx * TX, j0 = by * TY;
     const int k0 = bz * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
@@ -196,7 +213,7 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
     };
     auto fetch_vel = [&](int kk) {
         const size_t pv = (size_t)wrap1(kk, g.nz) * plane;
-        const int slot = vslot(kk);
+        const int slot = vs_of<D1>(kk);
         if constexpr (VEC) {
             if (csm < 0) return;
 #pragma unroll
@@ -221,7 +238,7 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
     };
     auto fetch_p = [&](int kk) {
         const size_t pp = (size_t)wrap1(kk, g.nz) * plane;
-        const int slot = kk & 3;
+        const int slot = ps_of<D1>(kk);
         if constexpr (VEC) {
             if (csm >= 0) cp_async16(&sm.P[slot][csm], a.P + pp + ccoff);
         } else {
@@ -257,7 +274,7 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
     auto fetch_s = [&](int kk) {
         if constexpr (SPRE) {
             const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
-            const int slot = vslot(kk);
+            const int slot = vs_of<D1>(kk);
             if constexpr (VEC) {
                 if (csm < 0) return;
 #pragma unroll
@@ -332,11 +349,11 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
             if (hch) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
-                    cp_async16(&sm.H[kk & 3][q][hr * TX + hq], a.NH[q] + (size_t)kk * plane + hoff);
+                    cp_async16(&sm.H[hs_of<D1>(kk)][q][hr * TX + hq], a.NH[q] + (size_t)kk * plane + hoff);
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) cp_async(&sm.H[kk & 3][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
+            for (int q = 0; q < 3; ++q) cp_async(&sm.H[hs_of<D1>(kk)][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
         }
     };
 
@@ -363,12 +380,14 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
             __syncthreads();
         }
     }
-    fetch_vel(k0 + 2);
-    fetch_braw(k0 + 2);
-    fetch_s(k0 + 2);
-    fetch_p(k0 + 2);
-    fetch_hist(k0 + 1);
-    cp_async_commit();
+    if constexpr (!D1) {
+        fetch_vel(k0 + 2);
+        fetch_braw(k0 + 2);
+        fetch_s(k0 + 2);
+        fetch_p(k0 + 2);
+        fetch_hist(k0 + 1);
+        cp_async_commit();
+    }
 
     const T h = T(0.5);
     const T idx2 = g.idx * g.idx, idy2 = g.idy * g.idy, idz2 = g.idz * g.idz;
@@ -379,14 +398,15 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
 
     for (int k = k0; k < k1; ++k) {
         // ---- asynchronous request of plane k+3 (velocity, raw B, p) and the history of k+2
-        fetch_vel(k + 3);
-        fetch_braw(k + 3);
-        fetch_s(k + 3);
-        fetch_p(k + 3);
-        fetch_hist(k + 2);
+        constexpr int AH = D1 ? 2 : 3;
+        fetch_vel(k + AH);
+        fetch_braw(k + AH);
+        fetch_s(k + AH);
+        fetch_p(k + AH);
+        fetch_hist(k + AH - 1);
         cp_async_commit();
 
-        const int vm1 = vslot(k - 1), v0s = vslot(k), vp1 = vslot(k + 1);
+        const int vm1 = vs_of<D1>(k - 1), v0s = vs_of<D1>(k), vp1 = vs_of<D1>(k + 1);
         const T* U0 = sm.V[0][v0s];
         const T* Um1 = sm.V[0][vm1];
         const T* Up1 = sm.V[0][vp1];
@@ -445,8 +465,8 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
         const T Nz = -Az + mun * Lw + fz;
 
         // ---- pressure gradient
-        const T* P0 = sm.P[k & 3];
-        const T* P1 = sm.P[(k + 1) & 3];
+        const T* P0 = sm.P[ps_of<D1>(k)];
+        const T* P1 = sm.P[ps_of<D1>(k + 1)];
         const T p0 = at(P0, 0, 0);
         const T gpx = (at(P0, 1, 0) - p0) * g.idx;
         const T gpy = (at(P0, 0, 1) - p0) * g.idy;
@@ -454,9 +474,9 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
 
         T ix = a.zeta * Nx, iy = a.zeta * Ny, iz = a.zeta * Nz;
         if (a.read_hist) {
-            ix += a.xi * sm.H[k & 3][0][tid];
-            iy += a.xi * sm.H[k & 3][1][tid];
-            iz += a.xi * sm.H[k & 3][2][tid];
+            ix += a.xi * sm.H[hs_of<D1>(k)][0][tid];
+            iy += a.xi * sm.H[hs_of<D1>(k)][1][tid];
+            iz += a.xi * sm.H[hs_of<D1>(k)][2][tid];
         }
         ix -= two_a * gpx;
         iy -= two_a * gpy;
@@ -468,8 +488,8 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
             iz += am * Lw;
         }
         if (stress) {
-            const int s0 = SPRE ? vslot(k) : pmod(k, 3), sm1 = SPRE ? vslot(k - 1) : pmod(k - 1, 3);
-            const int sp1 = SPRE ? vslot(k + 1) : pmod(k + 1, 3);
+            const int s0 = SPRE ? vs_of<D1>(k) : pmod(k, 3), sm1 = SPRE ? vs_of<D1>(k - 1) : pmod(k - 1, 3);
+            const int sp1 = SPRE ? vs_of<D1>(k + 1) : pmod(k + 1, 3);
             auto S = [&](int c, int slot, int di, int dj) { return sm.S[c][slot][o + dj * VW + di]; };
             // 4-point average over centres (0 or di) x (0 or dj) in one plane
             auto e4 = [&](int c, int slot, int di, int dj) {
@@ -515,7 +535,8 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
         // raw B becomes S plane k+2 (slot of plane k-1).  With the precomputed
         // stress every ring slot written at the next plane was last read before
         // this barrier, which is the only one per plane.
-        cp_async_wait_prev();
+        if constexpr (D1) cp_async_wait_all();   // plane k+2 has landed
+        else cp_async_wait_prev();
         __syncthreads();
         if constexpr (!SPRE) {
             build_s(k + 2);
@@ -531,6 +552,16 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     momentum_tile<T, MODEL, VEC, SPRE>(g, mc, a, kz_chunk, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
+}
+
+// the precomputed-stress kernel staged one plane ahead, five CTAs per SM in FP32
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 5 : 2)
+k_momentum_d1(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_chunk) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    momentum_tile<T, EVP_OLDROYD_B, VEC, true, true>(g, mc, a, kz_chunk, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
 }
 
 // Batched form (summed stress precomputed): a persistent grid walks a work list
@@ -564,6 +595,22 @@ cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const Momentu
     dim3 block(TX, TY, 1);
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
     const bool vec = (g.nx * sizeof(T)) % 16 == 0;
+    if (a.S[0] && sizeof(T) == 4) {
+        // summed stress precomputed by the stress kernel: staged one plane ahead
+        if (mc.model == EVP_NEWTONIAN) return cudaErrorInvalidValue;
+        const size_t smem = sizeof(MomSmemS1<T>);
+        int ch = (4 * 152 * 5 + tiles - 1) / tiles;
+        ch = ch > g.nz ? g.nz : ch;
+        const int kz1 = (g.nz + ch - 1) / ch;
+        ch = (g.nz + kz1 - 1) / kz1;
+        const dim3 grid1((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, ch);
+        th.b(K_MOMENTUM);
+        auto kern = vec ? k_momentum_d1<T, true> : k_momentum_d1<T, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaError_t e = launch_k(kern, grid1, block, smem, st, th.pdl, g, mc, a, kz1)) return e;
+        th.e(K_MOMENTUM);
+        return cudaGetLastError();
+    }
     if (a.S[0]) {
         // summed stress precomputed by the stress kernel
         if (mc.model == EVP_NEWTONIAN) return cudaErrorInvalidValue;
