@@ -2,10 +2,10 @@
 
 Requests (grid size, Wi / Bi / beta, number of steps, seed) arrive over time.
 The server keeps every admitted simulation resident on the device and groups the
-residents by grid size into batches of at most ``cells_per_batch`` cells; each
-batch (``evp_batch_*``) runs on its own CUDA stream, so one replayed CUDA graph
-advances all of a batch's members by one step with one launch per kernel phase,
-and batches of different sizes overlap on the device.
+residents by grid size into classes; each class is one libevp batch
+(``evp_batch_*``) on its own CUDA stream, so one replayed CUDA graph advances all
+of a class's members by one step with one launch per kernel phase, and classes of
+different sizes overlap on the device.
 
 The host loop never waits for the device: it polls each class's end-of-step
 event (``cudaEventQuery``).  When a class's step has finished, its finished
@@ -119,21 +119,12 @@ class SizeClass:
 
 class Server:
     def __init__(self, budget_bytes, precision=evp.EVP_FP32, use_graph=True,
-                 result_fields=(evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P, evp.EVP_BXY), tune=False,
-                 cells_per_batch=8 << 20):
+                 result_fields=(evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_P, evp.EVP_BXY), tune=False):
         self.budget = int(budget_bytes)
         self.precision = precision
         self.use_graph = use_graph
         self.result_fields = result_fields
         self.tune = tune
-        self.cells_per_batch = int(cells_per_batch)
-
-    def members_per_batch(self, n):
-        """At most ``cells_per_batch`` cells in one batch (and EVP_BATCH_MAX members):
-        a batch's step advances all its members, so a cap on its cells bounds the
-        step latency of large grids; further members of that size go to another
-        batch on its own stream."""
-        return max(1, min(evp.EVP_BATCH_MAX, self.cells_per_batch // n ** 3))
 
     def tune_sizes(self, requests):
         """Autotune the batched kernels' tiles for every grid size of the stream
@@ -154,7 +145,7 @@ class Server:
         tuned = self.tune_sizes(requests) if self.tune else None
         waiting = sorted(requests)
         ready = []              # arrived, not yet admitted (arrival order)
-        classes = {}            # (grid size, index) -> batch of that size
+        classes = {}
         results = {}
         lat = []
         lat_by_n = {}
@@ -196,23 +187,20 @@ class Server:
                         else:
                             keep.append(inst)
                     c.members = keep
-            # admission: arrival order within each size, into an idle batch of that
-            # size with room (a new batch on its own stream when every one is full),
+            # admission: arrival order within each size class, into idle classes,
             # while the budget allows
             still = []
             for req in ready:
-                cap = self.members_per_batch(req.n)
-                group = [c for key, c in classes.items() if key[0] == req.n]
-                room = [c for c in group if len(c.members) < cap]
+                c = classes.get(req.n)
                 need = evp.evp_state_bytes(request_grid(req), evp.EVP_SARAMITO,
                                            request_params(req, self.precision))
-                c = min(room, key=lambda x: len(x.members)) if room else None
                 busy = c is not None and c.in_flight
-                if busy or used + need > self.budget or any(r.n == req.n for r in still):
+                full = c is not None and len(c.members) >= evp.EVP_BATCH_MAX
+                if busy or full or used + need > self.budget or any(r.n == req.n for r in still):
                     still.append(req)
                     continue
                 if c is None:
-                    c = classes[(req.n, len(group))] = SizeClass(req.n, self.precision, self.use_graph)
+                    c = classes[req.n] = SizeClass(req.n, self.precision, self.use_graph)
                 inst = Instance(req, self.precision, None if prepared is None else prepared.get(req.rid))
                 c.batch.admit(inst.sim, req.dt)
                 c.members.append(inst)
@@ -246,9 +234,7 @@ class Server:
             "queue_p50_ms": pct(queue_ms, 0.5), "queue_p99_ms": pct(queue_ms, 0.99),
             "mean_resident": float(np.mean(resident_hist)) if resident_hist else 0.0,
             "max_resident": int(max_resident),
-            "size_classes": sorted({key[0] for key in classes}),
-            "batches": len(classes),
-            "cells_per_batch": self.cells_per_batch,
+            "size_classes": sorted(classes),
             "by_size": {str(n): {"request_steps": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)}
                         for n, v in sorted(lat_by_n.items())},
         }
