@@ -71,6 +71,10 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                                                      first substep under gravity)
   soft particles ................................... pinned (all-solid and all-fluid limits,
                                                      transport order)
+  monitoring quantities ............................ pinned (Fourier-mode energy, steady-shear
+                                                     det B, library determinant, deviator
+                                                     closed forms, yielded cells beyond
+                                                     the channel's plug edge y0)
 
 The substep predictors (``rk3_substep(..., predictor_only=True)``,
 ``ab2.ab2_predictor``) return u* and the updated conformation before the global
