@@ -312,6 +312,41 @@ int evp_stress_rhs(evp_state* s, void* rt);
  * Bits are cleared afterwards.                                                 */
 int evp_sync(evp_state* s, unsigned* bits, double* max_div);
 
+/* Monitoring quantities of the current state (the paper monitors flow
+ * histories such as the centre-line velocity, B_xx and the yielded region,
+ * Sec. 4, and names loss of positive definiteness of B as the failure mode,
+ * Sec. 3.1; these reductions are the library's summary of that state).  All
+ * are evaluated in FP64 on the stored values (FP32 states are widened first);
+ * every sum runs in a fixed order, so repeated calls on the same fields give
+ * the same bits.                                                               */
+typedef struct evp_diag {
+    double kinetic_energy;   /* 1/2 dx dy dz sum over all stored faces of u^2 + v^2 + w^2
+                                (rho = 1; with walls the wall v faces hold 0)          */
+    double max_div;          /* max |div u| over the cells whose divergence is finite
+                                (as evp_sync's max_div)                               */
+    double min_det_B;        /* min over the cells of det B; +inf for EVP_NEWTONIAN  */
+    double max_tr_B;         /* max over the cells of tr B; 0 for EVP_NEWTONIAN      */
+    double max_tr_B_over_L2; /* FENE-P: max tr B / L^2 (the closure is singular at 1);
+                                0 for the other models                                 */
+    double yielded_fraction; /* EVP_SARAMITO: fraction of the cells with F > 0 of
+                                Table 1, i.e. |tau^d| > tau_y with tau = mu_p/lambda
+                                (B - I); two-phase states form mu_p from the Heaviside
+                                of the last step's level set (0 before the first
+                                step).  1 for Oldroyd-B and FENE-P, 0 for Newtonian
+                                and neo-Hookean (no yield surface)                     */
+    unsigned long long nonfinite_cells; /* cells where u, v or w of the cell's faces
+                                (i, j, k) or a component of B is NaN or infinite    */
+    unsigned long long yielded_cells;   /* the count behind yielded_fraction         */
+} evp_diag;
+
+/* Fill *out with the current state's monitoring quantities.  Waits for the
+ * state's stream (and its batch's, for a batch member) and then for the
+ * reduction; allocates nothing (the state's arena holds the block partials).
+ * Non-finite cells are reported, not raised: the status bits of evp_sync are
+ * left as they are.
+ * Errors: EVP_ERR_ARG (null pointers), EVP_ERR_CUDA.                           */
+int evp_diagnostics(evp_state* s, evp_diag* out);
+
 /* Self-test of the current device (the paper has no counterpart): checks the
  * integer-operation conversions between binary32 and binary64 that the FP64
  * divergence residual and the FP32 Thomas sweep use against the hardware

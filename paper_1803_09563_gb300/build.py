@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, 'csrc')
 INCLUDE = os.path.join(ROOT, 'include')
 OUT = os.path.join(HERE, 'libevp.so')
 BUILD = os.path.join(HERE, '_build')
-SOURCES = ['evp_abi.cu', 'evp_batch.cu', 'k_stress_f32.cu', 'k_stress_f64.cu', 'k_momentum.cu', 'k_poisson.cu', 'k_twophase.cu', 'evp_static.cu', 'k_selftest.cu', 'k_ibm.cu']
+SOURCES = ['evp_abi.cu', 'evp_batch.cu', 'k_diag.cu', 'k_stress_f32.cu', 'k_stress_f64.cu', 'k_momentum.cu', 'k_poisson.cu', 'k_twophase.cu', 'evp_static.cu', 'k_selftest.cu', 'k_ibm.cu']
 
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '-Xcompiler', '-O3',

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <string>
 #include <vector>
@@ -222,6 +223,7 @@ size_t plan(evp_state* s, char* base) {
             for (int q = 0; q < 2; ++q) helm[k][q] = P((size_t)(g.nz / 2 + 1) * g.ny * nxh * sizeof(double2));
     void* st = P(sizeof(unsigned));
     void* md = P(sizeof(unsigned long long));
+    void* dg = P((evp::DIAG_BLOCKS + 1) * sizeof(evp::DiagPart));
     if (base) {
         s->P = p; s->PSI = psi; s->spec = spec;
         s->twx = twx; s->twy = twy; s->twz = twz;
@@ -230,6 +232,7 @@ size_t plan(evp_state* s, char* base) {
         s->thomas_d = static_cast<double*>(thd);
         s->d_status = static_cast<unsigned*>(st);
         s->d_maxdiv = static_cast<unsigned long long*>(md);
+        s->diag = dg;
         s->ab2 = ab2;
         s->PHI = ls[0];
         s->PHI0 = ls[1];
@@ -1311,6 +1314,63 @@ int evp_sync(evp_state* s, unsigned* bits, double* max_div) {
     // with the local artificial diffusion on, det B < 0 is the condition it treats
     if ((st & EVP_BIT_DET_NEG) && !(s->mc.art_diff > 0))
         return fail(EVP_ERR_UNPHYSICAL, "B lost positive definiteness");
+    return EVP_OK;
+}
+
+int evp_diagnostics(evp_state* s, evp_diag* out) {
+    if (!s || !out) return fail(EVP_ERR_ARG, "null state or output");
+    if (int r = wait_batch(s)) return r;
+    CK(cudaMemsetAsync(s->d_maxdiv, 0, sizeof(unsigned long long), s->st));
+    const int cu = s->cu, cb = s->cb;
+    const double ix = s->g.nx / s->g.lx, iy = s->g.ny / s->g.ly, iz = s->g.nz / s->g.lz;
+    DiagPart* parts = static_cast<DiagPart*>(s->diag);
+    DiagPart* res = parts + DIAG_BLOCKS;
+    auto go = [&](auto zero) -> int {
+        using T = decltype(zero);
+        DiagArgs<T> a;
+        a.U = static_cast<const T*>(s->U[cu]);
+        a.V = static_cast<const T*>(s->V[cu]);
+        a.W = static_cast<const T*>(s->W[cu]);
+        const bool hasB = s->model != EVP_NEWTONIAN;
+        for (int c = 0; c < 6; ++c) a.B[c] = hasB ? static_cast<const T*>(s->B[cb][c]) : nullptr;
+        a.H = nullptr;
+        a.gm = s->mc.gmod;
+        a.mp1 = 0.0;
+        a.inv_lam = s->mc.inv_lam;
+        a.tau_y = s->mc.tau_y;
+        a.yield_mode = (s->model == EVP_OLDROYD_B || s->model == EVP_FENE_P) ? 1
+                     : s->model == EVP_SARAMITO ? 2 : 0;
+        if (s->ab2 && s->model == EVP_SARAMITO) {
+            a.H = static_cast<const T*>(s->HF);
+            a.mp1 = (1.0 - s->prm.beta) * (1.0 / s->prm.Re);   // mu_p of fluid 1, as the AB2 step forms it
+        }
+        cudaError_t e = launch_div_residual<T>(geo_of<T>(s), a.U, a.V, a.W, ix, iy, iz, s->d_maxdiv,
+                                               s->d_status, s->st);
+        if (e == cudaSuccess) e = launch_diag<T>(geo_of<T>(s), a, parts, res, s->st);
+        return e == cudaSuccess ? EVP_OK : cuda_fail(e, "diagnostics kernels");
+    };
+    // the residual kernel would OR EVP_BIT_NONFINITE into the status word: read the
+    // word first and put it back, so that evp_sync reports only what the steps raised
+    unsigned st_before = 0;
+    CK(cudaMemcpyAsync(&st_before, s->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+    if (int r = s->fp32 ? go(float(0)) : go(double(0))) return r;
+    DiagPart h;
+    unsigned long long md = 0;
+    CK(cudaMemcpyAsync(&h, res, sizeof(h), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaMemcpyAsync(&md, s->d_maxdiv, sizeof(md), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    CK(cudaMemcpyAsync(s->d_status, &st_before, sizeof(unsigned), cudaMemcpyHostToDevice, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    const double dv = s->g.lx / s->g.nx * (s->g.ly / s->g.ny) * (s->g.lz / s->g.nz);
+    out->kinetic_energy = 0.5 * dv * h.ke;
+    std::memcpy(&out->max_div, &md, sizeof(double));
+    const bool hasB = s->model != EVP_NEWTONIAN;
+    out->min_det_B = hasB ? h.min_det : std::numeric_limits<double>::infinity();
+    out->max_tr_B = hasB ? h.max_tr : 0.0;
+    out->max_tr_B_over_L2 = s->model == EVP_FENE_P ? h.max_tr / s->prm.L2 : 0.0;
+    out->yielded_cells = h.yielded;
+    out->yielded_fraction = double(h.yielded) / double(s->N);
+    out->nonfinite_cells = h.nonfinite;
     return EVP_OK;
 }
 

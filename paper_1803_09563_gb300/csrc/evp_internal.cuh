@@ -572,6 +572,30 @@ template <typename T>
 cudaError_t launch_div_residual(const Geo<T>& g, const T* U, const T* V, const T* W, double idx, double idy,
                                 double idz, unsigned long long* maxdiv, unsigned* status, cudaStream_t st);
 
+// ---- monitoring reductions (evp_diagnostics)
+constexpr int DIAG_BLOCKS = 8 * 152;   // at most this many block partials
+struct DiagPart {
+    double ke;                     // sum of u^2 + v^2 + w^2 (not yet scaled by dx dy dz / 2)
+    double min_det, max_tr;        // of B over the cells
+    unsigned long long yielded;    // cells with F > 0
+    unsigned long long nonfinite;  // cells with a NaN or infinite value
+};
+template <typename T>
+struct DiagArgs {
+    const T* U;
+    const T* V;
+    const T* W;
+    const T* B[6];     // null: no conformation (Newtonian)
+    const T* H;        // Saramito two-phase: Heaviside, tau = (mp1 H / lambda)(B - I); null: single phase
+    double gm;         // single phase: mu_p / lambda
+    double mp1, inv_lam;
+    double tau_y;
+    int yield_mode;    // 0: no yield surface, 1: every cell flows, 2: Saramito |tau^d| > tau_y
+};
+// two launches on st: block partials into parts[0 .. DIAG_BLOCKS), their fold into *out
+template <typename T>
+cudaError_t launch_diag(const Geo<T>& g, const DiagArgs<T>& a, DiagPart* parts, DiagPart* out, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_ls_stage(const Geo<T>& g, const LsArgs<T>& a, bool reinit, cudaStream_t st,
                             const TimingHook& th);

@@ -46,6 +46,7 @@ struct evp_state_s {
     double* thomas_d;
     unsigned* d_status;
     unsigned long long* d_maxdiv;
+    void* diag;          // evp_diagnostics: DIAG_BLOCKS block partials, then the folded record
     // two-phase (AB2) fields
     bool ab2;
     void* PHI;

@@ -65,6 +65,15 @@ class evp_tile_config(ctypes.Structure):
         return (self.stress_kz, self.momentum_kz, self.stress_ctas_per_sm, self.momentum_ctas_per_sm, self.fft_cols)
 
 
+class evp_diag(ctypes.Structure):
+    _fields_ = [('kinetic_energy', c_double), ('max_div', c_double), ('min_det_B', c_double),
+                ('max_tr_B', c_double), ('max_tr_B_over_L2', c_double), ('yielded_fraction', c_double),
+                ('nonfinite_cells', c_ulonglong), ('yielded_cells', c_ulonglong)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -100,6 +109,7 @@ def load(path=None):
         'evp_stress_rhs': (c_int, [c_void_p, c_void_p]),
         'evp_poisson_solve_static': (c_int, [POINTER(evp_grid), c_int, c_void_p, c_void_p, c_void_p]),
         'evp_sync': (c_int, [c_void_p, POINTER(c_uint), POINTER(c_double)]),
+        'evp_diagnostics': (c_int, [c_void_p, POINTER(evp_diag)]),
         'evp_selftest': (c_int, [POINTER(c_ulonglong)]),
         'evp_fma_peak': (c_int, [c_int, POINTER(c_double)]),
         'evp_batch_create': (c_int, [c_int, c_size_t, c_void_p, POINTER(c_void_p)]),
@@ -137,7 +147,8 @@ def exported_symbols():
             'evp_set_graph', 'evp_selftest', 'evp_set_pdl', 'evp_set_particles', 'evp_get_particles',
             'evp_set_fields', 'evp_get_fields', 'evp_fma_peak', 'evp_batch_create', 'evp_batch_admit',
             'evp_batch_evict', 'evp_batch_step', 'evp_batch_info', 'evp_batch_set_graph', 'evp_batch_destroy',
-            'evp_tune', 'evp_tile_time', 'evp_tile_config_get', 'evp_tile_config_set', 'evp_step_io']
+            'evp_tune', 'evp_tile_time', 'evp_tile_config_get', 'evp_tile_config_set', 'evp_step_io',
+            'evp_diagnostics']
 
 
 def _check(code):
@@ -312,15 +323,23 @@ def evp_stress_rhs(state, rt):
     return _check(load().evp_stress_rhs(state, _ptr(rt)[0]))
 
 
-def evp_sync(state, raise_on_error=True):
+def evp_sync(state, raise_on_error=True, max_div=True):
     """Returns (code, status bits, FP64 max |div u| of the current velocity, which
-    after a step is the last projection's output)."""
+    after a step is the last projection's output; None with max_div=False, when
+    no residual kernel runs)."""
     bits = c_uint(0)
     md = c_double(0.0)
-    code = load().evp_sync(state, ctypes.byref(bits), ctypes.byref(md))
+    code = load().evp_sync(state, ctypes.byref(bits), ctypes.byref(md) if max_div else None)
     if raise_on_error and code not in (EVP_OK,):
         _check(code)
-    return code, bits.value, md.value
+    return code, bits.value, md.value if max_div else None
+
+
+def evp_diagnostics(state):
+    """Monitoring quantities of the current state as a dict (evp_diag of evp.h)."""
+    d = evp_diag()
+    _check(load().evp_diagnostics(state, ctypes.byref(d)))
+    return d.as_dict()
 
 
 def evp_fma_peak(precision):
@@ -481,8 +500,11 @@ class Simulation:
     def project(self):
         evp_project(self.handle)
 
-    def sync(self, raise_on_error=True):
-        return evp_sync(self.handle, raise_on_error)
+    def sync(self, raise_on_error=True, max_div=True):
+        return evp_sync(self.handle, raise_on_error, max_div)
+
+    def diagnostics(self):
+        return evp_diagnostics(self.handle)
 
 
 class Batch:

@@ -83,11 +83,13 @@ def test_batched_copies_reject_a_null_state(libpath):
 
 
 def test_binding_structs_match_the_header(tmp_path):
-    """The ctypes mirrors of evp_grid and evp_params have the C layout: a small C
+    """The ctypes mirrors of the header's structs have the C layout: a small C
     program compiled against include/evp.h prints sizeof and every offsetof."""
     from paper_1803_09563_gb300 import evp
+    structs = (('evp_grid', evp.evp_grid), ('evp_params', evp.evp_params), ('evp_diag', evp.evp_diag),
+               ('evp_tile_config', evp.evp_tile_config))
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "evp.h"', 'int main(void) {']
-    for cname, ct in (('evp_grid', evp.evp_grid), ('evp_params', evp.evp_params)):
+    for cname, ct in structs:
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
         for fname, _ in ct._fields_:
             lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
@@ -100,7 +102,7 @@ def test_binding_structs_match_the_header(tmp_path):
     for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
         cname, fname, val = line.split()
         got[(cname, fname)] = int(val)
-    for cname, ct in (('evp_grid', evp.evp_grid), ('evp_params', evp.evp_params)):
+    for cname, ct in structs:
         assert got[(cname, 'sizeof')] == ctypes.sizeof(ct), cname
         for fname, _ in ct._fields_:
             assert got[(cname, fname)] == getattr(ct, fname).offset, (cname, fname)
