@@ -47,13 +47,18 @@ typedef enum {
     EVP_ERR_NONFINITE = 4,   /* a kernel produced NaN/Inf (raised at evp_sync)      */
     EVP_ERR_UNPHYSICAL = 5,  /* FENE-P tr B >= L^2, or det B < 0 without art_diff (raised at sync) */
     EVP_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                       */
-    EVP_ERR_STATE = 7        /* call not valid in the state's configuration         */
+    EVP_ERR_STATE = 7,       /* call not valid in the state's configuration         */
+    EVP_ERR_BOUNDS = 8       /* debug build (EVP_DEBUG) only: a kernel's index, range
+                                or alignment check failed (raised at evp_sync)       */
 } evp_status;
 
 /* status bits accumulated by the kernels, returned by evp_sync */
 #define EVP_BIT_NONFINITE   0x1u
 #define EVP_BIT_TRACE_LIMIT 0x2u   /* FENE-P: tr B >= L^2 (Table 1 closure singular)  */
 #define EVP_BIT_DET_NEG     0x4u   /* det B < 0: B lost positive definiteness (Sec 3.1) */
+#define EVP_BIT_BOUNDS      0x8u   /* debug build only: a checked access of a stencil
+                                      kernel was out of its field, out of the kernel's
+                                      shared memory or misaligned; it was skipped      */
 
 /* Grid (Sec. 3): uniform spacing lx/nx, ly/ny, lz/nz.  x and z are periodic;
  * y is periodic (walls_y = 0) or bounded by no-slip walls at y = -ly/2 and

@@ -440,6 +440,7 @@ int substep_t(evp_state* s, double dt, int k, bool last_in_step) {
     }
     {
         MomentumArgs<T> a;
+        a.status = s->d_status;
         a.U = static_cast<const T*>(s->U[cu]);
         a.V = static_cast<const T*>(s->V[cu]);
         a.W = static_cast<const T*>(s->W[cu]);
@@ -1309,6 +1310,7 @@ int evp_sync(evp_state* s, unsigned* bits, double* max_div) {
         std::memcpy(&d, &md, sizeof(d));
         *max_div = d;
     }
+    if (st & EVP_BIT_BOUNDS) return fail(EVP_ERR_BOUNDS, "a checked kernel access failed (debug build)");
     if (st & EVP_BIT_NONFINITE) return fail(EVP_ERR_NONFINITE, "non-finite values in the fields");
     if (st & EVP_BIT_TRACE_LIMIT) return fail(EVP_ERR_UNPHYSICAL, "B reached the FENE-P trace limit");
     // with the local artificial diffusion on, det B < 0 is the condition it treats

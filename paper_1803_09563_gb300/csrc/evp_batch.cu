@@ -28,6 +28,11 @@
 
 using namespace evp;
 
+// The members' argument blocks travel in the batched kernels' parameter space
+// (at most 32764 bytes with the work-list pointer and count).
+static_assert(sizeof(MomentumBatch<double>) + 16 <= 32764, "momentum batch parameters too large");
+static_assert(sizeof(StressBatch<double>) + 16 <= 32764, "stress batch parameters too large");
+
 namespace {
 
 int bfail(int code, const std::string& m) {
@@ -319,6 +324,7 @@ int step_direct(evp_batch* b) {
                 M.kz = mb.cfg.momentum_kz;
                 MomentumArgs<T>& a = M.a;
                 a = MomentumArgs<T>();
+                a.status = s->d_status;
                 const int cu = s->cu, cb = s->cb;
                 a.U = static_cast<const T*>(s->U[cu]);
                 a.V = static_cast<const T*>(s->V[cu]);

@@ -205,6 +205,7 @@ struct MomentumArgs {
     // summed polymer stress tau^k + tau^{k-1} written by the stress kernel; null:
     // built here from Bo and Bn
     const T* S[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    unsigned* status = nullptr;  // the state's status word (reports of the bounds-checked build)
 };
 
 template <typename T>
@@ -436,6 +437,53 @@ struct TimingHook {
 // kernel launched without the attribute.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// ---- bounds-checked build (compiled with -DEVP_DEBUG into libevp_debug.so)
+// The stencil kernels check every staged copy: its source inside one of the
+// kernel's fields, its shared-memory destination inside the kernel's staging
+// area, 16-byte alignment of both for 16-byte copies.  A failed check skips the
+// copy and sets a per-thread flag, which the kernel ORs into its status word as
+// EVP_BIT_BOUNDS when it ends (evp_sync then returns EVP_ERR_BOUNDS); nothing
+// traps.  The staging area is filled with NaN bytes before a tile starts, so a
+// stencil that reads a value no copy has written makes its output non-finite.
+// Without EVP_DEBUG the checks compile to nothing.
+#ifdef EVP_DEBUG
+#define EVP_DBG_DECL bool dbg_fail_ = false
+#define EVP_DBG_OK(cond) ((cond) || (dbg_fail_ = true, false))
+#define EVP_DBG_REPORT(status)                                          \
+    do {                                                                \
+        if (dbg_fail_ && (status)) atomicOr((status), EVP_BIT_BOUNDS);  \
+    } while (0)
+// a staged copy of n elements from s (global) to d (shared); v16: a 16-byte copy.
+// The tile function defines dbg_src_ok(p, n) and dbg_dst_ok(p, n) for its fields
+// and its staging area.
+#define EVP_STAGE_OK(d, s, n, v16) \
+    EVP_DBG_OK(dbg_src_ok((s), (n)) && dbg_dst_ok((d), (n)) && (!(v16) || (dbg_aligned16(s) && dbg_aligned16(d))))
+#else
+#define EVP_DBG_DECL [[maybe_unused]] constexpr bool dbg_fail_ = false
+#define EVP_DBG_OK(cond) true
+#define EVP_STAGE_OK(d, s, n, v16) true
+#define EVP_DBG_REPORT(status) \
+    do {                       \
+    } while (0)
+#endif
+
+// [p, p + n) inside [base, base + count) (debug checks)
+template <typename T>
+__device__ __forceinline__ bool dbg_within(const T* p, int n, const T* base, size_t count) {
+    return base != nullptr && p >= base && p + n <= base + count;
+}
+__device__ __forceinline__ bool dbg_aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Fill [smem, smem + bytes) with 0xff bytes (a NaN in binary32 and binary64);
+// bytes a multiple of 16 and smem 16-byte aligned.  Ends with a barrier.
+__device__ __forceinline__ void dbg_poison(unsigned char* smem, size_t bytes) {
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    const int t = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    uint4* p = reinterpret_cast<uint4*>(smem);
+    for (size_t q = t; q < bytes / 16; q += nt) p[q] = make_uint4(~0u, ~0u, ~0u, ~0u);
+    __syncthreads();
+}
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,

@@ -111,6 +111,26 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
                                               int kz_chunk, int bx, int by, int bz, unsigned char* smraw) {
     static_assert(!D1 || SPRE, "one-ahead staging is a form of the precomputed-stress kernel");
     MomSmemOf<T, SPRE, D1>& sm = *reinterpret_cast<MomSmemOf<T, SPRE, D1>*>(smraw);
+    EVP_DBG_DECL;
+#ifdef EVP_DEBUG
+    dbg_poison(smraw, sizeof(MomSmemOf<T, SPRE, D1>));
+    const size_t dbg_n = (size_t)g.nx * g.ny * g.nz;
+    auto dbg_src_ok = [&](const T* p, int n) {
+        if (dbg_within(p, n, a.U, dbg_n) || dbg_within(p, n, a.V, dbg_n) || dbg_within(p, n, a.W, dbg_n) ||
+            dbg_within(p, n, a.P, dbg_n) || dbg_within(p, n, a.phis_o, dbg_n) || dbg_within(p, n, a.phis_n, dbg_n))
+            return true;
+        for (int c = 0; c < 6; ++c)
+            if (dbg_within(p, n, a.Bo[c], dbg_n) || dbg_within(p, n, a.Bn[c], dbg_n) || dbg_within(p, n, a.S[c], dbg_n))
+                return true;
+        for (int q = 0; q < 3; ++q)
+            if (dbg_within(p, n, (const T*)a.NH[q], dbg_n) || dbg_within(p, n, a.solid[q], dbg_n)) return true;
+        return false;
+    };
+    auto dbg_dst_ok = [&](const T* d, int n) {
+        return (const unsigned char*)d >= smraw &&
+               (const unsigned char*)(d + n) <= smraw + sizeof(MomSmemOf<T, SPRE, D1>);
+    };
+#endif
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int i0 = bx * TX, j0 = by * TY;
     const int k0 = bz * kz_chunk, k1 = min(k0 + kz_chunk, g.nz);
@@ -219,6 +239,7 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 T* dst = &sm.V[q][slot][csm];
+                if (!EVP_STAGE_OK(dst, vel[q] + pv + cvoff[q], E, true)) continue;
                 if (cvfac[q] == 1) cp_async16(dst, vel[q] + pv + cvoff[q]);
                 else copy_scaled(dst, vel[q] + pv + cvoff[q], cvfac[q]);
             }
@@ -229,6 +250,7 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
                 for (int r = 0; r < NV; ++r) {
                     if (psm[r] < 0) continue;
                     T* dst = &sm.V[q][slot][psm[r]];
+                    if (!EVP_STAGE_OK(dst, vel[q] + pv + voff[q][r], 1, false)) continue;
                     if (vfac[q][r] == 1)
                         cp_async(dst, vel[q] + pv + voff[q][r]);
                     else
@@ -240,11 +262,13 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
         const size_t pp = (size_t)wrap1(kk, g.nz) * plane;
         const int slot = ps_of<D1>(kk);
         if constexpr (VEC) {
-            if (csm >= 0) cp_async16(&sm.P[slot][csm], a.P + pp + ccoff);
+            if (csm >= 0 && EVP_STAGE_OK(&sm.P[slot][csm], a.P + pp + ccoff, E, true))
+                cp_async16(&sm.P[slot][csm], a.P + pp + ccoff);
         } else {
 #pragma unroll
             for (int r = 0; r < NV; ++r)
-                if (psm[r] >= 0) cp_async(&sm.P[slot][psm[r]], a.P + pp + coff[r]);
+                if (psm[r] >= 0 && EVP_STAGE_OK(&sm.P[slot][psm[r]], a.P + pp + coff[r], 1, false))
+                    cp_async(&sm.P[slot][psm[r]], a.P + pp + coff[r]);
         }
     };
     auto fetch_braw = [&](int kk) {
@@ -255,8 +279,10 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
             if (csm < 0) return;
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                cp_async16(&sm.Braw[kk & 1][c][csm], a.Bo[c] + pb + ccoff);
-                cp_async16(&sm.Braw[kk & 1][6 + c][csm], a.Bn[c] + pb + ccoff);
+                if (EVP_STAGE_OK(&sm.Braw[kk & 1][c][csm], a.Bo[c] + pb + ccoff, E, true))
+                    cp_async16(&sm.Braw[kk & 1][c][csm], a.Bo[c] + pb + ccoff);
+                if (EVP_STAGE_OK(&sm.Braw[kk & 1][6 + c][csm], a.Bn[c] + pb + ccoff, E, true))
+                    cp_async16(&sm.Braw[kk & 1][6 + c][csm], a.Bn[c] + pb + ccoff);
             }
         } else {
 #pragma unroll
@@ -264,8 +290,10 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
 #pragma unroll
                 for (int r = 0; r < NV; ++r)
                     if (psm[r] >= 0) {
-                        cp_async(&sm.Braw[kk & 1][c][psm[r]], a.Bo[c] + pb + coff[r]);
-                        cp_async(&sm.Braw[kk & 1][6 + c][psm[r]], a.Bn[c] + pb + coff[r]);
+                        if (EVP_STAGE_OK(&sm.Braw[kk & 1][c][psm[r]], a.Bo[c] + pb + coff[r], 1, false))
+                            cp_async(&sm.Braw[kk & 1][c][psm[r]], a.Bo[c] + pb + coff[r]);
+                        if (EVP_STAGE_OK(&sm.Braw[kk & 1][6 + c][psm[r]], a.Bn[c] + pb + coff[r], 1, false))
+                            cp_async(&sm.Braw[kk & 1][6 + c][psm[r]], a.Bn[c] + pb + coff[r]);
                     }
         }
         }
@@ -278,13 +306,16 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
             if constexpr (VEC) {
                 if (csm < 0) return;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) cp_async16(&sm.S[c][slot][csm], a.S[c] + pb + ccoff);
+                for (int c = 0; c < 6; ++c)
+                    if (EVP_STAGE_OK(&sm.S[c][slot][csm], a.S[c] + pb + ccoff, E, true))
+                        cp_async16(&sm.S[c][slot][csm], a.S[c] + pb + ccoff);
             } else {
 #pragma unroll
                 for (int c = 0; c < 6; ++c)
 #pragma unroll
                     for (int r = 0; r < NV; ++r)
-                        if (psm[r] >= 0) cp_async(&sm.S[c][slot][psm[r]], a.S[c] + pb + coff[r]);
+                        if (psm[r] >= 0 && EVP_STAGE_OK(&sm.S[c][slot][psm[r]], a.S[c] + pb + coff[r], 1, false))
+                            cp_async(&sm.S[c][slot][psm[r]], a.S[c] + pb + coff[r]);
             }
         }
     };
@@ -315,7 +346,10 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
                 if (a.phis_o) {
                     // soft particles: tau = phi_s G (B - I) at both levels
                     const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
-                    const T po = gm * __ldg(a.phis_o + pb + coff[r]), pn = gm * __ldg(a.phis_n + pb + coff[r]);
+                    const bool pok = EVP_DBG_OK(dbg_src_ok(a.phis_o + pb + coff[r], 1) &&
+                                                dbg_src_ok(a.phis_n + pb + coff[r], 1));
+                    const T po = pok ? gm * __ldg(a.phis_o + pb + coff[r]) : T(0);
+                    const T pn = pok ? gm * __ldg(a.phis_n + pb + coff[r]) : T(0);
 #pragma unroll
                     for (int c = 0; c < 6; ++c) {
                         const T d = (c == 0 || c == 3 || c == 5) ? T(1) : T(0);
@@ -349,11 +383,14 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
             if (hch) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
-                    cp_async16(&sm.H[hs_of<D1>(kk)][q][hr * TX + hq], a.NH[q] + (size_t)kk * plane + hoff);
+                    if (EVP_STAGE_OK(&sm.H[hs_of<D1>(kk)][q][hr * TX + hq], a.NH[q] + (size_t)kk * plane + hoff, E, true))
+                        cp_async16(&sm.H[hs_of<D1>(kk)][q][hr * TX + hq], a.NH[q] + (size_t)kk * plane + hoff);
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) cp_async(&sm.H[hs_of<D1>(kk)][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
+            for (int q = 0; q < 3; ++q)
+                if (EVP_STAGE_OK(&sm.H[hs_of<D1>(kk)][q][tid], a.NH[q] + (size_t)kk * plane + cell0, 1, false))
+                    cp_async(&sm.H[hs_of<D1>(kk)][q][tid], a.NH[q] + (size_t)kk * plane + cell0);
         }
     };
 
@@ -512,7 +549,7 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
             iy += a.alpha * fys;
             iz += a.alpha * fzs;
         }
-        if (active) {
+        if (active && EVP_DBG_OK((size_t)k * plane + (size_t)j * g.nx + i < plane * (size_t)g.nz)) {
             const size_t c0 = (size_t)k * plane + (size_t)j * g.nx + i;
             T us = u0 + a.dt * ix, vs = v0 + a.dt * iy, ws = w0 + a.dt * iz;
             if (a.solid[0]) {
@@ -543,6 +580,10 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
             __syncthreads();
         }
     }
+    // two-plane staging: the last request (two planes past the chunk) may still be
+    // in flight; let it land before the tile's shared memory is given up
+    if constexpr (!D1) cp_async_wait_all();
+    EVP_DBG_REPORT(a.status);
 }
 
 template <typename T, int MODEL, bool VEC, bool SPRE>
@@ -574,8 +615,6 @@ k_momentum_batch(const __grid_constant__ MomentumBatch<T> p, const int4* __restr
         const int4 t = __ldg(work + w);
         const MomentumMember<T>& m = p.m[t.x];
         momentum_tile<T, EVP_OLDROYD_B, VEC, true>(m.g, m.mc, m.a, m.kz, t.y, t.z, t.w, smraw);
-        // the tile's last request (two planes past its chunk) may still be in flight
-        cp_async_wait_all();
         __syncthreads();
     }
 }

@@ -123,6 +123,22 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
                                             int kz_chunk, int bx, int by, int bz, unsigned char* smraw) {
     constexpr bool RHS_ONLY = MODE == 0, READ_H = MODE >= 2, WRITE_H = MODE == 1 || MODE == 2;
     StressSmem<T>& sm = *reinterpret_cast<StressSmem<T>*>(smraw);
+    EVP_DBG_DECL;
+#ifdef EVP_DEBUG
+    dbg_poison(smraw, sizeof(StressSmem<T>));
+    const size_t dbg_n = (size_t)g.nx * g.ny * g.nz;
+    auto dbg_src_ok = [&](const T* p, int n) {
+        if (dbg_within(p, n, a.U, dbg_n) || dbg_within(p, n, a.V, dbg_n) || dbg_within(p, n, a.W, dbg_n) ||
+            dbg_within(p, n, a.H, dbg_n))
+            return true;
+        for (int c = 0; c < 6; ++c)
+            if (dbg_within(p, n, a.B[c], dbg_n) || dbg_within(p, n, (const T*)a.RT[c], dbg_n)) return true;
+        return false;
+    };
+    auto dbg_dst_ok = [&](const T* d, int n) {
+        return (const unsigned char*)d >= smraw && (const unsigned char*)(d + n) <= smraw + sizeof(StressSmem<T>);
+    };
+#endif
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int i0 = bx * TX, j0 = by * TY;
     const int k0 = bz * kz_chunk;
@@ -290,6 +306,7 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 T* dst = &sm.V[q][slot][csm];
+                if (!EVP_STAGE_OK(dst, cv_src[q] + pv, E, true)) continue;
                 if (cvfac[q] == 1) cp_async16(dst, cv_src[q] + pv);
                 else copy_scaled(dst, cv_src[q] + pv, cvfac[q]);
             }
@@ -300,6 +317,7 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
                 for (int r = 0; r < NVH; ++r) {
                     if (vsm[r] < 0) continue;
                     T* dst = &sm.V[q][slot][vsm[r]];
+                    if (!EVP_STAGE_OK(dst, vel[q] + pv + voff[q][r], 1, false)) continue;
                     if (vfac[q][r] == 1)
                         cp_async(dst, vel[q] + pv + voff[q][r]);
                     else
@@ -314,13 +332,15 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
         if constexpr (VEC) {
 #pragma unroll
             for (int r = 0; r < NRC; ++r)
-                if (rc_sm[r] >= 0) cp_async16(&sm.B[buf][0][0] + rc_sm[r], rc_src[r] + ph);
+                if (rc_sm[r] >= 0 && EVP_STAGE_OK(&sm.B[buf][0][0] + rc_sm[r], rc_src[r] + ph, E, true))
+                    cp_async16(&sm.B[buf][0][0] + rc_sm[r], rc_src[r] + ph);
         } else {
 #pragma unroll
             for (int c = 0; c < 6; ++c)
 #pragma unroll
                 for (int r = 0; r < NBH; ++r)
-                    if (hsm[r] >= 0) cp_async(&sm.B[buf][c][hsm[r]], a.B[c] + ph + hoff[r]);
+                    if (hsm[r] >= 0 && EVP_STAGE_OK(&sm.B[buf][c][hsm[r]], a.B[c] + ph + hoff[r], 1, false))
+                        cp_async(&sm.B[buf][c][hsm[r]], a.B[c] + ph + hoff[r]);
         }
     };
     // plane kk of B for the tile's own columns into ring slot kk & 7 (kk >= -nz)
@@ -330,10 +350,13 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
         if constexpr (VEC) {
 #pragma unroll
             for (int r = 0; r < NOC; ++r)
-                if (oc_sm[r] >= 0) cp_async16(slot + oc_sm[r], oc_src[r] + pb);
+                if (oc_sm[r] >= 0 && EVP_STAGE_OK(slot + oc_sm[r], oc_src[r] + pb, E, true))
+                    cp_async16(slot + oc_sm[r], oc_src[r] + pb);
         } else {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) cp_async(slot + c * NT + tid, a.B[c] + pb + col);
+            for (int c = 0; c < 6; ++c)
+                if (EVP_STAGE_OK(slot + c * NT + tid, a.B[c] + pb + col, 1, false))
+                    cp_async(slot + c * NT + tid, a.B[c] + pb + col);
         }
     };
 
@@ -353,12 +376,15 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
             if constexpr (VEC) {
 #pragma unroll
                 for (int r = 0; r < NOC; ++r)
-                    if (oc_sm[r] >= 0 && oc_act[r])
+                    if (oc_sm[r] >= 0 && oc_act[r] &&
+                        EVP_STAGE_OK(&sm.H[kk & 1][0][0] + oc_sm[r], oc_hsrc[r] + (size_t)kk * plane, E, true))
                         cp_async16(&sm.H[kk & 1][0][0] + oc_sm[r], oc_hsrc[r] + (size_t)kk * plane);
             } else {
                 if (!active) return;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) cp_async(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0);
+                for (int c = 0; c < 6; ++c)
+                    if (EVP_STAGE_OK(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0, 1, false))
+                        cp_async(&sm.H[kk & 1][c][tid], a.RT[c] + (size_t)kk * plane + cell0);
             }
         }
     };
@@ -438,7 +464,8 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
             T gm = kgm;
             if (a.H) {
                 // two-phase mixture: polymer viscosity mu_p(H) of the cell
-                const T Hc = __ldg(a.H + (size_t)k * plane + col);
+                const T* hp = a.H + (size_t)k * plane + col;
+                const T Hc = EVP_DBG_OK(dbg_src_ok(hp, 1)) ? __ldg(hp) : T(0);
                 gm = (a.mu_p1 * Hc + a.mu_p2 * (T(1) - Hc)) * inv_lam;
             }
             T t[6];
@@ -478,6 +505,7 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
         const int sx = uc > T(0) ? 1 : -1, syw = vc > T(0) ? BW : -BW;
         const bool zpos = wc > T(0);
         const size_t cell = (size_t)k * plane + (size_t)j * g.nx + i;
+        const bool wr = active && EVP_DBG_OK(cell < plane * (size_t)g.nz);   // this cell's outputs are written
         const T* Bk = sm.B[k & 1][0];
         const T vx_ = fabs(uc) * g.idx, vy_ = fabs(vc) * g.idy, vz_ = fabs(wc) * g.idz;
         // ring offsets of the z stencil of this cell, far upwind first: planes
@@ -532,18 +560,18 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
                              + (zm + zp - T(2) * bc) * (g.idz * g.idz));
             }
             if (RHS_ONLY) {
-                if (active) a.RT[c][cell] = rt;
+                if (wr) a.RT[c][cell] = rt;
             } else {
                 T inc = dtz * rt;
                 if (READ_H) inc += dtx * sm.H[k & 1][c][tid];
                 bn[c] = b0[c] + inc;
-                if (active) {
+                if (wr) {
                     a.Bn[c][cell] = bn[c];
                     if (WRITE_H) a.RT[c][cell] = rt;
                 }
             }
         }
-        if (active && !RHS_ONLY) {
+        if (wr && !RHS_ONLY) {
             // a non-finite component makes the sum non-finite
             if (!isfinite(bn[0] + bn[1] + bn[2] + bn[3] + bn[4] + bn[5])) bits |= EVP_BIT_NONFINITE;
             if (MODEL == EVP_FENE_P && bn[0] + bn[3] + bn[5] >= kL2) bits |= EVP_BIT_TRACE_LIMIT;
@@ -581,6 +609,7 @@ __device__ __forceinline__ void stress_tile(const Geo<T>& g, const ModelConst& m
         __syncthreads();
     }
     if (bits) atomicOr(a.status, bits);
+    EVP_DBG_REPORT(a.status);
 }
 
 template <typename T, int MODEL, int MODE, bool DIFF, bool VEC>

@@ -14,12 +14,14 @@ from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_size_t, c_u
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, 'libevp.so')
+# EVP_LIB selects another in-tree build of the library (the bounds-checked
+# libevp_debug.so of ``build.py --debug``)
+LIB_PATH = os.environ.get('EVP_LIB') or os.path.join(HERE, 'libevp.so')
 
 # evp_status
 EVP_OK, EVP_ERR_ARG, EVP_ERR_OOM, EVP_ERR_CUDA, EVP_ERR_NONFINITE, EVP_ERR_UNPHYSICAL, EVP_ERR_TIMEOUT, \
-    EVP_ERR_STATE = range(8)
-EVP_BIT_NONFINITE, EVP_BIT_TRACE_LIMIT, EVP_BIT_DET_NEG = 0x1, 0x2, 0x4
+    EVP_ERR_STATE, EVP_ERR_BOUNDS = range(9)
+EVP_BIT_NONFINITE, EVP_BIT_TRACE_LIMIT, EVP_BIT_DET_NEG, EVP_BIT_BOUNDS = 0x1, 0x2, 0x4, 0x8
 # evp_model
 EVP_NEWTONIAN, EVP_OLDROYD_B, EVP_FENE_P, EVP_SARAMITO, EVP_NEO_HOOKEAN = range(5)
 MODEL_IDS = {'newtonian': 0, 'oldroyd_b': 1, 'fene_p': 2, 'saramito': 3, 'neo_hookean': 4}
