@@ -3,7 +3,7 @@
 Workload (default): Saramito EVP channel, 256 x 128 x 128 (x, y, z), periodic in x
 and z, no-slip walls at y = +-1, Re = 100, Wi = 1, Bi = 0.5, beta = 0.5, body force
 dp/dx = 2/Re, dt = 2e-3, laminar Poiseuille base flow plus a seeded solenoidal
-perturbation of max-norm 1e-2 with |k| <= 8.  FP32 fields and stencils, FP64 Thomas
+perturbation of max-norm 1e-2 with |k| <= 8.  FP32 fields and stencils, double-single Thomas
 sweeps ("FP32-served"), with the same run in FP64 ("FP64 plain") beside it.  The
 FP64 divergence residual of the final state is evaluated at sync, after the timed
 steps (the steps compute none).
@@ -156,7 +156,7 @@ def algorithmic_bytes(kernel, w, elt, walls):
         return 3 * (3 * N * elt + spec), 3
     if kernel in ('fft_z_forward', 'fft_z_inverse', 'fft_y_modal_solve'):
         return 3 * 2 * spec, 3
-    if kernel == 'thomas_y_fp64':
+    if kernel == 'thomas_y':
         return 3 * 2 * spec, 3
     if kernel == 'ifft_x_psi':
         return 3 * (spec + N * elt), 3
@@ -413,7 +413,7 @@ def run_gpu(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": "Mcell-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 Thomas; FP64 divergence residual of the final state at sync)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (double-single Thomas sweep; FP64 divergence residual of the final state at sync)",
         "data": "synthetic (seeded Poiseuille + solenoidal perturbation)",
         "config": {"workload": w['name'], "grid": [w['nx'], w['ny'], w['nz']], "model": w['model'],
                    "Re": w['Re'], "Wi": w['Wi'], "Bi": w['Bi'], "beta": w['beta'], "dt": w['dt'],

@@ -101,7 +101,8 @@ typedef struct {
     int bi_def;
     double dpdx;
     double abc_amp, abc_k;
-    int precision;      /* EVP_FP64 or EVP_FP32 (the Thomas sweeps run in FP64 in both) */
+    int precision;      /* EVP_FP64 or EVP_FP32 (wall-normal Thomas sweeps: FP64 for EVP_FP64,
+                           double-single, two floats of about 48 bits, for EVP_FP32) */
     int integrator;     /* EVP_RK3 (Eq. RK) or EVP_AB2 (two-phase step)                 */
     double mu_ratio;    /* AB2: drop total viscosity / outer total viscosity            */
     double ls_eps_cells;/* AB2: half-width of the smoothed Heaviside, in cells          */
@@ -132,7 +133,7 @@ typedef struct {
                            NS-num1 read literally: alpha^k mu_s lap u at levels k-1
                            (explicit) and k (implicit), i.e. one Helmholtz solve
                            u* - alpha^k dt mu_s lap u* = rhs per velocity component and
-                           substep (FFT in x, z; FP64 Thomas along a wall-bounded y).
+                           substep (FFT in x, z; Thomas along a wall-bounded y).
                            Not with penalization.                                       */
     int soft_particles; /* RK3, model EVP_NEO_HOOKEAN: soft particles in one continuum
                            (Sec. 3.3.2): the solid volume fraction phi_s (field EVP_PHI,
@@ -266,7 +267,7 @@ int evp_substep(evp_state* s, double dt, int k);
 int evp_project(evp_state* s);
 
 /* Solve lap(psi) = rhs with the state's fast Poisson solver (FFT in periodic
- * directions, FP64 Thomas along a wall-bounded y; Eq. NS-num2).  rhs and psi
+ * directions, Thomas along a wall-bounded y; Eq. NS-num2).  rhs and psi
  * are device buffers of nx*ny*nz elements (state precision); rhs may equal psi.
  * Periodic: the mean of rhs is ignored and psi has zero mean.  Walls: the
  * (kx, kz) = (0, 0) system is pinned by psi = 0 in its first row.             */

@@ -36,7 +36,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 
 const char* KERNEL_NAMES[K_COUNT] = {"stress_weno_update", "momentum_predictor", "div_fft_x",
-                                     "fft_z_forward",      "fft_y_modal_solve",  "thomas_y_fp64",
+                                     "fft_z_forward",      "fft_y_modal_solve",  "thomas_y",
                                      "fft_z_inverse",      "ifft_x_psi",         "project_correct",
                                      "levelset_stage",     "interface_force",    "ibm_forcing"};
 
@@ -313,9 +313,15 @@ int upload_tables(evp_state* s) {
         CK(put(s->trig, t));
     }
     if (g.walls_y) {
-        // FP64 Thomas table (m_j, e_j) per (kz <= nz/2, kx)
+        // Thomas table (m_j, c'_j) per (kz <= nz/2, kx), built in FP64
         const std::vector<double> M = thomas_table(g.ny, g.nz, nxh, dy, lx, lam(g.nz, g.nz / 2 + 1, dz));
-        CK(cudaMemcpyAsync(s->thomas_m, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
+        if (sizeof(T) == 4) {
+            // single-precision states sweep in double-single arithmetic (k_thomas)
+            const std::vector<float> F = thomas_table_ds(M);
+            CK(cudaMemcpyAsync(s->thomas_m, F.data(), F.size() * sizeof(float), cudaMemcpyHostToDevice, s->st));
+        } else {
+            CK(cudaMemcpyAsync(s->thomas_m, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, s->st));
+        }
     }
     return cudaStreamSynchronize(s->st) == cudaSuccess ? EVP_OK : cuda_fail(cudaGetLastError(), "tables");
 }
@@ -382,7 +388,12 @@ int prepare_helmholtz(evp_state* s, double dt) {
     for (int k = 0; k < 3; ++k)
         for (int q = 0; q < 2; ++q) {
             const std::vector<double> M = helmholtz_table(g.ny, g.nz, nxh, dy, lx, lz, RK3_ALPHA_H[k] * dt * mu_s, q == 1);
-            CK(cudaMemcpy(s->helm[k][q], M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice));
+            if (s->fp32) {
+                const std::vector<float> F = thomas_table_ds(M);
+                CK(cudaMemcpy(s->helm[k][q], F.data(), F.size() * sizeof(float), cudaMemcpyHostToDevice));
+            } else {
+                CK(cudaMemcpy(s->helm[k][q], M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice));
+            }
         }
     s->helm_dt = dt;
     return EVP_OK;

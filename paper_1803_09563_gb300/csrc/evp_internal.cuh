@@ -567,6 +567,21 @@ inline std::vector<double> helmholtz_table(int ny, int nz, int nxh, double dy, c
     return M;
 }
 
+// Host: a Thomas table (pairs (m_j, c'_j) of doubles) in the format of the
+// single-precision states, whose sweep runs in double-single arithmetic: every
+// double x becomes the unevaluated sum hi + lo of two floats, hi = x rounded to
+// float and lo = the remainder x - hi rounded to float, so an entry is the four
+// floats (m_hi, m_lo, c'_hi, c'_lo) in the 16 bytes of the double pair.
+inline std::vector<float> thomas_table_ds(const std::vector<double>& M) {
+    std::vector<float> F(M.size() * 2);
+    for (size_t q = 0; q < M.size(); ++q) {
+        const float hi = static_cast<float>(M[q]);
+        F[2 * q] = hi;
+        F[2 * q + 1] = static_cast<float>(M[q] - static_cast<double>(hi));
+    }
+    return F;
+}
+
 // device self-test of widen_f32 / narrow_f64 (k_selftest.cu)
 cudaError_t run_selftest(unsigned long long* mismatches);
 // best rate of plain FMAs of the current device, in FLOP/s (k_selftest.cu)

@@ -6,7 +6,7 @@
 // plugins whose host framework owns every allocation, or processes that run
 // under a fixed device-memory budget and must not grow it.  For them this entry
 // point keeps all of its scratch (spectral buffer, FFT twiddles, modal
-// eigenvalues, Thomas pivots and the FP64 sweep buffer) in one file-scope device
+// eigenvalues, Thomas pivots and the sweep buffer) in one file-scope device
 // array of fixed size.  The caller passes only the right-hand side and the
 // output.
 //
@@ -83,7 +83,8 @@ StaticLayout layout_of(const evp_grid& g, size_t elt) {
 
 // Host-built tables (same definitions as the state-owning path): twiddles
 // exp(-2 pi i m/n), eigenvalues (2 - 2 cos(2 pi m/n))/h^2 and, with walls, the
-// FP64 Thomas pivots (m_j, c'_j) with Neumann rows and the (0, 0) system pinned.
+// Thomas pivots (m_j, c'_j) with Neumann rows and the (0, 0) system pinned (FP64
+// pairs, or their double-single form for single precision).
 template <typename T>
 int upload_static_tables(const evp_grid& g, unsigned char* base, const StaticLayout& L, cudaStream_t st) {
     const double dx = g.lx / g.nx, dy = g.ly / g.ny, dz = g.lz / g.nz;
@@ -118,9 +119,14 @@ int upload_static_tables(const evp_grid& g, unsigned char* base, const StaticLay
     if ((e = put(L.lamz, lam(g.nz, g.nz, dz))) != cudaSuccess) return EVP_ERR_CUDA;
     if (g.walls_y) {
         const std::vector<double> M = thomas_table(g.ny, g.nz, nxh, dy, lx, lam(g.nz, g.nz / 2 + 1, dz));
-        if ((e = cudaMemcpyAsync(base + L.thm, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, st)) !=
+        // single precision: the double-single table of k_thomas (same bytes per entry)
+        const std::vector<float> F = sizeof(T) == 4 ? thomas_table_ds(M) : std::vector<float>();
+        const void* src = sizeof(T) == 4 ? static_cast<const void*>(F.data()) : static_cast<const void*>(M.data());
+        if ((e = cudaMemcpyAsync(base + L.thm, src, M.size() * sizeof(double), cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
             return EVP_ERR_CUDA;
+        // the host vectors end with this scope: the copy from pageable memory has
+        // been staged when cudaMemcpyAsync returns
     }
     return EVP_OK;
 }

@@ -3,7 +3,8 @@
 //   lap(psi) = div(u*) / (2 alpha^k dt);  u^k = u* - 2 alpha^k dt grad(psi);  p^k = p^{k-1} + psi
 //
 // psi is found with FFTs in the periodic directions and, along a wall-bounded y,
-// an FP64 tridiagonal (Thomas) solve per Fourier mode; the modal eigenvalues are
+// a tridiagonal (Thomas) solve per Fourier mode (FP64, or double-single in FP32
+// states); the modal eigenvalues are
 // those of the discrete 7-point Laplacian, (2 - 2 cos(2 pi m/n))/h^2.
 //
 // Passes over the spectral buffer spec[nz][ny][nx/2+1] (complex):
@@ -12,7 +13,8 @@
 //   k_fft_col     forward complex FFT along z (columns of TK consecutive kx).
 //   k_fft_col     periodic y: forward FFT along y, modal division, inverse FFT
 //                 (one pass).
-//   k_thomas      walls: FP64 Thomas sweep along y per (kx, kz), pivots from a table.
+//   k_thomas      walls: Thomas sweep along y per (kx, kz), pivots from a table; FP64
+//                 for FP64 states, double-single (pairs of floats) for FP32 states.
 //   k_fft_col     inverse FFT along z.
 //   k_ifftx       x complex-to-real inverse FFT -> psi.
 //   k_correct     u = u* - c grad psi, p += psi (non-finite -> status).
@@ -603,6 +605,155 @@ k_ifftx_r_b(const Geo<T> g, const FFTTables<T> tb, const __grid_constant__ Poiss
 }
 
 
+// ---- double-single arithmetic (Dekker, "A floating-point technique for
+// extending the available precision", 1971; Knuth's two-sum): a value is the
+// unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2, about 48
+// significant bits.  Each operation is rounded as written (__fadd_rn, __fmul_rn,
+// __fmaf_rn: no contraction or reassociation by the compiler).
+struct DS {
+    float hi, lo;
+};
+// s + e = a + b exactly when |a| >= |b| or a = 0 (Dekker's fast two-sum)
+__device__ __forceinline__ DS ds_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// s + e = a + b exactly for any a, b (Knuth's two-sum)
+__device__ __forceinline__ DS ds_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    return {s, __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv))};
+}
+// a - b: the high parts exactly, the low parts with one rounding, then
+// renormalised; the error is a few units of 2^-48 (|a| + |b|)
+__device__ __forceinline__ DS ds_sub(DS a, DS b) {
+    DS s = ds_two_sum(a.hi, -b.hi);
+    s.lo = __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo));
+    return ds_fast_two_sum(s.hi, s.lo);
+}
+// a b: the rounding error of hi*hi exactly by one fused multiply-add, the cross
+// terms added to it, lo*lo dropped; error a few units of 2^-48 |a b|
+__device__ __forceinline__ DS ds_mul(DS a, DS b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ds_fast_two_sum(p, e);
+}
+
+// S6 with walls, single-precision states: the sweep of k_thomas_body below in
+// double-single arithmetic on the FP32 pipes (GB300 runs FP64 at 1/64 of the
+// FP32 rate).  The table holds (m_hi, m_lo, c'_hi, c'_lo) per entry
+// (thomas_table_ds), the scratch the forward values as (hi, lo) float pairs.  The
+// result is hi + lo rounded once to float.  With about 48 bits in every
+// operation the sweep's rounding stays some 2^-40 below the FP32 result even for
+// the worst-conditioned (lowest) modes of a 512-row wall-normal system.
+__device__ __forceinline__ void thomas_ds_body(const Geo<float>& g, const FFTTables<float>& tb,
+                                               const PoissonArgs<float>& a) {
+    constexpr int TB = 16;
+    const int nxh = g.nx / 2 + 1, ny = g.ny, nz = g.nz;
+    const int row = 2 * nxh;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= row * nz) return;
+    const int kz = gid / row, t = gid - kz * row;             // t = 2*kx + part
+    const int kx = t >> 1;
+    const int kzh = kz <= nz - kz ? kz : nz - kz;
+    const bool pinned = !a.ttab && kx == 0 && kz == 0;                     // Poisson only
+    // entries (m_hi, m_lo, c'_hi, c'_lo) (thomas_table_ds)
+    const float4* M = reinterpret_cast<const float4*>(a.ttab ? a.ttab : tb.thomas_m) + (size_t)kzh * ny * nxh + kx;
+    float* col = reinterpret_cast<float*>(a.spec + (size_t)kz * ny * nxh) + t;
+    float2* D = reinterpret_cast<float2*>(a.scratch) + (size_t)kz * ny * (2 * nxh) + t;
+    const size_t rs = 2 * (size_t)nxh;
+    const size_t ms = (size_t)nxh;
+    const double sub = a.ttab ? a.tsub : tb.idy2;                          // the sub-diagonal
+    const float sub_hi = (float)sub;
+    const DS lo = {sub_hi, (float)(sub - (double)sub_hi)};
+    auto m_at = [&](int j) { return __ldg(reinterpret_cast<const float2*>(M + j * ms)); };
+    auto c_at = [&](int j) { return __ldg(reinterpret_cast<const float2*>(M + j * ms) + 1); };
+
+    // ---- forward: d'_j = (r_j - sub d'_{j-1}) m_j, d'_0 = r_0 m_0
+    DS d = {0.f, 0.f};
+    auto fwd = [&](int jj, float r, float2 m) {
+        const DS rr = {(pinned && jj == 0) ? 0.f : r, 0.f};
+        const DS mv = {m.x, m.y};
+        d = ds_mul(jj > 0 ? ds_sub(rr, ds_mul(lo, d)) : rr, mv);
+        D[jj * rs] = make_float2(d.hi, d.lo);
+    };
+    const int nfull = ny / TB * TB;
+    float rf[TB];
+    float2 mm[TB];
+    if (nfull > 0) {
+#pragma unroll
+        for (int u = 0; u < TB; ++u) {
+            rf[u] = col[u * rs];
+            mm[u] = m_at(u);
+        }
+    }
+    for (int jb = 0; jb < nfull; jb += TB) {
+        float rn[TB];
+        float2 mn[TB];
+        const bool more = jb + TB < nfull;
+        if (more) {
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+                rn[u] = col[(jb + TB + u) * rs];
+                mn[u] = m_at(jb + TB + u);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TB; ++u) fwd(jb + u, rf[u], mm[u]);
+        if (more) {
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+                rf[u] = rn[u];
+                mm[u] = mn[u];
+            }
+        }
+    }
+    for (int jj = nfull; jj < ny; ++jj) fwd(jj, col[jj * rs], m_at(jj));
+
+    // ---- back substitution: psi_{ny-1} = d'_{ny-1}, psi_j = d'_j - c'_j psi_{j+1}
+    DS x = d;
+    col[(ny - 1) * rs] = __fadd_rn(x.hi, x.lo);
+    auto bwd = [&](int jj, float2 dp, float2 c) {
+        x = ds_sub(DS{dp.x, dp.y}, ds_mul(DS{c.x, c.y}, x));
+        col[jj * rs] = __fadd_rn(x.hi, x.lo);
+    };
+    const int top = ny - 2;
+    const int nrest = (ny - 1) % TB;
+    for (int jj = top; jj > top - nrest; --jj) bwd(jj, D[jj * rs], c_at(jj));
+    const int jstart = top - nrest;                 // first row of the first full batch (from the top)
+    if (jstart >= 0) {
+        float2 dd[TB], cc[TB];
+#pragma unroll
+        for (int u = 0; u < TB; ++u) {
+            dd[u] = D[(jstart - u) * rs];
+            cc[u] = c_at(jstart - u);
+        }
+        for (int jt = jstart; jt >= 0; jt -= TB) {
+            float2 dn[TB], cn[TB];
+            const bool more = jt - TB >= 0;
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < TB; ++u) {
+                    dn[u] = D[(jt - TB - u) * rs];
+                    cn[u] = c_at(jt - TB - u);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TB; ++u) bwd(jt - u, dd[u], cc[u]);
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < TB; ++u) {
+                    dd[u] = dn[u];
+                    cc[u] = cn[u];
+                }
+            }
+        }
+    }
+}
+
 // S6 with walls: for each (kx, kz) solve
 //   psi_{j-1}/dy^2 - (2/dy^2 + lx + lz) psi_j + psi_{j+1}/dy^2 = r_j
 // with Neumann rows at j = 0 and ny-1 and the (0, 0) system pinned by psi_0 = 0,
@@ -615,9 +766,7 @@ k_ifftx_r_b(const Geo<T> g, const FFTTables<T> tb, const __grid_constant__ Poiss
 // not wait on a memory round trip per row; rows that do not fill a batch are
 // done one by one.  The FFT normalisation is applied later, in the inverse x pass.
 template <typename T>
-__device__ __forceinline__ void k_thomas_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a) {
-    pdl_wait();
-    pdl_trigger();
+__device__ __forceinline__ void thomas_fp64_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a) {
     constexpr int TB = 16;
     const int nxh = g.nx / 2 + 1, ny = g.ny, nz = g.nz;
     const int row = 2 * nxh;
@@ -722,6 +871,13 @@ __device__ __forceinline__ void k_thomas_body(const Geo<T>& g, const FFTTables<T
             }
         }
     }
+}
+template <typename T>
+__device__ __forceinline__ void k_thomas_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a) {
+    pdl_wait();
+    pdl_trigger();
+    if constexpr (sizeof(T) == 4) thomas_ds_body(g, tb, a);
+    else thomas_fp64_body<T>(g, tb, a);
 }
 template <typename T>
 __global__ void __launch_bounds__(32)
@@ -937,7 +1093,7 @@ cudaError_t launch_col(const Geo<T>& g, const FFTTables<T>& tb, const PassLaunch
 }
 
 // The chain of Poisson passes (S4-S7): x pass with the right-hand side, z pass,
-// periodic y solve or FP64 Thomas sweep, inverse z and inverse x passes.
+// periodic y solve or Thomas sweep, inverse z and inverse x passes.
 template <typename T>
 cudaError_t poisson_chain(const Geo<T>& g, const FFTTables<T>& tb, const PassLaunch<T>& L, int tk,
                           const TimingHook& th) {

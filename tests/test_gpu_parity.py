@@ -796,6 +796,36 @@ def test_poisson_solve_power_of_two_sizes(evp, shape, prec, tol):
     assert rel(got, ref) < tol, (shape, prec, rel(got, ref))
 
 
+@pytest.mark.parametrize("shape", [(16, 512, 8, True), (32, 128, 16, True), (8, 36, 8, True)])
+def test_fp32_wall_solve_of_the_lowest_modes_is_rounding_exact(evp, shape):
+    """The (kx, kz) = (0, 0) system of a wall-bounded solve is the pinned 1-D
+    Neumann Laplacian, whose condition number grows like ny^2 (about 1e5 at 512
+    rows): a plain FP32 sweep loses about five digits on it.  A right-hand side
+    that varies in y only reaches the FP32 solve through exact x and z
+    transforms, so the FP32 result must be the FP64 solution of the same
+    (FP32-rounded) data rounded once: within 2 ulps of the oracle, and within 1
+    ulp of the FP64 state's own solve."""
+    import torch
+    nx, ny, nz, walls = shape
+    rng = np.random.default_rng(21)
+    prof = rng.standard_normal(ny) + np.cos(np.pi * (np.arange(ny) + 0.5) / ny)
+    r = np.ascontiguousarray(np.broadcast_to(prof[None, :, None], (nz, ny, nx)), dtype=np.float32).astype(np.float64)
+    out = {}
+    for prec in (evp.EVP_FP32, evp.EVP_FP64):
+        sim, st, g, prm = setup_case(evp, shape, 'oldroyd_b', {}, prec)
+        rd = torch.tensor(r, dtype=torch.float32 if prec else torch.float64, device='cuda').contiguous()
+        psi = torch.empty(rd.shape, dtype=rd.dtype, device='cuda')
+        evp.evp_poisson_solve(sim.handle, rd, psi)
+        sim.sync()
+        out[prec] = psi.cpu().numpy().astype(np.float64)
+        sim.close()
+    ref = oracle.solve_poisson(r, g)
+    scale = np.abs(ref).max()
+    ulp = np.spacing(np.float32(scale)).astype(np.float64)
+    assert np.abs(out[evp.EVP_FP32] - ref).max() <= 2 * ulp, np.abs(out[evp.EVP_FP32] - ref).max() / ulp
+    assert np.abs(out[evp.EVP_FP32] - out[evp.EVP_FP64]).max() <= ulp
+
+
 def test_fene_p_trace_limit_is_reported(evp):
     """A FENE-P state stretched beyond L^2 raises EVP_BIT_TRACE_LIMIT and evp_sync
     returns EVP_ERR_UNPHYSICAL (no clamping, no fault)."""

@@ -125,7 +125,7 @@ def test_ab2_mass_correction_fp32(evp):
 
 @pytest.mark.parametrize("walls", [False, True])
 def test_density_contrast_drop_fp32(evp, walls):
-    """The k_rho = 0.1 split projection in FP32 (FP64 Thomas where there are
+    """The k_rho = 0.1 split projection in FP32 (a double-single Thomas where there are
     walls): velocity, level set and conformation within 1e-5 of the FP64 oracle
     after two steps (the pressure, the projection variable itself, carries the
     FP32 rounding of u* divided by dt, as in the other FP32 AB2 checks)."""
