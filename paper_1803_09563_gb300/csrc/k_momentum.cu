@@ -85,11 +85,15 @@ struct MomSmemS {
     T H[4][3][NT];
 };
 // Staged one plane ahead (D1): while plane k is computed, plane k+2 is being
-// requested; fewer slots, so five CTAs fit on an SM in FP32.
+// requested; fewer slots, so six CTAs fit on an SM in FP32.  Of the summed
+// stress only xz and yz are read at planes k-1 and k+1 (the z derivatives and
+// edge averages of div tau); xx, xy, yy and zz are read at planes k (and k+1 for
+// zz) and keep three slots.
 template <typename T>
 struct MomSmemS1 {
     T V[3][4][VPL];      // planes k-1 .. k+2
-    T S[6][4][VPL];
+    T S4[2][4][VPL];     // S_xz, S_yz: planes k-1 .. k+2
+    T S3[4][3][VPL];     // S_xx, S_xy, S_yy, S_zz: planes k .. k+2
     T P[3][VPL];         // planes k .. k+2
     T H[2][3][NT];       // planes k, k+1
 };
@@ -298,24 +302,35 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
         }
         }
     };
-    // precomputed summed stress plane kk into ring slot kk mod 5 (a centred field)
+    // shared-memory plane of summed-stress component c at plane kk (kk >= -1): a
+    // 3-slot ring built here, a 5-slot ring staged two ahead, or the D1 rings
+    auto splane = [&](int c, int kk) -> T* {
+        if constexpr (!SPRE) {
+            return sm.S[c][pmod(kk, 3)];
+        } else if constexpr (!D1) {
+            return sm.S[c][vs_of<false>(kk)];
+        } else {
+            if (c == 2 || c == 4) return sm.S4[c == 2 ? 0 : 1][vs_of<true>(kk)];
+            return sm.S3[c < 2 ? c : (c == 3 ? 2 : 3)][ps_of<true>(kk)];
+        }
+    };
+    // precomputed summed stress plane kk into its ring slots (a centred field)
     auto fetch_s = [&](int kk) {
         if constexpr (SPRE) {
             const size_t pb = (size_t)wrap1(kk, g.nz) * plane;
-            const int slot = vs_of<D1>(kk);
             if constexpr (VEC) {
                 if (csm < 0) return;
 #pragma unroll
                 for (int c = 0; c < 6; ++c)
-                    if (EVP_STAGE_OK(&sm.S[c][slot][csm], a.S[c] + pb + ccoff, E, true))
-                        cp_async16(&sm.S[c][slot][csm], a.S[c] + pb + ccoff);
+                    if (EVP_STAGE_OK(splane(c, kk) + csm, a.S[c] + pb + ccoff, E, true))
+                        cp_async16(splane(c, kk) + csm, a.S[c] + pb + ccoff);
             } else {
 #pragma unroll
                 for (int c = 0; c < 6; ++c)
 #pragma unroll
                     for (int r = 0; r < NV; ++r)
-                        if (psm[r] >= 0 && EVP_STAGE_OK(&sm.S[c][slot][psm[r]], a.S[c] + pb + coff[r], 1, false))
-                            cp_async(&sm.S[c][slot][psm[r]], a.S[c] + pb + coff[r]);
+                        if (psm[r] >= 0 && EVP_STAGE_OK(splane(c, kk) + psm[r], a.S[c] + pb + coff[r], 1, false))
+                            cp_async(splane(c, kk) + psm[r], a.S[c] + pb + coff[r]);
             }
         }
     };
@@ -525,9 +540,9 @@ __device__ __forceinline__ void momentum_tile(const Geo<T>& g, const ModelConst&
             iz += am * Lw;
         }
         if (stress) {
-            const int s0 = SPRE ? vs_of<D1>(k) : pmod(k, 3), sm1 = SPRE ? vs_of<D1>(k - 1) : pmod(k - 1, 3);
-            const int sp1 = SPRE ? vs_of<D1>(k + 1) : pmod(k + 1, 3);
-            auto S = [&](int c, int slot, int di, int dj) { return sm.S[c][slot][o + dj * VW + di]; };
+            // planes k, k-1 and k+1 (the ring slot of each component comes from splane)
+            const int s0 = k, sm1 = k - 1, sp1 = k + 1;
+            auto S = [&](int c, int kk, int di, int dj) { return splane(c, kk)[o + dj * VW + di]; };
             // 4-point average over centres (0 or di) x (0 or dj) in one plane
             auto e4 = [&](int c, int slot, int di, int dj) {
                 return T(0.25) * (S(c, slot, 0, 0) + S(c, slot, 0, dj) + S(c, slot, di, 0) + S(c, slot, di, dj));
@@ -595,9 +610,9 @@ k_momentum(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_
     momentum_tile<T, MODEL, VEC, SPRE>(g, mc, a, kz_chunk, blockIdx.x, blockIdx.y, blockIdx.z, smraw);
 }
 
-// the precomputed-stress kernel staged one plane ahead, five CTAs per SM in FP32
+// the precomputed-stress kernel staged one plane ahead, six CTAs per SM in FP32
 template <typename T, bool VEC>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 5 : 2)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 6 : 2)
 k_momentum_d1(const Geo<T> g, const ModelConst mc, const MomentumArgs<T> a, int kz_chunk) {
     pdl_wait();
     pdl_trigger();
@@ -638,7 +653,7 @@ cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const Momentu
         // summed stress precomputed by the stress kernel: staged one plane ahead
         if (mc.model == EVP_NEWTONIAN) return cudaErrorInvalidValue;
         const size_t smem = sizeof(MomSmemS1<T>);
-        int ch = (4 * 152 * 5 + tiles - 1) / tiles;
+        int ch = (4 * 152 * 6 + tiles - 1) / tiles;
         ch = ch > g.nz ? g.nz : ch;
         const int kz1 = (g.nz + ch - 1) / ch;
         ch = (g.nz + kz1 - 1) / kz1;
@@ -646,6 +661,8 @@ cudaError_t launch_momentum(const Geo<T>& g, const ModelConst& mc, const Momentu
         th.b(K_MOMENTUM);
         auto kern = vec ? k_momentum_d1<T, true> : k_momentum_d1<T, false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // all of the SM's unified L1 / shared memory as shared memory: six CTAs of 36.7 KB
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (cudaError_t e = launch_k(kern, grid1, block, smem, st, th.pdl, g, mc, a, kz1)) return e;
         th.e(K_MOMENTUM);
         return cudaGetLastError();
