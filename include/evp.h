@@ -227,6 +227,15 @@ int evp_set_graph(evp_state* s, int enable);
  * step graphs are rebuilt on the next step.  The paper has no counterpart.      */
 int evp_set_pdl(evp_state* s, int enable);
 
+/* NVTX ranges for profilers (Nsight Systems timelines, Nsight Compute's --nvtx
+ * filters); off by default.  When on, evp_step and evp_substep each open a range
+ * ("evp_step", "evp_substep k"; "evp_step graph replay" around a replayed
+ * step graph, whose kernels carry no range of their own) and every directly
+ * launched kernel of the step opens one named as in evp_kernel_name.  Host-side
+ * markers only: results are identical either way, and without a profiler
+ * attached a range costs a function-pointer test.  The paper has no counterpart. */
+int evp_set_nvtx(evp_state* s, int enable);
+
 /* Rigid spherical particles coupled to the RK3 step by the discrete-forcing
  * immersed boundary method of Sec. 3.3.2 (Eqs. IBM a-d with the multi-direct
  * forcing of Eq. CoVe2, iters iterations per substep, 3 in the paper): after u*

@@ -12,6 +12,8 @@
 #include "evp_internal.cuh"
 #include "evp_state.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace evp;
 
 namespace {
@@ -85,24 +87,40 @@ void flush_timing(evp_state* s) {
     s->pending.clear();
 }
 
-void hook_begin(void* ctx, int) {
+void hook_begin(void* ctx, int kid) {
     evp_state* s = static_cast<evp_state*>(ctx);
+    if (s->nvtx) nvtxRangePushA(KERNEL_NAMES[kid]);
+    if (!s->timing) return;
     s->cur_start = get_event(s);
     cudaEventRecord(s->cur_start, s->st);
 }
 
 void hook_end(void* ctx, int kid) {
     evp_state* s = static_cast<evp_state*>(ctx);
-    cudaEvent_t e = get_event(s);
-    cudaEventRecord(e, s->st);
-    s->pending.push_back({kid, s->cur_start, e});
-    if (s->pending.size() >= 2048) flush_timing(s);
+    if (s->timing) {
+        cudaEvent_t e = get_event(s);
+        cudaEventRecord(e, s->st);
+        s->pending.push_back({kid, s->cur_start, e});
+        if (s->pending.size() >= 2048) flush_timing(s);
+    }
+    if (s->nvtx) nvtxRangePop();
 }
+
+// An NVTX range for the lifetime of the object when the state's ranges are on
+struct NvtxScope {
+    bool on;
+    NvtxScope(const evp_state* s, const char* name) : on(s && s->nvtx) {
+        if (on) nvtxRangePushA(name);
+    }
+    ~NvtxScope() {
+        if (on) nvtxRangePop();
+    }
+};
 
 TimingHook hook_of(evp_state* s) {
     TimingHook h;
-    h.begin = s->timing ? hook_begin : nullptr;
-    h.end = s->timing ? hook_end : nullptr;
+    h.begin = (s->timing || s->nvtx) ? hook_begin : nullptr;
+    h.end = (s->timing || s->nvtx) ? hook_end : nullptr;
     h.pdl = s->pdl;
     h.ctx = s;
     return h;
@@ -822,6 +840,7 @@ int evp_init(const evp_grid* grid, evp_model model, const evp_params* params, vo
     s->elt = s->fp32 ? 4 : 8;
     s->use_graph = false;
     s->pdl = true;
+    s->nvtx = false;
     s->batch = nullptr;
     s->batch_st = nullptr;
     s->n_part = s->n_lag = 0;
@@ -1000,6 +1019,8 @@ int evp_substep(evp_state* s, double dt, int k) {
     if (k < 0 || k > 2) return fail(EVP_ERR_ARG, "substep index must be 0, 1 or 2");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
     if (int r = prepare_helmholtz(s, dt)) return r;
+    static const char* const SUBSTEP_NAMES[3] = {"evp_substep 0", "evp_substep 1", "evp_substep 2"};
+    NvtxScope range(s, SUBSTEP_NAMES[k]);
     return s->fp32 ? substep_t<float>(s, dt, k, false) : substep_t<double>(s, dt, k, false);
 }
 
@@ -1061,6 +1082,12 @@ extern "C" int evp_set_graph(evp_state* s, int enable) {
     if (!s) return fail(EVP_ERR_ARG, "null state");
     if (enable && s->ab2) return fail(EVP_ERR_STATE, "graph replay covers the RK3 step only");
     s->use_graph = enable != 0;
+    return EVP_OK;
+}
+
+extern "C" int evp_set_nvtx(evp_state* s, int enable) {
+    if (!s) return fail(EVP_ERR_ARG, "null state");
+    s->nvtx = enable != 0;
     return EVP_OK;
 }
 
@@ -1200,9 +1227,18 @@ extern "C" int evp_step(evp_state* s, double dt) {
     if (s->batch) return fail(EVP_ERR_STATE, "the state is a member of a batch: it steps with evp_batch_step");
     if (!(dt > 0)) return fail(EVP_ERR_ARG, "dt must be positive");
     if (int r = prepare_helmholtz(s, dt)) return r;
-    if (s->ab2) return s->fp32 ? ab2_step_t<float>(s, dt) : ab2_step_t<double>(s, dt);
-    if (s->use_graph && !s->timing) return rk3_step_graph(s, dt);
+    if (s->ab2) {
+        NvtxScope range(s, "evp_step");
+        return s->fp32 ? ab2_step_t<float>(s, dt) : ab2_step_t<double>(s, dt);
+    }
+    if (s->use_graph && !s->timing) {
+        NvtxScope range(s, "evp_step graph replay");
+        return rk3_step_graph(s, dt);
+    }
+    NvtxScope range(s, "evp_step");
+    static const char* const SUBSTEP_NAMES[3] = {"evp_substep 0", "evp_substep 1", "evp_substep 2"};
     for (int k = 0; k < 3; ++k) {
+        NvtxScope sub(s, SUBSTEP_NAMES[k]);
         int r = s->fp32 ? substep_t<float>(s, dt, k, k == 2) : substep_t<double>(s, dt, k, k == 2);
         if (r) return r;
     }

@@ -77,6 +77,7 @@ struct evp_state_s {
     // buffer at the start of the step (the three substeps flip it each time)
     bool use_graph;
     bool pdl;            // programmatic dependent launch of the step's kernels
+    bool nvtx;           // NVTX ranges around steps, substeps and kernel launches
     struct StepGraph {
         bool valid;
         double dt;

@@ -103,6 +103,7 @@ def load(path=None):
                                 POINTER(c_void_p)]),
         'evp_set_graph': (c_int, [c_void_p, c_int]),
         'evp_set_pdl': (c_int, [c_void_p, c_int]),
+        'evp_set_nvtx': (c_int, [c_void_p, c_int]),
         'evp_set_particles': (c_int, [c_void_p, c_int, c_void_p, c_int]),
         'evp_get_particles': (c_int, [c_void_p, c_int, c_void_p]),
         'evp_substep': (c_int, [c_void_p, c_double, c_int]),
@@ -150,7 +151,7 @@ def exported_symbols():
             'evp_set_fields', 'evp_get_fields', 'evp_fma_peak', 'evp_batch_create', 'evp_batch_admit',
             'evp_batch_evict', 'evp_batch_step', 'evp_batch_info', 'evp_batch_set_graph', 'evp_batch_destroy',
             'evp_tune', 'evp_tile_time', 'evp_tile_config_get', 'evp_tile_config_set', 'evp_step_io',
-            'evp_diagnostics']
+            'evp_diagnostics', 'evp_set_nvtx']
 
 
 def _check(code):
@@ -280,6 +281,11 @@ def evp_set_graph(state, enable):
 
 def evp_set_pdl(state, enable):
     return _check(load().evp_set_pdl(state, int(bool(enable))))
+
+
+def evp_set_nvtx(state, enable):
+    """NVTX ranges around steps, substeps and directly launched kernels."""
+    return _check(load().evp_set_nvtx(state, int(bool(enable))))
 
 
 def evp_set_particles(state, particles, iters=3):

@@ -520,6 +520,32 @@ def test_programmatic_dependent_launch_changes_nothing(evp, graph, shape, model,
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_nvtx_ranges_change_nothing(evp, graph):
+    """NVTX ranges on (steps, substeps, kernels) with and without kernel timing give
+    the fields of a run without them, bit for bit, and the kernel timing still
+    counts every launch."""
+    out = []
+    for nvtx, timing in ((False, False), (True, False), (True, True)):
+        sim, st, g, prm = setup_case(evp, SHAPES[1], 'saramito', {'Bi': 0.4}, evp.EVP_FP32)
+        evp.evp_set_nvtx(sim.handle, nvtx)
+        evp.evp_set_graph(sim.handle, graph)
+        if timing:
+            evp.evp_kernel_timing(sim.handle, True)
+        for _ in range(2):
+            sim.step(2e-3)
+        sim.substep(2e-3, 0)
+        sim.sync()
+        if timing:
+            times = evp.evp_kernel_times(sim.handle)
+            assert times['stress_weno_update'][1] == 7 and times['project_correct'][1] == 7
+        out.append(fields(sim, evp))
+        sim.close()
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            np.testing.assert_array_equal(a, b)
+
+
 def implicit_case(evp, shape, prec, model='oldroyd_b', extra=None):
     extra = extra or {}
     nx, ny, nz, walls = shape
