@@ -664,6 +664,56 @@ def run_implicit_viscous(steps=50):
     return out
 
 
+def run_thomas_sweeps(steps=200):
+    """The C2 channel in FP32 with the wall-normal Thomas sweep in double-single
+    arithmetic (the default) and in FP64 (thomas_fp64 = 1): step time and the
+    sweep's own time, and the largest difference between the two runs' fields."""
+    import torch
+    from paper_1803_09563_gb300 import evp
+    w = WORKLOAD
+    geo, U, V, W = workload_inputs(w)
+    stream = torch.cuda.Stream()
+    out = {"workload": "saramito_channel_256x128x128_fp32", "steps": steps}
+    fields = {}
+    for name, t in (('double_single', 0), ('fp64', 1)):
+        grid = evp.make_grid(w['nx'], w['ny'], w['nz'], w['lx'], w['ly'], w['lz'], w['walls_y'])
+        prm = evp.make_params(Re=w['Re'], Wi=w['Wi'], beta=w['beta'], Bi=w['Bi'], dpdx=2.0 / w['Re'],
+                              precision=evp.EVP_FP32, thomas_fp64=t)
+        sim = evp.Simulation(grid, w['model'], prm, stream=stream.cuda_stream)
+        sim.set_state(U, V, W)
+        evp.evp_set_graph(sim.handle, True)
+        for _ in range(3):
+            sim.step(w['dt'])
+        sim.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            sim.step(w['dt'])
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        # the sweep's own time: an instrumented pass of direct launches
+        evp.evp_kernel_timing(sim.handle, True)
+        evp.evp_kernel_times(sim.handle)
+        for _ in range(5):
+            sim.step(w['dt'])
+        kt = evp.evp_kernel_times(sim.handle)
+        evp.evp_kernel_timing(sim.handle, False)
+        t_ms, n = kt['thomas_y']
+        out[name] = {"ms_per_step": ms, "Mcell_steps_per_s": w['nx'] * w['ny'] * w['nz'] / (ms * 1e-3) / 1e6,
+                     "thomas_us_per_launch": 1e3 * t_ms / max(n, 1)}
+        fields[name] = [sim.get(f) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W, evp.EVP_BXX, evp.EVP_BXY)]
+        sim.close()
+    rel = 0.0
+    for a, b in zip(fields['double_single'], fields['fp64']):
+        a = a.astype(np.float64)
+        b = b.astype(np.float64)
+        rel = max(rel, float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)))
+    out["max_rel_diff_u_v_w_Bxx_Bxy"] = rel
+    out["steps_compared"] = 3 + steps + 5
+    return out
+
+
 def run_small_grid():
     """Single-phase Oldroyd-B Taylor-Green box 32^3 in FP64 (the 10-step parity
     workload): per-step latency with direct launches and with graph replay."""
@@ -833,6 +883,7 @@ def main():
         line['small_grid'] = run_small_grid()
         line['fene_p_turbulence'] = run_fene_turbulence()
         line['implicit_viscous'] = run_implicit_viscous()
+        line['thomas_sweeps'] = run_thomas_sweeps()
         line['evp_drop'] = run_evp_drop()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:

@@ -140,6 +140,11 @@ typedef struct {
                            0 fluid .. 1 solid) is advected like B (WENO5, RK3 weights)
                            and the extra stress is phi_s G (B - I), G = mu_p/lambda; the
                            surrounding fluid is Newtonian (mu_s)                        */
+    int thomas_fp64;    /* EVP_FP32 states with walls: 0 (default) = the wall-normal Thomas
+                           sweeps in double-single arithmetic (pairs of floats, about 48
+                           significant bits, on the FP32 pipes); 1 = in FP64.  Both give
+                           the FP32 result of the FP64 solve to within an ulp; FP64
+                           states always sweep in FP64                                 */
     double reserved[4];
 } evp_params;
 

@@ -158,6 +158,7 @@ int validate(const evp_grid* g, evp_model model, const evp_params* p) {
     } else if (p->ls_mass_iters != 0) {
         return fail(EVP_ERR_ARG, "the level-set mass correction is part of the AB2 two-phase step");
     }
+    if (p->thomas_fp64 != 0 && p->thomas_fp64 != 1) return fail(EVP_ERR_ARG, "thomas_fp64 must be 0 or 1");
     if (p->soft_particles) {
         if (p->soft_particles != 1) return fail(EVP_ERR_ARG, "soft_particles must be 0 or 1");
         if (model != EVP_NEO_HOOKEAN) return fail(EVP_ERR_ARG, "soft particles need the neo-Hookean model");
@@ -333,7 +334,7 @@ int upload_tables(evp_state* s) {
     if (g.walls_y) {
         // Thomas table (m_j, c'_j) per (kz <= nz/2, kx), built in FP64
         const std::vector<double> M = thomas_table(g.ny, g.nz, nxh, dy, lx, lam(g.nz, g.nz / 2 + 1, dz));
-        if (sizeof(T) == 4) {
+        if (sizeof(T) == 4 && !s->prm.thomas_fp64) {
             // single-precision states sweep in double-single arithmetic (k_thomas)
             const std::vector<float> F = thomas_table_ds(M);
             CK(cudaMemcpyAsync(s->thomas_m, F.data(), F.size() * sizeof(float), cudaMemcpyHostToDevice, s->st));
@@ -406,7 +407,7 @@ int prepare_helmholtz(evp_state* s, double dt) {
     for (int k = 0; k < 3; ++k)
         for (int q = 0; q < 2; ++q) {
             const std::vector<double> M = helmholtz_table(g.ny, g.nz, nxh, dy, lx, lz, RK3_ALPHA_H[k] * dt * mu_s, q == 1);
-            if (s->fp32) {
+            if (s->fp32 && !s->prm.thomas_fp64) {
                 const std::vector<float> F = thomas_table_ds(M);
                 CK(cudaMemcpy(s->helm[k][q], F.data(), F.size() * sizeof(float), cudaMemcpyHostToDevice));
             } else {

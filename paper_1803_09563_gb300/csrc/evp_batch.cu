@@ -210,7 +210,8 @@ int prepare(evp_batch* b) {
         put(b->momentum, 0);
         bool placed = false;
         for (auto& gr : b->groups)
-            if (same_grid(b->m[gr.idx[0]].s->g, s->g)) {
+            if (same_grid(b->m[gr.idx[0]].s->g, s->g) &&
+                b->m[gr.idx[0]].s->prm.thomas_fp64 == s->prm.thomas_fp64) {   // same Thomas tables
                 gr.idx.push_back(i);
                 placed = true;
                 break;

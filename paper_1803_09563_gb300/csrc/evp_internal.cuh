@@ -220,6 +220,8 @@ struct FFTTables {
     const T* lamy;
     const T* lamz;
     const double2* thomas_m;  // walls: (m_j, c'_j) per system, [nz/2+1][ny][nxh]
+    int thomas_ds = 0;        // single precision: the table (and the Helmholtz tables) in the
+                              // double-single format of thomas_table_ds, swept so
     double idy2;              // walls: 1/dy^2 in FP64 (the Thomas sub-diagonal)
 };
 

@@ -135,6 +135,7 @@ inline FFTTables<T> tables_of(const evp_state* s) {
     t.lamy = static_cast<const T*>(s->lamy);
     t.lamz = static_cast<const T*>(s->lamz);
     t.thomas_m = s->thomas_m;
+    t.thomas_ds = s->fp32 && !s->prm.thomas_fp64;
     const double dy = s->g.ly / s->g.ny;
     t.idy2 = 1.0 / (dy * dy);
     return t;

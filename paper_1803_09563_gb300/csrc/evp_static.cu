@@ -154,6 +154,7 @@ int solve_static(const evp_grid& g, unsigned char* base, const StaticLayout& L, 
     tb.lamy = reinterpret_cast<const T*>(base + L.lamy);
     tb.lamz = reinterpret_cast<const T*>(base + L.lamz);
     tb.thomas_m = g.walls_y ? reinterpret_cast<const double2*>(base + L.thm) : nullptr;
+    tb.thomas_ds = sizeof(T) == 4 ? 1 : 0;
     const double dy = g.ly / g.ny;
     tb.idy2 = 1.0 / (dy * dy);
     PoissonArgs<T> a;

@@ -876,8 +876,12 @@ template <typename T>
 __device__ __forceinline__ void k_thomas_body(const Geo<T>& g, const FFTTables<T>& tb, const PoissonArgs<T>& a) {
     pdl_wait();
     pdl_trigger();
-    if constexpr (sizeof(T) == 4) thomas_ds_body(g, tb, a);
-    else thomas_fp64_body<T>(g, tb, a);
+    if constexpr (sizeof(T) == 4) {
+        if (tb.thomas_ds) thomas_ds_body(g, tb, a);
+        else thomas_fp64_body<T>(g, tb, a);
+    } else {
+        thomas_fp64_body<T>(g, tb, a);
+    }
 }
 template <typename T>
 __global__ void __launch_bounds__(32)

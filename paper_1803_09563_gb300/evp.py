@@ -50,7 +50,7 @@ class evp_params(ctypes.Structure):
                 ('sigma', c_double), ('drho_g', c_double), ('reinit_every', c_int), ('reinit_iters', c_int),
                 ('rho_ratio', c_double), ('gravity', c_double), ('penalization', c_int),
                 ('art_diff', c_double), ('ls_mass_iters', c_int), ('viscous_implicit', c_int),
-                ('soft_particles', c_int), ('reserved', c_double * 4)]
+                ('soft_particles', c_int), ('thomas_fp64', c_int), ('reserved', c_double * 4)]
 
 
 class EvpError(RuntimeError):
@@ -185,7 +185,7 @@ def make_grid(nx, ny, nz, lx, ly, lz, walls_y=False):
 def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_amp=0.0, abc_k=0.0,
                 precision=EVP_FP64, integrator=EVP_RK3, mu_ratio=1.0, ls_eps_cells=1.5, sigma=0.0, drho_g=0.0,
                 reinit_every=10, reinit_iters=3, penalization=0, rho_ratio=0.0, gravity=0.0, art_diff=0.0,
-                ls_mass_iters=0, viscous_implicit=0, soft_particles=0):
+                ls_mass_iters=0, viscous_implicit=0, soft_particles=0, thomas_fp64=0):
     p = evp_params()
     p.Re, p.Wi, p.beta, p.Bi, p.L2 = float(Re), float(Wi), float(beta), float(Bi), float(L2)
     p.bi_def, p.dpdx, p.abc_amp, p.abc_k = int(bi_def), float(dpdx), float(abc_amp), float(abc_k)
@@ -198,6 +198,7 @@ def make_params(Re, Wi=1.0, beta=1.0, Bi=0.0, L2=0.0, bi_def=0, dpdx=0.0, abc_am
     p.ls_mass_iters = int(ls_mass_iters)
     p.viscous_implicit = int(viscous_implicit)
     p.soft_particles = int(soft_particles)
+    p.thomas_fp64 = int(thomas_fp64)
     return p
 
 

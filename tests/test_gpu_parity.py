@@ -822,23 +822,28 @@ def test_poisson_solve_power_of_two_sizes(evp, shape, prec, tol):
     assert rel(got, ref) < tol, (shape, prec, rel(got, ref))
 
 
+@pytest.mark.parametrize("thomas_fp64", [0, 1])
 @pytest.mark.parametrize("shape", [(16, 512, 8, True), (32, 128, 16, True), (8, 36, 8, True)])
-def test_fp32_wall_solve_of_the_lowest_modes_is_rounding_exact(evp, shape):
+def test_fp32_wall_solve_of_the_lowest_modes_is_rounding_exact(evp, shape, thomas_fp64):
     """The (kx, kz) = (0, 0) system of a wall-bounded solve is the pinned 1-D
     Neumann Laplacian, whose condition number grows like ny^2 (about 1e5 at 512
     rows): a plain FP32 sweep loses about five digits on it.  A right-hand side
     that varies in y only reaches the FP32 solve through exact x and z
     transforms, so the FP32 result must be the FP64 solution of the same
     (FP32-rounded) data rounded once: within 2 ulps of the oracle, and within 1
-    ulp of the FP64 state's own solve."""
+    ulp of the FP64 state's own solve; with the double-single sweep (default) and
+    with the FP64 sweep (thomas_fp64 = 1)."""
     import torch
     nx, ny, nz, walls = shape
     rng = np.random.default_rng(21)
     prof = rng.standard_normal(ny) + np.cos(np.pi * (np.arange(ny) + 0.5) / ny)
     r = np.ascontiguousarray(np.broadcast_to(prof[None, :, None], (nz, ny, nx)), dtype=np.float32).astype(np.float64)
+    geo = inputs.geometry(nx, ny, nz, 2 * np.pi, 2.0, 2 * np.pi, walls)
+    g = oracle.Grid(nx, ny, nz, geo['lx'], geo['ly'], geo['lz'], walls)
     out = {}
     for prec in (evp.EVP_FP32, evp.EVP_FP64):
-        sim, st, g, prm = setup_case(evp, shape, 'oldroyd_b', {}, prec)
+        sim = evp.Simulation(evp.make_grid(nx, ny, nz, geo['lx'], geo['ly'], geo['lz'], walls), 'oldroyd_b',
+                             evp.make_params(Re=2.0, Wi=0.8, beta=0.4, precision=prec, thomas_fp64=thomas_fp64))
         rd = torch.tensor(r, dtype=torch.float32 if prec else torch.float64, device='cuda').contiguous()
         psi = torch.empty(rd.shape, dtype=rd.dtype, device='cuda')
         evp.evp_poisson_solve(sim.handle, rd, psi)
@@ -850,6 +855,30 @@ def test_fp32_wall_solve_of_the_lowest_modes_is_rounding_exact(evp, shape):
     ulp = np.spacing(np.float32(scale)).astype(np.float64)
     assert np.abs(out[evp.EVP_FP32] - ref).max() <= 2 * ulp, np.abs(out[evp.EVP_FP32] - ref).max() / ulp
     assert np.abs(out[evp.EVP_FP32] - out[evp.EVP_FP64]).max() <= ulp
+
+
+def test_fp32_thomas_sweeps_agree(evp):
+    """An FP32 channel stepped with the double-single and with the FP64 Thomas
+    sweep: the two runs' fields agree to FP32 rounding after three steps."""
+    out = []
+    for t in (0, 1):
+        nx, ny, nz, walls = SHAPES[1]
+        sim, st, g, prm = setup_case(evp, SHAPES[1], 'saramito', {'Bi': 0.4}, evp.EVP_FP32)
+        sim.close()
+        geo = inputs.geometry(nx, ny, nz, 2 * np.pi, 2.0, 2 * np.pi, walls)
+        sim = evp.Simulation(evp.make_grid(nx, ny, nz, geo['lx'], geo['ly'], geo['lz'], walls), 'saramito',
+                             evp.make_params(Re=2.0, Wi=0.8, beta=0.4, Bi=0.4, precision=evp.EVP_FP32,
+                                             thomas_fp64=t))
+        sim.set_state(st.U, st.V, st.W, st.p, st.B)
+        for _ in range(3):
+            sim.step(2e-3)
+        sim.sync()
+        out.append(fields(sim, evp))
+        sim.close()
+    for q, (a, b) in enumerate(zip(*out)):
+        # the pressure accumulates psi, which carries the FP32 rounding of u*/dt
+        tol = 1e-5 if q == 3 else 1e-6
+        assert rel(a, b.astype(np.float64)) < tol, (q, rel(a, b.astype(np.float64)))
 
 
 def test_fene_p_trace_limit_is_reported(evp):
