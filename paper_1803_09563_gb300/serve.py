@@ -17,7 +17,10 @@ steps of its own size class only, never for the largest grid resident.
 Reported per request-step: the step latency (device time from the start to the
 end of the class step that advanced it, CUDA events) and, per request, the
 queueing delay from its arrival to its admission (host clock).  Throughput is
-cell-steps over the whole run.
+cell-steps over the whole run.  Each result carries the final state's status,
+FP64 divergence residual and monitoring quantities (evp_diagnostics: kinetic
+energy, det B and tr B extremes, yielded fraction, non-finite cells) beside the
+requested fields.
 
 The loop is host logic only: every step of every simulation runs in libevp's
 kernels through the C ABI.
@@ -181,6 +184,7 @@ class Server:
                             c.batch.evict(inst.sim)
                             code, bits, maxdiv = inst.sim.sync(raise_on_error=False)
                             results[inst.req.rid] = dict(code=code, bits=bits, max_div=maxdiv,
+                                                         diagnostics=inst.sim.diagnostics(),
                                                          fields={f: inst.sim.get(f) for f in self.result_fields})
                             inst.sim.close()
                             used -= inst.bytes

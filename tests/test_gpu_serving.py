@@ -28,6 +28,14 @@ def test_result_alone_equals_result_in_the_mix(evp):
             b = mixed[r.rid]['fields'][f]
             assert np.array_equal(a, b), (r.rid, f)
         assert mixed[r.rid]['code'] == 0
+        # the monitoring quantities travel with the result, the same alone and in the mix
+        d = mixed[r.rid]['diagnostics']
+        assert d == alone[r.rid]['diagnostics']
+        assert d['nonfinite_cells'] == 0 and d['min_det_B'] > 0 and 0.0 <= d['yielded_fraction'] <= 1.0
+        U, V, W = (mixed[r.rid]['fields'][f].astype(np.float64) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W))
+        dv = (2 * np.pi / r.n) ** 3
+        assert d['kinetic_energy'] == pytest.approx(0.5 * dv * (np.sum(U * U) + np.sum(V * V) + np.sum(W * W)),
+                                                    rel=1e-12)
 
 
 def test_admission_respects_the_budget(evp):
