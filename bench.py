@@ -344,7 +344,7 @@ def run_gpu(args, rank, world, local_rank):
     for f, h in zip(fields_io, host_a):
         evp.evp_get_field(sim.handle, f, h.numpy())
     # further replicas start from the same state, each on its own stream
-    NREP = 3
+    NREP = 4
     pair = [sim]
     host = [host_a]
     grid_w = evp.make_grid(w['nx'], w['ny'], w['nz'], w['lx'], w['ly'], w['lz'], w['walls_y'])
@@ -372,6 +372,16 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_s = max_ranks(time.perf_counter() - t0)
     e2e_value = job_rate(N, e2e_steps, world, e2e_s)
+    # the same calls on one replica: its copies and steps follow each other on its
+    # stream, with nothing to overlap them (what the replicas buy)
+    one_steps = max(8, e2e_steps // 8)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(one_steps):
+        evp.evp_step_io(pair[0].handle, w['dt'], io[0])
+    torch.cuda.synchronize()
+    one_value = job_rate(N, one_steps, world, max_ranks(time.perf_counter() - t0))
     io_bytes = len(fields_io) * N * 4
     fp32_fields = [sim.get(f) for f in fields_io]
     for sr in pair:
@@ -393,7 +403,7 @@ def run_gpu(args, rank, world, local_rank):
     ms64 = max_ranks(e0.elapsed_time(e1))
     value64 = job_rate(N, n64, world, ms64 * 1e-3)
     # accuracy of FP32-served against FP64 plain after the same number of steps
-    steps_done = args.warmup + args.steps + k_steps + e2e_steps // NREP
+    steps_done = args.warmup + args.steps + k_steps + e2e_steps // NREP + one_steps
     sim64.close()
     sim64 = make(evp.EVP_FP64)
     for _ in range(steps_done):
@@ -429,7 +439,10 @@ def run_gpu(args, rank, world, local_rank):
                 "how": f"evp_step_io: {NREP} replicas of the state on their own streams step in turn; each step "
                        "copies its 10 fields in from pinned host memory, takes one RK3 step and copies them back "
                        "out, so one replica's copies overlap another's step; host-clock time from the first call "
-                       "to the final synchronisation"},
+                       "to the final synchronisation",
+                "one_replica": {"value": one_value, "steps": one_steps,
+                                "how": "the same evp_step_io calls on one replica: copies in, step and copies out "
+                                       "follow each other on its stream"}},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
