@@ -123,13 +123,14 @@ def test_diagnostics_after_steps_follow_the_oracle(evp):
     sim.close()
 
 
-def test_batch_member_diagnostics_wait_for_the_batch(evp):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_member_diagnostics_wait_for_the_batch(evp, precision):
     """A member's diagnostics after a batch step equal those of the same state
     stepped alone (the batch gives the member's own evp_step bit for bit)."""
     shape = (32, 16, 16, True)
-    alone = _case(evp, shape, 'saramito', None, evp.EVP_FP32, seed=11)[0]
-    member = _case(evp, shape, 'saramito', None, evp.EVP_FP32, seed=11)[0]
-    batch = evp.Batch(evp.EVP_FP32)
+    alone = _case(evp, shape, 'saramito', None, precision, seed=11)[0]
+    member = _case(evp, shape, 'saramito', None, precision, seed=11)[0]
+    batch = evp.Batch(precision)
     batch.admit(member, 1e-3)
     for _ in range(3):
         alone.step(1e-3)
@@ -143,13 +144,15 @@ def test_batch_member_diagnostics_wait_for_the_batch(evp):
     member.close()
 
 
-def test_two_phase_state_reads_its_current_buffers(evp):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_phase_state_reads_its_current_buffers(evp, precision):
     """An AB2 drop after two steps: the energy and the conformation extremes are
-    those of the fields evp_get_field returns."""
+    those of the fields evp_get_field returns (FP32 fields widened, as the
+    reductions do)."""
     nx = ny = nz = 32
     L = 2.0
     grid = evp.make_grid(nx, ny, nz, L, L, L, walls_y=True)
-    prm = evp.make_params(Re=10.0, Wi=0.5, beta=0.5, Bi=0.3, precision=evp.EVP_FP64, integrator=evp.EVP_AB2,
+    prm = evp.make_params(Re=10.0, Wi=0.5, beta=0.5, Bi=0.3, precision=precision, integrator=evp.EVP_AB2,
                           mu_ratio=1.0, ls_eps_cells=1.5, sigma=0.1, drho_g=1.0, reinit_every=0)
     sim = evp.Simulation(grid, 'saramito', prm)
     geo = inputs.geometry(nx, ny, nz, L, L, L, True)
@@ -158,8 +161,9 @@ def test_two_phase_state_reads_its_current_buffers(evp):
         sim.step(1e-3)
     sim.sync()
     got = sim.diagnostics()
-    U, V, W = (sim.get(f) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W))
-    B = [sim.get(f) for f in (evp.EVP_BXX, evp.EVP_BXY, evp.EVP_BXZ, evp.EVP_BYY, evp.EVP_BYZ, evp.EVP_BZZ)]
+    U, V, W = (sim.get(f).astype(np.float64) for f in (evp.EVP_U, evp.EVP_V, evp.EVP_W))
+    B = [sim.get(f).astype(np.float64)
+         for f in (evp.EVP_BXX, evp.EVP_BXY, evp.EVP_BXZ, evp.EVP_BYY, evp.EVP_BYZ, evp.EVP_BZZ)]
     dv = (L / nx) ** 3
     ke = 0.5 * dv * (np.sum(U * U) + np.sum(V * V) + np.sum(W * W))
     assert got['kinetic_energy'] == pytest.approx(ke, rel=1e-12)

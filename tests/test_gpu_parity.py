@@ -857,9 +857,11 @@ def test_fp32_wall_solve_of_the_lowest_modes_is_rounding_exact(evp, shape, thoma
     assert np.abs(out[evp.EVP_FP32] - out[evp.EVP_FP64]).max() <= ulp
 
 
-def test_fp32_thomas_sweeps_agree(evp):
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_fp32_thomas_sweeps_agree(evp, implicit):
     """An FP32 channel stepped with the double-single and with the FP64 Thomas
-    sweep: the two runs' fields agree to FP32 rounding after three steps."""
+    sweep (with the implicit viscous option: the Helmholtz tables too): the two
+    runs' fields agree to FP32 rounding after three steps."""
     out = []
     for t in (0, 1):
         nx, ny, nz, walls = SHAPES[1]
@@ -868,7 +870,7 @@ def test_fp32_thomas_sweeps_agree(evp):
         geo = inputs.geometry(nx, ny, nz, 2 * np.pi, 2.0, 2 * np.pi, walls)
         sim = evp.Simulation(evp.make_grid(nx, ny, nz, geo['lx'], geo['ly'], geo['lz'], walls), 'saramito',
                              evp.make_params(Re=2.0, Wi=0.8, beta=0.4, Bi=0.4, precision=evp.EVP_FP32,
-                                             thomas_fp64=t))
+                                             thomas_fp64=t, viscous_implicit=implicit))
         sim.set_state(st.U, st.V, st.W, st.p, st.B)
         for _ in range(3):
             sim.step(2e-3)
